@@ -1,0 +1,189 @@
+/*
+ * ffcz.h -- C ABI of the FFCz alternating-projection library for B300 (sm_103a).
+ *
+ * The library edits a lossy compressor's spatial error vector e = x_hat - x
+ * until it lies in both the s-cube |e_n| <= eps_s and the f-cube
+ * |Re delta_k| <= eps_f, |Im delta_k| <= eps_f, where delta = DFT(e) is the
+ * unnormalised DFT of Eq. 1 and its nD analogue (Sec. III, Sec. IV-A,
+ * constraints_v1).  The loop is Alg. 1 (Sec. IV-B): forward FFT, feasibility
+ * check, f-cube clip, inverse FFT, s-cube clip.
+ *
+ * Conventions shared by every call
+ *  - Device pointers are CUDA global-memory addresses on the device that was
+ *    current when the plan was made.  The caller owns them; the library never
+ *    frees or retains them after a call returns.
+ *  - The plan owns all of its workspace (spectrum buffers, loop state).
+ *  - All work is ordered on the plan's stream.  Each call blocks the calling
+ *    host thread until its stream work is done and its stats are written.
+ *  - Errors never cross the ABI as exceptions: every call returns an
+ *    ffcz_status; ffcz_last_error() gives a detail string for the calling
+ *    thread's most recent failure.
+ *  - A field is row-major with the LAST axis contiguous.  Supported items:
+ *    2D and 3D with every axis a power of two, each axis length in [8, 1024]
+ *    and the last axis in [16, 2048].  Other shapes return
+ *    FFCZ_ERR_UNSUPPORTED.
+ *  - Batches: `batch` items of one rank `ndim`; item i has the shape
+ *    shapes[i*ndim .. i*ndim+ndim-1]; items are packed back to back in the
+ *    float32 buffer, item i starting after the elements of items 0..i-1.
+ *    Every item runs its own loop and stops on its own (Alg. 1 per item).
+ */
+#ifndef FFCZ_H_
+#define FFCZ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffcz_plan_s* ffcz_plan_t;
+
+typedef enum {
+  FFCZ_OK = 0,
+  FFCZ_ERR_INVALID = 1,        /* bad argument (null pointer, bad bound, ...) */
+  FFCZ_ERR_UNSUPPORTED = 2,    /* shape or option the library does not handle */
+  FFCZ_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  FFCZ_ERR_NOT_CONVERGED = 4,  /* max_iters reached; the last iterate is in e */
+  FFCZ_ERR_CERT_FAILED = 5,    /* FP64 certification failed after all repairs */
+  FFCZ_ERR_NONFINITE = 6,      /* NaN or Inf met in e or in its spectrum */
+  FFCZ_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+  FFCZ_ERR_OOM = 8             /* workspace allocation failed */
+} ffcz_status;
+
+/* Options.  Fill with ffcz_default_opts() and change what you need. */
+typedef struct {
+  int32_t max_iters;   /* iteration cap (the paper loops without one); default 10000 */
+  int32_t min_iters;   /* do not stop before this many iterations (forced runs); 0 */
+  double shrink;       /* eta: clip to E(1-eta), Delta(1-eta), stop when the
+                          violation <= Delta(1-eta/2) (bound shrink of Sec. IV-B,
+                          m = 16); default 2^-16 */
+  int32_t precision;   /* 32: FP32 loop (default); 64: FP64 loop */
+  int32_t certify;     /* 1 (default): FP64 certification after the loop */
+  int32_t max_repairs; /* FP64 repair rounds when certification fails; default 2 */
+  int32_t K;           /* backward: number of forced forward iterations; 50 */
+  int32_t ckpt_every;  /* backward: checkpoint interval m; 10 */
+  int32_t chunk;       /* max iterations launched between host checks; 16 */
+  int32_t use_graph;   /* 1 (default): replay loop chunks as CUDA graphs */
+} ffcz_opts;
+
+/* Per-item results. */
+typedef struct {
+  int32_t status;      /* ffcz_status of this item */
+  int32_t iters;       /* (f-clip, s-clip) pairs executed */
+  int32_t repairs;     /* FP64 repair rounds run */
+  int32_t certified;   /* 1 if the FP64 check passed against the true bounds */
+  int32_t preclipped;  /* 1 if e0 was outside the s-cube and was clipped first */
+  int32_t pad_;
+  double f_ratio;      /* last loop violation / eps_f (working precision) */
+  double s_ratio;      /* max|e| / eps_s after the call (FP64 check) */
+  double f_margin64;   /* 1 - (FP64 violation + FP64 FFT error bound) / eps_f */
+  double s_margin64;   /* 1 - max|e| / eps_s (exact) */
+  int64_t active_s;    /* points moved by the last s-clip */
+  int64_t active_f;    /* full-spectrum bins moved by the last f-clip */
+  float ms_total;      /* device time of the whole call, milliseconds */
+  float ms_cert;       /* device time of certification, milliseconds */
+} ffcz_stats;
+
+/* Fill *opts with the defaults listed above. */
+void ffcz_default_opts(ffcz_opts* opts);
+
+/*
+ * ffcz_plan -- validate the shapes, size and allocate the workspace, upload
+ * the FP64-derived twiddle tables and bind the plan to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).
+ *   out     : receives the plan handle (owned by the caller; ffcz_destroy)
+ *   ndim    : 2 or 3
+ *   shapes  : host array of batch*ndim extents (see the batch convention)
+ *   batch   : number of items, >= 1
+ *   opts    : NULL for defaults; copied into the plan
+ * Errors: INVALID (null out, ndim/batch out of range), UNSUPPORTED (shape),
+ * OOM, CUDA.
+ * Workspace: two float32 spectrum buffers (4 bytes per point each), one FP64
+ * spectrum buffer for certification (8 bytes per point) and, when precision
+ * 64 or a repair needs them, two FP64 loop buffers (allocated on first use).
+ */
+ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes,
+                      int64_t batch, const ffcz_opts* opts, void* cuda_stream);
+
+/* Rebind the plan to another stream (e.g. torch's current stream). */
+ffcz_status ffcz_set_stream(ffcz_plan_t plan, void* cuda_stream);
+
+/* Bytes of device workspace the plan holds now. */
+size_t ffcz_workspace_bytes(ffcz_plan_t plan);
+
+/*
+ * ffcz_correct -- Alg. 1 on every item, in place.
+ *   e_dev  : device float32, the packed items; in: e0 = x_hat - x (Alg. 1,
+ *            first step); out: the corrected error e*.  x_hat' = x + e*.
+ *   eps_s  : host array[batch], spatial bounds E > 0 (constraints_v1)
+ *   eps_f  : host array[batch], frequency bounds Delta > 0 in unnormalised DFT
+ *            units (constraints_v1; Eq. 1 scaling)
+ *   stats  : host array[batch] or NULL
+ * Before the loop, an item with some |e0_n| > E is clipped to E(1-eta)
+ * (the paper assumes e0 starts in the s-cube).  An item that is already
+ * feasible returns after 0 iterations with e bit-identical.  On
+ * NOT_CONVERGED the last iterate is left in e.  With certify = 1 the result
+ * is checked in FP64 (see ffcz_check) and, on failure, refined by FP64
+ * iterations (at most max_repairs rounds).
+ * Returns the worst item status (OK < NOT_CONVERGED < CERT_FAILED <
+ * NONFINITE) or a call-level error.
+ */
+ffcz_status ffcz_correct(ffcz_plan_t plan, float* e_dev, const double* eps_s,
+                         const double* eps_f, ffcz_stats* stats);
+
+/*
+ * ffcz_correct_host -- ffcz_correct on host memory: copies e_host to the
+ * plan's device staging buffer, corrects, copies the result back.
+ * e_host may be pageable or pinned; it is read and written in place.
+ */
+ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps_s,
+                              const double* eps_f, ffcz_stats* stats);
+
+/*
+ * ffcz_check -- FP64 certification of e against the TRUE bounds
+ * (constraints_v1 with <=): max|e_n| <= E and, for every DFT bin,
+ * max(|Re|, |Im|) + b <= Delta, where b is a rigorous bound on the FP64 FFT's
+ * rounding error (error analysis of Cooley-Tukey FFTs: log2(N) stages of
+ * radix-2/4/8 butterflies with correctly rounded twiddles).
+ * Does not modify e.  stats[i].certified, s_ratio, f_margin64, s_margin64 are
+ * filled.  Returns OK if every item passes, CERT_FAILED otherwise.
+ */
+ffcz_status ffcz_check(ffcz_plan_t plan, const float* e_dev, const double* eps_s,
+                       const double* eps_f, ffcz_stats* stats);
+
+/*
+ * ffcz_correct_backward -- vector-Jacobian product of e0 -> e_K, where e_K
+ * is the result of exactly K forced iterations (opts.K; min_iters = max_iters
+ * = K; no certification).  One step e <- P_s(IDFT(P_f(DFT(e)))) has the
+ * Jacobian M_s IDFT M_f DFT; IDFT M_f DFT is symmetric in the real frequency
+ * basis of Sec. IV-A, so the transposed step is g <- IDFT(M_f DFT(M_s g)).
+ * M_s, M_f are the clips' active-set masks (1 where |value| <= bound).  The
+ * masks are regenerated by replaying the forward from float32 checkpoints of
+ * e taken every opts.ckpt_every iterations.
+ *   e0_dev       : device float32 input of the forward (not modified)
+ *   grad_out_dev : device float32 dL/de_K
+ *   grad_in_dev  : device float32 output dL/de0 (may not alias the others)
+ * Single-item plans only (batch == 1); else UNSUPPORTED.
+ */
+ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0_dev,
+                                  const float* grad_out_dev, float* grad_in_dev,
+                                  const double* eps_s, const double* eps_f);
+
+/* Release the plan and its workspace.  NULL is ignored. */
+void ffcz_destroy(ffcz_plan_t plan);
+
+/* Static description of a status code. */
+const char* ffcz_strerror(ffcz_status status);
+
+/* Detail of the calling thread's most recent failure ("" if none). */
+const char* ffcz_last_error(void);
+
+/* Number of kernel launches issued by this process so far (all plans). */
+int64_t ffcz_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFCZ_H_ */

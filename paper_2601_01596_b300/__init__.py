@@ -1,0 +1,215 @@
+"""FFCz on B300: Python binding of the C-ABI library ``libffcz.so``.
+
+Argument marshalling only: every step of the correction runs in the CUDA
+kernels behind the C ABI (``include/ffcz.h``).  PyTorch provides device
+memory and the current stream.  There is no CPU fallback: if the library is
+missing or no GPU is present, the calls raise.
+
+    import paper_2601_01596_b300 as ffcz
+    plan = ffcz.Plan([(512, 512, 512)])
+    stats = plan.correct(e, eps_s, eps_f)      # e: float32 CUDA tensor, in place
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libffcz.so")
+
+OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_CUDA = 0, 1, 2, 3
+ERR_NOT_CONVERGED, ERR_CERT_FAILED, ERR_NONFINITE, ERR_TIMEOUT, ERR_OOM = 4, 5, 6, 7, 8
+
+SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_bytes",
+           "ffcz_correct", "ffcz_correct_host", "ffcz_check", "ffcz_correct_backward",
+           "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("min_iters", ctypes.c_int32),
+                ("shrink", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("certify", ctypes.c_int32), ("max_repairs", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("repairs", ctypes.c_int32), ("certified", ctypes.c_int32),
+                ("preclipped", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("f_ratio", ctypes.c_double), ("s_ratio", ctypes.c_double),
+                ("f_margin64", ctypes.c_double), ("s_margin64", ctypes.c_double),
+                ("active_s", ctypes.c_int64), ("active_f", ctypes.c_int64),
+                ("ms_total", ctypes.c_float), ("ms_cert", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libffcz.so`` (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2601_01596_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        L.ffcz_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.ffcz_default_opts.restype = None
+        L.ffcz_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ctypes.c_int64), i64,
+                                ctypes.POINTER(Opts), vp]
+        L.ffcz_set_stream.argtypes = [vp, vp]
+        L.ffcz_workspace_bytes.argtypes = [vp]
+        L.ffcz_workspace_bytes.restype = ctypes.c_size_t
+        L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
+        L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
+        L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
+        L.ffcz_correct_backward.argtypes = [vp, vp, vp, vp, dp, dp]
+        L.ffcz_destroy.argtypes = [vp]
+        L.ffcz_destroy.restype = None
+        L.ffcz_strerror.argtypes = [i32]
+        L.ffcz_strerror.restype = ctypes.c_char_p
+        L.ffcz_last_error.restype = ctypes.c_char_p
+        L.ffcz_launch_count.restype = ctypes.c_int64
+        for name in ("ffcz_plan", "ffcz_set_stream", "ffcz_correct", "ffcz_correct_host",
+                     "ffcz_check", "ffcz_correct_backward"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class FFCzError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        msg = lib().ffcz_strerror(status).decode()
+        super().__init__(f"{msg} (status {status}){': ' + detail if detail else ''}")
+
+
+def _check(status: int, allow=()) -> int:
+    if status != OK and status not in allow:
+        raise FFCzError(status, lib().ffcz_last_error().decode())
+    return status
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().ffcz_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def launch_count() -> int:
+    return int(lib().ffcz_launch_count())
+
+
+def _dbl(values, n):
+    if isinstance(values, (int, float)):
+        values = [float(values)] * n
+    values = [float(v) for v in values]
+    if len(values) != n:
+        raise ValueError(f"expected {n} bounds, got {len(values)}")
+    return (ctypes.c_double * n)(*values)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """A plan for a batch of fields of one rank (2D or 3D), each axis a power
+    of two.  ``shapes``: list of per-item shapes.  Options as in ffcz_opts."""
+
+    def __init__(self, shapes: Sequence[Sequence[int]], stream=None, **opts):
+        shapes = [tuple(int(n) for n in s) for s in shapes]
+        if not shapes:
+            raise ValueError("no items")
+        ndim = len(shapes[0])
+        if any(len(s) != ndim for s in shapes):
+            raise ValueError("all items must have the same rank")
+        self.shapes = shapes
+        self.ndim = ndim
+        self.batch = len(shapes)
+        self.sizes = [int(__import__("math").prod(s)) for s in shapes]
+        self.total = sum(self.sizes)
+        self.opts = default_opts(**opts)
+        flat = (ctypes.c_int64 * (self.batch * ndim))(*[n for s in shapes for n in s])
+        h = ctypes.c_void_p()
+        _check(lib().ffcz_plan(ctypes.byref(h), ndim, flat, self.batch, ctypes.byref(self.opts),
+                               ctypes.c_void_p(_stream_ptr(stream))))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.ffcz_destroy(h)
+            self._h = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().ffcz_workspace_bytes(self._h))
+
+    def _bind_stream(self, stream=None):
+        _check(lib().ffcz_set_stream(self._h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def _ptr(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+            raise TypeError(f"{name} must be a float32 CUDA tensor")
+        if not t.is_contiguous() or t.numel() != self.total:
+            raise ValueError(f"{name} must be contiguous with {self.total} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def correct(self, e, eps_s, eps_f, stream=None, allow=(ERR_NOT_CONVERGED, ERR_CERT_FAILED,
+                                                           ERR_NONFINITE)):
+        """Correct ``e`` (packed items, float32 CUDA) in place; per-item stats."""
+        self._bind_stream(stream)
+        st = (Stats * self.batch)()
+        s = lib().ffcz_correct(self._h, self._ptr(e, "e"), _dbl(eps_s, self.batch),
+                               _dbl(eps_f, self.batch), st)
+        _check(s, allow)
+        return [x.as_dict() for x in st]
+
+    def correct_host(self, e_np, eps_s, eps_f, allow=(ERR_NOT_CONVERGED, ERR_CERT_FAILED,
+                                                      ERR_NONFINITE)):
+        """Correct a float32 host array in place through the host-buffer entry point."""
+        import numpy as np
+        if not isinstance(e_np, np.ndarray) or e_np.dtype != np.float32 or \
+                not e_np.flags.c_contiguous or e_np.size != self.total:
+            raise TypeError("e_np must be a contiguous float32 array with all items")
+        st = (Stats * self.batch)()
+        s = lib().ffcz_correct_host(self._h, ctypes.c_void_p(e_np.ctypes.data),
+                                    _dbl(eps_s, self.batch), _dbl(eps_f, self.batch), st)
+        _check(s, allow)
+        return [x.as_dict() for x in st]
+
+    def check(self, e, eps_s, eps_f, stream=None):
+        """FP64 certification of ``e``; returns per-item stats (``certified``)."""
+        self._bind_stream(stream)
+        st = (Stats * self.batch)()
+        s = lib().ffcz_check(self._h, self._ptr(e, "e"), _dbl(eps_s, self.batch),
+                             _dbl(eps_f, self.batch), st)
+        _check(s, (ERR_CERT_FAILED,))
+        return [x.as_dict() for x in st]
+
+    def backward(self, e0, grad_out, grad_in, eps_s, eps_f, stream=None):
+        """grad_in <- (d e_K / d e0)^T grad_out for K = opts.K forced iterations."""
+        self._bind_stream(stream)
+        _check(lib().ffcz_correct_backward(self._h, self._ptr(e0, "e0"),
+                                           self._ptr(grad_out, "grad_out"),
+                                           self._ptr(grad_in, "grad_in"),
+                                           _dbl(eps_s, 1), _dbl(eps_f, 1)))
+
+
+def correct(e, eps_s, eps_f, **opts):
+    """One-shot correction of a single field ``e`` (float32 CUDA tensor) in place."""
+    p = Plan([tuple(e.shape)], **opts)
+    return p.correct(e.reshape(-1), [eps_s], [eps_f])[0]

@@ -1,0 +1,1035 @@
+// ffcz.cu -- plan, executor and C ABI of the FFCz correction library.
+//
+// Host side of the hot path of Alg. 1 (Sec. IV-B) and its GPU mapping
+// (Sec. IV-D): every step runs in the kernels of passes.cuh; the host only
+// sequences launches, replays loop chunks as CUDA graphs and reads one
+// 4-byte "items still running" counter between chunks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ffcz.h"
+#include "passes.cuh"
+
+using namespace ffcz;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+struct Fail {
+  ffcz_status s;
+};
+
+void fail(ffcz_status s, const std::string& msg) {
+  g_err = msg;
+  throw Fail{s};
+}
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      fail(e_ == cudaErrorMemoryAllocation ? FFCZ_ERR_OOM : FFCZ_ERR_CUDA,        \
+           std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                             \
+  } while (0)
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// exp(-2 pi i m / L) for m < L, from long double sin/cos, rounded once.
+template <typename T>
+std::vector<v2<T>> twiddles(int L) {
+  std::vector<v2<T>> t(L);
+  const long double pi = acosl(-1.0L);
+  for (int m = 0; m < L; ++m) {
+    long double a = 2.0L * pi * (long double)m / (long double)L;
+    long double c = cosl(a), s = -sinl(a);
+    if (fabsl(c) < 1e-18L) c = 0.0L;
+    if (fabsl(s) < 1e-18L) s = 0.0L;
+    t[m].x = (T)c;
+    t[m].y = (T)s;
+  }
+  return t;
+}
+
+struct DevGroup {
+  Group g;            // device pointers inside
+  int count;
+  int ndim, Nz, Ny, Nx, M;
+  int64_t rows, n;
+};
+
+struct Tables {
+  // per power of two L = 2^p (p = 3..11): forward twiddles
+  void* f32[12] = {};
+  void* f64[12] = {};
+};
+
+template <typename T>
+const void* tw_of(const Tables& tb, int L) {
+  const int p = ilog2(L);
+  return sizeof(T) == 4 ? tb.f32[p] : tb.f64[p];
+}
+
+}  // namespace
+
+struct ffcz_plan_s {
+  int ndim = 0;
+  int64_t batch = 0;
+  std::vector<int64_t> shapes;
+  std::vector<int64_t> eoff;   // float offset per item
+  int64_t total = 0;           // floats
+  ffcz_opts opts{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+  int device = 0;
+
+  std::vector<DevGroup> groups;
+  std::vector<void*> allocs;
+  Tables tb;
+
+  void* B32[2] = {nullptr, nullptr};
+  void* B64[2] = {nullptr, nullptr};
+  void* Bc = nullptr;
+  float* staging = nullptr;
+  ItemParams* d_prm = nullptr;
+  ItemState* d_st = nullptr;
+  ItemState* d_st2 = nullptr;   // adjoint state
+  int* d_nactive = nullptr;
+  int* h_nactive = nullptr;     // pinned
+  ItemState* h_st = nullptr;    // pinned
+  ItemParams* h_prm = nullptr;  // pinned
+  size_t ws_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+
+  // graphs of loop chunks: key = (precision, chunk)
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  std::map<std::pair<int, int>, int> graph_nodes;
+
+  // backward workspace
+  float* bw_e = nullptr;
+  float* bw_ck = nullptr;
+  uint32_t* bw_smask = nullptr;
+  uint32_t* bw_fmask = nullptr;
+  void* bw_G[2] = {nullptr, nullptr};
+  int bw_K = -1, bw_m = -1;
+  int64_t px_words = 0, chk_words = 0;
+};
+
+namespace {
+
+void* dalloc(ffcz_plan_s* p, size_t bytes) {
+  void* ptr = nullptr;
+  CK(cudaMalloc(&ptr, bytes));
+  p->allocs.push_back(ptr);
+  p->ws_bytes += bytes;
+  return ptr;
+}
+
+template <typename Kern>
+void set_smem(Kern k, size_t bytes) {
+  if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+// When true, launch helpers only set kernel attributes (done once per plan,
+// before any graph capture).
+thread_local bool g_dry = false;
+
+// ----- kernel dispatch over the pencil length -------------------------------
+enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
+
+template <typename T, int M>
+void launch_x_t(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
+  using G_ = Geo<T, M>;
+  const int64_t tiles = rows / G_::W;
+  dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
+  const size_t sm = Smem<T, M>::bytes_x;
+  if (g_dry) {
+    set_smem(k_xfwd<T, M>, sm); set_smem(k_px<T, M>, sm); set_smem(k_xexit<T, M>, sm);
+    return;
+  }
+  switch (kind) {
+    case XFWD: k_xfwd<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XPX: k_px<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XEXIT: k_xexit<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
+  }
+  g_launches++;
+}
+
+template <typename T>
+void launch_x(XKind kind, int M, const Args& a, int64_t rows, int count, cudaStream_t s) {
+  switch (M) {
+    case 8: launch_x_t<T, 8>(kind, a, rows, count, s); break;
+    case 16: launch_x_t<T, 16>(kind, a, rows, count, s); break;
+    case 32: launch_x_t<T, 32>(kind, a, rows, count, s); break;
+    case 64: launch_x_t<T, 64>(kind, a, rows, count, s); break;
+    case 128: launch_x_t<T, 128>(kind, a, rows, count, s); break;
+    case 256: launch_x_t<T, 256>(kind, a, rows, count, s); break;
+    case 512: launch_x_t<T, 512>(kind, a, rows, count, s); break;
+    case 1024: launch_x_t<T, 1024>(kind, a, rows, count, s); break;
+    default: fail(FFCZ_ERR_UNSUPPORTED, "x length");
+  }
+}
+
+template <typename T, int L, int DIR>
+void launch_axis_t(const Args& a, int Nz, int M, int count, cudaStream_t s) {
+  using G_ = Geo<T, L>;
+  const int64_t tiles = (int64_t)Nz * (M / G_::W);
+  dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
+  const size_t sm = Smem<T, L>::bytes_axis;
+  if (g_dry) { set_smem(k_axis<T, L, DIR>, sm); return; }
+  k_axis<T, L, DIR><<<grid, G_::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+
+template <typename T, int DIR>
+void launch_axis(int L, const Args& a, int Nz, int M, int count, cudaStream_t s) {
+  switch (L) {
+    case 8: launch_axis_t<T, 8, DIR>(a, Nz, M, count, s); break;
+    case 16: launch_axis_t<T, 16, DIR>(a, Nz, M, count, s); break;
+    case 32: launch_axis_t<T, 32, DIR>(a, Nz, M, count, s); break;
+    case 64: launch_axis_t<T, 64, DIR>(a, Nz, M, count, s); break;
+    case 128: launch_axis_t<T, 128, DIR>(a, Nz, M, count, s); break;
+    case 256: launch_axis_t<T, 256, DIR>(a, Nz, M, count, s); break;
+    case 512: launch_axis_t<T, 512, DIR>(a, Nz, M, count, s); break;
+    case 1024: launch_axis_t<T, 1024, DIR>(a, Nz, M, count, s); break;
+    default: fail(FFCZ_ERR_UNSUPPORTED, "axis length");
+  }
+}
+
+template <typename T, int L>
+int64_t chk_tiles(int Nmid, int M) {
+  using G_ = Geo<T, L>;
+  const int64_t nmain = (int64_t)Nmid * (M / G_::W);
+  const int npairs = Nmid / 2 + 1;
+  return nmain + (npairs + G_::W / 2 - 1) / (G_::W / 2);
+}
+
+template <typename T, int L>
+void launch_chk_t(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+  using G_ = Geo<T, L>;
+  const int64_t tiles = chk_tiles<T, L>(Nmid, M);
+  dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
+  const size_t sm = Smem<T, L>::bytes_axis;
+  if (g_dry) { set_smem(k_chk<T, L>, sm); return; }
+  k_chk<T, L><<<grid, G_::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+
+template <typename T>
+void launch_chk(int L, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+  switch (L) {
+    case 8: launch_chk_t<T, 8>(a, Nmid, M, count, s); break;
+    case 16: launch_chk_t<T, 16>(a, Nmid, M, count, s); break;
+    case 32: launch_chk_t<T, 32>(a, Nmid, M, count, s); break;
+    case 64: launch_chk_t<T, 64>(a, Nmid, M, count, s); break;
+    case 128: launch_chk_t<T, 128>(a, Nmid, M, count, s); break;
+    case 256: launch_chk_t<T, 256>(a, Nmid, M, count, s); break;
+    case 512: launch_chk_t<T, 512>(a, Nmid, M, count, s); break;
+    case 1024: launch_chk_t<T, 1024>(a, Nmid, M, count, s); break;
+    default: fail(FFCZ_ERR_UNSUPPORTED, "check-axis length");
+  }
+}
+
+// Words of mask storage one pass writes (one uint32 per thread of a live tile).
+template <typename T>
+int64_t x_words(int M, int64_t rows) {
+  const int W = 64 / (int)sizeof(v2<T>);
+  return (rows / W) * (int64_t)(M / 8) * W;
+}
+template <typename T>
+int64_t chkw(int L, int Nmid, int M) {
+  const int W = 64 / (int)sizeof(v2<T>);
+  const int64_t nmain = (int64_t)Nmid * (M / W);
+  const int npairs = Nmid / 2 + 1;
+  return (nmain + (npairs + W / 2 - 1) / (W / 2)) * (int64_t)(L / 8) * W;
+}
+
+// ----- argument construction ------------------------------------------------
+template <typename T>
+Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState* st) {
+  Args a{};
+  a.g = dg.g;
+  a.prm = p->d_prm;
+  a.st = st;
+  a.B0 = b0;
+  a.B1 = b1;
+  a.pred = P_ACTIVE;
+  a.sel_in = a.sel_out = S_CUR;
+  a.ckpt_every = 0;
+  return a;
+}
+
+template <typename T>
+void tabs_x(ffcz_plan_s* p, Args& a, const DevGroup& dg) {
+  a.tw = tw_of<T>(p->tb, dg.M);
+  a.twr = tw_of<T>(p->tb, dg.Nx);   // first M entries: exp(-2 pi i k / Nx)
+}
+
+// ----- the loop ---------------------------------------------------------------
+struct LoopBufs {
+  void* b0;
+  void* b1;
+};
+
+template <typename T>
+void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStream_t s) {
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    tabs_x<T>(p, a, dg);
+    a.e = e;
+    a.mode = measure_preclip ? M_MEASURE : 0;
+    launch_x<T>(XFWD, dg.M, a, dg.rows, dg.count, s);
+  }
+  if (measure_preclip) {
+    k_mark_preclip<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch);
+    g_launches++;
+    for (auto& dg : p->groups) {
+      Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+      tabs_x<T>(p, a, dg);
+      a.e = e;
+      a.mode = M_PRECLIP;
+      a.pred = P_PRECLIP;
+      launch_x<T>(XFWD, dg.M, a, dg.rows, dg.count, s);
+    }
+  }
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    if (dg.ndim == 3) {
+      a.tw = tw_of<T>(p->tb, dg.Ny);
+      launch_axis<T, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+    }
+    a.tw = tw_of<T>(p->tb, dg.Nz);
+    a.mode = M_CLIP;
+    launch_chk<T>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+  }
+  k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
+                                                             p->d_nactive);
+  g_launches++;
+}
+
+template <typename T>
+void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    if (dg.ndim == 3) {
+      a.tw = tw_of<T>(p->tb, dg.Ny);
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+      launch_axis<T, +1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+      a.sel_in = S_CUR;
+    } else {
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+    }
+    tabs_x<T>(p, a, dg);
+    a.mode = M_CLIP;
+    launch_x<T>(XPX, dg.M, a, dg.rows, dg.count, s);
+    a.sel_in = a.sel_out = S_CUR;
+    if (dg.ndim == 3) {
+      a.tw = tw_of<T>(p->tb, dg.Ny);
+      a.mode = 0;
+      launch_axis<T, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+    }
+    a.tw = tw_of<T>(p->tb, dg.Nz);
+    a.mode = M_CLIP;
+    launch_chk<T>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+  }
+  k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
+                                                             p->d_nactive);
+  g_launches++;
+}
+
+template <typename T>
+void exit_pass(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    a.pred = P_EXIT;
+    a.e = e;
+    if (dg.ndim == 3) {
+      a.tw = tw_of<T>(p->tb, dg.Ny);
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+      launch_axis<T, +1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+      a.sel_in = S_CUR;
+    } else {
+      a.sel_in = S_PREV;
+    }
+    tabs_x<T>(p, a, dg);
+    a.mode = M_CLIP;
+    launch_x<T>(XEXIT, dg.M, a, dg.rows, dg.count, s);
+  }
+}
+
+template <typename T>
+LoopBufs loop_bufs(ffcz_plan_s* p) {
+  if (sizeof(T) == 4) return {p->B32[0], p->B32[1]};
+  if (!p->B64[0]) {
+    p->B64[0] = dalloc(p, (size_t)p->total * 8);
+    p->B64[1] = dalloc(p, (size_t)p->total * 8);
+  }
+  return {p->B64[0], p->B64[1]};
+}
+
+template <typename T>
+void run_chunk(ffcz_plan_s* p, LoopBufs B, int C) {
+  if (!p->opts.use_graph) {
+    for (int i = 0; i < C; ++i) body<T>(p, B, p->stream);
+    return;
+  }
+  const auto key = std::make_pair((int)sizeof(T), C);
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaGraph_t g;
+    const int64_t before = g_launches.load();
+    CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int i = 0; i < C; ++i) body<T>(p, B, p->cap_stream);
+    } catch (...) {
+      cudaGraph_t junk;
+      cudaStreamEndCapture(p->cap_stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      throw;
+    }
+    CK(cudaStreamEndCapture(p->cap_stream, &g));
+    g_launches -= (g_launches.load() - before);   // captured, not launched
+    cudaGraphExec_t ge;
+    CK(cudaGraphInstantiate(&ge, g, 0));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    cudaGraphDestroy(g);
+    it = p->graphs.emplace(key, ge).first;
+    p->graph_nodes[key] = (int)nn;
+  }
+  CK(cudaGraphLaunch(it->second, p->stream));
+  g_launches += p->graph_nodes[key];
+}
+
+void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int min_iters,
+                   int max_iters) {
+  const double eta = p->opts.shrink;
+  for (int64_t i = 0; i < p->batch; ++i) {
+    ItemParams& q = p->h_prm[i];
+    const double E = eps_s[i], D = eps_f[i];
+    if (!(E > 0) || !(D > 0) || !std::isfinite(E) || !std::isfinite(D))
+      fail(FFCZ_ERR_INVALID, "bounds must be finite and > 0");
+    int64_t n = 1;
+    for (int d = 0; d < p->ndim; ++d) n *= p->shapes[i * p->ndim + d];
+    q.E = E; q.D = D;
+    q.Es = E * (1.0 - eta); q.Ds = D * (1.0 - eta); q.thr = D * (1.0 - eta / 2.0);
+    q.inv_n = 1.0 / (double)n;
+    q.Esf = (float)q.Es; q.Dsf = (float)q.Ds; q.thrf = (float)q.thr; q.inv_nf = (float)q.inv_n;
+    q.n = n;
+    q.min_iters = min_iters;
+    q.max_iters = max_iters;
+  }
+  CK(cudaMemcpyAsync(p->d_prm, p->h_prm, sizeof(ItemParams) * p->batch, cudaMemcpyHostToDevice,
+                     p->stream));
+}
+
+int read_active(ffcz_plan_s* p) {
+  CK(cudaMemcpyAsync(p->h_nactive, p->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return *p->h_nactive;
+}
+
+template <typename T>
+void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
+  LoopBufs B = loop_bufs<T>(p);
+  CK(cudaMemsetAsync(p->d_nactive, 0, sizeof(int), p->stream));
+  k_init<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, (int)p->batch,
+                                                                   only_uncert ? 1 : 0, p->d_nactive);
+  g_launches++;
+  entry<T>(p, B, e, !only_uncert, p->stream);
+  int chunk = 1;
+  const int cmax = std::max(1, p->opts.chunk);
+  while (read_active(p) > 0) {
+    run_chunk<T>(p, B, chunk);
+    chunk = std::min(chunk * 2, cmax);
+  }
+  exit_pass<T>(p, B, e, p->stream);
+}
+
+void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
+  if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total * 8);
+  for (auto& dg : p->groups) {
+    Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_st);
+    a.pred = repair_round ? P_UNCERT : P_ALL;
+    tabs_x<double>(p, a, dg);
+    a.e = const_cast<float*>(e);
+    a.mode = M_MEASURE;
+    launch_x<double>(XFWD, dg.M, a, dg.rows, dg.count, p->stream);
+    if (dg.ndim == 3) {
+      a.tw = tw_of<double>(p->tb, dg.Ny);
+      a.mode = 0;
+      launch_axis<double, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, p->stream);
+    }
+    a.tw = tw_of<double>(p->tb, dg.Nz);
+    a.mode = M_NOWRITE;
+    launch_chk<double>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
+  }
+  k_certify<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(
+      p->d_prm, p->d_st, (int)p->batch, repair_round ? 1 : 0);
+  g_launches++;
+}
+
+// Reset the certification accumulators (they are shared with the loop).
+__global__ void k_cert_reset(ItemState* st, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  st[i].vbits = 0ull;
+  st[i].emaxbits = 0ull;
+  st[i].sumsq = 0.0;
+}
+
+void cert_reset(ffcz_plan_s* p) {
+  k_cert_reset<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, (int)p->batch);
+  g_launches++;
+}
+
+__global__ void k_set_repairs(ItemState* st, int n, int round) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!st[i].certified) st[i].repairs = round;
+}
+
+void fill_stats(ffcz_plan_s* p, ffcz_stats* out, float ms, float ms_cert, bool certified_run) {
+  CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(ItemState) * p->batch, cudaMemcpyDeviceToHost,
+                     p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (!out) return;
+  for (int64_t i = 0; i < p->batch; ++i) {
+    const ItemState& s = p->h_st[i];
+    const ItemParams& q = p->h_prm[i];
+    ffcz_stats& o = out[i];
+    memset(&o, 0, sizeof(o));
+    o.status = s.status;
+    o.iters = s.t;
+    o.repairs = s.repairs;
+    o.certified = certified_run ? s.certified : 0;
+    o.preclipped = s.preclip;
+    o.f_ratio = s.f_ratio;
+    if (certified_run) {
+      o.s_ratio = s.emax64 / q.E;
+      o.f_margin64 = 1.0 - (s.v64 + s.bound64) / q.D;
+      o.s_margin64 = 1.0 - s.emax64 / q.E;
+    }
+    o.active_s = (int64_t)s.last_act_s;
+    o.active_f = (int64_t)s.last_act_f;
+    o.ms_total = ms;
+    o.ms_cert = ms_cert;
+  }
+}
+
+ffcz_status worst_status(ffcz_plan_s* p, bool certified_run) {
+  int worst = 0;
+  auto rank = [](int s) { return s == 0 ? 0 : s == 4 ? 1 : s == 5 ? 2 : s == 6 ? 3 : 4; };
+  for (int64_t i = 0; i < p->batch; ++i) {
+    int s = p->h_st[i].status;
+    if (s == 0 && certified_run && !p->h_st[i].certified) s = FFCZ_ERR_CERT_FAILED;
+    if (rank(s) > rank(worst)) worst = s;
+  }
+  return (ffcz_status)worst;
+}
+
+template <typename F>
+ffcz_status guarded(F&& f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const Fail& x) {
+    return x.s;
+  } catch (const std::exception& x) {
+    g_err = x.what();
+    return FFCZ_ERR_CUDA;
+  } catch (...) {
+    g_err = "unknown error";
+    return FFCZ_ERR_CUDA;
+  }
+}
+
+void free_plan(ffcz_plan_s* p) {
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* a : p->allocs) cudaFree(a);
+  if (p->h_nactive) cudaFreeHost(p->h_nactive);
+  if (p->h_st) cudaFreeHost(p->h_st);
+  if (p->h_prm) cudaFreeHost(p->h_prm);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->ev2) cudaEventDestroy(p->ev2);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  delete p;
+}
+
+ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const double* eps_f,
+                         ffcz_stats* stats) {
+  if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
+  CK(cudaSetDevice(p->device));
+  upload_params(p, eps_s, eps_f, p->opts.min_iters, p->opts.max_iters);
+  CK(cudaEventRecord(p->ev0, p->stream));
+  if (p->opts.precision == 64) run_loop<double>(p, e, false);
+  else run_loop<float>(p, e, false);
+  CK(cudaEventRecord(p->ev1, p->stream));
+  bool cert = p->opts.certify != 0;
+  if (cert) {
+    cert_reset(p);
+    certify(p, e, false);
+    for (int round = 1; round <= p->opts.max_repairs; ++round) {
+      CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(ItemState) * p->batch, cudaMemcpyDeviceToHost,
+                         p->stream));
+      CK(cudaStreamSynchronize(p->stream));
+      bool all = true;
+      for (int64_t i = 0; i < p->batch; ++i)
+        if (!p->h_st[i].certified && p->h_st[i].status != FFCZ_ERR_NONFINITE) all = false;
+      if (all) break;
+      // FP64 repair: Alg. 1 in FP64 from the current e, then re-certify.
+      upload_params(p, eps_s, eps_f, 0, p->opts.max_iters);
+      k_set_repairs<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st,
+                                                                             (int)p->batch, round);
+      g_launches++;
+      run_loop<double>(p, e, true);
+      cert_reset(p);
+      certify(p, e, true);
+    }
+  }
+  CK(cudaEventRecord(p->ev2, p->stream));
+  CK(cudaEventSynchronize(p->ev2));
+  float ms = 0.f, ms_c = 0.f;
+  CK(cudaEventElapsedTime(&ms, p->ev0, p->ev2));
+  CK(cudaEventElapsedTime(&ms_c, p->ev1, p->ev2));
+  fill_stats(p, stats, ms, cert ? ms_c : 0.f, cert);
+  CK(cudaGetLastError());
+  return worst_status(p, cert);
+}
+
+// ----- backward ---------------------------------------------------------------
+__global__ void k_advance(ItemState* st, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) st[i].t += 1;
+}
+__global__ void k_set_t(ItemState* st, int n, int t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { st[i].t = t; st[i].done = 0; }
+}
+
+void advance(ffcz_plan_s* p, ItemState* st) {
+  k_advance<<<1, 32, 0, p->stream>>>(st, 1);
+  g_launches++;
+}
+void set_t(ffcz_plan_s* p, ItemState* st, int t) {
+  k_set_t<<<1, 32, 0, p->stream>>>(st, 1, t);
+  g_launches++;
+}
+
+// One forward iteration body with mask recording (replay), no decide.
+void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask,
+                 uint32_t* fmask, float* ckpt, bool do_chk) {
+  Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
+  a.pred = P_ALL;
+  if (dg.ndim == 3) {
+    a.tw = tw_of<float>(p->tb, dg.Ny);
+    a.sel_in = S_PREV; a.sel_out = S_CUR;
+    launch_axis<float, +1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+    a.sel_in = S_CUR;
+  } else {
+    a.sel_in = S_PREV; a.sel_out = S_CUR;
+  }
+  tabs_x<float>(p, a, dg);
+  a.mode = M_CLIP | (smask ? M_RECORD : 0) | (ckpt ? M_CKPT : 0);
+  a.mask = smask;
+  a.ckpt = ckpt;
+  a.ckpt_every = p->bw_m;
+  launch_x<float>(XPX, dg.M, a, dg.rows, 1, p->stream);
+  if (!do_chk) return;
+  a.sel_in = a.sel_out = S_CUR;
+  a.mask = nullptr;
+  a.ckpt = nullptr;
+  if (dg.ndim == 3) {
+    a.tw = tw_of<float>(p->tb, dg.Ny);
+    a.mode = 0;
+    launch_axis<float, -1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+  }
+  a.tw = tw_of<float>(p->tb, dg.Nz);
+  a.mode = M_CLIP | (fmask ? M_RECORD : 0);
+  a.mask = fmask;
+  launch_chk<float>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+}
+
+void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uint32_t* fmask) {
+  Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
+  a.pred = P_ALL;
+  tabs_x<float>(p, a, dg);
+  a.e = e0;
+  a.mode = 0;
+  launch_x<float>(XFWD, dg.M, a, dg.rows, 1, p->stream);
+  if (dg.ndim == 3) {
+    a.tw = tw_of<float>(p->tb, dg.Ny);
+    launch_axis<float, -1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+  }
+  a.tw = tw_of<float>(p->tb, dg.Nz);
+  a.mode = M_CLIP | (fmask ? M_RECORD : 0);
+  a.mask = fmask;
+  launch_chk<float>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+}
+
+ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, float* gin,
+                          const double* eps_s, const double* eps_f) {
+  if (p->batch != 1) fail(FFCZ_ERR_UNSUPPORTED, "backward needs a single-item plan");
+  if (!e0 || !gout || !gin || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
+  const int K = p->opts.K, m = p->opts.ckpt_every;
+  if (K < 1 || m < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
+  CK(cudaSetDevice(p->device));
+  const DevGroup& dg = p->groups[0];
+  const int64_t N = p->total;
+  const int nseg = (K + m - 1) / m;
+  if (p->bw_K != K || p->bw_m != m) {
+    p->px_words = x_words<float>(dg.M, dg.rows);
+    p->chk_words = chkw<float>(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M);
+    p->bw_e = (float*)dalloc(p, sizeof(float) * N);
+    p->bw_ck = (float*)dalloc(p, sizeof(float) * N * nseg);
+    p->bw_smask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->px_words * m);
+    p->bw_fmask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->chk_words * m);
+    if (!p->bw_G[0]) {
+      p->bw_G[0] = dalloc(p, sizeof(float) * N);
+      p->bw_G[1] = dalloc(p, sizeof(float) * N);
+    }
+    p->bw_K = K;
+    p->bw_m = m;
+  }
+  upload_params(p, eps_s, eps_f, K, K);
+  LoopBufs B{p->B32[0], p->B32[1]};
+  LoopBufs GB{p->bw_G[0], p->bw_G[1]};
+  // Forward with checkpoints of e_t at t = 0, m, 2m, ... (t < K).
+  CK(cudaMemcpyAsync(p->bw_e, e0, sizeof(float) * N, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemsetAsync(p->d_nactive, 0, sizeof(int), p->stream));
+  k_init<<<1, 32, 0, p->stream>>>(p->d_st, 1, 0, p->d_nactive);
+  g_launches++;
+  {
+    // entry with A3 pre-clip on the working copy
+    entry<float>(p, B, p->bw_e, true, p->stream);
+    CK(cudaMemcpyAsync(p->bw_ck, p->bw_e, sizeof(float) * N, cudaMemcpyDeviceToDevice, p->stream));
+    const int last_ck = (nseg - 1) * m;
+    for (int t = 1; t <= last_ck; ++t) {
+      // k_decide after entry set t = 1 (forced iterations never stop early)
+      replay_body(p, dg, B, nullptr, nullptr, p->bw_ck, t < last_ck);
+      if (t < last_ck) advance(p, p->d_st);
+    }
+  }
+  // Adjoint, segment by segment from the last.
+  set_t(p, p->d_st2, 0);
+  bool first = true;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int t0 = seg * m, t1 = std::min(K, t0 + m);
+    // replay the segment from its checkpoint, recording masks of steps t0..t1-1
+    set_t(p, p->d_st, t0);
+    replay_entry(p, dg, B, p->bw_ck + (int64_t)seg * N, p->bw_fmask);
+    for (int b = t0 + 1; b <= t1; ++b) {
+      advance(p, p->d_st);
+      replay_body(p, dg, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
+                  b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr,
+                  b < t1);
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      uint32_t* sm = p->bw_smask + (int64_t)(t - t0) * p->px_words;
+      uint32_t* fm = p->bw_fmask + (int64_t)(t - t0) * p->chk_words;
+      Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
+      a.pred = P_ALL;
+      if (first) {
+        tabs_x<float>(p, a, dg);
+        a.ein = gout;
+        a.e = const_cast<float*>(gout);
+        a.mask = sm;
+        a.mode = M_MASK;
+        launch_x<float>(XFWD, dg.M, a, dg.rows, 1, p->stream);
+        first = false;
+      } else {
+        advance(p, p->d_st2);
+        if (dg.ndim == 3) {
+          a.tw = tw_of<float>(p->tb, dg.Ny);
+          a.sel_in = S_PREV; a.sel_out = S_CUR;
+          launch_axis<float, +1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+          a.sel_in = S_CUR;
+        } else {
+          a.sel_in = S_PREV; a.sel_out = S_CUR;
+        }
+        tabs_x<float>(p, a, dg);
+        a.mask = sm;
+        a.mode = M_MASK;
+        launch_x<float>(XPX, dg.M, a, dg.rows, 1, p->stream);
+      }
+      a.sel_in = a.sel_out = S_CUR;
+      if (dg.ndim == 3) {
+        a.tw = tw_of<float>(p->tb, dg.Ny);
+        a.mode = 0;
+        a.mask = nullptr;
+        launch_axis<float, -1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+      }
+      a.tw = tw_of<float>(p->tb, dg.Nz);
+      a.mode = M_MASK;
+      a.mask = fm;
+      launch_chk<float>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+    }
+  }
+  // exit: inverse of the last step's spectrum, no clip
+  {
+    advance(p, p->d_st2);
+    Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
+    a.pred = P_ALL;
+    a.e = gin;
+    if (dg.ndim == 3) {
+      a.tw = tw_of<float>(p->tb, dg.Ny);
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+      launch_axis<float, +1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+      a.sel_in = S_CUR;
+    } else {
+      a.sel_in = S_PREV;
+    }
+    tabs_x<float>(p, a, dg);
+    a.mode = 0;
+    launch_x<float>(XEXIT, dg.M, a, dg.rows, 1, p->stream);
+    k_premask<<<1184, 256, 0, p->stream>>>(gin, e0, p->d_prm, p->d_st, 0, N);
+    g_launches++;
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaGetLastError());
+  return FFCZ_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void ffcz_default_opts(ffcz_opts* o) {
+  if (!o) return;
+  o->max_iters = 10000;
+  o->min_iters = 0;
+  o->shrink = 1.0 / 65536.0;
+  o->precision = 32;
+  o->certify = 1;
+  o->max_repairs = 2;
+  o->K = 50;
+  o->ckpt_every = 10;
+  o->chunk = 16;
+  o->use_graph = 1;
+}
+
+ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t batch,
+                      const ffcz_opts* opts, void* cuda_stream) {
+  return guarded([&]() -> ffcz_status {
+    if (!out) fail(FFCZ_ERR_INVALID, "out is null");
+    *out = nullptr;
+    if (!shapes) fail(FFCZ_ERR_INVALID, "shapes is null");
+    if (ndim < 1 || ndim > 3) fail(FFCZ_ERR_INVALID, "ndim must be 1..3");
+    if (batch < 1 || batch > 65535) fail(FFCZ_ERR_INVALID, "batch must be in [1, 65535]");
+    if (ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "1D items are not supported by this build");
+    ffcz_opts o;
+    ffcz_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != 32 && o.precision != 64) fail(FFCZ_ERR_INVALID, "precision must be 32 or 64");
+    if (!(o.shrink >= 0.0 && o.shrink < 0.5)) fail(FFCZ_ERR_INVALID, "shrink must be in [0, 0.5)");
+    if (o.max_iters < 0 || o.min_iters < 0) fail(FFCZ_ERR_INVALID, "iteration limits must be >= 0");
+    for (int64_t i = 0; i < batch; ++i) {
+      for (int d = 0; d < ndim; ++d) {
+        const int64_t n = shapes[i * ndim + d];
+        const bool last = d == ndim - 1;
+        if (!is_pow2(n) || n < (last ? 16 : 8) || n > (last ? 2048 : 1024))
+          fail(FFCZ_ERR_UNSUPPORTED, "axis lengths must be powers of two in [8, 1024] "
+                                     "([16, 2048] for the last axis)");
+      }
+    }
+    std::unique_ptr<ffcz_plan_s, void (*)(ffcz_plan_s*)> p(new ffcz_plan_s, free_plan);
+    p->ndim = ndim;
+    p->batch = batch;
+    p->shapes.assign(shapes, shapes + batch * ndim);
+    p->opts = o;
+    p->stream = (cudaStream_t)cuda_stream;
+    CK(cudaGetDevice(&p->device));
+    p->eoff.resize(batch);
+    int64_t off = 0;
+    std::map<std::vector<int64_t>, std::vector<int>> bys;
+    for (int64_t i = 0; i < batch; ++i) {
+      std::vector<int64_t> sh(shapes + i * ndim, shapes + (i + 1) * ndim);
+      int64_t n = 1;
+      for (auto v : sh) n *= v;
+      p->eoff[i] = off;
+      off += n;
+      bys[sh].push_back((int)i);
+    }
+    p->total = off;
+    CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&p->ev0));
+    CK(cudaEventCreate(&p->ev1));
+    CK(cudaEventCreate(&p->ev2));
+    // twiddle tables for every power of two 8..2048
+    for (int pw = 3; pw <= 11; ++pw) {
+      const int L = 1 << pw;
+      auto t32 = twiddles<float>(L);
+      auto t64 = twiddles<double>(L);
+      p->tb.f32[pw] = dalloc(p.get(), sizeof(float2) * L);
+      p->tb.f64[pw] = dalloc(p.get(), sizeof(double2) * L);
+      CK(cudaMemcpy(p->tb.f32[pw], t32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(p->tb.f64[pw], t64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice));
+    }
+    for (auto& kv : bys) {
+      const auto& sh = kv.first;
+      const auto& ids = kv.second;
+      DevGroup dg{};
+      dg.ndim = ndim;
+      dg.count = (int)ids.size();
+      dg.Nx = (int)sh[ndim - 1];
+      dg.M = dg.Nx / 2;
+      dg.Nz = (int)sh[0];
+      dg.Ny = ndim == 3 ? (int)sh[1] : 1;
+      dg.n = 1;
+      for (auto v : sh) dg.n *= v;
+      dg.rows = dg.n / dg.Nx;
+      std::vector<int32_t> it(ids.begin(), ids.end());
+      std::vector<int64_t> eo, so;
+      for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(p->eoff[id] / 2); }
+      int32_t* d_it = (int32_t*)dalloc(p.get(), sizeof(int32_t) * it.size());
+      int64_t* d_eo = (int64_t*)dalloc(p.get(), sizeof(int64_t) * eo.size());
+      int64_t* d_so = (int64_t*)dalloc(p.get(), sizeof(int64_t) * so.size());
+      CK(cudaMemcpy(d_it, it.data(), sizeof(int32_t) * it.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_eo, eo.data(), sizeof(int64_t) * eo.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(d_so, so.data(), sizeof(int64_t) * so.size(), cudaMemcpyHostToDevice));
+      dg.g.ndim = ndim;
+      dg.g.Nz = dg.Nz;
+      dg.g.Nmid = dg.Ny;
+      dg.g.M = dg.M;
+      dg.g.rows = dg.rows;
+      dg.g.item = d_it;
+      dg.g.eoff = d_eo;
+      dg.g.soff = d_so;
+      p->groups.push_back(dg);
+    }
+    // Set the shared-memory attributes of every kernel the plan can launch.
+    g_dry = true;
+    try {
+      Args a{};
+      for (auto& dg : p->groups) {
+        launch_x<float>(XFWD, dg.M, a, dg.rows, 1, nullptr);
+        launch_x<double>(XFWD, dg.M, a, dg.rows, 1, nullptr);
+        launch_axis<float, -1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
+        launch_axis<float, +1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
+        launch_axis<double, -1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
+        launch_axis<double, +1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
+        launch_chk<float>(dg.Nz, a, dg.Ny, dg.M, 1, nullptr);
+        launch_chk<double>(dg.Nz, a, dg.Ny, dg.M, 1, nullptr);
+      }
+    } catch (...) {
+      g_dry = false;
+      throw;
+    }
+    g_dry = false;
+    // float32 spectrum buffers: N/2 complex64 each (4 bytes per point)
+    p->B32[0] = dalloc(p.get(), sizeof(float) * p->total);
+    p->B32[1] = dalloc(p.get(), sizeof(float) * p->total);
+    p->d_prm = (ItemParams*)dalloc(p.get(), sizeof(ItemParams) * batch);
+    p->d_st = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
+    p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
+    p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
+    CK(cudaMemset(p->d_st, 0, sizeof(ItemState) * batch));
+    CK(cudaMemset(p->d_st2, 0, sizeof(ItemState) * batch));
+    CK(cudaMallocHost(&p->h_nactive, sizeof(int)));
+    CK(cudaMallocHost(&p->h_st, sizeof(ItemState) * batch));
+    CK(cudaMallocHost(&p->h_prm, sizeof(ItemParams) * batch));
+    *out = p.release();
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_set_stream(ffcz_plan_t plan, void* s) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  plan->stream = (cudaStream_t)s;
+  return FFCZ_OK;
+}
+
+size_t ffcz_workspace_bytes(ffcz_plan_t plan) { return plan ? plan->ws_bytes : 0; }
+
+ffcz_status ffcz_correct(ffcz_plan_t plan, float* e, const double* eps_s, const double* eps_f,
+                         ffcz_stats* stats) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() { return correct_impl(plan, e, eps_s, eps_f, stats); });
+}
+
+ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps_s,
+                              const double* eps_f, ffcz_stats* stats) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (!e_host) fail(FFCZ_ERR_INVALID, "e_host is null");
+    CK(cudaSetDevice(plan->device));
+    if (!plan->staging) plan->staging = (float*)dalloc(plan, sizeof(float) * plan->total);
+    CK(cudaMemcpyAsync(plan->staging, e_host, sizeof(float) * plan->total, cudaMemcpyHostToDevice,
+                       plan->stream));
+    ffcz_status s = correct_impl(plan, plan->staging, eps_s, eps_f, stats);
+    CK(cudaMemcpyAsync(e_host, plan->staging, sizeof(float) * plan->total, cudaMemcpyDeviceToHost,
+                       plan->stream));
+    CK(cudaStreamSynchronize(plan->stream));
+    return s;
+  });
+}
+
+ffcz_status ffcz_check(ffcz_plan_t plan, const float* e, const double* eps_s, const double* eps_f,
+                       ffcz_stats* stats) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
+    CK(cudaSetDevice(plan->device));
+    upload_params(plan, eps_s, eps_f, 0, 0);
+    CK(cudaEventRecord(plan->ev0, plan->stream));
+    cert_reset(plan);
+    certify(plan, e, false);
+    CK(cudaEventRecord(plan->ev2, plan->stream));
+    CK(cudaEventSynchronize(plan->ev2));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, plan->ev0, plan->ev2));
+    fill_stats(plan, stats, ms, ms, true);
+    if (stats)
+      for (int64_t i = 0; i < plan->batch; ++i) { stats[i].iters = 0; stats[i].status = 0; }
+    CK(cudaGetLastError());
+    for (int64_t i = 0; i < plan->batch; ++i)
+      if (!plan->h_st[i].certified) return FFCZ_ERR_CERT_FAILED;
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0, const float* gout, float* gin,
+                                  const double* eps_s, const double* eps_f) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() { return backward_impl(plan, e0, gout, gin, eps_s, eps_f); });
+}
+
+void ffcz_destroy(ffcz_plan_t plan) {
+  if (plan) free_plan(plan);
+}
+
+const char* ffcz_strerror(ffcz_status s) {
+  switch (s) {
+    case FFCZ_OK: return "ok";
+    case FFCZ_ERR_INVALID: return "invalid argument";
+    case FFCZ_ERR_UNSUPPORTED: return "unsupported shape or option";
+    case FFCZ_ERR_CUDA: return "CUDA error";
+    case FFCZ_ERR_NOT_CONVERGED: return "not converged within max_iters";
+    case FFCZ_ERR_CERT_FAILED: return "FP64 certification failed";
+    case FFCZ_ERR_NONFINITE: return "non-finite value in the error field or its spectrum";
+    case FFCZ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case FFCZ_ERR_OOM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* ffcz_last_error(void) { return g_err.c_str(); }
+
+int64_t ffcz_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"
