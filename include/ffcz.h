@@ -65,6 +65,7 @@ typedef struct {
   int32_t ckpt_every;  /* backward: checkpoint interval m; 10 */
   int32_t chunk;       /* max iterations launched between host checks; 16 */
   int32_t use_graph;   /* 1 (default): replay loop chunks as CUDA graphs */
+  int32_t count_active;/* 1 (default): count active clips for ffcz_stats */
 } ffcz_opts;
 
 /* Per-item results. */
@@ -181,6 +182,20 @@ const char* ffcz_last_error(void);
 
 /* Number of kernel launches issued by this process so far (all plans). */
 int64_t ffcz_launch_count(void);
+
+/*
+ * Per-kernel device-time profile of a plan (measurement support, not part of
+ * the method).  ffcz_profile_enable(plan, 1) clears the table and makes every
+ * later call record a CUDA event pair around each of its launches (loop
+ * chunks are then launched directly instead of as graphs); 0 turns it off.
+ * Entries are keyed by kernel kind, precision and pencil length, e.g.
+ * "chk<f32,512>"; ffcz_profile_entry copies entry i's key into name
+ * (truncated to name_len), its summed milliseconds and its launch count.
+ */
+ffcz_status ffcz_profile_enable(ffcz_plan_t plan, int on);
+int ffcz_profile_count(ffcz_plan_t plan);
+ffcz_status ffcz_profile_entry(ffcz_plan_t plan, int i, char* name, int name_len, double* ms,
+                               int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ ERR_NOT_CONVERGED, ERR_CERT_FAILED, ERR_NONFINITE, ERR_TIMEOUT, ERR_OOM = 4, 5, 
 
 SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_bytes",
            "ffcz_correct", "ffcz_correct_host", "ffcz_check", "ffcz_correct_backward",
-           "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count")
+           "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
+           "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry")
 
 
 class Opts(ctypes.Structure):
@@ -31,7 +32,8 @@ class Opts(ctypes.Structure):
                 ("shrink", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("certify", ctypes.c_int32), ("max_repairs", ctypes.c_int32),
                 ("K", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("count_active", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -75,8 +77,15 @@ def lib() -> ctypes.CDLL:
         L.ffcz_strerror.restype = ctypes.c_char_p
         L.ffcz_last_error.restype = ctypes.c_char_p
         L.ffcz_launch_count.restype = ctypes.c_int64
+        L.ffcz_profile_enable.argtypes = [vp, i32]
+        L.ffcz_profile_count.argtypes = [vp]
+        L.ffcz_profile_count.restype = ctypes.c_int
+        L.ffcz_profile_entry.argtypes = [vp, i32, ctypes.c_char_p, i32,
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64)]
         for name in ("ffcz_plan", "ffcz_set_stream", "ffcz_correct", "ffcz_correct_host",
-                     "ffcz_check", "ffcz_correct_backward"):
+                     "ffcz_check", "ffcz_correct_backward", "ffcz_profile_enable",
+                     "ffcz_profile_entry"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -156,6 +165,20 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(lib().ffcz_workspace_bytes(self._h))
+
+    def profile(self, on: bool = True):
+        """Turn per-kernel event timing on (clears the table) or off."""
+        _check(lib().ffcz_profile_enable(self._h, 1 if on else 0))
+
+    def profile_table(self):
+        """{kernel key: (total ms, launches)} accumulated since profile(True)."""
+        out = {}
+        buf = ctypes.create_string_buffer(64)
+        for i in range(lib().ffcz_profile_count(self._h)):
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            _check(lib().ffcz_profile_entry(self._h, i, buf, 64, ctypes.byref(ms), ctypes.byref(n)))
+            out[buf.value.decode()] = (ms.value, n.value)
+        return out
 
     def _bind_stream(self, stream=None):
         _check(lib().ffcz_set_stream(self._h, ctypes.c_void_p(_stream_ptr(stream))))

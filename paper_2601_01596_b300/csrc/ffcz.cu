@@ -46,20 +46,55 @@ void fail(ffcz_status s, const std::string& msg) {
 
 bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// exp(-2 pi i m / L) for m < L, from long double sin/cos, rounded once.
+// exp(-2 pi i m / L) in long double, rounded once (exact zeros kept exact).
 template <typename T>
-std::vector<v2<T>> twiddles(int L) {
-  std::vector<v2<T>> t(L);
-  const long double pi = acosl(-1.0L);
-  for (int m = 0; m < L; ++m) {
-    long double a = 2.0L * pi * (long double)m / (long double)L;
-    long double c = cosl(a), s = -sinl(a);
-    if (fabsl(c) < 1e-18L) c = 0.0L;
-    if (fabsl(s) < 1e-18L) s = 0.0L;
-    t[m].x = (T)c;
-    t[m].y = (T)s;
+v2<T> root(long double m, long double L) {
+  static const long double pi = acosl(-1.0L);
+  const long double a = 2.0L * pi * m / L;
+  long double c = cosl(a), s = -sinl(a);
+  if (fabsl(c) < 1e-18L) c = 0.0L;
+  if (fabsl(s) < 1e-18L) s = 0.0L;
+  v2<T> r;
+  r.x = (T)c;
+  r.y = (T)s;
+  return r;
+}
+
+// exp(-2 pi i k / Nx) for k < Nx/2 (R2C / C2R post- and pre-processing).
+template <typename T>
+std::vector<v2<T>> r2c_table(int Nx) {
+  std::vector<v2<T>> t(Nx / 2);
+  for (int k = 0; k < Nx / 2; ++k) t[k] = root<T>(k, Nx);
+  return t;
+}
+
+// Per-stage Stockham factors in the layout of Sched<L> (see fft_core.cuh).
+template <typename T, int L>
+std::vector<v2<T>> stage_table() {
+  using SC = Sched<L>;
+  std::vector<v2<T>> t(SC::twsize);
+  for (auto& x : t) { x.x = 0; x.y = 0; }
+  for (int s = 1; s < SC::nst; ++s) {
+    const int R = SC::radix(s), NS = SC::ns(s), sp = SC::sp(s), off = SC::twoff(s);
+    for (int k = 0; k < NS; ++k)
+      for (int tt = 1; tt < R; ++tt) t[off + k * sp + tt - 1] = root<T>((long double)k * tt, (long double)R * NS);
   }
   return t;
+}
+
+template <typename T>
+std::vector<v2<T>> stage_table_rt(int L) {
+  switch (L) {
+    case 8: return stage_table<T, 8>();
+    case 16: return stage_table<T, 16>();
+    case 32: return stage_table<T, 32>();
+    case 64: return stage_table<T, 64>();
+    case 128: return stage_table<T, 128>();
+    case 256: return stage_table<T, 256>();
+    case 512: return stage_table<T, 512>();
+    case 1024: return stage_table<T, 1024>();
+  }
+  return {};
 }
 
 struct DevGroup {
@@ -70,15 +105,23 @@ struct DevGroup {
 };
 
 struct Tables {
-  // per power of two L = 2^p (p = 3..11): forward twiddles
+  // per power of two 2^p: Stockham stage factors (p = 3..10) and R2C
+  // factors for Nx = 2^p (p = 4..11)
   void* f32[12] = {};
   void* f64[12] = {};
+  void* r32[12] = {};
+  void* r64[12] = {};
 };
 
 template <typename T>
 const void* tw_of(const Tables& tb, int L) {
   const int p = ilog2(L);
   return sizeof(T) == 4 ? tb.f32[p] : tb.f64[p];
+}
+template <typename T>
+const void* twr_of(const Tables& tb, int Nx) {
+  const int p = ilog2(Nx);
+  return sizeof(T) == 4 ? tb.r32[p] : tb.r64[p];
 }
 
 }  // namespace
@@ -116,6 +159,14 @@ struct ffcz_plan_s {
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   std::map<std::pair<int, int>, int> graph_nodes;
 
+  // per-kernel profile (events around every launch; graphs off while on)
+  bool prof = false;
+  struct Pending { std::string key; cudaEvent_t a, b; };
+  std::vector<Pending> pend;
+  std::vector<cudaEvent_t> evpool;
+  std::map<std::string, std::pair<double, int64_t>> prof_tab;
+  std::vector<std::string> prof_keys;
+
   // backward workspace
   float* bw_e = nullptr;
   float* bw_ck = nullptr;
@@ -145,6 +196,55 @@ void set_smem(Kern k, size_t bytes) {
 // before any graph capture).
 thread_local bool g_dry = false;
 
+// Plan whose launches are being profiled on this thread (nullptr: none).
+thread_local ffcz_plan_s* g_prof = nullptr;
+
+
+cudaEvent_t prof_event(ffcz_plan_s* p) {
+  if (!p->evpool.empty()) { cudaEvent_t e = p->evpool.back(); p->evpool.pop_back(); return e; }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+struct ProfScope {
+  ffcz_plan_s* p;
+  cudaEvent_t a = nullptr;
+  const char* kind;
+  int prec, len;
+  cudaStream_t s;
+  ProfScope(const char* kind_, int prec_, int len_, cudaStream_t s_)
+      : p(g_prof), kind(kind_), prec(prec_), len(len_), s(s_) {
+    if (p) { a = prof_event(p); CK(cudaEventRecord(a, s)); }
+  }
+  ~ProfScope() noexcept(false) {
+    if (!p) return;
+    cudaEvent_t b = prof_event(p);
+    CK(cudaEventRecord(b, s));
+    char key[64];
+    snprintf(key, sizeof key, "%s<f%d,%d>", kind, prec, len);
+    p->pend.push_back({key, a, b});
+  }
+};
+
+// Accumulate the elapsed times of all pending event pairs (stream is synced).
+void prof_collect(ffcz_plan_s* p) {
+  for (auto& x : p->pend) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, x.a, x.b));
+    auto it = p->prof_tab.find(x.key);
+    if (it == p->prof_tab.end()) {
+      p->prof_keys.push_back(x.key);
+      it = p->prof_tab.emplace(x.key, std::make_pair(0.0, (int64_t)0)).first;
+    }
+    it->second.first += ms;
+    it->second.second += 1;
+    p->evpool.push_back(x.a);
+    p->evpool.push_back(x.b);
+  }
+  p->pend.clear();
+}
+
 // ----- kernel dispatch over the pencil length -------------------------------
 enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
 
@@ -158,6 +258,7 @@ void launch_x_t(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t
     set_smem(k_xfwd<T, M>, sm); set_smem(k_px<T, M>, sm); set_smem(k_xexit<T, M>, sm);
     return;
   }
+  ProfScope ps(kind == XFWD ? "xfwd" : kind == XPX ? "px" : "xexit", 8 * (int)sizeof(T), M, s);
   switch (kind) {
     case XFWD: k_xfwd<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
     case XPX: k_px<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
@@ -187,7 +288,11 @@ void launch_axis_t(const Args& a, int Nz, int M, int count, cudaStream_t s) {
   const int64_t tiles = (int64_t)Nz * (M / G_::W);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L>::bytes_axis;
-  if (g_dry) { set_smem(k_axis<T, L, DIR>, sm); return; }
+  if (g_dry) {
+    set_smem(k_axis<T, L, DIR>, sm);
+    return;
+  }
+  ProfScope ps(DIR < 0 ? "axis_fwd" : "axis_inv", 8 * (int)sizeof(T), L, s);
   k_axis<T, L, DIR><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
@@ -209,10 +314,7 @@ void launch_axis(int L, const Args& a, int Nz, int M, int count, cudaStream_t s)
 
 template <typename T, int L>
 int64_t chk_tiles(int Nmid, int M) {
-  using G_ = Geo<T, L>;
-  const int64_t nmain = (int64_t)Nmid * (M / G_::W);
-  const int npairs = Nmid / 2 + 1;
-  return nmain + (npairs + G_::W / 2 - 1) / (G_::W / 2);
+  return chk_ntiles(Geo<T, L>::W, M, Nmid);
 }
 
 template <typename T, int L>
@@ -221,7 +323,12 @@ void launch_chk_t(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_tiles<T, L>(Nmid, M);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L>::bytes_axis;
-  if (g_dry) { set_smem(k_chk<T, L>, sm); return; }
+  if (g_dry) {
+    set_smem(k_chk<T, L>, sm);
+    return;
+  }
+  ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk",
+               8 * (int)sizeof(T), L, s);
   k_chk<T, L><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
@@ -256,6 +363,8 @@ int64_t chkw(int L, int Nmid, int M) {
 }
 
 // ----- argument construction ------------------------------------------------
+int cnt_flag(const ffcz_plan_s* p) { return p->opts.count_active ? M_COUNT : 0; }
+
 template <typename T>
 Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState* st) {
   Args a{};
@@ -273,7 +382,7 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
 template <typename T>
 void tabs_x(ffcz_plan_s* p, Args& a, const DevGroup& dg) {
   a.tw = tw_of<T>(p->tb, dg.M);
-  a.twr = tw_of<T>(p->tb, dg.Nx);   // first M entries: exp(-2 pi i k / Nx)
+  a.twr = twr_of<T>(p->tb, dg.Nx);
 }
 
 // ----- the loop ---------------------------------------------------------------
@@ -310,7 +419,7 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
       launch_axis<T, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
     }
     a.tw = tw_of<T>(p->tb, dg.Nz);
-    a.mode = M_CLIP;
+    a.mode = M_CLIP | cnt_flag(p);
     launch_chk<T>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
@@ -331,7 +440,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
       a.sel_in = S_PREV; a.sel_out = S_CUR;
     }
     tabs_x<T>(p, a, dg);
-    a.mode = M_CLIP;
+    a.mode = M_CLIP | cnt_flag(p);
     launch_x<T>(XPX, dg.M, a, dg.rows, dg.count, s);
     a.sel_in = a.sel_out = S_CUR;
     if (dg.ndim == 3) {
@@ -340,7 +449,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
       launch_axis<T, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
     }
     a.tw = tw_of<T>(p->tb, dg.Nz);
-    a.mode = M_CLIP;
+    a.mode = M_CLIP | cnt_flag(p);
     launch_chk<T>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
@@ -380,7 +489,7 @@ LoopBufs loop_bufs(ffcz_plan_s* p) {
 
 template <typename T>
 void run_chunk(ffcz_plan_s* p, LoopBufs B, int C) {
-  if (!p->opts.use_graph) {
+  if (!p->opts.use_graph || p->prof) {
     for (int i = 0; i < C; ++i) body<T>(p, B, p->stream);
     return;
   }
@@ -557,6 +666,8 @@ ffcz_status guarded(F&& f) {
 
 void free_plan(ffcz_plan_s* p) {
   for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& x : p->pend) { cudaEventDestroy(x.a); cudaEventDestroy(x.b); }
+  for (auto e : p->evpool) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
   if (p->h_nactive) cudaFreeHost(p->h_nactive);
   if (p->h_st) cudaFreeHost(p->h_st);
@@ -568,9 +679,23 @@ void free_plan(ffcz_plan_s* p) {
   delete p;
 }
 
+struct ProfOn {
+  ffcz_plan_s* p;
+  explicit ProfOn(ffcz_plan_s* p_) : p(p_) {
+    g_prof = p->prof ? p : nullptr;
+  }
+  ~ProfOn() {
+    if (g_prof) {
+      try { cudaStreamSynchronize(p->stream); prof_collect(p); } catch (...) {}
+    }
+    g_prof = nullptr;
+  }
+};
+
 ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const double* eps_f,
                          ffcz_stats* stats) {
   if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
+  ProfOn prof_on(p);
   CK(cudaSetDevice(p->device));
   upload_params(p, eps_s, eps_f, p->opts.min_iters, p->opts.max_iters);
   CK(cudaEventRecord(p->ev0, p->stream));
@@ -686,6 +811,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
   const int K = p->opts.K, m = p->opts.ckpt_every;
   if (K < 1 || m < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
   CK(cudaSetDevice(p->device));
+  ProfOn prof_on(p);
   const DevGroup& dg = p->groups[0];
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
@@ -821,6 +947,7 @@ void ffcz_default_opts(ffcz_opts* o) {
   o->ckpt_every = 10;
   o->chunk = 16;
   o->use_graph = 1;
+  o->count_active = 1;
 }
 
 ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t batch,
@@ -870,15 +997,24 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     CK(cudaEventCreate(&p->ev0));
     CK(cudaEventCreate(&p->ev1));
     CK(cudaEventCreate(&p->ev2));
-    // twiddle tables for every power of two 8..2048
-    for (int pw = 3; pw <= 11; ++pw) {
+    // twiddle tables: stage factors for L = 8..1024, R2C factors for Nx = 16..2048
+    for (int pw = 3; pw <= 10; ++pw) {
       const int L = 1 << pw;
-      auto t32 = twiddles<float>(L);
-      auto t64 = twiddles<double>(L);
-      p->tb.f32[pw] = dalloc(p.get(), sizeof(float2) * L);
-      p->tb.f64[pw] = dalloc(p.get(), sizeof(double2) * L);
-      CK(cudaMemcpy(p->tb.f32[pw], t32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(p->tb.f64[pw], t64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice));
+      auto t32 = stage_table_rt<float>(L);
+      auto t64 = stage_table_rt<double>(L);
+      p->tb.f32[pw] = dalloc(p.get(), sizeof(float2) * t32.size());
+      p->tb.f64[pw] = dalloc(p.get(), sizeof(double2) * t64.size());
+      CK(cudaMemcpy(p->tb.f32[pw], t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(p->tb.f64[pw], t64.data(), sizeof(double2) * t64.size(), cudaMemcpyHostToDevice));
+    }
+    for (int pw = 4; pw <= 11; ++pw) {
+      const int Nx = 1 << pw;
+      auto t32 = r2c_table<float>(Nx);
+      auto t64 = r2c_table<double>(Nx);
+      p->tb.r32[pw] = dalloc(p.get(), sizeof(float2) * t32.size());
+      p->tb.r64[pw] = dalloc(p.get(), sizeof(double2) * t64.size());
+      CK(cudaMemcpy(p->tb.r32[pw], t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(p->tb.r64[pw], t64.data(), sizeof(double2) * t64.size(), cudaMemcpyHostToDevice));
     }
     for (auto& kv : bys) {
       const auto& sh = kv.first;
@@ -985,6 +1121,7 @@ ffcz_status ffcz_check(ffcz_plan_t plan, const float* e, const double* eps_s, co
   return guarded([&]() -> ffcz_status {
     if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
     CK(cudaSetDevice(plan->device));
+    ProfOn prof_on(plan);
     upload_params(plan, eps_s, eps_f, 0, 0);
     CK(cudaEventRecord(plan->ev0, plan->stream));
     cert_reset(plan);
@@ -1029,6 +1166,28 @@ const char* ffcz_strerror(ffcz_status s) {
 }
 
 const char* ffcz_last_error(void) { return g_err.c_str(); }
+
+ffcz_status ffcz_profile_enable(ffcz_plan_t plan, int on) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  plan->prof = on != 0;
+  plan->prof_tab.clear();
+  plan->prof_keys.clear();
+  return FFCZ_OK;
+}
+
+int ffcz_profile_count(ffcz_plan_t plan) { return plan ? (int)plan->prof_keys.size() : 0; }
+
+ffcz_status ffcz_profile_entry(ffcz_plan_t plan, int i, char* name, int name_len, double* ms,
+                               int64_t* launches) {
+  if (!plan || i < 0 || i >= (int)plan->prof_keys.size() || !name || name_len < 1)
+    return FFCZ_ERR_INVALID;
+  const std::string& k = plan->prof_keys[i];
+  snprintf(name, (size_t)name_len, "%s", k.c_str());
+  const auto& v = plan->prof_tab[k];
+  if (ms) *ms = v.first;
+  if (launches) *launches = v.second;
+  return FFCZ_OK;
+}
 
 int64_t ffcz_launch_count(void) { return g_launches.load(); }
 

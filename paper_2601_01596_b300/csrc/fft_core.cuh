@@ -3,22 +3,26 @@
 // One "tile" is W pencils of length L (a power of two, 8..1024) processed by
 // (L/8)*W threads.  Thread (j, w) with w = tid % W, j = tid / W holds eight
 // complex values of pencil w in registers: v[u] = x[j + u*L/8] (u = 0..7).
-// Between the radix stages the values go through shared memory; the pencils
-// are interleaved there so that a half-warp touching the same index of its
-// W pencils reads one 64-byte row.  Two rows share a 128-byte line and a
-// one-bit XOR swizzle on the line half keeps the stage permutations nearly
-// free of bank conflicts (about 5% extra wavefronts, all L).
+// Between the radix stages the values go through shared memory, pencils
+// interleaved (element l of pencil w at row l, column w; rows of W elements
+// are 64 bytes) with one padding row after every 8 rows.  The padding keeps
+// every stage permutation within ~6% of the minimum number of shared-memory
+// wavefronts, and, unlike an XOR swizzle, gives each thread addresses of the
+// form base + compile-time offset.  Two tile buffers alternate ("ping-pong"),
+// so one barrier per exchange suffices.
 //
 // The transform is the unnormalised DFT of Eq. 1, X_k = sum_n x_n w^{nk},
-// w = exp(DIR 2 pi i / L), DIR = -1 forward, +1 inverse (no 1/L).  It is the
-// Stockham autosort formulation (Cooley-Tukey with a permuting store at
-// every stage, so input and output are in natural order): a first radix-2 or
-// radix-4 stage when log2(L) is not a multiple of 3, then radix-8 stages.
-// After the last stage thread j again holds X[j + u*L/8], which lets callers
-// fuse elementwise work (clips, masks, reductions) on the registers.
+// w = exp(DIR 2 pi i / L), DIR = -1 forward, +1 inverse (no 1/L), in the
+// Stockham autosort formulation (Cooley-Tukey with a permuting store after
+// every stage, natural order in and out).  Radix schedule: all radix-8 when
+// 3 | log2 L; otherwise one (log2 L = 3a+2) or two (3a+1) radix-4 stages
+// first.  After the last stage thread j again holds X[j + u*L/8], so callers
+// can fuse elementwise work (clips, masks, reductions) on the registers.
 //
-// Twiddles come from a table of exp(-2 pi i m / L), m < L, computed on the
-// host in long double and rounded once; the inverse uses the conjugate.
+// Twiddles: per stage (R, NS), for k < NS the factors exp(-2 pi i k t/(R NS)),
+// t = 1..R-1, stored contiguously (padded to 8 or 4 entries) so a thread
+// fetches its stage's factors with 128-bit loads.  They are computed on the
+// host in long double and rounded once; the inverse uses the conjugates.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -75,11 +79,7 @@ __device__ __forceinline__ v2<T> mul_w8_3(v2<T> a) {
   else return mk<T>(-(a.x + a.y) * s, (a.x - a.y) * s);
 }
 
-// In-register DFTs of size 2, 4, 8 in natural output order.
-template <typename T, int DIR>
-__device__ __forceinline__ void dft2(v2<T>& a0, v2<T>& a1) {
-  v2<T> t = a0; a0 = add<T>(t, a1); a1 = sub<T>(t, a1);
-}
+// In-register DFTs of size 4 and 8 in natural output order.
 template <typename T, int DIR>
 __device__ __forceinline__ void dft4(v2<T>& a0, v2<T>& a1, v2<T>& a2, v2<T>& a3) {
   v2<T> s02 = add<T>(a0, a2), d02 = sub<T>(a0, a2);
@@ -101,43 +101,75 @@ __device__ __forceinline__ void dft8(v2<T> (&a)[8]) {
   a[2] = add<T>(e2, o2); a[6] = sub<T>(e2, o2);
   a[3] = add<T>(e3, o3); a[7] = sub<T>(e3, o3);
 }
-
 template <int R, typename T, int DIR>
 __device__ __forceinline__ void dftR(v2<T> (&x)[R]) {
-  if constexpr (R == 2) dft2<T, DIR>(x[0], x[1]);
-  else if constexpr (R == 4) dft4<T, DIR>(x[0], x[1], x[2], x[3]);
+  if constexpr (R == 4) dft4<T, DIR>(x[0], x[1], x[2], x[3]);
   else dft8<T, DIR>(x);
 }
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
-// Shared-memory view of one pencil of an interleaved tile.
-// Rows of W elements are 64 bytes; element (l, w) of the tile lives at
-// line (l >> 1), half ((l & 1) ^ swz(l >> 1)), column w.
-template <typename T>
-struct Slot {
-  static constexpr int W = 64 / (int)sizeof(v2<T>);
-  v2<T>* base;  // tile base
-  int w;        // pencil index in the tile
-  __device__ __forceinline__ int idx(int l) const {
-    int m = l >> 1;
-    int half = (l & 1) ^ ((m ^ (m >> 2)) & 1);
-    return m * (2 * W) + half * W + w;
+// Radix schedule and twiddle-table layout for length L (host and device).
+template <int L>
+struct Sched {
+  static constexpr int lg = ilog2(L), a = lg / 3, b = lg % 3;
+  static constexpr int nst = (b == 0) ? a : a + 1;
+  __host__ __device__ static constexpr int radix(int s) {
+    return b == 0 ? 8 : (b == 2 ? (s == 0 ? 4 : 8) : (s < 2 ? 4 : 8));
   }
-  __device__ __forceinline__ v2<T>& at(int l) const { return base[idx(l)]; }
+  __host__ __device__ static constexpr int ns(int s) {
+    int n = 1;
+    for (int i = 0; i < s; ++i) n *= radix(i);
+    return n;
+  }
+  __host__ __device__ static constexpr int sp(int s) { return radix(s) == 8 ? 8 : 4; }
+  __host__ __device__ static constexpr int twoff(int s) {
+    int o = 0;
+    for (int i = 1; i < s; ++i) o += ns(i) * sp(i);
+    return o;
+  }
+  static constexpr int twsize = twoff(nst) > 0 ? twoff(nst) : 4;
 };
 
-// One Stockham stage: radix R, sub-transform size NS (R*NS divides L).
-// Every thread owns 8/R butterflies: j' = j + b*L/8, b < 8/R; butterfly j'
-// takes x[j' + t*L/R] (registers v[b + t*8/R]) and, after the twiddle
-// exp(DIR 2 pi i k t / (R NS)), k = j' mod NS, and the R-point DFT, puts
-// output t at position (j'/NS)*R*NS + k + t*NS.  The last stage keeps the
-// outputs in registers: they are then x[j + u*L/8] again.
-template <typename T, int L, int DIR, int R, int NS>
-__device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, const v2<T>* __restrict__ tw,
-                                               const Slot<T>& sm) {
-  constexpr int NT = L / 8, NB = 8 / R;
-  constexpr bool last = (R * NS == L);
+// Row index with one padding row after every 8 rows.
+__host__ __device__ constexpr int pidx(int l) { return l + (l >> 3); }
+
+// A thread's view of its pencil in two ping-pong tile buffers.
+template <typename T, int L>
+struct Tile {
+  static constexpr int W = 64 / (int)sizeof(v2<T>);
+  static constexpr int ROWS = L + L / 8;
+  static constexpr int ELEMS = ROWS * W;   // one buffer
+  v2<T>* p0;  // buffer used by even exchanges (+ w)
+  v2<T>* p1;  // buffer used by odd exchanges (+ w)
+  int ph;     // buffer the next exchange uses
+  __device__ __forceinline__ v2<T>* buf() const { return ph ? p1 : p0; }
+  __device__ __forceinline__ void flip() { ph ^= 1; }
+  // element l of this pencil / of the pencil `dw` columns away, current buffer
+  __device__ __forceinline__ v2<T>& at(int l) const { return buf()[pidx(l) * W]; }
+  __device__ __forceinline__ v2<T>& at_other(int l, int dw) const { return buf()[pidx(l) * W + dw]; }
+};
+
+// Natural-order row index of register u of thread j: pidx(j + u*NT).
+template <int NT>
+__device__ __forceinline__ int nat(int jb, int j, int u) {
+  if constexpr (NT % 8 == 0) return jb + u * (NT + NT / 8);
+  else return pidx(j + u * NT);
+}
+
+// One Stockham stage S of the schedule: radix R, sub-transform size NS.
+// Thread j owns 8/R butterflies j' = j + b*L/8; butterfly j' takes
+// x[j' + t*L/R] (registers v[b + t*8/R]); after the twiddles
+// exp(DIR 2 pi i k t/(R NS)), k = j' mod NS, and the R-point DFT, output t
+// goes to row (j'/NS)*R*NS + k + t*NS.  The last stage keeps the outputs in
+// registers: they are then x[j + u*L/8] again.
+template <typename T, int L, int DIR, int S>
+__device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, int jb,
+                                               const v2<T>* __restrict__ tw, Tile<T, L>& tl) {
+  using SC = Sched<L>;
+  constexpr int R = SC::radix(S), NS = SC::ns(S), NT = L / 8, NB = 8 / R, W = Tile<T, L>::W;
+  constexpr bool last = (S == SC::nst - 1);
+  v2<T>* dst = tl.buf();
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int jp = j + b * NT;
@@ -146,10 +178,19 @@ __device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, const v2<T>
 #pragma unroll
     for (int t = 0; t < R; ++t) x[t] = v[b + t * NB];
     if constexpr (NS > 1) {
+      // factors t = 1..R-1 of this butterfly, fetched two at a time
+      const v2<T>* twk = tw + SC::twoff(S) + k * SC::sp(S);
+      if constexpr (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(twk);
 #pragma unroll
-      for (int t = 1; t < R; ++t) {
-        const int m = k * t * (L / (R * NS));
-        x[t] = twmul<T, DIR>(x[t], tw[m]);
+        for (int i = 0; i < R / 2; ++i) {
+          const float4 f = q[i];
+          if (2 * i + 1 < R) x[2 * i + 1] = twmul<T, DIR>(x[2 * i + 1], mk<T>(f.x, f.y));
+          if (2 * i + 2 < R) x[2 * i + 2] = twmul<T, DIR>(x[2 * i + 2], mk<T>(f.z, f.w));
+        }
+      } else {
+#pragma unroll
+        for (int t = 1; t < R; ++t) x[t] = twmul<T, DIR>(x[t], twk[t - 1]);
       }
     }
     dftR<R, T, DIR>(x);
@@ -158,40 +199,58 @@ __device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, const v2<T>
       for (int t = 0; t < R; ++t) v[b + t * NB] = x[t];
     } else {
       const int o = (jp / NS) * (R * NS) + k;
+      if constexpr (NS >= 8) {
+        const int base = o + (o >> 3);
 #pragma unroll
-      for (int t = 0; t < R; ++t) sm.at(o + t * NS) = x[t];
+        for (int t = 0; t < R; ++t) dst[(base + t * (NS + NS / 8)) * W] = x[t];
+      } else if constexpr (NS == 4) {
+        const int base = o + (jp >> 2) * (R / 2);
+#pragma unroll
+        for (int t = 0; t < R; ++t) dst[(base + 4 * t + (t >> 1)) * W] = x[t];
+      } else {
+        const int base = jp * R + (R == 8 ? jp : (jp >> 1));
+#pragma unroll
+        for (int t = 0; t < R; ++t) dst[(base + t) * W] = x[t];
+      }
     }
   }
   if constexpr (!last) {
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = sm.at(j + u * NT);
-    __syncthreads();
+    for (int u = 0; u < 8; ++u) v[u] = dst[nat<NT>(jb, j, u) * W];
+    tl.flip();
   }
 }
 
-template <typename T, int L, int DIR, int NS>
-__device__ __forceinline__ void radix8_stages(v2<T> (&v)[8], int j, const v2<T>* __restrict__ tw,
-                                              const Slot<T>& sm) {
-  if constexpr (NS < L) {
-    stockham_stage<T, L, DIR, 8, NS>(v, j, tw, sm);
-    radix8_stages<T, L, DIR, NS * 8>(v, j, tw, sm);
+template <typename T, int L, int DIR, int S>
+__device__ __forceinline__ void stages_from(v2<T> (&v)[8], int j, int jb, const v2<T>* __restrict__ tw,
+                                            Tile<T, L>& tl) {
+  if constexpr (S < Sched<L>::nst) {
+    stockham_stage<T, L, DIR, S>(v, j, jb, tw, tl);
+    stages_from<T, L, DIR, S + 1>(v, j, jb, tw, tl);
   }
 }
 
-// Full length-L transform of the thread's pencil.  Must be called by every
-// thread of the CTA (it synchronises the block between stages).
+// Full length-L transform of the thread's pencil.  Every thread of the CTA
+// must call it (it synchronises the block between stages).  `jb` is
+// pidx(j) (precomputed by the caller).
 template <typename T, int L, int DIR>
-__device__ __forceinline__ void fft_pencil(v2<T> (&v)[8], int j, const v2<T>* __restrict__ tw,
-                                           const Slot<T>& sm) {
+__device__ __forceinline__ void fft_pencil(v2<T> (&v)[8], int j, int jb, const v2<T>* __restrict__ tw,
+                                           Tile<T, L>& tl) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "L must be a power of two >= 8");
-  constexpr int b = ilog2(L) % 3;
-  if constexpr (b == 0) {
-    radix8_stages<T, L, DIR, 1>(v, j, tw, sm);
-  } else {
-    stockham_stage<T, L, DIR, (1 << b), 1>(v, j, tw, sm);
-    radix8_stages<T, L, DIR, (1 << b)>(v, j, tw, sm);
-  }
+  stages_from<T, L, DIR, 0>(v, j, jb, tw, tl);
+}
+
+// Exchange: every thread stores its natural-order registers, the block
+// synchronises, and `f(l)` below reads other rows; afterwards the buffers
+// flip.  Used where an elementwise step needs X[-k] next to X[k].
+template <typename T, int L>
+__device__ __forceinline__ void store_nat(const v2<T> (&v)[8], int j, int jb, Tile<T, L>& tl) {
+  constexpr int NT = L / 8, W = Tile<T, L>::W;
+  v2<T>* dst = tl.buf();
+#pragma unroll
+  for (int u = 0; u < 8; ++u) dst[nat<NT>(jb, j, u) * W] = v[u];
+  __syncthreads();
 }
 
 }  // namespace ffcz

@@ -63,7 +63,7 @@ enum Pred : int { P_ALL = 0, P_ACTIVE = 1, P_EXIT = 2, P_PRECLIP = 3, P_UNCERT =
 enum Sel : int { S_CUR = 0, S_PREV = 1 };
 enum Mode : int {
   M_CLIP = 1, M_MASK = 2, M_RECORD = 4, M_MEASURE = 8, M_PRECLIP = 16, M_NOWRITE = 32,
-  M_CKPT = 64
+  M_CKPT = 64, M_COUNT = 128
 };
 
 struct Args {
@@ -86,7 +86,11 @@ __device__ __forceinline__ bool pred_ok(int pred, const ItemState& s, const Item
   switch (pred) {
     case P_ACTIVE: return !s.done;
     case P_EXIT: return s.done && s.t >= 1;
-    case P_PRECLIP: return __longlong_as_double((long long)s.emaxbits) > p.E;
+    case P_PRECLIP: {
+      // a non-finite field is left as it is: the check reports it
+      const double em = __longlong_as_double((long long)s.emaxbits);
+      return em > p.E && em <= DBL_MAX;
+    }
     case P_UNCERT: return !s.certified;
     default: return true;
   }
@@ -106,45 +110,112 @@ struct Geo {
   static constexpr int TPT = NT * W;                   // threads per tile
   static constexpr int G = TPT >= 256 ? 1 : 256 / TPT; // tiles per CTA
   static constexpr int NTHR = G * TPT;
-  static constexpr int TILE_ELEMS = L * W;
+  // resident CTAs per SM the register budget is sized for: float32 tiles
+  // get 1024 threads per SM (64 registers), float64 tiles 512 (128 registers)
   static constexpr int MINB = sizeof(T) == 4 ? (1024 / NTHR > 0 ? 1024 / NTHR : 1)
                                              : (512 / NTHR > 0 ? 512 / NTHR : 1);
 };
 
-// Block reduction of (max, count, sum, nan flag); thread 0 publishes.
+// Shared-memory carve-up: [G tiles x 2 buffers][stage twiddles][R2C twiddles][reduction].
+template <typename T, int L>
+struct Smem {
+  static constexpr size_t tiles = (size_t)Geo<T, L>::G * 2 * Tile<T, L>::ELEMS * sizeof(v2<T>);
+  static constexpr size_t tw = (size_t)Sched<L>::twsize * sizeof(v2<T>);
+  static constexpr size_t twr = (size_t)L * sizeof(v2<T>);
+  static constexpr size_t red = 32 * 8 * 3 + 32 * 4;
+  static constexpr size_t bytes_axis = tiles + tw + red;
+  static constexpr size_t bytes_x = tiles + tw + twr + red;
+};
+
+// Block reduction of (max as non-negative double bits, count, sum).
 struct Red {
-  double vmax;
+  unsigned long long vbits;
   double sum;
   unsigned long long cnt;
-  int nan;
 };
-__device__ __forceinline__ void block_reduce(Red& r, double* sm_d, unsigned long long* sm_c,
-                                             int* sm_n) {
+__device__ __forceinline__ void block_reduce(Red& r, unsigned long long* sm) {
   const unsigned full = 0xffffffffu;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    r.vmax = fmax(r.vmax, __shfl_xor_sync(full, r.vmax, o));
+    r.vbits = max(r.vbits, __shfl_xor_sync(full, r.vbits, o));
     r.sum += __shfl_xor_sync(full, r.sum, o);
     r.cnt += __shfl_xor_sync(full, r.cnt, o);
-    r.nan |= __shfl_xor_sync(full, r.nan, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double* smd = reinterpret_cast<double*>(sm + 32);
+  __syncthreads();
+  if (lane == 0) { sm[wid] = r.vbits; smd[wid] = r.sum; sm[64 + wid] = r.cnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < nw; ++i) { r.vbits = max(r.vbits, sm[i]); r.sum += smd[i]; r.cnt += sm[64 + i]; }
+  }
+}
+
+// Block reduction of a max (double bits) and, if `with_count`, a count.
+__device__ __forceinline__ void block_max_count(unsigned long long& vb, unsigned long long& c,
+                                                bool with_count, unsigned long long* sm) {
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vb = max(vb, __shfl_xor_sync(full, vb, o));
+    if (with_count) c += __shfl_xor_sync(full, c, o);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();
-  if (lane == 0) { sm_d[wid] = r.vmax; sm_d[32 + wid] = r.sum; sm_c[wid] = r.cnt; sm_n[wid] = r.nan; }
+  if (lane == 0) { sm[wid] = vb; sm[64 + wid] = c; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < nw; ++i) {
-      r.vmax = fmax(r.vmax, sm_d[i]); r.sum += sm_d[32 + i]; r.cnt += sm_c[i]; r.nan |= sm_n[i];
-    }
+    for (int i = 1; i < nw; ++i) { vb = max(vb, sm[i]); c += sm[64 + i]; }
   }
 }
 
-__device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v) {
-  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+// Running max of |x|.  float32: one FMNMX per value (NaN is caught apart);
+// float64: integer max of the magnitude bits (keeps the FP64 pipe for the
+// butterflies; NaN orders above +inf).
+template <typename T> struct AbsMax;
+template <> struct AbsMax<float> {
+  float m = 0.f;
+  __device__ __forceinline__ void add(float x) { m = fmaxf(m, fabsf(x)); }
+  __device__ __forceinline__ float val() const { return m; }
+  __device__ __forceinline__ unsigned long long dbits(bool bad) const {
+    return (unsigned long long)__double_as_longlong(bad ? (double)INFINITY : (double)m);
+  }
+};
+template <> struct AbsMax<double> {
+  unsigned long long b = 0;
+  __device__ __forceinline__ void add(double x) {
+    b = max(b, (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull);
+  }
+  __device__ __forceinline__ double val() const { return __longlong_as_double((long long)b); }
+  __device__ __forceinline__ unsigned long long dbits(bool bad) const {
+    return (bad || b > 0x7ff0000000000000ull) ? 0x7ff0000000000000ull : b;
+  }
+};
+
+// A NaN or Inf anywhere in a field reaches every bin of the transform along
+// each axis it passes (butterflies add it into every output, and Inf times an
+// exact-zero twiddle component is NaN), so after the forward passes either the
+// magnitude max is Inf or every value is NaN.  Two probes per thread detect
+// the all-NaN case.
+template <typename T>
+__device__ __forceinline__ bool nan_probe(const v2<T> (&v)[8]) {
+  return (v[0].x != v[0].x) | (v[7].y != v[7].y);
 }
 
+__device__ __forceinline__ float clampT(float x, float b) { return fminf(fmaxf(x, -b), b); }
+__device__ __forceinline__ double clampT(double x, double b) { return fmin(fmax(x, -b), b); }
+
 template <typename T>
-__device__ __forceinline__ T clampT(T x, T b) { return x > b ? b : (x < -b ? -b : x); }
+__device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int ntw, v2<T>* s_twr,
+                                            const void* twr, int M) {
+  const v2<T>* gtw = reinterpret_cast<const v2<T>*>(tw);
+  for (int i = threadIdx.x; i < ntw; i += blockDim.x) s_tw[i] = gtw[i];
+  if (s_twr) {
+    const v2<T>* gtr = reinterpret_cast<const v2<T>*>(twr);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) s_twr[i] = gtr[i];
+  }
+  __syncthreads();
+}
 
 // ---------------------------------------------------------------------------
 // x passes: real rows <-> packed complex rows (R2C / C2R of length Nx = 2M
@@ -152,19 +223,17 @@ __device__ __forceinline__ T clampT(T x, T b) { return x > b ? b : (x < -b ? -b 
 // ---------------------------------------------------------------------------
 
 // Post-processing of Z = FFT_M(z) into the packed half spectrum P (in place
-// in registers).  Needs Z[M-k]; it is fetched from the tile in shared memory.
+// in registers).  Needs Z[M-k], fetched through one shared-memory exchange.
 template <typename T, int M>
-__device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, const Slot<T>& sm,
+__device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, int jb, Tile<T, M>& tl,
                                          const v2<T>* __restrict__ twr) {
   constexpr int NT = M / 8;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) sm.at(j + u * NT) = v[u];
-  __syncthreads();
+  store_nat<T, M>(v, j, jb, tl);
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int k = j + u * NT;
     const v2<T> zk = v[u];
-    const v2<T> zm = sm.at((M - k) & (M - 1));
+    const v2<T> zm = tl.at((M - k) & (M - 1));
     if (k == 0) {
       v[u] = mk<T>(zk.x + zk.y, zk.x - zk.y);
     } else {
@@ -174,23 +243,21 @@ __device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, const Slot<T>& sm
       v[u] = add<T>(fe, cmul<T>(twr[k], fo));
     }
   }
-  __syncthreads();
+  tl.flip();
 }
 
 // Pre-processing of packed P into Z' = 2 Z so that IFFT_M(Z') / Nx gives
 // the real row (again one exchange for P[M-k]).
 template <typename T, int M>
-__device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, const Slot<T>& sm,
+__device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, Tile<T, M>& tl,
                                         const v2<T>* __restrict__ twr) {
   constexpr int NT = M / 8;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) sm.at(j + u * NT) = v[u];
-  __syncthreads();
+  store_nat<T, M>(v, j, jb, tl);
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int k = j + u * NT;
     const v2<T> xk = v[u];
-    const v2<T> xm = sm.at((M - k) & (M - 1));
+    const v2<T> xm = tl.at((M - k) & (M - 1));
     if (k == 0) {
       v[u] = mk<T>(xk.x + xk.y, xk.x - xk.y);
     } else {
@@ -200,75 +267,58 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, const Slot<T>& sm,
       v[u] = mk<T>(s.x - d.y, s.y + d.x);
     }
   }
-  __syncthreads();
+  tl.flip();
 }
 
-template <typename T>
-__device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int L, v2<T>* s_twr,
-                                            const void* twr, int M) {
-  const v2<T>* gtw = reinterpret_cast<const v2<T>*>(tw);
-  for (int i = threadIdx.x; i < L; i += blockDim.x) s_tw[i] = gtw[i];
-  if (s_twr) {
-    const v2<T>* gtr = reinterpret_cast<const v2<T>*>(twr);
-    for (int i = threadIdx.x; i < M; i += blockDim.x) s_twr[i] = gtr[i];
-  }
-}
-
-// Shared-memory carve-up: [tiles][twiddles][R2C twiddles][reduction scratch].
-template <typename T, int L>
-struct Smem {
-  static constexpr size_t tiles = (size_t)Geo<T, L>::G * Geo<T, L>::TILE_ELEMS * sizeof(v2<T>);
-  static constexpr size_t tw = (size_t)L * sizeof(v2<T>);
-  static constexpr size_t red = 32 * 8 * 2 + 32 * 8 + 32 * 4;
-  static constexpr size_t bytes_axis = tiles + tw + red;
-  static constexpr size_t bytes_x = tiles + 2 * tw + red;
-};
+#define FFCZ_X_PROLOGUE(T_, M_)                                                   \
+  using G_ = Geo<T_, M_>;                                                         \
+  using TL = Tile<T_, M_>;                                                        \
+  extern __shared__ __align__(16) unsigned char smraw[];                          \
+  v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
+  v2<T_>* s_tw = s_tiles + G_::G * 2 * TL::ELEMS;                                \
+  v2<T_>* s_twr = s_tw + Sched<M_>::twsize;                                       \
+  unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M_); \
+  const int gi = blockIdx.y;                                                      \
+  const int item = a.g.item[gi];                                                  \
+  const ItemParams& p = a.prm[item];                                              \
+  ItemState& st = a.st[item];                                                     \
+  if (!pred_ok(a.pred, st, p)) return;                                            \
+  const int t_it = st.t;                                                          \
+  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
+  const int w = tid % G_::W, j = tid / G_::W, jb = pidx(j);                       \
+  const int tile = blockIdx.x * G_::G + g;                                        \
+  const int ntiles = (int)(a.g.rows / G_::W);                                     \
+  const bool live = tile < ntiles;                                                \
+  const int row = live ? tile * G_::W + w : 0;                                    \
+  TL tl{s_tiles + g * 2 * TL::ELEMS + w, s_tiles + g * 2 * TL::ELEMS + TL::ELEMS + w, 0}; \
+  (void)t_it;
 
 // Entry / certification x pass: float32 real rows -> packed spectrum.
 template <typename T, int M>
 __global__ void __launch_bounds__(Geo<T, M>::NTHR, Geo<T, M>::MINB)
 k_xfwd(Args a) {
-  using G_ = Geo<T, M>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  v2<T>* s_tiles = reinterpret_cast<v2<T>*>(smraw);
-  v2<T>* s_tw = s_tiles + G_::G * G_::TILE_ELEMS;
-  v2<T>* s_twr = s_tw + M;
-  double* s_red = reinterpret_cast<double*>(s_twr + M);
-
-  const int gi = blockIdx.y;
-  const int item = a.g.item[gi];
-  const ItemParams& p = a.prm[item];
-  ItemState& st = a.st[item];
-  if (!pred_ok(a.pred, st, p)) return;
-  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
-
-  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
-  const int w = tid % G_::W, j = tid / G_::W;
-  const int64_t tile = (int64_t)blockIdx.x * G_::G + g;
-  const int64_t ntiles = a.g.rows / G_::W;
-  const bool live = tile < ntiles;
-  const int64_t row = live ? tile * G_::W + w : 0;
-  Slot<T> sm{s_tiles + g * G_::TILE_ELEMS, w};
-
+  FFCZ_X_PROLOGUE(T, M)
   const float* src = (a.mode & M_MASK) ? a.ein : a.e;
   const float2* erow = reinterpret_cast<const float2*>(src + a.g.eoff[gi]) + row * M;
   float2* erow_w = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
-  Red r{0.0, 0.0, 0ull, 0};
+  AbsMax<float> mx;
+  float ssq = 0.f;
+  unsigned long long cnt = 0;
   uint32_t bits = 0;
   if ((a.mode & M_MASK) && live) bits = a.mask[tile * G_::TPT + tid];
   v2<T> v[8];
+  bool bad = false;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     float2 x = erow[j + u * G_::NT];
     if (a.mode & M_MEASURE) {
-      const double ax = fabs((double)x.x), ay = fabs((double)x.y);
-      r.vmax = fmax(r.vmax, fmax(ax, ay));
-      r.sum += (double)x.x * x.x + (double)x.y * x.y;
-      r.nan |= (x.x != x.x) | (x.y != x.y);
+      mx.add(x.x); mx.add(x.y);
+      bad |= (x.x != x.x) | (x.y != x.y);
+      ssq = fmaf(x.x, x.x, fmaf(x.y, x.y, ssq));
     }
     if (a.mode & M_PRECLIP) {
-      const float cx = clampT<float>(x.x, p.Esf), cy = clampT<float>(x.y, p.Esf);
-      r.cnt += (cx != x.x) + (cy != x.y);
+      const float cx = clampT(x.x, p.Esf), cy = clampT(x.y, p.Esf);
+      cnt += (cx != x.x) + (cy != x.y);
       x.x = cx; x.y = cy;
       if (live) erow_w[j + u * G_::NT] = x;
     }
@@ -278,21 +328,22 @@ k_xfwd(Args a) {
     }
     v[u] = mk<T>((T)x.x, (T)x.y);
   }
-  if (!live) r = Red{0.0, 0.0, 0ull, 0};
-  __syncthreads();
-  fft_pencil<T, M, -1>(v, j, s_tw, sm);
-  r2c_post<T, M>(v, j, sm, s_twr);
+  load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
+  fft_pencil<T, M, -1>(v, j, jb, s_tw, tl);
+  r2c_post<T, M>(v, j, jb, tl, s_twr);
   if (live) {
-    v2<T>* out = pick<T>(a, a.sel_out, st.t) + a.g.soff[gi] + row * M;
+    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
     for (int u = 0; u < 8; ++u) out[j + u * G_::NT] = v[u];
   }
   if (a.mode & (M_MEASURE | M_PRECLIP)) {
-    block_reduce(r, s_red, reinterpret_cast<unsigned long long*>(s_red + 64),
-                 reinterpret_cast<int*>(s_red + 96));
+    // 16 float32 squares summed in float32: relative error < 17 u32; the
+    // bound that uses this sum takes (1 + 2^-18) of it.
+    Red r{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-18) : 0.0, live ? cnt : 0ull};
+    block_reduce(r, s_red);
     if (threadIdx.x == 0) {
       if (a.mode & M_MEASURE) {
-        atomic_max_pos(&st.emaxbits, r.nan ? INFINITY : r.vmax);
+        atomicMax(&st.emaxbits, r.vbits);
         atomicAdd(&st.sumsq, r.sum);
       }
       if ((a.mode & M_PRECLIP) && r.cnt) atomicAdd(&st.act_s, r.cnt);
@@ -300,116 +351,108 @@ k_xfwd(Args a) {
   }
 }
 
-// Loop body x pass: C2R, scale 1/N, s-clip (or adjoint mask), R2C.
+// s-clip of the thread's 16 values with every option (mask recording,
+// checkpoint writes); the lean loop path uses s_clip_fast.
+template <typename T>
+__device__ __forceinline__ void s_clip_full(v2<T> (&v)[8], T Es, bool count, uint32_t& bits,
+                                            unsigned long long& cnt, float2* ck, int j, int NT) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    T x = v[u].x, y = v[u].y;
+    const T cx = clampT(x, Es), cy = clampT(y, Es);
+    const bool ix = (cx == x), iy = (cy == y);   // inside the s-cube
+    if (count) cnt += (!ix) + (!iy);
+    bits |= ((uint32_t)ix << (2 * u)) | ((uint32_t)iy << (2 * u + 1));
+    v[u] = mk<T>(cx, cy);
+    if (ck) ck[j + u * NT] = make_float2((float)cx, (float)cy);
+  }
+}
+
+// Loop body x pass on one tile held in registers: C2R, scale 1/N, s-clip
+// (or adjoint mask), R2C.  Returns the active-clip count of the thread.
+template <typename T, int M>
+__device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[8],
+                                                      int j, int jb, int tid, int tile, int row, bool live,
+                                                      int t_it, Tile<T, M>& tl, const v2<T>* twg,
+                                                      const v2<T>* twr) {
+  using G_ = Geo<T, M>;
+  c2r_pre<T, M>(v, j, jb, tl, twr);
+  fft_pencil<T, M, +1>(v, j, jb, twg, tl);
+  unsigned long long cnt = 0;
+  uint32_t bits = 0;
+  const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
+  const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
+  AbsMax<T> mx;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    v[u] = mk<T>(v[u].x * inv_n, v[u].y * inv_n);
+    mx.add(v[u].x); mx.add(v[u].y);
+  }
+  const bool count = (a.mode & M_COUNT) != 0;
+  const bool need_clip = __any_sync(0xffffffffu, mx.val() > Es);   // all lanes vote
+  if (a.mode & M_MASK) {
+    if (live) bits = a.mask[tile * G_::TPT + tid];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (!((bits >> (2 * u)) & 1u)) v[u].x = T(0);
+      if (!((bits >> (2 * u + 1)) & 1u)) v[u].y = T(0);
+    }
+  } else if (a.mode & (M_RECORD | M_CKPT)) {
+    const bool ckn = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 && live;
+    float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * (2 * M * a.g.rows)) + (int64_t)row * M
+                     : nullptr;
+    s_clip_full<T>(v, Es, count, bits, cnt, ck, j, G_::NT);
+    if ((a.mode & M_RECORD) && live) a.mask[tile * G_::TPT + tid] = bits;
+  } else if (need_clip) {
+    // lean path: only warps holding a value outside the s-cube clip
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T cx = clampT(v[u].x, Es), cy = clampT(v[u].y, Es);
+      if (count) cnt += (cx != v[u].x) + (cy != v[u].y);
+      v[u] = mk<T>(cx, cy);
+    }
+  }
+  fft_pencil<T, M, -1>(v, j, jb, twg, tl);
+  r2c_post<T, M>(v, j, jb, tl, twr);
+  return live ? cnt : 0ull;
+}
+
 template <typename T, int M>
 __global__ void __launch_bounds__(Geo<T, M>::NTHR, Geo<T, M>::MINB)
 k_px(Args a) {
-  using G_ = Geo<T, M>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  v2<T>* s_tiles = reinterpret_cast<v2<T>*>(smraw);
-  v2<T>* s_tw = s_tiles + G_::G * G_::TILE_ELEMS;
-  v2<T>* s_twr = s_tw + M;
-  double* s_red = reinterpret_cast<double*>(s_twr + M);
-
-  const int gi = blockIdx.y;
-  const int item = a.g.item[gi];
-  const ItemParams& p = a.prm[item];
-  ItemState& st = a.st[item];
-  if (!pred_ok(a.pred, st, p)) return;
-  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
-  const int t = st.t;
-
-  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
-  const int w = tid % G_::W, j = tid / G_::W;
-  const int64_t tile = (int64_t)blockIdx.x * G_::G + g;
-  const int64_t ntiles = a.g.rows / G_::W;
-  const bool live = tile < ntiles;
-  const int64_t row = live ? tile * G_::W + w : 0;
-  Slot<T> sm{s_tiles + g * G_::TILE_ELEMS, w};
-
-  const v2<T>* in = pick<T>(a, a.sel_in, t) + a.g.soff[gi] + row * M;
+  FFCZ_X_PROLOGUE(T, M)
+  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) v[u] = in[j + u * G_::NT];
-  __syncthreads();
-  c2r_pre<T, M>(v, j, sm, s_twr);
-  fft_pencil<T, M, +1>(v, j, s_tw, sm);
-
-  Red r{0.0, 0.0, 0ull, 0};
-  uint32_t bits = 0;
-  const bool ck = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t % a.ckpt_every) == 0;
-  float2* ck_row = ck ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t / a.ckpt_every) * (2 * M * a.g.rows)) + row * M
-                      : nullptr;
-  if ((a.mode & M_MASK) && live) bits = a.mask[tile * G_::TPT + tid];
-  const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
-  const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    T x = v[u].x * inv_n, y = v[u].y * inv_n;
-    if (a.mode & M_CLIP) {
-      const T cx = clampT<T>(x, Es), cy = clampT<T>(y, Es);
-      const bool ix = (cx == x), iy = (cy == y);   // inside the s-cube
-      r.cnt += (!ix) + (!iy);
-      bits |= ((uint32_t)ix << (2 * u)) | ((uint32_t)iy << (2 * u + 1));
-      x = cx; y = cy;
-      if (ck && live) ck_row[j + u * G_::NT] = make_float2((float)x, (float)y);
-    } else if (a.mode & M_MASK) {
-      if (!((bits >> (2 * u)) & 1u)) x = T(0);
-      if (!((bits >> (2 * u + 1)) & 1u)) y = T(0);
-    }
-    v[u] = mk<T>(x, y);
-  }
-  if ((a.mode & M_RECORD) && live) a.mask[tile * G_::TPT + tid] = bits;
-  fft_pencil<T, M, -1>(v, j, s_tw, sm);
-  r2c_post<T, M>(v, j, sm, s_twr);
+  load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
+  unsigned long long cnt = px_core<T, M>(a, p, v, j, jb, tid, tile, row, live, t_it, tl, s_tw, s_twr);
   if (live) {
-    v2<T>* out = pick<T>(a, a.sel_out, t) + a.g.soff[gi] + row * M;
+    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
     for (int u = 0; u < 8; ++u) out[j + u * G_::NT] = v[u];
   }
-  if (a.mode & M_CLIP) {
-    if (!live) r.cnt = 0;
-    block_reduce(r, s_red, reinterpret_cast<unsigned long long*>(s_red + 64),
-                 reinterpret_cast<int*>(s_red + 96));
+  if (a.mode & M_COUNT) {
+    Red r{0ull, 0.0, cnt};
+    block_reduce(r, s_red);
     if (threadIdx.x == 0 && r.cnt) atomicAdd(&st.act_s, r.cnt);
   }
 }
 
 // Exit x pass: C2R, scale 1/N, s-clip, store float32 e (rebuilds the iterate
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
-// no clip is applied.
+// no clip is applied.  With M_COUNT it counts the final iterate's s-clips.
 template <typename T, int M>
 __global__ void __launch_bounds__(Geo<T, M>::NTHR, Geo<T, M>::MINB)
 k_xexit(Args a) {
-  using G_ = Geo<T, M>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  v2<T>* s_tiles = reinterpret_cast<v2<T>*>(smraw);
-  v2<T>* s_tw = s_tiles + G_::G * G_::TILE_ELEMS;
-  v2<T>* s_twr = s_tw + M;
-
-  const int gi = blockIdx.y;
-  const int item = a.g.item[gi];
-  const ItemParams& p = a.prm[item];
-  ItemState& st = a.st[item];
-  if (!pred_ok(a.pred, st, p)) return;
-  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
-  const int t = st.t;
-
-  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
-  const int w = tid % G_::W, j = tid / G_::W;
-  const int64_t tile = (int64_t)blockIdx.x * G_::G + g;
-  const int64_t ntiles = a.g.rows / G_::W;
-  const bool live = tile < ntiles;
-  const int64_t row = live ? tile * G_::W + w : 0;
-  Slot<T> sm{s_tiles + g * G_::TILE_ELEMS, w};
-
-  const v2<T>* in = pick<T>(a, a.sel_in, t) + a.g.soff[gi] + row * M;
+  FFCZ_X_PROLOGUE(T, M)
+  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) v[u] = in[j + u * G_::NT];
-  __syncthreads();
-  c2r_pre<T, M>(v, j, sm, s_twr);
-  fft_pencil<T, M, +1>(v, j, s_tw, sm);
+  load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
+  c2r_pre<T, M>(v, j, jb, tl, s_twr);
+  fft_pencil<T, M, +1>(v, j, jb, s_tw, tl);
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
@@ -417,11 +460,11 @@ k_xexit(Args a) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       T x = v[u].x * inv_n, y = v[u].y * inv_n;
-      if (a.mode & M_CLIP) { x = clampT<T>(x, Es); y = clampT<T>(y, Es); }
+      if (a.mode & M_CLIP) { x = clampT(x, Es); y = clampT(y, Es); }
       float fx = (float)x, fy = (float)y;
       if (a.mode & M_CLIP) {
         // keep the float32 result inside the shrunk cube after rounding
-        fx = clampT<float>(fx, p.Esf); fy = clampT<float>(fy, p.Esf);
+        fx = clampT(fx, p.Esf); fy = clampT(fy, p.Esf);
       }
       erow[j + u * G_::NT] = make_float2(fx, fy);
     }
@@ -432,45 +475,50 @@ k_xexit(Args a) {
 // Strided axis passes
 // ---------------------------------------------------------------------------
 
+#define FFCZ_AXIS_PROLOGUE(T_, L_)                                                \
+  using G_ = Geo<T_, L_>;                                                         \
+  using TL = Tile<T_, L_>;                                                        \
+  extern __shared__ __align__(16) unsigned char smraw[];                          \
+  v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
+  v2<T_>* s_tw = s_tiles + G_::G * 2 * TL::ELEMS;                                \
+  unsigned long long* s_red =                                                     \
+      reinterpret_cast<unsigned long long*>(s_tw + Sched<L_>::twsize);            \
+  (void)s_red;                                                                    \
+  const int gi = blockIdx.y;                                                      \
+  const int item = a.g.item[gi];                                                  \
+  const ItemParams& p = a.prm[item];                                              \
+  ItemState& st = a.st[item];                                                     \
+  if (!pred_ok(a.pred, st, p)) return;                                            \
+  const int t_it = st.t;                                                          \
+  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
+  const int w = tid % G_::W, j = tid / G_::W, jb = pidx(j);                       \
+  const int tile = blockIdx.x * G_::G + g;                                        \
+  TL tl{s_tiles + g * 2 * TL::ELEMS + w, s_tiles + g * 2 * TL::ELEMS + TL::ELEMS + w, 0};
+
 // Plain C2C along the middle axis of a 3D item (y): pencils at fixed (z, kx).
 template <typename T, int L, int DIR>
 __global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
 k_axis(Args a) {
-  using G_ = Geo<T, L>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  v2<T>* s_tiles = reinterpret_cast<v2<T>*>(smraw);
-  v2<T>* s_tw = s_tiles + G_::G * G_::TILE_ELEMS;
-
-  const int gi = blockIdx.y;
-  const int item = a.g.item[gi];
-  const ItemParams& p = a.prm[item];
-  ItemState& st = a.st[item];
-  if (!pred_ok(a.pred, st, p)) return;
-  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);
-  const int t = st.t;
-
-  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
-  const int w = tid % G_::W, j = tid / G_::W;
+  FFCZ_AXIS_PROLOGUE(T, L)
   const int M = a.g.M;
-  const int tpr = M / G_::W;                      // tiles per z-plane
-  const int64_t tile = (int64_t)blockIdx.x * G_::G + g;
-  const int64_t ntiles = (int64_t)a.g.Nz * tpr;
+  const unsigned tpr = (unsigned)(M / G_::W);     // tiles per z-plane
+  const int ntiles = a.g.Nz * (int)tpr;
   const bool live = tile < ntiles;
-  const int64_t z = live ? tile / tpr : 0;
-  const int kx = live ? (int)(tile % tpr) * G_::W + w : 0;
-  const int64_t base = a.g.soff[gi] + z * (int64_t)L * M + kx;
-  Slot<T> sm{s_tiles + g * G_::TILE_ELEMS, w};
+  const int z = live ? (int)((unsigned)tile / tpr) : 0;
+  const int kx = live ? (int)((unsigned)tile % tpr) * G_::W + w : 0;
+  const int off = z * L * M + kx;
 
-  const v2<T>* in = pick<T>(a, a.sel_in, t) + base;
+  const int64_t ustride = (int64_t)G_::NT * M;
+  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + off + j * M;
   v2<T> v[8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = in[(int64_t)(j + u * G_::NT) * M];
-  __syncthreads();
-  fft_pencil<T, L, DIR>(v, j, s_tw, sm);
+  for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
+  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);   // overlaps the loads
+  fft_pencil<T, L, DIR>(v, j, jb, s_tw, tl);
   if (live) {
-    v2<T>* out = pick<T>(a, a.sel_out, t) + base;
+    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + off + j * M;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[(int64_t)(j + u * G_::NT) * M] = v[u];
+    for (int u = 0; u < 8; ++u) out[u * ustride] = v[u];
   }
 }
 
@@ -479,101 +527,87 @@ k_axis(Args a) {
 // (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
 // the inverse FFT of this axis is applied before the store.
 //
-// Tiles are of two kinds.  Main tiles: W consecutive kx >= 1 at one middle
-// index (slot kx = 0 skipped).  Mirror tiles: the kx = 0 pencils, in pairs
-// (m, -m) of middle indices so that A and B can be separated; a pencil that
-// is its own mirror (m = 0 or Nmid/2) fills both slots of its pair and only
-// the first slot stores.
-template <typename T, int L>
-__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
-k_chk(Args a) {
-  using G_ = Geo<T, L>;
-  constexpr int W = G_::W, NT = G_::NT;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  v2<T>* s_tiles = reinterpret_cast<v2<T>*>(smraw);
-  v2<T>* s_tw = s_tiles + G_::G * G_::TILE_ELEMS;
-  double* s_red = reinterpret_cast<double*>(s_tw + L);
+// Tiles are of two kinds.  Main tiles: W consecutive kx at one middle index
+// (slot kx = 0 skipped).  Mirror tiles: the kx = 0 pencils, in pairs (m, -m)
+// of middle indices so that A and B can be separated; a pencil that is its
+// own mirror (m = 0 or Nmid/2) fills both slots of its pair and only the
+// first slot stores.
+struct ChkTile {
+  int off;       // complex offset of the pencil in the item's spectrum
+  bool owner;    // this slot stores its pencil
+  bool valid;    // this slot holds bins to check
+  bool mirror;   // the tile is a kx = 0 mirror tile
+  bool live;
+};
 
-  const int gi = blockIdx.y;
-  const int item = a.g.item[gi];
-  const ItemParams& p = a.prm[item];
-  ItemState& st = a.st[item];
-  if (!pred_ok(a.pred, st, p)) return;
-  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);
-  const int t = st.t;
-
-  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
-  const int w = tid % W, j = tid / W;
-  const int M = a.g.M, Nmid = a.g.Nmid;
-  const int tpr = M / W;
-  const int64_t nmain = (int64_t)Nmid * tpr;
+template <int W>
+__device__ __forceinline__ ChkTile chk_decode(int tile, int w, int M, int Nmid) {
+  ChkTile c{0, false, false, false, false};
+  const unsigned tpr = (unsigned)(M / W);
+  const int nmain = Nmid * (int)tpr;
   const int npairs = Nmid / 2 + 1;   // pairs (m, -m), m = 0..Nmid/2
-  const int64_t nmirror = (npairs + W / 2 - 1) / (W / 2);
-  const int64_t tile = (int64_t)blockIdx.x * G_::G + g;
-  const bool live = tile < nmain + nmirror;
-  const bool mirror = live && tile >= nmain;
-  const int64_t estride = (int64_t)Nmid * M;
-
-  int64_t base = 0;
-  bool owner = false, valid = false;
-  if (live && !mirror) {
-    const int mid = (int)(tile / tpr);
-    const int kx = (int)(tile % tpr) * W + w;
-    base = (int64_t)mid * M + kx;
-    valid = kx != 0;
-    owner = valid;
-  } else if (mirror) {
-    const int q = (int)(tile - nmain) * (W / 2) + (w >> 1);
+  const int nmirror = (npairs + W / 2 - 1) / (W / 2);
+  c.live = tile < nmain + nmirror;
+  c.mirror = c.live && tile >= nmain;
+  if (c.live && !c.mirror) {
+    const int mid = (int)((unsigned)tile / tpr);
+    const int kx = (int)((unsigned)tile % tpr) * W + w;
+    c.off = mid * M + kx;
+    c.valid = kx != 0;
+    c.owner = c.valid;
+  } else if (c.mirror) {
+    const int q = (tile - nmain) * (W / 2) + (w >> 1);
     const int m = w & 1;
     const int nh = Nmid / 2;
-    valid = q < npairs;
+    c.valid = q < npairs;
     const bool selfm = (q == 0) || (q == nh);
-    const int mid = !valid ? 0 : (selfm ? q : (m ? Nmid - q : q));
-    base = (int64_t)mid * M;
-    owner = valid && (m == 0 || !selfm);
+    const int mid = !c.valid ? 0 : (selfm ? q : (m ? Nmid - q : q));
+    c.off = mid * M;
+    c.owner = c.valid && (m == 0 || !selfm);
   }
-  Slot<T> sm{s_tiles + g * G_::TILE_ELEMS, w};
+  return c;
+}
 
-  v2<T>* buf = pick<T>(a, a.sel_in, t) + a.g.soff[gi] + base;
-  v2<T> v[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = buf[(int64_t)(j + u * NT) * estride];
-  __syncthreads();
-  fft_pencil<T, L, -1>(v, j, s_tw, sm);
+__host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
+  const int npairs = Nmid / 2 + 1;
+  return Nmid * (M / W) + (npairs + W / 2 - 1) / (W / 2);
+}
 
-  // Any tile of this CTA may be a mirror tile; the exchange below needs the
-  // whole CTA, so it runs whenever one of the CTA's tiles is.
-  const int64_t first_tile = (int64_t)blockIdx.x * G_::G;
-  const int64_t last_tile = first_tile + G_::G - 1;
-  const bool cta_has_mirror = last_tile >= nmain && first_tile < nmain + nmirror;
-
+// Everything of the check pass between load and store for one tile in
+// registers.  cta_has_mirror must be uniform over the CTA.
+template <typename T, int L>
+__device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st, v2<T> (&v)[8],
+                                         int j, int jb, int w, int tid, int tile, const ChkTile& c,
+                                         bool cta_has_mirror, Tile<T, L>& tl, const v2<T>* twg,
+                                         unsigned long long* s_red) {
+  using G_ = Geo<T, L>;
+  constexpr int NT = G_::NT;
+  fft_pencil<T, L, -1>(v, j, jb, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
-  Red r{0.0, 0.0, 0ull, 0};
+  AbsMax<T> mx;
+  bool bad = false;
+  unsigned long long cnt = 0;
   uint32_t bits = 0;
   const bool rec = (a.mode & M_RECORD) != 0, use_mask = (a.mode & M_MASK) != 0;
-  if (use_mask && live) bits = a.mask[tile * G_::TPT + tid];
-  T vloc = T(0);
+  const bool clip = (a.mode & M_CLIP) != 0, count = (a.mode & M_COUNT) != 0;
+  if (use_mask && c.live) bits = a.mask[tile * G_::TPT + tid];
   if (cta_has_mirror) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) sm.at(j + u * NT) = v[u];
-    __syncthreads();
-    const Slot<T> smm{sm.base, w ^ 1};
-    if (mirror) {
+    store_nat<T, L>(v, j, jb, tl);
+    if (c.mirror) {
+      const int dw = (w ^ 1) - w;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const v2<T> c = v[u], m = smm.at((L - (j + u * NT)) & (L - 1));
+        const v2<T> cc = v[u], m = tl.at_other((L - (j + u * NT)) & (L - 1), dw);
         // A = (C + conj Cm)/2, B = (C - conj Cm)/(2i)
-        T ar = T(0.5) * (c.x + m.x), ai = T(0.5) * (c.y - m.y);
-        T br = T(0.5) * (c.y + m.y), bi = T(0.5) * (m.x - c.x);
-        if (valid) {
-          vloc = fmax(vloc, fmax(fmax(fabs(ar), fabs(ai)), fmax(fabs(br), fabs(bi))));
-          r.nan |= (ar != ar) | (ai != ai) | (br != br) | (bi != bi);
-        }
-        if (a.mode & M_CLIP) {
-          const T car = clampT<T>(ar, Ds), cai = clampT<T>(ai, Ds);
-          const T cbr = clampT<T>(br, Ds), cbi = clampT<T>(bi, Ds);
+        T ar = T(0.5) * (cc.x + m.x), ai = T(0.5) * (cc.y - m.y);
+        T br = T(0.5) * (cc.y + m.y), bi = T(0.5) * (m.x - cc.x);
+        if (c.valid) { mx.add(ar); mx.add(ai); mx.add(br); mx.add(bi); }
+        bad |= c.valid && ((ar != ar) | (ai != ai) | (br != br) | (bi != bi));
+        if (clip) {
+          const T car = clampT(ar, Ds), cai = clampT(ai, Ds);
+          const T cbr = clampT(br, Ds), cbi = clampT(bi, Ds);
           const bool iar = car == ar, iai = cai == ai, ibr = cbr == br, ibi = cbi == bi;
-          if (owner) r.cnt += (!(iar && iai)) + (!(ibr && ibi));
+          if (c.owner) cnt += (!iar) + (!iai) + (!ibr) + (!ibi);
           bits |= ((uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) | ((uint32_t)ibi << 3))
                   << (4 * u);
           ar = car; ai = cai; br = cbr; bi = cbi;
@@ -587,47 +621,83 @@ k_chk(Args a) {
         v[u] = mk<T>(ar - bi, ai + br);   // C' = A' + i B'
       }
     }
-    __syncthreads();
+    tl.flip();
   }
-  if (!mirror) {
+  // Main-tile magnitude max, and one vote over all lanes (a warp can span
+  // several tiles when tiles are small, so the vote is outside any branch
+  // that depends on the tile).
+  AbsMax<T> tm;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      T x = v[u].x, y = v[u].y;
-      if (valid) {
-        vloc = fmax(vloc, fmax(fabs(x), fabs(y)));
-        r.nan |= (x != x) | (y != y);
+  for (int u = 0; u < 8; ++u) { tm.add(v[u].x); tm.add(v[u].y); }
+  const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
+  if (!c.mirror) {
+    if (c.valid) { mx = tm; bad = nan_probe<T>(v); }
+    if (use_mask) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (!((bits >> (2 * u)) & 1u)) v[u].x = T(0);
+        if (!((bits >> (2 * u + 1)) & 1u)) v[u].y = T(0);
       }
-      if (a.mode & M_CLIP) {
-        const T cx = clampT<T>(x, Ds), cy = clampT<T>(y, Ds);
+    } else if (clip && (rec || need_clip)) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T x = v[u].x, y = v[u].y;
+        const T cx = clampT(x, Ds), cy = clampT(y, Ds);
         const bool ix = cx == x, iy = cy == y;
-        if (owner) r.cnt += 2 * (!(ix && iy));   // a stored bin stands for k and -k
+        if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
         bits |= ((uint32_t)ix << (2 * u)) | ((uint32_t)iy << (2 * u + 1));
-        x = cx; y = cy;
-      } else if (use_mask) {
-        if (!((bits >> (2 * u)) & 1u)) x = T(0);
-        if (!((bits >> (2 * u + 1)) & 1u)) y = T(0);
+        v[u] = mk<T>(cx, cy);
       }
-      v[u] = mk<T>(x, y);
+    } else if (clip) {
+      bits = 0xffffu;   // nothing clipped
     }
   }
-  if (rec && live) a.mask[tile * G_::TPT + tid] = bits;
-  r.vmax = (double)vloc;
-  if (!(a.mode & M_MASK)) {
-    block_reduce(r, s_red, reinterpret_cast<unsigned long long*>(s_red + 64),
-                 reinterpret_cast<int*>(s_red + 96));
+  if (rec && c.live) a.mask[tile * G_::TPT + tid] = bits;
+  if (!use_mask) {
+    unsigned long long vb = mx.dbits(bad), cc = cnt;
+    block_max_count(vb, cc, count, s_red);
     if (threadIdx.x == 0) {
-      atomic_max_pos(&st.vbits, r.nan ? INFINITY : r.vmax);
-      if (r.cnt) atomicAdd(&st.act_f, r.cnt);
+      atomicMax(&st.vbits, vb);
+      if (cc) atomicAdd(&st.act_f, cc);
     }
   }
   if (a.mode & M_NOWRITE) return;
-  __syncthreads();
-  fft_pencil<T, L, +1>(v, j, s_tw, sm);
-  if (owner) {
-    v2<T>* out = pick<T>(a, a.sel_out, t) + a.g.soff[gi] + base;
+  fft_pencil<T, L, +1>(v, j, jb, twg, tl);
+}
+
+// Check / f-clip pass along the outermost axis (z in 3D, y in 2D): forward
+// FFT completes the spectrum; the violation max over all bins is reduced
+// (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
+// the inverse FFT of this axis is applied before the store.
+//
+// Tiles are of two kinds.  Main tiles: W consecutive kx at one middle index
+// (slot kx = 0 skipped).  Mirror tiles: the kx = 0 pencils, in pairs (m, -m)
+// of middle indices so that A and B can be separated; a pencil that is its
+// own mirror (m = 0 or Nmid/2) fills both slots of its pair and only the
+// first slot stores.
+template <typename T, int L>
+__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+k_chk(Args a) {
+  FFCZ_AXIS_PROLOGUE(T, L)
+  constexpr int W = G_::W, NT = G_::NT;
+  const int M = a.g.M, Nmid = a.g.Nmid;
+  const ChkTile c = chk_decode<W>(tile, w, M, Nmid);
+  const int estride = Nmid * M;
+  const int64_t ustride = (int64_t)NT * estride;
+  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + c.off + j * estride;
+  v2<T> v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[(int64_t)(j + u * NT) * estride] = v[u];
-  }
+  for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
+  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);   // overlaps the loads
+  const int nmain = Nmid * (M / W);
+  const int ntot = chk_ntiles(W, M, Nmid);
+  const int first_tile = blockIdx.x * G_::G;
+  const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
+  chk_core<T, L>(a, p, st, v, j, jb, w, tid, tile, c, cta_has_mirror, tl, s_tw, s_red);
+  if ((a.mode & M_NOWRITE) || !c.owner) return;
+  v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) out[u * ustride] = v[u];
 }
 
 // ---------------------------------------------------------------------------
