@@ -197,6 +197,39 @@ int ffcz_profile_count(ffcz_plan_t plan);
 ffcz_status ffcz_profile_entry(ffcz_plan_t plan, int i, char* name, int name_len, double* ms,
                                int64_t* launches);
 
+/*
+ * ffcz_check_static -- ffcz_check for one 2D or 3D field WITHOUT a plan and
+ * WITHOUT allocating device memory.  The paper has no counterpart: this is an
+ * entry point for callers that cannot allocate when they need the check --
+ * code running inside a CUDA graph capture (cudaMalloc cannot be captured),
+ * callback or interrupt-style pipelines that must not reach the allocator,
+ * and hosts whose memory manager owns the whole device pool.
+ *   e_dev       : device float32 field (row-major, last axis contiguous);
+ *                 read only
+ *   ndim, shape : 2 or 3 extents, same rules as ffcz_plan
+ *   eps_s, eps_f: the true bounds E, Delta (> 0)
+ *   cuda_stream : cudaStream_t the work is ordered on (NULL = legacy stream);
+ *                 the call waits for it before returning
+ *   stats       : host pointer or NULL; certified, s_ratio, f_margin64 and
+ *                 s_margin64 are filled, the rest is zero
+ * Scratch: a fixed file-scope device array (about 32 MiB plus 260 KiB of
+ * tables and state) that every device loading the library holds until the
+ * process exits.  Fields of more than FFCZ_STATIC_MAX_POINTS points are
+ * rejected with FFCZ_ERR_INVALID (detail in ffcz_last_error()) before any
+ * GPU work.  The FIRST call on each device sets that device up (takes the
+ * array's address with cudaGetSymbolAddress and uploads the twiddle tables
+ * with blocking copies): make it before any stream capture.  All calls on a
+ * device share the array (each call re-initialises what must start at zero);
+ * calls whose GPU work overlaps -- other streams, other host threads -- race
+ * and may return wrong results.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ * Returns OK (certified), CERT_FAILED, INVALID, UNSUPPORTED or CUDA.
+ */
+#define FFCZ_STATIC_MAX_POINTS (1 << 22)
+ffcz_status ffcz_check_static(const float* e_dev, int ndim, const int64_t* shape,
+                              double eps_s, double eps_f, void* cuda_stream,
+                              ffcz_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,9 @@ ERR_NOT_CONVERGED, ERR_CERT_FAILED, ERR_NONFINITE, ERR_TIMEOUT, ERR_OOM = 4, 5, 
 SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_bytes",
            "ffcz_correct", "ffcz_correct_host", "ffcz_check", "ffcz_correct_backward",
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
-           "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry")
+           "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
+           "ffcz_check_static")
+STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
 class Opts(ctypes.Structure):
@@ -83,6 +85,9 @@ def lib() -> ctypes.CDLL:
         L.ffcz_profile_entry.argtypes = [vp, i32, ctypes.c_char_p, i32,
                                          ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64)]
+        L.ffcz_check_static.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
+                                        ctypes.c_double, vp, ctypes.POINTER(Stats)]
+        L.ffcz_check_static.restype = ctypes.c_int
         for name in ("ffcz_plan", "ffcz_set_stream", "ffcz_correct", "ffcz_correct_host",
                      "ffcz_check", "ffcz_correct_backward", "ffcz_profile_enable",
                      "ffcz_profile_entry"):
@@ -230,6 +235,21 @@ class Plan:
                                            self._ptr(grad_out, "grad_out"),
                                            self._ptr(grad_in, "grad_in"),
                                            _dbl(eps_s, 1), _dbl(eps_f, 1)))
+
+
+def check_static(e, eps_s: float, eps_f: float, stream=None):
+    """FP64 certification of one field without a plan or any device allocation
+    (``ffcz_check_static``); returns (status, stats dict)."""
+    import torch
+    if not isinstance(e, torch.Tensor) or e.dtype != torch.float32 or not e.is_cuda \
+            or not e.is_contiguous():
+        raise TypeError("e must be a contiguous float32 CUDA tensor")
+    shape = (ctypes.c_int64 * e.dim())(*e.shape)
+    st = Stats()
+    s = lib().ffcz_check_static(ctypes.c_void_p(e.data_ptr()), e.dim(), shape, float(eps_s),
+                                float(eps_f), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(st))
+    _check(s, (ERR_CERT_FAILED,))
+    return s, st.as_dict()
 
 
 def correct(e, eps_s, eps_f, **opts):

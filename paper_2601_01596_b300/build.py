@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libffcz.so")
-SRC = [os.path.join(HERE, "csrc", "ffcz.cu")]
+SRC = [os.path.join(HERE, "csrc", "ffcz.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("fft_core.cuh", "passes.cuh")] + [
     os.path.join(ROOT, "include", "ffcz.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -930,6 +930,12 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
 
 }  // namespace
 
+// Lets the library's other translation unit report a detail message through
+// ffcz_last_error() (not exported).
+__attribute__((visibility("hidden"))) void ffcz_set_last_error(const char* msg) {
+  g_err = msg ? msg : "";
+}
+
 // ============================================================================
 // C ABI
 // ============================================================================

@@ -706,7 +706,7 @@ k_chk(Args a) {
 
 // Loop decision after a check (Alg. 1: break when CheckConvergence passes;
 // readings: stop at v <= D(1 - eta/2) once t >= min_iters, cap at max_iters).
-__global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int* n_active) {
+static __global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int* n_active) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ItemState& s = st[i];
@@ -734,7 +734,7 @@ __global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int* n_act
 
 // Initialise loop state; items with pred P_UNCERT set only reset those not
 // yet certified (repair rounds).
-__global__ void k_init(ItemState* st, int n, int only_uncertified, int* n_active) {
+static __global__ void k_init(ItemState* st, int n, int only_uncertified, int* n_active) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ItemState& s = st[i];
@@ -747,7 +747,7 @@ __global__ void k_init(ItemState* st, int n, int only_uncertified, int* n_active
   if (run) atomicAdd(n_active, 1);
 }
 
-__global__ void k_mark_preclip(const ItemParams* prm, ItemState* st, int n) {
+static __global__ void k_mark_preclip(const ItemParams* prm, ItemState* st, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double emax = __longlong_as_double((long long)st[i].emaxbits);
@@ -760,7 +760,7 @@ __global__ void k_mark_preclip(const ItemParams* prm, ItemState* st, int n) {
 // ||y||_2 = sqrt(N sum e^2) (Parseval), u = 2^-53, c = 10 (>= the per-level
 // constant of radix-2 butterflies with rounded twiddles, radix 4/8 being
 // compositions of them).
-__global__ void k_certify(const ItemParams* prm, ItemState* st, int n, int repair_round) {
+static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, int repair_round) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ItemState& s = st[i];
@@ -781,7 +781,7 @@ __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, int repai
 
 // g <- g * [|e0| <= E'] for items whose input was pre-clipped (adjoint of
 // the pre-loop s-projection).
-__global__ void k_premask(float* g, const float* e0, const ItemParams* prm, const ItemState* st,
+static __global__ void k_premask(float* g, const float* e0, const ItemParams* prm, const ItemState* st,
                           int item, int64_t n) {
   if (!st[item].preclip) return;
   const float Es = prm[item].Esf;
