@@ -20,7 +20,9 @@
  *    thread's most recent failure.
  *  - A field is row-major with the LAST axis contiguous.  Supported items:
  *    2D and 3D with every axis a power of two, each axis length in [8, 1024]
- *    and the last axis in [16, 2048].  Other shapes return
+ *    and the last axis in [16, 2048]; 1D of ANY length N in [32, 524288]
+ *    (the DFT is then computed by Bluestein's chirp-z identity on a
+ *    power-of-two length P >= 2N - 1).  Other shapes return
  *    FFCZ_ERR_UNSUPPORTED.
  *  - Batches: `batch` items of one rank `ndim`; item i has the shape
  *    shapes[i*ndim .. i*ndim+ndim-1]; items are packed back to back in the
@@ -94,15 +96,18 @@ void ffcz_default_opts(ffcz_opts* opts);
  * the FP64-derived twiddle tables and bind the plan to `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).
  *   out     : receives the plan handle (owned by the caller; ffcz_destroy)
- *   ndim    : 2 or 3
+ *   ndim    : 1, 2 or 3 (every item of a plan has this rank)
  *   shapes  : host array of batch*ndim extents (see the batch convention)
  *   batch   : number of items, >= 1
  *   opts    : NULL for defaults; copied into the plan
  * Errors: INVALID (null out, ndim/batch out of range), UNSUPPORTED (shape),
  * OOM, CUDA.
- * Workspace: two float32 spectrum buffers (4 bytes per point each), one FP64
- * spectrum buffer for certification (8 bytes per point) and, when precision
- * 64 or a repair needs them, two FP64 loop buffers (allocated on first use).
+ * Workspace: two float32 spectrum buffers (4 bytes per point each; 8 bytes
+ * per Bluestein point P for 1D items), one FP64 spectrum buffer for
+ * certification (twice that) and, when precision 64 or a repair needs them,
+ * two FP64 loop buffers (allocated on first use).  1D plans also hold the
+ * FFT of each item's wrapped chirp (built here in float32, in float64 on
+ * first use).
  */
 ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes,
                       int64_t batch, const ffcz_opts* opts, void* cuda_stream);
@@ -165,7 +170,7 @@ ffcz_status ffcz_check(ffcz_plan_t plan, const float* e_dev, const double* eps_s
  *   e0_dev       : device float32 input of the forward (not modified)
  *   grad_out_dev : device float32 dL/de_K
  *   grad_in_dev  : device float32 output dL/de0 (may not alias the others)
- * Single-item plans only (batch == 1); else UNSUPPORTED.
+ * Single-item 2D/3D plans only (batch == 1); else UNSUPPORTED.
  */
 ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0_dev,
                                   const float* grad_out_dev, float* grad_in_dev,

@@ -1,0 +1,242 @@
+// bluestein.cuh -- 1D items of any length N: the DFT of Eq. 1 by Bluestein's
+// chirp-z identity on a power-of-two length P >= 2N - 1 (sm_103a).
+//
+// With b_m = exp(i pi m^2 / N):  X_k = conj(b_k) sum_n (x_n conj(b_n)) b_{k-n},
+// a circular convolution of length P with the wrapped chirp f (f[m] = b_m and
+// f[P-m] = b_m for 0 <= m < N, zero between):  X = conj(b) IFFT_P(FFT_P(a) Bt)/P,
+// Bt = FFT_P(f).  The inverse DFT uses the conjugate chirps; as f is even,
+// FFT_P(conj f) = conj(Bt).
+//
+// FFT_P runs as a four-step transform over a [P1][P2] array (index
+// n = P2 n1 + n2): column FFTs of length P1, the factor exp(-2 pi i n2 k1/P),
+// row FFTs of length P2, leaving the spectrum in [k1][k2] order
+// (k = k1 + P1 k2); the inverse walks the same steps backwards and returns to
+// natural order.  Pointwise work rides on the passes:
+//   row pass  : FFT along the row, times Bt (or conj Bt), IFFT along the row
+//   column pass: inverse column step (twiddle, IFFT), chirp post-multiply
+//               (-> X_k or x_n in natural order), the check and the clip of
+//               Alg. 1, chirp pre-multiply, forward column step.
+// One iteration is: row(conj Bt), column(s-clip), row(Bt), column(f-check,
+// f-clip) -- four passes, like the 3D schedule.  Only k, n < N carry data;
+// the rest of the P-length buffers is the zero padding of the convolution.
+#pragma once
+#include "passes.cuh"
+
+namespace ffcz {
+
+enum Op1 : int {
+  OP1_ENTRY = 0,   // column: load real x, pre-multiply, forward column step
+  OP1_FCLIP = 1,   // column: inverse step, X = conj(b) c / P, check, clip, pre, forward
+  OP1_SCLIP = 2,   // column: inverse step, x = Re(b c)/(P N), s-clip, pre, forward
+  OP1_EXIT = 3,    // column: inverse step, x, s-clip, store float32 e
+  OP1_FILTER = 4,  // column: forward column step of the wrapped chirp f (Bt build)
+  OP1_CONV = 8,    // row: FFT, times Bt, IFFT
+  OP1_CONVC = 9,   // row: FFT, times conj Bt, IFFT
+  OP1_FWD = 10     // row: FFT only (Bt build)
+};
+
+// Chirp b_m = exp(i pi m^2 / N) from r = m^2 mod 2N: the phase r/N is in
+// [0, 2); sincospi of the part below 1 (the CUDA function is called), the
+// sign flipped for the upper half.
+template <typename T>
+__device__ __forceinline__ v2<T> chirp_r(uint64_t r, uint64_t N) {
+  const bool hi = r >= N;
+  const uint64_t rr = hi ? r - N : r;
+  T s, c;
+  if constexpr (sizeof(T) == 4) sincospif((float)rr / (float)N, &s, &c);
+  else sincospi((double)rr / (double)N, &s, &c);
+  return hi ? mk<T>(-c, -s) : mk<T>(c, s);
+}
+
+// Chirps of the eight rows m_u = m0 + u D of a thread, m_u^2 mod 2N by exact
+// integer increments: m_{u+1}^2 - m_u^2 = 2 D m0 + (2u + 1) D^2 (D^2 mod 2N
+// comes from the host).
+template <typename T>
+__device__ __forceinline__ void chirps(v2<T> (&b)[8], uint64_t m0, uint64_t D, uint64_t dd2N, uint64_t N) {
+  const uint64_t twoN = 2 * N;
+  const uint64_t m0r = m0 % twoN;
+  uint64_t r = m0r * m0r % twoN;
+  uint64_t inc = ((2 * (D % twoN)) % twoN * m0r + dd2N) % twoN;
+  const uint64_t step = (2 * dd2N) % twoN;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    b[u] = chirp_r<T>(r, N);
+    r += inc; if (r >= twoN) r -= twoN;
+    inc += step; if (inc >= twoN) inc -= twoN;
+  }
+}
+
+// Column pass along n1 / k1 (length P1 = L), tile = W consecutive columns.
+template <typename T, int L>
+__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+k1_col(Args a) {
+  FFCZ_AXIS_PROLOGUE(T, L)
+  constexpr int NT = G_::NT, W = G_::W;
+  const int P2 = a.g.M;
+  const int64_t N = p.n;
+  const int ntiles = P2 / W;
+  const bool live = tile < ntiles;
+  const int n2 = live ? tile * W + w : 0;
+  const int64_t ustride = (int64_t)NT * P2;
+  const v2<T>* twp = reinterpret_cast<const v2<T>*>(a.twr);      // exp(-2 pi i m / P), m < P
+  const int op = a.op1;
+  const uint64_t m0 = (uint64_t)j * P2 + n2, D = (uint64_t)NT * P2;
+  const int64_t Pn = (int64_t)L * P2;
+  v2<T> v[8];
+  AbsMax<T> mx;
+  bool bad = false;
+  float ssq = 0.f;
+  unsigned long long cnt = 0;
+  if (op == OP1_ENTRY) {
+    float* src = a.e + a.g.eoff[gi];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t n = (int64_t)m0 + (int64_t)u * D;
+      float x = (live && n < N) ? src[n] : 0.f;
+      if (a.mode & M_MEASURE) {
+        mx.add((T)x);
+        bad |= (x != x);
+        ssq = fmaf(x, x, ssq);
+      }
+      if (a.mode & M_PRECLIP) {
+        const float cx = clampT(x, p.Esf);
+        cnt += (cx != x);
+        x = cx;
+        if (live && n < N) src[n] = x;
+      }
+      v[u] = mk<T>((T)x, T(0));
+    }
+  } else if (op != OP1_FILTER) {
+    const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + m0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
+  }
+  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);
+  v2<T> b[8];
+  chirps<T>(b, m0, D, (uint64_t)p.dd2N, (uint64_t)N);
+
+  if (op == OP1_FILTER) {
+    // wrapped chirp: f[m] = b_m for m < N, f[m] = b_{P-m} for 0 < P - m < N
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t m = (int64_t)m0 + (int64_t)u * D, q = Pn - m;
+      v2<T> f = mk<T>(T(0), T(0));
+      if (m < N) f = b[u];
+      else if (q < N) f = chirp_r<T>((uint64_t)q % (2 * N) * ((uint64_t)q % (2 * N)) % (2 * N), N);
+      v[u] = f;
+    }
+  } else if (op == OP1_ENTRY) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = cmulc<T>(v[u], b[u]);   // a_n = x_n conj(b_n)
+    if (a.mode & (M_MEASURE | M_PRECLIP)) {
+      Red rr{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-18) : 0.0, live ? cnt : 0ull};
+      block_reduce(rr, s_red);
+      if (threadIdx.x == 0) {
+        if (a.mode & M_MEASURE) {
+          atomicMax(&st.emaxbits, rr.vbits);
+          atomicAdd(&st.sumsq, rr.sum);
+        }
+        if ((a.mode & M_PRECLIP) && rr.cnt) atomicAdd(&st.act_s, rr.cnt);
+      }
+    }
+  } else {
+    // inverse column step: conj twiddle, IFFT along k1 -> c[n1][n2] * P
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = cmulc<T>(v[u], twp[(j + u * NT) * n2]);
+    fft_pencil<T, L, +1>(v, j, jb, s_tw, tl);
+    const bool count = (a.mode & M_COUNT) != 0;
+    if (op == OP1_FCLIP) {
+      const T invP = T(1) / (T)Pn;   // exact: P is a power of two
+      const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
+      const bool clip = (a.mode & M_CLIP) != 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t k = (int64_t)m0 + (int64_t)u * D;
+        const bool in_range = live && k < N;
+        v2<T> X = cmulc<T>(v[u], b[u]);            // X_k = conj(b_k) c_k / P
+        X = mk<T>(X.x * invP, X.y * invP);
+        if (in_range) { mx.add(X.x); mx.add(X.y); bad |= (X.x != X.x) | (X.y != X.y); }
+        if (clip) {
+          const T cx = clampT(X.x, Ds), cy = clampT(X.y, Ds);
+          if (count && in_range) cnt += (cx != X.x) + (cy != X.y);
+          X = mk<T>(cx, cy);
+        }
+        v[u] = in_range ? cmul<T>(X, b[u]) : mk<T>(T(0), T(0));   // pre: X'_k b_k
+      }
+      unsigned long long vb = mx.dbits(bad);
+      block_max_count(vb, cnt, count, s_red);
+      if (threadIdx.x == 0) {
+        atomicMax(&st.vbits, vb);
+        if (cnt) atomicAdd(&st.act_f, cnt);
+      }
+      if (a.mode & M_NOWRITE) return;
+    } else {
+      const T inv_pn = sizeof(T) == 4 ? (T)p.inv_pnf : (T)p.inv_pn;
+      const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
+      float* eo = a.e + a.g.eoff[gi];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t n = (int64_t)m0 + (int64_t)u * D;
+        const bool in_range = live && n < N;
+        T x = (b[u].x * v[u].x - b[u].y * v[u].y) * inv_pn;   // Re(b_n c'_n) / (P N)
+        if (a.mode & M_CLIP) {
+          const T cx = clampT(x, Es);
+          if (count && in_range) cnt += (cx != x);
+          x = cx;
+        }
+        if (op == OP1_EXIT) {
+          if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf) : (float)x;
+        } else {
+          v[u] = in_range ? cmulc<T>(mk<T>(x, T(0)), b[u]) : mk<T>(T(0), T(0));   // x_n conj(b_n)
+        }
+      }
+      if (op == OP1_EXIT) return;
+      if (count) {
+        unsigned long long vb = 0ull;
+        block_max_count(vb, cnt, true, s_red);
+        if (threadIdx.x == 0 && cnt) atomicAdd(&st.act_s, cnt);
+      }
+    }
+  }
+  // forward column step: FFT along n1, twiddle exp(-2 pi i n2 k1 / P)
+  fft_pencil<T, L, -1>(v, j, jb, s_tw, tl);
+  if (live) {
+    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + m0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) out[u * ustride] = cmul<T>(v[u], twp[(j + u * NT) * n2]);
+  }
+}
+
+// Row pass along n2 / k2 (length P2 = L), tile = W consecutive rows.
+template <typename T, int L>
+__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+k1_row(Args a) {
+  FFCZ_AXIS_PROLOGUE(T, L)
+  constexpr int NT = G_::NT;
+  const int P1 = a.g.Nz;
+  const int ntiles = P1 / G_::W;
+  const bool live = tile < ntiles;
+  const int row = live ? tile * G_::W + w : 0;
+  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + (int64_t)row * L + j;
+  v2<T> v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) v[u] = in[u * NT];
+  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);
+  fft_pencil<T, L, -1>(v, j, jb, s_tw, tl);
+  if (a.op1 != OP1_FWD) {
+    const v2<T>* bt = reinterpret_cast<const v2<T>*>(a.bt) + a.g.soff[gi] + (int64_t)row * L + j;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const v2<T> f = bt[u * NT];
+      v[u] = a.op1 == OP1_CONVC ? cmulc<T>(v[u], f) : cmul<T>(v[u], f);
+    }
+    fft_pencil<T, L, +1>(v, j, jb, s_tw, tl);
+  }
+  if (live) {
+    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + (int64_t)row * L + j;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) out[u * NT] = v[u];
+  }
+}
+
+}  // namespace ffcz

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ffcz.h"
+#include "bluestein.cuh"
 #include "passes.cuh"
 
 using namespace ffcz;
@@ -102,6 +103,10 @@ struct DevGroup {
   int count;
   int ndim, Nz, Ny, Nx, M;
   int64_t rows, n;
+  // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
+  int P1 = 0, P2 = 0;
+  const void* twp32 = nullptr;
+  const void* twp64 = nullptr;
 };
 
 struct Tables {
@@ -132,6 +137,7 @@ struct ffcz_plan_s {
   std::vector<int64_t> shapes;
   std::vector<int64_t> eoff;   // float offset per item
   int64_t total = 0;           // floats
+  int64_t total_c = 0;         // complex values per spectrum buffer
   ffcz_opts opts{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
@@ -142,6 +148,8 @@ struct ffcz_plan_s {
   Tables tb;
 
   void* B32[2] = {nullptr, nullptr};
+  void* Bt32 = nullptr;        // 1D: FFT_P of the wrapped chirps (float32 / float64)
+  void* Bt64 = nullptr;
   void* B64[2] = {nullptr, nullptr};
   void* Bc = nullptr;
   float* staging = nullptr;
@@ -348,6 +356,61 @@ void launch_chk(int L, const Args& a, int Nmid, int M, int count, cudaStream_t s
   }
 }
 
+// ----- 1D (Bluestein) passes ---------------------------------------------------
+template <typename T, int L>
+void launch_col1_t(const Args& a, int P2, int count, cudaStream_t s) {
+  using G_ = Geo<T, L>;
+  const int64_t tiles = P2 / G_::W;
+  dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
+  const size_t sm = Smem<T, L>::bytes_axis;
+  if (g_dry) { set_smem(k1_col<T, L>, sm); return; }
+  ProfScope ps(a.op1 == OP1_FCLIP ? ((a.mode & M_NOWRITE) ? "col1_cert" : "col1_fclip")
+               : a.op1 == OP1_SCLIP ? "col1_sclip" : a.op1 == OP1_EXIT ? "col1_exit"
+               : a.op1 == OP1_FILTER ? "col1_filter" : "col1_entry",
+               8 * (int)sizeof(T), L, s);
+  k1_col<T, L><<<grid, G_::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+template <typename T>
+void launch_col1(int L, const Args& a, int P2, int count, cudaStream_t s) {
+  switch (L) {
+    case 8: launch_col1_t<T, 8>(a, P2, count, s); break;
+    case 16: launch_col1_t<T, 16>(a, P2, count, s); break;
+    case 32: launch_col1_t<T, 32>(a, P2, count, s); break;
+    case 64: launch_col1_t<T, 64>(a, P2, count, s); break;
+    case 128: launch_col1_t<T, 128>(a, P2, count, s); break;
+    case 256: launch_col1_t<T, 256>(a, P2, count, s); break;
+    case 512: launch_col1_t<T, 512>(a, P2, count, s); break;
+    case 1024: launch_col1_t<T, 1024>(a, P2, count, s); break;
+    default: fail(FFCZ_ERR_UNSUPPORTED, "1D column length");
+  }
+}
+template <typename T, int L>
+void launch_row1_t(const Args& a, int P1, int count, cudaStream_t s) {
+  using G_ = Geo<T, L>;
+  const int64_t tiles = P1 / G_::W;
+  dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
+  const size_t sm = Smem<T, L>::bytes_axis;
+  if (g_dry) { set_smem(k1_row<T, L>, sm); return; }
+  ProfScope ps(a.op1 == OP1_FWD ? "row1_fwd" : "row1_conv", 8 * (int)sizeof(T), L, s);
+  k1_row<T, L><<<grid, G_::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+template <typename T>
+void launch_row1(int L, const Args& a, int P1, int count, cudaStream_t s) {
+  switch (L) {
+    case 8: launch_row1_t<T, 8>(a, P1, count, s); break;
+    case 16: launch_row1_t<T, 16>(a, P1, count, s); break;
+    case 32: launch_row1_t<T, 32>(a, P1, count, s); break;
+    case 64: launch_row1_t<T, 64>(a, P1, count, s); break;
+    case 128: launch_row1_t<T, 128>(a, P1, count, s); break;
+    case 256: launch_row1_t<T, 256>(a, P1, count, s); break;
+    case 512: launch_row1_t<T, 512>(a, P1, count, s); break;
+    case 1024: launch_row1_t<T, 1024>(a, P1, count, s); break;
+    default: fail(FFCZ_ERR_UNSUPPORTED, "1D row length");
+  }
+}
+
 // Words of mask storage one pass writes (one uint32 per thread of a live tile).
 template <typename T>
 int64_t x_words(int M, int64_t rows) {
@@ -385,6 +448,34 @@ void tabs_x(ffcz_plan_s* p, Args& a, const DevGroup& dg) {
   a.twr = twr_of<T>(p->tb, dg.Nx);
 }
 
+template <typename T>
+void col1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
+  a.tw = tw_of<T>(p->tb, dg.P1);
+  a.twr = sizeof(T) == 4 ? dg.twp32 : dg.twp64;
+  a.op1 = op;
+}
+template <typename T>
+void row1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
+  a.tw = tw_of<T>(p->tb, dg.P2);
+  a.bt = sizeof(T) == 4 ? p->Bt32 : p->Bt64;
+  a.op1 = op;
+}
+
+// Bt = FFT_P(wrapped chirp) for every 1D item, in the precision T.
+template <typename T>
+void build_bt(ffcz_plan_s* p) {
+  void*& bt = sizeof(T) == 4 ? p->Bt32 : p->Bt64;
+  if (!bt) bt = dalloc(p, (size_t)p->total_c * sizeof(v2<T>));
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, bt, bt, p->d_st);
+    a.pred = P_ALL;
+    col1_args<T>(p, a, dg, OP1_FILTER);
+    launch_col1<T>(dg.P1, a, dg.P2, dg.count, p->stream);
+    row1_args<T>(p, a, dg, OP1_FWD);
+    launch_row1<T>(dg.P2, a, dg.P1, dg.count, p->stream);
+  }
+}
+
 // ----- the loop ---------------------------------------------------------------
 struct LoopBufs {
   void* b0;
@@ -392,7 +483,81 @@ struct LoopBufs {
 };
 
 template <typename T>
+void entry1(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStream_t s) {
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    col1_args<T>(p, a, dg, OP1_ENTRY);
+    a.e = e;
+    a.mode = measure_preclip ? M_MEASURE : 0;
+    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+  }
+  if (measure_preclip) {
+    k_mark_preclip<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch);
+    g_launches++;
+    for (auto& dg : p->groups) {
+      Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+      col1_args<T>(p, a, dg, OP1_ENTRY);
+      a.e = e;
+      a.mode = M_PRECLIP;
+      a.pred = P_PRECLIP;
+      launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    }
+  }
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    row1_args<T>(p, a, dg, OP1_CONV);
+    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    col1_args<T>(p, a, dg, OP1_FCLIP);
+    a.mode = M_CLIP | cnt_flag(p);
+    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+  }
+  k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
+                                                             p->d_nactive);
+  g_launches++;
+}
+
+template <typename T>
+void body1(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    row1_args<T>(p, a, dg, OP1_CONVC);
+    a.sel_in = S_PREV; a.sel_out = S_CUR;
+    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    a.sel_in = S_CUR;
+    col1_args<T>(p, a, dg, OP1_SCLIP);
+    a.mode = M_CLIP | cnt_flag(p);
+    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    row1_args<T>(p, a, dg, OP1_CONV);
+    a.mode = 0;
+    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    col1_args<T>(p, a, dg, OP1_FCLIP);
+    a.mode = M_CLIP | cnt_flag(p);
+    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+  }
+  k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
+                                                             p->d_nactive);
+  g_launches++;
+}
+
+template <typename T>
+void exit1(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
+  for (auto& dg : p->groups) {
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    a.pred = P_EXIT;
+    a.e = e;
+    row1_args<T>(p, a, dg, OP1_CONVC);
+    a.sel_in = S_PREV; a.sel_out = S_CUR;
+    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    a.sel_in = S_CUR;
+    col1_args<T>(p, a, dg, OP1_EXIT);
+    a.mode = M_CLIP;
+    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+  }
+}
+
+template <typename T>
 void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStream_t s) {
+  if (p->ndim == 1) { entry1<T>(p, B, e, measure_preclip, s); return; }
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     tabs_x<T>(p, a, dg);
@@ -429,6 +594,7 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
 
 template <typename T>
 void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
+  if (p->ndim == 1) { body1<T>(p, B, s); return; }
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     if (dg.ndim == 3) {
@@ -459,6 +625,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
 
 template <typename T>
 void exit_pass(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
+  if (p->ndim == 1) { exit1<T>(p, B, e, s); return; }
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     a.pred = P_EXIT;
@@ -479,10 +646,12 @@ void exit_pass(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
 
 template <typename T>
 LoopBufs loop_bufs(ffcz_plan_s* p) {
+  // 1D plans need the chirp spectrum in the loop's precision
+  if (p->ndim == 1 && sizeof(T) == 8 && !p->Bt64) build_bt<double>(p);
   if (sizeof(T) == 4) return {p->B32[0], p->B32[1]};
   if (!p->B64[0]) {
-    p->B64[0] = dalloc(p, (size_t)p->total * 8);
-    p->B64[1] = dalloc(p, (size_t)p->total * 8);
+    p->B64[0] = dalloc(p, (size_t)p->total_c * sizeof(double2));
+    p->B64[1] = dalloc(p, (size_t)p->total_c * sizeof(double2));
   }
   return {p->B64[0], p->B64[1]};
 }
@@ -521,6 +690,13 @@ void run_chunk(ffcz_plan_s* p, LoopBufs B, int C) {
   g_launches += p->graph_nodes[key];
 }
 
+// Bluestein length of a 1D item: the smallest power of two >= 2N - 1.
+int64_t p1d_len(int64_t n) {
+  int64_t P = 64;
+  while (P < 2 * n - 1) P <<= 1;
+  return P;
+}
+
 void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int min_iters,
                    int max_iters) {
   const double eta = p->opts.shrink;
@@ -538,6 +714,15 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
     q.n = n;
     q.min_iters = min_iters;
     q.max_iters = max_iters;
+    q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0; q.dd2N = 0;
+    if (p->ndim == 1) {
+      const int64_t P = p1d_len(n);
+      const uint64_t D = (uint64_t)(P / 8), twoN = 2 * (uint64_t)n;
+      q.inv_pn = 1.0 / ((double)P * (double)n);
+      q.inv_pnf = (float)q.inv_pn;
+      q.logP = ilog2((int)P);
+      q.dd2N = (D % twoN) * (D % twoN) % twoN;
+    }
   }
   CK(cudaMemcpyAsync(p->d_prm, p->h_prm, sizeof(ItemParams) * p->batch, cudaMemcpyHostToDevice,
                      p->stream));
@@ -567,8 +752,24 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
 }
 
 void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
-  if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total * 8);
+  if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total_c * sizeof(double2));
+  if (p->ndim == 1 && !p->Bt64) build_bt<double>(p);
   for (auto& dg : p->groups) {
+    if (p->ndim == 1) {
+      Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_st);
+      a.pred = repair_round ? P_UNCERT : P_ALL;
+      a.e = const_cast<float*>(e);
+      col1_args<double>(p, a, dg, OP1_ENTRY);
+      a.mode = M_MEASURE;
+      launch_col1<double>(dg.P1, a, dg.P2, dg.count, p->stream);
+      row1_args<double>(p, a, dg, OP1_CONV);
+      a.mode = 0;
+      launch_row1<double>(dg.P2, a, dg.P1, dg.count, p->stream);
+      col1_args<double>(p, a, dg, OP1_FCLIP);
+      a.mode = M_NOWRITE;
+      launch_col1<double>(dg.P1, a, dg.P2, dg.count, p->stream);
+      continue;
+    }
     Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_st);
     a.pred = repair_round ? P_UNCERT : P_ALL;
     tabs_x<double>(p, a, dg);
@@ -807,6 +1008,7 @@ void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uin
 ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, float* gin,
                           const double* eps_s, const double* eps_f) {
   if (p->batch != 1) fail(FFCZ_ERR_UNSUPPORTED, "backward needs a single-item plan");
+  if (p->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "backward supports 2D and 3D items");
   if (!e0 || !gout || !gin || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
   const int K = p->opts.K, m = p->opts.ckpt_every;
   if (K < 1 || m < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
@@ -964,7 +1166,6 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (!shapes) fail(FFCZ_ERR_INVALID, "shapes is null");
     if (ndim < 1 || ndim > 3) fail(FFCZ_ERR_INVALID, "ndim must be 1..3");
     if (batch < 1 || batch > 65535) fail(FFCZ_ERR_INVALID, "batch must be in [1, 65535]");
-    if (ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "1D items are not supported by this build");
     ffcz_opts o;
     ffcz_default_opts(&o);
     if (opts) o = *opts;
@@ -972,6 +1173,12 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (!(o.shrink >= 0.0 && o.shrink < 0.5)) fail(FFCZ_ERR_INVALID, "shrink must be in [0, 0.5)");
     if (o.max_iters < 0 || o.min_iters < 0) fail(FFCZ_ERR_INVALID, "iteration limits must be >= 0");
     for (int64_t i = 0; i < batch; ++i) {
+      if (ndim == 1) {
+        const int64_t n = shapes[i];
+        if (n < 32 || n > (1 << 19))
+          fail(FFCZ_ERR_UNSUPPORTED, "1D lengths must be in [32, 524288]");
+        continue;
+      }
       for (int d = 0; d < ndim; ++d) {
         const int64_t n = shapes[i * ndim + d];
         const bool last = d == ndim - 1;
@@ -988,17 +1195,30 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->stream = (cudaStream_t)cuda_stream;
     CK(cudaGetDevice(&p->device));
     p->eoff.resize(batch);
-    int64_t off = 0;
+    std::vector<int64_t> soff_c(batch);
+    int64_t off = 0, offc = 0;
+    // group key: the shape (2D/3D) or the Bluestein split (P1, P2) (1D)
     std::map<std::vector<int64_t>, std::vector<int>> bys;
     for (int64_t i = 0; i < batch; ++i) {
       std::vector<int64_t> sh(shapes + i * ndim, shapes + (i + 1) * ndim);
       int64_t n = 1;
       for (auto v : sh) n *= v;
       p->eoff[i] = off;
+      soff_c[i] = offc;
       off += n;
-      bys[sh].push_back((int)i);
+      if (ndim == 1) {
+        const int64_t P = p1d_len(n);
+        const int lg = ilog2((int)P);
+        const int64_t P1 = (int64_t)1 << (lg / 2);
+        offc += P;
+        bys[{P1, P / P1}].push_back((int)i);
+      } else {
+        offc += n / 2;
+        bys[sh].push_back((int)i);
+      }
     }
     p->total = off;
+    p->total_c = offc;
     CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     CK(cudaEventCreate(&p->ev0));
     CK(cudaEventCreate(&p->ev1));
@@ -1028,16 +1248,42 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       DevGroup dg{};
       dg.ndim = ndim;
       dg.count = (int)ids.size();
-      dg.Nx = (int)sh[ndim - 1];
-      dg.M = dg.Nx / 2;
-      dg.Nz = (int)sh[0];
-      dg.Ny = ndim == 3 ? (int)sh[1] : 1;
-      dg.n = 1;
-      for (auto v : sh) dg.n *= v;
-      dg.rows = dg.n / dg.Nx;
+      if (ndim == 1) {
+        dg.P1 = (int)sh[0];
+        dg.P2 = (int)sh[1];
+        dg.Nz = dg.P1;           // rows of the [P1][P2] array
+        dg.M = dg.P2;            // row length
+        dg.Ny = 1;
+        dg.Nx = 2 * dg.P2;
+        dg.n = (int64_t)dg.P1 * dg.P2;
+        dg.rows = dg.P1;
+        const int P = dg.P1 * dg.P2;
+        std::vector<float2> t32(P);
+        std::vector<double2> t64(P);
+        for (int m = 0; m < P; ++m) {
+          const double2 r = root<double>(m, P);
+          t64[m] = r;
+          const float2 f = root<float>(m, P);
+          t32[m] = f;
+        }
+        void* d32 = dalloc(p.get(), sizeof(float2) * P);
+        void* d64 = dalloc(p.get(), sizeof(double2) * P);
+        CK(cudaMemcpy(d32, t32.data(), sizeof(float2) * P, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d64, t64.data(), sizeof(double2) * P, cudaMemcpyHostToDevice));
+        dg.twp32 = d32;
+        dg.twp64 = d64;
+      } else {
+        dg.Nx = (int)sh[ndim - 1];
+        dg.M = dg.Nx / 2;
+        dg.Nz = (int)sh[0];
+        dg.Ny = ndim == 3 ? (int)sh[1] : 1;
+        dg.n = 1;
+        for (auto v : sh) dg.n *= v;
+        dg.rows = dg.n / dg.Nx;
+      }
       std::vector<int32_t> it(ids.begin(), ids.end());
       std::vector<int64_t> eo, so;
-      for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(p->eoff[id] / 2); }
+      for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(soff_c[id]); }
       int32_t* d_it = (int32_t*)dalloc(p.get(), sizeof(int32_t) * it.size());
       int64_t* d_eo = (int64_t*)dalloc(p.get(), sizeof(int64_t) * eo.size());
       int64_t* d_so = (int64_t*)dalloc(p.get(), sizeof(int64_t) * so.size());
@@ -1059,6 +1305,13 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     try {
       Args a{};
       for (auto& dg : p->groups) {
+        if (ndim == 1) {
+          launch_col1<float>(dg.P1, a, dg.P2, 1, nullptr);
+          launch_col1<double>(dg.P1, a, dg.P2, 1, nullptr);
+          launch_row1<float>(dg.P2, a, dg.P1, 1, nullptr);
+          launch_row1<double>(dg.P2, a, dg.P1, 1, nullptr);
+          continue;
+        }
         launch_x<float>(XFWD, dg.M, a, dg.rows, 1, nullptr);
         launch_x<double>(XFWD, dg.M, a, dg.rows, 1, nullptr);
         launch_axis<float, -1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
@@ -1074,8 +1327,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     }
     g_dry = false;
     // float32 spectrum buffers: N/2 complex64 each (4 bytes per point)
-    p->B32[0] = dalloc(p.get(), sizeof(float) * p->total);
-    p->B32[1] = dalloc(p.get(), sizeof(float) * p->total);
+    p->B32[0] = dalloc(p.get(), sizeof(float2) * p->total_c);
+    p->B32[1] = dalloc(p.get(), sizeof(float2) * p->total_c);
     p->d_prm = (ItemParams*)dalloc(p.get(), sizeof(ItemParams) * batch);
     p->d_st = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
@@ -1085,6 +1338,14 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     CK(cudaMallocHost(&p->h_nactive, sizeof(int)));
     CK(cudaMallocHost(&p->h_st, sizeof(ItemState) * batch));
     CK(cudaMallocHost(&p->h_prm, sizeof(ItemParams) * batch));
+    if (ndim == 1) {
+      // FFT of the wrapped chirp of every item (float32 now, float64 on first
+      // certification); the bounds are placeholders here
+      std::vector<double> one(batch, 1.0);
+      upload_params(p.get(), one.data(), one.data(), 0, 0);
+      build_bt<float>(p.get());
+      CK(cudaStreamSynchronize(p->stream));
+    }
     *out = p.release();
     return FFCZ_OK;
   });

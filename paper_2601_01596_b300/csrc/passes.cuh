@@ -37,6 +37,11 @@ struct ItemParams {
   float Esf, Dsf, thrf, inv_nf;      // the same in float32
   int64_t n;                         // points
   int32_t min_iters, max_iters;
+  // 1D items (Bluestein): 1/(P N), (P/8)^2 mod 2N, log2 P (0 for 2D/3D items)
+  double inv_pn;
+  float inv_pnf;
+  int32_t logP;
+  uint64_t dd2N;
 };
 
 struct ItemState {
@@ -78,8 +83,10 @@ struct Args {
   float* ckpt;             // checkpoint buffer for e_t
   int ckpt_every;
   int pred, sel_in, sel_out, mode;
-  const void* tw;          // exp(-2 pi i m / L), m < L
-  const void* twr;         // exp(-2 pi i k / Nx), k < M (x passes)
+  const void* tw;          // Stockham stage factors for the pass length
+  const void* twr;         // exp(-2 pi i k / Nx), k < M (x passes); exp(-2 pi i m / P) (1D)
+  const void* bt;          // 1D: FFT of the wrapped chirp, [k1][k2] order, per item at soff
+  int op1;                 // 1D pass operation (Op1)
 };
 
 __device__ __forceinline__ bool pred_ok(int pred, const ItemState& s, const ItemParams& p) {
@@ -769,7 +776,12 @@ static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, in
   const double emax = __longlong_as_double((long long)s.emaxbits);
   const double v = __longlong_as_double((long long)s.vbits);
   const double ln = log2((double)p.n);
-  const double b = 10.0 * (ln + 2.0) * 1.1102230246251565e-16 * sqrt((double)p.n * s.sumsq);
+  double b = 10.0 * (ln + 2.0) * 1.1102230246251565e-16 * sqrt((double)p.n * s.sumsq);
+  if (p.logP > 0) {
+    // Bluestein: FFT_P, product with Bt (|Bt_k| <= 2N), IFFT_P and two chirp
+    // products; |err_k| <= ||err||_2 <= c (2 log2 P + 6) u 2N ||x||_2
+    b = 10.0 * (2.0 * p.logP + 6.0) * 1.1102230246251565e-16 * 2.0 * (double)p.n * sqrt(s.sumsq);
+  }
   s.v64 = v;
   s.emax64 = emax;
   s.bound64 = b;
