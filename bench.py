@@ -37,6 +37,7 @@ import numpy as np  # noqa: E402
 from paper_2601_01596_b300 import workloads as W  # noqa: E402
 
 METRIC = "field GB/s to certified feasibility, 512^3 fp32; % HBM roofline/iteration"
+FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
 
 
 def load_peaks():
@@ -175,6 +176,139 @@ def bytes_per_launch(key, n):
     return 2 * sb                    # px, axis_*, chk: spectrum in and out
 
 
+def fft_flops_per_point(L):
+    """Real FP64/FP32 operations per complex point of one length-L transform
+    of the Stockham schedule (radix-8, one or two radix-4 stages first):
+    radix-8 butterfly 56 flops per 8 points, radix-4 16 per 4, twiddle
+    products 6 flops each for all but one input of every stage after the
+    first."""
+    lg = int(round(math.log2(L)))
+    a, b = divmod(lg, 3)
+    radices = [8] * a if b == 0 else ([4] + [8] * a if b == 2 else [4, 4] + [8] * (a - 1))
+    f = 0.0
+    for i, r in enumerate(radices):
+        f += 7.0 if r == 8 else 4.0
+        if i > 0:
+            f += 6.0 * (r - 1) / r
+    return f
+
+
+def flops_per_launch(key, n):
+    """Algorithmic floating-point work of one launch on an n-point 2D/3D item
+    (n/2 packed complex points)."""
+    kind, rest = key.split("<")
+    L = int(rest.split(",")[1].rstrip(">"))
+    pts = n / 2
+    f = fft_flops_per_point(L)
+    if kind in ("xfwd", "xexit"):
+        f += 16.0                      # R2C / C2R pre- or post-processing
+    elif kind == "px":
+        f = 2 * f + 32.0
+    elif kind in ("chk", "chk_adj"):
+        f = 2 * f
+    return f * pts
+
+
+def _timed(torch, fn, reps=2, warm=1):
+    for _ in range(warm):
+        fn()
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return float(np.median(out)), r
+
+
+def _batch_form(ffcz, torch, items, name):
+    shapes = [x["shape"] for x in items]
+    host = np.concatenate([x["e0"].reshape(-1) for x in items])
+    d0 = torch.from_numpy(host).cuda()
+    d = torch.empty_like(d0)
+    Es = [x["E"] for x in items]
+    Ds = [x["D"] for x in items]
+    plan = ffcz.Plan(shapes)
+
+    def call():
+        d.copy_(d0)
+        return plan.correct(d, Es, Ds)
+
+    call()
+    ms_total, st = _timed(torch, lambda: plan.correct(d.copy_(d0), Es, Ds))
+    copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
+    ms = ms_total - copy_ms
+    iters = [x["iters"] for x in st]
+    byts = 4 * host.size
+    del plan
+    return {"workload": name, "items": len(items), "field_bytes": int(byts),
+            "ms_per_call": round(ms, 3), "GBps": round(byts / (ms / 1e3) / 1e9, 3),
+            "iters_min": int(min(iters)), "iters_max": int(max(iters)),
+            "iters_mean": round(float(np.mean(iters)), 3),
+            "certified": int(sum(x["certified"] for x in st)),
+            "ms_cert": round(float(st[0]["ms_cert"]), 3)}
+
+
+def measure_forms(ffcz, torch, fin, it, hbm):
+    """The stress variant, the batched and the differentiable forms (each a
+    median of 2 calls after 1 warm-up; CUDA events on the current stream)."""
+    out = {}
+    shape, E = it["shape"], it["E"]
+    n = int(np.prod(shape))
+    d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
+    d = torch.empty_like(d0)
+    plan = ffcz.Plan([shape])
+    Dst = fin["stress_D"]
+    ms_total, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [Dst])[0])
+    copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
+    ms = ms_total - copy_ms
+    out["stress_512"] = {"workload": it["name"] + " stress eps_f = 0.2 max box violation of e0",
+                         "ms_per_call": round(ms, 3), "GBps": round(4 * n / (ms / 1e3) / 1e9, 3),
+                         "iters": st["iters"], "certified": st["certified"],
+                         "ms_cert": round(st["ms_cert"], 3)}
+    del plan, d, d0
+    torch.cuda.empty_cache()
+    out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
+                                    "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")
+    torch.cuda.empty_cache()
+    out["batched_1d"] = _batch_form(ffcz, torch, fin["c4"],
+                                    "4096 EEG-like signals, lengths U{1024..65536} (Bluestein)")
+    torch.cuda.empty_cache()
+    # differentiable: K = 50 forced iterations, checkpoint every 10, loss on the
+    # log power spectrum of x + e_K (torch.fft in the loss only)
+    from paper_2601_01596_b300.autograd import FFCzCorrect, power_spectrum_loss
+    c5 = fin["c5"]
+    x = torch.from_numpy(c5["x"]).cuda()
+    e0 = torch.from_numpy(c5["e0"]).cuda()
+    K, m = 50, 10
+
+    def fwd():
+        return FFCzCorrect.apply(e0, c5["E"], c5["D"], K, m)
+
+    fwd_ms, _ = _timed(torch, fwd)
+
+    def fwd_bwd():
+        ee = e0.clone().requires_grad_(True)
+        eK = FFCzCorrect.apply(ee, c5["E"], c5["D"], K, m)
+        loss = power_spectrum_loss(x, eK)
+        loss.backward()
+        return float(loss.item())
+
+    fb_ms, loss = _timed(torch, fwd_bwd)
+    n5 = int(np.prod(c5["shape"]))
+    out["differentiable"] = {"workload": c5["name"] + f", K={K} forced iterations, checkpoint every {m}",
+                             "forward_ms": round(fwd_ms, 3),
+                             "forward_backward_ms": round(fb_ms, 3),
+                             "backward_over_forward": round((fb_ms - fwd_ms) / fwd_ms, 3),
+                             "forward_ms_per_iteration": round(fwd_ms / K, 4),
+                             "field_GBps_forward": round(4 * n5 / (fwd_ms / 1e3) / 1e9, 3),
+                             "loss": loss}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,6 +318,8 @@ def main():
     ap.add_argument("--workload", default="lognormal512")
     ap.add_argument("--forced", type=int, default=20, help="forced iterations for the per-iteration roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the stress, batched and differentiable forms")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -193,6 +329,18 @@ def main():
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
+
+    # every input is generated on the host before the first CUDA call
+    it = make_workload(args.workload)
+    forms_in = None
+    if not args.no_forms:
+        workers = min(8, os.cpu_count() or 1)
+        forms_in = {
+            "stress_D": W.max_box_fft(it["e0"]) * 0.2,
+            "c3": W.diffraction_batch(workers=workers),
+            "c4": W.eeg_batch(workers=workers),
+            "c5": W.turbulence_field(256),
+        }
 
     import torch
     import paper_2601_01596_b300 as ffcz
@@ -204,7 +352,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     hbm, peak_kind = load_peaks()
-    it = make_workload(args.workload)
     shape, E, D = it["shape"], it["E"], it["D"]
     n = int(np.prod(shape))
     field_bytes = 4 * n
@@ -261,7 +408,25 @@ def main():
     top_key, (top_ms, top_n) = max(prof.items(), key=lambda kv: kv[1][0])
     top_avg = top_ms / top_n
     top_bytes = bytes_per_launch(top_key, n)
-    achieved = top_bytes / (top_avg / 1e3) / 1e9
+    if "f64" in top_key:
+        # FP64 kernels are bound by the FP64 pipe: nominal B300 FP64 rate
+        top_flops = flops_per_launch(top_key, n)
+        roof = {"bound": "alu", "kernel": top_key,
+                "achieved": round(top_flops / (top_avg / 1e3) / 1e12, 4),
+                "peak": FP64_TFLOPS, "unit": "TFLOP/s (FP64)",
+                "frac": round(top_flops / (top_avg / 1e3) / 1e12 / FP64_TFLOPS, 4),
+                "traffic": None, "peak_kind": "nominal FP64 (no measured FP64 peak)",
+                "avg_launch_ms": round(top_avg, 4), "algorithmic_flops": top_flops,
+                "algorithmic_bytes": top_bytes,
+                "achieved_GBps": round(top_bytes / (top_avg / 1e3) / 1e9, 1),
+                "share_of_step": round(top_ms / tot, 3) if tot else None}
+    else:
+        roof = {"bound": "hbm", "kernel": top_key,
+                "achieved": round(top_bytes / (top_avg / 1e3) / 1e9, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(top_bytes / (top_avg / 1e3) / 1e9 / hbm, 4),
+                "traffic": None, "peak_kind": peak_kind, "avg_launch_ms": round(top_avg, 4),
+                "algorithmic_bytes": top_bytes,
+                "share_of_step": round(top_ms / tot, 3) if tot else None}
 
     # -- per-iteration roofline: forced iterations, no certification -----------
     fplan = ffcz.Plan([shape], min_iters=args.forced, max_iters=args.forced, certify=0)
@@ -292,6 +457,13 @@ def main():
     body = {k: v for k, v in fprof.items() if k.split("<")[0] in ("px", "chk", "axis_fwd", "axis_inv")
             and "f32" in k}
     body_ms = sum(v[0] for v in body.values()) / args.forced
+    body_kernels = {}
+    for k, (tms, cnt) in body.items():
+        # loop-body launches (the entry's axis/chk launch is one of them)
+        avg = tms / cnt
+        body_kernels[k] = {"ms_per_launch": round(avg, 4), "launches": cnt,
+                           "GBps": round(bytes_per_launch(k, n) / (avg / 1e3) / 1e9, 1),
+                           "frac_hbm": round(bytes_per_launch(k, n) / (avg / 1e3) / 1e9 / hbm, 4)}
 
     # -- end to end through the host-buffer entry point -----------------------
     h_work = torch.empty_like(h_e0).pin_memory()
@@ -310,6 +482,8 @@ def main():
     if dist:
         dist.all_reduce(e2e_ms_t, op=dist.ReduceOp.MAX)
     e2e_val = world * field_bytes / (float(e2e_ms_t.item()) / 1e3) / 1e9
+
+    forms = measure_forms(ffcz, torch, forms_in, it, hbm) if forms_in else None
 
     if rank != 0:
         if dist:
@@ -331,23 +505,20 @@ def main():
                    "step": "ffcz_correct (loop + FP64 certification), e0 resident in HBM"},
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": field_bytes + 64,
                 "d2h_bytes_per_step": field_bytes + 4 + 160},
-        "roofline": {"bound": "hbm", "kernel": top_key, "achieved": round(achieved, 1),
-                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "traffic": None, "peak_kind": peak_kind,
-                     "avg_launch_ms": round(top_avg, 4), "algorithmic_bytes": top_bytes,
-                     "share_of_step": round(top_ms / tot, 3) if tot else None},
+        "roofline": roof,
         "per_iteration": {"ms": round(it_ms, 4), "body_kernels_ms": round(body_ms, 4),
                           "design_bytes": design, "passes": passes,
                           "design_GBps": round(design / (it_ms / 1e3) / 1e9, 1),
                           "frac_hbm_design": round(design / (it_ms / 1e3) / 1e9 / hbm, 4),
                           "frac_hbm_two_pass_minimum": round(minimum / (it_ms / 1e3) / 1e9 / hbm, 4),
-                          "forced_iters": args.forced},
+                          "forced_iters": args.forced, "kernels": body_kernels},
         "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1],
                         "share": round(v[0] / tot, 3)} for k, v in prof.items()},
         "ms_cert": round(st["ms_cert"], 4),
         "clocks": clk,
         "gpu_launches": int(launches),
         "cpu_baseline": cpu,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -1,0 +1,82 @@
+"""Differentiable correction: e_K = F(e0) for K forced iterations of Alg. 1.
+
+``FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every)`` runs K iterations
+(min_iters = max_iters = K, no certification) in the CUDA library; its
+backward calls ``ffcz_correct_backward``, the vector-Jacobian product built
+from the clips' active-set masks, regenerated from float32 checkpoints taken
+every ``ckpt_every`` iterations.  One step e <- P_s(IDFT(P_f(DFT(e)))) has the
+Jacobian M_s IDFT M_f DFT, and IDFT M_f DFT is symmetric in the real frequency
+basis of Sec. IV-A, so the transposed step is g <- IDFT(M_f DFT(M_s g)).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import Plan
+
+_plans: dict = {}
+
+
+def _plan(shape, K, m):
+    key = (tuple(shape), int(K), int(m), torch.cuda.current_device())
+    p = _plans.get(key)
+    if p is None:
+        p = Plan([tuple(shape)], min_iters=K, max_iters=K, certify=0, K=K, ckpt_every=m)
+        _plans[key] = p
+    return p
+
+
+class FFCzCorrect(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, e0, eps_s: float, eps_f: float, K: int = 50, ckpt_every: int = 10):
+        if e0.dtype != torch.float32 or not e0.is_cuda:
+            raise TypeError("e0 must be a float32 CUDA tensor")
+        e0c = e0.detach().contiguous()
+        plan = _plan(e0c.shape, K, ckpt_every)
+        e = e0c.clone()
+        plan.correct(e.reshape(-1), [eps_s], [eps_f])
+        ctx.save_for_backward(e0c)
+        ctx.cfg = (float(eps_s), float(eps_f), int(K), int(ckpt_every))
+        return e
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (e0,) = ctx.saved_tensors
+        eps_s, eps_f, K, m = ctx.cfg
+        plan = _plan(e0.shape, K, m)
+        g = grad_out.detach().to(torch.float32).contiguous()
+        gin = torch.empty_like(e0)
+        plan.backward(e0.reshape(-1), g.reshape(-1), gin.reshape(-1), [eps_s], [eps_f])
+        return gin, None, None, None, None
+
+
+def correct_differentiable(e0, eps_s, eps_f, K=50, ckpt_every=10):
+    return FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every)
+
+
+def power_spectrum_loss(x, e, k_max=None):
+    """Squared log power-spectrum mismatch between x + e and x (float64 sums).
+
+    Shell-summed power spectrum of Sec. III on the fluctuation x - mean
+    (A13), integer shells round(|k|) in 1..N/2, half-spectrum bins weighted 2
+    except the self-conjugate planes.  Test and benchmark use only (torch.fft).
+    """
+    def spectrum(f):
+        f = f.to(torch.float64)
+        F = torch.fft.rfftn(f - f.mean())
+        p = F.real ** 2 + F.imag ** 2
+        n = f.shape
+        ks = [torch.fft.fftfreq(s, d=1.0 / s, device=f.device, dtype=torch.float64) for s in n[:-1]]
+        ks.append(torch.arange(n[-1] // 2 + 1, device=f.device, dtype=torch.float64))
+        grids = torch.meshgrid(*ks, indexing="ij")
+        kr = torch.sqrt(sum(g * g for g in grids)).round().long()
+        w = torch.full_like(p, 2.0)
+        w[..., 0] = 1.0
+        if n[-1] % 2 == 0:
+            w[..., -1] = 1.0
+        km = k_max or min(n) // 2
+        shells = torch.zeros(km + 1, dtype=torch.float64, device=f.device)
+        mask = kr <= km
+        shells.index_add_(0, kr[mask], (w * p)[mask])
+        return shells[1:]
+    return torch.sum((torch.log(spectrum(x + e)) - torch.log(spectrum(x))) ** 2)

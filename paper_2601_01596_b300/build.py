@@ -34,8 +34,9 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    extra = os.environ.get("FFCZ_NVCC_EXTRA", "").split()   # e.g. -DFFCZ_W32=4
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-cudart", "static", "-I", os.path.join(ROOT, "include"), *SRC, "-o", LIB + ".tmp"]
+           "-cudart", "static", "-I", os.path.join(ROOT, "include"), *extra, *SRC, "-o", LIB + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

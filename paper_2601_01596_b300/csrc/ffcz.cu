@@ -414,12 +414,12 @@ void launch_row1(int L, const Args& a, int P1, int count, cudaStream_t s) {
 // Words of mask storage one pass writes (one uint32 per thread of a live tile).
 template <typename T>
 int64_t x_words(int M, int64_t rows) {
-  const int W = 64 / (int)sizeof(v2<T>);
+  const int W = TileW<T>::value;
   return (rows / W) * (int64_t)(M / 8) * W;
 }
 template <typename T>
 int64_t chkw(int L, int Nmid, int M) {
-  const int W = 64 / (int)sizeof(v2<T>);
+  const int W = TileW<T>::value;
   const int64_t nmain = (int64_t)Nmid * (M / W);
   const int npairs = Nmid / 2 + 1;
   return (nmain + (npairs + W / 2 - 1) / (W / 2)) * (int64_t)(L / 8) * W;
@@ -742,10 +742,13 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
                                                                    only_uncert ? 1 : 0, p->d_nactive);
   g_launches++;
   entry<T>(p, B, e, !only_uncert, p->stream);
-  int chunk = 1;
+  int chunk = 1, launched = 0;
   const int cmax = std::max(1, p->opts.chunk);
-  while (read_active(p) > 0) {
-    run_chunk<T>(p, B, chunk);
+  const int cap = p->h_prm[0].max_iters;   // no item iterates past it
+  while (launched < cap && read_active(p) > 0) {
+    const int c = std::min(chunk, cap - launched);
+    run_chunk<T>(p, B, c);
+    launched += c;
     chunk = std::min(chunk * 2, cmax);
   }
   exit_pass<T>(p, B, e, p->stream);

@@ -1,7 +1,7 @@
 // fft_core.cuh -- register/shared-memory Stockham FFT on pencils (sm_103a).
 //
 // One "tile" is W pencils of length L (a power of two, 8..1024) processed by
-// (L/8)*W threads.  Thread (j, w) with w = tid % W, j = tid / W holds eight
+// (L/8)*W threads (W: see TileW).  Thread (j, w) with w = tid % W, j = tid / W holds eight
 // complex values of pencil w in registers: v[u] = x[j + u*L/8] (u = 0..7).
 // Between the radix stages the values go through shared memory, pencils
 // interleaved (element l of pencil w at row l, column w; rows of W elements
@@ -109,6 +109,15 @@ __device__ __forceinline__ void dftR(v2<T> (&x)[R]) {
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
+// Pencils per tile: float64 tiles use 4 (64-byte rows); float32 tiles use
+// FFCZ_W32 pencils (4: 32-byte rows, CTAs half the size and twice as many
+// resident; 8: 64-byte rows).
+#ifndef FFCZ_W32
+#define FFCZ_W32 8
+#endif
+template <typename T> struct TileW { static constexpr int value = 4; };
+template <> struct TileW<float> { static constexpr int value = FFCZ_W32; };
+
 // Radix schedule and twiddle-table layout for length L (host and device).
 template <int L>
 struct Sched {
@@ -137,7 +146,7 @@ __host__ __device__ constexpr int pidx(int l) { return l + (l >> 3); }
 // A thread's view of its pencil in two ping-pong tile buffers.
 template <typename T, int L>
 struct Tile {
-  static constexpr int W = 64 / (int)sizeof(v2<T>);
+  static constexpr int W = TileW<T>::value;
   static constexpr int ROWS = L + L / 8;
   static constexpr int ELEMS = ROWS * W;   // one buffer
   v2<T>* p0;  // buffer used by even exchanges (+ w)

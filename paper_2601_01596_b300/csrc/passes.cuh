@@ -112,10 +112,10 @@ __device__ __forceinline__ v2<T>* pick(const Args& a, int sel, int t) {
 // Per-tile launch geometry, shared by host and device.
 template <typename T, int L>
 struct Geo {
-  static constexpr int W = 64 / (int)sizeof(v2<T>);   // pencils per tile
+  static constexpr int W = TileW<T>::value;            // pencils per tile
   static constexpr int NT = L / 8;                     // threads per pencil
   static constexpr int TPT = NT * W;                   // threads per tile
-  static constexpr int G = TPT >= 256 ? 1 : 256 / TPT; // tiles per CTA
+  static constexpr int G = TPT >= 128 ? 1 : 128 / TPT; // tiles per CTA (>= 128 threads)
   static constexpr int NTHR = G * TPT;
   // resident CTAs per SM the register budget is sized for: float32 tiles
   // get 1024 threads per SM (64 registers), float64 tiles 512 (128 registers)

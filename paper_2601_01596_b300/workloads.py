@@ -140,8 +140,27 @@ def diffraction_image(n: int, rng: np.random.Generator) -> np.ndarray:
     return np.log10(I + 1e-12 * I.max())
 
 
+def _item_rng(seed: int, i: int) -> np.random.Generator:
+    """Independent stream of batch item i (so items can be built in parallel)."""
+    return np.random.default_rng(np.random.SeedSequence([seed, i]))
+
+
+def _map(fn, args, workers):
+    if workers and workers > 1 and len(args) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            return pool.starmap(fn, args, chunksize=max(1, len(args) // (4 * workers)))
+    return [fn(*a) for a in args]
+
+
+def _diffraction_item(i, n, seed, rel_s, eps_f):
+    x = diffraction_image(int(n), _item_rng(seed, i)).astype(np.float32)
+    E = rel_s * (float(x.max()) - float(x.min()))
+    return _item(f"img{i}_{n}", x, E, eps_f)
+
+
 def diffraction_batch(count=512, sizes=(256, 512, 1024), seed=0, rel_s=1e-3,
-                      eps_f=1e-2):
+                      eps_f=1e-2, workers=0):
     """Images of mixed sizes in near-equal thirds, order shuffled by rng(seed).
 
     eps_f is absolute (the workload gives no normaliser for it)."""
@@ -150,12 +169,8 @@ def diffraction_batch(count=512, sizes=(256, 512, 1024), seed=0, rel_s=1e-3,
     ns = np.concatenate([np.full(p, s) for p, s in zip(per, sizes)])
     rng = np.random.default_rng(seed)
     rng.shuffle(ns)
-    items = []
-    for i, n in enumerate(ns):
-        x = diffraction_image(int(n), rng).astype(np.float32)
-        E = rel_s * (float(x.max()) - float(x.min()))
-        items.append(_item(f"img{i}_{n}", x, E, eps_f))
-    return items
+    return _map(_diffraction_item, [(i, int(n), seed, rel_s, eps_f) for i, n in enumerate(ns)],
+                workers)
 
 
 # -- batched 1D EEG-like signals ---------------------------------------------
@@ -174,18 +189,19 @@ def eeg_signal(n: int, rng: np.random.Generator, fs=256.0) -> np.ndarray:
     return pink + A * np.sin(2 * np.pi * 10.0 * t + ph) + rng.normal(0.0, 0.1, n)
 
 
+def _eeg_item(i, n, seed, rel_s, rel_f):
+    x = eeg_signal(int(n), _item_rng(seed, i)).astype(np.float32)
+    E = rel_s * (float(x.max()) - float(x.min()))
+    D = rel_f * float(np.max(np.abs(np.fft.rfft(x.astype(np.float64)))))
+    return _item(f"eeg{i}_{n}", x, E, D)
+
+
 def eeg_batch(count=4096, lo=1024, hi=65536, seed=0, rel_s=1e-3, rel_f=5e-3,
-              lengths=None):
+              lengths=None, workers=0):
     """1D signals of uneven length ~ U{lo..hi} (or the given ``lengths``)."""
     rng = np.random.default_rng(seed)
     ns = lengths if lengths is not None else rng.integers(lo, hi + 1, size=count)
-    items = []
-    for i, n in enumerate(ns):
-        x = eeg_signal(int(n), rng).astype(np.float32)
-        E = rel_s * (float(x.max()) - float(x.min()))
-        D = rel_f * float(np.max(np.abs(np.fft.rfft(x.astype(np.float64)))))
-        items.append(_item(f"eeg{i}_{n}", x, E, D))
-    return items
+    return _map(_eeg_item, [(i, int(n), seed, rel_s, rel_f) for i, n in enumerate(ns)], workers)
 
 
 def bimodal_error(shape, seed, E=1.0, dtype=np.float64):

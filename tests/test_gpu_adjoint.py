@@ -29,3 +29,25 @@ def test_backward_matches_oracle_vjp(shape, K, m):
     err = np.abs(got - ref)
     assert np.mean(err > 1e-4 * scale) < 1e-3
     assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+
+
+def test_autograd_function_matches_oracle_through_spectrum_loss():
+    """d loss / d e0 for loss = log power-spectrum mismatch of x + e_K vs x."""
+    import torch
+    from paper_2601_01596_b300.autograd import FFCzCorrect, power_spectrum_loss
+    it = W.turbulence_field(16, seed=4)
+    x = torch.from_numpy(it["x"].astype(np.float32)).cuda()
+    e0 = torch.from_numpy(it["e0"]).cuda().requires_grad_(True)
+    K, m = 6, 4
+    eK = FFCzCorrect.apply(e0, it["E"], it["D"], K, m)
+    loss = power_spectrum_loss(x, eK)
+    loss.backward()
+    g_gpu = e0.grad.cpu().numpy().astype(np.float64)
+    # reference: same loss in float64 on the oracle's e_K, then the oracle VJP
+    eK_ref, _, _ = O.forward_masks(it["e0"], it["E"], it["D"], K)
+    et = torch.from_numpy(eK_ref).requires_grad_(True)
+    lref = power_spectrum_loss(torch.from_numpy(it["x"].astype(np.float64)), et)
+    lref.backward()
+    g_ref = O.correct_backward(it["e0"], et.grad.numpy(), it["E"], it["D"], K)
+    assert abs(loss.item() - lref.item()) <= 1e-3 * abs(lref.item()) + 1e-9
+    assert np.linalg.norm(g_gpu - g_ref) <= 2e-3 * np.linalg.norm(g_ref)
