@@ -37,7 +37,7 @@ enum Op1 : int {
 
 // Chirp b_m = exp(i pi m^2 / N) from r = m^2 mod 2N: the phase r/N is in
 // [0, 2); sincospi of the part below 1 (the CUDA function is called), the
-// sign flipped for the upper half.
+// sign flipped for the upper half.  Used once per plan to fill the tables.
 template <typename T>
 __device__ __forceinline__ v2<T> chirp_r(uint64_t r, uint64_t N) {
   const bool hi = r >= N;
@@ -48,29 +48,26 @@ __device__ __forceinline__ v2<T> chirp_r(uint64_t r, uint64_t N) {
   return hi ? mk<T>(-c, -s) : mk<T>(c, s);
 }
 
-// Chirps of the eight rows m_u = m0 + u D of a thread, m_u^2 mod 2N by exact
-// integer increments: m_{u+1}^2 - m_u^2 = 2 D m0 + (2u + 1) D^2 (D^2 mod 2N
-// comes from the host).
+// Chirp table b_n, n < N, of every item of a group (one launch per plan and
+// precision); stored like the items' float32 data, at the item's e offset.
 template <typename T>
-__device__ __forceinline__ void chirps(v2<T> (&b)[8], uint64_t m0, uint64_t D, uint64_t dd2N, uint64_t N) {
-  const uint64_t twoN = 2 * N;
-  const uint64_t m0r = m0 % twoN;
-  uint64_t r = m0r * m0r % twoN;
-  uint64_t inc = ((2 * (D % twoN)) % twoN * m0r + dd2N) % twoN;
-  const uint64_t step = (2 * dd2N) % twoN;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    b[u] = chirp_r<T>(r, N);
-    r += inc; if (r >= twoN) r -= twoN;
-    inc += step; if (inc >= twoN) inc -= twoN;
+__global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const uint64_t N = (uint64_t)prm[item].n, twoN = 2 * N;
+  v2<T>* out = tab + g.eoff[gi];
+  for (uint64_t n = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; n < N;
+       n += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = n % twoN * (n % twoN) % twoN;
+    out[n] = chirp_r<T>(r, N);
   }
 }
 
 // Column pass along n1 / k1 (length P1 = L), tile = W consecutive columns.
-template <typename T, int L>
-__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+template <typename T, int L, int W_ = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
 k1_col(Args a) {
-  FFCZ_AXIS_PROLOGUE(T, L)
+  FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int NT = G_::NT, W = G_::W;
   const int P2 = a.g.M;
   const int64_t N = p.n;
@@ -112,8 +109,14 @@ k1_col(Args a) {
     for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
   }
   load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);
+  // chirps b_n of the thread's rows from the item's table (zero past N)
+  const v2<T>* ctab = reinterpret_cast<const v2<T>*>(a.chirp) + a.g.eoff[gi];
   v2<T> b[8];
-  chirps<T>(b, m0, D, (uint64_t)p.dd2N, (uint64_t)N);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int64_t n = (int64_t)m0 + (int64_t)u * D;
+    b[u] = (live && n < N) ? ctab[n] : mk<T>(T(0), T(0));
+  }
 
   if (op == OP1_FILTER) {
     // wrapped chirp: f[m] = b_m for m < N, f[m] = b_{P-m} for 0 < P - m < N
@@ -121,8 +124,8 @@ k1_col(Args a) {
     for (int u = 0; u < 8; ++u) {
       const int64_t m = (int64_t)m0 + (int64_t)u * D, q = Pn - m;
       v2<T> f = mk<T>(T(0), T(0));
-      if (m < N) f = b[u];
-      else if (q < N) f = chirp_r<T>((uint64_t)q % (2 * N) * ((uint64_t)q % (2 * N)) % (2 * N), N);
+      if (live && m < N) f = b[u];
+      else if (live && q < N) f = ctab[q];
       v[u] = f;
     }
   } else if (op == OP1_ENTRY) {
@@ -208,10 +211,10 @@ k1_col(Args a) {
 }
 
 // Row pass along n2 / k2 (length P2 = L), tile = W consecutive rows.
-template <typename T, int L>
-__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+template <typename T, int L, int W_ = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
 k1_row(Args a) {
-  FFCZ_AXIS_PROLOGUE(T, L)
+  FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int NT = G_::NT;
   const int P1 = a.g.Nz;
   const int ntiles = P1 / G_::W;

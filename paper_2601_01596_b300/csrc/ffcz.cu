@@ -13,6 +13,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -103,6 +104,8 @@ struct DevGroup {
   int count;
   int ndim, Nz, Ny, Nx, M;
   int64_t rows, n;
+  // float32 tile widths (pencils per tile) picked by the tuner per pass kind
+  int wx = 4, wa = 8, wc = 8, w1c = 8, w1r = 4;
   // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
   int P1 = 0, P2 = 0;
   const void* twp32 = nullptr;
@@ -150,6 +153,8 @@ struct ffcz_plan_s {
   void* B32[2] = {nullptr, nullptr};
   void* Bt32 = nullptr;        // 1D: FFT_P of the wrapped chirps (float32 / float64)
   void* Bt64 = nullptr;
+  void* ch32 = nullptr;        // 1D: chirp tables b_n (float32 / float64)
+  void* ch64 = nullptr;
   void* B64[2] = {nullptr, nullptr};
   void* Bc = nullptr;
   float* staging = nullptr;
@@ -253,173 +258,185 @@ void prof_collect(ffcz_plan_s* p) {
   p->pend.clear();
 }
 
-// ----- kernel dispatch over the pencil length -------------------------------
+// ----- kernel dispatch over the pencil length and the tile width -------------
+// float32 kernels exist with 4- and 8-pencil tiles (chosen per plan by the
+// tuner); float64 kernels use 4-pencil tiles.
 enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
 
-template <typename T, int M>
-void launch_x_t(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
-  using G_ = Geo<T, M>;
+#define FFCZ_DISPATCH_L(Lv, FN, ...)                                     \
+  switch (Lv) {                                                           \
+    case 8: FN<8>(__VA_ARGS__); break;                                    \
+    case 16: FN<16>(__VA_ARGS__); break;                                  \
+    case 32: FN<32>(__VA_ARGS__); break;                                  \
+    case 64: FN<64>(__VA_ARGS__); break;                                  \
+    case 128: FN<128>(__VA_ARGS__); break;                                \
+    case 256: FN<256>(__VA_ARGS__); break;                                \
+    case 512: FN<512>(__VA_ARGS__); break;                                \
+    case 1024: FN<1024>(__VA_ARGS__); break;                              \
+    default: fail(FFCZ_ERR_UNSUPPORTED, "transform length");              \
+  }
+
+template <typename T, int M, int W>
+void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
+  using G_ = Geo<T, M, W>;
   const int64_t tiles = rows / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
-  const size_t sm = Smem<T, M>::bytes_x;
+  const size_t sm = Smem<T, M, W>::bytes_x;
   if (g_dry) {
-    set_smem(k_xfwd<T, M>, sm); set_smem(k_px<T, M>, sm); set_smem(k_xexit<T, M>, sm);
+    set_smem(k_xfwd<T, M, W>, sm); set_smem(k_px<T, M, W>, sm); set_smem(k_xexit<T, M, W>, sm);
     return;
   }
   ProfScope ps(kind == XFWD ? "xfwd" : kind == XPX ? "px" : "xexit", 8 * (int)sizeof(T), M, s);
   switch (kind) {
-    case XFWD: k_xfwd<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XPX: k_px<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XEXIT: k_xexit<T, M><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XFWD: k_xfwd<T, M, W><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XPX: k_px<T, M, W><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XEXIT: k_xexit<T, M, W><<<grid, G_::NTHR, sm, s>>>(a); break;
   }
   g_launches++;
 }
-
 template <typename T>
-void launch_x(XKind kind, int M, const Args& a, int64_t rows, int count, cudaStream_t s) {
-  switch (M) {
-    case 8: launch_x_t<T, 8>(kind, a, rows, count, s); break;
-    case 16: launch_x_t<T, 16>(kind, a, rows, count, s); break;
-    case 32: launch_x_t<T, 32>(kind, a, rows, count, s); break;
-    case 64: launch_x_t<T, 64>(kind, a, rows, count, s); break;
-    case 128: launch_x_t<T, 128>(kind, a, rows, count, s); break;
-    case 256: launch_x_t<T, 256>(kind, a, rows, count, s); break;
-    case 512: launch_x_t<T, 512>(kind, a, rows, count, s); break;
-    case 1024: launch_x_t<T, 1024>(kind, a, rows, count, s); break;
-    default: fail(FFCZ_ERR_UNSUPPORTED, "x length");
+struct XL {
+  template <int M>
+  static void go(XKind kind, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      if (w == 4) launch_x_tw<T, M, 4>(kind, a, rows, count, s);
+      else launch_x_tw<T, M, 8>(kind, a, rows, count, s);
+    } else {
+      launch_x_tw<T, M, 4>(kind, a, rows, count, s);
+    }
   }
+};
+template <typename T>
+void launch_x(XKind kind, int M, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
+  FFCZ_DISPATCH_L(M, XL<T>::template go, kind, w, a, rows, count, s)
 }
 
-template <typename T, int L, int DIR>
-void launch_axis_t(const Args& a, int Nz, int M, int count, cudaStream_t s) {
-  using G_ = Geo<T, L>;
+template <typename T, int L, int DIR, int W>
+void launch_axis_tw(const Args& a, int Nz, int M, int count, cudaStream_t s) {
+  using G_ = Geo<T, L, W>;
   const int64_t tiles = (int64_t)Nz * (M / G_::W);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
-  const size_t sm = Smem<T, L>::bytes_axis;
-  if (g_dry) {
-    set_smem(k_axis<T, L, DIR>, sm);
-    return;
-  }
+  const size_t sm = Smem<T, L, W>::bytes_axis;
+  if (g_dry) { set_smem(k_axis<T, L, DIR, W>, sm); return; }
   ProfScope ps(DIR < 0 ? "axis_fwd" : "axis_inv", 8 * (int)sizeof(T), L, s);
-  k_axis<T, L, DIR><<<grid, G_::NTHR, sm, s>>>(a);
+  k_axis<T, L, DIR, W><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
-
 template <typename T, int DIR>
-void launch_axis(int L, const Args& a, int Nz, int M, int count, cudaStream_t s) {
-  switch (L) {
-    case 8: launch_axis_t<T, 8, DIR>(a, Nz, M, count, s); break;
-    case 16: launch_axis_t<T, 16, DIR>(a, Nz, M, count, s); break;
-    case 32: launch_axis_t<T, 32, DIR>(a, Nz, M, count, s); break;
-    case 64: launch_axis_t<T, 64, DIR>(a, Nz, M, count, s); break;
-    case 128: launch_axis_t<T, 128, DIR>(a, Nz, M, count, s); break;
-    case 256: launch_axis_t<T, 256, DIR>(a, Nz, M, count, s); break;
-    case 512: launch_axis_t<T, 512, DIR>(a, Nz, M, count, s); break;
-    case 1024: launch_axis_t<T, 1024, DIR>(a, Nz, M, count, s); break;
-    default: fail(FFCZ_ERR_UNSUPPORTED, "axis length");
+struct AL {
+  template <int L>
+  static void go(int w, const Args& a, int Nz, int M, int count, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      if (w == 4) launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
+      else launch_axis_tw<T, L, DIR, 8>(a, Nz, M, count, s);
+    } else {
+      launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
+    }
   }
+};
+template <typename T, int DIR>
+void launch_axis(int L, int w, const Args& a, int Nz, int M, int count, cudaStream_t s) {
+  using D = AL<T, DIR>;
+  FFCZ_DISPATCH_L(L, D::template go, w, a, Nz, M, count, s)
 }
 
-template <typename T, int L>
-int64_t chk_tiles(int Nmid, int M) {
-  return chk_ntiles(Geo<T, L>::W, M, Nmid);
-}
-
-template <typename T, int L>
-void launch_chk_t(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
-  using G_ = Geo<T, L>;
-  const int64_t tiles = chk_tiles<T, L>(Nmid, M);
+template <typename T, int L, int W>
+void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+  using G_ = Geo<T, L, W>;
+  const int64_t tiles = chk_ntiles(W, M, Nmid);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
-  const size_t sm = Smem<T, L>::bytes_axis;
-  if (g_dry) {
-    set_smem(k_chk<T, L>, sm);
-    return;
-  }
+  const size_t sm = Smem<T, L, W>::bytes_axis;
+  if (g_dry) { set_smem(k_chk<T, L, W>, sm); return; }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk",
                8 * (int)sizeof(T), L, s);
-  k_chk<T, L><<<grid, G_::NTHR, sm, s>>>(a);
+  k_chk<T, L, W><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
-
 template <typename T>
-void launch_chk(int L, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
-  switch (L) {
-    case 8: launch_chk_t<T, 8>(a, Nmid, M, count, s); break;
-    case 16: launch_chk_t<T, 16>(a, Nmid, M, count, s); break;
-    case 32: launch_chk_t<T, 32>(a, Nmid, M, count, s); break;
-    case 64: launch_chk_t<T, 64>(a, Nmid, M, count, s); break;
-    case 128: launch_chk_t<T, 128>(a, Nmid, M, count, s); break;
-    case 256: launch_chk_t<T, 256>(a, Nmid, M, count, s); break;
-    case 512: launch_chk_t<T, 512>(a, Nmid, M, count, s); break;
-    case 1024: launch_chk_t<T, 1024>(a, Nmid, M, count, s); break;
-    default: fail(FFCZ_ERR_UNSUPPORTED, "check-axis length");
+struct CL {
+  template <int L>
+  static void go(int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      if (w == 4) launch_chk_tw<T, L, 4>(a, Nmid, M, count, s);
+      else launch_chk_tw<T, L, 8>(a, Nmid, M, count, s);
+    } else {
+      launch_chk_tw<T, L, 4>(a, Nmid, M, count, s);
+    }
   }
+};
+template <typename T>
+void launch_chk(int L, int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+  FFCZ_DISPATCH_L(L, CL<T>::template go, w, a, Nmid, M, count, s)
 }
 
 // ----- 1D (Bluestein) passes ---------------------------------------------------
-template <typename T, int L>
-void launch_col1_t(const Args& a, int P2, int count, cudaStream_t s) {
-  using G_ = Geo<T, L>;
+template <typename T, int L, int W>
+void launch_col1_tw(const Args& a, int P2, int count, cudaStream_t s) {
+  using G_ = Geo<T, L, W>;
   const int64_t tiles = P2 / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
-  const size_t sm = Smem<T, L>::bytes_axis;
-  if (g_dry) { set_smem(k1_col<T, L>, sm); return; }
+  const size_t sm = Smem<T, L, W>::bytes_axis;
+  if (g_dry) { set_smem(k1_col<T, L, W>, sm); return; }
   ProfScope ps(a.op1 == OP1_FCLIP ? ((a.mode & M_NOWRITE) ? "col1_cert" : "col1_fclip")
                : a.op1 == OP1_SCLIP ? "col1_sclip" : a.op1 == OP1_EXIT ? "col1_exit"
                : a.op1 == OP1_FILTER ? "col1_filter" : "col1_entry",
                8 * (int)sizeof(T), L, s);
-  k1_col<T, L><<<grid, G_::NTHR, sm, s>>>(a);
+  k1_col<T, L, W><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
 template <typename T>
-void launch_col1(int L, const Args& a, int P2, int count, cudaStream_t s) {
-  switch (L) {
-    case 8: launch_col1_t<T, 8>(a, P2, count, s); break;
-    case 16: launch_col1_t<T, 16>(a, P2, count, s); break;
-    case 32: launch_col1_t<T, 32>(a, P2, count, s); break;
-    case 64: launch_col1_t<T, 64>(a, P2, count, s); break;
-    case 128: launch_col1_t<T, 128>(a, P2, count, s); break;
-    case 256: launch_col1_t<T, 256>(a, P2, count, s); break;
-    case 512: launch_col1_t<T, 512>(a, P2, count, s); break;
-    case 1024: launch_col1_t<T, 1024>(a, P2, count, s); break;
-    default: fail(FFCZ_ERR_UNSUPPORTED, "1D column length");
+struct C1L {
+  template <int L>
+  static void go(int w, const Args& a, int P2, int count, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      if (w == 4) launch_col1_tw<T, L, 4>(a, P2, count, s);
+      else launch_col1_tw<T, L, 8>(a, P2, count, s);
+    } else {
+      launch_col1_tw<T, L, 4>(a, P2, count, s);
+    }
   }
+};
+template <typename T>
+void launch_col1(int L, int w, const Args& a, int P2, int count, cudaStream_t s) {
+  FFCZ_DISPATCH_L(L, C1L<T>::template go, w, a, P2, count, s)
 }
-template <typename T, int L>
-void launch_row1_t(const Args& a, int P1, int count, cudaStream_t s) {
-  using G_ = Geo<T, L>;
+template <typename T, int L, int W>
+void launch_row1_tw(const Args& a, int P1, int count, cudaStream_t s) {
+  using G_ = Geo<T, L, W>;
   const int64_t tiles = P1 / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
-  const size_t sm = Smem<T, L>::bytes_axis;
-  if (g_dry) { set_smem(k1_row<T, L>, sm); return; }
+  const size_t sm = Smem<T, L, W>::bytes_axis;
+  if (g_dry) { set_smem(k1_row<T, L, W>, sm); return; }
   ProfScope ps(a.op1 == OP1_FWD ? "row1_fwd" : "row1_conv", 8 * (int)sizeof(T), L, s);
-  k1_row<T, L><<<grid, G_::NTHR, sm, s>>>(a);
+  k1_row<T, L, W><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
 template <typename T>
-void launch_row1(int L, const Args& a, int P1, int count, cudaStream_t s) {
-  switch (L) {
-    case 8: launch_row1_t<T, 8>(a, P1, count, s); break;
-    case 16: launch_row1_t<T, 16>(a, P1, count, s); break;
-    case 32: launch_row1_t<T, 32>(a, P1, count, s); break;
-    case 64: launch_row1_t<T, 64>(a, P1, count, s); break;
-    case 128: launch_row1_t<T, 128>(a, P1, count, s); break;
-    case 256: launch_row1_t<T, 256>(a, P1, count, s); break;
-    case 512: launch_row1_t<T, 512>(a, P1, count, s); break;
-    case 1024: launch_row1_t<T, 1024>(a, P1, count, s); break;
-    default: fail(FFCZ_ERR_UNSUPPORTED, "1D row length");
+struct R1L {
+  template <int L>
+  static void go(int w, const Args& a, int P1, int count, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+      if (w == 4) launch_row1_tw<T, L, 4>(a, P1, count, s);
+      else launch_row1_tw<T, L, 8>(a, P1, count, s);
+    } else {
+      launch_row1_tw<T, L, 4>(a, P1, count, s);
+    }
   }
+};
+template <typename T>
+void launch_row1(int L, int w, const Args& a, int P1, int count, cudaStream_t s) {
+  FFCZ_DISPATCH_L(L, R1L<T>::template go, w, a, P1, count, s)
 }
 
 // Words of mask storage one pass writes (one uint32 per thread of a live tile).
 template <typename T>
-int64_t x_words(int M, int64_t rows) {
-  const int W = TileW<T>::value;
+int64_t x_words(int M, int64_t rows, int W) {
+  if (sizeof(T) == 8) W = 4;
   return (rows / W) * (int64_t)(M / 8) * W;
 }
 template <typename T>
-int64_t chkw(int L, int Nmid, int M) {
-  const int W = TileW<T>::value;
+int64_t chkw(int L, int Nmid, int M, int W) {
+  if (sizeof(T) == 8) W = 4;
   const int64_t nmain = (int64_t)Nmid * (M / W);
   const int npairs = Nmid / 2 + 1;
   return (nmain + (npairs + W / 2 - 1) / (W / 2)) * (int64_t)(L / 8) * W;
@@ -452,6 +469,7 @@ template <typename T>
 void col1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
   a.tw = tw_of<T>(p->tb, dg.P1);
   a.twr = sizeof(T) == 4 ? dg.twp32 : dg.twp64;
+  a.chirp = sizeof(T) == 4 ? p->ch32 : p->ch64;
   a.op1 = op;
 }
 template <typename T>
@@ -461,18 +479,26 @@ void row1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
   a.op1 = op;
 }
 
-// Bt = FFT_P(wrapped chirp) for every 1D item, in the precision T.
+// Chirp tables and Bt = FFT_P(wrapped chirp) for every 1D item, in the
+// precision T.
 template <typename T>
 void build_bt(ffcz_plan_s* p) {
+  void*& ch = sizeof(T) == 4 ? p->ch32 : p->ch64;
+  if (!ch) ch = dalloc(p, (size_t)p->total * sizeof(v2<T>));
+  for (auto& dg : p->groups) {
+    dim3 grid(64, (unsigned)dg.count);
+    k1_chirp_table<T><<<grid, 256, 0, p->stream>>>(dg.g, p->d_prm, reinterpret_cast<v2<T>*>(ch));
+    g_launches++;
+  }
   void*& bt = sizeof(T) == 4 ? p->Bt32 : p->Bt64;
   if (!bt) bt = dalloc(p, (size_t)p->total_c * sizeof(v2<T>));
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, bt, bt, p->d_st);
     a.pred = P_ALL;
     col1_args<T>(p, a, dg, OP1_FILTER);
-    launch_col1<T>(dg.P1, a, dg.P2, dg.count, p->stream);
+    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
     row1_args<T>(p, a, dg, OP1_FWD);
-    launch_row1<T>(dg.P2, a, dg.P1, dg.count, p->stream);
+    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
   }
 }
 
@@ -489,7 +515,7 @@ void entry1(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStre
     col1_args<T>(p, a, dg, OP1_ENTRY);
     a.e = e;
     a.mode = measure_preclip ? M_MEASURE : 0;
-    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
   if (measure_preclip) {
     k_mark_preclip<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch);
@@ -500,16 +526,16 @@ void entry1(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStre
       a.e = e;
       a.mode = M_PRECLIP;
       a.pred = P_PRECLIP;
-      launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+      launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
     }
   }
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     row1_args<T>(p, a, dg, OP1_CONV);
-    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
     col1_args<T>(p, a, dg, OP1_FCLIP);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
                                                              p->d_nactive);
@@ -522,17 +548,17 @@ void body1(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     row1_args<T>(p, a, dg, OP1_CONVC);
     a.sel_in = S_PREV; a.sel_out = S_CUR;
-    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
     a.sel_in = S_CUR;
     col1_args<T>(p, a, dg, OP1_SCLIP);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
     row1_args<T>(p, a, dg, OP1_CONV);
     a.mode = 0;
-    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
     col1_args<T>(p, a, dg, OP1_FCLIP);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
                                                              p->d_nactive);
@@ -547,11 +573,11 @@ void exit1(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
     a.e = e;
     row1_args<T>(p, a, dg, OP1_CONVC);
     a.sel_in = S_PREV; a.sel_out = S_CUR;
-    launch_row1<T>(dg.P2, a, dg.P1, dg.count, s);
+    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
     a.sel_in = S_CUR;
     col1_args<T>(p, a, dg, OP1_EXIT);
     a.mode = M_CLIP;
-    launch_col1<T>(dg.P1, a, dg.P2, dg.count, s);
+    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
 }
 
@@ -563,7 +589,7 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
     tabs_x<T>(p, a, dg);
     a.e = e;
     a.mode = measure_preclip ? M_MEASURE : 0;
-    launch_x<T>(XFWD, dg.M, a, dg.rows, dg.count, s);
+    launch_x<T>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, s);
   }
   if (measure_preclip) {
     k_mark_preclip<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch);
@@ -574,18 +600,18 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
       a.e = e;
       a.mode = M_PRECLIP;
       a.pred = P_PRECLIP;
-      launch_x<T>(XFWD, dg.M, a, dg.rows, dg.count, s);
+      launch_x<T>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, s);
     }
   }
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     if (dg.ndim == 3) {
       a.tw = tw_of<T>(p->tb, dg.Ny);
-      launch_axis<T, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+      launch_axis<T, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
     }
     a.tw = tw_of<T>(p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_chk<T>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+    launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
                                                              p->d_nactive);
@@ -600,23 +626,23 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     if (dg.ndim == 3) {
       a.tw = tw_of<T>(p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
-      launch_axis<T, +1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+      launch_axis<T, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
       a.sel_in = S_CUR;
     } else {
       a.sel_in = S_PREV; a.sel_out = S_CUR;
     }
     tabs_x<T>(p, a, dg);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_x<T>(XPX, dg.M, a, dg.rows, dg.count, s);
+    launch_x<T>(XPX, dg.M, dg.wx, a, dg.rows, dg.count, s);
     a.sel_in = a.sel_out = S_CUR;
     if (dg.ndim == 3) {
       a.tw = tw_of<T>(p->tb, dg.Ny);
       a.mode = 0;
-      launch_axis<T, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+      launch_axis<T, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
     }
     a.tw = tw_of<T>(p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_chk<T>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+    launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
                                                              p->d_nactive);
@@ -633,14 +659,14 @@ void exit_pass(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
     if (dg.ndim == 3) {
       a.tw = tw_of<T>(p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
-      launch_axis<T, +1>(dg.Ny, a, dg.Nz, dg.M, dg.count, s);
+      launch_axis<T, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
       a.sel_in = S_CUR;
     } else {
       a.sel_in = S_PREV;
     }
     tabs_x<T>(p, a, dg);
     a.mode = M_CLIP;
-    launch_x<T>(XEXIT, dg.M, a, dg.rows, dg.count, s);
+    launch_x<T>(XEXIT, dg.M, dg.wx, a, dg.rows, dg.count, s);
   }
 }
 
@@ -714,14 +740,12 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
     q.n = n;
     q.min_iters = min_iters;
     q.max_iters = max_iters;
-    q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0; q.dd2N = 0;
+    q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0;
     if (p->ndim == 1) {
       const int64_t P = p1d_len(n);
-      const uint64_t D = (uint64_t)(P / 8), twoN = 2 * (uint64_t)n;
       q.inv_pn = 1.0 / ((double)P * (double)n);
       q.inv_pnf = (float)q.inv_pn;
       q.logP = ilog2((int)P);
-      q.dd2N = (D % twoN) * (D % twoN) % twoN;
     }
   }
   CK(cudaMemcpyAsync(p->d_prm, p->h_prm, sizeof(ItemParams) * p->batch, cudaMemcpyHostToDevice,
@@ -764,13 +788,13 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
       a.e = const_cast<float*>(e);
       col1_args<double>(p, a, dg, OP1_ENTRY);
       a.mode = M_MEASURE;
-      launch_col1<double>(dg.P1, a, dg.P2, dg.count, p->stream);
+      launch_col1<double>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
       row1_args<double>(p, a, dg, OP1_CONV);
       a.mode = 0;
-      launch_row1<double>(dg.P2, a, dg.P1, dg.count, p->stream);
+      launch_row1<double>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
       col1_args<double>(p, a, dg, OP1_FCLIP);
       a.mode = M_NOWRITE;
-      launch_col1<double>(dg.P1, a, dg.P2, dg.count, p->stream);
+      launch_col1<double>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
       continue;
     }
     Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_st);
@@ -778,15 +802,15 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
     tabs_x<double>(p, a, dg);
     a.e = const_cast<float*>(e);
     a.mode = M_MEASURE;
-    launch_x<double>(XFWD, dg.M, a, dg.rows, dg.count, p->stream);
+    launch_x<double>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
     if (dg.ndim == 3) {
       a.tw = tw_of<double>(p->tb, dg.Ny);
       a.mode = 0;
-      launch_axis<double, -1>(dg.Ny, a, dg.Nz, dg.M, dg.count, p->stream);
+      launch_axis<double, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
     }
     a.tw = tw_of<double>(p->tb, dg.Nz);
     a.mode = M_NOWRITE;
-    launch_chk<double>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
+    launch_chk<double>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
   }
   k_certify<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(
       p->d_prm, p->d_st, (int)p->batch, repair_round ? 1 : 0);
@@ -965,7 +989,7 @@ void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask
   if (dg.ndim == 3) {
     a.tw = tw_of<float>(p->tb, dg.Ny);
     a.sel_in = S_PREV; a.sel_out = S_CUR;
-    launch_axis<float, +1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+    launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
     a.sel_in = S_CUR;
   } else {
     a.sel_in = S_PREV; a.sel_out = S_CUR;
@@ -975,7 +999,7 @@ void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask
   a.mask = smask;
   a.ckpt = ckpt;
   a.ckpt_every = p->bw_m;
-  launch_x<float>(XPX, dg.M, a, dg.rows, 1, p->stream);
+  launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, 1, p->stream);
   if (!do_chk) return;
   a.sel_in = a.sel_out = S_CUR;
   a.mask = nullptr;
@@ -983,12 +1007,12 @@ void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask
   if (dg.ndim == 3) {
     a.tw = tw_of<float>(p->tb, dg.Ny);
     a.mode = 0;
-    launch_axis<float, -1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+    launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
   }
   a.tw = tw_of<float>(p->tb, dg.Nz);
   a.mode = M_CLIP | (fmask ? M_RECORD : 0);
   a.mask = fmask;
-  launch_chk<float>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+  launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
 }
 
 void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uint32_t* fmask) {
@@ -997,15 +1021,15 @@ void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uin
   tabs_x<float>(p, a, dg);
   a.e = e0;
   a.mode = 0;
-  launch_x<float>(XFWD, dg.M, a, dg.rows, 1, p->stream);
+  launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, p->stream);
   if (dg.ndim == 3) {
     a.tw = tw_of<float>(p->tb, dg.Ny);
-    launch_axis<float, -1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+    launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
   }
   a.tw = tw_of<float>(p->tb, dg.Nz);
   a.mode = M_CLIP | (fmask ? M_RECORD : 0);
   a.mask = fmask;
-  launch_chk<float>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+  launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
 }
 
 ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, float* gin,
@@ -1021,8 +1045,8 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
   if (p->bw_K != K || p->bw_m != m) {
-    p->px_words = x_words<float>(dg.M, dg.rows);
-    p->chk_words = chkw<float>(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M);
+    p->px_words = x_words<float>(dg.M, dg.rows, dg.wx);
+    p->chk_words = chkw<float>(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc);
     p->bw_e = (float*)dalloc(p, sizeof(float) * N);
     p->bw_ck = (float*)dalloc(p, sizeof(float) * N * nseg);
     p->bw_smask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->px_words * m);
@@ -1078,14 +1102,14 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
         a.e = const_cast<float*>(gout);
         a.mask = sm;
         a.mode = M_MASK;
-        launch_x<float>(XFWD, dg.M, a, dg.rows, 1, p->stream);
+        launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, p->stream);
         first = false;
       } else {
         advance(p, p->d_st2);
         if (dg.ndim == 3) {
           a.tw = tw_of<float>(p->tb, dg.Ny);
           a.sel_in = S_PREV; a.sel_out = S_CUR;
-          launch_axis<float, +1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+          launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
           a.sel_in = S_CUR;
         } else {
           a.sel_in = S_PREV; a.sel_out = S_CUR;
@@ -1093,19 +1117,19 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
         tabs_x<float>(p, a, dg);
         a.mask = sm;
         a.mode = M_MASK;
-        launch_x<float>(XPX, dg.M, a, dg.rows, 1, p->stream);
+        launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, 1, p->stream);
       }
       a.sel_in = a.sel_out = S_CUR;
       if (dg.ndim == 3) {
         a.tw = tw_of<float>(p->tb, dg.Ny);
         a.mode = 0;
         a.mask = nullptr;
-        launch_axis<float, -1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+        launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
       }
       a.tw = tw_of<float>(p->tb, dg.Nz);
       a.mode = M_MASK;
       a.mask = fm;
-      launch_chk<float>(dg.Nz, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+      launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
     }
   }
   // exit: inverse of the last step's spectrum, no clip
@@ -1117,20 +1141,135 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     if (dg.ndim == 3) {
       a.tw = tw_of<float>(p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
-      launch_axis<float, +1>(dg.Ny, a, dg.Nz, dg.M, 1, p->stream);
+      launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
       a.sel_in = S_CUR;
     } else {
       a.sel_in = S_PREV;
     }
     tabs_x<float>(p, a, dg);
     a.mode = 0;
-    launch_x<float>(XEXIT, dg.M, a, dg.rows, 1, p->stream);
+    launch_x<float>(XEXIT, dg.M, dg.wx, a, dg.rows, 1, p->stream);
     k_premask<<<1184, 256, 0, p->stream>>>(gin, e0, p->d_prm, p->d_st, 0, N);
     g_launches++;
   }
   CK(cudaStreamSynchronize(p->stream));
   CK(cudaGetLastError());
   return FFCZ_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// ----- tile-width tuner ----------------------------------------------------------
+// For every group and float32 pass kind, time the 4- and 8-pencil variants on
+// the plan's own buffers (three launches each after one warm-up, CUDA events)
+// and keep the faster.  Results can be cached in a text file named by
+// FFCZ_TUNE_CACHE (lines "key width"); FFCZ_TUNE=0 keeps the defaults.
+std::map<std::string, int>& tune_table() {
+  static std::map<std::string, int> t;
+  return t;
+}
+std::mutex& tune_mu() {
+  static std::mutex m;
+  return m;
+}
+void tune_load() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* f = getenv("FFCZ_TUNE_CACHE");
+  if (!f) return;
+  FILE* fp = fopen(f, "r");
+  if (!fp) return;
+  char key[256];
+  int w;
+  while (fscanf(fp, "%255s %d", key, &w) == 2) tune_table()[key] = w;
+  fclose(fp);
+}
+void tune_store(const std::string& key, int w) {
+  tune_table()[key] = w;
+  const char* f = getenv("FFCZ_TUNE_CACHE");
+  if (!f) return;
+  FILE* fp = fopen(f, "a");
+  if (!fp) return;
+  fprintf(fp, "%s %d\n", key.c_str(), w);
+  fclose(fp);
+}
+
+template <typename F>
+float time_launches(ffcz_plan_s* p, F&& f) {
+  f();   // warm-up (and module load)
+  CK(cudaEventRecord(p->ev0, p->stream));
+  for (int i = 0; i < 3; ++i) f();
+  CK(cudaEventRecord(p->ev1, p->stream));
+  CK(cudaEventSynchronize(p->ev1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+  return ms;
+}
+
+template <typename F>
+int pick_width(ffcz_plan_s* p, const std::string& key, F&& run_w) {
+  {
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_load();
+    auto it = tune_table().find(key);
+    if (it != tune_table().end()) return it->second;
+  }
+  const float t4 = time_launches(p, [&] { run_w(4); });
+  const float t8 = time_launches(p, [&] { run_w(8); });
+  const int w = t4 < t8 ? 4 : 8;
+  std::lock_guard<std::mutex> lk(tune_mu());
+  tune_store(key, w);
+  return w;
+}
+
+void tune(ffcz_plan_s* p) {
+  const char* env = getenv("FFCZ_TUNE");
+  if (env && env[0] == '0') return;
+  cudaStream_t s = p->stream;
+  for (auto& dg : p->groups) {
+    char base[160];
+    snprintf(base, sizeof base, "d%d_z%d_y%d_x%d_n%d_c%d", dg.ndim, dg.Nz, dg.Ny, dg.Nx, dg.P1,
+             dg.count);
+    Args a = make_args<float>(p, dg, p->B32[0], p->B32[1], p->d_st);
+    a.pred = P_ALL;
+    if (dg.ndim == 1) {
+      dg.w1c = pick_width(p, std::string("col1_") + base, [&](int w) {
+        Args b = a;
+        col1_args<float>(p, b, dg, OP1_SCLIP);
+        b.mode = 0;
+        launch_col1<float>(dg.P1, w, b, dg.P2, dg.count, s);
+      });
+      dg.w1r = pick_width(p, std::string("row1_") + base, [&](int w) {
+        Args b = a;
+        row1_args<float>(p, b, dg, OP1_FWD);
+        launch_row1<float>(dg.P2, w, b, dg.P1, dg.count, s);
+      });
+      continue;
+    }
+    dg.wx = pick_width(p, std::string("px_") + base, [&](int w) {
+      Args b = a;
+      tabs_x<float>(p, b, dg);
+      b.mode = 0;
+      launch_x<float>(XPX, dg.M, w, b, dg.rows, dg.count, s);
+    });
+    if (dg.ndim == 3)
+      dg.wa = pick_width(p, std::string("axis_") + base, [&](int w) {
+        Args b = a;
+        b.tw = tw_of<float>(p->tb, dg.Ny);
+        launch_axis<float, -1>(dg.Ny, w, b, dg.Nz, dg.M, dg.count, s);
+      });
+    dg.wc = pick_width(p, std::string("chk_") + base, [&](int w) {
+      Args b = a;
+      b.tw = tw_of<float>(p->tb, dg.Nz);
+      b.mode = 0;
+      launch_chk<float>(dg.Nz, w, b, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+    });
+  }
+  CK(cudaMemsetAsync(p->d_st, 0, sizeof(ItemState) * p->batch, s));
+  CK(cudaStreamSynchronize(s));
 }
 
 }  // namespace
@@ -1303,26 +1442,31 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       dg.g.soff = d_so;
       p->groups.push_back(dg);
     }
-    // Set the shared-memory attributes of every kernel the plan can launch.
+    // Set the shared-memory attributes of every kernel the plan can launch
+    // (both float32 tile widths).
     g_dry = true;
     try {
       Args a{};
-      for (auto& dg : p->groups) {
-        if (ndim == 1) {
-          launch_col1<float>(dg.P1, a, dg.P2, 1, nullptr);
-          launch_col1<double>(dg.P1, a, dg.P2, 1, nullptr);
-          launch_row1<float>(dg.P2, a, dg.P1, 1, nullptr);
-          launch_row1<double>(dg.P2, a, dg.P1, 1, nullptr);
-          continue;
+      for (const auto& dg0 : p->groups) {
+        for (int w : {4, 8}) {
+          DevGroup dg = dg0;
+          dg.wx = dg.wa = dg.wc = dg.w1c = dg.w1r = w;
+          if (ndim == 1) {
+            launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, 1, nullptr);
+            launch_col1<double>(dg.P1, dg.w1c, a, dg.P2, 1, nullptr);
+            launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, 1, nullptr);
+            launch_row1<double>(dg.P2, dg.w1r, a, dg.P1, 1, nullptr);
+            continue;
+          }
+          launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, nullptr);
+          launch_x<double>(XFWD, dg.M, dg.wx, a, dg.rows, 1, nullptr);
+          launch_axis<float, -1>(dg.Ny < 8 ? 8 : dg.Ny, dg.wa, a, 1, dg.M, 1, nullptr);
+          launch_axis<float, +1>(dg.Ny < 8 ? 8 : dg.Ny, dg.wa, a, 1, dg.M, 1, nullptr);
+          launch_axis<double, -1>(dg.Ny < 8 ? 8 : dg.Ny, dg.wa, a, 1, dg.M, 1, nullptr);
+          launch_axis<double, +1>(dg.Ny < 8 ? 8 : dg.Ny, dg.wa, a, 1, dg.M, 1, nullptr);
+          launch_chk<float>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
+          launch_chk<double>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
         }
-        launch_x<float>(XFWD, dg.M, a, dg.rows, 1, nullptr);
-        launch_x<double>(XFWD, dg.M, a, dg.rows, 1, nullptr);
-        launch_axis<float, -1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
-        launch_axis<float, +1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
-        launch_axis<double, -1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
-        launch_axis<double, +1>(dg.Ny < 8 ? 8 : dg.Ny, a, 1, dg.M, 1, nullptr);
-        launch_chk<float>(dg.Nz, a, dg.Ny, dg.M, 1, nullptr);
-        launch_chk<double>(dg.Nz, a, dg.Ny, dg.M, 1, nullptr);
       }
     } catch (...) {
       g_dry = false;
@@ -1341,14 +1485,18 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     CK(cudaMallocHost(&p->h_nactive, sizeof(int)));
     CK(cudaMallocHost(&p->h_st, sizeof(ItemState) * batch));
     CK(cudaMallocHost(&p->h_prm, sizeof(ItemParams) * batch));
-    if (ndim == 1) {
-      // FFT of the wrapped chirp of every item (float32 now, float64 on first
-      // certification); the bounds are placeholders here
+    {
+      // placeholder bounds for the set-up launches below
       std::vector<double> one(batch, 1.0);
       upload_params(p.get(), one.data(), one.data(), 0, 0);
+    }
+    if (ndim == 1) {
+      // chirp tables and FFT of the wrapped chirp of every item (float32 now,
+      // float64 on first use)
       build_bt<float>(p.get());
       CK(cudaStreamSynchronize(p->stream));
     }
+    tune(p.get());   // tile widths only regroup pencils: Bt and the tables are unchanged
     *out = p.release();
     return FFCZ_OK;
   });

@@ -144,9 +144,9 @@ struct Sched {
 __host__ __device__ constexpr int pidx(int l) { return l + (l >> 3); }
 
 // A thread's view of its pencil in two ping-pong tile buffers.
-template <typename T, int L>
+template <typename T, int L, int W_ = TileW<T>::value>
 struct Tile {
-  static constexpr int W = TileW<T>::value;
+  static constexpr int W = W_;
   static constexpr int ROWS = L + L / 8;
   static constexpr int ELEMS = ROWS * W;   // one buffer
   v2<T>* p0;  // buffer used by even exchanges (+ w)
@@ -172,11 +172,11 @@ __device__ __forceinline__ int nat(int jb, int j, int u) {
 // exp(DIR 2 pi i k t/(R NS)), k = j' mod NS, and the R-point DFT, output t
 // goes to row (j'/NS)*R*NS + k + t*NS.  The last stage keeps the outputs in
 // registers: they are then x[j + u*L/8] again.
-template <typename T, int L, int DIR, int S>
+template <typename T, int L, int DIR, int S, class TL>
 __device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, int jb,
-                                               const v2<T>* __restrict__ tw, Tile<T, L>& tl) {
+                                               const v2<T>* __restrict__ tw, TL& tl) {
   using SC = Sched<L>;
-  constexpr int R = SC::radix(S), NS = SC::ns(S), NT = L / 8, NB = 8 / R, W = Tile<T, L>::W;
+  constexpr int R = SC::radix(S), NS = SC::ns(S), NT = L / 8, NB = 8 / R, W = TL::W;
   constexpr bool last = (S == SC::nst - 1);
   v2<T>* dst = tl.buf();
 #pragma unroll
@@ -231,31 +231,31 @@ __device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, int jb,
   }
 }
 
-template <typename T, int L, int DIR, int S>
+template <typename T, int L, int DIR, int S, class TL>
 __device__ __forceinline__ void stages_from(v2<T> (&v)[8], int j, int jb, const v2<T>* __restrict__ tw,
-                                            Tile<T, L>& tl) {
+                                            TL& tl) {
   if constexpr (S < Sched<L>::nst) {
-    stockham_stage<T, L, DIR, S>(v, j, jb, tw, tl);
-    stages_from<T, L, DIR, S + 1>(v, j, jb, tw, tl);
+    stockham_stage<T, L, DIR, S, TL>(v, j, jb, tw, tl);
+    stages_from<T, L, DIR, S + 1, TL>(v, j, jb, tw, tl);
   }
 }
 
 // Full length-L transform of the thread's pencil.  Every thread of the CTA
 // must call it (it synchronises the block between stages).  `jb` is
 // pidx(j) (precomputed by the caller).
-template <typename T, int L, int DIR>
+template <typename T, int L, int DIR, class TL>
 __device__ __forceinline__ void fft_pencil(v2<T> (&v)[8], int j, int jb, const v2<T>* __restrict__ tw,
-                                           Tile<T, L>& tl) {
+                                           TL& tl) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "L must be a power of two >= 8");
-  stages_from<T, L, DIR, 0>(v, j, jb, tw, tl);
+  stages_from<T, L, DIR, 0, TL>(v, j, jb, tw, tl);
 }
 
 // Exchange: every thread stores its natural-order registers, the block
 // synchronises, and `f(l)` below reads other rows; afterwards the buffers
 // flip.  Used where an elementwise step needs X[-k] next to X[k].
-template <typename T, int L>
-__device__ __forceinline__ void store_nat(const v2<T> (&v)[8], int j, int jb, Tile<T, L>& tl) {
-  constexpr int NT = L / 8, W = Tile<T, L>::W;
+template <typename T, int L, class TL>
+__device__ __forceinline__ void store_nat(const v2<T> (&v)[8], int j, int jb, TL& tl) {
+  constexpr int NT = L / 8, W = TL::W;
   v2<T>* dst = tl.buf();
 #pragma unroll
   for (int u = 0; u < 8; ++u) dst[nat<NT>(jb, j, u) * W] = v[u];

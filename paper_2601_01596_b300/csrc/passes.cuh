@@ -37,11 +37,10 @@ struct ItemParams {
   float Esf, Dsf, thrf, inv_nf;      // the same in float32
   int64_t n;                         // points
   int32_t min_iters, max_iters;
-  // 1D items (Bluestein): 1/(P N), (P/8)^2 mod 2N, log2 P (0 for 2D/3D items)
+  // 1D items (Bluestein): 1/(P N) and log2 P (0 for 2D/3D items)
   double inv_pn;
   float inv_pnf;
   int32_t logP;
-  uint64_t dd2N;
 };
 
 struct ItemState {
@@ -86,6 +85,7 @@ struct Args {
   const void* tw;          // Stockham stage factors for the pass length
   const void* twr;         // exp(-2 pi i k / Nx), k < M (x passes); exp(-2 pi i m / P) (1D)
   const void* bt;          // 1D: FFT of the wrapped chirp, [k1][k2] order, per item at soff
+  const void* chirp;       // 1D: chirps b_n, n < N, per item at eoff
   int op1;                 // 1D pass operation (Op1)
 };
 
@@ -110,9 +110,9 @@ __device__ __forceinline__ v2<T>* pick(const Args& a, int sel, int t) {
 }
 
 // Per-tile launch geometry, shared by host and device.
-template <typename T, int L>
+template <typename T, int L, int W_ = TileW<T>::value>
 struct Geo {
-  static constexpr int W = TileW<T>::value;            // pencils per tile
+  static constexpr int W = W_;                         // pencils per tile
   static constexpr int NT = L / 8;                     // threads per pencil
   static constexpr int TPT = NT * W;                   // threads per tile
   static constexpr int G = TPT >= 128 ? 1 : 128 / TPT; // tiles per CTA (>= 128 threads)
@@ -124,9 +124,9 @@ struct Geo {
 };
 
 // Shared-memory carve-up: [G tiles x 2 buffers][stage twiddles][R2C twiddles][reduction].
-template <typename T, int L>
+template <typename T, int L, int W = TileW<T>::value>
 struct Smem {
-  static constexpr size_t tiles = (size_t)Geo<T, L>::G * 2 * Tile<T, L>::ELEMS * sizeof(v2<T>);
+  static constexpr size_t tiles = (size_t)Geo<T, L, W>::G * 2 * Tile<T, L, W>::ELEMS * sizeof(v2<T>);
   static constexpr size_t tw = (size_t)Sched<L>::twsize * sizeof(v2<T>);
   static constexpr size_t twr = (size_t)L * sizeof(v2<T>);
   static constexpr size_t red = 32 * 8 * 3 + 32 * 4;
@@ -231,11 +231,11 @@ __device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int ntw
 
 // Post-processing of Z = FFT_M(z) into the packed half spectrum P (in place
 // in registers).  Needs Z[M-k], fetched through one shared-memory exchange.
-template <typename T, int M>
-__device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, int jb, Tile<T, M>& tl,
+template <typename T, int M, class TL>
+__device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, int jb, TL& tl,
                                          const v2<T>* __restrict__ twr) {
   constexpr int NT = M / 8;
-  store_nat<T, M>(v, j, jb, tl);
+  store_nat<T, M, TL>(v, j, jb, tl);
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int k = j + u * NT;
@@ -255,11 +255,11 @@ __device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, int jb, Tile<T, M
 
 // Pre-processing of packed P into Z' = 2 Z so that IFFT_M(Z') / Nx gives
 // the real row (again one exchange for P[M-k]).
-template <typename T, int M>
-__device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, Tile<T, M>& tl,
+template <typename T, int M, class TL>
+__device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, TL& tl,
                                         const v2<T>* __restrict__ twr) {
   constexpr int NT = M / 8;
-  store_nat<T, M>(v, j, jb, tl);
+  store_nat<T, M, TL>(v, j, jb, tl);
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int k = j + u * NT;
@@ -277,9 +277,9 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, Tile<T, M>
   tl.flip();
 }
 
-#define FFCZ_X_PROLOGUE(T_, M_)                                                   \
-  using G_ = Geo<T_, M_>;                                                         \
-  using TL = Tile<T_, M_>;                                                        \
+#define FFCZ_X_PROLOGUE(T_, M_, W_)                                               \
+  using G_ = Geo<T_, M_, W_>;                                                     \
+  using TL = Tile<T_, M_, W_>;                                                    \
   extern __shared__ __align__(16) unsigned char smraw[];                          \
   v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
   v2<T_>* s_tw = s_tiles + G_::G * 2 * TL::ELEMS;                                \
@@ -301,10 +301,10 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, Tile<T, M>
   (void)t_it;
 
 // Entry / certification x pass: float32 real rows -> packed spectrum.
-template <typename T, int M>
-__global__ void __launch_bounds__(Geo<T, M>::NTHR, Geo<T, M>::MINB)
+template <typename T, int M, int W = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xfwd(Args a) {
-  FFCZ_X_PROLOGUE(T, M)
+  FFCZ_X_PROLOGUE(T, M, W)
   const float* src = (a.mode & M_MASK) ? a.ein : a.e;
   const float2* erow = reinterpret_cast<const float2*>(src + a.g.eoff[gi]) + row * M;
   float2* erow_w = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
@@ -377,12 +377,12 @@ __device__ __forceinline__ void s_clip_full(v2<T> (&v)[8], T Es, bool count, uin
 
 // Loop body x pass on one tile held in registers: C2R, scale 1/N, s-clip
 // (or adjoint mask), R2C.  Returns the active-clip count of the thread.
-template <typename T, int M>
+template <typename T, int M, class TL>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[8],
                                                       int j, int jb, int tid, int tile, int row, bool live,
-                                                      int t_it, Tile<T, M>& tl, const v2<T>* twg,
+                                                      int t_it, TL& tl, const v2<T>* twg,
                                                       const v2<T>* twr) {
-  using G_ = Geo<T, M>;
+  using G_ = Geo<T, M, TL::W>;
   c2r_pre<T, M>(v, j, jb, tl, twr);
   fft_pencil<T, M, +1>(v, j, jb, twg, tl);
   unsigned long long cnt = 0;
@@ -424,16 +424,16 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
   return live ? cnt : 0ull;
 }
 
-template <typename T, int M>
-__global__ void __launch_bounds__(Geo<T, M>::NTHR, Geo<T, M>::MINB)
+template <typename T, int M, int W = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_px(Args a) {
-  FFCZ_X_PROLOGUE(T, M)
+  FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) v[u] = in[j + u * G_::NT];
   load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
-  unsigned long long cnt = px_core<T, M>(a, p, v, j, jb, tid, tile, row, live, t_it, tl, s_tw, s_twr);
+  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, jb, tid, tile, row, live, t_it, tl, s_tw, s_twr);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
@@ -449,10 +449,10 @@ k_px(Args a) {
 // Exit x pass: C2R, scale 1/N, s-clip, store float32 e (rebuilds the iterate
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
 // no clip is applied.  With M_COUNT it counts the final iterate's s-clips.
-template <typename T, int M>
-__global__ void __launch_bounds__(Geo<T, M>::NTHR, Geo<T, M>::MINB)
+template <typename T, int M, int W = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xexit(Args a) {
-  FFCZ_X_PROLOGUE(T, M)
+  FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[8];
 #pragma unroll
@@ -482,9 +482,9 @@ k_xexit(Args a) {
 // Strided axis passes
 // ---------------------------------------------------------------------------
 
-#define FFCZ_AXIS_PROLOGUE(T_, L_)                                                \
-  using G_ = Geo<T_, L_>;                                                         \
-  using TL = Tile<T_, L_>;                                                        \
+#define FFCZ_AXIS_PROLOGUE(T_, L_, W_)                                            \
+  using G_ = Geo<T_, L_, W_>;                                                     \
+  using TL = Tile<T_, L_, W_>;                                                    \
   extern __shared__ __align__(16) unsigned char smraw[];                          \
   v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
   v2<T_>* s_tw = s_tiles + G_::G * 2 * TL::ELEMS;                                \
@@ -503,10 +503,10 @@ k_xexit(Args a) {
   TL tl{s_tiles + g * 2 * TL::ELEMS + w, s_tiles + g * 2 * TL::ELEMS + TL::ELEMS + w, 0};
 
 // Plain C2C along the middle axis of a 3D item (y): pencils at fixed (z, kx).
-template <typename T, int L, int DIR>
-__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+template <typename T, int L, int DIR, int W = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W>::NTHR, Geo<T, L, W>::MINB)
 k_axis(Args a) {
-  FFCZ_AXIS_PROLOGUE(T, L)
+  FFCZ_AXIS_PROLOGUE(T, L, W)
   const int M = a.g.M;
   const unsigned tpr = (unsigned)(M / G_::W);     // tiles per z-plane
   const int ntiles = a.g.Nz * (int)tpr;
@@ -582,12 +582,12 @@ __host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
 
 // Everything of the check pass between load and store for one tile in
 // registers.  cta_has_mirror must be uniform over the CTA.
-template <typename T, int L>
+template <typename T, int L, class TL>
 __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st, v2<T> (&v)[8],
                                          int j, int jb, int w, int tid, int tile, const ChkTile& c,
-                                         bool cta_has_mirror, Tile<T, L>& tl, const v2<T>* twg,
+                                         bool cta_has_mirror, TL& tl, const v2<T>* twg,
                                          unsigned long long* s_red) {
-  using G_ = Geo<T, L>;
+  using G_ = Geo<T, L, TL::W>;
   constexpr int NT = G_::NT;
   fft_pencil<T, L, -1>(v, j, jb, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
@@ -599,7 +599,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   const bool clip = (a.mode & M_CLIP) != 0, count = (a.mode & M_COUNT) != 0;
   if (use_mask && c.live) bits = a.mask[tile * G_::TPT + tid];
   if (cta_has_mirror) {
-    store_nat<T, L>(v, j, jb, tl);
+    store_nat<T, L, TL>(v, j, jb, tl);
     if (c.mirror) {
       const int dw = (w ^ 1) - w;
 #pragma unroll
@@ -682,10 +682,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 // of middle indices so that A and B can be separated; a pencil that is its
 // own mirror (m = 0 or Nmid/2) fills both slots of its pair and only the
 // first slot stores.
-template <typename T, int L>
-__global__ void __launch_bounds__(Geo<T, L>::NTHR, Geo<T, L>::MINB)
+template <typename T, int L, int W_ = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
 k_chk(Args a) {
-  FFCZ_AXIS_PROLOGUE(T, L)
+  FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int W = G_::W, NT = G_::NT;
   const int M = a.g.M, Nmid = a.g.Nmid;
   const ChkTile c = chk_decode<W>(tile, w, M, Nmid);
@@ -700,7 +700,7 @@ k_chk(Args a) {
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
-  chk_core<T, L>(a, p, st, v, j, jb, w, tid, tile, c, cta_has_mirror, tl, s_tw, s_red);
+  chk_core<T, L, TL>(a, p, st, v, j, jb, w, tid, tile, c, cta_has_mirror, tl, s_tw, s_red);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
