@@ -39,6 +39,15 @@ from paper_2601_01596_b300 import workloads as W  # noqa: E402
 METRIC = "field GB/s to certified feasibility, 512^3 fp32; % HBM roofline/iteration"
 FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
 
+# DRAM bytes (read + write) per launch from one ncu capture of these kernels
+# at 512^3 (profiles/); a kernel changed since its capture must be removed.
+NCU_TRAFFIC = {
+    "xfwd<f64,256>": 537027072 + 1016915000,
+    "chk<f32,512>": 565569536 + 506454272,
+    "px<f32,256>": 536921856 + 480724736,
+}
+NCU_FP64_PIPE = {"xfwd<f64,256>": 0.854}
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -415,7 +424,9 @@ def main():
                 "achieved": round(top_flops / (top_avg / 1e3) / 1e12, 4),
                 "peak": FP64_TFLOPS, "unit": "TFLOP/s (FP64)",
                 "frac": round(top_flops / (top_avg / 1e3) / 1e12 / FP64_TFLOPS, 4),
-                "traffic": None, "peak_kind": "nominal FP64 (no measured FP64 peak)",
+                "traffic": NCU_TRAFFIC.get(top_key) if n == 512 ** 3 else None,
+                "fp64_pipe_active_ncu": NCU_FP64_PIPE.get(top_key) if n == 512 ** 3 else None,
+                "peak_kind": "nominal FP64 (no measured FP64 peak)",
                 "avg_launch_ms": round(top_avg, 4), "algorithmic_flops": top_flops,
                 "algorithmic_bytes": top_bytes,
                 "achieved_GBps": round(top_bytes / (top_avg / 1e3) / 1e9, 1),
@@ -424,7 +435,8 @@ def main():
         roof = {"bound": "hbm", "kernel": top_key,
                 "achieved": round(top_bytes / (top_avg / 1e3) / 1e9, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(top_bytes / (top_avg / 1e3) / 1e9 / hbm, 4),
-                "traffic": None, "peak_kind": peak_kind, "avg_launch_ms": round(top_avg, 4),
+                "traffic": NCU_TRAFFIC.get(top_key) if n == 512 ** 3 else None,
+                "peak_kind": peak_kind, "avg_launch_ms": round(top_avg, 4),
                 "algorithmic_bytes": top_bytes,
                 "share_of_step": round(top_ms / tot, 3) if tot else None}
 
