@@ -66,7 +66,10 @@ typedef struct {
   int32_t K;           /* backward: number of forced forward iterations; 50 */
   int32_t ckpt_every;  /* backward: checkpoint interval m; 10 */
   int32_t chunk;       /* max iterations launched between host checks; 16 */
-  int32_t use_graph;   /* 1 (default): replay loop chunks as CUDA graphs */
+  int32_t use_graph;   /* 0: direct launches, host checks between chunks;
+                          1: chunks replayed as CUDA graphs, host checks between;
+                          2 (default): the whole loop on the device, one graph
+                          with a conditional WHILE node (no host round trip) */
   int32_t count_active;/* 1 (default): count active clips for ffcz_stats */
 } ffcz_opts;
 

@@ -168,9 +168,15 @@ struct ffcz_plan_s {
   size_t ws_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
 
-  // graphs of loop chunks: key = (precision, chunk)
+  // graphs of loop chunks: key = (precision, chunk); the device-side WHILE
+  // loop graph: key = (-precision, 0)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   std::map<std::pair<int, int>, int> graph_nodes;
+  int* d_loopcount = nullptr;   // bodies executed by the WHILE graph
+  int* h_loopcount = nullptr;   // pinned copy
+  bool count_pending = false;
+  int while_cap[2] = {-1, -1};
+  int pending_bodies_per = 0;
 
   // per-kernel profile (events around every launch; graphs off while on)
   bool prof = false;
@@ -682,6 +688,64 @@ LoopBufs loop_bufs(ffcz_plan_s* p) {
   return {p->B64[0], p->B64[1]};
 }
 
+// Loop control inside a graph: counts executed bodies and keeps the WHILE
+// node running while some item is active and the cap is not reached.
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, const int* n_active, int* count, int cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int c = *count + 1;
+  *count = c;
+  cudaGraphSetConditional(h, (*n_active > 0 && c < cap) ? 1u : 0u);
+}
+
+// Whole loop on the device: a graph with one conditional WHILE node whose
+// body is one captured iteration followed by k_loop_ctl (built once per plan
+// and precision, replayed by one cudaGraphLaunch per call).
+template <typename T>
+void run_while_graph(ffcz_plan_s* p, LoopBufs B, int cap) {
+  const auto key = std::make_pair(-(int)sizeof(T), 0);
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    const int64_t before = g_launches.load();
+    CK(cudaStreamBeginCaptureToGraph(p->cap_stream, bodyg, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    try {
+      body<T>(p, B, p->cap_stream);
+      k_loop_ctl<<<1, 32, 0, p->cap_stream>>>(h, p->d_nactive, p->d_loopcount, cap);
+    } catch (...) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(p->cap_stream, &junk);
+      cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraph_t captured = nullptr;
+    CK(cudaStreamEndCapture(p->cap_stream, &captured));
+    const int per_body = (int)(g_launches.load() - before) + 1;
+    g_launches -= (g_launches.load() - before);
+    cudaGraphExec_t ge;
+    CK(cudaGraphInstantiate(&ge, g, 0));
+    cudaGraphDestroy(g);
+    it = p->graphs.emplace(key, ge).first;
+    p->graph_nodes[key] = per_body;
+    p->while_cap[sizeof(T) == 4 ? 0 : 1] = cap;
+  }
+  CK(cudaMemsetAsync(p->d_loopcount, 0, sizeof(int), p->stream));
+  CK(cudaGraphLaunch(it->second, p->stream));
+  // kernels per executed body; the count read back with the stats
+  p->pending_bodies_per = p->graph_nodes[key];
+}
+
 template <typename T>
 void run_chunk(ffcz_plan_s* p, LoopBufs B, int C) {
   if (!p->opts.use_graph || p->prof) {
@@ -766,14 +830,30 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
                                                                    only_uncert ? 1 : 0, p->d_nactive);
   g_launches++;
   entry<T>(p, B, e, !only_uncert, p->stream);
-  int chunk = 1, launched = 0;
-  const int cmax = std::max(1, p->opts.chunk);
   const int cap = p->h_prm[0].max_iters;   // no item iterates past it
-  while (launched < cap && read_active(p) > 0) {
-    const int c = std::min(chunk, cap - launched);
-    run_chunk<T>(p, B, c);
-    launched += c;
-    chunk = std::min(chunk * 2, cmax);
+  if (p->opts.use_graph == 2 && !p->prof && cap > 0) {
+    // the whole loop on the device (conditional WHILE node); graphs are
+    // rebuilt when the cap changes
+    const int slot = sizeof(T) == 4 ? 0 : 1;
+    const auto key = std::make_pair(-(int)sizeof(T), 0);
+    if (p->while_cap[slot] != cap && p->graphs.count(key)) {
+      cudaGraphExecDestroy(p->graphs[key]);
+      p->graphs.erase(key);
+    }
+    run_while_graph<T>(p, B, cap);
+    // the executed-body count is read with the stats at the end of the call
+    // (launch accounting only)
+    CK(cudaMemcpyAsync(p->h_loopcount, p->d_loopcount, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    p->count_pending = true;
+  } else {
+    int chunk = 1, launched = 0;
+    const int cmax = std::max(1, p->opts.chunk);
+    while (launched < cap && read_active(p) > 0) {
+      const int c = std::min(chunk, cap - launched);
+      run_chunk<T>(p, B, c);
+      launched += c;
+      chunk = std::min(chunk * 2, cmax);
+    }
   }
   exit_pass<T>(p, B, e, p->stream);
 }
@@ -841,6 +921,10 @@ void fill_stats(ffcz_plan_s* p, ffcz_stats* out, float ms, float ms_cert, bool c
   CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(ItemState) * p->batch, cudaMemcpyDeviceToHost,
                      p->stream));
   CK(cudaStreamSynchronize(p->stream));
+  if (p->count_pending) {
+    g_launches += (int64_t)(*p->h_loopcount) * p->pending_bodies_per;
+    p->count_pending = false;
+  }
   if (!out) return;
   for (int64_t i = 0; i < p->batch; ++i) {
     const ItemState& s = p->h_st[i];
@@ -898,6 +982,7 @@ void free_plan(ffcz_plan_s* p) {
   for (auto e : p->evpool) cudaEventDestroy(e);
   for (void* a : p->allocs) cudaFree(a);
   if (p->h_nactive) cudaFreeHost(p->h_nactive);
+  if (p->h_loopcount) cudaFreeHost(p->h_loopcount);
   if (p->h_st) cudaFreeHost(p->h_st);
   if (p->h_prm) cudaFreeHost(p->h_prm);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -1296,7 +1381,7 @@ void ffcz_default_opts(ffcz_opts* o) {
   o->K = 50;
   o->ckpt_every = 10;
   o->chunk = 16;
-  o->use_graph = 1;
+  o->use_graph = 2;
   o->count_active = 1;
 }
 
@@ -1480,9 +1565,11 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->d_st = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
+    p->d_loopcount = (int*)dalloc(p.get(), sizeof(int));
     CK(cudaMemset(p->d_st, 0, sizeof(ItemState) * batch));
     CK(cudaMemset(p->d_st2, 0, sizeof(ItemState) * batch));
     CK(cudaMallocHost(&p->h_nactive, sizeof(int)));
+    CK(cudaMallocHost(&p->h_loopcount, sizeof(int)));
     CK(cudaMallocHost(&p->h_st, sizeof(ItemState) * batch));
     CK(cudaMallocHost(&p->h_prm, sizeof(ItemParams) * batch));
     {

@@ -215,8 +215,15 @@ def test_host_buffer_entry_point_matches_device():
     assert np.array_equal(host, dev)
 
 
-def test_graph_and_direct_launch_agree():
-    e0, E, D = stress((32, 32, 32), 41)
-    a, sa = run_gpu(e0, E, D, use_graph=1)
-    b, sb = run_gpu(e0, E, D, use_graph=0)
-    assert sa[0]["iters"] == sb[0]["iters"] and np.array_equal(a, b)
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128)])
+def test_device_loop_graph_chunk_graphs_and_direct_launch_agree(shape):
+    e0, E, D = stress(shape, 41)
+    a, sa = run_gpu(e0, E, D, use_graph=2)     # conditional WHILE node
+    b, sb = run_gpu(e0, E, D, use_graph=1)     # chunk graphs, host checks
+    c, sc = run_gpu(e0, E, D, use_graph=0)     # direct launches
+    assert sa[0]["iters"] == sb[0]["iters"] == sc[0]["iters"] >= 2
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    # caps inside the device loop
+    d, sd = run_gpu(e0, E, D, use_graph=2, max_iters=1)
+    import paper_2601_01596_b300 as ffcz
+    assert sd[0]["iters"] == 1 and sd[0]["status"] == ffcz.ERR_NOT_CONVERGED
