@@ -27,6 +27,7 @@ import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -73,18 +74,60 @@ def make_workload(name):
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """SM clocks and throttle reasons sampled DURING a region (read-only).
+
+    NVML is polled from a thread every 10 ms, so even a region of a few tens of
+    milliseconds gets samples; without NVML, nvidia-smi is polled at 200 ms.
+    """
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, dev):
         self.dev = dev
         self.proc = None
-        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.thread = None
+        self.samples = []
+        self.stop_evt = threading.Event()
+        self.nvml = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            # the CUDA ordinal of this process maps to the NVML index through
+            # CUDA_VISIBLE_DEVICES when it is set
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            idx = dev
+            if vis:
+                ids = [x.strip() for x in vis.split(",") if x.strip()]
+                if dev < len(ids) and ids[dev].isdigit():
+                    idx = int(ids[dev])
+            self.handle = pynvml.nvmlDeviceGetHandleByIndex(idx)
+            self.nvml = pynvml
+        except Exception:
+            self.nvml = None
+
+    def _poll(self):
+        n = self.nvml
+        bits = [n.nvmlClocksEventReasonHwSlowdown, n.nvmlClocksEventReasonHwThermalSlowdown,
+                n.nvmlClocksEventReasonSwThermalSlowdown, n.nvmlClocksEventReasonSwPowerCap]
+        while not self.stop_evt.is_set():
+            try:
+                sm = n.nvmlDeviceGetClockInfo(self.handle, n.NVML_CLOCK_SM)
+                smax = n.nvmlDeviceGetMaxClockInfo(self.handle, n.NVML_CLOCK_SM)
+                r = n.nvmlDeviceGetCurrentClocksEventReasons(self.handle)
+                self.samples.append((float(sm), float(smax), [nm for nm, b in zip(self.NAMES, bits) if r & b]))
+            except Exception:
+                pass
+            self.stop_evt.wait(0.01)
 
     def start(self):
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
@@ -94,6 +137,15 @@ class Clocks:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_evt.set()
+            self.thread.join(timeout=5)
+            sm = [x[0] for x in self.samples]
+            smax = [x[1] for x in self.samples]
+            reasons = sorted({r for x in self.samples for r in x[2]})
+            return {"sm_mhz": float(np.median(sm)) if sm else None,
+                    "sm_max_mhz": max(smax) if smax else None,
+                    "reasons": reasons, "samples": len(sm), "source": "nvml"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -102,7 +154,6 @@ class Clocks:
         rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
         os.unlink(self.f.name)
         sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             r = [x.strip() for x in r]
             try:
@@ -110,12 +161,12 @@ class Clocks:
                 smax.append(float(r[2]))
             except (ValueError, IndexError):
                 continue
-            for n, v in zip(names, r[5:9]):
+            for nm, v in zip(self.NAMES, r[5:9]):
                 if v.lower().startswith("active"):
-                    reasons.add(n)
+                    reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -321,7 +372,7 @@ def measure_forms(ffcz, torch, fin, it, hbm):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffcz", choices=["ffcz", "reference"])
     ap.add_argument("--workload", default="lognormal512")

@@ -64,6 +64,7 @@ __global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab) {
 }
 
 // Column pass along n1 / k1 (length P1 = L), tile = W consecutive columns.
+// The chirp of each value is read from the item's table where it is used.
 template <typename T, int L, int W_ = TileW<T>::value>
 __global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
 k1_col(Args a) {
@@ -79,7 +80,12 @@ k1_col(Args a) {
   const int op = a.op1;
   const uint64_t m0 = (uint64_t)j * P2 + n2, D = (uint64_t)NT * P2;
   const int64_t Pn = (int64_t)L * P2;
-  v2<T> v[8];
+  const v2<T>* ctab = reinterpret_cast<const v2<T>*>(a.chirp) + a.g.eoff[gi];
+  auto chirp = [&](int u) -> v2<T> {   // b_n of value u (zero past N)
+    const int64_t n = (int64_t)m0 + (int64_t)u * D;
+    return (live && n < N) ? ctab[n] : mk<T>(T(0), T(0));
+  };
+  v2<T> v[V];
   AbsMax<T> mx;
   bool bad = false;
   float ssq = 0.f;
@@ -87,7 +93,7 @@ k1_col(Args a) {
   if (op == OP1_ENTRY) {
     float* src = a.e + a.g.eoff[gi];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < V; ++u) {
       const int64_t n = (int64_t)m0 + (int64_t)u * D;
       float x = (live && n < N) ? src[n] : 0.f;
       if (a.mode & M_MEASURE) {
@@ -106,32 +112,25 @@ k1_col(Args a) {
   } else if (op != OP1_FILTER) {
     const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + m0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
+    for (int u = 0; u < V; ++u) v[u] = in[u * ustride];
   }
-  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);
-  // chirps b_n of the thread's rows from the item's table (zero past N)
-  const v2<T>* ctab = reinterpret_cast<const v2<T>*>(a.chirp) + a.g.eoff[gi];
-  v2<T> b[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int64_t n = (int64_t)m0 + (int64_t)u * D;
-    b[u] = (live && n < N) ? ctab[n] : mk<T>(T(0), T(0));
-  }
+  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);
 
   if (op == OP1_FILTER) {
     // wrapped chirp: f[m] = b_m for m < N, f[m] = b_{P-m} for 0 < P - m < N
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < V; ++u) {
       const int64_t m = (int64_t)m0 + (int64_t)u * D, q = Pn - m;
       v2<T> f = mk<T>(T(0), T(0));
-      if (live && m < N) f = b[u];
+      if (live && m < N) f = ctab[m];
       else if (live && q < N) f = ctab[q];
       v[u] = f;
     }
   } else if (op == OP1_ENTRY) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = cmulc<T>(v[u], b[u]);   // a_n = x_n conj(b_n)
+    for (int u = 0; u < V; ++u) v[u] = cmulc<T>(v[u], chirp(u));   // a_n = x_n conj(b_n)
     if (a.mode & (M_MEASURE | M_PRECLIP)) {
+      // V <= 32 float32 squares: relative error of the sum < 2^-19
       Red rr{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-18) : 0.0, live ? cnt : 0ull};
       block_reduce(rr, s_red);
       if (threadIdx.x == 0) {
@@ -145,18 +144,19 @@ k1_col(Args a) {
   } else {
     // inverse column step: conj twiddle, IFFT along k1 -> c[n1][n2] * P
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = cmulc<T>(v[u], twp[(j + u * NT) * n2]);
-    fft_pencil<T, L, +1>(v, j, jb, s_tw, tl);
+    for (int u = 0; u < V; ++u) v[u] = cmulc<T>(v[u], twp[(j + u * NT) * n2]);
+    fft_pencil<T, L, +1>(v, j, s_tw, tl);
     const bool count = (a.mode & M_COUNT) != 0;
     if (op == OP1_FCLIP) {
       const T invP = T(1) / (T)Pn;   // exact: P is a power of two
       const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
       const bool clip = (a.mode & M_CLIP) != 0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < V; ++u) {
         const int64_t k = (int64_t)m0 + (int64_t)u * D;
         const bool in_range = live && k < N;
-        v2<T> X = cmulc<T>(v[u], b[u]);            // X_k = conj(b_k) c_k / P
+        const v2<T> bk = chirp(u);
+        v2<T> X = cmulc<T>(v[u], bk);            // X_k = conj(b_k) c_k / P
         X = mk<T>(X.x * invP, X.y * invP);
         if (in_range) { mx.add(X.x); mx.add(X.y); bad |= (X.x != X.x) | (X.y != X.y); }
         if (clip) {
@@ -164,7 +164,7 @@ k1_col(Args a) {
           if (count && in_range) cnt += (cx != X.x) + (cy != X.y);
           X = mk<T>(cx, cy);
         }
-        v[u] = in_range ? cmul<T>(X, b[u]) : mk<T>(T(0), T(0));   // pre: X'_k b_k
+        v[u] = in_range ? cmul<T>(X, bk) : mk<T>(T(0), T(0));   // pre: X'_k b_k
       }
       unsigned long long vb = mx.dbits(bad);
       block_max_count(vb, cnt, count, s_red);
@@ -178,10 +178,11 @@ k1_col(Args a) {
       const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
       float* eo = a.e + a.g.eoff[gi];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < V; ++u) {
         const int64_t n = (int64_t)m0 + (int64_t)u * D;
         const bool in_range = live && n < N;
-        T x = (b[u].x * v[u].x - b[u].y * v[u].y) * inv_pn;   // Re(b_n c'_n) / (P N)
+        const v2<T> bn = chirp(u);
+        T x = (bn.x * v[u].x - bn.y * v[u].y) * inv_pn;   // Re(b_n c'_n) / (P N)
         if (a.mode & M_CLIP) {
           const T cx = clampT(x, Es);
           if (count && in_range) cnt += (cx != x);
@@ -190,7 +191,7 @@ k1_col(Args a) {
         if (op == OP1_EXIT) {
           if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf) : (float)x;
         } else {
-          v[u] = in_range ? cmulc<T>(mk<T>(x, T(0)), b[u]) : mk<T>(T(0), T(0));   // x_n conj(b_n)
+          v[u] = in_range ? cmulc<T>(mk<T>(x, T(0)), bn) : mk<T>(T(0), T(0));   // x_n conj(b_n)
         }
       }
       if (op == OP1_EXIT) return;
@@ -202,11 +203,11 @@ k1_col(Args a) {
     }
   }
   // forward column step: FFT along n1, twiddle exp(-2 pi i n2 k1 / P)
-  fft_pencil<T, L, -1>(v, j, jb, s_tw, tl);
+  fft_pencil<T, L, -1>(v, j, s_tw, tl);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + m0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[u * ustride] = cmul<T>(v[u], twp[(j + u * NT) * n2]);
+    for (int u = 0; u < V; ++u) out[u * ustride] = cmul<T>(v[u], twp[(j + u * NT) * n2]);
   }
 }
 
@@ -217,28 +218,28 @@ k1_row(Args a) {
   FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int NT = G_::NT;
   const int P1 = a.g.Nz;
-  const int ntiles = P1 / G_::W;
-  const bool live = tile < ntiles;
-  const int row = live ? tile * G_::W + w : 0;
+  const int prow = tile * G_::W + w;
+  const bool live = prow < P1;
+  const int row = live ? prow : 0;
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + (int64_t)row * L + j;
-  v2<T> v[8];
+  v2<T> v[V];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = in[u * NT];
-  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);
-  fft_pencil<T, L, -1>(v, j, jb, s_tw, tl);
+  for (int u = 0; u < V; ++u) v[u] = in[u * NT];
+  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);
+  fft_pencil<T, L, -1>(v, j, s_tw, tl);
   if (a.op1 != OP1_FWD) {
     const v2<T>* bt = reinterpret_cast<const v2<T>*>(a.bt) + a.g.soff[gi] + (int64_t)row * L + j;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < V; ++u) {
       const v2<T> f = bt[u * NT];
       v[u] = a.op1 == OP1_CONVC ? cmulc<T>(v[u], f) : cmul<T>(v[u], f);
     }
-    fft_pencil<T, L, +1>(v, j, jb, s_tw, tl);
+    fft_pencil<T, L, +1>(v, j, s_tw, tl);
   }
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + (int64_t)row * L + j;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[u * NT] = v[u];
+    for (int u = 0; u < V; ++u) out[u * NT] = v[u];
   }
 }
 

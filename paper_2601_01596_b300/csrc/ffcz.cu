@@ -70,33 +70,16 @@ std::vector<v2<T>> r2c_table(int Nx) {
   return t;
 }
 
-// Per-stage Stockham factors in the layout of Sched<L> (see fft_core.cuh).
-template <typename T, int L>
-std::vector<v2<T>> stage_table() {
-  using SC = Sched<L>;
-  std::vector<v2<T>> t(SC::twsize);
-  for (auto& x : t) { x.x = 0; x.y = 0; }
-  for (int s = 1; s < SC::nst; ++s) {
-    const int R = SC::radix(s), NS = SC::ns(s), sp = SC::sp(s), off = SC::twoff(s);
-    for (int k = 0; k < NS; ++k)
-      for (int tt = 1; tt < R; ++tt) t[off + k * sp + tt - 1] = root<T>((long double)k * tt, (long double)R * NS);
-  }
-  return t;
-}
-
+// Stage-2 twiddles of the two-stage split of L (layout in fft_core.cuh):
+// entry k1 * R2 + t - 1 = exp(-2 pi i k1 t / L), k1 < R1, t = 1..R2-1.
 template <typename T>
 std::vector<v2<T>> stage_table_rt(int L) {
-  switch (L) {
-    case 8: return stage_table<T, 8>();
-    case 16: return stage_table<T, 16>();
-    case 32: return stage_table<T, 32>();
-    case 64: return stage_table<T, 64>();
-    case 128: return stage_table<T, 128>();
-    case 256: return stage_table<T, 256>();
-    case 512: return stage_table<T, 512>();
-    case 1024: return stage_table<T, 1024>();
-  }
-  return {};
+  const int R1 = f2_nt(L), R2 = L / R1;
+  std::vector<v2<T>> t(L);
+  for (auto& x : t) { x.x = 0; x.y = 0; }
+  for (int k1 = 0; k1 < R1; ++k1)
+    for (int tt = 1; tt < R2; ++tt) t[k1 * R2 + tt - 1] = root<T>((long double)k1 * tt, (long double)L);
+  return t;
 }
 
 struct DevGroup {
@@ -104,8 +87,10 @@ struct DevGroup {
   int count;
   int ndim, Nz, Ny, Nx, M;
   int64_t rows, n;
-  // float32 tile widths (pencils per tile) picked by the tuner per pass kind
-  int wx = 4, wa = 8, wc = 8, w1c = 8, w1r = 4;
+  // float32 tile widths (pencils per tile) picked by the tuner per pass kind:
+  // strided passes (y, chk, 1D column) 4 or 8; contiguous passes (x, 1D
+  // row) 32/NT or 64/NT (a tile of one or two warps); set at plan creation
+  int wx = 0, wa = 8, wc = 8, w1c = 8, w1r = 0;
   // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
   int P1 = 0, P2 = 0;
   const void* twp32 = nullptr;
@@ -113,7 +98,7 @@ struct DevGroup {
 };
 
 struct Tables {
-  // per power of two 2^p: Stockham stage factors (p = 3..10) and R2C
+  // per power of two 2^p: stage-2 twiddles (p = 3..10) and R2C
   // factors for Nx = 2^p (p = 4..11)
   void* f32[12] = {};
   void* f64[12] = {};
@@ -265,8 +250,9 @@ void prof_collect(ffcz_plan_s* p) {
 }
 
 // ----- kernel dispatch over the pencil length and the tile width -------------
-// float32 kernels exist with 4- and 8-pencil tiles (chosen per plan by the
-// tuner); float64 kernels use 4-pencil tiles.
+// Strided float32 kernels exist with 4- and 8-pencil tiles, contiguous ones
+// (rows along x, 1D rows) with tiles of one or two warps; the tuner picks per
+// plan.  float64 kernels use 4-pencil strided tiles and one-warp rows.
 enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
 
 #define FFCZ_DISPATCH_L(Lv, FN, ...)                                     \
@@ -282,10 +268,14 @@ enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
     default: fail(FFCZ_ERR_UNSUPPORTED, "transform length");              \
   }
 
+// Row-tile widths of a contiguous pass of length L: one warp, two warps.
+constexpr int row_w1(int L) { return 32 / (1 << (ilog2(L) / 2)) > 0 ? 32 / (1 << (ilog2(L) / 2)) : 1; }
+constexpr int row_w2(int L) { return 2 * row_w1(L); }
+
 template <typename T, int M, int W>
 void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
   using G_ = Geo<T, M, W>;
-  const int64_t tiles = rows / G_::W;
+  const int64_t tiles = (rows + G_::W - 1) / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, M, W>::bytes_x;
   if (g_dry) {
@@ -305,10 +295,10 @@ struct XL {
   template <int M>
   static void go(XKind kind, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-      if (w == 4) launch_x_tw<T, M, 4>(kind, a, rows, count, s);
-      else launch_x_tw<T, M, 8>(kind, a, rows, count, s);
+      if (w == row_w2(M)) launch_x_tw<T, M, row_w2(M)>(kind, a, rows, count, s);
+      else launch_x_tw<T, M, row_w1(M)>(kind, a, rows, count, s);
     } else {
-      launch_x_tw<T, M, 4>(kind, a, rows, count, s);
+      launch_x_tw<T, M, row_w1(M)>(kind, a, rows, count, s);
     }
   }
 };
@@ -409,7 +399,7 @@ void launch_col1(int L, int w, const Args& a, int P2, int count, cudaStream_t s)
 template <typename T, int L, int W>
 void launch_row1_tw(const Args& a, int P1, int count, cudaStream_t s) {
   using G_ = Geo<T, L, W>;
-  const int64_t tiles = P1 / G_::W;
+  const int64_t tiles = (P1 + G_::W - 1) / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L, W>::bytes_axis;
   if (g_dry) { set_smem(k1_row<T, L, W>, sm); return; }
@@ -422,10 +412,10 @@ struct R1L {
   template <int L>
   static void go(int w, const Args& a, int P1, int count, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-      if (w == 4) launch_row1_tw<T, L, 4>(a, P1, count, s);
-      else launch_row1_tw<T, L, 8>(a, P1, count, s);
+      if (w == row_w2(L)) launch_row1_tw<T, L, row_w2(L)>(a, P1, count, s);
+      else launch_row1_tw<T, L, row_w1(L)>(a, P1, count, s);
     } else {
-      launch_row1_tw<T, L, 4>(a, P1, count, s);
+      launch_row1_tw<T, L, row_w1(L)>(a, P1, count, s);
     }
   }
 };
@@ -434,18 +424,15 @@ void launch_row1(int L, int w, const Args& a, int P1, int count, cudaStream_t s)
   FFCZ_DISPATCH_L(L, R1L<T>::template go, w, a, P1, count, s)
 }
 
-// Words of mask storage one pass writes (one uint32 per thread of a live tile).
-template <typename T>
-int64_t x_words(int M, int64_t rows, int W) {
-  if (sizeof(T) == 8) W = 4;
-  return (rows / W) * (int64_t)(M / 8) * W;
+// Words of mask storage one float32 pass writes: MW words per thread of
+// every tile (tiles x threads per tile x words per thread).
+inline int64_t mask_words_per_thread(int L) { return (f2_v(L) + 7) / 8; }
+inline int64_t x_words(int M, int64_t rows, int W) {
+  const int64_t tiles = (rows + W - 1) / W;
+  return tiles * (int64_t)f2_nt(M) * W * mask_words_per_thread(M);
 }
-template <typename T>
-int64_t chkw(int L, int Nmid, int M, int W) {
-  if (sizeof(T) == 8) W = 4;
-  const int64_t nmain = (int64_t)Nmid * (M / W);
-  const int npairs = Nmid / 2 + 1;
-  return (nmain + (npairs + W / 2 - 1) / (W / 2)) * (int64_t)(L / 8) * W;
+inline int64_t chkw(int L, int Nmid, int M, int W) {
+  return (int64_t)chk_ntiles(W, M, Nmid) * f2_nt(L) * W * mask_words_per_thread(L);
 }
 
 // ----- argument construction ------------------------------------------------
@@ -1130,8 +1117,8 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
   if (p->bw_K != K || p->bw_m != m) {
-    p->px_words = x_words<float>(dg.M, dg.rows, dg.wx);
-    p->chk_words = chkw<float>(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc);
+    p->px_words = x_words(dg.M, dg.rows, dg.wx);
+    p->chk_words = chkw(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc);
     p->bw_e = (float*)dalloc(p, sizeof(float) * N);
     p->bw_ck = (float*)dalloc(p, sizeof(float) * N * nseg);
     p->bw_smask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->px_words * m);
@@ -1247,9 +1234,10 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
 namespace {
 
 // ----- tile-width tuner ----------------------------------------------------------
-// For every group and float32 pass kind, time the 4- and 8-pencil variants on
-// the plan's own buffers (three launches each after one warm-up, CUDA events)
-// and keep the faster.  Results can be cached in a text file named by
+// For every group and float32 pass kind, time the two tile widths of the
+// pass (strided passes: 4 and 8 pencils; contiguous passes: tiles of one and
+// two warps) on the plan's own buffers (three launches each after one
+// warm-up, CUDA events) and keep the faster.  Results can be cached in a text file named by
 // FFCZ_TUNE_CACHE (lines "key width"); FFCZ_TUNE=0 keeps the defaults.
 std::map<std::string, int>& tune_table() {
   static std::map<std::string, int> t;
@@ -1295,16 +1283,16 @@ float time_launches(ffcz_plan_s* p, F&& f) {
 }
 
 template <typename F>
-int pick_width(ffcz_plan_s* p, const std::string& key, F&& run_w) {
+int pick_width(ffcz_plan_s* p, const std::string& key, int wa, int wb, F&& run_w) {
   {
     std::lock_guard<std::mutex> lk(tune_mu());
     tune_load();
     auto it = tune_table().find(key);
-    if (it != tune_table().end()) return it->second;
+    if (it != tune_table().end() && (it->second == wa || it->second == wb)) return it->second;
   }
-  const float t4 = time_launches(p, [&] { run_w(4); });
-  const float t8 = time_launches(p, [&] { run_w(8); });
-  const int w = t4 < t8 ? 4 : 8;
+  const float ta = time_launches(p, [&] { run_w(wa); });
+  const float tb = time_launches(p, [&] { run_w(wb); });
+  const int w = ta <= tb ? wa : wb;
   std::lock_guard<std::mutex> lk(tune_mu());
   tune_store(key, w);
   return w;
@@ -1321,32 +1309,32 @@ void tune(ffcz_plan_s* p) {
     Args a = make_args<float>(p, dg, p->B32[0], p->B32[1], p->d_st);
     a.pred = P_ALL;
     if (dg.ndim == 1) {
-      dg.w1c = pick_width(p, std::string("col1_") + base, [&](int w) {
+      dg.w1c = pick_width(p, std::string("col1_") + base, 4, 8, [&](int w) {
         Args b = a;
         col1_args<float>(p, b, dg, OP1_SCLIP);
         b.mode = 0;
         launch_col1<float>(dg.P1, w, b, dg.P2, dg.count, s);
       });
-      dg.w1r = pick_width(p, std::string("row1_") + base, [&](int w) {
+      dg.w1r = pick_width(p, std::string("row1_") + base, row_w1(dg.P2), row_w2(dg.P2), [&](int w) {
         Args b = a;
         row1_args<float>(p, b, dg, OP1_FWD);
         launch_row1<float>(dg.P2, w, b, dg.P1, dg.count, s);
       });
       continue;
     }
-    dg.wx = pick_width(p, std::string("px_") + base, [&](int w) {
+    dg.wx = pick_width(p, std::string("px_") + base, row_w1(dg.M), row_w2(dg.M), [&](int w) {
       Args b = a;
       tabs_x<float>(p, b, dg);
       b.mode = 0;
       launch_x<float>(XPX, dg.M, w, b, dg.rows, dg.count, s);
     });
     if (dg.ndim == 3)
-      dg.wa = pick_width(p, std::string("axis_") + base, [&](int w) {
+      dg.wa = pick_width(p, std::string("axis_") + base, 4, 8, [&](int w) {
         Args b = a;
         b.tw = tw_of<float>(p->tb, dg.Ny);
         launch_axis<float, -1>(dg.Ny, w, b, dg.Nz, dg.M, dg.count, s);
       });
-    dg.wc = pick_width(p, std::string("chk_") + base, [&](int w) {
+    dg.wc = pick_width(p, std::string("chk_") + base, 4, 8, [&](int w) {
       Args b = a;
       b.tw = tw_of<float>(p->tb, dg.Nz);
       b.mode = 0;
@@ -1508,6 +1496,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         for (auto v : sh) dg.n *= v;
         dg.rows = dg.n / dg.Nx;
       }
+      dg.wx = row_w1(dg.M);
+      dg.w1r = row_w1(dg.M);
       std::vector<int32_t> it(ids.begin(), ids.end());
       std::vector<int64_t> eo, so;
       for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(soff_c[id]); }
@@ -1533,9 +1523,11 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     try {
       Args a{};
       for (const auto& dg0 : p->groups) {
-        for (int w : {4, 8}) {
+        for (int alt = 0; alt < 2; ++alt) {
           DevGroup dg = dg0;
-          dg.wx = dg.wa = dg.wc = dg.w1c = dg.w1r = w;
+          dg.wa = dg.wc = dg.w1c = alt ? 8 : 4;
+          dg.wx = alt ? row_w2(dg.M) : row_w1(dg.M);
+          dg.w1r = alt ? row_w2(dg.M) : row_w1(dg.M);
           if (ndim == 1) {
             launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, 1, nullptr);
             launch_col1<double>(dg.P1, dg.w1c, a, dg.P2, 1, nullptr);

@@ -1,28 +1,37 @@
-// fft_core.cuh -- register/shared-memory Stockham FFT on pencils (sm_103a).
+// fft_core.cuh -- register/shared-memory FFT on pencils (sm_103a).
 //
-// One "tile" is W pencils of length L (a power of two, 8..1024) processed by
-// (L/8)*W threads (W: see TileW).  Thread (j, w) with w = tid % W, j = tid / W holds eight
-// complex values of pencil w in registers: v[u] = x[j + u*L/8] (u = 0..7).
-// Between the radix stages the values go through shared memory, pencils
-// interleaved (element l of pencil w at row l, column w; rows of W elements
-// are 64 bytes) with one padding row after every 8 rows.  The padding keeps
-// every stage permutation within ~6% of the minimum number of shared-memory
-// wavefronts, and, unlike an XOR swizzle, gives each thread addresses of the
-// form base + compile-time offset.  Two tile buffers alternate ("ping-pong"),
-// so one barrier per exchange suffices.
+// Every length L = 2^p (8 <= L <= 1024) is split once, L = R1 * R2 with
+// R1 = 2^floor(p/2) and R2 = L / R1 (R2 = R1 or 2 R1), and transformed in two
+// radix stages with ONE shared-memory exchange between them (the four-step /
+// Stockham split of Cooley-Tukey):
+//
+//   stage 1: R2 DFTs of size R1 over x[n2 + R2 n1]            (registers)
+//   exchange through shared memory                           (one barrier)
+//   twiddle  exp(DIR 2 pi i k1 n2 / L)                        (table)
+//   stage 2: R1 DFTs of size R2 over the twiddled values      (registers)
+//
+// A pencil is worked by NT = R1 threads holding V = R2 complex values each:
+// thread j holds v[u] = x[j + u*NT] before the transform and X[j + u*NT]
+// after it (natural order in and out), so callers fuse elementwise work
+// (clips, masks, reductions) on the registers.  The register DFTs of size
+// 2..32 are split recursively into sizes 4 and 8 with their internal twiddles
+// as compile-time constants.
+//
+// A "tile" is W pencils interleaved in shared memory (element l of pencil w
+// at row l, column w; a row is W complex values) with one padding row after
+// every R1 rows: the stage-1 stores (rows R1-strided across threads) and the
+// stage-2 loads (consecutive rows across threads) both stay within the
+// minimum number of shared-memory wavefronts.  One buffer per tile; the
+// barrier before an exchange that reuses it is taken only when needed.  A
+// tile of at most 32 threads lies inside one warp and synchronises with
+// __syncwarp instead of a block barrier.
 //
 // The transform is the unnormalised DFT of Eq. 1, X_k = sum_n x_n w^{nk},
-// w = exp(DIR 2 pi i / L), DIR = -1 forward, +1 inverse (no 1/L), in the
-// Stockham autosort formulation (Cooley-Tukey with a permuting store after
-// every stage, natural order in and out).  Radix schedule: all radix-8 when
-// 3 | log2 L; otherwise one (log2 L = 3a+2) or two (3a+1) radix-4 stages
-// first.  After the last stage thread j again holds X[j + u*L/8], so callers
-// can fuse elementwise work (clips, masks, reductions) on the registers.
+// w = exp(DIR 2 pi i / L), DIR = -1 forward, +1 inverse (no 1/L).
 //
-// Twiddles: per stage (R, NS), for k < NS the factors exp(-2 pi i k t/(R NS)),
-// t = 1..R-1, stored contiguously (padded to 8 or 4 entries) so a thread
-// fetches its stage's factors with 128-bit loads.  They are computed on the
-// host in long double and rounded once; the inverse uses the conjugates.
+// Twiddle table of length L: entry k1 * R2 + t - 1 holds exp(-2 pi i k1 t / L)
+// for k1 < R1 and t = 1..R2-1 (computed on the host in long double and
+// rounded once; the inverse uses the conjugates).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -79,7 +88,38 @@ __device__ __forceinline__ v2<T> mul_w8_3(v2<T> a) {
   else return mk<T>(-(a.x + a.y) * s, (a.x - a.y) * s);
 }
 
-// In-register DFTs of size 4 and 8 in natural output order.
+// cos(2 pi r / 32) for r = 0..8 (decimal values of the exact constants).
+__host__ __device__ constexpr double cos32_oct(int r) {
+  return r == 0 ? 1.0 : r == 1 ? 0.98078528040323044913 : r == 2 ? 0.92387953251128675613
+       : r == 3 ? 0.83146961230254523708 : r == 4 ? 0.70710678118654752440
+       : r == 5 ? 0.55557023301960222474 : r == 6 ? 0.38268343236508977173
+       : r == 7 ? 0.19509032201612826785 : 0.0;
+}
+// cos and sin of 2 pi m / 32 for any integer m, by quadrant.
+__host__ __device__ constexpr double cos32(int m) {
+  return ((m & 31) >> 3) == 0 ? cos32_oct(m & 7) : ((m & 31) >> 3) == 1 ? -cos32_oct(8 - (m & 7))
+       : ((m & 31) >> 3) == 2 ? -cos32_oct(m & 7) : cos32_oct(8 - (m & 7));
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// a * exp(DIR 2 pi i m / 32); m is a constant after unrolling, so every
+// branch but one folds away.  Multiples of pi/4 take the cheap forms.
+template <typename T, int DIR>
+__device__ __forceinline__ v2<T> mul_w32(v2<T> a, int m) {
+  m &= 31;
+  if (m == 0) return a;
+  if (m == 8) return mul_i<T, DIR>(a);
+  if (m == 16) return mk<T>(-a.x, -a.y);
+  if (m == 24) return mul_i<T, -DIR>(a);
+  if (m == 4) return mul_w8_1<T, DIR>(a);
+  if (m == 12) return mul_w8_3<T, DIR>(a);
+  if (m == 20) { const v2<T> b = mul_w8_1<T, DIR>(a); return mk<T>(-b.x, -b.y); }
+  if (m == 28) { const v2<T> b = mul_w8_3<T, DIR>(a); return mk<T>(-b.x, -b.y); }
+  const T c = (T)cos32(m), s = (T)(DIR * sin32(m));
+  return mk<T>(a.x * c - a.y * s, a.y * c + a.x * s);
+}
+
+// In-register DFTs in natural output order.
 template <typename T, int DIR>
 __device__ __forceinline__ void dft4(v2<T>& a0, v2<T>& a1, v2<T>& a2, v2<T>& a3) {
   v2<T> s02 = add<T>(a0, a2), d02 = sub<T>(a0, a2);
@@ -101,165 +141,158 @@ __device__ __forceinline__ void dft8(v2<T> (&a)[8]) {
   a[2] = add<T>(e2, o2); a[6] = sub<T>(e2, o2);
   a[3] = add<T>(e3, o3); a[7] = sub<T>(e3, o3);
 }
+
 template <int R, typename T, int DIR>
-__device__ __forceinline__ void dftR(v2<T> (&x)[R]) {
-  if constexpr (R == 4) dft4<T, DIR>(x[0], x[1], x[2], x[3]);
-  else dft8<T, DIR>(x);
+__device__ __forceinline__ void dftN(v2<T> (&x)[R]);
+
+// DFT of size N = A * B: B DFTs of size A over x[b + B a], internal twiddles
+// w_N^{b k1}, A DFTs of size B, output k = k1 + A k2 (Cooley-Tukey).
+template <typename T, int DIR, int A, int B>
+__device__ __forceinline__ void dft_ab(v2<T> (&x)[A * B]) {
+  constexpr int N = A * B;
+  static_assert(N <= 32, "internal twiddles are tabulated in 32nds");
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    v2<T> t[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) t[a] = x[b + B * a];
+    dftN<A, T, DIR>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) x[b + B * k1] = mul_w32<T, DIR>(t[k1], b * k1 * (32 / N));
+  }
+  v2<T> o[N];
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    v2<T> t[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) t[b] = x[b + B * k1];
+    dftN<B, T, DIR>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) o[k1 + A * k2] = t[k2];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = o[i];
+}
+
+template <int R, typename T, int DIR>
+__device__ __forceinline__ void dftN(v2<T> (&x)[R]) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    const v2<T> a = x[0];
+    x[0] = add<T>(a, x[1]);
+    x[1] = sub<T>(a, x[1]);
+  } else if constexpr (R == 4) {
+    dft4<T, DIR>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 8) {
+    dft8<T, DIR>(x);
+  } else if constexpr (R == 16) {
+    dft_ab<T, DIR, 4, 4>(x);
+  } else {
+    static_assert(R == 32, "register DFT sizes 1..32");
+    dft_ab<T, DIR, 8, 4>(x);
+  }
 }
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
-// Pencils per tile: float64 tiles use 4 (64-byte rows); float32 tiles use
-// FFCZ_W32 pencils (4: 32-byte rows, CTAs half the size and twice as many
-// resident; 8: 64-byte rows).
-#ifndef FFCZ_W32
-#define FFCZ_W32 8
-#endif
-template <typename T> struct TileW { static constexpr int value = 4; };
-template <> struct TileW<float> { static constexpr int value = FFCZ_W32; };
-
-// Radix schedule and twiddle-table layout for length L (host and device).
+// The two-stage split of length L.
 template <int L>
-struct Sched {
-  static constexpr int lg = ilog2(L), a = lg / 3, b = lg % 3;
-  static constexpr int nst = (b == 0) ? a : a + 1;
-  __host__ __device__ static constexpr int radix(int s) {
-    return b == 0 ? 8 : (b == 2 ? (s == 0 ? 4 : 8) : (s < 2 ? 4 : 8));
-  }
-  __host__ __device__ static constexpr int ns(int s) {
-    int n = 1;
-    for (int i = 0; i < s; ++i) n *= radix(i);
-    return n;
-  }
-  __host__ __device__ static constexpr int sp(int s) { return radix(s) == 8 ? 8 : 4; }
-  __host__ __device__ static constexpr int twoff(int s) {
-    int o = 0;
-    for (int i = 1; i < s; ++i) o += ns(i) * sp(i);
-    return o;
-  }
-  static constexpr int twsize = twoff(nst) > 0 ? twoff(nst) : 4;
+struct F2 {
+  static_assert(L >= 8 && L <= 1024 && (L & (L - 1)) == 0, "L must be a power of two in [8, 1024]");
+  static constexpr int lg = ilog2(L);
+  static constexpr int lg1 = lg / 2;
+  static constexpr int R1 = 1 << lg1;     // stage-1 size = threads per pencil
+  static constexpr int R2 = L / R1;       // stage-2 size = values per thread
+  static constexpr int NT = R1, V = R2;
+  static constexpr int NB1 = R2 / R1;     // stage-1 DFTs per thread (1 or 2)
+  static constexpr int ROWS = L + R2;     // rows of one tile buffer (padding included)
+  // buffer row of natural element l
+  __host__ __device__ static constexpr int row(int l) { return l + (l >> lg1); }
 };
+// Host-side values of the same split.
+inline int f2_nt(int L) { return 1 << (ilog2(L) / 2); }
+inline int f2_v(int L) { return L / f2_nt(L); }
 
-// Row index with one padding row after every 8 rows.
-__host__ __device__ constexpr int pidx(int l) { return l + (l >> 3); }
+// Pencils per tile of the strided passes: 64-byte rows (8 float32 or 4
+// float64 complex values).
+template <typename T> struct TileW { static constexpr int value = 16 / (int)sizeof(T) * 2; };
 
-// A thread's view of its pencil in two ping-pong tile buffers.
-template <typename T, int L, int W_ = TileW<T>::value>
+// A thread's view of its pencil's column in the tile buffer.
+template <typename T, int L, int W_>
 struct Tile {
   static constexpr int W = W_;
-  static constexpr int ROWS = L + L / 8;
-  static constexpr int ELEMS = ROWS * W;   // one buffer
-  v2<T>* p0;  // buffer used by even exchanges (+ w)
-  v2<T>* p1;  // buffer used by odd exchanges (+ w)
-  int ph;     // buffer the next exchange uses
-  __device__ __forceinline__ v2<T>* buf() const { return ph ? p1 : p0; }
-  __device__ __forceinline__ void flip() { ph ^= 1; }
-  // element l of this pencil / of the pencil `dw` columns away, current buffer
-  __device__ __forceinline__ v2<T>& at(int l) const { return buf()[pidx(l) * W]; }
-  __device__ __forceinline__ v2<T>& at_other(int l, int dw) const { return buf()[pidx(l) * W + dw]; }
+  static constexpr int TPT = F2<L>::NT * W;       // threads of the tile
+  static constexpr int ELEMS = F2<L>::ROWS * W;   // complex values of the buffer
+  v2<T>* p;    // buffer + w
+  bool used;   // an earlier exchange has read the buffer
+  __device__ __forceinline__ static void sync() {
+    if constexpr (TPT <= 32) __syncwarp();
+    else __syncthreads();
+  }
+  // before storing: wait until every thread has read the previous exchange
+  __device__ __forceinline__ void begin() {
+    if (used) sync();
+  }
+  __device__ __forceinline__ void done() { used = true; }
+  __device__ __forceinline__ v2<T>* buf() const { return p; }
+  // natural element l of this pencil / of the pencil `dw` columns away
+  __device__ __forceinline__ v2<T>& at(int l) const { return p[F2<L>::row(l) * W]; }
+  __device__ __forceinline__ v2<T>& at_other(int l, int dw) const { return p[F2<L>::row(l) * W + dw]; }
 };
 
-// Natural-order row index of register u of thread j: pidx(j + u*NT).
-template <int NT>
-__device__ __forceinline__ int nat(int jb, int j, int u) {
-  if constexpr (NT % 8 == 0) return jb + u * (NT + NT / 8);
-  else return pidx(j + u * NT);
-}
-
-// One Stockham stage S of the schedule: radix R, sub-transform size NS.
-// Thread j owns 8/R butterflies j' = j + b*L/8; butterfly j' takes
-// x[j' + t*L/R] (registers v[b + t*8/R]); after the twiddles
-// exp(DIR 2 pi i k t/(R NS)), k = j' mod NS, and the R-point DFT, output t
-// goes to row (j'/NS)*R*NS + k + t*NS.  The last stage keeps the outputs in
-// registers: they are then x[j + u*L/8] again.
-template <typename T, int L, int DIR, int S, class TL>
-__device__ __forceinline__ void stockham_stage(v2<T> (&v)[8], int j, int jb,
-                                               const v2<T>* __restrict__ tw, TL& tl) {
-  using SC = Sched<L>;
-  constexpr int R = SC::radix(S), NS = SC::ns(S), NT = L / 8, NB = 8 / R, W = TL::W;
-  constexpr bool last = (S == SC::nst - 1);
-  v2<T>* dst = tl.buf();
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int jp = j + b * NT;
-    const int k = jp & (NS - 1);
-    v2<T> x[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) x[t] = v[b + t * NB];
-    if constexpr (NS > 1) {
-      // factors t = 1..R-1 of this butterfly, fetched two at a time
-      const v2<T>* twk = tw + SC::twoff(S) + k * SC::sp(S);
-      if constexpr (sizeof(T) == 4) {
-        const float4* q = reinterpret_cast<const float4*>(twk);
-#pragma unroll
-        for (int i = 0; i < R / 2; ++i) {
-          const float4 f = q[i];
-          if (2 * i + 1 < R) x[2 * i + 1] = twmul<T, DIR>(x[2 * i + 1], mk<T>(f.x, f.y));
-          if (2 * i + 2 < R) x[2 * i + 2] = twmul<T, DIR>(x[2 * i + 2], mk<T>(f.z, f.w));
-        }
-      } else {
-#pragma unroll
-        for (int t = 1; t < R; ++t) x[t] = twmul<T, DIR>(x[t], twk[t - 1]);
-      }
-    }
-    dftR<R, T, DIR>(x);
-    if constexpr (last) {
-#pragma unroll
-      for (int t = 0; t < R; ++t) v[b + t * NB] = x[t];
-    } else {
-      const int o = (jp / NS) * (R * NS) + k;
-      if constexpr (NS >= 8) {
-        const int base = o + (o >> 3);
-#pragma unroll
-        for (int t = 0; t < R; ++t) dst[(base + t * (NS + NS / 8)) * W] = x[t];
-      } else if constexpr (NS == 4) {
-        const int base = o + (jp >> 2) * (R / 2);
-#pragma unroll
-        for (int t = 0; t < R; ++t) dst[(base + 4 * t + (t >> 1)) * W] = x[t];
-      } else {
-        const int base = jp * R + (R == 8 ? jp : (jp >> 1));
-#pragma unroll
-        for (int t = 0; t < R; ++t) dst[(base + t) * W] = x[t];
-      }
-    }
-  }
-  if constexpr (!last) {
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = dst[nat<NT>(jb, j, u) * W];
-    tl.flip();
-  }
-}
-
-template <typename T, int L, int DIR, int S, class TL>
-__device__ __forceinline__ void stages_from(v2<T> (&v)[8], int j, int jb, const v2<T>* __restrict__ tw,
-                                            TL& tl) {
-  if constexpr (S < Sched<L>::nst) {
-    stockham_stage<T, L, DIR, S, TL>(v, j, jb, tw, tl);
-    stages_from<T, L, DIR, S + 1, TL>(v, j, jb, tw, tl);
-  }
-}
-
-// Full length-L transform of the thread's pencil.  Every thread of the CTA
-// must call it (it synchronises the block between stages).  `jb` is
-// pidx(j) (precomputed by the caller).
+// Full length-L transform of the thread's pencil (all threads of the tile
+// must call it).  tw: the length-L twiddle table (shared memory).
 template <typename T, int L, int DIR, class TL>
-__device__ __forceinline__ void fft_pencil(v2<T> (&v)[8], int j, int jb, const v2<T>* __restrict__ tw,
+__device__ __forceinline__ void fft_pencil(v2<T> (&v)[F2<L>::V], int j, const v2<T>* __restrict__ tw,
                                            TL& tl) {
-  static_assert(L >= 8 && (L & (L - 1)) == 0, "L must be a power of two >= 8");
-  stages_from<T, L, DIR, 0, TL>(v, j, jb, tw, tl);
+  using F = F2<L>;
+  constexpr int R1 = F::R1, R2 = F::R2, NB1 = F::NB1, W = TL::W;
+  tl.begin();
+  v2<T>* buf = tl.buf();
+#pragma unroll
+  for (int b = 0; b < NB1; ++b) {
+    v2<T> x[R1];
+#pragma unroll
+    for (int t = 0; t < R1; ++t) x[t] = v[b + t * NB1];
+    dftN<R1, T, DIR>(x);
+    // output t of stage-1 DFT n2 = j + b R1 is element n2 R1 + t
+    const int r0 = (j + b * R1) * (R1 + 1);
+#pragma unroll
+    for (int t = 0; t < R1; ++t) buf[(r0 + t) * W] = x[t];
+  }
+  TL::sync();
+  // element j + t R1 (row j + t (R1 + 1)), twiddled by w_L^{j t}
+#pragma unroll
+  for (int t = 0; t < R2; ++t) v[t] = buf[(j + t * (R1 + 1)) * W];
+  tl.done();
+  const v2<T>* twj = tw + j * R2;
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(twj);
+#pragma unroll
+    for (int i = 0; i < R2 / 2; ++i) {
+      const float4 f = q[i];
+      v[2 * i + 1] = twmul<T, DIR>(v[2 * i + 1], mk<T>(f.x, f.y));
+      if (2 * i + 2 < R2) v[2 * i + 2] = twmul<T, DIR>(v[2 * i + 2], mk<T>(f.z, f.w));
+    }
+  } else {
+#pragma unroll
+    for (int t = 1; t < R2; ++t) v[t] = twmul<T, DIR>(v[t], twj[t - 1]);
+  }
+  dftN<R2, T, DIR>(v);
 }
 
-// Exchange: every thread stores its natural-order registers, the block
-// synchronises, and `f(l)` below reads other rows; afterwards the buffers
-// flip.  Used where an elementwise step needs X[-k] next to X[k].
+// Exchange in natural order: every thread stores its registers, the tile
+// synchronises, and the caller reads other elements with at()/at_other();
+// the caller then calls tl.done().  Used where an elementwise step needs
+// X[-k] next to X[k].
 template <typename T, int L, class TL>
-__device__ __forceinline__ void store_nat(const v2<T> (&v)[8], int j, int jb, TL& tl) {
-  constexpr int NT = L / 8, W = TL::W;
+__device__ __forceinline__ void store_nat(const v2<T> (&v)[F2<L>::V], int j, TL& tl) {
+  constexpr int R1 = F2<L>::R1, W = TL::W;
+  tl.begin();
   v2<T>* dst = tl.buf();
 #pragma unroll
-  for (int u = 0; u < 8; ++u) dst[nat<NT>(jb, j, u) * W] = v[u];
-  __syncthreads();
+  for (int u = 0; u < F2<L>::V; ++u) dst[(j + u * (R1 + 1)) * W] = v[u];
+  TL::sync();
 }
 
 }  // namespace ffcz

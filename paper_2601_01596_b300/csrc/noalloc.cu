@@ -56,7 +56,7 @@ thread_local ErrSink s_err;
 struct DevSetup {
   bool ready = false;
   unsigned char* base = nullptr;            // device address of g_static_scratch
-  const void* stage_tab[12] = {};           // float64 Stockham factors, L = 2^p
+  const void* stage_tab[12] = {};           // float64 stage-2 twiddles, L = 2^p
   const void* r2c_tab[12] = {};             // float64 R2C factors, Nx = 2^p
 };
 constexpr int kMaxDev = 64;
@@ -73,28 +73,12 @@ double2 root64(long double m, long double L) {
   return make_double2((double)c, (double)s);
 }
 
-template <int L>
-void stage_factors(std::vector<double2>& out) {
-  using SC = Sched<L>;
-  out.assign(SC::twsize, make_double2(0.0, 0.0));
-  for (int s = 1; s < SC::nst; ++s) {
-    const int R = SC::radix(s), NS = SC::ns(s), sp = SC::sp(s), off = SC::twoff(s);
-    for (int k = 0; k < NS; ++k)
-      for (int t = 1; t < R; ++t) out[off + k * sp + t - 1] = root64((long double)k * t, (long double)R * NS);
-  }
-}
-
+// Stage-2 twiddles of the two-stage split of L (layout in fft_core.cuh).
 void stage_factors_rt(int L, std::vector<double2>& out) {
-  switch (L) {
-    case 8: stage_factors<8>(out); break;
-    case 16: stage_factors<16>(out); break;
-    case 32: stage_factors<32>(out); break;
-    case 64: stage_factors<64>(out); break;
-    case 128: stage_factors<128>(out); break;
-    case 256: stage_factors<256>(out); break;
-    case 512: stage_factors<512>(out); break;
-    case 1024: stage_factors<1024>(out); break;
-  }
+  const int R1 = f2_nt(L), R2 = L / R1;
+  out.assign(L, make_double2(0.0, 0.0));
+  for (int k1 = 0; k1 < R1; ++k1)
+    for (int t = 1; t < R2; ++t) out[k1 * R2 + t - 1] = root64((long double)k1 * t, (long double)L);
 }
 
 template <typename K>
@@ -175,7 +159,7 @@ __global__ void k_static_init(int32_t* item, int64_t* eoff, int64_t* soff, ItemP
 template <int M>
 void launch_xfwd(const Args& a, int64_t rows, cudaStream_t s) {
   using G_ = Geo<double, M>;
-  dim3 grid((unsigned)((rows / G_::W + G_::G - 1) / G_::G), 1);
+  dim3 grid((unsigned)(((rows + G_::W - 1) / G_::W + G_::G - 1) / G_::G), 1);
   k_xfwd<double, M><<<grid, G_::NTHR, Smem<double, M>::bytes_x, s>>>(a);
 }
 template <int L>

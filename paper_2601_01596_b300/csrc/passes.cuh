@@ -113,25 +113,56 @@ __device__ __forceinline__ v2<T>* pick(const Args& a, int sel, int t) {
 template <typename T, int L, int W_ = TileW<T>::value>
 struct Geo {
   static constexpr int W = W_;                         // pencils per tile
-  static constexpr int NT = L / 8;                     // threads per pencil
+  static constexpr int NT = F2<L>::NT;                 // threads per pencil
+  static constexpr int V = F2<L>::V;                   // values per thread
   static constexpr int TPT = NT * W;                   // threads per tile
   static constexpr int G = TPT >= 128 ? 1 : 128 / TPT; // tiles per CTA (>= 128 threads)
   static constexpr int NTHR = G * TPT;
-  // resident CTAs per SM the register budget is sized for: float32 tiles
-  // get 1024 threads per SM (64 registers), float64 tiles 512 (128 registers)
-  static constexpr int MINB = sizeof(T) == 4 ? (1024 / NTHR > 0 ? 1024 / NTHR : 1)
-                                             : (512 / NTHR > 0 ? 512 / NTHR : 1);
+  static constexpr int MW = (V + 7) / 8;               // mask words per thread
+  // threads per SM the register budget is sized for: float32 with up to 8
+  // values per thread 1024 (64 registers), 16 values 512 (128), 32 values
+  // 384 (170); float64 512 (128) up to 8 values, else 256 (255)
+  static constexpr int SMT = sizeof(T) == 4 ? (V >= 32 ? 384 : V >= 16 ? 512 : 1024) : (V >= 16 ? 256 : 512);
+  static constexpr int MINB = SMT / NTHR > 0 ? SMT / NTHR : 1;
 };
 
-// Shared-memory carve-up: [G tiles x 2 buffers][stage twiddles][R2C twiddles][reduction].
+// Shared-memory carve-up: [G tile buffers][twiddles][R2C twiddles][reduction].
 template <typename T, int L, int W = TileW<T>::value>
 struct Smem {
-  static constexpr size_t tiles = (size_t)Geo<T, L, W>::G * 2 * Tile<T, L, W>::ELEMS * sizeof(v2<T>);
-  static constexpr size_t tw = (size_t)Sched<L>::twsize * sizeof(v2<T>);
+  static constexpr size_t tiles = (size_t)Geo<T, L, W>::G * Tile<T, L, W>::ELEMS * sizeof(v2<T>);
+  static constexpr size_t tw = (size_t)L * sizeof(v2<T>);
   static constexpr size_t twr = (size_t)L * sizeof(v2<T>);
   static constexpr size_t red = 32 * 8 * 3 + 32 * 4;
   static constexpr size_t bytes_axis = tiles + tw + red;
   static constexpr size_t bytes_x = tiles + tw + twr + red;
+};
+
+// Per-thread adjoint mask words: value u of the thread owns bits
+// [PER (u % 8), PER (u % 8) + PER) of word u / 8 (PER = 2: Re, Im inside;
+// PER = 4 on kx = 0 mirror tiles: Re A, Im A, Re B, Im B inside).
+template <int MW>
+struct MaskBits {
+  uint32_t w[MW];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < MW; ++i) w[i] = 0u;
+  }
+  __device__ __forceinline__ void fill() {
+#pragma unroll
+    for (int i = 0; i < MW; ++i) w[i] = 0xffffffffu;
+  }
+  __device__ __forceinline__ void load(const uint32_t* m, int64_t thr) {
+#pragma unroll
+    for (int i = 0; i < MW; ++i) w[i] = m[thr * MW + i];
+  }
+  __device__ __forceinline__ void store(uint32_t* m, int64_t thr) const {
+#pragma unroll
+    for (int i = 0; i < MW; ++i) m[thr * MW + i] = w[i];
+  }
+  template <int PER>
+  __device__ __forceinline__ uint32_t get(int u) const { return (w[u >> 3] >> (PER * (u & 7))) & ((1u << PER) - 1u); }
+  template <int PER>
+  __device__ __forceinline__ void put(int u, uint32_t b) { w[u >> 3] |= b << (PER * (u & 7)); }
 };
 
 // Block reduction of (max as non-negative double bits, count, sum).
@@ -204,14 +235,16 @@ template <> struct AbsMax<double> {
 // exact-zero twiddle component is NaN), so after the forward passes either the
 // magnitude max is Inf or every value is NaN.  Two probes per thread detect
 // the all-NaN case.
-template <typename T>
-__device__ __forceinline__ bool nan_probe(const v2<T> (&v)[8]) {
-  return (v[0].x != v[0].x) | (v[7].y != v[7].y);
+template <typename T, int V>
+__device__ __forceinline__ bool nan_probe(const v2<T> (&v)[V]) {
+  return (v[0].x != v[0].x) | (v[V - 1].y != v[V - 1].y);
 }
 
 __device__ __forceinline__ float clampT(float x, float b) { return fminf(fmaxf(x, -b), b); }
 __device__ __forceinline__ double clampT(double x, double b) { return fmin(fmax(x, -b), b); }
 
+// Twiddle tables into shared memory: the length-L stage table and, for x
+// passes, the M-entry R2C table; ends with a block barrier.
 template <typename T>
 __device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int ntw, v2<T>* s_twr,
                                             const void* twr, int M) {
@@ -230,14 +263,16 @@ __device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int ntw
 // ---------------------------------------------------------------------------
 
 // Post-processing of Z = FFT_M(z) into the packed half spectrum P (in place
-// in registers).  Needs Z[M-k], fetched through one shared-memory exchange.
+// in registers).  Each k needs Z[M-k], which another thread holds; it is
+// read through one exchange in natural order (a warp barrier only, when the
+// tile lies inside one warp).
 template <typename T, int M, class TL>
-__device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, int jb, TL& tl,
+__device__ __forceinline__ void r2c_post(v2<T> (&v)[F2<M>::V], int j, TL& tl,
                                          const v2<T>* __restrict__ twr) {
-  constexpr int NT = M / 8;
-  store_nat<T, M, TL>(v, j, jb, tl);
+  constexpr int NT = F2<M>::NT, V = F2<M>::V;
+  store_nat<T, M, TL>(v, j, tl);
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < V; ++u) {
     const int k = j + u * NT;
     const v2<T> zk = v[u];
     const v2<T> zm = tl.at((M - k) & (M - 1));
@@ -250,18 +285,18 @@ __device__ __forceinline__ void r2c_post(v2<T> (&v)[8], int j, int jb, TL& tl,
       v[u] = add<T>(fe, cmul<T>(twr[k], fo));
     }
   }
-  tl.flip();
+  tl.done();
 }
 
 // Pre-processing of packed P into Z' = 2 Z so that IFFT_M(Z') / Nx gives
-// the real row (again one exchange for P[M-k]).
+// the real row (P[M-k] read through one exchange as above).
 template <typename T, int M, class TL>
-__device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, TL& tl,
+__device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
                                         const v2<T>* __restrict__ twr) {
-  constexpr int NT = M / 8;
-  store_nat<T, M, TL>(v, j, jb, tl);
+  constexpr int NT = F2<M>::NT, V = F2<M>::V;
+  store_nat<T, M, TL>(v, j, tl);
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < V; ++u) {
     const int k = j + u * NT;
     const v2<T> xk = v[u];
     const v2<T> xm = tl.at((M - k) & (M - 1));
@@ -274,16 +309,17 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, TL& tl,
       v[u] = mk<T>(s.x - d.y, s.y + d.x);
     }
   }
-  tl.flip();
+  tl.done();
 }
 
 #define FFCZ_X_PROLOGUE(T_, M_, W_)                                               \
   using G_ = Geo<T_, M_, W_>;                                                     \
   using TL = Tile<T_, M_, W_>;                                                    \
+  constexpr int V = G_::V;                                                        \
   extern __shared__ __align__(16) unsigned char smraw[];                          \
   v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
-  v2<T_>* s_tw = s_tiles + G_::G * 2 * TL::ELEMS;                                \
-  v2<T_>* s_twr = s_tw + Sched<M_>::twsize;                                       \
+  v2<T_>* s_tw = s_tiles + G_::G * TL::ELEMS;                                     \
+  v2<T_>* s_twr = s_tw + M_;                                                      \
   unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M_); \
   const int gi = blockIdx.y;                                                      \
   const int item = a.g.item[gi];                                                  \
@@ -292,13 +328,14 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[8], int j, int jb, TL& tl,
   if (!pred_ok(a.pred, st, p)) return;                                            \
   const int t_it = st.t;                                                          \
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
-  const int w = tid % G_::W, j = tid / G_::W, jb = pidx(j);                       \
+  const int w = tid % G_::W, j = tid / G_::W;                                     \
   const int tile = blockIdx.x * G_::G + g;                                        \
-  const int ntiles = (int)(a.g.rows / G_::W);                                     \
-  const bool live = tile < ntiles;                                                \
-  const int row = live ? tile * G_::W + w : 0;                                    \
-  TL tl{s_tiles + g * 2 * TL::ELEMS + w, s_tiles + g * 2 * TL::ELEMS + TL::ELEMS + w, 0}; \
-  (void)t_it;
+  const int64_t prow = (int64_t)tile * G_::W + w;                                 \
+  const bool live = prow < a.g.rows;                                              \
+  const int64_t row = live ? prow : 0;                                            \
+  const int64_t mthr = (int64_t)tile * G_::TPT + tid;                             \
+  TL tl{s_tiles + g * TL::ELEMS + w, false};                                      \
+  (void)t_it; (void)mthr;
 
 // Entry / certification x pass: float32 real rows -> packed spectrum.
 template <typename T, int M, int W = TileW<T>::value>
@@ -311,12 +348,13 @@ k_xfwd(Args a) {
   AbsMax<float> mx;
   float ssq = 0.f;
   unsigned long long cnt = 0;
-  uint32_t bits = 0;
-  if ((a.mode & M_MASK) && live) bits = a.mask[tile * G_::TPT + tid];
-  v2<T> v[8];
+  MaskBits<G_::MW> mb;
+  mb.clear();
+  if ((a.mode & M_MASK) && live) mb.load(a.mask, mthr);
+  v2<T> v[V];
   bool bad = false;
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < V; ++u) {
     float2 x = erow[j + u * G_::NT];
     if (a.mode & M_MEASURE) {
       mx.add(x.x); mx.add(x.y);
@@ -330,23 +368,24 @@ k_xfwd(Args a) {
       if (live) erow_w[j + u * G_::NT] = x;
     }
     if (a.mode & M_MASK) {
-      if (!((bits >> (2 * u)) & 1u)) x.x = 0.f;
-      if (!((bits >> (2 * u + 1)) & 1u)) x.y = 0.f;
+      const uint32_t b2 = mb.template get<2>(u);
+      if (!(b2 & 1u)) x.x = 0.f;
+      if (!(b2 & 2u)) x.y = 0.f;
     }
     v[u] = mk<T>((T)x.x, (T)x.y);
   }
-  load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
-  fft_pencil<T, M, -1>(v, j, jb, s_tw, tl);
-  r2c_post<T, M>(v, j, jb, tl, s_twr);
+  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
+  fft_pencil<T, M, -1>(v, j, s_tw, tl);
+  r2c_post<T, M>(v, j, tl, s_twr);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[j + u * G_::NT] = v[u];
+    for (int u = 0; u < V; ++u) out[j + u * G_::NT] = v[u];
   }
   if (a.mode & (M_MEASURE | M_PRECLIP)) {
-    // 16 float32 squares summed in float32: relative error < 17 u32; the
-    // bound that uses this sum takes (1 + 2^-18) of it.
-    Red r{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-18) : 0.0, live ? cnt : 0ull};
+    // 2V float32 squares summed in float32: relative error < (2V+1) u32; the
+    // bound that uses this sum takes (1 + 2^-17) of it (2V <= 64).
+    Red r{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-17) : 0.0, live ? cnt : 0ull};
     block_reduce(r, s_red);
     if (threadIdx.x == 0) {
       if (a.mode & M_MEASURE) {
@@ -358,18 +397,18 @@ k_xfwd(Args a) {
   }
 }
 
-// s-clip of the thread's 16 values with every option (mask recording,
-// checkpoint writes); the lean loop path uses s_clip_fast.
-template <typename T>
-__device__ __forceinline__ void s_clip_full(v2<T> (&v)[8], T Es, bool count, uint32_t& bits,
+// s-clip of the thread's values with every option (mask recording,
+// checkpoint writes); the lean loop path clips without recording.
+template <typename T, int V, int MW>
+__device__ __forceinline__ void s_clip_full(v2<T> (&v)[V], T Es, bool count, MaskBits<MW>& mb,
                                             unsigned long long& cnt, float2* ck, int j, int NT) {
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < V; ++u) {
     T x = v[u].x, y = v[u].y;
     const T cx = clampT(x, Es), cy = clampT(y, Es);
     const bool ix = (cx == x), iy = (cy == y);   // inside the s-cube
     if (count) cnt += (!ix) + (!iy);
-    bits |= ((uint32_t)ix << (2 * u)) | ((uint32_t)iy << (2 * u + 1));
+    mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
     v[u] = mk<T>(cx, cy);
     if (ck) ck[j + u * NT] = make_float2((float)cx, (float)cy);
   }
@@ -378,49 +417,53 @@ __device__ __forceinline__ void s_clip_full(v2<T> (&v)[8], T Es, bool count, uin
 // Loop body x pass on one tile held in registers: C2R, scale 1/N, s-clip
 // (or adjoint mask), R2C.  Returns the active-clip count of the thread.
 template <typename T, int M, class TL>
-__device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[8],
-                                                      int j, int jb, int tid, int tile, int row, bool live,
+__device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
+                                                      int j, int64_t mthr, int64_t row, bool live,
                                                       int t_it, TL& tl, const v2<T>* twg,
                                                       const v2<T>* twr) {
-  using G_ = Geo<T, M, TL::W>;
-  c2r_pre<T, M>(v, j, jb, tl, twr);
-  fft_pencil<T, M, +1>(v, j, jb, twg, tl);
+  constexpr int V = F2<M>::V, NT = F2<M>::NT, MW = (V + 7) / 8;
+  c2r_pre<T, M>(v, j, tl, twr);
+  fft_pencil<T, M, +1>(v, j, twg, tl);
   unsigned long long cnt = 0;
-  uint32_t bits = 0;
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   AbsMax<T> mx;
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < V; ++u) {
     v[u] = mk<T>(v[u].x * inv_n, v[u].y * inv_n);
     mx.add(v[u].x); mx.add(v[u].y);
   }
   const bool count = (a.mode & M_COUNT) != 0;
   const bool need_clip = __any_sync(0xffffffffu, mx.val() > Es);   // all lanes vote
   if (a.mode & M_MASK) {
-    if (live) bits = a.mask[tile * G_::TPT + tid];
+    MaskBits<MW> mb;
+    mb.clear();
+    if (live) mb.load(a.mask, mthr);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (!((bits >> (2 * u)) & 1u)) v[u].x = T(0);
-      if (!((bits >> (2 * u + 1)) & 1u)) v[u].y = T(0);
+    for (int u = 0; u < V; ++u) {
+      const uint32_t b2 = mb.template get<2>(u);
+      if (!(b2 & 1u)) v[u].x = T(0);
+      if (!(b2 & 2u)) v[u].y = T(0);
     }
   } else if (a.mode & (M_RECORD | M_CKPT)) {
     const bool ckn = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 && live;
-    float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * (2 * M * a.g.rows)) + (int64_t)row * M
+    float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * (2 * M * a.g.rows)) + row * M
                      : nullptr;
-    s_clip_full<T>(v, Es, count, bits, cnt, ck, j, G_::NT);
-    if ((a.mode & M_RECORD) && live) a.mask[tile * G_::TPT + tid] = bits;
+    MaskBits<MW> mb;
+    mb.clear();
+    s_clip_full<T, V, MW>(v, Es, count, mb, cnt, ck, j, NT);
+    if ((a.mode & M_RECORD) && live) mb.store(a.mask, mthr);
   } else if (need_clip) {
     // lean path: only warps holding a value outside the s-cube clip
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < V; ++u) {
       const T cx = clampT(v[u].x, Es), cy = clampT(v[u].y, Es);
       if (count) cnt += (cx != v[u].x) + (cy != v[u].y);
       v[u] = mk<T>(cx, cy);
     }
   }
-  fft_pencil<T, M, -1>(v, j, jb, twg, tl);
-  r2c_post<T, M>(v, j, jb, tl, twr);
+  fft_pencil<T, M, -1>(v, j, twg, tl);
+  r2c_post<T, M>(v, j, tl, twr);
   return live ? cnt : 0ull;
 }
 
@@ -429,15 +472,15 @@ __global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_px(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
-  v2<T> v[8];
+  v2<T> v[V];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = in[j + u * G_::NT];
-  load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
-  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, jb, tid, tile, row, live, t_it, tl, s_tw, s_twr);
+  for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
+  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
+  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[j + u * G_::NT] = v[u];
+    for (int u = 0; u < V; ++u) out[j + u * G_::NT] = v[u];
   }
   if (a.mode & M_COUNT) {
     Red r{0ull, 0.0, cnt};
@@ -448,24 +491,24 @@ k_px(Args a) {
 
 // Exit x pass: C2R, scale 1/N, s-clip, store float32 e (rebuilds the iterate
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
-// no clip is applied.  With M_COUNT it counts the final iterate's s-clips.
+// no clip is applied.
 template <typename T, int M, int W = TileW<T>::value>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xexit(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
-  v2<T> v[8];
+  v2<T> v[V];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = in[j + u * G_::NT];
-  load_tables<T>(s_tw, a.tw, Sched<M>::twsize, s_twr, a.twr, M);
-  c2r_pre<T, M>(v, j, jb, tl, s_twr);
-  fft_pencil<T, M, +1>(v, j, jb, s_tw, tl);
+  for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
+  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
+  c2r_pre<T, M>(v, j, tl, s_twr);
+  fft_pencil<T, M, +1>(v, j, s_tw, tl);
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
   if (live) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < V; ++u) {
       T x = v[u].x * inv_n, y = v[u].y * inv_n;
       if (a.mode & M_CLIP) { x = clampT(x, Es); y = clampT(y, Es); }
       float fx = (float)x, fy = (float)y;
@@ -485,11 +528,11 @@ k_xexit(Args a) {
 #define FFCZ_AXIS_PROLOGUE(T_, L_, W_)                                            \
   using G_ = Geo<T_, L_, W_>;                                                     \
   using TL = Tile<T_, L_, W_>;                                                    \
+  constexpr int V = G_::V;                                                        \
   extern __shared__ __align__(16) unsigned char smraw[];                          \
   v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
-  v2<T_>* s_tw = s_tiles + G_::G * 2 * TL::ELEMS;                                \
-  unsigned long long* s_red =                                                     \
-      reinterpret_cast<unsigned long long*>(s_tw + Sched<L_>::twsize);            \
+  v2<T_>* s_tw = s_tiles + G_::G * TL::ELEMS;                                     \
+  unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_tw + L_);  \
   (void)s_red;                                                                    \
   const int gi = blockIdx.y;                                                      \
   const int item = a.g.item[gi];                                                  \
@@ -498,9 +541,11 @@ k_xexit(Args a) {
   if (!pred_ok(a.pred, st, p)) return;                                            \
   const int t_it = st.t;                                                          \
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
-  const int w = tid % G_::W, j = tid / G_::W, jb = pidx(j);                       \
+  const int w = tid % G_::W, j = tid / G_::W;                                     \
   const int tile = blockIdx.x * G_::G + g;                                        \
-  TL tl{s_tiles + g * 2 * TL::ELEMS + w, s_tiles + g * 2 * TL::ELEMS + TL::ELEMS + w, 0};
+  const int64_t mthr = (int64_t)tile * G_::TPT + tid;                             \
+  TL tl{s_tiles + g * TL::ELEMS + w, false};                                      \
+  (void)mthr;
 
 // Plain C2C along the middle axis of a 3D item (y): pencils at fixed (z, kx).
 template <typename T, int L, int DIR, int W = TileW<T>::value>
@@ -513,19 +558,19 @@ k_axis(Args a) {
   const bool live = tile < ntiles;
   const int z = live ? (int)((unsigned)tile / tpr) : 0;
   const int kx = live ? (int)((unsigned)tile % tpr) * G_::W + w : 0;
-  const int off = z * L * M + kx;
+  const int64_t off = (int64_t)z * L * M + kx;
 
   const int64_t ustride = (int64_t)G_::NT * M;
-  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + off + j * M;
-  v2<T> v[8];
+  const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + off + (int64_t)j * M;
+  v2<T> v[V];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
-  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);   // overlaps the loads
-  fft_pencil<T, L, DIR>(v, j, jb, s_tw, tl);
+  for (int u = 0; u < V; ++u) v[u] = in[u * ustride];
+  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
+  fft_pencil<T, L, DIR>(v, j, s_tw, tl);
   if (live) {
-    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + off + j * M;
+    v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + off + (int64_t)j * M;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) out[u * ustride] = v[u];
+    for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
   }
 }
 
@@ -583,27 +628,27 @@ __host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
 // Everything of the check pass between load and store for one tile in
 // registers.  cta_has_mirror must be uniform over the CTA.
 template <typename T, int L, class TL>
-__device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st, v2<T> (&v)[8],
-                                         int j, int jb, int w, int tid, int tile, const ChkTile& c,
-                                         bool cta_has_mirror, TL& tl, const v2<T>* twg,
-                                         unsigned long long* s_red) {
-  using G_ = Geo<T, L, TL::W>;
-  constexpr int NT = G_::NT;
-  fft_pencil<T, L, -1>(v, j, jb, twg, tl);
+__device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st,
+                                         v2<T> (&v)[F2<L>::V], int j, int w, int64_t mthr,
+                                         const ChkTile& c, bool cta_has_mirror, TL& tl,
+                                         const v2<T>* twg, unsigned long long* s_red) {
+  constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
+  fft_pencil<T, L, -1>(v, j, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
   AbsMax<T> mx;
   bool bad = false;
   unsigned long long cnt = 0;
-  uint32_t bits = 0;
+  MaskBits<MW> mb;
+  mb.clear();
   const bool rec = (a.mode & M_RECORD) != 0, use_mask = (a.mode & M_MASK) != 0;
   const bool clip = (a.mode & M_CLIP) != 0, count = (a.mode & M_COUNT) != 0;
-  if (use_mask && c.live) bits = a.mask[tile * G_::TPT + tid];
+  if (use_mask && c.live) mb.load(a.mask, mthr);
   if (cta_has_mirror) {
-    store_nat<T, L, TL>(v, j, jb, tl);
+    store_nat<T, L, TL>(v, j, tl);
     if (c.mirror) {
       const int dw = (w ^ 1) - w;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < V; ++u) {
         const v2<T> cc = v[u], m = tl.at_other((L - (j + u * NT)) & (L - 1), dw);
         // A = (C + conj Cm)/2, B = (C - conj Cm)/(2i)
         T ar = T(0.5) * (cc.x + m.x), ai = T(0.5) * (cc.y - m.y);
@@ -615,11 +660,11 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           const T cbr = clampT(br, Ds), cbi = clampT(bi, Ds);
           const bool iar = car == ar, iai = cai == ai, ibr = cbr == br, ibi = cbi == bi;
           if (c.owner) cnt += (!iar) + (!iai) + (!ibr) + (!ibi);
-          bits |= ((uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) | ((uint32_t)ibi << 3))
-                  << (4 * u);
+          mb.template put<4>(u, (uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) |
+                                    ((uint32_t)ibi << 3));
           ar = car; ai = cai; br = cbr; bi = cbi;
         } else if (use_mask) {
-          const uint32_t b4 = bits >> (4 * u);
+          const uint32_t b4 = mb.template get<4>(u);
           if (!(b4 & 1u)) ar = T(0);
           if (!(b4 & 2u)) ai = T(0);
           if (!(b4 & 4u)) br = T(0);
@@ -628,38 +673,39 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         v[u] = mk<T>(ar - bi, ai + br);   // C' = A' + i B'
       }
     }
-    tl.flip();
+    tl.done();
   }
   // Main-tile magnitude max, and one vote over all lanes (a warp can span
   // several tiles when tiles are small, so the vote is outside any branch
   // that depends on the tile).
   AbsMax<T> tm;
 #pragma unroll
-  for (int u = 0; u < 8; ++u) { tm.add(v[u].x); tm.add(v[u].y); }
+  for (int u = 0; u < V; ++u) { tm.add(v[u].x); tm.add(v[u].y); }
   const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
   if (!c.mirror) {
-    if (c.valid) { mx = tm; bad = nan_probe<T>(v); }
+    if (c.valid) { mx = tm; bad = nan_probe<T, V>(v); }
     if (use_mask) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (!((bits >> (2 * u)) & 1u)) v[u].x = T(0);
-        if (!((bits >> (2 * u + 1)) & 1u)) v[u].y = T(0);
+      for (int u = 0; u < V; ++u) {
+        const uint32_t b2 = mb.template get<2>(u);
+        if (!(b2 & 1u)) v[u].x = T(0);
+        if (!(b2 & 2u)) v[u].y = T(0);
       }
     } else if (clip && (rec || need_clip)) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < V; ++u) {
         const T x = v[u].x, y = v[u].y;
         const T cx = clampT(x, Ds), cy = clampT(y, Ds);
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
-        bits |= ((uint32_t)ix << (2 * u)) | ((uint32_t)iy << (2 * u + 1));
+        mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
         v[u] = mk<T>(cx, cy);
       }
     } else if (clip) {
-      bits = 0xffffu;   // nothing clipped
+      mb.fill();   // nothing clipped
     }
   }
-  if (rec && c.live) a.mask[tile * G_::TPT + tid] = bits;
+  if (rec && c.live) mb.store(a.mask, mthr);
   if (!use_mask) {
     unsigned long long vb = mx.dbits(bad), cc = cnt;
     block_max_count(vb, cc, count, s_red);
@@ -669,19 +715,14 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
     }
   }
   if (a.mode & M_NOWRITE) return;
-  fft_pencil<T, L, +1>(v, j, jb, twg, tl);
+  fft_pencil<T, L, +1>(v, j, twg, tl);
 }
 
 // Check / f-clip pass along the outermost axis (z in 3D, y in 2D): forward
 // FFT completes the spectrum; the violation max over all bins is reduced
 // (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
-// the inverse FFT of this axis is applied before the store.
-//
-// Tiles are of two kinds.  Main tiles: W consecutive kx at one middle index
-// (slot kx = 0 skipped).  Mirror tiles: the kx = 0 pencils, in pairs (m, -m)
-// of middle indices so that A and B can be separated; a pencil that is its
-// own mirror (m = 0 or Nmid/2) fills both slots of its pair and only the
-// first slot stores.
+// the inverse FFT of this axis is applied before the store.  Tiles: see
+// ChkTile.
 template <typename T, int L, int W_ = TileW<T>::value>
 __global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
 k_chk(Args a) {
@@ -689,22 +730,22 @@ k_chk(Args a) {
   constexpr int W = G_::W, NT = G_::NT;
   const int M = a.g.M, Nmid = a.g.Nmid;
   const ChkTile c = chk_decode<W>(tile, w, M, Nmid);
-  const int estride = Nmid * M;
+  const int64_t estride = (int64_t)Nmid * M;
   const int64_t ustride = (int64_t)NT * estride;
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + c.off + j * estride;
-  v2<T> v[8];
+  v2<T> v[V];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) v[u] = in[u * ustride];
-  load_tables<T>(s_tw, a.tw, Sched<L>::twsize, nullptr, nullptr, 0);   // overlaps the loads
+  for (int u = 0; u < V; ++u) v[u] = in[u * ustride];
+  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
   const int nmain = Nmid * (M / W);
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
-  chk_core<T, L, TL>(a, p, st, v, j, jb, w, tid, tile, c, cta_has_mirror, tl, s_tw, s_red);
+  chk_core<T, L, TL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
-  for (int u = 0; u < 8; ++u) out[u * ustride] = v[u];
+  for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
 }
 
 // ---------------------------------------------------------------------------
