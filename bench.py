@@ -42,12 +42,10 @@ FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
 
 # DRAM bytes (read + write) per launch from one ncu capture of these kernels
 # at 512^3 (profiles/); a kernel changed since its capture must be removed.
-NCU_TRAFFIC = {
-    "xfwd<f64,256>": 537027072 + 1016915000,
-    "chk<f32,512>": 565569536 + 506454272,
-    "px<f32,256>": 536921856 + 480724736,
-}
-NCU_FP64_PIPE = {"xfwd<f64,256>": 0.854}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# at 512^3 (profiles/); an entry is removed when its kernel changes.
+NCU_TRAFFIC = {}
+NCU_FP64_PIPE = {}
 
 
 def load_peaks():
@@ -73,6 +71,49 @@ def make_workload(name):
 
 
 # ---------------------------------------------------------------- clocks
+class _NvmlC:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes)."""
+
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.c.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(self.c.c_uint(i), self.c.byref(h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex_v2 failed")
+        return h
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        v = self.c.c_uint()
+        if self.lib.nvmlDeviceGetClockInfo(h, self.c.c_int(kind), self.c.byref(v)) != 0:
+            raise RuntimeError("nvmlDeviceGetClockInfo failed")
+        return v.value
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        v = self.c.c_uint()
+        if self.lib.nvmlDeviceGetMaxClockInfo(h, self.c.c_int(kind), self.c.byref(v)) != 0:
+            raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
+        return v.value
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.c.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        if fn(h, self.c.byref(v)) != 0:
+            raise RuntimeError("clock event reasons query failed")
+        return v.value
+
+
 class Clocks:
     """SM clocks and throttle reasons sampled DURING a region (read-only).
 
@@ -92,21 +133,25 @@ class Clocks:
         self.samples = []
         self.stop_evt = threading.Event()
         self.nvml = None
-        try:
-            import pynvml
-            pynvml.nvmlInit()
-            # the CUDA ordinal of this process maps to the NVML index through
-            # CUDA_VISIBLE_DEVICES when it is set
-            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-            idx = dev
-            if vis:
-                ids = [x.strip() for x in vis.split(",") if x.strip()]
-                if dev < len(ids) and ids[dev].isdigit():
-                    idx = int(ids[dev])
-            self.handle = pynvml.nvmlDeviceGetHandleByIndex(idx)
-            self.nvml = pynvml
-        except Exception:
-            self.nvml = None
+        self.err = None
+        # the CUDA ordinal of this process maps to the NVML index through
+        # CUDA_VISIBLE_DEVICES when it is set
+        idx = dev
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            ids = [x.strip() for x in vis.split(",") if x.strip()]
+            if dev < len(ids) and ids[dev].isdigit():
+                idx = int(ids[dev])
+        for make in (lambda: __import__("pynvml"), _NvmlC):
+            try:
+                n = make()
+                if hasattr(n, "nvmlInit"):
+                    n.nvmlInit()
+                self.handle = n.nvmlDeviceGetHandleByIndex(idx)
+                self.nvml = n
+                break
+            except Exception as ex:   # try the next binding, else nvidia-smi
+                self.err = f"{type(ex).__name__}: {ex}"
 
     def _poll(self):
         n = self.nvml
@@ -147,7 +192,8 @@ class Clocks:
                     "sm_max_mhz": max(smax) if smax else None,
                     "reasons": reasons, "samples": len(sm), "source": "nvml"}
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "nvml_error": self.err}
         self.proc.terminate()
         self.proc.wait(timeout=10)
         self.f.flush()
@@ -166,7 +212,8 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi",
+                "nvml_error": self.err}
 
 
 # ---------------------------------------------------------------- oracle arm

@@ -4,6 +4,8 @@
 // (Sec. IV-D): every step runs in the kernels of passes.cuh; the host only
 // sequences launches, replays loop chunks as CUDA graphs and reads one
 // 4-byte "items still running" counter between chunks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,14 +73,14 @@ std::vector<v2<T>> r2c_table(int Nx) {
 }
 
 // Stage-2 twiddles of the two-stage split of L (layout in fft_core.cuh):
-// entry k1 * R2 + t - 1 = exp(-2 pi i k1 t / L), k1 < R1, t = 1..R2-1.
+// exp(-2 pi i k1 t / L), k1 < R1, t = 1..R2-1, at tw_index(R1, k1, t).
 template <typename T>
 std::vector<v2<T>> stage_table_rt(int L) {
   const int R1 = f2_nt(L), R2 = L / R1;
   std::vector<v2<T>> t(L);
   for (auto& x : t) { x.x = 0; x.y = 0; }
   for (int k1 = 0; k1 < R1; ++k1)
-    for (int tt = 1; tt < R2; ++tt) t[k1 * R2 + tt - 1] = root<T>((long double)k1 * tt, (long double)L);
+    for (int tt = 1; tt < R2; ++tt) t[tw_index(R1, k1, tt)] = root<T>((long double)k1 * tt, (long double)L);
   return t;
 }
 
@@ -91,6 +93,12 @@ struct DevGroup {
   // strided passes (y, chk, 1D column) 4 or 8; contiguous passes (x, 1D
   // row) 32/NT or 64/NT (a tile of one or two warps); set at plan creation
   int wx = 0, wa = 8, wc = 8, w1c = 8, w1r = 0;
+  // TMA tensor maps of the float32 spectrum buffers (device arrays of
+  // 2 x count maps, [2 gi + buffer]) for the y pass and the check pass;
+  // null where the TMA-fed kernels do not apply
+  const CUtensorMap* tm_axis = nullptr;
+  const CUtensorMap* tm_chk = nullptr;
+  std::vector<int64_t> h_soff;   // host copy of the members' spectrum offsets
   // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
   int P1 = 0, P2 = 0;
   const void* twp32 = nullptr;
@@ -148,6 +156,9 @@ struct ffcz_plan_s {
   ItemState* d_st2 = nullptr;   // adjoint state
   int* d_nactive = nullptr;
   int* h_nactive = nullptr;     // pinned
+  int* d_err = nullptr;         // device error word (DevErr), cleared per call
+  int* h_err = nullptr;         // pinned copy
+  int num_sms = 148;
   ItemState* h_st = nullptr;    // pinned
   ItemParams* h_prm = nullptr;  // pinned
   size_t ws_bytes = 0;
@@ -318,11 +329,44 @@ void launch_axis_tw(const Args& a, int Nz, int M, int count, cudaStream_t s) {
   k_axis<T, L, DIR, W><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
+// Persistent TMA-fed variants (float32, 8-pencil tiles, L >= 256): CTAs
+// per SM slot and per item as picked at plan time.
+int g_num_sms = 148;   // set from the device at plan creation
+constexpr int kTmaCtasPerSm = TmaGeo<256, 8>::MINB;   // the kernels' launch bound
+inline unsigned tma_grid_x(int64_t tiles, int count) {
+  const int64_t want = ((int64_t)kTmaCtasPerSm * g_num_sms + count - 1) / count;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, want));
+}
+template <int L>
+constexpr bool tma_ok() { return Geo<float, L, 8>::G == 1; }
+
+template <int L, int DIR>
+void launch_axis_tma(const Args& a, int Nz, int M, int count, cudaStream_t s) {
+  const int64_t tiles = (int64_t)Nz * (M / 8);
+  const size_t sm = TmaGeo<L, 8>::bytes;
+  if (g_dry) { set_smem(k_axis_tma<L, DIR, 8>, sm); return; }
+  ProfScope ps(DIR < 0 ? "axis_fwd" : "axis_inv", 32, L, s);
+  k_axis_tma<L, DIR, 8><<<dim3(tma_grid_x(tiles, count), (unsigned)count), Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+template <int L>
+void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+  const int64_t tiles = chk_ntiles(8, M, Nmid);
+  const size_t sm = TmaGeo<L, 8>::bytes;
+  if (g_dry) { set_smem(k_chk_tma<L, 8>, sm); return; }
+  ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk", 32, L, s);
+  k_chk_tma<L, 8><<<dim3(tma_grid_x(tiles, count), (unsigned)count), Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+
 template <typename T, int DIR>
 struct AL {
   template <int L>
   static void go(int w, const Args& a, int Nz, int M, int count, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+      if constexpr (tma_ok<L>()) {
+        if (w < 0 && (a.tm_axis || g_dry)) { launch_axis_tma<L, DIR>(a, Nz, M, count, s); return; }
+      }
       if (w == 4) launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
       else launch_axis_tw<T, L, DIR, 8>(a, Nz, M, count, s);
     } else {
@@ -353,6 +397,9 @@ struct CL {
   template <int L>
   static void go(int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+      if constexpr (tma_ok<L>()) {
+        if (w < 0 && (a.tm_chk || g_dry)) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
+      }
       if (w == 4) launch_chk_tw<T, L, 4>(a, Nmid, M, count, s);
       else launch_chk_tw<T, L, 8>(a, Nmid, M, count, s);
     } else {
@@ -428,15 +475,80 @@ void launch_row1(int L, int w, const Args& a, int P1, int count, cudaStream_t s)
 // every tile (tiles x threads per tile x words per thread).
 inline int64_t mask_words_per_thread(int L) { return (f2_v(L) + 7) / 8; }
 inline int64_t x_words(int M, int64_t rows, int W) {
+  W = std::abs(W);
   const int64_t tiles = (rows + W - 1) / W;
   return tiles * (int64_t)f2_nt(M) * W * mask_words_per_thread(M);
 }
 inline int64_t chkw(int L, int Nmid, int M, int W) {
+  W = std::abs(W);   // the TMA-fed variant (-8) tiles like the 8-pencil one
   return (int64_t)chk_ntiles(W, M, Nmid) * f2_nt(L) * W * mask_words_per_thread(L);
 }
 
 // ----- argument construction ------------------------------------------------
 int cnt_flag(const ffcz_plan_s* p) { return p->opts.count_active ? M_COUNT : 0; }
+
+// ----- TMA tensor maps ------------------------------------------------------
+// The encoder is the driver's cuTensorMapEncodeTiled, reached through the
+// runtime's entry-point query (no link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2D view [outer][inner] of 8-byte elements (one complex64 each) at base,
+// row pitch inner * 8 bytes, boxes of boxw x boxr elements.
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t boxw,
+               uint32_t boxr) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) || (inner * 8) % 16 || inner < boxw || outer < boxr) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 8};
+  cuuint32_t box[2] = {boxw, boxr};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Maps of both float32 spectrum buffers for every member of every 2D/3D
+// group: the y pass reads tiles of the [Nz Ny][M] view, the check pass of
+// the [Nz][Nmid M] view, in boxes of 8 pencils x min(L, 256) rows.  The
+// TMA-fed kernels exist for pencil lengths L >= 256 (tiles of one CTA).
+void build_tensor_maps(ffcz_plan_s* p) {
+  for (auto& dg : p->groups) {
+    if (dg.ndim == 1) continue;
+    const int Nmid = dg.ndim == 3 ? dg.Ny : 1;
+    for (int kind = 0; kind < 2; ++kind) {
+      if (kind == 0 && dg.ndim != 3) continue;
+      const int L = kind == 0 ? dg.Ny : dg.Nz;
+      if (L < 256) continue;
+      std::vector<CUtensorMap> maps(2 * (size_t)dg.count);
+      bool ok = true;
+      for (int gi = 0; gi < dg.count && ok; ++gi)
+        for (int b = 0; b < 2 && ok; ++b) {
+          const char* base = static_cast<const char*>(p->B32[b]) + dg.h_soff[gi] * 8;
+          const uint32_t rows = (uint32_t)std::min(L, 256);
+          ok = kind == 0 ? encode_2d(&maps[2 * gi + b], base, (uint64_t)dg.M, (uint64_t)dg.Nz * dg.Ny, 8, rows)
+                         : encode_2d(&maps[2 * gi + b], base, (uint64_t)Nmid * dg.M, (uint64_t)dg.Nz, 8, rows);
+        }
+      if (!ok) continue;
+      void* d = dalloc(p, sizeof(CUtensorMap) * maps.size());
+      CK(cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+      (kind == 0 ? dg.tm_axis : dg.tm_chk) = static_cast<const CUtensorMap*>(d);
+    }
+  }
+}
 
 template <typename T>
 Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState* st) {
@@ -449,6 +561,11 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   a.pred = P_ACTIVE;
   a.sel_in = a.sel_out = S_CUR;
   a.ckpt_every = 0;
+  a.err = p->d_err;
+  if (sizeof(T) == 4 && b0 == p->B32[0] && b1 == p->B32[1]) {
+    a.tm_axis = dg.tm_axis;
+    a.tm_chk = dg.tm_chk;
+  }
   return a;
 }
 
@@ -904,10 +1021,21 @@ __global__ void k_set_repairs(ItemState* st, int n, int round) {
   if (!st[i].certified) st[i].repairs = round;
 }
 
+void check_dev_err(ffcz_plan_s* p) {
+  if (*p->h_err == DERR_NONE) return;
+  const int e = *p->h_err;
+  *p->h_err = 0;
+  CK(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
+  if (e == DERR_TMA_TIMEOUT) fail(FFCZ_ERR_TIMEOUT, "a TMA tile load did not complete within its poll limit");
+  fail(FFCZ_ERR_CUDA, "a TMA staging buffer was not 128-byte aligned");
+}
+
 void fill_stats(ffcz_plan_s* p, ffcz_stats* out, float ms, float ms_cert, bool certified_run) {
   CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(ItemState) * p->batch, cudaMemcpyDeviceToHost,
                      p->stream));
+  CK(cudaMemcpyAsync(p->h_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
+  check_dev_err(p);
   if (p->count_pending) {
     g_launches += (int64_t)(*p->h_loopcount) * p->pending_bodies_per;
     p->count_pending = false;
@@ -970,6 +1098,7 @@ void free_plan(ffcz_plan_s* p) {
   for (void* a : p->allocs) cudaFree(a);
   if (p->h_nactive) cudaFreeHost(p->h_nactive);
   if (p->h_loopcount) cudaFreeHost(p->h_loopcount);
+  if (p->h_err) cudaFreeHost(p->h_err);
   if (p->h_st) cudaFreeHost(p->h_st);
   if (p->h_prm) cudaFreeHost(p->h_prm);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -1234,10 +1363,11 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
 namespace {
 
 // ----- tile-width tuner ----------------------------------------------------------
-// For every group and float32 pass kind, time the two tile widths of the
-// pass (strided passes: 4 and 8 pencils; contiguous passes: tiles of one and
-// two warps) on the plan's own buffers (three launches each after one
-// warm-up, CUDA events) and keep the faster.  Results can be cached in a text file named by
+// For every group and float32 pass kind, time the variants of the pass
+// (strided passes: 4- and 8-pencil tiles and, for lengths >= 256, the
+// persistent TMA-fed kernel, code -8; contiguous passes: tiles of one and two
+// warps) on the plan's own buffers (three launches each after one warm-up,
+// CUDA events) and keep the fastest.  Results can be cached in a text file named by
 // FFCZ_TUNE_CACHE (lines "key width"); FFCZ_TUNE=0 keeps the defaults.
 std::map<std::string, int>& tune_table() {
   static std::map<std::string, int> t;
@@ -1282,25 +1412,57 @@ float time_launches(ffcz_plan_s* p, F&& f) {
   return ms;
 }
 
+// FFCZ_TUNE_FORCE="kind=w,..." (kinds px, axis, chk, col1, row1) fixes a
+// pass's variant for plans created while it is set, if w is one of the
+// pass's candidates.
+int forced_width(const std::string& key, const std::vector<int>& cand) {
+  const char* f = getenv("FFCZ_TUNE_FORCE");
+  if (!f) return 0;
+  const std::string kind = key.substr(0, key.find('_'));
+  std::string spec(f);
+  size_t pos = 0;
+  while (pos < spec.size()) {
+    size_t end = spec.find(',', pos);
+    if (end == std::string::npos) end = spec.size();
+    const std::string item = spec.substr(pos, end - pos);
+    const size_t eq = item.find('=');
+    if (eq != std::string::npos && item.substr(0, eq) == kind) {
+      const int w = atoi(item.c_str() + eq + 1);
+      if (std::find(cand.begin(), cand.end(), w) != cand.end()) return w;
+    }
+    pos = end + 1;
+  }
+  return 0;
+}
+
+thread_local bool g_no_tune = false;   // FFCZ_TUNE=0: keep the defaults
+
 template <typename F>
-int pick_width(ffcz_plan_s* p, const std::string& key, int wa, int wb, F&& run_w) {
+int pick_width(ffcz_plan_s* p, const std::string& key, int dflt, std::vector<int> cand, F&& run_w) {
+  if (const int w = forced_width(key, cand)) return w;
+  if (g_no_tune) return dflt;
   {
     std::lock_guard<std::mutex> lk(tune_mu());
     tune_load();
     auto it = tune_table().find(key);
-    if (it != tune_table().end() && (it->second == wa || it->second == wb)) return it->second;
+    if (it != tune_table().end() && std::find(cand.begin(), cand.end(), it->second) != cand.end())
+      return it->second;
   }
-  const float ta = time_launches(p, [&] { run_w(wa); });
-  const float tb = time_launches(p, [&] { run_w(wb); });
-  const int w = ta <= tb ? wa : wb;
+  int best = cand[0];
+  float tbest = 0.f;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    const float t = time_launches(p, [&] { run_w(cand[i]); });
+    if (i == 0 || t < tbest) { tbest = t; best = cand[i]; }
+  }
   std::lock_guard<std::mutex> lk(tune_mu());
-  tune_store(key, w);
-  return w;
+  tune_store(key, best);
+  return best;
 }
 
 void tune(ffcz_plan_s* p) {
   const char* env = getenv("FFCZ_TUNE");
-  if (env && env[0] == '0') return;
+  g_no_tune = env && env[0] == '0';
+  if (g_no_tune && !getenv("FFCZ_TUNE_FORCE")) return;
   cudaStream_t s = p->stream;
   for (auto& dg : p->groups) {
     char base[160];
@@ -1309,32 +1471,34 @@ void tune(ffcz_plan_s* p) {
     Args a = make_args<float>(p, dg, p->B32[0], p->B32[1], p->d_st);
     a.pred = P_ALL;
     if (dg.ndim == 1) {
-      dg.w1c = pick_width(p, std::string("col1_") + base, 4, 8, [&](int w) {
+      dg.w1c = pick_width(p, std::string("col1_") + base, dg.w1c, {4, 8}, [&](int w) {
         Args b = a;
         col1_args<float>(p, b, dg, OP1_SCLIP);
         b.mode = 0;
         launch_col1<float>(dg.P1, w, b, dg.P2, dg.count, s);
       });
-      dg.w1r = pick_width(p, std::string("row1_") + base, row_w1(dg.P2), row_w2(dg.P2), [&](int w) {
+      dg.w1r = pick_width(p, std::string("row1_") + base, dg.w1r, {row_w1(dg.P2), row_w2(dg.P2)}, [&](int w) {
         Args b = a;
         row1_args<float>(p, b, dg, OP1_FWD);
         launch_row1<float>(dg.P2, w, b, dg.P1, dg.count, s);
       });
       continue;
     }
-    dg.wx = pick_width(p, std::string("px_") + base, row_w1(dg.M), row_w2(dg.M), [&](int w) {
+    dg.wx = pick_width(p, std::string("px_") + base, dg.wx, {row_w1(dg.M), row_w2(dg.M)}, [&](int w) {
       Args b = a;
       tabs_x<float>(p, b, dg);
       b.mode = 0;
       launch_x<float>(XPX, dg.M, w, b, dg.rows, dg.count, s);
     });
     if (dg.ndim == 3)
-      dg.wa = pick_width(p, std::string("axis_") + base, 4, 8, [&](int w) {
+      dg.wa = pick_width(p, std::string("axis_") + base, dg.wa,
+                         dg.tm_axis ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, [&](int w) {
         Args b = a;
         b.tw = tw_of<float>(p->tb, dg.Ny);
         launch_axis<float, -1>(dg.Ny, w, b, dg.Nz, dg.M, dg.count, s);
       });
-    dg.wc = pick_width(p, std::string("chk_") + base, 4, 8, [&](int w) {
+    dg.wc = pick_width(p, std::string("chk_") + base, dg.wc,
+                       dg.tm_chk ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, [&](int w) {
       Args b = a;
       b.tw = tw_of<float>(p->tb, dg.Nz);
       b.mode = 0;
@@ -1342,7 +1506,9 @@ void tune(ffcz_plan_s* p) {
     });
   }
   CK(cudaMemsetAsync(p->d_st, 0, sizeof(ItemState) * p->batch, s));
+  CK(cudaMemcpyAsync(p->h_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  check_dev_err(p);
 }
 
 }  // namespace
@@ -1409,6 +1575,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->opts = o;
     p->stream = (cudaStream_t)cuda_stream;
     CK(cudaGetDevice(&p->device));
+    CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    g_num_sms = p->num_sms;
     p->eoff.resize(batch);
     std::vector<int64_t> soff_c(batch);
     int64_t off = 0, offc = 0;
@@ -1515,6 +1683,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       dg.g.item = d_it;
       dg.g.eoff = d_eo;
       dg.g.soff = d_so;
+      dg.h_soff = so;
       p->groups.push_back(dg);
     }
     // Set the shared-memory attributes of every kernel the plan can launch
@@ -1523,9 +1692,10 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     try {
       Args a{};
       for (const auto& dg0 : p->groups) {
-        for (int alt = 0; alt < 2; ++alt) {
+        for (int alt = 0; alt < 3; ++alt) {
           DevGroup dg = dg0;
-          dg.wa = dg.wc = dg.w1c = alt ? 8 : 4;
+          dg.wa = dg.wc = alt == 2 ? -8 : alt ? 8 : 4;
+          dg.w1c = alt ? 8 : 4;
           dg.wx = alt ? row_w2(dg.M) : row_w1(dg.M);
           dg.w1r = alt ? row_w2(dg.M) : row_w1(dg.M);
           if (ndim == 1) {
@@ -1553,10 +1723,14 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     // float32 spectrum buffers: N/2 complex64 each (4 bytes per point)
     p->B32[0] = dalloc(p.get(), sizeof(float2) * p->total_c);
     p->B32[1] = dalloc(p.get(), sizeof(float2) * p->total_c);
+    build_tensor_maps(p.get());
     p->d_prm = (ItemParams*)dalloc(p.get(), sizeof(ItemParams) * batch);
     p->d_st = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
+    p->d_err = (int*)dalloc(p.get(), sizeof(int));
+    CK(cudaMemset(p->d_err, 0, sizeof(int)));
+    CK(cudaMallocHost(&p->h_err, sizeof(int)));
     p->d_loopcount = (int*)dalloc(p.get(), sizeof(int));
     CK(cudaMemset(p->d_st, 0, sizeof(ItemState) * batch));
     CK(cudaMemset(p->d_st2, 0, sizeof(ItemState) * batch));

@@ -29,9 +29,12 @@
 // The transform is the unnormalised DFT of Eq. 1, X_k = sum_n x_n w^{nk},
 // w = exp(DIR 2 pi i / L), DIR = -1 forward, +1 inverse (no 1/L).
 //
-// Twiddle table of length L: entry k1 * R2 + t - 1 holds exp(-2 pi i k1 t / L)
-// for k1 < R1 and t = 1..R2-1 (computed on the host in long double and
-// rounded once; the inverse uses the conjugates).
+// Twiddle table of length L: exp(-2 pi i k1 t / L) for k1 < R1, t = 1..R2-1
+// at entry tw_index(k1, t) = ((t-1)/2) 2 R1 + 2 k1 + (t-1)%2: factors t and
+// t+1 of one k1 are adjacent (one 128-bit load in float32) and, for a fixed
+// pair, the k1 of consecutive threads are consecutive, so a warp's loads hit
+// distinct banks.  Computed on the host in long double and rounded once; the
+// inverse uses the conjugates.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -212,6 +215,10 @@ struct F2 {
 // Host-side values of the same split.
 inline int f2_nt(int L) { return 1 << (ilog2(L) / 2); }
 inline int f2_v(int L) { return L / f2_nt(L); }
+// Table entry of factor t (1 <= t < R2) of stage-2 row k1 (layout above).
+__host__ __device__ constexpr int tw_index(int R1, int k1, int t) {
+  return ((t - 1) >> 1) * 2 * R1 + 2 * k1 + ((t - 1) & 1);
+}
 
 // Pencils per tile of the strided passes: 64-byte rows (8 float32 or 4
 // float64 complex values).
@@ -265,18 +272,17 @@ __device__ __forceinline__ void fft_pencil(v2<T> (&v)[F2<L>::V], int j, const v2
 #pragma unroll
   for (int t = 0; t < R2; ++t) v[t] = buf[(j + t * (R1 + 1)) * W];
   tl.done();
-  const v2<T>* twj = tw + j * R2;
   if constexpr (sizeof(T) == 4) {
-    const float4* q = reinterpret_cast<const float4*>(twj);
+    const float4* q = reinterpret_cast<const float4*>(tw) + j;
 #pragma unroll
     for (int i = 0; i < R2 / 2; ++i) {
-      const float4 f = q[i];
+      const float4 f = q[i * R1];   // factors 2i+1, 2i+2 of row j
       v[2 * i + 1] = twmul<T, DIR>(v[2 * i + 1], mk<T>(f.x, f.y));
       if (2 * i + 2 < R2) v[2 * i + 2] = twmul<T, DIR>(v[2 * i + 2], mk<T>(f.z, f.w));
     }
   } else {
 #pragma unroll
-    for (int t = 1; t < R2; ++t) v[t] = twmul<T, DIR>(v[t], twj[t - 1]);
+    for (int t = 1; t < R2; ++t) v[t] = twmul<T, DIR>(v[t], tw[tw_index(R1, j, t)]);
   }
   dftN<R2, T, DIR>(v);
 }

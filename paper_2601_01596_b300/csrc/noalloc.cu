@@ -78,7 +78,7 @@ void stage_factors_rt(int L, std::vector<double2>& out) {
   const int R1 = f2_nt(L), R2 = L / R1;
   out.assign(L, make_double2(0.0, 0.0));
   for (int k1 = 0; k1 < R1; ++k1)
-    for (int t = 1; t < R2; ++t) out[k1 * R2 + t - 1] = root64((long double)k1 * t, (long double)L);
+    for (int t = 1; t < R2; ++t) out[tw_index(R1, k1, t)] = root64((long double)k1 * t, (long double)L);
 }
 
 template <typename K>

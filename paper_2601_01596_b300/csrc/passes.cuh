@@ -29,6 +29,7 @@
 #include <math.h>
 
 #include "fft_core.cuh"
+#include "tma.cuh"
 
 namespace ffcz {
 
@@ -87,6 +88,12 @@ struct Args {
   const void* bt;          // 1D: FFT of the wrapped chirp, [k1][k2] order, per item at soff
   const void* chirp;       // 1D: chirps b_n, n < N, per item at eoff
   int op1;                 // 1D pass operation (Op1)
+  // 2D tensor maps of the float32 spectrum buffers for the TMA-fed passes,
+  // two per group member ([2 gi + buffer]); null when the pass's buffers are
+  // not the plan's float32 pair
+  const CUtensorMap* tm_axis;
+  const CUtensorMap* tm_chk;
+  int* err;                // device error word (DevErr)
 };
 
 __device__ __forceinline__ bool pred_ok(int pred, const ItemState& s, const ItemParams& p) {
@@ -631,7 +638,9 @@ template <typename T, int L, class TL>
 __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st,
                                          v2<T> (&v)[F2<L>::V], int j, int w, int64_t mthr,
                                          const ChkTile& c, bool cta_has_mirror, TL& tl,
-                                         const v2<T>* twg, unsigned long long* s_red) {
+                                         const v2<T>* twg, unsigned long long* s_red,
+                                         unsigned long long* acc_vb = nullptr,
+                                         unsigned long long* acc_cnt = nullptr) {
   constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
   fft_pencil<T, L, -1>(v, j, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
@@ -706,7 +715,11 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
     }
   }
   if (rec && c.live) mb.store(a.mask, mthr);
-  if (!use_mask) {
+  if (acc_vb) {
+    // persistent callers reduce once per CTA after their last tile
+    *acc_vb = max(*acc_vb, mx.dbits(bad));
+    *acc_cnt += cnt;
+  } else if (!use_mask) {
     unsigned long long vb = mx.dbits(bad), cc = cnt;
     block_max_count(vb, cc, count, s_red);
     if (threadIdx.x == 0) {
@@ -746,6 +759,161 @@ k_chk(Args a) {
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
   for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
+}
+
+// ---------------------------------------------------------------------------
+// Persistent float32 strided passes fed by TMA
+// ---------------------------------------------------------------------------
+//
+// One CTA per SM slot loops over the tiles of its item; while it transforms
+// tile t, the copy engine loads tile t + gridDim.x into the staging buffer,
+// so the DRAM latency of a tile hides behind the arithmetic of the previous
+// one.  Shared memory: [staging L x W][tile buffer][twiddles][reduction],
+// the staging buffer at a 128-byte aligned address.  Tiles of one CTA only
+// (G = 1).
+
+template <int L, int W>
+struct TmaGeo {
+  using G_ = Geo<float, L, W>;
+  static_assert(G_::G == 1, "TMA-fed passes use one tile per CTA");
+  static constexpr int BOX = L < 256 ? L : 256;        // rows per box
+  static constexpr int MINB = 2;                       // CTAs per SM the grid is sized for
+  static constexpr size_t stage = (size_t)L * W * sizeof(float2);
+  static constexpr size_t bytes =
+      128 + stage + (size_t)Tile<float, L, W>::ELEMS * sizeof(float2) + (size_t)L * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
+};
+
+#define FFCZ_TMA_PROLOGUE(L_, W_)                                                        \
+  using G_ = Geo<float, L_, W_>;                                                         \
+  using TL = Tile<float, L_, W_>;                                                        \
+  using TG = TmaGeo<L_, W_>;                                                             \
+  constexpr int V = G_::V, NT = G_::NT;                                                  \
+  extern __shared__ __align__(16) unsigned char smraw[];                                 \
+  const uint32_t s0_ = smem_addr(smraw);   /* staging rounded up to 128 bytes below */   \
+  float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0_ + 127u) & ~127u) - s0_));  \
+  float2* s_tiles = s_stage + L_ * W_;                                                   \
+  float2* s_tw = s_tiles + TL::ELEMS;                                                    \
+  unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_tw + L_);         \
+  __shared__ __align__(8) uint64_t bar;                                                  \
+  const int gi = blockIdx.y;                                                             \
+  const int item = a.g.item[gi];                                                         \
+  const ItemParams& p = a.prm[item];                                                     \
+  ItemState& st = a.st[item];                                                            \
+  if (!pred_ok(a.pred, st, p)) return;                                                   \
+  const int t_it = st.t;                                                                 \
+  const int tid = threadIdx.x, w = tid % W_, j = tid / W_;                               \
+  const int bin = (a.sel_in == S_CUR) ? (t_it & 1) : ((t_it - 1) & 1);                   \
+  if ((smem_addr(s_stage) & 127u) != 0u) {                                               \
+    if (tid == 0) atomicExch(a.err, DERR_TMA_ALIGN);                                     \
+    return;                                                                              \
+  }                                                                                      \
+  load_tables<float>(s_tw, a.tw, L_, nullptr, nullptr, 0);                               \
+  if (tid == 0) mbar_init(&bar, 1);                                                      \
+  __syncthreads();                                                                       \
+  uint32_t parity = 0;                                                                   \
+  (void)p; (void)NT; (void)s_red;
+
+// Wait for the staging buffer, copy it to registers, release it and start
+// the load of the next tile.  Returns false (uniformly) after a timeout.
+#define FFCZ_TMA_TAKE(ISSUE_NEXT)                                                        \
+  {                                                                                      \
+    const bool ok_ = mbar_wait_bounded(&bar, parity, kTmaPollLimit);                     \
+    if (__syncthreads_or(!ok_)) {                                                        \
+      if (tid == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);                                 \
+      mbar_wait_bounded(&bar, parity, kTmaPollLimit); /* copies still in flight */       \
+      return;                                                                            \
+    }                                                                                    \
+    _Pragma("unroll") for (int u = 0; u < V; ++u) v[u] = s_stage[(j + u * NT) * W + w]; \
+    __syncthreads();                                                                     \
+    if (tid == 0) { ISSUE_NEXT; }                                                        \
+    parity ^= 1u;                                                                        \
+  }
+
+template <int L, int DIR, int W>
+__global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
+k_axis_tma(Args a) {
+  FFCZ_TMA_PROLOGUE(L, W)
+  const int M = a.g.M;
+  const int tpr = M / W;
+  const int ntiles = a.g.Nz * tpr;
+  const CUtensorMap* map = a.tm_axis + 2 * gi + bin;
+  // tile t: pencils kx0..kx0+W-1 of plane z; rows z L + y of the [Nz L][M] view
+  auto issue = [&](int t) {
+    const int x = (t % tpr) * W, y0 = (t / tpr) * L;
+    mbar_arrive_expect_tx(&bar, (uint32_t)TG::stage);
+#pragma unroll
+    for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_stage + b * TG::BOX * W, map, x, y0 + b * TG::BOX, &bar);
+  };
+  int tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile);
+  float2* outb = pick<float>(a, a.sel_out, t_it) + a.g.soff[gi];
+  while (tile < ntiles) {
+    const int next = tile + gridDim.x;
+    float2 v[V];
+    FFCZ_TMA_TAKE(if (next < ntiles) { fence_proxy_async_smem(); issue(next); })
+    TL tl{s_tiles + w, false};
+    fft_pencil<float, L, DIR>(v, j, s_tw, tl);
+    const int z = tile / tpr, kx = (tile % tpr) * W + w;
+    float2* out = outb + (int64_t)z * L * M + kx + (int64_t)j * M;
+#pragma unroll
+    for (int u = 0; u < V; ++u) out[(int64_t)u * NT * M] = v[u];
+    __syncthreads();   // the tile buffer is reused by the next tile
+    tile = next;
+  }
+}
+
+template <int L, int W>
+__global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
+k_chk_tma(Args a) {
+  FFCZ_TMA_PROLOGUE(L, W)
+  const int M = a.g.M, Nmid = a.g.Nmid;
+  const int tpr = M / W;
+  const int nmain = Nmid * tpr;
+  const int ntot = chk_ntiles(W, M, Nmid);
+  const int64_t estride = (int64_t)Nmid * M;
+  const CUtensorMap* map = a.tm_chk + 2 * gi + bin;
+  // main tile t: pencils kx0..kx0+W-1 at middle index mid; [Nz][Nmid M] view
+  auto issue = [&](int t) {
+    const int x = (t / tpr) * M + (t % tpr) * W;
+    mbar_arrive_expect_tx(&bar, (uint32_t)TG::stage);
+#pragma unroll
+    for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_stage + b * TG::BOX * W, map, x, b * TG::BOX, &bar);
+  };
+  int tile = blockIdx.x;
+  if (tid == 0 && tile < nmain) issue(tile);
+  const float2* inb = pick<float>(a, a.sel_in, t_it) + a.g.soff[gi];
+  float2* outb = pick<float>(a, a.sel_out, t_it) + a.g.soff[gi];
+  unsigned long long acc_vb = 0ull, acc_cnt = 0ull;
+  while (tile < ntot) {
+    const int next = tile + gridDim.x;
+    const ChkTile c = chk_decode<W>(tile, w, M, Nmid);
+    float2 v[V];
+    if (tile < nmain) {
+      FFCZ_TMA_TAKE(if (next < nmain) { fence_proxy_async_smem(); issue(next); })
+    } else {
+      // kx = 0 mirror pencils are not one box: plain loads
+      const float2* in = inb + c.off + j * estride;
+#pragma unroll
+      for (int u = 0; u < V; ++u) v[u] = in[(int64_t)u * NT * estride];
+    }
+    TL tl{s_tiles + w, false};
+    const int64_t mthr = (int64_t)tile * G_::TPT + tid;
+    chk_core<float, L, TL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red, &acc_vb, &acc_cnt);
+    if (!(a.mode & M_NOWRITE) && c.owner) {
+      float2* out = outb + c.off + j * estride;
+#pragma unroll
+      for (int u = 0; u < V; ++u) out[(int64_t)u * NT * estride] = v[u];
+    }
+    __syncthreads();   // the tile buffer is reused by the next tile
+    tile = next;
+  }
+  if (!(a.mode & M_MASK)) {
+    block_max_count(acc_vb, acc_cnt, (a.mode & M_COUNT) != 0, s_red);
+    if (threadIdx.x == 0) {
+      atomicMax(&st.vbits, acc_vb);
+      if (acc_cnt) atomicAdd(&st.act_f, acc_cnt);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -227,3 +227,36 @@ def test_device_loop_graph_chunk_graphs_and_direct_launch_agree(shape):
     d, sd = run_gpu(e0, E, D, use_graph=2, max_iters=1)
     import paper_2601_01596_b300 as ffcz
     assert sd[0]["iters"] == 1 and sd[0]["status"] == ffcz.ERR_NOT_CONVERGED
+
+
+# ------------------------------------------------- TMA-fed persistent passes
+@pytest.mark.parametrize("shape", [(256, 256, 32), (512, 32, 16), (256, 64)])
+def test_tma_fed_passes_equal_plain_passes_and_match_oracle(shape, monkeypatch):
+    e0, E, D = stress(shape, 43)
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=-8,chk=-8")
+    a, sa = run_gpu(e0, E, D)
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=8,chk=8")
+    b, sb = run_gpu(e0, E, D)
+    assert sa[0]["iters"] == sb[0]["iters"] >= 2
+    assert np.array_equal(a, b)          # same arithmetic, other load path
+    ref = O.correct(e0, E, D)
+    assert abs(sa[0]["iters"] - ref.iters) <= 2 and sa[0]["certified"] == 1
+    np.testing.assert_allclose(a.reshape(shape), ref.e, rtol=0, atol=TOL * E)
+
+
+def test_tma_fed_batch_equals_singles(monkeypatch):
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=-8,chk=-8")
+    shapes = [(256, 64), (256, 32), (256, 64), (512, 16)]
+    items, Es, Ds = [], [], []
+    for i, sh in enumerate(shapes):
+        e0, E, D = stress(sh, 60 + i, frac=0.3 + 0.1 * (i % 3))
+        items.append(e0); Es.append(E); Ds.append(D)
+    packed = np.concatenate([x.reshape(-1) for x in items])
+    out, st = run_gpu(packed, Es, Ds, shapes=shapes)
+    off = 0
+    for i, sh in enumerate(shapes):
+        n = int(np.prod(sh))
+        single, s1 = run_gpu(items[i], Es[i], Ds[i])
+        assert np.array_equal(out[off:off + n], single), f"item {i}"
+        assert st[i]["iters"] == s1[0]["iters"] and st[i]["certified"] == 1
+        off += n
