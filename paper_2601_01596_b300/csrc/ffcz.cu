@@ -301,11 +301,39 @@ void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_
   }
   g_launches++;
 }
+int g_num_sms_x = 148;   // set from the device at plan creation
+
+// Persistent bulk-copy-fed loop x pass (float32, one-warp tiles): as many
+// CTAs as fit on the device, spread over the group's items.
+template <int M>
+void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
+  constexpr int W = row_w1(M);
+  using PG = PxTmaGeo<M, W>;
+  const size_t sm = PG::bytes;
+  if (g_dry) { set_smem(k_px_tma<M, W>, sm); return; }
+  static int per_sm = 0;   // resident CTAs per SM (same for every plan)
+  if (per_sm == 0) {
+    int n = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W>, Geo<float, M, W>::NTHR, sm));
+    per_sm = n > 0 ? n : 1;
+  }
+  const int64_t nblk = (rows + PG::RG - 1) / PG::RG;
+  const int64_t want = ((int64_t)per_sm * g_num_sms_x + count - 1) / count;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, want));
+  ProfScope ps("px", 32, M, s);
+  k_px_tma<M, W><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+
 template <typename T>
 struct XL {
   template <int M>
   static void go(XKind kind, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+      if (w < 0 && (kind == XPX || g_dry)) {
+        launch_px_tma<M>(a, rows, count, s);
+        if (!g_dry) return;
+      }
       if (w == row_w2(M)) launch_x_tw<T, M, row_w2(M)>(kind, a, rows, count, s);
       else launch_x_tw<T, M, row_w1(M)>(kind, a, rows, count, s);
     } else {
@@ -1412,9 +1440,9 @@ float time_launches(ffcz_plan_s* p, F&& f) {
   return ms;
 }
 
-// FFCZ_TUNE_FORCE="kind=w,..." (kinds px, axis, chk, col1, row1) fixes a
-// pass's variant for plans created while it is set, if w is one of the
-// pass's candidates.
+// FFCZ_TUNE_FORCE="kind=w,..." (kinds px, axis, chk, col1, row1; w a tile
+// width or "tma" for the persistent copy-engine-fed variant) fixes a pass's
+// variant for plans created while it is set, if w is one of its candidates.
 int forced_width(const std::string& key, const std::vector<int>& cand) {
   const char* f = getenv("FFCZ_TUNE_FORCE");
   if (!f) return 0;
@@ -1427,7 +1455,13 @@ int forced_width(const std::string& key, const std::vector<int>& cand) {
     const std::string item = spec.substr(pos, end - pos);
     const size_t eq = item.find('=');
     if (eq != std::string::npos && item.substr(0, eq) == kind) {
-      const int w = atoi(item.c_str() + eq + 1);
+      const std::string val = item.substr(eq + 1);
+      if (val == "tma") {   // the persistent copy-engine-fed variant (negative code)
+        for (int c : cand)
+          if (c < 0) return c;
+        return 0;
+      }
+      const int w = atoi(val.c_str());
       if (std::find(cand.begin(), cand.end(), w) != cand.end()) return w;
     }
     pos = end + 1;
@@ -1484,7 +1518,7 @@ void tune(ffcz_plan_s* p) {
       });
       continue;
     }
-    dg.wx = pick_width(p, std::string("px_") + base, dg.wx, {row_w1(dg.M), row_w2(dg.M)}, [&](int w) {
+    dg.wx = pick_width(p, std::string("px_") + base, dg.wx, {row_w1(dg.M), row_w2(dg.M), -row_w1(dg.M)}, [&](int w) {
       Args b = a;
       tabs_x<float>(p, b, dg);
       b.mode = 0;
@@ -1577,6 +1611,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     CK(cudaGetDevice(&p->device));
     CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
     g_num_sms = p->num_sms;
+    g_num_sms_x = p->num_sms;
     p->eoff.resize(batch);
     std::vector<int64_t> soff_c(batch);
     int64_t off = 0, offc = 0;
@@ -1696,7 +1731,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
           DevGroup dg = dg0;
           dg.wa = dg.wc = alt == 2 ? -8 : alt ? 8 : 4;
           dg.w1c = alt ? 8 : 4;
-          dg.wx = alt ? row_w2(dg.M) : row_w1(dg.M);
+          dg.wx = alt == 2 ? -row_w1(dg.M) : alt ? row_w2(dg.M) : row_w1(dg.M);
           dg.w1r = alt ? row_w2(dg.M) : row_w1(dg.M);
           if (ndim == 1) {
             launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, 1, nullptr);

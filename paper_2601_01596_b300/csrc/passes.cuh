@@ -916,6 +916,104 @@ k_chk_tma(Args a) {
   }
 }
 
+// Persistent float32 x pass (C2R, s-clip, R2C) fed by bulk copies: a CTA
+// holds G tiles of W rows each (one warp per tile); its G W consecutive rows
+// are one contiguous block of the packed spectrum, loaded by a single
+// cp.async.bulk while the previous block is transformed.  Shared memory:
+// [staging G W M][G tile buffers][twiddles][R2C twiddles][reduction].
+template <int M, int W>
+struct PxTmaGeo {
+  using G_ = Geo<float, M, W>;
+  static constexpr int RG = G_::G * W;                     // rows per block
+  static constexpr size_t stage = (size_t)RG * M * sizeof(float2);
+  static constexpr size_t bytes = 128 + stage + (size_t)G_::G * Tile<float, M, W>::ELEMS * sizeof(float2) +
+                                  2 * (size_t)M * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
+};
+
+template <int M, int W>
+__global__ void __launch_bounds__(Geo<float, M, W>::NTHR, Geo<float, M, W>::MINB)
+k_px_tma(Args a) {
+  using G_ = Geo<float, M, W>;
+  using TL = Tile<float, M, W>;
+  using PG = PxTmaGeo<M, W>;
+  constexpr int V = G_::V, NT = G_::NT, RG = PG::RG;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const uint32_t s0 = smem_addr(smraw);   // staging rounded up to 128 bytes
+  float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0 + 127u) & ~127u) - s0));
+  float2* s_tiles = s_stage + RG * M;
+  float2* s_tw = s_tiles + G_::G * TL::ELEMS;
+  float2* s_twr = s_tw + M;
+  unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M);
+  __shared__ __align__(8) uint64_t bar;
+  const int gi = blockIdx.y;
+  const int item = a.g.item[gi];
+  const ItemParams& p = a.prm[item];
+  ItemState& st = a.st[item];
+  if (!pred_ok(a.pred, st, p)) return;
+  const int t_it = st.t;
+  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
+  const int w = tid % W, j = tid / W;
+  const int64_t rows = a.g.rows;
+  const int64_t nblk = (rows + RG - 1) / RG;
+  const float2* inb = pick<float>(a, a.sel_in, t_it) + a.g.soff[gi];
+  float2* outb = pick<float>(a, a.sel_out, t_it) + a.g.soff[gi];
+  if ((smem_addr(s_stage) & 127u) != 0u || (reinterpret_cast<uintptr_t>(inb) & 15u) != 0u) {
+    if (threadIdx.x == 0) atomicExch(a.err, DERR_TMA_ALIGN);
+    return;
+  }
+  load_tables<float>(s_tw, a.tw, M, s_twr, a.twr, M);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t parity = 0;
+  auto issue = [&](int64_t blk) {
+    const int64_t r0 = blk * RG;
+    const int64_t nr = rows - r0 < RG ? rows - r0 : RG;
+    const uint32_t bytes = (uint32_t)(nr * M * sizeof(float2));
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_load(s_stage, inb + r0 * M, bytes, &bar);
+  };
+  int64_t blk = blockIdx.x;
+  if (threadIdx.x == 0 && blk < nblk) issue(blk);
+  unsigned long long cnt = 0;
+  while (blk < nblk) {
+    const int64_t next = blk + gridDim.x;
+    const bool ok = mbar_wait_bounded(&bar, parity, kTmaPollLimit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);
+      mbar_wait_bounded(&bar, parity, kTmaPollLimit);   // copies still in flight
+      return;
+    }
+    float2 v[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) v[u] = s_stage[(g * W + w) * M + j + u * NT];
+    __syncthreads();
+    if (threadIdx.x == 0 && next < nblk) {
+      fence_proxy_async_smem();
+      issue(next);
+    }
+    parity ^= 1u;
+    const int tile = (int)(blk * G_::G + g);
+    const int64_t prow = (int64_t)tile * W + w;
+    const bool live = prow < rows;
+    const int64_t row = live ? prow : 0;
+    const int64_t mthr = (int64_t)tile * G_::TPT + tid;
+    TL tl{s_tiles + g * TL::ELEMS + w, false};
+    cnt += px_core<float, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr);
+    if (live) {
+      float2* out = outb + row * M;
+#pragma unroll
+      for (int u = 0; u < V; ++u) out[j + u * NT] = v[u];
+    }
+    TL::sync();   // the warp's tile buffer is reused by the next block
+    blk = next;
+  }
+  if (a.mode & M_COUNT) {
+    Red r{0ull, 0.0, cnt};
+    block_reduce(r, s_red);
+    if (threadIdx.x == 0 && r.cnt) atomicAdd(&st.act_s, r.cnt);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Per-item control kernels
 // ---------------------------------------------------------------------------

@@ -51,3 +51,28 @@ def test_autograd_function_matches_oracle_through_spectrum_loss():
     g_ref = O.correct_backward(it["e0"], et.grad.numpy(), it["E"], it["D"], K)
     assert abs(loss.item() - lref.item()) <= 1e-3 * abs(lref.item()) + 1e-9
     assert np.linalg.norm(g_gpu - g_ref) <= 2e-3 * np.linalg.norm(g_ref)
+
+
+def test_backward_with_copy_engine_fed_x_pass_equals_plain(monkeypatch):
+    """The bulk-copy-fed x pass records and replays the same masks."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shape, K, m = (16, 32, 512), 4, 2
+    e0 = W.bimodal_error(shape, 52, dtype=np.float32)
+    E = 1.0
+    D = 0.4 * O.f_violation(O.dft(e0.astype(np.float64)))
+    g = np.random.default_rng(53).standard_normal(shape).astype(np.float32)
+    out = []
+    for force in ("px=tma", None):
+        if force:
+            monkeypatch.setenv("FFCZ_TUNE_FORCE", force)
+        else:
+            monkeypatch.delenv("FFCZ_TUNE_FORCE")
+            monkeypatch.setenv("FFCZ_TUNE", "0")
+        plan = ffcz.Plan([shape], K=K, ckpt_every=m)
+        te0 = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+        tg = torch.from_numpy(g.reshape(-1).copy()).cuda()
+        gi = torch.empty_like(te0)
+        plan.backward(te0, tg, gi, [E], [D])
+        out.append(gi.cpu().numpy())
+    assert np.array_equal(out[0], out[1])

@@ -230,12 +230,13 @@ def test_device_loop_graph_chunk_graphs_and_direct_launch_agree(shape):
 
 
 # ------------------------------------------------- TMA-fed persistent passes
-@pytest.mark.parametrize("shape", [(256, 256, 32), (512, 32, 16), (256, 64)])
+@pytest.mark.parametrize("shape", [(256, 256, 32), (512, 32, 16), (256, 64), (16, 32, 512), (8, 16, 16)])
 def test_tma_fed_passes_equal_plain_passes_and_match_oracle(shape, monkeypatch):
     e0, E, D = stress(shape, 43)
-    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=-8,chk=-8")
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,chk=tma,px=tma")
     a, sa = run_gpu(e0, E, D)
-    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=8,chk=8")
+    monkeypatch.delenv("FFCZ_TUNE_FORCE")
+    monkeypatch.setenv("FFCZ_TUNE", "0")     # default plain variants
     b, sb = run_gpu(e0, E, D)
     assert sa[0]["iters"] == sb[0]["iters"] >= 2
     assert np.array_equal(a, b)          # same arithmetic, other load path
@@ -245,7 +246,7 @@ def test_tma_fed_passes_equal_plain_passes_and_match_oracle(shape, monkeypatch):
 
 
 def test_tma_fed_batch_equals_singles(monkeypatch):
-    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=-8,chk=-8")
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,chk=tma,px=tma")
     shapes = [(256, 64), (256, 32), (256, 64), (512, 16)]
     items, Es, Ds = [], [], []
     for i, sh in enumerate(shapes):
