@@ -353,6 +353,7 @@ def _batch_form(ffcz, torch, items, name):
     del plan
     return {"workload": name, "items": len(items), "field_bytes": int(byts),
             "ms_per_call": round(ms, 3), "GBps": round(byts / (ms / 1e3) / 1e9, 3),
+            "ms_device": round(float(st[0]["ms_total"]), 3),
             "iters_min": int(min(iters)), "iters_max": int(max(iters)),
             "iters_mean": round(float(np.mean(iters)), 3),
             "certified": int(sum(x["certified"] for x in st)),

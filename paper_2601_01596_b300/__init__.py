@@ -11,6 +11,7 @@ missing or no GPU is present, the calls raise.
 """
 from __future__ import annotations
 
+import collections.abc
 import ctypes
 import os
 from typing import Sequence
@@ -49,6 +50,28 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class StatsList(collections.abc.Sequence):
+    """Per-item stats of one call: a sequence of dicts built on access (no
+    per-item work when the call returns); ``.array`` is the same data as a
+    numpy structured array without a copy."""
+
+    def __init__(self, arr):
+        self._c = arr
+
+    def __len__(self):
+        return len(self._c)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        return self._c[i].as_dict()
+
+    @property
+    def array(self):
+        import numpy as np
+        return np.ctypeslib.as_array(self._c)
 
 
 _lib = None
@@ -204,7 +227,7 @@ class Plan:
         s = lib().ffcz_correct(self._h, self._ptr(e, "e"), _dbl(eps_s, self.batch),
                                _dbl(eps_f, self.batch), st)
         _check(s, allow)
-        return [x.as_dict() for x in st]
+        return StatsList(st)
 
     def correct_host(self, e_np, eps_s, eps_f, allow=(ERR_NOT_CONVERGED, ERR_CERT_FAILED,
                                                       ERR_NONFINITE)):
@@ -217,7 +240,7 @@ class Plan:
         s = lib().ffcz_correct_host(self._h, ctypes.c_void_p(e_np.ctypes.data),
                                     _dbl(eps_s, self.batch), _dbl(eps_f, self.batch), st)
         _check(s, allow)
-        return [x.as_dict() for x in st]
+        return StatsList(st)
 
     def check(self, e, eps_s, eps_f, stream=None):
         """FP64 certification of ``e``; returns per-item stats (``certified``)."""
@@ -226,7 +249,7 @@ class Plan:
         s = lib().ffcz_check(self._h, self._ptr(e, "e"), _dbl(eps_s, self.batch),
                              _dbl(eps_f, self.batch), st)
         _check(s, (ERR_CERT_FAILED,))
-        return [x.as_dict() for x in st]
+        return StatsList(st)
 
     def backward(self, e0, grad_out, grad_in, eps_s, eps_f, stream=None):
         """grad_in <- (d e_K / d e0)^T grad_out for K = opts.K forced iterations."""

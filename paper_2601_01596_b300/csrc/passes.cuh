@@ -269,6 +269,9 @@ __device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int ntw
 // through one length-M complex FFT of z[n] = r[2n] + i r[2n+1]).
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
 // Post-processing of Z = FFT_M(z) into the packed half spectrum P (in place
 // in registers).  Each k needs Z[M-k], which another thread holds; it is
 // read through one exchange in natural order (a warp barrier only, when the
@@ -286,10 +289,12 @@ __device__ __forceinline__ void r2c_post(v2<T> (&v)[F2<M>::V], int j, TL& tl,
     if (k == 0) {
       v[u] = mk<T>(zk.x + zk.y, zk.x - zk.y);
     } else {
-      // Fe = (Zk + conj Zm)/2, Fo = (Zk - conj Zm)/(2i), X = Fe + W^k Fo
-      const v2<T> fe = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
-      const v2<T> fo = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
-      v[u] = add<T>(fe, cmul<T>(twr[k], fo));
+      // Fe = (Zk + conj Zm)/2, Fo = (Zk - conj Zm)/(2i), X = Fe + W^k Fo;
+      // with A = Zk + conj Zm, B = Zk - conj Zm:
+      // X = ((A.x + W.x B.y + W.y B.x) / 2, (A.y - W.x B.x + W.y B.y) / 2)
+      const v2<T> w = twr[k];
+      const T ax = zk.x + zm.x, ay = zk.y - zm.y, bx = zk.x - zm.x, by = zk.y + zm.y;
+      v[u] = mk<T>(T(0.5) * fmaT(w.x, by, fmaT(w.y, bx, ax)), T(0.5) * fmaT(-w.x, bx, fmaT(w.y, by, ay)));
     }
   }
   tl.done();
@@ -310,10 +315,11 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
     if (k == 0) {
       v[u] = mk<T>(xk.x + xk.y, xk.x - xk.y);
     } else {
-      // Z' = (Xk + conj Xm) + i (Xk - conj Xm) conj(W^k)
-      const v2<T> s = mk<T>(xk.x + xm.x, xk.y - xm.y);
-      const v2<T> d = cmulc<T>(mk<T>(xk.x - xm.x, xk.y + xm.y), twr[k]);
-      v[u] = mk<T>(s.x - d.y, s.y + d.x);
+      // Z' = (Xk + conj Xm) + i (Xk - conj Xm) conj(W^k); with A, B as in
+      // r2c_post: Z' = (A.x - W.x B.y + W.y B.x, A.y + W.x B.x + W.y B.y)
+      const v2<T> w = twr[k];
+      const T ax = xk.x + xm.x, ay = xk.y - xm.y, bx = xk.x - xm.x, by = xk.y + xm.y;
+      v[u] = mk<T>(fmaT(-w.x, by, fmaT(w.y, bx, ax)), fmaT(w.x, bx, fmaT(w.y, by, ay)));
     }
   }
   tl.done();
