@@ -122,6 +122,16 @@ ffcz_status ffcz_set_stream(ffcz_plan_t plan, void* cuda_stream);
 size_t ffcz_workspace_bytes(ffcz_plan_t plan);
 
 /*
+ * ffcz_plan_describe -- one line per item group: the group's shape, member
+ * count and the pass variants the tuner chose for it (tile width, or "tma"
+ * for the persistent copy-engine-fed kernels).  Writes at most `len` bytes
+ * including the terminating NUL into `buf` (host memory, caller-owned);
+ * returns the length the full text needs (excluding the NUL), or -1 for a
+ * null plan.
+ */
+int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len);
+
+/*
  * ffcz_correct -- Alg. 1 on every item, in place.
  *   e_dev  : device float32, the packed items; in: e0 = x_hat - x (Alg. 1,
  *            first step); out: the corrected error e*.  x_hat' = x + e*.

@@ -26,7 +26,7 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_correct", "ffcz_correct_host", "ffcz_check", "ffcz_correct_backward",
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
-           "ffcz_check_static")
+           "ffcz_check_static", "ffcz_plan_describe")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
         L.ffcz_set_stream.argtypes = [vp, vp]
         L.ffcz_workspace_bytes.argtypes = [vp]
         L.ffcz_workspace_bytes.restype = ctypes.c_size_t
+        L.ffcz_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
+        L.ffcz_plan_describe.restype = i32
         L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
@@ -193,6 +195,13 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(lib().ffcz_workspace_bytes(self._h))
+
+    def describe(self) -> str:
+        """Item groups and the pass variants the tuner chose for them."""
+        n = lib().ffcz_plan_describe(self._h, None, 0)
+        buf = ctypes.create_string_buffer(n + 1)
+        lib().ffcz_plan_describe(self._h, buf, n + 1)
+        return buf.value.decode()
 
     def profile(self, on: bool = True):
         """Turn per-kernel event timing on (clears the table) or off."""

@@ -1798,6 +1798,36 @@ ffcz_status ffcz_set_stream(ffcz_plan_t plan, void* s) {
 
 size_t ffcz_workspace_bytes(ffcz_plan_t plan) { return plan ? plan->ws_bytes : 0; }
 
+int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len) {
+  if (!plan) return -1;
+  std::string out;
+  auto var = [](int w) { return w < 0 ? "tma(" + std::to_string(-w) + ")" : std::to_string(w); };
+  for (const auto& dg : plan->groups) {
+    char head[160];
+    if (dg.ndim == 1)
+      snprintf(head, sizeof head, "1d P=%dx%d count=%d:", dg.P1, dg.P2, dg.count);
+    else if (dg.ndim == 2)
+      snprintf(head, sizeof head, "2d %dx%d count=%d:", dg.Nz, dg.Nx, dg.count);
+    else
+      snprintf(head, sizeof head, "3d %dx%dx%d count=%d:", dg.Nz, dg.Ny, dg.Nx, dg.count);
+    out += head;
+    if (dg.ndim == 1) {
+      out += " col1=" + var(dg.w1c) + " row1=" + var(dg.w1r);
+    } else {
+      out += " px=" + var(dg.wx);
+      if (dg.ndim == 3) out += " axis=" + var(dg.wa);
+      out += " chk=" + var(dg.wc);
+    }
+    out += "\n";
+  }
+  if (buf && len > 0) {
+    const size_t n = std::min(out.size(), (size_t)len - 1);
+    memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return (int)out.size();
+}
+
 ffcz_status ffcz_correct(ffcz_plan_t plan, float* e, const double* eps_s, const double* eps_f,
                          ffcz_stats* stats) {
   if (!plan) return FFCZ_ERR_INVALID;
