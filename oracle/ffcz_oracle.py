@@ -9,7 +9,7 @@ the method's arithmetic.
 Everything is float64.  The DFT step is a library primitive (``scipy.fft``,
 full complex spectrum, no half-spectrum tricks); everything else is written out
 in the paper's order.  Readings of passages the paper leaves open are tagged
-``A1``..``A16`` and listed, with the reasons, in the design notes.
+``A1``..``A20`` and listed, with the reasons, in the design notes.
 
 Notation: ``e`` is the spatial error vector (epsilon in the paper), ``delta``
 its frequency error vector, ``E`` the spatial bound and ``D`` the frequency
@@ -97,6 +97,11 @@ class Result:
     active_s: int = 0               # points moved by the last s-clip
     active_f: int = 0               # bins moved by the last f-clip
     trajectory: list = field(default_factory=list)   # e after every iteration
+    # Alg. 1 edit accumulators (when requested): the displacement of the error
+    # vector along the spatial basis (spat_edits, shape of e) and along the
+    # frequency basis (freq_edits, full complex spectrum, Hermitian)
+    spat_edits: np.ndarray | None = None
+    freq_edits: np.ndarray | None = None
 
 
 def thresholds(E: float, D: float, eta: float):
@@ -106,36 +111,55 @@ def thresholds(E: float, D: float, eta: float):
 
 def correct(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
             max_iters: int = 10000, eta: float = ETA_DEFAULT,
-            record: bool = False) -> Result:
+            record: bool = False, edits: bool = False) -> Result:
     """Alg. 1 (Sec. IV-B), the loop of FFT, CheckConvergence, ProjectOntoFCube,
     IFFT, ProjectOntoSCube, with the readings A3 (pre-loop s-projection), A7
     (shrunk projections, midpoint stopping test) and A9 (iteration cap).
 
     ``e0`` is the base compressor's error x_hat - x (Alg. 1, first step; A1).
     Returns the iterate at which the check passed, or the last one at the cap.
+
+    With ``edits`` the spatial and frequency edits of Alg. 1 are accumulated:
+    after each ProjectOntoFCube freq_edits += delta' - delta, after each
+    ProjectOntoSCube spat_edits += eps' - eps (A18: the pre-loop s-projection
+    of A3 is a spatial edit too; the check that stops the loop projects
+    nothing).
     """
     e = np.asarray(e0, dtype=np.float64).copy()
     Es, Ds, thr = thresholds(E, D, eta)
+    S = np.zeros_like(e) if edits else None
+    F = np.zeros(e.shape, dtype=np.complex128) if edits else None
     pre = bool(e.size and np.max(np.abs(e)) > E)          # A3
     if pre:
-        e = project_s(e, Es)
+        e_p = project_s(e, Es)
+        if edits:
+            S += e_p - e
+        e = e_p
     t = 0
     act_s = act_f = 0
     traj = []
+
+    def done(status, v):
+        return Result(e, t, status, pre, v / D if D > 0 else v, act_s, act_f, traj, S, F)
+
     while True:
         delta = dft(e)                                    # FFT(eps)
         v = f_violation(delta)                            # CheckConvergence
         if not np.isfinite(v):
-            return Result(e, t, NONFINITE, pre, v / D if D > 0 else v, act_s, act_f, traj)
+            return done(NONFINITE, v)
         if v <= thr and t >= min_iters:
-            return Result(e, t, OK, pre, v / D, act_s, act_f, traj)
+            return done(OK, v)
         if t >= max_iters:
-            return Result(e, t, NOT_CONVERGED, pre, v / D, act_s, act_f, traj)
+            return done(NOT_CONVERGED, v)
         delta_c = project_f(delta, Ds)                    # ProjectOntoFCube
         act_f = int(np.count_nonzero(delta_c != delta))
+        if edits:
+            F += delta_c - delta                          # freq_edits += delta' - delta
         e_i = idft(delta_c)                               # IFFT
         e = project_s(e_i, Es)                            # ProjectOntoSCube
         act_s = int(np.count_nonzero(e != e_i))
+        if edits:
+            S += e - e_i                                  # spat_edits += eps' - eps
         t += 1
         if record:
             traj.append(e.copy())
@@ -151,6 +175,70 @@ def certify(e: np.ndarray, E: float, D: float):
     s = float(np.max(np.abs(e))) if e.size else 0.0
     v = f_violation(dft(e))
     return bool(s <= E and v <= D), s, v
+
+
+# --------------------------------------------------------------------------
+# Edits: storage form and application (Alg. 1 after the loop; Sec. IV-B,
+# "Compaction, quantization ..." and "Applying edits ...")
+# --------------------------------------------------------------------------
+def half_spectrum(F: np.ndarray) -> np.ndarray:
+    """The stored half of a Hermitian spectrum: last axis k = 0..N/2 (the
+    layout of a real-input FFT); the other half is its conjugate (A19)."""
+    return F[..., : F.shape[-1] // 2 + 1]
+
+
+def compact_edits(values: np.ndarray):
+    """CompactEdits: flags = 1 where the edit is nonzero (a complex edit is one
+    component, nonzero if its real or imaginary part is), packed 8 per byte
+    with the first component in the least significant bit (A20); compact =
+    the nonzero edits in C order."""
+    flat = np.asarray(values).reshape(-1)
+    nz = (flat.real != 0) | (flat.imag != 0) if np.iscomplexobj(flat) else flat != 0
+    return np.packbits(nz, bitorder="little"), flat[nz]
+
+
+def expand_edits(flags: np.ndarray, compact: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of :func:`compact_edits` for n components."""
+    nz = np.unpackbits(np.asarray(flags, dtype=np.uint8), count=n, bitorder="little").astype(bool)
+    out = np.zeros(n, dtype=np.asarray(compact).dtype)
+    out[nz] = compact
+    return out
+
+
+def quant_step(bound: float, m: int = 16, dtype=np.float64):
+    """QuantizeEdits splits each axis [-bound, bound] of the s- or f-cube into
+    2^m intervals: step q = 2 bound / 2^m (in the given precision)."""
+    return dtype(dtype(bound) * dtype(2.0 ** (1 - m)))
+
+
+def quantize_edits(compact: np.ndarray, bound: float, m: int = 16, dtype=np.float64) -> np.ndarray:
+    """QuantizeEdits: integer codes rint(edit / q), ties to even, the division
+    and the rounding in ``dtype`` (A20).  Complex edits give (Re, Im) code
+    pairs."""
+    q = quant_step(bound, m, dtype)
+    c = np.asarray(compact)
+    if np.iscomplexobj(c):
+        parts = np.stack([c.real.astype(dtype), c.imag.astype(dtype)], axis=-1)
+    else:
+        parts = c.astype(dtype)
+    return np.rint(parts / q).astype(np.int64)
+
+
+def dequantize_edits(codes: np.ndarray, bound: float, m: int = 16, complex_pairs: bool = False):
+    """Edits from codes: code * q (float64)."""
+    q = quant_step(bound, m)
+    v = np.asarray(codes, dtype=np.float64) * q
+    return v[..., 0] + 1j * v[..., 1] if complex_pairs else v
+
+
+def apply_edits(xhat: np.ndarray, spat: np.ndarray, freq_half: np.ndarray) -> np.ndarray:
+    """Applying edits (Sec. IV-B): the complete spatial edit is the spatial
+    edits plus the inverse FFT of the frequency edits; the result is the base
+    reconstruction plus that complete edit.  ``freq_half`` is the stored half
+    spectrum of the (Hermitian) frequency edits."""
+    xhat = np.asarray(xhat, dtype=np.float64)
+    full = sfft.irfftn(np.asarray(freq_half, dtype=np.complex128), s=xhat.shape, workers=_WORKERS)
+    return xhat + np.asarray(spat, dtype=np.float64) + full
 
 
 # --------------------------------------------------------------------------

@@ -337,3 +337,163 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     got = O.correct(e1, 1.0, 0.1 * 0.5 * 32, max_iters=3)
     Ds = 0.1 * 0.5 * 32 * (1 - O.ETA_DEFAULT)
     assert not np.allclose(got.e, W.single_mode((64,), (5,), 2 * Ds / 64), atol=1e-12)
+
+
+# --------------------------------------------- edits (Alg. 1, Sec. IV-B/C)
+def _mirror(F):
+    """F at -k for every k (index reversal modulo each axis length)."""
+    idx = np.ix_(*[(-np.arange(n)) % n for n in F.shape])
+    return F[idx]
+
+
+@pytest.mark.parametrize("shape,seed", [((16, 16), 31), ((8, 16, 16), 32), ((61,), 33), ((6, 10), 34)])
+def test_edits_sum_to_total_displacement(shape, seed):
+    """eps* - eps0 = spatial edits + IDFT(frequency edits), and F Hermitian."""
+    e0, E, D = _stress(shape, seed, 0.4)
+    r = O.correct(e0, E, D, edits=True)
+    assert r.iters >= 2
+    idft_F = np.fft.ifftn(r.freq_edits)                    # numpy, not the oracle's scipy call
+    np.testing.assert_allclose(r.e - e0, r.spat_edits + idft_F.real, rtol=0, atol=1e-12)
+    assert np.max(np.abs(idft_F.imag)) < 1e-12
+    np.testing.assert_allclose(_mirror(r.freq_edits), np.conj(r.freq_edits), rtol=0, atol=1e-12)
+    assert np.count_nonzero(r.spat_edits) > 0 and np.count_nonzero(r.freq_edits) > 0
+
+
+@pytest.mark.parametrize("shape,k0", [((64,), (5,)), ((8, 16, 16), (1, 2, 3))])
+def test_edits_single_mode_closed_form(shape, k0):
+    """One f-clip: delta(+-k0) = A N / 2 clipped to D' gives F(+-k0) = D' - A N/2,
+    zero elsewhere, and no spatial edit."""
+    N = int(np.prod(shape))
+    A, E = 0.5, 1.0
+    D = 0.1 * A * N / 2
+    r = O.correct(W.single_mode(shape, k0, A), E, D, edits=True)
+    Ds = D * (1 - O.ETA_DEFAULT)
+    want = np.zeros(shape, dtype=complex)
+    want[tuple(k0)] = Ds - A * N / 2
+    want[tuple((-k) % n for k, n in zip(k0, shape))] = Ds - A * N / 2
+    assert r.iters == 1
+    np.testing.assert_allclose(r.freq_edits, want, rtol=0, atol=1e-10)
+    assert not r.spat_edits.any()
+
+
+@pytest.mark.parametrize("shape", [(17,), (4, 6, 8)])
+def test_edits_spike_closed_form(shape):
+    """e0 = E' at n = 0: every bin E' clipped to D', so F_k = D' - E' for all k."""
+    E, D = 1.0, 0.5
+    Es, Ds, _ = O.thresholds(E, D, O.ETA_DEFAULT)
+    e0 = np.zeros(shape); e0.flat[0] = Es
+    r = O.correct(e0, E, D, edits=True)
+    np.testing.assert_allclose(r.freq_edits, np.full(shape, Ds - Es), rtol=0, atol=1e-14)
+    assert not r.spat_edits.any()
+
+
+def test_edits_preclip_is_a_spatial_edit():
+    e0, E, D = _stress((8, 8), 35, 0.5)
+    e0 = e0.copy(); e0[2, 3] = 1.5; e0[5, 1] = -3.0
+    r = O.correct(e0, E, D, edits=True)
+    assert r.preclipped
+    np.testing.assert_allclose(r.e - e0, r.spat_edits + np.fft.ifftn(r.freq_edits).real, atol=1e-12)
+
+
+def dense_pocs_edits(e0, E, D, eta=O.ETA_DEFAULT, max_iters=1000):
+    """The dense cos/sin-coordinate POCS above, accumulating its own edits: a
+    coordinate move dc of the cos row of bin k changes Re delta_k by dc and
+    Re delta_-k by dc; of the sin row, Im delta_k by -dc and Im delta_-k by +dc
+    (delta_k = sum e_n (cos - i sin))."""
+    shape = e0.shape
+    idx = list(itertools.product(*[range(n) for n in shape]))
+    grid = np.array(idx, dtype=np.float64)
+    rows, seen = [], set()
+    for k in idx:
+        mk = tuple((-kk) % n for kk, n in zip(k, shape))
+        if mk in seen:
+            continue
+        seen.add(k)
+        ph = 2 * np.pi * sum(grid[:, i] * k[i] / shape[i] for i in range(len(shape)))
+        rows.append((np.cos(ph), k, mk, "c"))
+        if mk != k:
+            rows.append((np.sin(ph), k, mk, "s"))
+    B = np.array([r[0] for r in rows])
+    nrm = np.sum(B * B, axis=1)
+    Es, Ds, thr = E * (1 - eta), D * (1 - eta), D * (1 - eta / 2)
+    e = e0.reshape(-1).astype(np.float64).copy()
+    S = np.zeros_like(e)
+    F = np.zeros(shape, dtype=complex)
+    for _ in range(max_iters + 1):
+        c = B @ e
+        if np.max(np.abs(c)) <= thr:
+            return e.reshape(shape), S.reshape(shape), F
+        cc = np.clip(c, -Ds, Ds)
+        for (_, k, mk, kind), dc in zip(rows, cc - c):
+            if dc == 0:
+                continue
+            if kind == "c":
+                F[k] += dc
+                if mk != k:
+                    F[mk] += dc
+            else:
+                F[k] += -1j * dc
+                F[mk] += 1j * dc
+        ei = e + ((cc - c) / nrm) @ B
+        e = np.clip(ei, -Es, Es)
+        S += e - ei
+    raise AssertionError("dense POCS did not converge")
+
+
+@pytest.mark.parametrize("shape,seed", [((12,), 36), ((4, 6), 37), ((2, 4, 4), 38)])
+def test_edits_match_dense_coordinate_pocs(shape, seed):
+    r0 = np.random.default_rng(seed)
+    E = 1.0
+    e0 = r0.uniform(-E, E, shape)
+    D = 0.3 * O.f_violation(O.dft(e0))
+    e_d, S_d, F_d = dense_pocs_edits(e0, E, D)
+    r = O.correct(e0, E, D, edits=True)
+    np.testing.assert_allclose(r.e, e_d, atol=1e-12)
+    np.testing.assert_allclose(r.spat_edits, S_d, atol=1e-12)
+    np.testing.assert_allclose(r.freq_edits, F_d, atol=1e-12)
+
+
+def test_compaction_quantization_and_application():
+    """CompactEdits round trip, code error <= q/2, and the decompression side:
+    x_hat + S + IFFT(F) from the stored half spectrum gives x + eps*."""
+    shape = (8, 16, 16)
+    e0, E, D = _stress(shape, 39, 0.4)
+    r = O.correct(e0, E, D, edits=True)
+    Fh = O.half_spectrum(r.freq_edits)
+    assert Fh.shape == (8, 16, 9)
+    for vals, bound in ((r.spat_edits, E), (Fh, D)):
+        flags, comp = O.compact_edits(vals)
+        n = vals.size
+        assert flags.size == (n + 7) // 8
+        assert int(np.unpackbits(flags, bitorder="little")[:n].sum()) == comp.size
+        np.testing.assert_array_equal(O.expand_edits(flags, comp, n), vals.reshape(-1))
+        codes = O.quantize_edits(comp, bound)
+        back = O.dequantize_edits(codes, bound, complex_pairs=np.iscomplexobj(comp))
+        q = 2 * bound / 2 ** 16
+        err = back - comp
+        assert max(np.max(np.abs(err.real)), np.max(np.abs(np.imag(err)))) <= q / 2 + 1e-18
+    # bit order: component 0 in the least significant bit of byte 0
+    f, _ = O.compact_edits(np.array([1.0, 0, 0, 0, 0, 0, 0, 0, 0, 2.0]))
+    assert list(f) == [1, 2]
+    # x_hat = x + e0; applying the exact edits reproduces x + eps*
+    x = np.random.default_rng(40).standard_normal(shape)
+    out = O.apply_edits(x + e0, r.spat_edits, Fh)
+    np.testing.assert_allclose(out, x + r.e, rtol=0, atol=1e-12)
+    # float32 decisions: the same codes from numpy float32 arithmetic
+    v32 = r.spat_edits[r.spat_edits != 0].astype(np.float32)
+    q32 = np.float32(E) * np.float32(2.0 ** -15)
+    np.testing.assert_array_equal(O.quantize_edits(v32, E, dtype=np.float32),
+                                  np.rint(v32 / q32).astype(np.int64))
+
+
+def test_edit_pin_catches_recording_the_stopping_clip():
+    """Planted mistake: also recording the f-clip of the check that stops the
+    loop (Alg. 1 breaks before ProjectOntoFCube) breaks the displacement pin."""
+    e0, E, D = _stress((16, 16), 41, 0.4)
+    r = O.correct(e0, E, D, edits=True)
+    Ds = D * (1 - O.ETA_DEFAULT)
+    delta = O.dft(r.e)
+    F_bad = r.freq_edits + (O.project_f(delta, Ds) - delta)
+    assert np.max(np.abs(O.project_f(delta, Ds) - delta)) > 0
+    bad = r.spat_edits + np.fft.ifftn(F_bad).real
+    assert np.max(np.abs(r.e - e0 - bad)) > 1e-12
