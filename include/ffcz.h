@@ -71,6 +71,9 @@ typedef struct {
                           2 (default): the whole loop on the device, one graph
                           with a conditional WHILE node (no host round trip) */
   int32_t count_active;/* 1 (default): count active clips for ffcz_stats */
+  int32_t edits;       /* 1: record the spatial and frequency edits of Alg. 1
+                          (ffcz_edits_dense / ffcz_edits_compact read them);
+                          2D and 3D items; default 0 */
 } ffcz_opts;
 
 /* Per-item results. */
@@ -120,6 +123,44 @@ ffcz_status ffcz_set_stream(ffcz_plan_t plan, void* cuda_stream);
 
 /* Bytes of device workspace the plan holds now. */
 size_t ffcz_workspace_bytes(ffcz_plan_t plan);
+
+/*
+ * Edits (Alg. 1 "spat_edits"/"freq_edits", Sec. IV-B), recorded by
+ * ffcz_correct when the plan was created with opts.edits = 1 (2D and 3D
+ * items).  Spatial edits: the sum of the s-clip displacements eps' - eps
+ * (the pre-loop clip of an input outside the s-cube included), float32,
+ * laid out like e.  Frequency edits: the sum of the f-clip displacements
+ * delta' - delta of every check that did not stop the loop, stored as the
+ * half spectrum of a real-input FFT: complex64 (Re, Im float pairs)
+ * [Nz][Ny][Nx/2+1] per item (2D: [Ny][Nx/2+1]), items back to back.  In
+ * exact arithmetic e_out - e_in = spatial edits + IFFT(frequency edits).
+ * The edits describe the last ffcz_correct call on the plan.
+ *
+ * ffcz_edit_layout -- sizes and offsets for item `item` (0-based), or the
+ * totals for item = -1, into out[6] (host): points, half-spectrum bins,
+ * offset of the item's spatial flags (bytes), spatial codes (int32), frequency
+ * flags (bytes), frequency codes (int32; two per bin).  For item = -1 the
+ * last four are the array sizes ffcz_edits_compact needs.
+ *
+ * ffcz_edits_dense -- copy the dense edits to device memory: s_dev (float32,
+ * total points) and f_dev (float32 pairs, total bins x 2); either may be NULL.
+ *
+ * ffcz_edits_compact -- CompactEdits and QuantizeEdits (Alg. 1) of every
+ * item into device arrays at the offsets of ffcz_edit_layout: flags = 1 for
+ * each nonzero component (a frequency bin is nonzero if Re or Im is), packed
+ * 8 per byte with the first component in the least significant bit; codes =
+ * rint(edit / q) for the nonzero components in order, q = 2 eps / 2^m_bits
+ * (eps = eps_s or eps_f of the last call, m_bits in [2, 30]; the paper uses
+ * 16), the division and rounding in float32, ties to even, Re and Im coded
+ * separately.  counts (host, 2 per item, may be NULL) receives the number of
+ * nonzero spatial and frequency components of each item.  Synchronises the
+ * plan's stream.  All three return FFCZ_ERR_INVALID for a plan created without
+ * opts.edits.
+ */
+ffcz_status ffcz_edit_layout(ffcz_plan_t plan, int64_t item, int64_t* out);
+ffcz_status ffcz_edits_dense(ffcz_plan_t plan, float* s_dev, float* f_dev);
+ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, int32_t* s_codes,
+                               uint8_t* f_flags, int32_t* f_codes, int64_t* counts);
 
 /*
  * ffcz_plan_describe -- one line per item group: the group's shape, member

@@ -26,7 +26,8 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_correct", "ffcz_correct_host", "ffcz_check", "ffcz_correct_backward",
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
-           "ffcz_check_static", "ffcz_plan_describe")
+           "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
+           "ffcz_edits_compact")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -36,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("certify", ctypes.c_int32), ("max_repairs", ctypes.c_int32),
                 ("K", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("count_active", ctypes.c_int32)]
+                ("count_active", ctypes.c_int32), ("edits", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +95,9 @@ def lib() -> ctypes.CDLL:
         L.ffcz_workspace_bytes.restype = ctypes.c_size_t
         L.ffcz_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
         L.ffcz_plan_describe.restype = i32
+        L.ffcz_edit_layout.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.ffcz_edits_dense.argtypes = [vp, vp, vp]
+        L.ffcz_edits_compact.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
         L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
@@ -195,6 +199,41 @@ class Plan:
     @property
     def workspace_bytes(self) -> int:
         return int(lib().ffcz_workspace_bytes(self._h))
+
+    def edit_layout(self, item: int = -1):
+        """(points, bins, s_flag_off, s_code_off, f_flag_off, f_code_off) of one
+        item, or the totals / array sizes for item = -1 (plan with edits=1)."""
+        out = (ctypes.c_int64 * 6)()
+        _check(lib().ffcz_edit_layout(self._h, item, out))
+        return tuple(int(x) for x in out)
+
+    def edits_dense(self):
+        """Dense edits of the last call: (spatial float32 [points], frequency
+        complex64 [half-spectrum bins]) as CUDA tensors."""
+        import torch
+        tot = self.edit_layout(-1)
+        s = torch.empty(tot[0], dtype=torch.float32, device="cuda")
+        f = torch.empty(2 * tot[1], dtype=torch.float32, device="cuda")
+        _check(lib().ffcz_edits_dense(self._h, ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(f.data_ptr())))
+        return s, torch.view_as_complex(f.view(-1, 2))
+
+    def edits_compact(self, m_bits: int = 16):
+        """CompactEdits + QuantizeEdits: dict of CUDA tensors (s_flags, s_codes,
+        f_flags, f_codes, regions at ``edit_layout(i)`` offsets) and ``counts``
+        (numpy [batch, 2]: nonzero spatial / frequency components per item)."""
+        import numpy as np
+        import torch
+        tot = self.edit_layout(-1)
+        d = dict(s_flags=torch.zeros(max(1, tot[2]), dtype=torch.uint8, device="cuda"),
+                 s_codes=torch.zeros(max(1, tot[3]), dtype=torch.int32, device="cuda"),
+                 f_flags=torch.zeros(max(1, tot[4]), dtype=torch.uint8, device="cuda"),
+                 f_codes=torch.zeros(max(1, tot[5]), dtype=torch.int32, device="cuda"))
+        counts = (ctypes.c_int64 * (2 * self.batch))()
+        _check(lib().ffcz_edits_compact(self._h, m_bits, *[ctypes.c_void_p(d[k].data_ptr()) for k in
+                                                         ("s_flags", "s_codes", "f_flags", "f_codes")],
+                                        counts))
+        d["counts"] = np.array(counts, dtype=np.int64).reshape(self.batch, 2)
+        return d
 
     def describe(self) -> str:
         """Item groups and the pass variants the tuner chose for them."""

@@ -1,0 +1,155 @@
+// edits.cuh -- storage form of the Alg. 1 edits (Sec. IV-B, "Compaction,
+// quantization, and lossless compression of edits"; the lossless back end
+// is not part of this library).
+//
+// Canonical layout: spatial edits like the field (float32 per point);
+// frequency edits as the half spectrum of a real-input FFT, complex64
+// [Nz][Ny][Nx/2+1] per item (2D: [Ny][Nx/2+1]).
+// CompactEdits: flags = 1 where a component is nonzero (a complex bin counts
+// once), packed 8 per byte, first component in bit 0; compact edits = the
+// nonzero components in order.  QuantizeEdits: code = rint(edit / q),
+// q = 2 bound / 2^m, division and rounding in float32, Re and Im coded
+// separately.  Items are compacted independently into fixed regions.
+#pragma once
+#include "passes.cuh"
+
+namespace ffcz {
+
+// Packed spectrum (kx = 0 slot = A + iB, A, B the kx = 0 and kx = Nx/2
+// planes) -> canonical half spectrum.  Grid (x: bins, y: group members).
+static __global__ void k_edits_canon(Group g, const float2* ed_f, float2* out, const int64_t* ooff) {
+  const int gi = blockIdx.y;
+  const int Nz = g.Nz, Ny = g.Nmid, M = g.M;
+  const int64_t nb = (int64_t)Nz * Ny * (M + 1);
+  const float2* F = ed_f + g.soff[gi];
+  float2* o = out + ooff[gi];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % (M + 1));
+    const int64_t r = i / (M + 1);               // kz Ny + ky
+    if (kx > 0 && kx < M) {
+      o[i] = F[r * M + kx];
+      continue;
+    }
+    const int ky = (int)(r % Ny), kz = (int)(r / Ny);
+    const int64_t rm = (int64_t)((Nz - kz) % Nz) * Ny + (Ny - ky) % Ny;
+    const float2 c = F[r * M], cm = F[rm * M];
+    // A = (C + conj Cm) / 2, B = (C - conj Cm) / (2i)
+    o[i] = kx == 0 ? make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y))
+                   : make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+  }
+}
+
+__device__ __forceinline__ bool nz_comp(float v) { return v != 0.f; }
+__device__ __forceinline__ bool nz_comp(float2 v) { return v.x != 0.f || v.y != 0.f; }
+
+// One region to compact: n components at `vals`, flags at `flags`, codes at
+// `codes`, chunk counts at `chunks`, step q.
+template <typename C>
+struct EdRegion {
+  const C* vals;
+  int64_t n;
+  uint8_t* flags;
+  int32_t* codes;
+  int* chunks;
+  float q;
+};
+
+constexpr int kEdThreads = 256;
+constexpr int kEdChunk = kEdThreads * 8;   // components per CTA
+
+// Flags and per-chunk counts.  Each thread owns 8 consecutive components
+// (one flag byte).
+template <typename C>
+static __global__ void k_edits_count(const EdRegion<C>* regs) {
+  const EdRegion<C> r = regs[blockIdx.y];
+  const int64_t c0 = (int64_t)blockIdx.x * kEdChunk;
+  if (c0 >= r.n) return;
+  const int64_t b = c0 / 8 + threadIdx.x;     // flag byte
+  int cnt = 0;
+  if (b * 8 < r.n) {
+    unsigned byte = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t i = b * 8 + k;
+      if (i < r.n && nz_comp(r.vals[i])) byte |= 1u << k;
+    }
+    r.flags[b] = (uint8_t)byte;
+    cnt = __popc(byte);
+  }
+  __shared__ int s[kEdThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kEdThreads / 32; ++w) t += s[w];
+    r.chunks[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the chunk counts of each region (one CTA per region);
+// the region's total goes to totals[region].
+template <typename C>
+static __global__ void k_edits_scan(const EdRegion<C>* regs, int64_t* totals) {
+  const EdRegion<C> r = regs[blockIdx.x];
+  const int64_t nch = (r.n + kEdChunk - 1) / kEdChunk;
+  __shared__ long long carry;
+  __shared__ long long s[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nch; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const long long v = i < nch ? r.chunks[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive Hillis-Steele scan
+      const long long add = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nch) r.chunks[i] = (int)(carry + s[threadIdx.x] - v);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__device__ __forceinline__ int32_t quant_code(float v, float q) {
+  const float r = rintf(v / q);                // IEEE division, ties to even
+  return (int32_t)fminf(fmaxf(r, -2147483520.f), 2147483520.f);
+}
+__device__ __forceinline__ void put_codes(int32_t* codes, int64_t k, float v, float q) { codes[k] = quant_code(v, q); }
+__device__ __forceinline__ void put_codes(int32_t* codes, int64_t k, float2 v, float q) {
+  codes[2 * k] = quant_code(v.x, q);
+  codes[2 * k + 1] = quant_code(v.y, q);
+}
+
+// Quantized nonzero components at their compacted positions.
+template <typename C>
+static __global__ void k_edits_scatter(const EdRegion<C>* regs) {
+  const EdRegion<C> r = regs[blockIdx.y];
+  const int64_t c0 = (int64_t)blockIdx.x * kEdChunk;
+  if (c0 >= r.n) return;
+  const int64_t b = c0 / 8 + threadIdx.x;
+  const unsigned byte = (b * 8 < r.n) ? r.flags[b] : 0u;
+  const int cnt = __popc(byte);
+  // block exclusive scan of the per-thread counts
+  __shared__ int s[kEdThreads / 32];
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((threadIdx.x & 31) >= (unsigned)o) incl += y;
+  }
+  if ((threadIdx.x & 31) == 31) s[threadIdx.x >> 5] = incl;
+  __syncthreads();
+  int wbase = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbase += s[w];
+  int64_t k = (int64_t)r.chunks[blockIdx.x] + wbase + incl - cnt;
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (byte & (1u << t)) put_codes(r.codes, k++, r.vals[b * 8 + t], r.q);
+}
+
+}  // namespace ffcz

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -22,6 +23,7 @@
 #include "../../include/ffcz.h"
 #include "bluestein.cuh"
 #include "passes.cuh"
+#include "edits.cuh"
 
 using namespace ffcz;
 
@@ -99,6 +101,7 @@ struct DevGroup {
   const CUtensorMap* tm_axis = nullptr;
   const CUtensorMap* tm_chk = nullptr;
   std::vector<int64_t> h_soff;   // host copy of the members' spectrum offsets
+  const int64_t* d_canon = nullptr;   // members' offsets in the canonical edit spectra
   // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
   int P1 = 0, P2 = 0;
   const void* twp32 = nullptr;
@@ -157,6 +160,25 @@ struct ffcz_plan_s {
   int* d_nactive = nullptr;
   int* h_nactive = nullptr;     // pinned
   int* d_err = nullptr;         // device error word (DevErr), cleared per call
+  // Alg. 1 edits (opts.edits): spatial edits (float32, like e), frequency
+  // edits in the packed spectrum layout (committed, pending, pending tag),
+  // recorded only by the correction loops (ed_on), plus the canonical
+  // half-spectrum form and compaction scratch built on request
+  float* ed_s = nullptr;
+  float2* ed_f = nullptr;
+  float2* ed_p = nullptr;
+  int* ed_t = nullptr;
+  bool ed_on = false;
+  float2* ed_canon = nullptr;
+  int* ed_chunks = nullptr;
+  // per item: points, half-spectrum bins, and the offsets of its regions in
+  // the caller's edit arrays (spatial flags/codes, frequency flags/codes)
+  std::vector<std::array<int64_t, 6>> ed_layout;
+  std::array<int64_t, 6> ed_total{};
+  void* ed_reg_s = nullptr;      // device EdRegion<float>[batch]
+  void* ed_reg_f = nullptr;      // device EdRegion<float2>[batch]
+  int64_t* ed_tot = nullptr;     // device per-region counts [2 batch]
+  int64_t ed_chunk_cap = 0;
   int* h_err = nullptr;         // pinned copy
   int num_sms = 148;
   ItemState* h_st = nullptr;    // pinned
@@ -590,6 +612,12 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   a.sel_in = a.sel_out = S_CUR;
   a.ckpt_every = 0;
   a.err = p->d_err;
+  if (p->ed_on) {
+    a.ed_s = p->ed_s;
+    a.ed_f = p->ed_f;
+    a.ed_p = p->ed_p;
+    a.ed_t = p->ed_t;
+  }
   if (sizeof(T) == 4 && b0 == p->B32[0] && b1 == p->B32[1]) {
     a.tm_axis = dg.tm_axis;
     a.tm_chk = dg.tm_chk;
@@ -954,8 +982,88 @@ int read_active(ffcz_plan_s* p) {
   return *p->h_nactive;
 }
 
+// Commit the pending frequency edits of checks that did not stop the loop.
+void edits_finalize(ffcz_plan_s* p) {
+  for (auto& dg : p->groups) {
+    const int64_t slots = dg.n / 2;
+    const unsigned gx = (unsigned)std::min<int64_t>((slots + 255) / 256, 4096);
+    k_edits_finalize<<<dim3(gx, (unsigned)dg.count), 256, 0, p->stream>>>(dg.g, p->d_st, p->ed_f, p->ed_p,
+                                                                            p->ed_t, slots);
+    g_launches++;
+  }
+}
+
+// Canonical half-spectrum form of the committed frequency edits.
+void edits_canon(ffcz_plan_s* p) {
+  if (!p->ed_canon) p->ed_canon = (float2*)dalloc(p, sizeof(float2) * std::max<int64_t>(1, p->ed_total[1]));
+  for (auto& dg : p->groups) {
+    const int64_t nb = (int64_t)dg.Nz * (dg.ndim == 3 ? dg.Ny : 1) * (dg.M + 1);
+    const unsigned gx = (unsigned)std::min<int64_t>((nb + 255) / 256, 4096);
+    k_edits_canon<<<dim3(gx, (unsigned)dg.count), 256, 0, p->stream>>>(dg.g, p->ed_f, p->ed_canon, dg.d_canon);
+    g_launches++;
+  }
+}
+
+// CompactEdits + QuantizeEdits of both domains of every item into the
+// caller's arrays (regions from ed_layout); counts[2 i], counts[2 i + 1] get
+// item i's spatial and frequency nonzero counts.
+void edits_compact(ffcz_plan_s* p, int m, uint8_t* sf, int32_t* sc, uint8_t* ff, int32_t* fc, int64_t* counts) {
+  edits_canon(p);
+  const int64_t B = p->batch;
+  std::vector<EdRegion<float>> rs(B);
+  std::vector<EdRegion<float2>> rf(B);
+  int64_t chunks = 0, maxs = 1, maxf = 1;
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    chunks += (L[0] + kEdChunk - 1) / kEdChunk + (L[1] + kEdChunk - 1) / kEdChunk;
+    maxs = std::max<int64_t>(maxs, (L[0] + kEdChunk - 1) / kEdChunk);
+    maxf = std::max<int64_t>(maxf, (L[1] + kEdChunk - 1) / kEdChunk);
+  }
+  if (chunks > p->ed_chunk_cap) {
+    p->ed_chunks = (int*)dalloc(p, sizeof(int) * chunks);
+    p->ed_chunk_cap = chunks;
+  }
+  if (!p->ed_reg_s) {
+    p->ed_reg_s = dalloc(p, sizeof(EdRegion<float>) * B);
+    p->ed_reg_f = dalloc(p, sizeof(EdRegion<float2>) * B);
+    p->ed_tot = (int64_t*)dalloc(p, sizeof(int64_t) * 2 * B);
+  }
+  int64_t ch = 0;
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    const float qs = (float)p->h_prm[i].E * ldexpf(1.f, 1 - m);
+    const float qf = (float)p->h_prm[i].D * ldexpf(1.f, 1 - m);
+    int64_t canon = 0;
+    for (int64_t j = 0; j < i; ++j) canon += p->ed_layout[j][1];
+    rs[i] = {p->ed_s + p->eoff[i], L[0], sf + L[2], sc + L[3], p->ed_chunks + ch, qs};
+    ch += (L[0] + kEdChunk - 1) / kEdChunk;
+    rf[i] = {p->ed_canon + canon, L[1], ff + L[4], fc + L[5], p->ed_chunks + ch, qf};
+    ch += (L[1] + kEdChunk - 1) / kEdChunk;
+  }
+  cudaStream_t s = p->stream;
+  CK(cudaMemcpyAsync(p->ed_reg_s, rs.data(), sizeof(EdRegion<float>) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ed_reg_f, rf.data(), sizeof(EdRegion<float2>) * B, cudaMemcpyHostToDevice, s));
+  auto* ds = static_cast<const EdRegion<float>*>(p->ed_reg_s);
+  auto* df = static_cast<const EdRegion<float2>*>(p->ed_reg_f);
+  k_edits_count<float><<<dim3((unsigned)maxs, (unsigned)B), kEdThreads, 0, s>>>(ds);
+  k_edits_scan<float><<<(unsigned)B, 1024, 0, s>>>(ds, p->ed_tot);
+  k_edits_scatter<float><<<dim3((unsigned)maxs, (unsigned)B), kEdThreads, 0, s>>>(ds);
+  k_edits_count<float2><<<dim3((unsigned)maxf, (unsigned)B), kEdThreads, 0, s>>>(df);
+  k_edits_scan<float2><<<(unsigned)B, 1024, 0, s>>>(df, p->ed_tot + B);
+  k_edits_scatter<float2><<<dim3((unsigned)maxf, (unsigned)B), kEdThreads, 0, s>>>(df);
+  g_launches += 6;
+  std::vector<int64_t> tot(2 * B);
+  CK(cudaMemcpyAsync(tot.data(), p->ed_tot, sizeof(int64_t) * 2 * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (counts)
+    for (int64_t i = 0; i < B; ++i) { counts[2 * i] = tot[i]; counts[2 * i + 1] = tot[B + i]; }
+}
+
 template <typename T>
 void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
+  p->ed_on = p->opts.edits != 0;   // the loop's kernels record edits
+  struct Off { ffcz_plan_s* p; ~Off() { p->ed_on = false; } } off_{p};
   LoopBufs B = loop_bufs<T>(p);
   CK(cudaMemsetAsync(p->d_nactive, 0, sizeof(int), p->stream));
   k_init<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, (int)p->batch,
@@ -988,6 +1096,7 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
     }
   }
   exit_pass<T>(p, B, e, p->stream);
+  if (p->ed_on) edits_finalize(p);
 }
 
 void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
@@ -1156,6 +1265,12 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
   CK(cudaSetDevice(p->device));
   upload_params(p, eps_s, eps_f, p->opts.min_iters, p->opts.max_iters);
   CK(cudaEventRecord(p->ev0, p->stream));
+  if (p->opts.edits) {
+    CK(cudaMemsetAsync(p->ed_s, 0, sizeof(float) * p->total, p->stream));
+    CK(cudaMemsetAsync(p->ed_f, 0, sizeof(float2) * p->total_c, p->stream));
+    CK(cudaMemsetAsync(p->ed_p, 0, sizeof(float2) * p->total_c, p->stream));
+    CK(cudaMemsetAsync(p->ed_t, 0, sizeof(int) * p->total_c, p->stream));
+  }
   if (p->opts.precision == 64) run_loop<double>(p, e, false);
   else run_loop<float>(p, e, false);
   CK(cudaEventRecord(p->ev1, p->stream));
@@ -1571,6 +1686,7 @@ void ffcz_default_opts(ffcz_opts* o) {
   o->chunk = 16;
   o->use_graph = 2;
   o->count_active = 1;
+  o->edits = 0;
 }
 
 ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t batch,
@@ -1704,6 +1820,21 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       std::vector<int32_t> it(ids.begin(), ids.end());
       std::vector<int64_t> eo, so;
       for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(soff_c[id]); }
+      if (p->opts.edits && ndim > 1) {
+        std::vector<int64_t> co;
+        int64_t acc = 0;
+        std::vector<int64_t> canon(batch);
+        for (int64_t i = 0; i < batch; ++i) {
+          canon[i] = acc;
+          int64_t nb = 1;
+          for (int d = 0; d < ndim - 1; ++d) nb *= shapes[i * ndim + d];
+          acc += nb * (shapes[i * ndim + ndim - 1] / 2 + 1);
+        }
+        for (int id : ids) co.push_back(canon[id]);
+        int64_t* d_co = (int64_t*)dalloc(p.get(), sizeof(int64_t) * co.size());
+        CK(cudaMemcpy(d_co, co.data(), sizeof(int64_t) * co.size(), cudaMemcpyHostToDevice));
+        dg.d_canon = d_co;
+      }
       int32_t* d_it = (int32_t*)dalloc(p.get(), sizeof(int32_t) * it.size());
       int64_t* d_eo = (int64_t*)dalloc(p.get(), sizeof(int64_t) * eo.size());
       int64_t* d_so = (int64_t*)dalloc(p.get(), sizeof(int64_t) * so.size());
@@ -1764,6 +1895,29 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
     p->d_err = (int*)dalloc(p.get(), sizeof(int));
+    if (p->opts.edits) {
+      if (ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edit recording supports 2D and 3D items");
+      p->ed_layout.resize(batch);
+      std::array<int64_t, 6> acc{};
+      for (int64_t i = 0; i < batch; ++i) {
+        int64_t npt = 1, nb = 1;
+        for (int d = 0; d < ndim; ++d) npt *= shapes[i * ndim + d];
+        for (int d = 0; d < ndim - 1; ++d) nb *= shapes[i * ndim + d];
+        nb *= shapes[i * ndim + ndim - 1] / 2 + 1;
+        p->ed_layout[i] = {npt, nb, acc[2], acc[3], acc[4], acc[5]};
+        acc[0] += npt; acc[1] += nb;
+        acc[2] += (npt + 7) / 8; acc[3] += npt; acc[4] += (nb + 7) / 8; acc[5] += 2 * nb;
+      }
+      p->ed_total = acc;
+      p->ed_s = (float*)dalloc(p.get(), sizeof(float) * p->total);
+      p->ed_f = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
+      p->ed_p = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
+      p->ed_t = (int*)dalloc(p.get(), sizeof(int) * p->total_c);
+      CK(cudaMemset(p->ed_s, 0, sizeof(float) * p->total));
+      CK(cudaMemset(p->ed_f, 0, sizeof(float2) * p->total_c));
+      CK(cudaMemset(p->ed_p, 0, sizeof(float2) * p->total_c));
+      CK(cudaMemset(p->ed_t, 0, sizeof(int) * p->total_c));
+    }
     CK(cudaMemset(p->d_err, 0, sizeof(int)));
     CK(cudaMallocHost(&p->h_err, sizeof(int)));
     p->d_loopcount = (int*)dalloc(p.get(), sizeof(int));
@@ -1797,6 +1951,48 @@ ffcz_status ffcz_set_stream(ffcz_plan_t plan, void* s) {
 }
 
 size_t ffcz_workspace_bytes(ffcz_plan_t plan) { return plan ? plan->ws_bytes : 0; }
+
+ffcz_status ffcz_edit_layout(ffcz_plan_t plan, int64_t item, int64_t* out) {
+  if (!plan || !out) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (!plan->opts.edits) fail(FFCZ_ERR_INVALID, "the plan was created without opts.edits");
+    if (item < -1 || item >= plan->batch) fail(FFCZ_ERR_INVALID, "item out of range");
+    const auto& L = item < 0 ? plan->ed_total : plan->ed_layout[item];
+    for (int k = 0; k < 6; ++k) out[k] = L[k];
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_edits_dense(ffcz_plan_t plan, float* s_dev, float* f_dev) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (!plan->opts.edits) fail(FFCZ_ERR_INVALID, "the plan was created without opts.edits");
+    CK(cudaSetDevice(plan->device));
+    if (s_dev)
+      CK(cudaMemcpyAsync(s_dev, plan->ed_s, sizeof(float) * plan->total, cudaMemcpyDeviceToDevice, plan->stream));
+    if (f_dev) {
+      edits_canon(plan);
+      CK(cudaMemcpyAsync(f_dev, plan->ed_canon, sizeof(float2) * plan->ed_total[1], cudaMemcpyDeviceToDevice,
+                         plan->stream));
+    }
+    CK(cudaStreamSynchronize(plan->stream));
+    CK(cudaGetLastError());
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, int32_t* s_codes,
+                               uint8_t* f_flags, int32_t* f_codes, int64_t* counts) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (!plan->opts.edits) fail(FFCZ_ERR_INVALID, "the plan was created without opts.edits");
+    if (m_bits < 2 || m_bits > 30) fail(FFCZ_ERR_INVALID, "m_bits must be in [2, 30]");
+    if (!s_flags || !s_codes || !f_flags || !f_codes) fail(FFCZ_ERR_INVALID, "null edit array");
+    CK(cudaSetDevice(plan->device));
+    edits_compact(plan, m_bits, s_flags, s_codes, f_flags, f_codes, counts);
+    return FFCZ_OK;
+  });
+}
 
 int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len) {
   if (!plan) return -1;

@@ -94,7 +94,42 @@ struct Args {
   const CUtensorMap* tm_axis;
   const CUtensorMap* tm_chk;
   int* err;                // device error word (DevErr)
+  // Alg. 1 edit recording (null: off).  ed_s: spatial edits, float32 laid
+  // out like e.  Frequency edits in the packed spectrum layout: ed_f the
+  // committed sum, ed_p the displacement of the latest f-clip of each slot,
+  // ed_t 1 + the check index of that pending clip (0: none pending).
+  float* ed_s;
+  float2* ed_f;
+  float2* ed_p;
+  int* ed_t;
 };
+
+// Spatial edit of one complex register (two real points): S += (c - v).
+template <typename T>
+__device__ __forceinline__ void record_s(float2* at, T dx, T dy) {
+  if (dx != T(0) || dy != T(0)) {
+    float2 o = *at;
+    o.x += (float)dx;
+    o.y += (float)dy;
+    *at = o;
+  }
+}
+
+// Frequency edit of one packed slot clipped at check `t`: the previous
+// pending displacement (from an earlier check, so the loop went on after
+// it) is committed, this one becomes pending.
+__device__ __forceinline__ void record_f(const Args& a, int64_t slot, float dx, float dy, int t) {
+  if (dx == 0.f && dy == 0.f) return;
+  if (a.ed_t[slot] != 0) {
+    float2 f = a.ed_f[slot];
+    const float2 q = a.ed_p[slot];
+    f.x += q.x;
+    f.y += q.y;
+    a.ed_f[slot] = f;
+  }
+  a.ed_p[slot] = make_float2(dx, dy);
+  a.ed_t[slot] = t + 1;
+}
 
 __device__ __forceinline__ bool pred_ok(int pred, const ItemState& s, const ItemParams& p) {
   switch (pred) {
@@ -377,6 +412,9 @@ k_xfwd(Args a) {
     if (a.mode & M_PRECLIP) {
       const float cx = clampT(x.x, p.Esf), cy = clampT(x.y, p.Esf);
       cnt += (cx != x.x) + (cy != x.y);
+      if (a.ed_s && live)
+        record_s<float>(reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M + j + u * G_::NT,
+                        cx - x.x, cy - x.y);
       x.x = cx; x.y = cy;
       if (live) erow_w[j + u * G_::NT] = x;
     }
@@ -433,7 +471,7 @@ template <typename T, int M, class TL>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
                                                       int j, int64_t mthr, int64_t row, bool live,
                                                       int t_it, TL& tl, const v2<T>* twg,
-                                                      const v2<T>* twr) {
+                                                      const v2<T>* twr, float2* edrow = nullptr) {
   constexpr int V = F2<M>::V, NT = F2<M>::NT, MW = (V + 7) / 8;
   c2r_pre<T, M>(v, j, tl, twr);
   fft_pencil<T, M, +1>(v, j, twg, tl);
@@ -468,10 +506,12 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
     if ((a.mode & M_RECORD) && live) mb.store(a.mask, mthr);
   } else if (need_clip) {
     // lean path: only warps holding a value outside the s-cube clip
+    const bool rec_s = edrow != nullptr && live;
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       const T cx = clampT(v[u].x, Es), cy = clampT(v[u].y, Es);
       if (count) cnt += (cx != v[u].x) + (cy != v[u].y);
+      if (rec_s) record_s<T>(edrow + j + u * NT, cx - v[u].x, cy - v[u].y);   // spat_edits += eps' - eps
       v[u] = mk<T>(cx, cy);
     }
   }
@@ -489,7 +529,8 @@ k_px(Args a) {
 #pragma unroll
   for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
-  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr);
+  float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
+  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
@@ -646,7 +687,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
                                          const ChkTile& c, bool cta_has_mirror, TL& tl,
                                          const v2<T>* twg, unsigned long long* s_red,
                                          unsigned long long* acc_vb = nullptr,
-                                         unsigned long long* acc_cnt = nullptr) {
+                                         unsigned long long* acc_cnt = nullptr,
+                                         int64_t ed_slot0 = 0, int64_t ed_ustride = 0, int t_chk = 0) {
   constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
   fft_pencil<T, L, -1>(v, j, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
@@ -657,6 +699,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   mb.clear();
   const bool rec = (a.mode & M_RECORD) != 0, use_mask = (a.mode & M_MASK) != 0;
   const bool clip = (a.mode & M_CLIP) != 0, count = (a.mode & M_COUNT) != 0;
+  const bool rec_f = clip && a.ed_t != nullptr && c.owner;   // freq_edits += delta' - delta
   if (use_mask && c.live) mb.load(a.mask, mthr);
   if (cta_has_mirror) {
     store_nat<T, L, TL>(v, j, tl);
@@ -678,6 +721,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           mb.template put<4>(u, (uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) |
                                     ((uint32_t)ibi << 3));
           ar = car; ai = cai; br = cbr; bi = cbi;
+          if (rec_f) {
+            const T nx = ar - bi, ny = ai + br;
+            record_f(a, ed_slot0 + u * ed_ustride, (float)(nx - cc.x), (float)(ny - cc.y), t_chk);
+          }
         } else if (use_mask) {
           const uint32_t b4 = mb.template get<4>(u);
           if (!(b4 & 1u)) ar = T(0);
@@ -714,6 +761,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
         mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
+        if (rec_f) record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk);
         v[u] = mk<T>(cx, cy);
       }
     } else if (clip) {
@@ -760,7 +808,8 @@ k_chk(Args a) {
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
-  chk_core<T, L, TL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red);
+  chk_core<T, L, TL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
+                     a.g.soff[gi] + c.off + j * estride, ustride, t_it);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
@@ -904,7 +953,8 @@ k_chk_tma(Args a) {
     }
     TL tl{s_tiles + w, false};
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
-    chk_core<float, L, TL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red, &acc_vb, &acc_cnt);
+    chk_core<float, L, TL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red, &acc_vb, &acc_cnt,
+                           a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
 #pragma unroll
@@ -1004,7 +1054,8 @@ k_px_tma(Args a) {
     const int64_t row = live ? prow : 0;
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
     TL tl{s_tiles + g * TL::ELEMS + w, false};
-    cnt += px_core<float, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr);
+    float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
+    cnt += px_core<float, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow);
     if (live) {
       float2* out = outb + row * M;
 #pragma unroll
@@ -1017,6 +1068,31 @@ k_px_tma(Args a) {
     Red r{0ull, 0.0, cnt};
     block_reduce(r, s_red);
     if (threadIdx.x == 0 && r.cnt) atomicAdd(&st.act_s, r.cnt);
+  }
+}
+
+// After a loop: a pending frequency edit from a check before the last one
+// was applied (the loop went on) and is committed; one from the last check
+// (which stopped the loop, Alg. 1: no projection there) is dropped.  Every
+// slot of every member of the group; grid (x: slots, y: members).
+static __global__ void k_edits_finalize(Group g, const ItemState* st, float2* ed_f, float2* ed_p,
+                                        int* ed_t, int64_t slots_per_item) {
+  const int gi = blockIdx.y;
+  const int T = st[g.item[gi]].t;
+  const int64_t base = g.soff[gi];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < slots_per_item;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int tg = ed_t[base + i];
+    if (tg == 0) continue;
+    if (tg - 1 < T) {
+      float2 f = ed_f[base + i];
+      const float2 q = ed_p[base + i];
+      f.x += q.x;
+      f.y += q.y;
+      ed_f[base + i] = f;
+    }
+    ed_t[base + i] = 0;
+    ed_p[base + i] = make_float2(0.f, 0.f);
   }
 }
 

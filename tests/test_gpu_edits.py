@@ -1,0 +1,113 @@
+"""Alg. 1 edits recorded by the GPU loop (opts.edits) vs the FP64 oracle.
+
+Bars: after k forced iterations the dense spatial edits match the oracle's
+to 1e-3 eps_s and the frequency edits to 1e-3 eps_f (plus float32 rounding of
+the spectrum); the GPU's own output satisfies e_out - e_in = S + IFFT(F) to
+1e-4 eps_s (in converged runs too, where the stopping check's clip must not be
+recorded); flags and codes are bit-exact against the oracle's CompactEdits /
+QuantizeEdits applied to the GPU's float32 edits in float32.
+"""
+import numpy as np
+import pytest
+
+from oracle import ffcz_oracle as O
+from paper_2601_01596_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def stress(shape, seed, frac=0.4):
+    e0 = W.bimodal_error(shape, seed, E=1.0, dtype=np.float32)
+    return e0, 1.0, frac * O.f_violation(O.dft(e0.astype(np.float64)))
+
+
+def run(items, Es, Ds, **opts):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shapes = [x.shape for x in items]
+    plan = ffcz.Plan(shapes, edits=1, **opts)
+    t = torch.from_numpy(np.concatenate([x.reshape(-1) for x in items]).astype(np.float32)).cuda()
+    st = plan.correct(t, Es, Ds)
+    S, F = plan.edits_dense()
+    torch.cuda.synchronize()
+    return plan, t.cpu().numpy(), st, S.cpu().numpy(), F.cpu().numpy()
+
+
+def split(plan, S, F, shapes):
+    out = []
+    for i, sh in enumerate(shapes):
+        npt, nb, *_ = plan.edit_layout(i)
+        s0 = sum(plan.edit_layout(j)[0] for j in range(i))
+        f0 = sum(plan.edit_layout(j)[1] for j in range(i))
+        half = tuple(sh[:-1]) + (sh[-1] // 2 + 1,)
+        out.append((S[s0:s0 + npt].reshape(sh), F[f0:f0 + nb].reshape(half)))
+    return out
+
+
+@pytest.mark.parametrize("shape,k", [((32, 32, 32), 3), ((64, 128), 4), ((16, 32, 64), 2)])
+def test_forced_iterations_edits_match_oracle(shape, k):
+    e0, E, D = stress(shape, 70)
+    ref = O.correct(e0, E, D, min_iters=k, max_iters=k, edits=True)
+    plan, e, st, S, F = run([e0], [E], [D], min_iters=k, max_iters=k, certify=0)
+    assert st[0]["iters"] == k
+    (Sg, Fg), = split(plan, S, F, [shape])
+    np.testing.assert_allclose(Sg, ref.spat_edits, rtol=0, atol=1e-3 * E)
+    Fh = O.half_spectrum(ref.freq_edits)
+    np.testing.assert_allclose(Fg, Fh, rtol=0, atol=1e-3 * D + 1e-5 * np.max(np.abs(Fh)))
+    assert np.count_nonzero(Sg) > 0 and np.count_nonzero(Fg) > 0
+    # the GPU's own trajectory: e_k - e_0 = S + IFFT(F)
+    disp = Sg.astype(np.float64) + np.fft.irfftn(Fg.astype(np.complex128), s=shape, axes=tuple(range(len(shape))))
+    np.testing.assert_allclose(e.reshape(shape) - e0, disp, rtol=0, atol=1e-4 * E)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (256, 64)])
+def test_converged_run_drops_the_stopping_clip(shape):
+    e0, E, D = stress(shape, 71)
+    plan, e, st, S, F = run([e0], [E], [D])
+    assert st[0]["status"] == 0 and st[0]["iters"] >= 2 and st[0]["certified"] == 1
+    (Sg, Fg), = split(plan, S, F, [shape])
+    disp = Sg.astype(np.float64) + np.fft.irfftn(Fg.astype(np.complex128), s=shape, axes=tuple(range(len(shape))))
+    np.testing.assert_allclose(e.reshape(shape) - e0, disp, rtol=0, atol=1e-4 * E)
+
+
+def test_preclip_recorded_as_spatial_edit():
+    e0, E, D = stress((32, 64), 72)
+    e0 = e0.copy(); e0[3, 5] = 1.75; e0[20, 7] = -2.5
+    plan, e, st, S, F = run([e0], [E], [D])
+    assert st[0]["preclipped"] == 1
+    (Sg, Fg), = split(plan, S, F, [(32, 64)])
+    disp = Sg.astype(np.float64) + np.fft.irfftn(Fg.astype(np.complex128), s=(32, 64), axes=(0, 1))
+    np.testing.assert_allclose(e.reshape(32, 64) - e0, disp, rtol=0, atol=1e-4 * E)
+
+
+def test_compaction_bit_exact_against_oracle_quantizer():
+    shapes = [(32, 32, 32), (16, 32, 64), (32, 32, 32)]
+    items, Es, Ds = [], [], []
+    for i, sh in enumerate(shapes):
+        e0, E, D = stress(sh, 73 + i)
+        items.append(e0); Es.append(E * (1 + 0.5 * i)); Ds.append(D * (1 + 0.25 * i))
+        items[-1] = (items[-1] * (1 + 0.5 * i)).astype(np.float32)
+    plan, e, st, S, F = run(items, Es, Ds)
+    for m in (16, 12):
+        c = plan.edits_compact(m)
+        sf, sc = c["s_flags"].cpu().numpy(), c["s_codes"].cpu().numpy()
+        ff, fc = c["f_flags"].cpu().numpy(), c["f_codes"].cpu().numpy()
+        for i, (Sg, Fg) in enumerate(split(plan, S, F, shapes)):
+            npt, nb, so, sco, fo, fco = plan.edit_layout(i)
+            flags, comp = O.compact_edits(Sg)
+            np.testing.assert_array_equal(sf[so:so + flags.size], flags)
+            assert c["counts"][i, 0] == comp.size
+            want = O.quantize_edits(comp.astype(np.float32), Es[i], m, dtype=np.float32)
+            np.testing.assert_array_equal(sc[sco:sco + comp.size], want)
+            flags, comp = O.compact_edits(Fg)
+            np.testing.assert_array_equal(ff[fo:fo + flags.size], flags)
+            assert c["counts"][i, 1] == comp.size
+            want = O.quantize_edits(comp.astype(np.complex64), Ds[i], m, dtype=np.float32)
+            np.testing.assert_array_equal(fc[fco:fco + 2 * comp.size].reshape(-1, 2), want)
+
+
+def test_edits_off_by_default_and_plan_without_edits_refuses():
+    import paper_2601_01596_b300 as ffcz
+    plan = ffcz.Plan([(32, 32)])
+    with pytest.raises(Exception):
+        plan.edit_layout(-1)
