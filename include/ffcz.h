@@ -136,8 +136,8 @@ size_t ffcz_workspace_bytes(ffcz_plan_t plan);
  * exact arithmetic e_out - e_in = spatial edits + IFFT(frequency edits).
  * The edits describe the last ffcz_correct call on the plan.
  *
- * ffcz_edit_layout -- sizes and offsets for item `item` (0-based), or the
- * totals for item = -1, into out[6] (host): points, half-spectrum bins,
+ * ffcz_edit_layout -- (any 2D/3D plan) sizes and offsets for item `item`
+ * (0-based), or the totals for item = -1, into out[6] (host): points, half-spectrum bins,
  * offset of the item's spatial flags (bytes), spatial codes (int32), frequency
  * flags (bytes), frequency codes (int32; two per bin).  For item = -1 the
  * last four are the array sizes ffcz_edits_compact needs.
@@ -161,6 +161,21 @@ ffcz_status ffcz_edit_layout(ffcz_plan_t plan, int64_t item, int64_t* out);
 ffcz_status ffcz_edits_dense(ffcz_plan_t plan, float* s_dev, float* f_dev);
 ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, int32_t* s_codes,
                                uint8_t* f_flags, int32_t* f_codes, int64_t* counts);
+
+/*
+ * ffcz_apply_edits -- the decompression side (Sec. IV-B, "Applying edits to
+ * the decompressed data"): x_hat += S~ + IFFT(F~), where S~ and F~ are the
+ * dequantized edits (code * q, q = 2 eps / 2^m_bits, eps = eps_s / eps_f per
+ * item) given in the stored form of ffcz_edits_compact (flags and codes at
+ * the offsets of ffcz_edit_layout; device memory, read only).  xhat_dev:
+ * device float32, the packed items of the base reconstruction, updated in
+ * place.  Any 2D/3D plan (opts.edits not needed); uses the plan's spectrum
+ * buffers, so it must not overlap a ffcz_correct call on the same plan.
+ * Synchronises the plan's stream.
+ */
+ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* eps_s, const double* eps_f,
+                             int m_bits, const uint8_t* s_flags, const int32_t* s_codes,
+                             const uint8_t* f_flags, const int32_t* f_codes);
 
 /*
  * ffcz_plan_describe -- one line per item group: the group's shape, member

@@ -27,7 +27,7 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
            "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
-           "ffcz_edits_compact")
+           "ffcz_edits_compact", "ffcz_apply_edits")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.ffcz_edit_layout.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64)]
         L.ffcz_edits_dense.argtypes = [vp, vp, vp]
         L.ffcz_edits_compact.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+        L.ffcz_apply_edits.argtypes = [vp, vp, dp, dp, i32, vp, vp, vp, vp]
         L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
@@ -234,6 +235,15 @@ class Plan:
                                         counts))
         d["counts"] = np.array(counts, dtype=np.int64).reshape(self.batch, 2)
         return d
+
+    def apply_edits(self, xhat, eps_s, eps_f, stored, m_bits: int = 16, stream=None):
+        """x_hat += S~ + IFFT(F~) from the stored form (``edits_compact``'s
+        dict: s_flags, s_codes, f_flags, f_codes); ``xhat`` float32 CUDA, the
+        packed items, updated in place."""
+        self._bind_stream(stream)
+        ptrs = [ctypes.c_void_p(stored[k].data_ptr()) for k in ("s_flags", "s_codes", "f_flags", "f_codes")]
+        _check(lib().ffcz_apply_edits(self._h, self._ptr(xhat, "xhat"), _dbl(eps_s, self.batch),
+                                      _dbl(eps_f, self.batch), m_bits, *ptrs))
 
     def describe(self) -> str:
         """Item groups and the pass variants the tuner chose for them."""

@@ -152,4 +152,117 @@ static __global__ void k_edits_scatter(const EdRegion<C>* regs) {
     if (byte & (1u << t)) put_codes(r.codes, k++, r.vals[b * 8 + t], r.q);
 }
 
+// ----- decompression side: edits from their stored form ----------------------
+// (Sec. IV-B, "Applying edits to the decompressed data")
+
+struct ApRegion {
+  const uint8_t* flags;
+  const int32_t* codes;
+  int64_t n;
+  int* chunks;
+  float q;
+  float* xhat;      // spatial: the item's reconstruction (edits added in place)
+  float2* dense;    // frequency: the item's canonical half spectrum (written)
+};
+
+// Nonzero components per chunk from the flag bytes.
+static __global__ void k_apply_count(const ApRegion* regs) {
+  const ApRegion r = regs[blockIdx.y];
+  const int64_t c0 = (int64_t)blockIdx.x * kEdChunk;
+  if (c0 >= r.n) return;
+  const int64_t b = c0 / 8 + threadIdx.x;
+  int cnt = (b * 8 < r.n) ? __popc((unsigned)r.flags[b]) : 0;
+  __shared__ int s[kEdThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kEdThreads / 32; ++w) t += s[w];
+    r.chunks[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the chunk counts (one CTA per region).
+static __global__ void k_apply_scan(const ApRegion* regs) {
+  const ApRegion r = regs[blockIdx.x];
+  const int64_t nch = (r.n + kEdChunk - 1) / kEdChunk;
+  __shared__ long long carry;
+  __shared__ long long s[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nch; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const long long v = i < nch ? r.chunks[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+      const long long add = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nch) r.chunks[i] = (int)(carry + s[threadIdx.x] - v);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// Dequantize (code * q) and place: spatial edits are added to x_hat,
+// frequency edits written densely (zero where the flag is clear).
+template <bool FREQ>
+static __global__ void k_apply_expand(const ApRegion* regs) {
+  const ApRegion r = regs[blockIdx.y];
+  const int64_t c0 = (int64_t)blockIdx.x * kEdChunk;
+  if (c0 >= r.n) return;
+  const int64_t b = c0 / 8 + threadIdx.x;
+  const unsigned byte = (b * 8 < r.n) ? r.flags[b] : 0u;
+  const int cnt = __popc(byte);
+  __shared__ int s[kEdThreads / 32];
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((threadIdx.x & 31) >= (unsigned)o) incl += y;
+  }
+  if ((threadIdx.x & 31) == 31) s[threadIdx.x >> 5] = incl;
+  __syncthreads();
+  int wbase = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbase += s[w];
+  int64_t k = (int64_t)r.chunks[blockIdx.x] + wbase + incl - cnt;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t i = b * 8 + t;
+    if (i >= r.n) break;
+    const bool on = (byte >> t) & 1u;
+    if constexpr (FREQ) {
+      r.dense[i] = on ? make_float2((float)r.codes[2 * k] * r.q, (float)r.codes[2 * k + 1] * r.q)
+                      : make_float2(0.f, 0.f);
+    } else if (on) {
+      r.xhat[i] += (float)r.codes[k] * r.q;
+    }
+    k += on;
+  }
+}
+
+// Canonical half spectrum -> packed layout (kx = 0 slot = A + iB with
+// A, B the kx = 0 and kx = Nx/2 planes).  Grid (x: slots, y: members).
+static __global__ void k_edits_pack(Group g, const float2* canon, const int64_t* coff, float2* packed) {
+  const int gi = blockIdx.y;
+  const int Nz = g.Nz, Ny = g.Nmid, M = g.M;
+  const int64_t ns = (int64_t)Nz * Ny * M;
+  const float2* c = canon + coff[gi];
+  float2* o = packed + g.soff[gi];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % M);
+    const int64_t r = i / M;
+    if (kx) {
+      o[i] = c[r * (M + 1) + kx];
+    } else {
+      const float2 A = c[r * (M + 1)], B = c[r * (M + 1) + M];
+      o[i] = make_float2(A.x - B.y, A.y + B.x);
+    }
+  }
+}
+
 }  // namespace ffcz

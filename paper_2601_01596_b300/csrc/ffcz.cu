@@ -178,6 +178,7 @@ struct ffcz_plan_s {
   void* ed_reg_s = nullptr;      // device EdRegion<float>[batch]
   void* ed_reg_f = nullptr;      // device EdRegion<float2>[batch]
   int64_t* ed_tot = nullptr;     // device per-region counts [2 batch]
+  void* ap_reg = nullptr;        // device ApRegion[2 batch] (edit application)
   int64_t ed_chunk_cap = 0;
   int* h_err = nullptr;         // pinned copy
   int num_sms = 148;
@@ -1060,6 +1061,79 @@ void edits_compact(ffcz_plan_s* p, int m, uint8_t* sf, int32_t* sc, uint8_t* ff,
     for (int64_t i = 0; i < B; ++i) { counts[2 * i] = tot[i]; counts[2 * i + 1] = tot[B + i]; }
 }
 
+// Applying edits (Sec. IV-B): x_hat += S~ + IFFT(F~) from the stored form
+// (flags and codes at the offsets of ed_layout).  Spatial codes are added in
+// place; frequency codes are expanded to the canonical half spectrum, packed,
+// and transformed back by the inverse passes (outer axis, middle axis, x C2R
+// with 1/N), the last of which adds its result to x_hat.
+void apply_edits(ffcz_plan_s* p, float* xhat, int m, const uint8_t* sf, const int32_t* sc,
+                 const uint8_t* ff, const int32_t* fc) {
+  const int64_t B = p->batch;
+  if (!p->ed_canon) p->ed_canon = (float2*)dalloc(p, sizeof(float2) * std::max<int64_t>(1, p->ed_total[1]));
+  int64_t chunks = 0, maxs = 1, maxf = 1;
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    chunks += (L[0] + kEdChunk - 1) / kEdChunk + (L[1] + kEdChunk - 1) / kEdChunk;
+    maxs = std::max<int64_t>(maxs, (L[0] + kEdChunk - 1) / kEdChunk);
+    maxf = std::max<int64_t>(maxf, (L[1] + kEdChunk - 1) / kEdChunk);
+  }
+  if (chunks > p->ed_chunk_cap) {
+    p->ed_chunks = (int*)dalloc(p, sizeof(int) * chunks);
+    p->ed_chunk_cap = chunks;
+  }
+  if (!p->ap_reg) p->ap_reg = dalloc(p, sizeof(ApRegion) * 2 * B);
+  std::vector<ApRegion> r(2 * B);
+  int64_t ch = 0, canon = 0;
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    const float qs = (float)p->h_prm[i].E * ldexpf(1.f, 1 - m);
+    const float qf = (float)p->h_prm[i].D * ldexpf(1.f, 1 - m);
+    r[i] = {sf + L[2], sc + L[3], L[0], p->ed_chunks + ch, qs, xhat + p->eoff[i], nullptr};
+    ch += (L[0] + kEdChunk - 1) / kEdChunk;
+    r[B + i] = {ff + L[4], fc + L[5], L[1], p->ed_chunks + ch, qf, nullptr, p->ed_canon + canon};
+    ch += (L[1] + kEdChunk - 1) / kEdChunk;
+    canon += L[1];
+  }
+  cudaStream_t s = p->stream;
+  CK(cudaMemcpyAsync(p->ap_reg, r.data(), sizeof(ApRegion) * 2 * B, cudaMemcpyHostToDevice, s));
+  auto* rs = static_cast<const ApRegion*>(p->ap_reg);
+  auto* rf = rs + B;
+  k_apply_count<<<dim3((unsigned)maxs, (unsigned)B), kEdThreads, 0, s>>>(rs);
+  k_apply_scan<<<(unsigned)B, 1024, 0, s>>>(rs);
+  k_apply_expand<false><<<dim3((unsigned)maxs, (unsigned)B), kEdThreads, 0, s>>>(rs);
+  k_apply_count<<<dim3((unsigned)maxf, (unsigned)B), kEdThreads, 0, s>>>(rf);
+  k_apply_scan<<<(unsigned)B, 1024, 0, s>>>(rf);
+  k_apply_expand<true><<<dim3((unsigned)maxf, (unsigned)B), kEdThreads, 0, s>>>(rf);
+  g_launches += 6;
+  for (auto& dg : p->groups) {
+    const int Nmid = dg.ndim == 3 ? dg.Ny : 1;
+    const int64_t slots = (int64_t)dg.Nz * Nmid * dg.M;
+    const unsigned gx = (unsigned)std::min<int64_t>((slots + 255) / 256, 4096);
+    k_edits_pack<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->ed_canon, dg.d_canon,
+                                                              static_cast<float2*>(p->B32[0]));
+    g_launches++;
+    Args a = make_args<float>(p, dg, p->B32[0], p->B32[0], p->d_st);
+    a.pred = P_ALL;
+    a.sel_in = a.sel_out = S_CUR;
+    // outer axis as a [Nz][Nmid M] view (pencils of length Nz, stride Nmid M)
+    Args az = a;
+    az.g.Nz = 1;
+    az.g.M = Nmid * dg.M;
+    az.tw = tw_of<float>(p->tb, dg.Nz);
+    launch_axis<float, +1>(dg.Nz, dg.wa, az, 1, Nmid * dg.M, dg.count, s);
+    if (dg.ndim == 3) {
+      a.tw = tw_of<float>(p->tb, dg.Ny);
+      launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
+    }
+    tabs_x<float>(p, a, dg);
+    a.e = xhat;
+    a.mode = M_ACC;
+    launch_x<float>(XEXIT, dg.M, dg.wx, a, dg.rows, dg.count, s);
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+}
+
 template <typename T>
 void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
   p->ed_on = p->opts.edits != 0;   // the loop's kernels record edits
@@ -1820,7 +1894,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       std::vector<int32_t> it(ids.begin(), ids.end());
       std::vector<int64_t> eo, so;
       for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(soff_c[id]); }
-      if (p->opts.edits && ndim > 1) {
+      if (ndim > 1) {
         std::vector<int64_t> co;
         int64_t acc = 0;
         std::vector<int64_t> canon(batch);
@@ -1879,6 +1953,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
           launch_axis<double, +1>(dg.Ny < 8 ? 8 : dg.Ny, dg.wa, a, 1, dg.M, 1, nullptr);
           launch_chk<float>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
           launch_chk<double>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
+          launch_axis<float, +1>(dg.Nz, dg.wa, a, 1, dg.M, 1, nullptr);   // edit application
         }
       }
     } catch (...) {
@@ -1895,8 +1970,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
     p->d_err = (int*)dalloc(p.get(), sizeof(int));
-    if (p->opts.edits) {
-      if (ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edit recording supports 2D and 3D items");
+    if (p->opts.edits && ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edit recording supports 2D and 3D items");
+    if (ndim > 1) {
       p->ed_layout.resize(batch);
       std::array<int64_t, 6> acc{};
       for (int64_t i = 0; i < batch; ++i) {
@@ -1909,6 +1984,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         acc[2] += (npt + 7) / 8; acc[3] += npt; acc[4] += (nb + 7) / 8; acc[5] += 2 * nb;
       }
       p->ed_total = acc;
+    }
+    if (p->opts.edits) {
       p->ed_s = (float*)dalloc(p.get(), sizeof(float) * p->total);
       p->ed_f = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
       p->ed_p = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
@@ -1955,7 +2032,7 @@ size_t ffcz_workspace_bytes(ffcz_plan_t plan) { return plan ? plan->ws_bytes : 0
 ffcz_status ffcz_edit_layout(ffcz_plan_t plan, int64_t item, int64_t* out) {
   if (!plan || !out) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
-    if (!plan->opts.edits) fail(FFCZ_ERR_INVALID, "the plan was created without opts.edits");
+    if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edits exist for 2D and 3D items");
     if (item < -1 || item >= plan->batch) fail(FFCZ_ERR_INVALID, "item out of range");
     const auto& L = item < 0 ? plan->ed_total : plan->ed_layout[item];
     for (int k = 0; k < 6; ++k) out[k] = L[k];
@@ -1990,6 +2067,22 @@ ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, i
     if (!s_flags || !s_codes || !f_flags || !f_codes) fail(FFCZ_ERR_INVALID, "null edit array");
     CK(cudaSetDevice(plan->device));
     edits_compact(plan, m_bits, s_flags, s_codes, f_flags, f_codes, counts);
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* eps_s, const double* eps_f,
+                             int m_bits, const uint8_t* s_flags, const int32_t* s_codes,
+                             const uint8_t* f_flags, const int32_t* f_codes) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edits exist for 2D and 3D items");
+    if (!xhat_dev || !eps_s || !eps_f || !s_flags || !s_codes || !f_flags || !f_codes)
+      fail(FFCZ_ERR_INVALID, "null pointer argument");
+    if (m_bits < 2 || m_bits > 30) fail(FFCZ_ERR_INVALID, "m_bits must be in [2, 30]");
+    CK(cudaSetDevice(plan->device));
+    upload_params(plan, eps_s, eps_f, 0, 0);
+    apply_edits(plan, xhat_dev, m_bits, s_flags, s_codes, f_flags, f_codes);
     return FFCZ_OK;
   });
 }

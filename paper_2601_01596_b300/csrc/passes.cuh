@@ -68,7 +68,8 @@ enum Pred : int { P_ALL = 0, P_ACTIVE = 1, P_EXIT = 2, P_PRECLIP = 3, P_UNCERT =
 enum Sel : int { S_CUR = 0, S_PREV = 1 };
 enum Mode : int {
   M_CLIP = 1, M_MASK = 2, M_RECORD = 4, M_MEASURE = 8, M_PRECLIP = 16, M_NOWRITE = 32,
-  M_CKPT = 64, M_COUNT = 128
+  M_CKPT = 64, M_COUNT = 128,
+  M_ACC = 256   // exit x pass: add the result to e instead of storing it
 };
 
 struct Args {
@@ -569,6 +570,10 @@ k_xexit(Args a) {
       if (a.mode & M_CLIP) {
         // keep the float32 result inside the shrunk cube after rounding
         fx = clampT(fx, p.Esf); fy = clampT(fy, p.Esf);
+      }
+      if (a.mode & M_ACC) {
+        const float2 o = erow[j + u * G_::NT];
+        fx += o.x; fy += o.y;
       }
       erow[j + u * G_::NT] = make_float2(fx, fy);
     }

@@ -109,5 +109,46 @@ def test_compaction_bit_exact_against_oracle_quantizer():
 def test_edits_off_by_default_and_plan_without_edits_refuses():
     import paper_2601_01596_b300 as ffcz
     plan = ffcz.Plan([(32, 32)])
-    with pytest.raises(Exception):
-        plan.edit_layout(-1)
+    assert plan.edit_layout(-1)[:2] == (32 * 32, 32 * 17)     # layout exists for application
+    with pytest.raises(ffcz.FFCzError):
+        plan.edits_dense()
+    with pytest.raises(ffcz.FFCzError):
+        plan.edits_compact()
+
+
+@pytest.mark.parametrize("shapes", [[(32, 32, 32)], [(64, 128), (32, 256)], [(16, 32, 64), (16, 32, 64)]])
+def test_apply_edits_matches_oracle_application(shapes):
+    """Decompression side: x_hat + S~ + IFFT(F~) from the stored codes, GPU vs
+    the oracle's apply_edits on the same dequantized edits."""
+    import torch
+    items, Es, Ds = [], [], []
+    for i, sh in enumerate(shapes):
+        e0, E, D = stress(sh, 80 + i)
+        items.append(e0); Es.append(E); Ds.append(D)
+    plan, e, st, S, F = run(items, Es, Ds)
+    stored = plan.edits_compact(16)
+    rng = np.random.default_rng(81)
+    xs = [rng.standard_normal(sh) for sh in shapes]
+    xhat = np.concatenate([(x + e0).reshape(-1) for x, e0 in zip(xs, items)]).astype(np.float32)
+    t = torch.from_numpy(xhat.copy()).cuda()
+    plan.apply_edits(t, Es, Ds, stored, 16)
+    got = t.cpu().numpy()
+    sf, sc = stored["s_flags"].cpu().numpy(), stored["s_codes"].cpu().numpy()
+    ff, fc = stored["f_flags"].cpu().numpy(), stored["f_codes"].cpu().numpy()
+    off = 0
+    for i, sh in enumerate(shapes):
+        npt, nb, so, sco, fo, fco = plan.edit_layout(i)
+        ns, nf = stored["counts"][i]
+        half = tuple(sh[:-1]) + (sh[-1] // 2 + 1,)
+        Sq = O.expand_edits(sf[so:so + (npt + 7) // 8],
+                            O.dequantize_edits(sc[sco:sco + ns], Es[i], 16), npt).reshape(sh)
+        Fq = O.expand_edits(ff[fo:fo + (nb + 7) // 8],
+                            O.dequantize_edits(fc[fco:fco + 2 * nf].reshape(-1, 2), Ds[i], 16, complex_pairs=True),
+                            nb).reshape(half)
+        want = O.apply_edits(xhat[off:off + npt].reshape(sh).astype(np.float64), Sq, Fq)
+        scale = np.max(np.abs(want))
+        np.testing.assert_allclose(got[off:off + npt].reshape(sh), want, rtol=0, atol=2e-6 * scale)
+        # and the round trip lands within quantization error of x + e_out
+        np.testing.assert_allclose(got[off:off + npt].reshape(sh), xs[i] + e[off:off + npt].reshape(sh),
+                                   rtol=0, atol=1e-3 * Es[i] + 2e-6 * scale)
+        off += npt
