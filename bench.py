@@ -402,6 +402,36 @@ def paper_design_cufft(torch, it, D, hbm, K=20):
             "iterations": K}
 
 
+def edits_form(ffcz, torch, it, D):
+    """Alg. 1 edits on the stress variant: the call with edit recording vs
+    without, CompactEdits + QuantizeEdits (m = 16), and the decompression
+    side x_hat += S~ + IFFT(F~) (CUDA events; median of 2 after 1 warm-up)."""
+    shape, E = it["shape"], it["E"]
+    n = int(np.prod(shape))
+    d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
+    d = torch.empty_like(d0)
+    plain = ffcz.Plan([shape])
+    ms_plain, _ = _timed(torch, lambda: plain.correct(d.copy_(d0), [E], [D]))
+    del plain
+    plan = ffcz.Plan([shape], edits=1)
+    ms_edits, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [D])[0])
+    copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
+    ms_compact, stored = _timed(torch, lambda: plan.edits_compact(16))
+    xhat = torch.zeros_like(d0)
+    ms_apply, _ = _timed(torch, lambda: plan.apply_edits(xhat, [E], [D], stored, 16))
+    ns, nf = (int(v) for v in stored["counts"][0])
+    tot = plan.edit_layout(-1)
+    stored_bytes = tot[2] + tot[4] + 2 * ns + 4 * nf      # flags + 16-bit codes (Re, Im for bins)
+    del plan
+    return {"workload": it["name"] + " stress bounds, edits recorded",
+            "iters": st["iters"], "ms_correct_plain": round(ms_plain - copy_ms, 3),
+            "ms_correct_with_edits": round(ms_edits - copy_ms, 3),
+            "ms_compact_quantize": round(ms_compact, 3), "ms_apply": round(ms_apply, 3),
+            "spatial_edits": ns, "frequency_edits": nf,
+            "stored_bytes_before_lossless": int(stored_bytes),
+            "field_bytes": 4 * n}
+
+
 def measure_forms(ffcz, torch, fin, it, hbm):
     """The stress variant, the batched and the differentiable forms (each a
     median of 2 calls after 1 warm-up; CUDA events on the current stream)."""
@@ -422,6 +452,8 @@ def measure_forms(ffcz, torch, fin, it, hbm):
     del plan, d, d0
     torch.cuda.empty_cache()
     out["paper_design_cufft"] = paper_design_cufft(torch, it, fin["stress_D"], hbm)
+    torch.cuda.empty_cache()
+    out["edits_stress_512"] = edits_form(ffcz, torch, it, fin["stress_D"])
     torch.cuda.empty_cache()
     out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
                                     "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")

@@ -106,30 +106,28 @@ struct Args {
 };
 
 // Spatial edit of one complex register (two real points): S += (c - v).
+// Each slot is touched by one thread per pass, so the add is a plain
+// fire-and-forget reduction (no load on the thread's critical path) with
+// the same result as a load, add and store.
 template <typename T>
 __device__ __forceinline__ void record_s(float2* at, T dx, T dy) {
-  if (dx != T(0) || dy != T(0)) {
-    float2 o = *at;
-    o.x += (float)dx;
-    o.y += (float)dy;
-    *at = o;
-  }
+  if (dx != T(0) || dy != T(0)) atomicAdd(at, make_float2((float)dx, (float)dy));
 }
 
-// Frequency edit of one packed slot clipped at check `t`: the previous
-// pending displacement (from an earlier check, so the loop went on after
-// it) is committed, this one becomes pending.
-__device__ __forceinline__ void record_f(const Args& a, int64_t slot, float dx, float dy, int t) {
+// Frequency edit of one packed slot clipped at check `t`: F += d.  Only a
+// check whose violation is at most the stopping threshold can stop the loop
+// (Alg. 1 projects nothing there), so a clip of a value above the threshold,
+// or before min_iters, is final; a "marginal" clip also keeps d and 1 + t
+// so that the edits pass after the loop can take it back if check t was the
+// one that stopped.  Clips at the max_iters check are not recorded at all.
+__device__ __forceinline__ void record_f(const Args& a, int64_t slot, float dx, float dy, int t,
+                                         bool marginal) {
   if (dx == 0.f && dy == 0.f) return;
-  if (a.ed_t[slot] != 0) {
-    float2 f = a.ed_f[slot];
-    const float2 q = a.ed_p[slot];
-    f.x += q.x;
-    f.y += q.y;
-    a.ed_f[slot] = f;
+  atomicAdd(a.ed_f + slot, make_float2(dx, dy));   // one writer per slot and pass
+  if (marginal) {
+    a.ed_p[slot] = make_float2(dx, dy);
+    a.ed_t[slot] = t + 1;
   }
-  a.ed_p[slot] = make_float2(dx, dy);
-  a.ed_t[slot] = t + 1;
 }
 
 __device__ __forceinline__ bool pred_ok(int pred, const ItemState& s, const ItemParams& p) {
@@ -704,7 +702,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   mb.clear();
   const bool rec = (a.mode & M_RECORD) != 0, use_mask = (a.mode & M_MASK) != 0;
   const bool clip = (a.mode & M_CLIP) != 0, count = (a.mode & M_COUNT) != 0;
-  const bool rec_f = clip && a.ed_t != nullptr && c.owner;   // freq_edits += delta' - delta
+  // freq_edits += delta' - delta (not at the max_iters check, which stops)
+  const bool rec_f = clip && a.ed_t != nullptr && c.owner && t_chk < p.max_iters;
+  const bool may_stop = t_chk >= p.min_iters;
+  const T thr = sizeof(T) == 4 ? (T)p.thrf : (T)p.thr;
   if (use_mask && c.live) mb.load(a.mask, mthr);
   if (cta_has_mirror) {
     store_nat<T, L, TL>(v, j, tl);
@@ -728,7 +729,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           ar = car; ai = cai; br = cbr; bi = cbi;
           if (rec_f) {
             const T nx = ar - bi, ny = ai + br;
-            record_f(a, ed_slot0 + u * ed_ustride, (float)(nx - cc.x), (float)(ny - cc.y), t_chk);
+            const T big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)), fabs(T(0.5) * (cc.y - m.y))),
+                               fmax(fabs(T(0.5) * (cc.y + m.y)), fabs(T(0.5) * (m.x - cc.x))));
+            record_f(a, ed_slot0 + u * ed_ustride, (float)(nx - cc.x), (float)(ny - cc.y), t_chk,
+                     may_stop && big <= thr);
           }
         } else if (use_mask) {
           const uint32_t b4 = mb.template get<4>(u);
@@ -766,7 +770,9 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
         mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
-        if (rec_f) record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk);
+        if (rec_f)
+          record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk,
+                   may_stop && fmax(fabs(x), fabs(y)) <= thr);
         v[u] = mk<T>(cx, cy);
       }
     } else if (clip) {
@@ -1076,10 +1082,10 @@ k_px_tma(Args a) {
   }
 }
 
-// After a loop: a pending frequency edit from a check before the last one
-// was applied (the loop went on) and is committed; one from the last check
-// (which stopped the loop, Alg. 1: no projection there) is dropped.  Every
-// slot of every member of the group; grid (x: slots, y: members).
+// After a loop: a marginal frequency edit recorded at the check that
+// stopped the loop (index T = the item's iteration count; Alg. 1 projects
+// nothing there) is taken back; the other marks are cleared.  Every slot of
+// every member of the group; grid (x: slots, y: members).
 static __global__ void k_edits_finalize(Group g, const ItemState* st, float2* ed_f, float2* ed_p,
                                         int* ed_t, int64_t slots_per_item) {
   const int gi = blockIdx.y;
@@ -1089,11 +1095,11 @@ static __global__ void k_edits_finalize(Group g, const ItemState* st, float2* ed
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tg = ed_t[base + i];
     if (tg == 0) continue;
-    if (tg - 1 < T) {
+    if (tg - 1 == T) {
       float2 f = ed_f[base + i];
       const float2 q = ed_p[base + i];
-      f.x += q.x;
-      f.y += q.y;
+      f.x -= q.x;
+      f.y -= q.y;
       ed_f[base + i] = f;
     }
     ed_t[base + i] = 0;
