@@ -9,7 +9,7 @@ the method's arithmetic.
 Everything is float64.  The DFT step is a library primitive (``scipy.fft``,
 full complex spectrum, no half-spectrum tricks); everything else is written out
 in the paper's order.  Readings of passages the paper leaves open are tagged
-``A1``..``A20`` and listed, with the reasons, in the design notes.
+``A1``..``A24`` and listed, with the reasons, in the design notes.
 
 Notation: ``e`` is the spatial error vector (epsilon in the paper), ``delta``
 its frequency error vector, ``E`` the spatial bound and ``D`` the frequency
@@ -79,9 +79,28 @@ def project_f(delta: np.ndarray, D: float) -> np.ndarray:
     return np.clip(delta.real, -D, D) + 1j * np.clip(delta.imag, -D, D)
 
 
-def project_s(e: np.ndarray, E: float) -> np.ndarray:
-    """ProjectOntoSCube: clip every spatial error to [-E, E] (constraints_v2c)."""
+def project_s(e: np.ndarray, E) -> np.ndarray:
+    """ProjectOntoSCube: clip every spatial error to [-E, E] (constraints_v2c);
+    E a scalar or, for pointwise bounds E_n (footnote of Sec. IV-A), an array
+    of the field's shape."""
     return np.clip(e, -E, E)
+
+
+def project_f_pw(delta: np.ndarray, D_re: np.ndarray, D_im: np.ndarray) -> np.ndarray:
+    """ProjectOntoFCube with pointwise bounds Delta_k^Re, Delta_k^Im (full
+    spectrum arrays, even in k so that Hermitian symmetry is kept; A23)."""
+    return np.clip(delta.real, -D_re, D_re) + 1j * np.clip(delta.imag, -D_im, D_im)
+
+
+def f_ratio_pw(delta: np.ndarray, D_re: np.ndarray, D_im: np.ndarray) -> float:
+    """Normalised violation max_k max(|Re delta_k| / D_re_k, |Im delta_k| / D_im_k)
+    (NaN maps to +inf)."""
+    if delta.size == 0:
+        return 0.0
+    r = max(float(np.max(np.abs(delta.real) / D_re)), float(np.max(np.abs(delta.imag) / D_im)))
+    if np.isnan(r) or not np.all(np.isfinite(delta)):
+        return float("inf")
+    return r
 
 
 # --------------------------------------------------------------------------
@@ -126,10 +145,19 @@ def correct(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
     nothing).
     """
     e = np.asarray(e0, dtype=np.float64).copy()
-    Es, Ds, thr = thresholds(E, D, eta)
+    pw_f = isinstance(D, tuple)
+    if pw_f:
+        # pointwise frequency bounds (A23): (Delta^Re, Delta^Im) full-spectrum arrays
+        D_re, D_im = (np.asarray(x, dtype=np.float64) for x in D)
+        Es = np.asarray(E, dtype=np.float64) * (1.0 - eta)
+        Ds_re, Ds_im = D_re * (1.0 - eta), D_im * (1.0 - eta)
+        thr_r = 1.0 - eta / 2.0
+        D = 1.0                                           # the ratio is normalised
+    else:
+        Es, Ds, thr = thresholds(E, D, eta)
     S = np.zeros_like(e) if edits else None
     F = np.zeros(e.shape, dtype=np.complex128) if edits else None
-    pre = bool(e.size and np.max(np.abs(e)) > E)          # A3
+    pre = bool(e.size and np.any(np.abs(e) > E))          # A3
     if pre:
         e_p = project_s(e, Es)
         if edits:
@@ -144,14 +172,19 @@ def correct(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
 
     while True:
         delta = dft(e)                                    # FFT(eps)
-        v = f_violation(delta)                            # CheckConvergence
+        if pw_f:
+            v = f_ratio_pw(delta, D_re, D_im)             # CheckConvergence (normalised)
+            stop = v <= thr_r
+        else:
+            v = f_violation(delta)                        # CheckConvergence
+            stop = v <= thr
         if not np.isfinite(v):
             return done(NONFINITE, v)
-        if v <= thr and t >= min_iters:
+        if stop and t >= min_iters:
             return done(OK, v)
         if t >= max_iters:
             return done(NOT_CONVERGED, v)
-        delta_c = project_f(delta, Ds)                    # ProjectOntoFCube
+        delta_c = project_f_pw(delta, Ds_re, Ds_im) if pw_f else project_f(delta, Ds)   # ProjectOntoFCube
         act_f = int(np.count_nonzero(delta_c != delta))
         if edits:
             F += delta_c - delta                          # freq_edits += delta' - delta
@@ -165,16 +198,69 @@ def correct(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
             traj.append(e.copy())
 
 
-def certify(e: np.ndarray, E: float, D: float):
+def certify(e: np.ndarray, E, D):
     """Check |e_n| <= E and |Re|,|Im| of every DFT bin <= D (constraints_v1).
 
     Returns (ok, max|e|, f_violation).  Comparisons are <= against the true,
-    unshrunk bounds (A7).
+    unshrunk bounds (A7).  With pointwise bounds (E an array, D a pair of
+    full-spectrum arrays) the two maxima are the ratios max|e_n|/E_n and the
+    normalised violation, each compared with 1.
     """
     e = np.asarray(e, dtype=np.float64)
+    if isinstance(D, tuple) or np.ndim(E) > 0:
+        s = float(np.max(np.abs(e) / E)) if e.size else 0.0
+        if isinstance(D, tuple):
+            v = f_ratio_pw(dft(e), *D)
+        else:
+            v = f_violation(dft(e)) / D
+        return bool(s <= 1.0 and v <= 1.0), s, v
     s = float(np.max(np.abs(e))) if e.size else 0.0
     v = f_violation(dft(e))
     return bool(s <= E and v <= D), s, v
+
+
+def shell_index(shape) -> np.ndarray:
+    """Power-spectrum shell of every DFT bin: the rounded radius of its signed
+    frequency vector (Sec. III, P(k) sums |X|^2 over bins at distance k from
+    the centre after the zero-frequency shift; A12)."""
+    grids = np.meshgrid(*[np.fft.fftfreq(n) * n for n in shape], indexing="ij")
+    return np.rint(np.sqrt(sum(g * g for g in grids))).astype(np.int64)
+
+
+def power_spectrum(x: np.ndarray, mean: float | None = None) -> np.ndarray:
+    """P(k) of Sec. III: normalise (x - mean) / mean (the field's own mean by
+    default), FFT, sum |X|^2 over each shell."""
+    x = np.asarray(x, dtype=np.float64)
+    m = float(np.mean(x)) if mean is None else mean
+    X = dft((x - m) / m)
+    return np.bincount(shell_index(x.shape).reshape(-1), weights=(np.abs(X) ** 2).reshape(-1))
+
+
+def power_spectrum_bounds(x: np.ndarray, rho: float):
+    """Pointwise frequency bounds from a relative bound rho on every shell of
+    the power spectrum (Sec. V, power-spectrum preservation; reading A24).
+
+    With X' = FFT((x - xbar)/xbar) and an error delta' = delta/xbar whose Re
+    and Im are within d_s on shell s, |X' + delta'|^2 - |X'|^2 <= 2 sqrt(2)
+    d_s |X'_k| + 2 d_s^2 per bin, so the shell total stays within rho P(s) if
+    2 n_s d_s^2 + 2 sqrt(2) A_s d_s = rho P(s), A_s = sum |X'_k| over the
+    shell, n_s its bin count: d_s is the positive root.  The zero-frequency
+    shell (P(0) = 0 once the mean is removed, so no relative bound exists)
+    takes the smallest bound of the other shells.  Returns (Delta^Re, Delta^Im) = (|xbar| d, |xbar| d), full
+    spectrum, even in k.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    xbar = float(np.mean(x))
+    Xp = dft((x - xbar) / xbar)
+    s = shell_index(x.shape).reshape(-1)
+    P = np.bincount(s, weights=(np.abs(Xp) ** 2).reshape(-1))
+    A = np.bincount(s, weights=np.abs(Xp).reshape(-1))
+    n = np.bincount(s).astype(np.float64)
+    d = (-2.0 * np.sqrt(2.0) * A + np.sqrt(8.0 * A * A + 8.0 * n * rho * P)) / (4.0 * np.maximum(n, 1.0))
+    if d.size > 1:
+        d[0] = d[1:][n[1:] > 0].min()        # the zero-frequency shell
+    bound = (abs(xbar) * d[s]).reshape(x.shape)
+    return bound, bound.copy()
 
 
 # --------------------------------------------------------------------------

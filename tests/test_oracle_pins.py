@@ -497,3 +497,114 @@ def test_edit_pin_catches_recording_the_stopping_clip():
     assert np.max(np.abs(O.project_f(delta, Ds) - delta)) > 0
     bad = r.spat_edits + np.fft.ifftn(F_bad).real
     assert np.max(np.abs(r.e - e0 - bad)) > 1e-12
+
+
+# ------------------------------------------ pointwise bounds (footnote, Sec. IV-A)
+def test_pointwise_uniform_bounds_equal_scalar_bounds():
+    for shape, seed in (((16, 16, 16), 42), ((32, 48), 43)):
+        e0, E, D = _stress(shape, seed, 0.4)
+        a = O.correct(e0, E, D)
+        b = O.correct(e0, np.full(shape, E), (np.full(shape, D), np.full(shape, D)))
+        assert a.iters == b.iters >= 2
+        np.testing.assert_array_equal(a.e, b.e)
+
+
+def dense_pocs_pw(e0, E_n, D_re, D_im, eta=O.ETA_DEFAULT, max_iters=2000):
+    """The dense cos/sin-coordinate POCS with a bound per coordinate: the cos
+    row of bin k carries Delta^Re_k, the sin row Delta^Im_k."""
+    shape = e0.shape
+    idx = list(itertools.product(*[range(n) for n in shape]))
+    grid = np.array(idx, dtype=np.float64)
+    rows, bnd, seen = [], [], set()
+    for k in idx:
+        mk = tuple((-kk) % n for kk, n in zip(k, shape))
+        if mk in seen:
+            continue
+        seen.add(k)
+        ph = 2 * np.pi * sum(grid[:, i] * k[i] / shape[i] for i in range(len(shape)))
+        rows.append(np.cos(ph)); bnd.append(D_re[k])
+        if mk != k:
+            rows.append(np.sin(ph)); bnd.append(D_im[k])
+    B, bnd = np.array(rows), np.array(bnd)
+    nrm = np.sum(B * B, axis=1)
+    Es = E_n.reshape(-1) * (1 - eta)
+    e = e0.reshape(-1).astype(np.float64).copy()
+    for t in range(max_iters + 1):
+        c = B @ e
+        if np.max(np.abs(c) / bnd) <= 1 - eta / 2:
+            return e.reshape(shape), t
+        cc = np.clip(c, -bnd * (1 - eta), bnd * (1 - eta))
+        e = np.clip(e + ((cc - c) / nrm) @ B, -Es, Es)
+    raise AssertionError("dense POCS did not converge")
+
+
+@pytest.mark.parametrize("shape,seed", [((12,), 44), ((4, 6), 45), ((2, 4, 4), 46)])
+def test_pointwise_trajectory_matches_dense_coordinate_pocs(shape, seed):
+    r = np.random.default_rng(seed)
+    e0 = r.uniform(-1, 1, shape)
+    E_n = r.uniform(0.6, 1.4, shape)
+    e0 = np.clip(e0, -E_n * 0.9, E_n * 0.9)
+    v = np.abs(O.dft(e0))
+    base = r.uniform(0.2, 0.5, shape)
+    base = 0.5 * (base + base[np.ix_(*[(-np.arange(n)) % n for n in shape])])   # even in k
+    D_re = base * np.max(v)
+    D_im = base[::-1].copy() if len(shape) == 1 else base * np.max(v) * 1.1
+    if len(shape) == 1:
+        D_im = 0.5 * (D_im + D_im[(-np.arange(shape[0])) % shape[0]]) * np.max(v)
+    e_d, t_d = dense_pocs_pw(e0, E_n, D_re, D_im)
+    res = O.correct(e0, E_n, (D_re, D_im))
+    assert t_d >= 1 and res.iters == t_d
+    np.testing.assert_allclose(res.e, e_d, atol=1e-12)
+
+
+def test_pointwise_single_mode_closed_form():
+    """Only the bins +-k0 are bounded tightly: one iteration, the mode is
+    scaled to the shrunk bin bound, every other bin is untouched."""
+    shape, k0 = (16, 32), (3, 5)
+    N = int(np.prod(shape))
+    A = 0.5
+    e0 = W.single_mode(shape, k0, A)
+    D_re = np.full(shape, 10.0 * A * N)
+    d = 0.1 * A * N / 2
+    D_re[k0] = d
+    D_re[tuple((-k) % n for k, n in zip(k0, shape))] = d
+    r = O.correct(e0, np.full(shape, 1.0), (D_re, D_re.copy()))
+    assert r.iters == 1
+    np.testing.assert_allclose(r.e, W.single_mode(shape, k0, 2 * d * (1 - O.ETA_DEFAULT) / N), atol=1e-14)
+
+
+def test_pointwise_certification():
+    e0, E, D = _stress((16, 16), 47, 0.4)
+    E_n = np.full(e0.shape, E)
+    Db = (np.full(e0.shape, D), np.full(e0.shape, D))
+    r = O.correct(e0, E_n, Db)
+    ok, s, v = O.certify(r.e, E_n, Db)
+    assert ok and s <= 1 and v <= 1
+    E_n2 = E_n.copy(); E_n2[0, 0] = 0.5 * abs(r.e[0, 0]) + 1e-12
+    assert not O.certify(r.e, E_n2, Db)[0]
+
+
+def test_power_spectrum_bounds_guarantee():
+    """Any error inside the pointwise f-cube built for relative bound rho keeps
+    every power-spectrum shell (the zero-frequency one excepted) within rho,
+    P measured with the original field's mean (reading A24)."""
+    it = W.grf_field(16)
+    x = it["x"].astype(np.float64) + 3.0          # positive mean
+    rho = 1e-2
+    D_re, D_im = O.power_spectrum_bounds(x, rho)
+    np.testing.assert_array_equal(D_re, D_re[np.ix_(*[(-np.arange(n)) % n for n in x.shape])])
+    P = O.power_spectrum(x)
+    shells = O.shell_index(x.shape)
+    r = np.random.default_rng(48)
+    worst = 0.0
+    for trial in range(20):
+        # a real error whose spectrum sits on (or inside) the box: project hard
+        e = r.standard_normal(x.shape) * 10
+        delta = O.project_f_pw(O.dft(e), D_re, D_im)
+        e = O.idft(delta)
+        Ph = O.power_spectrum(x + e, mean=float(np.mean(x)))
+        rel = np.abs(Ph[1:] - P[1:]) / P[1:]
+        worst = max(worst, float(np.max(rel)))
+        assert np.all(rel <= rho * (1 + 1e-9))
+    assert worst > 0.1 * rho       # the bound is not vacuous
+    assert shells[0, 0, 0] == 0 and D_re[0, 0, 0] == D_re[shells >= 1].min()
