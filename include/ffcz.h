@@ -74,6 +74,8 @@ typedef struct {
   int32_t edits;       /* 1: record the spatial and frequency edits of Alg. 1
                           (ffcz_edits_dense / ffcz_edits_compact read them);
                           2D and 3D items; default 0 */
+  int32_t pointwise;   /* 1: pointwise bounds E_n, Delta_k (ffcz_correct_pw);
+                          2D and 3D items; default 0 */
 } ffcz_opts;
 
 /* Per-item results. */
@@ -176,6 +178,30 @@ ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, i
 ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* eps_s, const double* eps_f,
                              int m_bits, const uint8_t* s_flags, const int32_t* s_codes,
                              const uint8_t* f_flags, const int32_t* f_codes);
+
+/*
+ * ffcz_correct_pw -- ffcz_correct with pointwise bounds (the generalisation
+ * E_n, Delta_k^Re, Delta_k^Im named in Sec. IV-A), for a plan created with
+ * opts.pointwise = 1.
+ *   eb_dev : device float32, E_n > 0 for every point, laid out like e.
+ *   db_dev : device float32 pairs (Delta^Re, Delta^Im) > 0 on each item's
+ *            half spectrum of a real-input FFT, [Nz][Ny][Nx/2+1] (2D:
+ *            [Ny][Nx/2+1]), items back to back (the offsets of
+ *            ffcz_edit_layout).  Bounds in the kx = 0 and kx = Nx/2 planes
+ *            must be even in (ky, kz), as the spectrum of a real field is.
+ * The point n is clipped to E_n (1 - eta), Re/Im of bin k to
+ * Delta_k^Re/Im (1 - eta); the loop stops when max_k max(|Re|/Delta^Re,
+ * |Im|/Delta^Im) <= 1 - eta/2.  Stats carry the normalised ratios (f_ratio,
+ * s_ratio; margins 1 - ratio), and certification requires max|e_n|/E_n <= 1
+ * and (FP64 normalised violation) + (FP64 rounding bound) / min_k Delta_k <= 1.
+ * The bounds are copied into the plan (the call may reuse its inputs at
+ * once).  Non-positive or non-finite bounds give FFCZ_ERR_INVALID.  On a
+ * pointwise plan ffcz_correct, ffcz_correct_host, ffcz_check, the backward and
+ * the edit compaction/application (whose codes are relative to scalar bounds)
+ * return FFCZ_ERR_INVALID.
+ */
+ffcz_status ffcz_correct_pw(ffcz_plan_t plan, float* e_dev, const float* eb_dev, const float* db_dev,
+                            ffcz_stats* stats);
 
 /*
  * ffcz_plan_describe -- one line per item group: the group's shape, member

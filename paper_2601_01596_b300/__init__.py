@@ -27,7 +27,7 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
            "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
-           "ffcz_edits_compact", "ffcz_apply_edits")
+           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("certify", ctypes.c_int32), ("max_repairs", ctypes.c_int32),
                 ("K", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("count_active", ctypes.c_int32), ("edits", ctypes.c_int32)]
+                ("count_active", ctypes.c_int32), ("edits", ctypes.c_int32),
+                ("pointwise", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
         L.ffcz_edits_dense.argtypes = [vp, vp, vp]
         L.ffcz_edits_compact.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
         L.ffcz_apply_edits.argtypes = [vp, vp, dp, dp, i32, vp, vp, vp, vp]
+        L.ffcz_correct_pw.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
@@ -284,6 +286,24 @@ class Plan:
         st = (Stats * self.batch)()
         s = lib().ffcz_correct(self._h, self._ptr(e, "e"), _dbl(eps_s, self.batch),
                                _dbl(eps_f, self.batch), st)
+        _check(s, allow)
+        return StatsList(st)
+
+    def correct_pw(self, e, e_bounds, f_bounds, stream=None, allow=(ERR_NOT_CONVERGED, ERR_CERT_FAILED,
+                                                                     ERR_NONFINITE)):
+        """Correct ``e`` in place with pointwise bounds (plan made with
+        pointwise=1): ``e_bounds`` float32 like ``e``; ``f_bounds`` the
+        (Delta^Re, Delta^Im) pairs on every item's half spectrum, complex64 or
+        float32 pairs (``edit_layout`` bins, items back to back)."""
+        import torch
+        self._bind_stream(stream)
+        fb = torch.view_as_real(f_bounds) if f_bounds.is_complex() else f_bounds
+        nb = self.edit_layout(-1)[1]
+        if not (fb.is_cuda and fb.dtype == torch.float32 and fb.is_contiguous() and fb.numel() == 2 * nb):
+            raise ValueError(f"f_bounds must be {nb} contiguous complex64 / float32-pair values on the GPU")
+        st = (Stats * self.batch)()
+        s = lib().ffcz_correct_pw(self._h, self._ptr(e, "e"), self._ptr(e_bounds, "e_bounds"),
+                                  ctypes.c_void_p(fb.data_ptr()), st)
         _check(s, allow)
         return StatsList(st)
 

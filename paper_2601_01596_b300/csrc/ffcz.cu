@@ -171,6 +171,11 @@ struct ffcz_plan_s {
   bool ed_on = false;
   float2* ed_canon = nullptr;
   int* ed_chunks = nullptr;
+  // pointwise bounds (opts.pointwise): copies of the caller's E_n and Delta_k
+  float* pw_e = nullptr;
+  float2* pw_f = nullptr;
+  unsigned int* pw_min = nullptr;   // per item min Delta (float bits)
+  int* pw_bad = nullptr;
   // per item: points, half-spectrum bins, and the offsets of its regions in
   // the caller's edit arrays (spatial flags/codes, frequency flags/codes)
   std::vector<std::array<int64_t, 6>> ed_layout;
@@ -613,6 +618,10 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   a.sel_in = a.sel_out = S_CUR;
   a.ckpt_every = 0;
   a.err = p->d_err;
+  if (p->opts.pointwise) {
+    a.pw_e = p->pw_e;
+    a.pw_f = p->pw_f;
+  }
   if (p->ed_on) {
     a.ed_s = p->ed_s;
     a.ed_f = p->ed_f;
@@ -966,6 +975,7 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
     q.min_iters = min_iters;
     q.max_iters = max_iters;
     q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0;
+    q.bscale = 1.0;
     if (p->ndim == 1) {
       const int64_t P = p1d_len(n);
       q.inv_pn = 1.0 / ((double)P * (double)n);
@@ -1332,12 +1342,36 @@ struct ProfOn {
   }
 };
 
+// Validate the plan's copies of the pointwise bounds and set, per item,
+// bscale = 1 / min_k Delta_k (the certification's bound is absolute while the
+// violations are ratios).
+void pw_prepare(ffcz_plan_s* p) {
+  cudaStream_t s = p->stream;
+  CK(cudaMemsetAsync(p->pw_bad, 0, sizeof(int), s));
+  std::vector<unsigned int> inf(p->batch, 0x7f800000u);
+  CK(cudaMemcpyAsync(p->pw_min, inf.data(), sizeof(unsigned int) * p->batch, cudaMemcpyHostToDevice, s));
+  for (auto& dg : p->groups) {
+    const int64_t nb = (int64_t)dg.Nz * (dg.ndim == 3 ? dg.Ny : 1) * (dg.M + 1);
+    const unsigned gx = (unsigned)std::min<int64_t>((std::max(dg.n, nb) + 255) / 256, 2048);
+    k_pw_check<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->pw_e, p->pw_f, dg.n, nb, p->pw_min,
+                                                            p->pw_bad);
+    g_launches++;
+  }
+  k_pw_scale<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->pw_min, (int)p->batch);
+  g_launches++;
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, p->pw_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) fail(FFCZ_ERR_INVALID, "pointwise bounds must be finite and > 0");
+}
+
 ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const double* eps_f,
                          ffcz_stats* stats) {
   if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
   ProfOn prof_on(p);
   CK(cudaSetDevice(p->device));
   upload_params(p, eps_s, eps_f, p->opts.min_iters, p->opts.max_iters);
+  if (p->opts.pointwise) pw_prepare(p);
   CK(cudaEventRecord(p->ev0, p->stream));
   if (p->opts.edits) {
     CK(cudaMemsetAsync(p->ed_s, 0, sizeof(float) * p->total, p->stream));
@@ -1454,6 +1488,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
                           const double* eps_s, const double* eps_f) {
   if (p->batch != 1) fail(FFCZ_ERR_UNSUPPORTED, "backward needs a single-item plan");
   if (p->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "backward supports 2D and 3D items");
+  if (p->opts.pointwise) fail(FFCZ_ERR_INVALID, "backward uses scalar bounds");
   if (!e0 || !gout || !gin || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
   const int K = p->opts.K, m = p->opts.ckpt_every;
   if (K < 1 || m < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
@@ -1761,6 +1796,7 @@ void ffcz_default_opts(ffcz_opts* o) {
   o->use_graph = 2;
   o->count_active = 1;
   o->edits = 0;
+  o->pointwise = 0;
 }
 
 ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t batch,
@@ -1908,6 +1944,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         int64_t* d_co = (int64_t*)dalloc(p.get(), sizeof(int64_t) * co.size());
         CK(cudaMemcpy(d_co, co.data(), sizeof(int64_t) * co.size(), cudaMemcpyHostToDevice));
         dg.d_canon = d_co;
+        dg.g.coff = d_co;
       }
       int32_t* d_it = (int32_t*)dalloc(p.get(), sizeof(int32_t) * it.size());
       int64_t* d_eo = (int64_t*)dalloc(p.get(), sizeof(int64_t) * eo.size());
@@ -1971,6 +2008,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
     p->d_err = (int*)dalloc(p.get(), sizeof(int));
     if (p->opts.edits && ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edit recording supports 2D and 3D items");
+    if (p->opts.pointwise && ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "pointwise bounds support 2D and 3D items");
     if (ndim > 1) {
       p->ed_layout.resize(batch);
       std::array<int64_t, 6> acc{};
@@ -1984,6 +2022,12 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         acc[2] += (npt + 7) / 8; acc[3] += npt; acc[4] += (nb + 7) / 8; acc[5] += 2 * nb;
       }
       p->ed_total = acc;
+    }
+    if (p->opts.pointwise) {
+      p->pw_e = (float*)dalloc(p.get(), sizeof(float) * p->total);
+      p->pw_f = (float2*)dalloc(p.get(), sizeof(float2) * p->ed_total[1]);
+      p->pw_min = (unsigned int*)dalloc(p.get(), sizeof(unsigned int) * batch);
+      p->pw_bad = (int*)dalloc(p.get(), sizeof(int));
     }
     if (p->opts.edits) {
       p->ed_s = (float*)dalloc(p.get(), sizeof(float) * p->total);
@@ -2063,6 +2107,7 @@ ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, i
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
     if (!plan->opts.edits) fail(FFCZ_ERR_INVALID, "the plan was created without opts.edits");
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "edit codes are relative to scalar bounds");
     if (m_bits < 2 || m_bits > 30) fail(FFCZ_ERR_INVALID, "m_bits must be in [2, 30]");
     if (!s_flags || !s_codes || !f_flags || !f_codes) fail(FFCZ_ERR_INVALID, "null edit array");
     CK(cudaSetDevice(plan->device));
@@ -2077,6 +2122,7 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
     if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edits exist for 2D and 3D items");
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "edit codes are relative to scalar bounds");
     if (!xhat_dev || !eps_s || !eps_f || !s_flags || !s_codes || !f_flags || !f_codes)
       fail(FFCZ_ERR_INVALID, "null pointer argument");
     if (m_bits < 2 || m_bits > 30) fail(FFCZ_ERR_INVALID, "m_bits must be in [2, 30]");
@@ -2120,13 +2166,31 @@ int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len) {
 ffcz_status ffcz_correct(ffcz_plan_t plan, float* e, const double* eps_s, const double* eps_f,
                          ffcz_stats* stats) {
   if (!plan) return FFCZ_ERR_INVALID;
-  return guarded([&]() { return correct_impl(plan, e, eps_s, eps_f, stats); });
+  return guarded([&]() {
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "pointwise plan: use ffcz_correct_pw");
+    return correct_impl(plan, e, eps_s, eps_f, stats);
+  });
+}
+
+ffcz_status ffcz_correct_pw(ffcz_plan_t plan, float* e, const float* eb, const float* db, ffcz_stats* stats) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() {
+    if (!plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "the plan was created without opts.pointwise");
+    if (!e || !eb || !db) fail(FFCZ_ERR_INVALID, "null pointer argument");
+    CK(cudaSetDevice(plan->device));
+    CK(cudaMemcpyAsync(plan->pw_e, eb, sizeof(float) * plan->total, cudaMemcpyDeviceToDevice, plan->stream));
+    CK(cudaMemcpyAsync(plan->pw_f, db, sizeof(float2) * plan->ed_total[1], cudaMemcpyDeviceToDevice,
+                       plan->stream));
+    std::vector<double> ones(plan->batch, 1.0);   // the item bounds become ratios
+    return correct_impl(plan, e, ones.data(), ones.data(), stats);
+  });
 }
 
 ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps_s,
                               const double* eps_f, ffcz_stats* stats) {
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "pointwise plan: use ffcz_correct_pw");
     if (!e_host) fail(FFCZ_ERR_INVALID, "e_host is null");
     CK(cudaSetDevice(plan->device));
     if (!plan->staging) plan->staging = (float*)dalloc(plan, sizeof(float) * plan->total);
@@ -2144,6 +2208,7 @@ ffcz_status ffcz_check(ffcz_plan_t plan, const float* e, const double* eps_s, co
                        ffcz_stats* stats) {
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "pointwise plan: use ffcz_correct_pw");
     if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
     CK(cudaSetDevice(plan->device));
     ProfOn prof_on(plan);

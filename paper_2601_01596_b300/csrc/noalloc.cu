@@ -233,7 +233,7 @@ ffcz_status run(const float* e, int ndim, const int64_t* shape, double E, double
   ItemParams q{};
   q.E = E; q.D = D; q.Es = E; q.Ds = D; q.thr = D; q.inv_n = 1.0 / (double)n;
   q.Esf = (float)E; q.Dsf = (float)D; q.thrf = (float)D; q.inv_nf = (float)q.inv_n;
-  q.n = n; q.min_iters = 0; q.max_iters = 0;
+  q.n = n; q.min_iters = 0; q.max_iters = 0; q.bscale = 1.0;
   k_static_init<<<1, 32, 0, s>>>(item, eoff, soff, prm, st, q);
 
   Args a{};

@@ -42,6 +42,9 @@ struct ItemParams {
   double inv_pn;
   float inv_pnf;
   int32_t logP;
+  // factor on the FP64 rounding bound in the certification: 1, or for
+  // pointwise bounds (where D = 1 and violations are ratios) 1 / min_k Delta_k
+  double bscale;
 };
 
 struct ItemState {
@@ -62,6 +65,7 @@ struct Group {
   const int32_t* item;           // global item index of each group member
   const int64_t* eoff;           // float offset of each member in e
   const int64_t* soff;           // complex offset of each member's spectrum
+  const int64_t* coff;           // offset of each member's canonical half spectrum
 };
 
 enum Pred : int { P_ALL = 0, P_ACTIVE = 1, P_EXIT = 2, P_PRECLIP = 3, P_UNCERT = 4 };
@@ -103,6 +107,12 @@ struct Args {
   float2* ed_f;
   float2* ed_p;
   int* ed_t;
+  // pointwise bounds (null: the item's scalar bounds): E_n laid out like e,
+  // (Delta^Re, Delta^Im) on each member's canonical half spectrum
+  // [Nz][Nmid][M+1]; with them the item's E and D are 1 and the kernels
+  // compare and reduce ratios
+  const float* pw_e;
+  const float2* pw_f;
 };
 
 // Spatial edit of one complex register (two real points): S += (c - v).
@@ -400,16 +410,19 @@ k_xfwd(Args a) {
   if ((a.mode & M_MASK) && live) mb.load(a.mask, mthr);
   v2<T> v[V];
   bool bad = false;
+  const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     float2 x = erow[j + u * G_::NT];
+    const float2 eb = ebrow ? ebrow[j + u * G_::NT] : make_float2(1.f, 1.f);
     if (a.mode & M_MEASURE) {
-      mx.add(x.x); mx.add(x.y);
+      if (ebrow) { mx.add(x.x / eb.x); mx.add(x.y / eb.y); }
+      else { mx.add(x.x); mx.add(x.y); }
       bad |= (x.x != x.x) | (x.y != x.y);
       ssq = fmaf(x.x, x.x, fmaf(x.y, x.y, ssq));
     }
     if (a.mode & M_PRECLIP) {
-      const float cx = clampT(x.x, p.Esf), cy = clampT(x.y, p.Esf);
+      const float cx = clampT(x.x, p.Esf * eb.x), cy = clampT(x.y, p.Esf * eb.y);
       cnt += (cx != x.x) + (cy != x.y);
       if (a.ed_s && live)
         record_s<float>(reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M + j + u * G_::NT,
@@ -470,7 +483,8 @@ template <typename T, int M, class TL>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
                                                       int j, int64_t mthr, int64_t row, bool live,
                                                       int t_it, TL& tl, const v2<T>* twg,
-                                                      const v2<T>* twr, float2* edrow = nullptr) {
+                                                      const v2<T>* twr, float2* edrow = nullptr,
+                                                      const float2* ebrow = nullptr) {
   constexpr int V = F2<M>::V, NT = F2<M>::NT, MW = (V + 7) / 8;
   c2r_pre<T, M>(v, j, tl, twr);
   fft_pencil<T, M, +1>(v, j, twg, tl);
@@ -481,7 +495,12 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     v[u] = mk<T>(v[u].x * inv_n, v[u].y * inv_n);
-    mx.add(v[u].x); mx.add(v[u].y);
+    if (ebrow) {   // pointwise E_n: the vote runs on ratios
+      const float2 eb = ebrow[j + u * NT];
+      mx.add(v[u].x / (T)eb.x); mx.add(v[u].y / (T)eb.y);
+    } else {
+      mx.add(v[u].x); mx.add(v[u].y);
+    }
   }
   const bool count = (a.mode & M_COUNT) != 0;
   const bool need_clip = __any_sync(0xffffffffu, mx.val() > Es);   // all lanes vote
@@ -508,7 +527,9 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
     const bool rec_s = edrow != nullptr && live;
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-      const T cx = clampT(v[u].x, Es), cy = clampT(v[u].y, Es);
+      T bx = Es, by = Es;
+      if (ebrow) { const float2 eb = ebrow[j + u * NT]; bx = Es * (T)eb.x; by = Es * (T)eb.y; }
+      const T cx = clampT(v[u].x, bx), cy = clampT(v[u].y, by);
       if (count) cnt += (cx != v[u].x) + (cy != v[u].y);
       if (rec_s) record_s<T>(edrow + j + u * NT, cx - v[u].x, cy - v[u].y);   // spat_edits += eps' - eps
       v[u] = mk<T>(cx, cy);
@@ -529,7 +550,8 @@ k_px(Args a) {
   for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
-  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow);
+  const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
@@ -559,15 +581,17 @@ k_xexit(Args a) {
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
+  const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
   if (live) {
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       T x = v[u].x * inv_n, y = v[u].y * inv_n;
-      if (a.mode & M_CLIP) { x = clampT(x, Es); y = clampT(y, Es); }
+      const float2 eb = ebrow ? ebrow[j + u * G_::NT] : make_float2(1.f, 1.f);
+      if (a.mode & M_CLIP) { x = clampT(x, Es * (T)eb.x); y = clampT(y, Es * (T)eb.y); }
       float fx = (float)x, fy = (float)y;
       if (a.mode & M_CLIP) {
         // keep the float32 result inside the shrunk cube after rounding
-        fx = clampT(fx, p.Esf); fy = clampT(fy, p.Esf);
+        fx = clampT(fx, p.Esf * eb.x); fy = clampT(fy, p.Esf * eb.y);
       }
       if (a.mode & M_ACC) {
         const float2 o = erow[j + u * G_::NT];
@@ -691,7 +715,11 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
                                          const v2<T>* twg, unsigned long long* s_red,
                                          unsigned long long* acc_vb = nullptr,
                                          unsigned long long* acc_cnt = nullptr,
-                                         int64_t ed_slot0 = 0, int64_t ed_ustride = 0, int t_chk = 0) {
+                                         int64_t ed_slot0 = 0, int64_t ed_ustride = 0, int t_chk = 0,
+                                         const float2* pwb = nullptr, int64_t pws = 0, int pwM = 0) {
+  // pwb: pointwise (Delta^Re, Delta^Im) of this pencil's bins at kz = 0 on the
+  // canonical half spectrum, pws the step per kz; on mirror tiles pwb is the
+  // kx = 0 bin (bounds of A) and pwb + pwM the kx = Nx/2 bin (bounds of B)
   constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
   fft_pencil<T, L, -1>(v, j, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
@@ -717,11 +745,19 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         // A = (C + conj Cm)/2, B = (C - conj Cm)/(2i)
         T ar = T(0.5) * (cc.x + m.x), ai = T(0.5) * (cc.y - m.y);
         T br = T(0.5) * (cc.y + m.y), bi = T(0.5) * (m.x - cc.x);
-        if (c.valid) { mx.add(ar); mx.add(ai); mx.add(br); mx.add(bi); }
+        T bar = T(1), bai = T(1), bbr = T(1), bbi = T(1);   // pointwise bounds (ratios)
+        if (pwb) {
+          const float2 qa = pwb[(int64_t)(j + u * NT) * pws], qb = pwb[(int64_t)(j + u * NT) * pws + pwM];
+          bar = (T)qa.x; bai = (T)qa.y; bbr = (T)qb.x; bbi = (T)qb.y;
+        }
+        if (c.valid) {
+          if (pwb) { mx.add(ar / bar); mx.add(ai / bai); mx.add(br / bbr); mx.add(bi / bbi); }
+          else { mx.add(ar); mx.add(ai); mx.add(br); mx.add(bi); }
+        }
         bad |= c.valid && ((ar != ar) | (ai != ai) | (br != br) | (bi != bi));
         if (clip) {
-          const T car = clampT(ar, Ds), cai = clampT(ai, Ds);
-          const T cbr = clampT(br, Ds), cbi = clampT(bi, Ds);
+          const T car = clampT(ar, Ds * bar), cai = clampT(ai, Ds * bai);
+          const T cbr = clampT(br, Ds * bbr), cbi = clampT(bi, Ds * bbi);
           const bool iar = car == ar, iai = cai == ai, ibr = cbr == br, ibi = cbi == bi;
           if (c.owner) cnt += (!iar) + (!iai) + (!ibr) + (!ibi);
           mb.template put<4>(u, (uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) |
@@ -729,8 +765,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           ar = car; ai = cai; br = cbr; bi = cbi;
           if (rec_f) {
             const T nx = ar - bi, ny = ai + br;
-            const T big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)), fabs(T(0.5) * (cc.y - m.y))),
-                               fmax(fabs(T(0.5) * (cc.y + m.y)), fabs(T(0.5) * (m.x - cc.x))));
+            const T big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)) / bar, fabs(T(0.5) * (cc.y - m.y)) / bai),
+                               fmax(fabs(T(0.5) * (cc.y + m.y)) / bbr, fabs(T(0.5) * (m.x - cc.x)) / bbi));
             record_f(a, ed_slot0 + u * ed_ustride, (float)(nx - cc.x), (float)(ny - cc.y), t_chk,
                      may_stop && big <= thr);
           }
@@ -751,7 +787,14 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   // that depends on the tile).
   AbsMax<T> tm;
 #pragma unroll
-  for (int u = 0; u < V; ++u) { tm.add(v[u].x); tm.add(v[u].y); }
+  for (int u = 0; u < V; ++u) {
+    if (pwb) {
+      const float2 q = pwb[(int64_t)(j + u * NT) * pws];
+      tm.add(v[u].x / (T)q.x); tm.add(v[u].y / (T)q.y);
+    } else {
+      tm.add(v[u].x); tm.add(v[u].y);
+    }
+  }
   const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
   if (!c.mirror) {
     if (c.valid) { mx = tm; bad = nan_probe<T, V>(v); }
@@ -766,13 +809,15 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 #pragma unroll
       for (int u = 0; u < V; ++u) {
         const T x = v[u].x, y = v[u].y;
-        const T cx = clampT(x, Ds), cy = clampT(y, Ds);
+        T qx = T(1), qy = T(1);
+        if (pwb) { const float2 q = pwb[(int64_t)(j + u * NT) * pws]; qx = (T)q.x; qy = (T)q.y; }
+        const T cx = clampT(x, Ds * qx), cy = clampT(y, Ds * qy);
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
         mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
         if (rec_f)
           record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk,
-                   may_stop && fmax(fabs(x), fabs(y)) <= thr);
+                   may_stop && fmax(fabs(x) / qx, fabs(y) / qy) <= thr);
         v[u] = mk<T>(cx, cy);
       }
     } else if (clip) {
@@ -819,8 +864,9 @@ k_chk(Args a) {
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
+  const float2* pwb = a.pw_f ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
   chk_core<T, L, TL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
-                     a.g.soff[gi] + c.off + j * estride, ustride, t_it);
+                     a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
@@ -964,8 +1010,10 @@ k_chk_tma(Args a) {
     }
     TL tl{s_tiles + w, false};
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
+    const float2* pwb = a.pw_f ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
     chk_core<float, L, TL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red, &acc_vb, &acc_cnt,
-                           a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it);
+                           a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it, pwb,
+                           (int64_t)Nmid * (M + 1), M);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
 #pragma unroll
@@ -1066,7 +1114,8 @@ k_px_tma(Args a) {
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
     TL tl{s_tiles + g * TL::ELEMS + w, false};
     float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
-    cnt += px_core<float, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow);
+    const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+    cnt += px_core<float, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
     if (live) {
       float2* out = outb + row * M;
 #pragma unroll
@@ -1105,6 +1154,41 @@ static __global__ void k_edits_finalize(Group g, const ItemState* st, float2* ed
     ed_t[base + i] = 0;
     ed_p[base + i] = make_float2(0.f, 0.f);
   }
+}
+
+// Pointwise bounds of every member of a group: counts non-positive or
+// non-finite bounds into *bad and takes min_k Delta_k (Re and Im) per item
+// into minbits (positive floats order like their bit patterns).  Grid
+// (x: any, y: members).
+static __global__ void k_pw_check(Group g, const float* pw_e, const float2* pw_f, int64_t npt, int64_t nb,
+                                  unsigned int* minbits, int* bad) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const float* eb = pw_e + g.eoff[gi];
+  const float2* fb = pw_f + g.coff[gi];
+  int nbad = 0;
+  float mn = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npt; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = eb[i];
+    nbad += !(v > 0.f && v <= FLT_MAX);
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 q = fb[i];
+    nbad += !(q.x > 0.f && q.x <= FLT_MAX) + !(q.y > 0.f && q.y <= FLT_MAX);
+    mn = fminf(mn, fminf(q.x, q.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nbad) atomicAdd(bad, nbad);
+    if (mn > 0.f) atomicMin(minbits + item, __float_as_uint(mn));
+  }
+}
+static __global__ void k_pw_scale(ItemParams* prm, const unsigned int* minbits, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) prm[i].bscale = 1.0 / (double)__uint_as_float(minbits[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1185,7 +1269,7 @@ static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, in
   s.v64 = v;
   s.emax64 = emax;
   s.bound64 = b;
-  s.certified = (emax <= p.E) && (v + b <= p.D);
+  s.certified = (emax <= p.E) && (v + b * p.bscale <= p.D);
   s.vbits = 0ull;
   s.emaxbits = 0ull;
   s.sumsq = 0.0;

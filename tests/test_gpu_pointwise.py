@@ -1,0 +1,94 @@
+"""Pointwise bounds (E_n, Delta_k^Re, Delta_k^Im; ffcz_correct_pw) vs the oracle.
+
+Bars as for scalar bounds: max|delta e| <= 1e-3 min(E_n) against the FP64
+oracle run with the same pointwise bounds, iteration count within +-2, and
+the FP64 certification on the GPU passes.
+"""
+import numpy as np
+import pytest
+
+from oracle import ffcz_oracle as O
+from paper_2601_01596_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _even(a):
+    return 0.5 * (a + a[np.ix_(*[(-np.arange(n)) % n for n in a.shape])])
+
+
+def run_pw(e0, E_n, D_re, D_im, **opts):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shape = e0.shape
+    plan = ffcz.Plan([shape], pointwise=1, **opts)
+    half = O.half_spectrum(D_re + 1j * D_im).astype(np.complex64)
+    t = torch.from_numpy(e0.reshape(-1).astype(np.float32).copy()).cuda()
+    eb = torch.from_numpy(E_n.reshape(-1).astype(np.float32)).cuda()
+    db = torch.from_numpy(half.reshape(-1)).cuda()
+    st = plan.correct_pw(t, eb, db)
+    return t.cpu().numpy().reshape(shape), st
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (16, 32, 64)])
+def test_uniform_pointwise_bounds_behave_like_scalar(shape):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    e0 = W.bimodal_error(shape, 90, E=1.0, dtype=np.float32)
+    E, D = 1.0, 0.4 * O.f_violation(O.dft(e0.astype(np.float64)))
+    e_pw, st = run_pw(e0, np.full(shape, E), np.full(shape, D), np.full(shape, D))
+    plan = ffcz.Plan([shape])
+    t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    st_s = plan.correct(t, [E], [D])
+    assert abs(st[0]["iters"] - st_s[0]["iters"]) <= 1 and st[0]["certified"] == 1
+    np.testing.assert_allclose(e_pw.reshape(-1), t.cpu().numpy(), rtol=0, atol=1e-4 * E)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (16, 32, 64)])
+def test_varying_pointwise_bounds_match_oracle(shape):
+    r = np.random.default_rng(91)
+    x = W.grf_field(shape[0], seed=3)["x"] if len(shape) == 3 and len(set(shape)) == 1 else \
+        r.standard_normal(shape)
+    x = x.astype(np.float64) + 4.0
+    E_n = 0.01 * (0.6 + 0.8 * r.random(shape))
+    e0 = (r.uniform(-1, 1, shape) * E_n * 0.999).astype(np.float32)
+    D_re, D_im = O.power_spectrum_bounds(x, 2e-2)
+    # keep the f-clip active: tighten toward the error's own spectrum
+    scale = 0.3 * O.f_ratio_pw(O.dft(e0.astype(np.float64)), D_re, D_im)
+    D_re, D_im = D_re * scale, D_im * scale
+    ref = O.correct(e0, E_n, (D_re, D_im))
+    e, st = run_pw(e0, E_n, D_re, D_im)
+    assert ref.iters >= 2
+    assert abs(st[0]["iters"] - ref.iters) <= 2
+    assert st[0]["status"] == 0 and st[0]["certified"] == 1
+    np.testing.assert_allclose(e, ref.e, rtol=0, atol=1e-3 * E_n.min())
+    ok, s, v = O.certify(e.astype(np.float64), E_n, (D_re, D_im))
+    assert ok
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_pointwise_forced_iterations(k):
+    shape = (32, 64)
+    r = np.random.default_rng(92)
+    E_n = 0.5 + r.random(shape)
+    e0 = (r.uniform(-1, 1, shape) * E_n).astype(np.float32)
+    base = _even(0.5 + r.random(shape))
+    v = O.f_violation(O.dft(e0.astype(np.float64)))
+    D_re, D_im = 0.3 * v * base, 0.3 * v * _even(0.5 + r.random(shape))
+    ref = O.correct(e0, E_n, (D_re, D_im), min_iters=k, max_iters=k)
+    e, st = run_pw(e0, E_n, D_re, D_im, min_iters=k, max_iters=k, certify=0)
+    assert st[0]["iters"] == k
+    np.testing.assert_allclose(e, ref.e, rtol=0, atol=1e-3 * E_n.min())
+
+
+def test_invalid_bounds_and_scalar_calls_are_refused():
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shape = (32, 32)
+    e0 = np.zeros(shape, np.float32)
+    E_n = np.ones(shape); E_n[3, 4] = 0.0
+    with pytest.raises(ffcz.FFCzError):
+        run_pw(e0, E_n, np.ones(shape), np.ones(shape))
+    plan = ffcz.Plan([shape], pointwise=1)
+    with pytest.raises(ffcz.FFCzError):
+        plan.correct(torch.zeros(32 * 32, device="cuda"), [1.0], [1.0])
