@@ -204,6 +204,26 @@ ffcz_status ffcz_correct_pw(ffcz_plan_t plan, float* e_dev, const float* eb_dev,
                             ffcz_stats* stats);
 
 /*
+ * ffcz_power_spectrum_bounds -- pointwise frequency bounds that keep every
+ * shell of the power spectrum (Sec. III: P(k) = sum of |X|^2 over the bins
+ * at rounded distance k from the zero frequency, after the normalisation
+ * (x - mean)/mean) within a relative error rho (Sec. V, power-spectrum
+ * preservation).  Reading of the unspecified mapping: per shell s, with
+ * A_s = sum |X_k| and P_s = sum |X_k|^2 over the shell's n_s bins, any error
+ * with |Re|, |Im| <= d_s changes P_s by at most 2 sqrt2 d_s A_s + 2 n_s d_s^2,
+ * so d_s is the positive root of that expression = rho P_s; the
+ * zero-frequency shell takes the smallest d of the other shells.  The mean
+ * normalisation cancels out of d (a relative bound is scale-free).
+ *   x_dev  : device float32, the ORIGINAL fields (packed items).
+ *   rho    : host, one relative bound > 0 per item.
+ *   db_dev : device float32 pairs, output in the layout ffcz_correct_pw reads
+ *            (Delta^Re = Delta^Im = d of the bin's shell).
+ * The transform runs in float32 on the plan's first spectrum buffer (not
+ * concurrently with a ffcz_correct on the same plan); synchronises.
+ */
+ffcz_status ffcz_power_spectrum_bounds(ffcz_plan_t plan, const float* x_dev, const double* rho, float* db_dev);
+
+/*
  * ffcz_plan_describe -- one line per item group: the group's shape, member
  * count and the pass variants the tuner chose for it (tile width, or "tma"
  * for the persistent copy-engine-fed kernels).  Writes at most `len` bytes

@@ -27,7 +27,7 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
            "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
-           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw")
+           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw", "ffcz_power_spectrum_bounds")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         L.ffcz_edits_compact.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
         L.ffcz_apply_edits.argtypes = [vp, vp, dp, dp, i32, vp, vp, vp, vp]
         L.ffcz_correct_pw.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.ffcz_power_spectrum_bounds.argtypes = [vp, vp, dp, vp]
         L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
@@ -306,6 +307,19 @@ class Plan:
                                   ctypes.c_void_p(fb.data_ptr()), st)
         _check(s, allow)
         return StatsList(st)
+
+    def power_spectrum_bounds(self, x, rho, stream=None):
+        """Per-bin (Delta^Re, Delta^Im) keeping every power-spectrum shell of
+        the original fields ``x`` (float32 CUDA, packed items) within the
+        relative bound(s) ``rho``; complex64 CUDA tensor for ``correct_pw``."""
+        import torch
+        self._bind_stream(stream)
+        nb = self.edit_layout(-1)[1]
+        out = torch.empty(2 * nb, dtype=torch.float32, device="cuda")
+        rho = [rho] * self.batch if isinstance(rho, (int, float)) else rho
+        _check(lib().ffcz_power_spectrum_bounds(self._h, self._ptr(x, "x"), _dbl(rho, self.batch),
+                                                ctypes.c_void_p(out.data_ptr())))
+        return torch.view_as_complex(out.view(-1, 2))
 
     def correct_host(self, e_np, eps_s, eps_f, allow=(ERR_NOT_CONVERGED, ERR_CERT_FAILED,
                                                       ERR_NONFINITE)):

@@ -152,6 +152,85 @@ static __global__ void k_edits_scatter(const EdRegion<C>* regs) {
     if (byte & (1u << t)) put_codes(r.codes, k++, r.vals[b * 8 + t], r.q);
 }
 
+// ----- power-spectrum relative bounds (reading: the per-shell positive root) -------
+// Shell of a canonical bin (kz, ky, kx): rounded radius of the signed
+// frequency vector; kx in [0, M] is already non-negative.
+__device__ __forceinline__ int ps_shell(int kz, int ky, int kx, int Nz, int Ny) {
+  const int sz = kz <= Nz / 2 ? kz : kz - Nz, sy = ky <= Ny / 2 ? ky : ky - Ny;
+  return (int)rint(sqrt((double)kx * kx + (double)sy * sy + (double)sz * sz));
+}
+
+// Per-item shell sums over the full spectrum (a canonical bin with
+// 0 < kx < M stands for k and -k): A = sum |X|, P = sum |X|^2, n = bins.
+// Block-local histograms in shared memory, then one atomic per shell.
+// acc: per item 3 x S doubles.  Grid (x: bins, y: members).
+static __global__ void k_ps_shells(Group g, const float2* canon, double* acc, int S) {
+  extern __shared__ double hist[];   // 3 S
+  const int gi = blockIdx.y;
+  const int Nz = g.Nz, Ny = g.Nmid, M = g.M;
+  const int64_t nb = (int64_t)Nz * Ny * (M + 1);
+  const float2* c = canon + g.coff[gi];
+  for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) hist[i] = 0.0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % (M + 1));
+    const int64_t r = i / (M + 1);
+    const int ky = (int)(r % Ny), kz = (int)(r / Ny);
+    const int s = ps_shell(kz, ky, kx, Nz, Ny);
+    const double w = (kx > 0 && kx < M) ? 2.0 : 1.0;
+    const double a = hypot((double)c[i].x, (double)c[i].y);
+    atomicAdd(&hist[s], w * a);
+    atomicAdd(&hist[S + s], w * a * a);
+    atomicAdd(&hist[2 * S + s], w);
+  }
+  __syncthreads();
+  double* dst = acc + (int64_t)g.item[gi] * 3 * S;
+  for (int i = threadIdx.x; i < 3 * S; i += blockDim.x)
+    if (hist[i] != 0.0) atomicAdd(&dst[i], hist[i]);
+}
+
+// d_s = (-2 sqrt2 A + sqrt(8 A^2 + 8 n rho P)) / (4 n) per shell; shell 0 (the
+// mean) takes the smallest of the others.  One CTA per item.
+static __global__ void k_ps_roots(double* acc, int S, const double* rho) {
+  const int item = blockIdx.x;
+  double* A = acc + (int64_t)item * 3 * S;
+  double* P = A + S;
+  double* n = A + 2 * S;
+  __shared__ double smin[32];
+  double mn = INFINITY;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    double d = 0.0;
+    if (n[s] > 0.0) {
+      d = (-2.0 * sqrt(2.0) * A[s] + sqrt(8.0 * A[s] * A[s] + 8.0 * n[s] * rho[item] * P[s])) / (4.0 * n[s]);
+      if (s > 0) mn = fmin(mn, d);
+    }
+    A[s] = d;   // the root replaces the sum
+  }
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmin(m, smin[w]);
+    if (m < INFINITY) A[0] = m;
+  }
+}
+
+// Bounds (Delta^Re, Delta^Im) = (d, d) of every canonical bin.
+static __global__ void k_ps_write(Group g, const double* acc, int S, float2* out) {
+  const int gi = blockIdx.y;
+  const int Nz = g.Nz, Ny = g.Nmid, M = g.M;
+  const int64_t nb = (int64_t)Nz * Ny * (M + 1);
+  const double* d = acc + (int64_t)g.item[gi] * 3 * S;
+  float2* o = out + g.coff[gi];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % (M + 1));
+    const int64_t r = i / (M + 1);
+    const float b = (float)d[ps_shell((int)(r / Ny), (int)(r % Ny), kx, Nz, Ny)];
+    o[i] = make_float2(b, b);
+  }
+}
+
 // ----- decompression side: edits from their stored form ----------------------
 // (Sec. IV-B, "Applying edits to the decompressed data")
 

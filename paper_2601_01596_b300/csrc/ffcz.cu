@@ -176,6 +176,9 @@ struct ffcz_plan_s {
   float2* pw_f = nullptr;
   unsigned int* pw_min = nullptr;   // per item min Delta (float bits)
   int* pw_bad = nullptr;
+  double* ps_acc = nullptr;         // power-spectrum shell sums (3 S per item)
+  double* ps_rho = nullptr;
+  int ps_S = 0;
   // per item: points, half-spectrum bins, and the offsets of its regions in
   // the caller's edit arrays (spatial flags/codes, frequency flags/codes)
   std::vector<std::array<int64_t, 6>> ed_layout;
@@ -1069,6 +1072,70 @@ void edits_compact(ffcz_plan_s* p, int m, uint8_t* sf, int32_t* sc, uint8_t* ff,
   CK(cudaGetLastError());
   if (counts)
     for (int64_t i = 0; i < B; ++i) { counts[2 * i] = tot[i]; counts[2 * i + 1] = tot[B + i]; }
+}
+
+// Power-spectrum relative bounds (Sec. V; the mapping is a reading): the
+// forward transform of x (x R2C, y FFT, outer-axis FFT as a [Nz][Nmid M]
+// view) into the first spectrum buffer, its canonical half spectrum, shell
+// sums of |X| and |X|^2, the positive root per shell, one bound per bin.
+// The normalisation (x - mean)/mean of the power spectrum cancels out of the
+// bound (a relative bound is scale-free and the mean only moves shell 0).
+void ps_bounds(ffcz_plan_s* p, const float* x, const double* rho, float2* out) {
+  cudaStream_t s = p->stream;
+  if (!p->ed_canon) p->ed_canon = (float2*)dalloc(p, sizeof(float2) * std::max<int64_t>(1, p->ed_total[1]));
+  int S = 1;
+  for (auto& dg : p->groups) {
+    const double r = std::sqrt((double)dg.M * dg.M + std::pow(dg.Nz / 2, 2.0) +
+                               (dg.ndim == 3 ? std::pow(dg.Ny / 2, 2.0) : 0.0));
+    S = std::max(S, (int)std::ceil(r) + 2);
+  }
+  if (!p->ps_acc) {
+    p->ps_acc = (double*)dalloc(p, sizeof(double) * 3 * (size_t)S * p->batch);
+    p->ps_rho = (double*)dalloc(p, sizeof(double) * p->batch);
+    p->ps_S = S;
+  }
+  double* acc = p->ps_acc;
+  double* d_rho = p->ps_rho;
+  CK(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)S * p->batch, s));
+  CK(cudaMemcpyAsync(d_rho, rho, sizeof(double) * p->batch, cudaMemcpyHostToDevice, s));
+  for (auto& dg : p->groups) {
+    const int Nmid = dg.ndim == 3 ? dg.Ny : 1;
+    Args a = make_args<float>(p, dg, p->B32[0], p->B32[0], p->d_st);
+    a.pred = P_ALL;
+    a.sel_in = a.sel_out = S_CUR;
+    a.pw_e = nullptr; a.pw_f = nullptr;
+    tabs_x<float>(p, a, dg);
+    a.e = const_cast<float*>(x);
+    a.mode = 0;
+    launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, s);
+    if (dg.ndim == 3) {
+      a.tw = tw_of<float>(p->tb, dg.Ny);
+      launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
+    }
+    Args az = a;
+    az.g.Nz = 1;
+    az.g.M = Nmid * dg.M;
+    az.tw = tw_of<float>(p->tb, dg.Nz);
+    launch_axis<float, -1>(dg.Nz, dg.wa, az, 1, Nmid * dg.M, dg.count, s);
+    const int64_t nb = (int64_t)dg.Nz * Nmid * (dg.M + 1);
+    const unsigned gx = (unsigned)std::min<int64_t>((nb + 255) / 256, 1024);
+    k_edits_canon<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, static_cast<const float2*>(p->B32[0]),
+                                                                p->ed_canon, dg.d_canon);
+    const size_t hs = sizeof(double) * 3 * S;
+    if (hs > 48 * 1024) CK(cudaFuncSetAttribute(k_ps_shells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
+    k_ps_shells<<<dim3(std::min<unsigned>(gx, 296), (unsigned)dg.count), 256, hs, s>>>(dg.g, p->ed_canon, acc, S);
+    g_launches += 2;
+  }
+  k_ps_roots<<<(unsigned)p->batch, 256, 0, s>>>(acc, S, d_rho);
+  g_launches++;
+  for (auto& dg : p->groups) {
+    const int64_t nb = (int64_t)dg.Nz * (dg.ndim == 3 ? dg.Ny : 1) * (dg.M + 1);
+    const unsigned gx = (unsigned)std::min<int64_t>((nb + 255) / 256, 1024);
+    k_ps_write<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, acc, S, out);
+    g_launches++;
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
 }
 
 // Applying edits (Sec. IV-B): x_hat += S~ + IFFT(F~) from the stored form
@@ -1991,6 +2058,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
           launch_chk<float>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
           launch_chk<double>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
           launch_axis<float, +1>(dg.Nz, dg.wa, a, 1, dg.M, 1, nullptr);   // edit application
+          launch_axis<float, -1>(dg.Nz, dg.wa, a, 1, dg.M, 1, nullptr);   // power-spectrum bounds
         }
       }
     } catch (...) {
@@ -2129,6 +2197,19 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
     CK(cudaSetDevice(plan->device));
     upload_params(plan, eps_s, eps_f, 0, 0);
     apply_edits(plan, xhat_dev, m_bits, s_flags, s_codes, f_flags, f_codes);
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_power_spectrum_bounds(ffcz_plan_t plan, const float* x_dev, const double* rho, float* db_dev) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "power-spectrum bounds for 2D and 3D items");
+    if (!x_dev || !rho || !db_dev) fail(FFCZ_ERR_INVALID, "null pointer argument");
+    for (int64_t i = 0; i < plan->batch; ++i)
+      if (!(rho[i] > 0) || !std::isfinite(rho[i])) fail(FFCZ_ERR_INVALID, "rho must be finite and > 0");
+    CK(cudaSetDevice(plan->device));
+    ps_bounds(plan, x_dev, rho, reinterpret_cast<float2*>(db_dev));
     return FFCZ_OK;
   });
 }

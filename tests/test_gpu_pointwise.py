@@ -92,3 +92,44 @@ def test_invalid_bounds_and_scalar_calls_are_refused():
     plan = ffcz.Plan([shape], pointwise=1)
     with pytest.raises(ffcz.FFCzError):
         plan.correct(torch.zeros(32 * 32, device="cuda"), [1.0], [1.0])
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (16, 32, 64)])
+def test_power_spectrum_bounds_match_oracle(shape):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    r = np.random.default_rng(93)
+    x = (r.standard_normal(shape) + 5.0).astype(np.float32)
+    rho = 3e-3
+    plan = ffcz.Plan([shape])
+    got = plan.power_spectrum_bounds(torch.from_numpy(x.reshape(-1).copy()).cuda(), rho).cpu().numpy()
+    D_re, D_im = O.power_spectrum_bounds(x.astype(np.float64), rho)
+    want = O.half_spectrum(D_re + 1j * D_im).reshape(-1)
+    np.testing.assert_allclose(got.real, want.real, rtol=1e-4)
+    np.testing.assert_allclose(got.imag, want.imag, rtol=1e-4)
+
+
+def test_power_spectrum_mode_end_to_end():
+    """x_hat = x + e0; bounds from x for rho; after ffcz_correct_pw every
+    shell but the zero-frequency one of x_hat' is within rho of x's."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shape = (32, 32, 32)
+    it = W.grf_field(32, seed=5)
+    x = (it["x"].astype(np.float64) + 6.0).astype(np.float32)
+    rng = np.random.default_rng(94)
+    E_n = np.full(shape, 0.05)
+    e0 = (rng.uniform(-1, 1, shape) * 0.05 * 0.999).astype(np.float32)
+    rho = 1e-3
+    plan = ffcz.Plan([shape], pointwise=1)
+    db = plan.power_spectrum_bounds(torch.from_numpy(x.reshape(-1).copy()).cuda(), rho)
+    t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    st = plan.correct_pw(t, torch.from_numpy(E_n.reshape(-1).astype(np.float32)).cuda(), db)
+    assert st[0]["status"] == 0 and st[0]["certified"] == 1 and st[0]["iters"] >= 1
+    e = t.cpu().numpy().reshape(shape).astype(np.float64)
+    P = O.power_spectrum(x.astype(np.float64))
+    P_hat = O.power_spectrum(x.astype(np.float64) + e, mean=float(np.mean(x.astype(np.float64))))
+    rel = np.abs(P_hat[1:] - P[1:]) / P[1:]
+    assert np.max(rel) <= rho * (1 + 1e-3)
+    P_base = O.power_spectrum(x.astype(np.float64) + e0, mean=float(np.mean(x.astype(np.float64))))
+    assert np.max(np.abs(P_base[1:] - P[1:]) / P[1:]) > rho     # the base error did violate it
