@@ -365,6 +365,31 @@ def _batch_form(ffcz, torch, items, name):
             "ms_cert": round(float(st[0]["ms_cert"]), 3)}
 
 
+def aggregate_ranks(torch, dist, local_ms, bytes_per_rank, world, device="cpu"):
+    """Whole-job figure of N replicas (one process per GPU, each doing the same
+    step): the step time is the MAX over ranks, the value the bytes all ranks
+    processed divided by it (GB/s).  ``dist`` is torch.distributed or None."""
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * bytes_per_rank / (ms / 1e3) / 1e9
+
+
+def shard_items(nbytes, rank, world):
+    """Items of a batched workload for one rank when a batch is spread over
+    GPUs: greedy bin packing by bytes (largest first onto the least loaded
+    rank); every item lands on exactly one rank and no data crosses ranks."""
+    order = sorted(range(len(nbytes)), key=lambda i: (-nbytes[i], i))
+    load = [0] * world
+    owner = [0] * len(nbytes)
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += nbytes[i]
+    return [i for i in range(len(nbytes)) if owner[i] == rank]
+
+
 def paper_design_cufft(torch, it, D, hbm, K=20):
     """Bench-only comparator (not on the product path): the paper's loop body
     as separate library kernels on the same B300 -- cuFFT R2C (torch.fft),
@@ -574,11 +599,7 @@ def main():
     if dist:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = world * field_bytes / (ms / 1e3) / 1e9
+    ms, value = aggregate_ranks(torch, dist, ms, field_bytes, world, device="cuda")
     st = stats[-1]
 
     # -- per-kernel profile of the same step (live CUDA events per launch) -----
