@@ -457,6 +457,32 @@ def edits_form(ffcz, torch, it, D):
             "field_bytes": 4 * n}
 
 
+def pointwise_form(ffcz, torch, it, D, hbm, K=20):
+    """Pointwise bounds (ffcz_correct_pw) on the stress variant: per-iteration
+    time from K forced iterations minus 0, and its fraction of the HBM peak
+    for the 4-pass traffic plus the bound reads (E_n in the x pass, the
+    (Delta^Re, Delta^Im) pairs in the check pass): 40N bytes per iteration."""
+    shape, E = it["shape"], it["E"]
+    n = int(np.prod(shape))
+    d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
+    d = torch.empty_like(d0)
+    eb = torch.full((n,), float(E), dtype=torch.float32, device="cuda")
+    out = {}
+    for k in (K, 0):
+        plan = ffcz.Plan([shape], pointwise=1, min_iters=k, max_iters=k, certify=0)
+        nb = plan.edit_layout(-1)[1]
+        db = torch.full((2 * nb,), float(D), dtype=torch.float32, device="cuda")
+        ms, st = _timed(torch, lambda: plan.correct_pw(d.copy_(d0), eb, db)[0], reps=3)
+        out[k] = (ms, st)
+        del plan, db
+    it_ms = (out[K][0] - out[0][0]) / K
+    design = 40.0 * n
+    return {"workload": it["name"] + " stress bounds as uniform pointwise arrays",
+            "forced_iters": K, "ms_per_iteration": round(it_ms, 4),
+            "design_bytes": int(design),
+            "frac_hbm_design": round(design / (it_ms / 1e3) / 1e9 / hbm, 4)}
+
+
 def measure_forms(ffcz, torch, fin, it, hbm):
     """The stress variant, the batched and the differentiable forms (each a
     median of 2 calls after 1 warm-up; CUDA events on the current stream)."""
@@ -479,6 +505,8 @@ def measure_forms(ffcz, torch, fin, it, hbm):
     out["paper_design_cufft"] = paper_design_cufft(torch, it, fin["stress_D"], hbm)
     torch.cuda.empty_cache()
     out["edits_stress_512"] = edits_form(ffcz, torch, it, fin["stress_D"])
+    torch.cuda.empty_cache()
+    out["pointwise_512"] = pointwise_form(ffcz, torch, it, fin["stress_D"], hbm)
     torch.cuda.empty_cache()
     out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
                                     "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")

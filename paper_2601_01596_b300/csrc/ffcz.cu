@@ -314,21 +314,25 @@ enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
 constexpr int row_w1(int L) { return 32 / (1 << (ilog2(L) / 2)) > 0 ? 32 / (1 << (ilog2(L) / 2)) : 1; }
 constexpr int row_w2(int L) { return 2 * row_w1(L); }
 
-template <typename T, int M, int W>
+// Pointwise-bound plans select the PW kernel variants (the dry run sets
+// g_pw_sel to reach them without bound pointers).
+thread_local bool g_pw_sel = false;
+
+template <typename T, int M, int W, bool PW = false>
 void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
   using G_ = Geo<T, M, W>;
   const int64_t tiles = (rows + G_::W - 1) / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, M, W>::bytes_x;
   if (g_dry) {
-    set_smem(k_xfwd<T, M, W>, sm); set_smem(k_px<T, M, W>, sm); set_smem(k_xexit<T, M, W>, sm);
+    set_smem(k_xfwd<T, M, W, PW>, sm); set_smem(k_px<T, M, W, PW>, sm); set_smem(k_xexit<T, M, W, PW>, sm);
     return;
   }
   ProfScope ps(kind == XFWD ? "xfwd" : kind == XPX ? "px" : "xexit", 8 * (int)sizeof(T), M, s);
   switch (kind) {
-    case XFWD: k_xfwd<T, M, W><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XPX: k_px<T, M, W><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XEXIT: k_xexit<T, M, W><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XFWD: k_xfwd<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XPX: k_px<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XEXIT: k_xexit<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
   }
   g_launches++;
 }
@@ -336,30 +340,45 @@ int g_num_sms_x = 148;   // set from the device at plan creation
 
 // Persistent bulk-copy-fed loop x pass (float32, one-warp tiles): as many
 // CTAs as fit on the device, spread over the group's items.
-template <int M>
-void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
+template <int M, bool ED>
+void launch_px_tma_ed(const Args& a, int64_t rows, int count, cudaStream_t s) {
   constexpr int W = row_w1(M);
   using PG = PxTmaGeo<M, W>;
   const size_t sm = PG::bytes;
-  if (g_dry) { set_smem(k_px_tma<M, W>, sm); return; }
+  if (g_dry) { set_smem(k_px_tma<M, W, ED>, sm); return; }
   static int per_sm = 0;   // resident CTAs per SM (same for every plan)
   if (per_sm == 0) {
     int n = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W>, Geo<float, M, W>::NTHR, sm));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W, ED>, Geo<float, M, W>::NTHR, sm));
     per_sm = n > 0 ? n : 1;
   }
   const int64_t nblk = (rows + PG::RG - 1) / PG::RG;
   const int64_t want = ((int64_t)per_sm * g_num_sms_x + count - 1) / count;
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, want));
   ProfScope ps("px", 32, M, s);
-  k_px_tma<M, W><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
+  k_px_tma<M, W, ED><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
   g_launches++;
+}
+template <int M>
+void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
+  if (g_dry) {
+    launch_px_tma_ed<M, false>(a, rows, count, s);
+    launch_px_tma_ed<M, true>(a, rows, count, s);
+  } else if (a.ed_s) {
+    launch_px_tma_ed<M, true>(a, rows, count, s);
+  } else {
+    launch_px_tma_ed<M, false>(a, rows, count, s);
+  }
 }
 
 template <typename T>
 struct XL {
   template <int M>
   static void go(XKind kind, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
+    if (a.pw_e || g_pw_sel) {
+      launch_x_tw<T, M, row_w1(M), true>(kind, a, rows, count, s);
+      return;
+    }
     if constexpr (sizeof(T) == 4) {
       if (w < 0 && (kind == XPX || g_dry)) {
         launch_px_tma<M>(a, rows, count, s);
@@ -439,22 +458,26 @@ void launch_axis(int L, int w, const Args& a, int Nz, int M, int count, cudaStre
   FFCZ_DISPATCH_L(L, D::template go, w, a, Nz, M, count, s)
 }
 
-template <typename T, int L, int W>
+template <typename T, int L, int W, bool PW = false>
 void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   using G_ = Geo<T, L, W>;
   const int64_t tiles = chk_ntiles(W, M, Nmid);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L, W>::bytes_axis;
-  if (g_dry) { set_smem(k_chk<T, L, W>, sm); return; }
+  if (g_dry) { set_smem(k_chk<T, L, W, PW>, sm); return; }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk",
                8 * (int)sizeof(T), L, s);
-  k_chk<T, L, W><<<grid, G_::NTHR, sm, s>>>(a);
+  k_chk<T, L, W, PW><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
 template <typename T>
 struct CL {
   template <int L>
   static void go(int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
+    if (a.pw_f || g_pw_sel) {
+      launch_chk_tw<T, L, TileW<T>::value, true>(a, Nmid, M, count, s);
+      return;
+    }
     if constexpr (sizeof(T) == 4) {
       if constexpr (tma_ok<L>()) {
         if (w < 0 && (a.tm_chk || g_dry)) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
@@ -2035,6 +2058,16 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     g_dry = true;
     try {
       Args a{};
+      if (p->opts.pointwise) {
+        g_pw_sel = true;
+        for (const auto& dg : p->groups) {
+          launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, nullptr);
+          launch_x<double>(XFWD, dg.M, dg.wx, a, dg.rows, 1, nullptr);
+          launch_chk<float>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
+          launch_chk<double>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
+        }
+        g_pw_sel = false;
+      }
       for (const auto& dg0 : p->groups) {
         for (int alt = 0; alt < 3; ++alt) {
           DevGroup dg = dg0;
@@ -2063,6 +2096,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       }
     } catch (...) {
       g_dry = false;
+      g_pw_sel = false;
       throw;
     }
     g_dry = false;

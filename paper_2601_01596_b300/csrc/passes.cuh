@@ -175,6 +175,8 @@ struct Geo {
   // 384 (170); float64 512 (128) up to 8 values, else 256 (255)
   static constexpr int SMT = sizeof(T) == 4 ? (V >= 32 ? 384 : V >= 16 ? 512 : 1024) : (V >= 16 ? 256 : 512);
   static constexpr int MINB = SMT / NTHR > 0 ? SMT / NTHR : 1;
+  // pointwise-bound variants hold the bounds of their values in registers too
+  static constexpr int MINB_PW = MINB > 1 ? MINB - 1 : 1;
 };
 
 // Shared-memory carve-up: [G tile buffers][twiddles][R2C twiddles][reduction].
@@ -395,7 +397,8 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
   (void)t_it; (void)mthr;
 
 // Entry / certification x pass: float32 real rows -> packed spectrum.
-template <typename T, int M, int W = TileW<T>::value>
+// PW: pointwise E_n (the measured maximum is max |e_n| / E_n).
+template <typename T, int M, int W = TileW<T>::value, bool PW = false>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xfwd(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
@@ -410,19 +413,21 @@ k_xfwd(Args a) {
   if ((a.mode & M_MASK) && live) mb.load(a.mask, mthr);
   v2<T> v[V];
   bool bad = false;
-  const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+  const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     float2 x = erow[j + u * G_::NT];
-    const float2 eb = ebrow ? ebrow[j + u * G_::NT] : make_float2(1.f, 1.f);
+    float2 eb = make_float2(1.f, 1.f);
+    if constexpr (PW) eb = ebrow[j + u * G_::NT];
     if (a.mode & M_MEASURE) {
-      if (ebrow) { mx.add(x.x / eb.x); mx.add(x.y / eb.y); }
+      if constexpr (PW) { mx.add(x.x / eb.x); mx.add(x.y / eb.y); }
       else { mx.add(x.x); mx.add(x.y); }
       bad |= (x.x != x.x) | (x.y != x.y);
       ssq = fmaf(x.x, x.x, fmaf(x.y, x.y, ssq));
     }
     if (a.mode & M_PRECLIP) {
-      const float cx = clampT(x.x, p.Esf * eb.x), cy = clampT(x.y, p.Esf * eb.y);
+      const float cx = PW ? clampT(x.x, p.Esf * eb.x) : clampT(x.x, p.Esf);
+      const float cy = PW ? clampT(x.y, p.Esf * eb.y) : clampT(x.y, p.Esf);
       cnt += (cx != x.x) + (cy != x.y);
       if (a.ed_s && live)
         record_s<float>(reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M + j + u * G_::NT,
@@ -479,13 +484,18 @@ __device__ __forceinline__ void s_clip_full(v2<T> (&v)[V], T Es, bool count, Mas
 
 // Loop body x pass on one tile held in registers: C2R, scale 1/N, s-clip
 // (or adjoint mask), R2C.  Returns the active-clip count of the thread.
-template <typename T, int M, class TL>
+template <typename T, int M, class TL, bool PW = false, bool ED = true>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
                                                       int j, int64_t mthr, int64_t row, bool live,
                                                       int t_it, TL& tl, const v2<T>* twg,
                                                       const v2<T>* twr, float2* edrow = nullptr,
                                                       const float2* ebrow = nullptr) {
   constexpr int V = F2<M>::V, NT = F2<M>::NT, MW = (V + 7) / 8;
+  float2 eb[PW ? V : 1];   // pointwise E_n of the thread's points, loaded before the transform
+  if constexpr (PW) {
+#pragma unroll
+    for (int u = 0; u < V; ++u) eb[u] = ebrow[j + u * NT];
+  }
   c2r_pre<T, M>(v, j, tl, twr);
   fft_pencil<T, M, +1>(v, j, twg, tl);
   unsigned long long cnt = 0;
@@ -495,9 +505,8 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     v[u] = mk<T>(v[u].x * inv_n, v[u].y * inv_n);
-    if (ebrow) {   // pointwise E_n: the vote runs on ratios
-      const float2 eb = ebrow[j + u * NT];
-      mx.add(v[u].x / (T)eb.x); mx.add(v[u].y / (T)eb.y);
+    if constexpr (PW) {   // pointwise E_n: the vote runs on ratios
+      mx.add(v[u].x / (T)eb[u].x); mx.add(v[u].y / (T)eb[u].y);
     } else {
       mx.add(v[u].x); mx.add(v[u].y);
     }
@@ -524,11 +533,11 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
     if ((a.mode & M_RECORD) && live) mb.store(a.mask, mthr);
   } else if (need_clip) {
     // lean path: only warps holding a value outside the s-cube clip
-    const bool rec_s = edrow != nullptr && live;
+    const bool rec_s = ED && edrow != nullptr && live;   // ED = false compiles the recording out
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       T bx = Es, by = Es;
-      if (ebrow) { const float2 eb = ebrow[j + u * NT]; bx = Es * (T)eb.x; by = Es * (T)eb.y; }
+      if constexpr (PW) { bx = Es * (T)eb[u].x; by = Es * (T)eb[u].y; }
       const T cx = clampT(v[u].x, bx), cy = clampT(v[u].y, by);
       if (count) cnt += (cx != v[u].x) + (cy != v[u].y);
       if (rec_s) record_s<T>(edrow + j + u * NT, cx - v[u].x, cy - v[u].y);   // spat_edits += eps' - eps
@@ -540,8 +549,8 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
   return live ? cnt : 0ull;
 }
 
-template <typename T, int M, int W = TileW<T>::value>
-__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
+template <typename T, int M, int W = TileW<T>::value, bool PW = false>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, PW ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
 k_px(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
@@ -550,8 +559,8 @@ k_px(Args a) {
   for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
-  const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
-  unsigned long long cnt = px_core<T, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
+  const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+  unsigned long long cnt = px_core<T, M, TL, PW>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
@@ -567,7 +576,7 @@ k_px(Args a) {
 // Exit x pass: C2R, scale 1/N, s-clip, store float32 e (rebuilds the iterate
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
 // no clip is applied.
-template <typename T, int M, int W = TileW<T>::value>
+template <typename T, int M, int W = TileW<T>::value, bool PW = false>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xexit(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
@@ -581,17 +590,22 @@ k_xexit(Args a) {
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
-  const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+  const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
   if (live) {
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       T x = v[u].x * inv_n, y = v[u].y * inv_n;
-      const float2 eb = ebrow ? ebrow[j + u * G_::NT] : make_float2(1.f, 1.f);
-      if (a.mode & M_CLIP) { x = clampT(x, Es * (T)eb.x); y = clampT(y, Es * (T)eb.y); }
+      float2 eb = make_float2(1.f, 1.f);
+      if constexpr (PW) eb = ebrow[j + u * G_::NT];
+      if (a.mode & M_CLIP) {
+        if constexpr (PW) { x = clampT(x, Es * (T)eb.x); y = clampT(y, Es * (T)eb.y); }
+        else { x = clampT(x, Es); y = clampT(y, Es); }
+      }
       float fx = (float)x, fy = (float)y;
       if (a.mode & M_CLIP) {
         // keep the float32 result inside the shrunk cube after rounding
-        fx = clampT(fx, p.Esf * eb.x); fy = clampT(fy, p.Esf * eb.y);
+        if constexpr (PW) { fx = clampT(fx, p.Esf * eb.x); fy = clampT(fy, p.Esf * eb.y); }
+        else { fx = clampT(fx, p.Esf); fy = clampT(fy, p.Esf); }
       }
       if (a.mode & M_ACC) {
         const float2 o = erow[j + u * G_::NT];
@@ -708,7 +722,7 @@ __host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
 
 // Everything of the check pass between load and store for one tile in
 // registers.  cta_has_mirror must be uniform over the CTA.
-template <typename T, int L, class TL>
+template <typename T, int L, class TL, bool PW = false>
 __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st,
                                          v2<T> (&v)[F2<L>::V], int j, int w, int64_t mthr,
                                          const ChkTile& c, bool cta_has_mirror, TL& tl,
@@ -721,6 +735,13 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   // canonical half spectrum, pws the step per kz; on mirror tiles pwb is the
   // kx = 0 bin (bounds of A) and pwb + pwM the kx = Nx/2 bin (bounds of B)
   constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
+  // pointwise bounds of the thread's bins, loaded before the forward
+  // transform so that their latency hides behind it
+  float2 qb[PW ? V : 1];
+  if constexpr (PW) {
+#pragma unroll
+    for (int u = 0; u < V; ++u) qb[u] = pwb[(int64_t)(j + u * NT) * pws];
+  }
   fft_pencil<T, L, -1>(v, j, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
   AbsMax<T> mx;
@@ -746,18 +767,18 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         T ar = T(0.5) * (cc.x + m.x), ai = T(0.5) * (cc.y - m.y);
         T br = T(0.5) * (cc.y + m.y), bi = T(0.5) * (m.x - cc.x);
         T bar = T(1), bai = T(1), bbr = T(1), bbi = T(1);   // pointwise bounds (ratios)
-        if (pwb) {
-          const float2 qa = pwb[(int64_t)(j + u * NT) * pws], qb = pwb[(int64_t)(j + u * NT) * pws + pwM];
-          bar = (T)qa.x; bai = (T)qa.y; bbr = (T)qb.x; bbi = (T)qb.y;
+        if constexpr (PW) {
+          const float2 qB = pwb[(int64_t)(j + u * NT) * pws + pwM];
+          bar = (T)qb[u].x; bai = (T)qb[u].y; bbr = (T)qB.x; bbi = (T)qB.y;
         }
         if (c.valid) {
-          if (pwb) { mx.add(ar / bar); mx.add(ai / bai); mx.add(br / bbr); mx.add(bi / bbi); }
+          if constexpr (PW) { mx.add(ar / bar); mx.add(ai / bai); mx.add(br / bbr); mx.add(bi / bbi); }
           else { mx.add(ar); mx.add(ai); mx.add(br); mx.add(bi); }
         }
         bad |= c.valid && ((ar != ar) | (ai != ai) | (br != br) | (bi != bi));
         if (clip) {
-          const T car = clampT(ar, Ds * bar), cai = clampT(ai, Ds * bai);
-          const T cbr = clampT(br, Ds * bbr), cbi = clampT(bi, Ds * bbi);
+          const T car = clampT(ar, PW ? Ds * bar : Ds), cai = clampT(ai, PW ? Ds * bai : Ds);
+          const T cbr = clampT(br, PW ? Ds * bbr : Ds), cbi = clampT(bi, PW ? Ds * bbi : Ds);
           const bool iar = car == ar, iai = cai == ai, ibr = cbr == br, ibi = cbi == bi;
           if (c.owner) cnt += (!iar) + (!iai) + (!ibr) + (!ibi);
           mb.template put<4>(u, (uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) |
@@ -765,8 +786,11 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           ar = car; ai = cai; br = cbr; bi = cbi;
           if (rec_f) {
             const T nx = ar - bi, ny = ai + br;
-            const T big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)) / bar, fabs(T(0.5) * (cc.y - m.y)) / bai),
-                               fmax(fabs(T(0.5) * (cc.y + m.y)) / bbr, fabs(T(0.5) * (m.x - cc.x)) / bbi));
+            T big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)), fabs(T(0.5) * (cc.y - m.y))),
+                         fmax(fabs(T(0.5) * (cc.y + m.y)), fabs(T(0.5) * (m.x - cc.x))));
+            if constexpr (PW)
+              big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)) / bar, fabs(T(0.5) * (cc.y - m.y)) / bai),
+                         fmax(fabs(T(0.5) * (cc.y + m.y)) / bbr, fabs(T(0.5) * (m.x - cc.x)) / bbi));
             record_f(a, ed_slot0 + u * ed_ustride, (float)(nx - cc.x), (float)(ny - cc.y), t_chk,
                      may_stop && big <= thr);
           }
@@ -788,12 +812,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   AbsMax<T> tm;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
-    if (pwb) {
-      const float2 q = pwb[(int64_t)(j + u * NT) * pws];
-      tm.add(v[u].x / (T)q.x); tm.add(v[u].y / (T)q.y);
-    } else {
-      tm.add(v[u].x); tm.add(v[u].y);
-    }
+    if constexpr (PW) { tm.add(v[u].x / (T)qb[u].x); tm.add(v[u].y / (T)qb[u].y); }
+    else { tm.add(v[u].x); tm.add(v[u].y); }
   }
   const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
   if (!c.mirror) {
@@ -810,14 +830,14 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
       for (int u = 0; u < V; ++u) {
         const T x = v[u].x, y = v[u].y;
         T qx = T(1), qy = T(1);
-        if (pwb) { const float2 q = pwb[(int64_t)(j + u * NT) * pws]; qx = (T)q.x; qy = (T)q.y; }
-        const T cx = clampT(x, Ds * qx), cy = clampT(y, Ds * qy);
+        if constexpr (PW) { qx = (T)qb[u].x; qy = (T)qb[u].y; }
+        const T cx = clampT(x, PW ? Ds * qx : Ds), cy = clampT(y, PW ? Ds * qy : Ds);
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
         mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
         if (rec_f)
           record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk,
-                   may_stop && fmax(fabs(x) / qx, fabs(y) / qy) <= thr);
+                   may_stop && (PW ? fmax(fabs(x) / qx, fabs(y) / qy) : fmax(fabs(x), fabs(y))) <= thr);
         v[u] = mk<T>(cx, cy);
       }
     } else if (clip) {
@@ -846,8 +866,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 // (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
 // the inverse FFT of this axis is applied before the store.  Tiles: see
 // ChkTile.
-template <typename T, int L, int W_ = TileW<T>::value>
-__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
+template <typename T, int L, int W_ = TileW<T>::value, bool PW = false>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, PW ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
 k_chk(Args a) {
   FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int W = G_::W, NT = G_::NT;
@@ -864,9 +884,9 @@ k_chk(Args a) {
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
-  const float2* pwb = a.pw_f ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
-  chk_core<T, L, TL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
-                     a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
+  const float2* pwb = PW ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
+  chk_core<T, L, TL, PW>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
+                         a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
@@ -1010,10 +1030,8 @@ k_chk_tma(Args a) {
     }
     TL tl{s_tiles + w, false};
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
-    const float2* pwb = a.pw_f ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
     chk_core<float, L, TL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red, &acc_vb, &acc_cnt,
-                           a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it, pwb,
-                           (int64_t)Nmid * (M + 1), M);
+                           a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
 #pragma unroll
@@ -1031,7 +1049,8 @@ k_chk_tma(Args a) {
   }
 }
 
-// Persistent float32 x pass (C2R, s-clip, R2C) fed by bulk copies: a CTA
+// Persistent float32 x pass (C2R, s-clip, R2C) fed by bulk copies (ED: with
+// the recording of spatial edits compiled in): a CTA
 // holds G tiles of W rows each (one warp per tile); its G W consecutive rows
 // are one contiguous block of the packed spectrum, loaded by a single
 // cp.async.bulk while the previous block is transformed.  Shared memory:
@@ -1045,7 +1064,7 @@ struct PxTmaGeo {
                                   2 * (size_t)M * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
 };
 
-template <int M, int W>
+template <int M, int W, bool ED = false>
 __global__ void __launch_bounds__(Geo<float, M, W>::NTHR, Geo<float, M, W>::MINB)
 k_px_tma(Args a) {
   using G_ = Geo<float, M, W>;
@@ -1114,8 +1133,7 @@ k_px_tma(Args a) {
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
     TL tl{s_tiles + g * TL::ELEMS + w, false};
     float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
-    const float2* ebrow = a.pw_e ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
-    cnt += px_core<float, M, TL>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
+    cnt += px_core<float, M, TL, false, ED>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow);
     if (live) {
       float2* out = outb + row * M;
 #pragma unroll
