@@ -45,8 +45,9 @@ FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # at 512^3 (profiles/); an entry is removed when its kernel changes.
 NCU_TRAFFIC = {
-    "chk<f32,512>": 566234112 + 509775872,        # k_chk_tma<512, 8>
-    "axis_fwd<f32,512>": 536907008 + 483582464,   # k_axis_tma<512, -1, 8>
+    "chk<f32,512>": 566073344 + 506883584,        # k_chk_tma<512, 8>
+    "axis_fwd<f32,512>": 536967424 + 483203328,   # k_axis_tma<512, -1, 8>
+    "px<f32,256>": 536958976 + 479542016,         # k_px_tma<256, 2>
     "axis_fwd<f64,512>": 1073873000 + 1018597000,  # k_axis<double, 512, -1, 4>
     "chk_cert<f64,512>": 1105932000 + 3677696,     # k_chk<double, 512, 4> (check only)
 }

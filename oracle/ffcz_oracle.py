@@ -9,7 +9,7 @@ the method's arithmetic.
 Everything is float64.  The DFT step is a library primitive (``scipy.fft``,
 full complex spectrum, no half-spectrum tricks); everything else is written out
 in the paper's order.  Readings of passages the paper leaves open are tagged
-``A1``..``A24`` and listed, with the reasons, in the design notes.
+``A1``..``A25`` and listed, with the reasons, in the design notes.
 
 Notation: ``e`` is the spatial error vector (epsilon in the paper), ``delta``
 its frequency error vector, ``E`` the spatial bound and ``D`` the frequency
@@ -375,6 +375,148 @@ def correct_backward(e0: np.ndarray, g_out: np.ndarray, E: float, D: float,
     if pre_mask is not None:
         g = g * pre_mask
     return g
+
+
+# --------------------------------------------------------------------------
+# Projection variants named as alternatives to POCS (Sec. III, POCS
+# paragraph; a direct or faster scheme is future work in Sec. VI).  A25.
+# --------------------------------------------------------------------------
+def project_f_spatial(z: np.ndarray, Ds) -> np.ndarray:
+    """P_F' as a map of spatial vectors: IDFT(ProjectOntoFCube(DFT(z)))."""
+    return idft(project_f(dft(z), Ds))
+
+
+def _variant_start(e0, E, eta):
+    e = np.asarray(e0, dtype=np.float64).copy()
+    pre = bool(e.size and np.any(np.abs(e) > E))          # A3, as in Alg. 1
+    if pre:
+        e = project_s(e, E * (1.0 - eta))
+    return e, pre
+
+
+def correct_dykstra(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
+                    max_iters: int = 10000, eta: float = ETA_DEFAULT,
+                    record: bool = False) -> Result:
+    """Dykstra's alternating projection onto F' then S' (Sec. III names it).
+
+    x_0 = e0 (after A3), p_0 = q_0 = 0, and per iteration
+        y = P_F'(x + p),  p <- x + p - y,
+        x' = P_S'(y + q), q <- y + q - x'.
+    The iterates converge to the point of S' and F' nearest to e0 (the
+    Euclidean projection of e0 onto the intersection), where POCS converges
+    to some point of it.  The check of Alg. 1 runs on x (always inside S'):
+    stop when its DFT violation <= D(1 - eta/2); the count is the number of
+    (P_F', P_S') pairs run, as for Alg. 1 (A8).
+    """
+    Es, Ds, thr = thresholds(E, D, eta)
+    x, pre = _variant_start(e0, E, eta)
+    p = np.zeros_like(x)
+    q = np.zeros_like(x)
+    t = 0
+    traj = []
+    while True:
+        v = f_violation(dft(x))
+        if not np.isfinite(v):
+            return Result(x, t, NONFINITE, pre, v / D, trajectory=traj)
+        if v <= thr and t >= min_iters:
+            return Result(x, t, OK, pre, v / D, trajectory=traj)
+        if t >= max_iters:
+            return Result(x, t, NOT_CONVERGED, pre, v / D, trajectory=traj)
+        y = project_f_spatial(x + p, Ds)
+        p = x + p - y
+        x_new = project_s(y + q, Es)
+        q = y + q - x_new
+        x = x_new
+        t += 1
+        if record:
+            traj.append(x.copy())
+
+
+def correct_douglas_rachford(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
+                             max_iters: int = 10000, eta: float = ETA_DEFAULT,
+                             record: bool = False) -> Result:
+    """Douglas-Rachford splitting for the feasibility problem of F' and S'
+    (Sec. III names it; its governing sequence z may end outside the
+    intersection, which is why the check runs on the S'-point x).
+
+    z_0 = e0 (after A3), and per iteration
+        y = P_F'(z),  x = P_S'(2y - z),  z <- z + x - y.
+    The candidate checked (as in Alg. 1) is x, e0 before the first iteration.
+    """
+    Es, Ds, thr = thresholds(E, D, eta)
+    z, pre = _variant_start(e0, E, eta)
+    x = z.copy()
+    t = 0
+    traj = []
+    while True:
+        v = f_violation(dft(x))
+        if not np.isfinite(v):
+            return Result(x, t, NONFINITE, pre, v / D, trajectory=traj)
+        if v <= thr and t >= min_iters:
+            return Result(x, t, OK, pre, v / D, trajectory=traj)
+        if t >= max_iters:
+            return Result(x, t, NOT_CONVERGED, pre, v / D, trajectory=traj)
+        y = project_f_spatial(z, Ds)
+        x = project_s(2.0 * y - z, Es)
+        z = z + x - y
+        t += 1
+        if record:
+            traj.append(x.copy())
+
+
+def correct_admm(e0: np.ndarray, E: float, D: float, *, min_iters: int = 0,
+                 max_iters: int = 10000, eta: float = ETA_DEFAULT,
+                 record: bool = False) -> Result:
+    """ADMM (scaled form) for: find a in F', b in S' with a = b (Sec. III
+    names it), i.e. minimise i_F'(a) + i_S'(b) subject to a - b = 0:
+
+        a <- P_F'(b - u),  b <- P_S'(a + u),  u <- u + a - b,
+
+    from b_0 = e0 (after A3), u_0 = 0.  The penalty parameter drops out
+    because both functions are indicators.  The candidate checked before the
+    first iteration is b_0 = e0 (its DFT violation, as in Alg. 1); after
+    iteration t it is a_t, which lies in F' by construction and is checked
+    against the s-cube: stop when max|a_t| <= E(1 - eta/2) (the midpoint rule
+    of A7 applied to the spatial bound).
+    """
+    Es, Ds, thr = thresholds(E, D, eta)
+    thr_s = E * (1.0 - eta / 2.0)
+    b, pre = _variant_start(e0, E, eta)
+    u = np.zeros_like(b)
+    v = f_violation(dft(b))
+    if not np.isfinite(v):
+        return Result(b, 0, NONFINITE, pre, v / D)
+    if v <= thr and min_iters <= 0:
+        return Result(b, 0, OK, pre, v / D)
+    if max_iters <= 0:
+        return Result(b, 0, NOT_CONVERGED, pre, v / D)
+    t = 0
+    traj = []
+    while True:
+        a = project_f_spatial(b - u, Ds)
+        t += 1
+        if record:
+            traj.append(a.copy())
+        sv = float(np.max(np.abs(a))) if a.size else 0.0
+        if not np.isfinite(sv):
+            return Result(a, t, NONFINITE, pre, sv / E, trajectory=traj)
+        if sv <= thr_s and t >= min_iters:
+            return Result(a, t, OK, pre, sv / E, trajectory=traj)
+        if t >= max_iters:
+            return Result(a, t, NOT_CONVERGED, pre, sv / E, trajectory=traj)
+        b = project_s(a + u, Es)
+        u = u + a - b
+
+
+METHODS = {"pocs": None, "dykstra": correct_dykstra, "dr": correct_douglas_rachford,
+           "admm": correct_admm}
+
+
+def correct_method(e0, E, D, method: str = "pocs", **kw) -> Result:
+    """Alg. 1 (``pocs``) or one of the projection variants of Sec. III."""
+    if method == "pocs":
+        return correct(e0, E, D, **kw)
+    return METHODS[method](e0, E, D, **kw)
 
 
 # --------------------------------------------------------------------------
