@@ -484,6 +484,41 @@ def pointwise_form(ffcz, torch, it, D, hbm, K=20):
             "frac_hbm_design": round(design / (it_ms / 1e3) / 1e9 / hbm, 4)}
 
 
+def variants_form(ffcz, torch, it, D, hbm, K=20):
+    """The projection variants of Sec. III (ffcz_opts.method) on the stress
+    variant: time to certified feasibility (the copy of e0 subtracted),
+    iterations, the size of the correction relative to e0, and per-iteration
+    time from K forced iterations minus 0 against the design traffic (Alg. 1
+    32N bytes; Dykstra + the residual spectrum and q read and written 48N;
+    Douglas-Rachford + the residual 40N; ADMM + u 40N)."""
+    shape, E = it["shape"], it["E"]
+    n = int(np.prod(shape))
+    d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
+    d = torch.empty_like(d0)
+    copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
+    nrm0 = float(torch.linalg.vector_norm(d0.double()))
+    design = {"pocs": 32.0, "dykstra": 48.0, "dr": 40.0, "admm": 40.0}
+    out = {"workload": it["name"] + " stress eps_f = 0.2 max box violation of e0"}
+    for m, bpn in design.items():
+        plan = ffcz.Plan([shape], method=m)
+        ms, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [D])[0])
+        edit = float(torch.linalg.vector_norm((d - d0).double())) / nrm0
+        del plan
+        per = {}
+        for k in (K, 0):
+            plan = ffcz.Plan([shape], method=m, min_iters=k, max_iters=k, certify=0)
+            per[k], _ = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [D])[0], reps=3)
+            del plan
+        it_ms = (per[K] - per[0]) / K
+        out[m] = {"ms_to_certified": round(ms - copy_ms, 3), "iters": st["iters"],
+                  "certified": st["certified"], "repairs": st["repairs"],
+                  "edit_norm_rel": round(edit, 6), "ms_per_iteration": round(it_ms, 4),
+                  "design_bytes": int(design[m] * n),
+                  "frac_hbm_design": round(design[m] * n / (it_ms / 1e3) / 1e9 / hbm, 4)}
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_forms(ffcz, torch, fin, it, hbm):
     """The stress variant, the batched and the differentiable forms (each a
     median of 2 calls after 1 warm-up; CUDA events on the current stream)."""
@@ -508,6 +543,8 @@ def measure_forms(ffcz, torch, fin, it, hbm):
     out["edits_stress_512"] = edits_form(ffcz, torch, it, fin["stress_D"])
     torch.cuda.empty_cache()
     out["pointwise_512"] = pointwise_form(ffcz, torch, it, fin["stress_D"], hbm)
+    torch.cuda.empty_cache()
+    out["variants_512"] = variants_form(ffcz, torch, it, fin["stress_D"], hbm)
     torch.cuda.empty_cache()
     out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
                                     "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")

@@ -76,6 +76,24 @@ typedef struct {
                           2D and 3D items; default 0 */
   int32_t pointwise;   /* 1: pointwise bounds E_n, Delta_k (ffcz_correct_pw);
                           2D and 3D items; default 0 */
+  int32_t method;      /* projection of the loop (the alternatives Sec. III
+                          names to POCS); every method checks its candidate
+                          point with the rule of Alg. 1 and returns it:
+                          0 (default) POCS, Alg. 1;
+                          1 Dykstra: y = P_F'(x + p), p += x - y,
+                            x = P_S'(y + q), q += y - x; converges to the
+                            point of the intersection nearest to e0; checks x;
+                          2 Douglas-Rachford on (F', S'): y = P_F'(z),
+                            x = P_S'(2y - z), z += x - y; checks x;
+                          3 ADMM, a = P_F'(b - u), b = P_S'(a + u),
+                            u += a - b; checks a against the s-cube
+                            (max|a| <= E(1 - eta/2)).
+                          Methods 1-3 need precision 32, 2D/3D items, no
+                          edits or pointwise bounds (else UNSUPPORTED); they
+                          use one more half-spectrum buffer (1, 2) and two
+                          float32 fields (1, 3); a failed certification is
+                          repaired with FP64 iterations of Alg. 1 */
+  int32_t reserved_;   /* 0 */
 } ffcz_opts;
 
 /* Per-item results. */
@@ -86,7 +104,9 @@ typedef struct {
   int32_t certified;   /* 1 if the FP64 check passed against the true bounds */
   int32_t preclipped;  /* 1 if e0 was outside the s-cube and was clipped first */
   int32_t pad_;
-  double f_ratio;      /* last loop violation / eps_f (working precision) */
+  double f_ratio;      /* last loop violation / eps_f (working precision);
+                          method 3 after >= 1 iteration: max|a_t| / eps_s,
+                          its stopping measure */
   double s_ratio;      /* max|e| / eps_s after the call (FP64 check) */
   double f_margin64;   /* 1 - (FP64 violation + FP64 FFT error bound) / eps_f */
   double s_margin64;   /* 1 - max|e| / eps_s (exact) */

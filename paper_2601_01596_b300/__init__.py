@@ -38,7 +38,13 @@ class Opts(ctypes.Structure):
                 ("K", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("count_active", ctypes.c_int32), ("edits", ctypes.c_int32),
-                ("pointwise", ctypes.c_int32)]
+                ("pointwise", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
+# Projection of the loop (ffcz_opts.method): Alg. 1 or one of the
+# alternatives Sec. III names.
+METHODS = {"pocs": 0, "dykstra": 1, "dr": 2, "douglas_rachford": 2, "admm": 3}
 
 
 class Stats(ctypes.Structure):
@@ -148,6 +154,8 @@ def default_opts(**kw) -> Opts:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
+        if k == "method" and isinstance(v, str):
+            v = METHODS[v]
         setattr(o, k, v)
     return o
 

@@ -176,6 +176,11 @@ struct ffcz_plan_s {
   float2* pw_f = nullptr;
   unsigned int* pw_min = nullptr;   // per item min Delta (float bits)
   int* pw_bad = nullptr;
+  // projection variant (opts.method): residual spectrum and the two
+  // parity buffers of q / u, used by the float32 loop only (pv_on)
+  float2* pv_r = nullptr;
+  float* pv_q[2] = {nullptr, nullptr};
+  bool pv_on = false;
   double* ps_acc = nullptr;         // power-spectrum shell sums (3 S per item)
   double* ps_rho = nullptr;
   int ps_S = 0;
@@ -318,21 +323,23 @@ constexpr int row_w2(int L) { return 2 * row_w1(L); }
 // g_pw_sel to reach them without bound pointers).
 thread_local bool g_pw_sel = false;
 
-template <typename T, int M, int W, bool PW = false>
+template <typename T, int M, int W, bool PW = false, int PV = PV_POCS>
 void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
   using G_ = Geo<T, M, W>;
   const int64_t tiles = (rows + G_::W - 1) / G_::W;
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, M, W>::bytes_x;
   if (g_dry) {
-    set_smem(k_xfwd<T, M, W, PW>, sm); set_smem(k_px<T, M, W, PW>, sm); set_smem(k_xexit<T, M, W, PW>, sm);
+    set_smem(k_xfwd<T, M, W, PW>, sm);
+    set_smem(k_px<T, M, W, PW, PV>, sm);
+    set_smem(k_xexit<T, M, W, PW, PV>, sm);
     return;
   }
   ProfScope ps(kind == XFWD ? "xfwd" : kind == XPX ? "px" : "xexit", 8 * (int)sizeof(T), M, s);
   switch (kind) {
     case XFWD: k_xfwd<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XPX: k_px<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XEXIT: k_xexit<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XPX: k_px<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XEXIT: k_xexit<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
   }
   g_launches++;
 }
@@ -378,6 +385,17 @@ struct XL {
     if (a.pw_e || g_pw_sel) {
       launch_x_tw<T, M, row_w1(M), true>(kind, a, rows, count, s);
       return;
+    }
+    if constexpr (sizeof(T) == 4) {
+      // projection variants: the x passes that carry q / u (one tile width)
+      if (a.pv == PV_DYKSTRA && kind != XFWD) {
+        launch_x_tw<T, M, row_w1(M), false, PV_DYKSTRA>(kind, a, rows, count, s);
+        return;
+      }
+      if (a.pv == PV_ADMM && kind == XPX) {
+        launch_x_tw<T, M, row_w1(M), false, PV_ADMM>(kind, a, rows, count, s);
+        return;
+      }
     }
     if constexpr (sizeof(T) == 4) {
       if (w < 0 && (kind == XPX || g_dry)) {
@@ -458,16 +476,16 @@ void launch_axis(int L, int w, const Args& a, int Nz, int M, int count, cudaStre
   FFCZ_DISPATCH_L(L, D::template go, w, a, Nz, M, count, s)
 }
 
-template <typename T, int L, int W, bool PW = false>
+template <typename T, int L, int W, bool PW = false, int PV = PV_POCS>
 void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   using G_ = Geo<T, L, W>;
   const int64_t tiles = chk_ntiles(W, M, Nmid);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L, W>::bytes_axis;
-  if (g_dry) { set_smem(k_chk<T, L, W, PW>, sm); return; }
+  if (g_dry) { set_smem(k_chk<T, L, W, PW, PV>, sm); return; }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk",
                8 * (int)sizeof(T), L, s);
-  k_chk<T, L, W, PW><<<grid, G_::NTHR, sm, s>>>(a);
+  k_chk<T, L, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
 template <typename T>
@@ -477,6 +495,11 @@ struct CL {
     if (a.pw_f || g_pw_sel) {
       launch_chk_tw<T, L, TileW<T>::value, true>(a, Nmid, M, count, s);
       return;
+    }
+    if constexpr (sizeof(T) == 4) {
+      // projection variants with a frequency residual (one tile width)
+      if (a.pv == PV_DYKSTRA) { launch_chk_tw<T, L, TileW<T>::value, false, PV_DYKSTRA>(a, Nmid, M, count, s); return; }
+      if (a.pv == PV_DR) { launch_chk_tw<T, L, TileW<T>::value, false, PV_DR>(a, Nmid, M, count, s); return; }
     }
     if constexpr (sizeof(T) == 4) {
       if constexpr (tma_ok<L>()) {
@@ -658,6 +681,12 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
     a.tm_axis = dg.tm_axis;
     a.tm_chk = dg.tm_chk;
   }
+  if (sizeof(T) == 4 && p->pv_on) {
+    a.pv = p->opts.method;
+    a.pv_r = p->pv_r;
+    a.pv_q[0] = p->pv_q[0];
+    a.pv_q[1] = p->pv_q[1];
+  }
   return a;
 }
 
@@ -705,6 +734,12 @@ void build_bt(ffcz_plan_s* p) {
 }
 
 // ----- the loop ---------------------------------------------------------------
+// 1 when the loop's stopping test is ADMM's spatial check (k_decide)
+template <typename T>
+int s_check_of(const ffcz_plan_s* p) {
+  return (sizeof(T) == 4 && p->pv_on && p->opts.method == PV_ADMM) ? 1 : 0;
+}
+
 struct LoopBufs {
   void* b0;
   void* b1;
@@ -816,7 +851,7 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
     launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
-                                                             p->d_nactive);
+                                                             p->d_nactive, s_check_of<T>(p));
   g_launches++;
 }
 
@@ -847,7 +882,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
-                                                             p->d_nactive);
+                                                             p->d_nactive, s_check_of<T>(p));
   g_launches++;
 }
 
@@ -867,7 +902,8 @@ void exit_pass(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
       a.sel_in = S_PREV;
     }
     tabs_x<T>(p, a, dg);
-    a.mode = M_CLIP;
+    // ADMM returns a_t, which its check found inside the s-cube, unclipped
+    a.mode = s_check_of<T>(p) ? 0 : M_CLIP;
     launch_x<T>(XEXIT, dg.M, dg.wx, a, dg.rows, dg.count, s);
   }
 }
@@ -1002,6 +1038,8 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
     q.max_iters = max_iters;
     q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0;
     q.bscale = 1.0;
+    q.thrs = E * (1.0 - eta / 2.0);
+    q.thrsf = (float)q.thrs;
     if (p->ndim == 1) {
       const int64_t P = p1d_len(n);
       q.inv_pn = 1.0 / ((double)P * (double)n);
@@ -1237,7 +1275,9 @@ void apply_edits(ffcz_plan_s* p, float* xhat, int m, const uint8_t* sf, const in
 template <typename T>
 void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
   p->ed_on = p->opts.edits != 0;   // the loop's kernels record edits
-  struct Off { ffcz_plan_s* p; ~Off() { p->ed_on = false; } } off_{p};
+  // the projection variant runs in the float32 loop; FP64 repairs use Alg. 1
+  p->pv_on = sizeof(T) == 4 && p->opts.method != PV_POCS;
+  struct Off { ffcz_plan_s* p; ~Off() { p->ed_on = false; p->pv_on = false; } } off_{p};
   LoopBufs B = loop_bufs<T>(p);
   CK(cudaMemsetAsync(p->d_nactive, 0, sizeof(int), p->stream));
   k_init<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, (int)p->batch,
@@ -1579,6 +1619,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
   if (p->batch != 1) fail(FFCZ_ERR_UNSUPPORTED, "backward needs a single-item plan");
   if (p->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "backward supports 2D and 3D items");
   if (p->opts.pointwise) fail(FFCZ_ERR_INVALID, "backward uses scalar bounds");
+  if (p->opts.method != PV_POCS) fail(FFCZ_ERR_UNSUPPORTED, "backward differentiates Alg. 1 (method 0)");
   if (!e0 || !gout || !gin || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
   const int K = p->opts.K, m = p->opts.ckpt_every;
   if (K < 1 || m < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
@@ -1887,6 +1928,8 @@ void ffcz_default_opts(ffcz_opts* o) {
   o->count_active = 1;
   o->edits = 0;
   o->pointwise = 0;
+  o->method = 0;
+  o->reserved_ = 0;
 }
 
 ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t batch,
@@ -1903,6 +1946,10 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (o.precision != 32 && o.precision != 64) fail(FFCZ_ERR_INVALID, "precision must be 32 or 64");
     if (!(o.shrink >= 0.0 && o.shrink < 0.5)) fail(FFCZ_ERR_INVALID, "shrink must be in [0, 0.5)");
     if (o.max_iters < 0 || o.min_iters < 0) fail(FFCZ_ERR_INVALID, "iteration limits must be >= 0");
+    if (o.method < PV_POCS || o.method > PV_ADMM) fail(FFCZ_ERR_INVALID, "method must be 0..3");
+    if (o.method != PV_POCS && (ndim == 1 || o.edits || o.pointwise || o.precision != 32))
+      fail(FFCZ_ERR_UNSUPPORTED, "projection variants run float32 loops on 2D/3D items without "
+                                 "edits or pointwise bounds");
     for (int64_t i = 0; i < batch; ++i) {
       if (ndim == 1) {
         const int64_t n = shapes[i];
@@ -2068,6 +2115,14 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         }
         g_pw_sel = false;
       }
+      if (p->opts.method != PV_POCS) {
+        Args b{};
+        b.pv = p->opts.method;
+        for (const auto& dg : p->groups) {
+          launch_x<float>(XPX, dg.M, dg.wx, b, dg.rows, 1, nullptr);
+          launch_chk<float>(dg.Nz, dg.wc, b, dg.Ny, dg.M, 1, nullptr);
+        }
+      }
       for (const auto& dg0 : p->groups) {
         for (int alt = 0; alt < 3; ++alt) {
           DevGroup dg = dg0;
@@ -2103,6 +2158,12 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     // float32 spectrum buffers: N/2 complex64 each (4 bytes per point)
     p->B32[0] = dalloc(p.get(), sizeof(float2) * p->total_c);
     p->B32[1] = dalloc(p.get(), sizeof(float2) * p->total_c);
+    // projection variants: frequency residual (Dykstra, DR), q / u (Dykstra, ADMM)
+    if (o.method == PV_DYKSTRA || o.method == PV_DR) p->pv_r = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
+    if (o.method == PV_DYKSTRA || o.method == PV_ADMM) {
+      p->pv_q[0] = (float*)dalloc(p.get(), sizeof(float) * p->total);
+      p->pv_q[1] = (float*)dalloc(p.get(), sizeof(float) * p->total);
+    }
     build_tensor_maps(p.get());
     p->d_prm = (ItemParams*)dalloc(p.get(), sizeof(ItemParams) * batch);
     p->d_st = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);

@@ -45,6 +45,9 @@ struct ItemParams {
   // factor on the FP64 rounding bound in the certification: 1, or for
   // pointwise bounds (where D = 1 and violations are ratios) 1 / min_k Delta_k
   double bscale;
+  // spatial stopping threshold E(1 - eta/2) of the ADMM variant
+  double thrs;
+  float thrsf, pad_f;
 };
 
 struct ItemState {
@@ -57,6 +60,7 @@ struct ItemState {
   double v64, emax64, bound64;   // certification results
   int32_t t, done, status, preclip;
   int32_t certified, repairs, pad0, pad1;
+  unsigned long long svbits;     // ADMM: max |a_t| of the loop's spatial check (double bits)
 };
 
 struct Group {
@@ -67,6 +71,11 @@ struct Group {
   const int64_t* soff;           // complex offset of each member's spectrum
   const int64_t* coff;           // offset of each member's canonical half spectrum
 };
+
+// Projection of the loop: Alg. 1 (POCS) or one of the variants that Sec. III
+// names as alternatives (Dykstra; Douglas-Rachford on F' then S'; ADMM, which
+// on F' then S' is Douglas-Rachford on S' then F').
+enum Variant : int { PV_POCS = 0, PV_DYKSTRA = 1, PV_DR = 2, PV_ADMM = 3 };
 
 enum Pred : int { P_ALL = 0, P_ACTIVE = 1, P_EXIT = 2, P_PRECLIP = 3, P_UNCERT = 4 };
 enum Sel : int { S_CUR = 0, S_PREV = 1 };
@@ -113,6 +122,14 @@ struct Args {
   // compare and reduce ratios
   const float* pw_e;
   const float2* pw_f;
+  // projection variant (Variant; float32 loops only).  pv_r: residual of the
+  // frequency projection (Dykstra's p, Douglas-Rachford's z - P_F'(z)) in the
+  // packed spectrum layout, read and rewritten in place by the check pass;
+  // pv_q: Dykstra's q or ADMM's scaled dual u, float32 laid out like e, one
+  // buffer per iteration parity (the exit pass rebuilds x_t from q_{t-1})
+  int pv;
+  float2* pv_r;
+  float* pv_q[2];
 };
 
 // Spatial edit of one complex register (two real points): S += (c - v).
@@ -484,23 +501,63 @@ __device__ __forceinline__ void s_clip_full(v2<T> (&v)[V], T Es, bool count, Mas
 
 // Loop body x pass on one tile held in registers: C2R, scale 1/N, s-clip
 // (or adjoint mask), R2C.  Returns the active-clip count of the thread.
-template <typename T, int M, class TL, bool PW = false, bool ED = true>
+template <typename T, int M, class TL, bool PW = false, bool ED = true, int PV = PV_POCS>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
                                                       int j, int64_t mthr, int64_t row, bool live,
                                                       int t_it, TL& tl, const v2<T>* twg,
                                                       const v2<T>* twr, float2* edrow = nullptr,
-                                                      const float2* ebrow = nullptr) {
+                                                      const float2* ebrow = nullptr,
+                                                      const float2* qin = nullptr, float2* qout = nullptr,
+                                                      AbsMax<T>* svm = nullptr) {
   constexpr int V = F2<M>::V, NT = F2<M>::NT, MW = (V + 7) / 8;
   float2 eb[PW ? V : 1];   // pointwise E_n of the thread's points, loaded before the transform
   if constexpr (PW) {
 #pragma unroll
     for (int u = 0; u < V; ++u) eb[u] = ebrow[j + u * NT];
   }
+  // Dykstra's q / ADMM's u of the previous iteration (zero before the
+  // second s-projection), loaded before the transform
+  constexpr bool QV = (PV == PV_DYKSTRA || PV == PV_ADMM);
+  float2 qv[QV ? V : 1];
+  if constexpr (QV) {
+    const bool q_in = t_it >= 2 && live;
+#pragma unroll
+    for (int u = 0; u < V; ++u) qv[u] = q_in ? qin[j + u * NT] : make_float2(0.f, 0.f);
+  }
   c2r_pre<T, M>(v, j, tl, twr);
   fft_pencil<T, M, +1>(v, j, twg, tl);
   unsigned long long cnt = 0;
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
+  if constexpr (QV) {
+    const bool count = (a.mode & M_COUNT) != 0;
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const T x = v[u].x * inv_n, y = v[u].y * inv_n;
+      if constexpr (PV == PV_DYKSTRA) {
+        // x' = P_S'(y + q), q <- y + q - x'
+        const T wx = x + (T)qv[u].x, wy = y + (T)qv[u].y;
+        const T cx = clampT(wx, Es), cy = clampT(wy, Es);
+        if (count) cnt += (cx != wx) + (cy != wy);
+        if (live) qout[j + u * NT] = make_float2((float)(wx - cx), (float)(wy - cy));
+        v[u] = mk<T>(cx, cy);
+      } else {
+        // ADMM: a_t (the input) is checked against the s-cube; then
+        // b = P_S'(a + u), u <- a + u - b, and the pass forwards b - u
+        svm->add(x);
+        svm->add(y);
+        const T wx = x + (T)qv[u].x, wy = y + (T)qv[u].y;
+        const T bx = clampT(wx, Es), by = clampT(wy, Es);
+        if (count) cnt += (bx != wx) + (by != wy);
+        const T ux = wx - bx, uy = wy - by;
+        if (live) qout[j + u * NT] = make_float2((float)ux, (float)uy);
+        v[u] = mk<T>(bx - ux, by - uy);
+      }
+    }
+    fft_pencil<T, M, -1>(v, j, twg, tl);
+    r2c_post<T, M>(v, j, tl, twr);
+    return live ? cnt : 0ull;
+  }
   AbsMax<T> mx;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
@@ -549,8 +606,9 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
   return live ? cnt : 0ull;
 }
 
-template <typename T, int M, int W = TileW<T>::value, bool PW = false>
-__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, PW ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR,
+                                  (PW || PV != PV_POCS) ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
 k_px(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
@@ -560,11 +618,25 @@ k_px(Args a) {
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
   const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
-  unsigned long long cnt = px_core<T, M, TL, PW>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
+  const float2* qin = nullptr;
+  float2* qout = nullptr;
+  if constexpr (PV != PV_POCS) {
+    qin = reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M;
+    qout = reinterpret_cast<float2*>(a.pv_q[t_it & 1] + a.g.eoff[gi]) + row * M;
+  }
+  AbsMax<T> svm;
+  unsigned long long cnt = px_core<T, M, TL, PW, true, PV>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr,
+                                                           edrow, ebrow, qin, qout, &svm);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
     for (int u = 0; u < V; ++u) out[j + u * G_::NT] = v[u];
+  }
+  if constexpr (PV == PV_ADMM) {
+    // spatial check of a_t: block max, one atomic per CTA (NaN -> +inf)
+    unsigned long long vb = live ? svm.dbits(svm.val() != svm.val()) : 0ull, cz = 0ull;
+    block_max_count(vb, cz, false, s_red);
+    if (threadIdx.x == 0) atomicMax(&st.svbits, vb);
   }
   if (a.mode & M_COUNT) {
     Red r{0ull, 0.0, cnt};
@@ -576,7 +648,7 @@ k_px(Args a) {
 // Exit x pass: C2R, scale 1/N, s-clip, store float32 e (rebuilds the iterate
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
 // no clip is applied.
-template <typename T, int M, int W = TileW<T>::value, bool PW = false>
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xexit(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
@@ -591,10 +663,19 @@ k_xexit(Args a) {
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
   const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+  // Dykstra: x_t = P_S'(y_{t-1} + q_{t-1}) (q_0 = 0)
+  const float2* qrow = (PV == PV_DYKSTRA && t_it >= 2)
+                           ? reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M
+                           : nullptr;
   if (live) {
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       T x = v[u].x * inv_n, y = v[u].y * inv_n;
+      if (PV == PV_DYKSTRA && qrow) {
+        const float2 q = qrow[j + u * G_::NT];
+        x += (T)q.x;
+        y += (T)q.y;
+      }
       float2 eb = make_float2(1.f, 1.f);
       if constexpr (PW) eb = ebrow[j + u * G_::NT];
       if (a.mode & M_CLIP) {
@@ -722,7 +803,7 @@ __host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
 
 // Everything of the check pass between load and store for one tile in
 // registers.  cta_has_mirror must be uniform over the CTA.
-template <typename T, int L, class TL, bool PW = false>
+template <typename T, int L, class TL, bool PW = false, int PV = PV_POCS>
 __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st,
                                          v2<T> (&v)[F2<L>::V], int j, int w, int64_t mthr,
                                          const ChkTile& c, bool cta_has_mirror, TL& tl,
@@ -742,6 +823,15 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 #pragma unroll
     for (int u = 0; u < V; ++u) qb[u] = pwb[(int64_t)(j + u * NT) * pws];
   }
+  // Dykstra / Douglas-Rachford: the residual r of the previous frequency
+  // projection (zero before the first one), loaded before the transform
+  constexpr bool RES = (PV == PV_DYKSTRA || PV == PV_DR);
+  float2 rr[RES ? V : 1];
+  if constexpr (RES) {
+    const bool res_in = t_chk >= 1 && c.valid;
+#pragma unroll
+    for (int u = 0; u < V; ++u) rr[u] = res_in ? a.pv_r[ed_slot0 + u * ed_ustride] : make_float2(0.f, 0.f);
+  }
   fft_pencil<T, L, -1>(v, j, twg, tl);
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
   AbsMax<T> mx;
@@ -756,7 +846,46 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   const bool may_stop = t_chk >= p.min_iters;
   const T thr = sizeof(T) == 4 ? (T)p.thrf : (T)p.thr;
   if (use_mask && c.live) mb.load(a.mask, mthr);
-  if (cta_has_mirror) {
+  if constexpr (RES) {
+    if (cta_has_mirror) {
+      // check on x's spectrum C (A, B separated), then the projection of
+      // C' = C + r, whose partner values need a second exchange
+      store_nat<T, L, TL>(v, j, tl);
+      if (c.mirror) {
+        const int dw = (w ^ 1) - w;
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+          const v2<T> cc = v[u], m = tl.at_other((L - (j + u * NT)) & (L - 1), dw);
+          const T ar = T(0.5) * (cc.x + m.x), ai = T(0.5) * (cc.y - m.y);
+          const T br = T(0.5) * (cc.y + m.y), bi = T(0.5) * (m.x - cc.x);
+          if (c.valid) { mx.add(ar); mx.add(ai); mx.add(br); mx.add(bi); }
+          bad |= c.valid && ((ar != ar) | (ai != ai) | (br != br) | (bi != bi));
+        }
+      }
+      tl.done();
+      if (c.mirror) {
+#pragma unroll
+        for (int u = 0; u < V; ++u) v[u] = mk<T>(v[u].x + (T)rr[u].x, v[u].y + (T)rr[u].y);
+      }
+      store_nat<T, L, TL>(v, j, tl);
+      if (c.mirror) {
+        const int dw = (w ^ 1) - w;
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+          const v2<T> cc = v[u], m = tl.at_other((L - (j + u * NT)) & (L - 1), dw);
+          const T ar = T(0.5) * (cc.x + m.x), ai = T(0.5) * (cc.y - m.y);
+          const T br = T(0.5) * (cc.y + m.y), bi = T(0.5) * (m.x - cc.x);
+          const T car = clampT(ar, Ds), cai = clampT(ai, Ds), cbr = clampT(br, Ds), cbi = clampT(bi, Ds);
+          if (c.owner && count) cnt += (car != ar) + (cai != ai) + (cbr != br) + (cbi != bi);
+          const T yx = car - cbi, yy = cai + cbr;          // Y = A' + i B'
+          const T rx = cc.x - yx, ry = cc.y - yy;          // r <- C' - Y
+          if (c.owner) a.pv_r[ed_slot0 + u * ed_ustride] = make_float2((float)rx, (float)ry);
+          v[u] = PV == PV_DYKSTRA ? mk<T>(yx, yy) : mk<T>(yx - rx, yy - ry);
+        }
+      }
+      tl.done();
+    }
+  } else if (cta_has_mirror) {
     store_nat<T, L, TL>(v, j, tl);
     if (c.mirror) {
       const int dw = (w ^ 1) - w;
@@ -816,7 +945,20 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
     else { tm.add(v[u].x); tm.add(v[u].y); }
   }
   const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
-  if (!c.mirror) {
+  if (RES && !c.mirror) {
+    if (c.valid) { mx = tm; bad = nan_probe<T, V>(v); }
+    // y = P_F'(x + r), r <- x + r - y; output y (Dykstra) or 2y - (x + r) =
+    // y - r (Douglas-Rachford)
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const T x = v[u].x + (T)rr[u].x, y = v[u].y + (T)rr[u].y;
+      const T cx = clampT(x, Ds), cy = clampT(y, Ds);
+      if (count && c.owner) cnt += 2 * ((cx != x) + (cy != y));
+      const T rx = x - cx, ry = y - cy;
+      if (c.owner) a.pv_r[ed_slot0 + u * ed_ustride] = make_float2((float)rx, (float)ry);
+      v[u] = PV == PV_DYKSTRA ? mk<T>(cx, cy) : mk<T>(cx - rx, cy - ry);
+    }
+  } else if (!c.mirror) {
     if (c.valid) { mx = tm; bad = nan_probe<T, V>(v); }
     if (use_mask) {
 #pragma unroll
@@ -866,8 +1008,9 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 // (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
 // the inverse FFT of this axis is applied before the store.  Tiles: see
 // ChkTile.
-template <typename T, int L, int W_ = TileW<T>::value, bool PW = false>
-__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, PW ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
+template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR,
+                                  (PW || PV != PV_POCS) ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
 k_chk(Args a) {
   FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int W = G_::W, NT = G_::NT;
@@ -885,8 +1028,8 @@ k_chk(Args a) {
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
   const float2* pwb = PW ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
-  chk_core<T, L, TL, PW>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
-                         a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
+  chk_core<T, L, TL, PW, PV>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
+                             a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
@@ -1215,15 +1358,24 @@ static __global__ void k_pw_scale(ItemParams* prm, const unsigned int* minbits, 
 
 // Loop decision after a check (Alg. 1: break when CheckConvergence passes;
 // readings: stop at v <= D(1 - eta/2) once t >= min_iters, cap at max_iters).
-static __global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int* n_active) {
+// s_check: ADMM loops, whose candidate after iteration t >= 1 is a_t (inside
+// F' by construction) and whose stopping test is max|a_t| <= E(1 - eta/2).
+static __global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int* n_active, int s_check = 0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ItemState& s = st[i];
   if (s.done) return;
   const ItemParams& p = prm[i];
-  const double v = __longlong_as_double((long long)s.vbits);
+  double v = __longlong_as_double((long long)s.vbits);
+  double thr = p.thr;
   s.vbits = 0ull;
   s.f_ratio = v / p.D;
+  if (s_check && s.t >= 1) {
+    const double sv = __longlong_as_double((long long)s.svbits);
+    if (!(sv <= DBL_MAX)) v = sv;   // non-finite either way
+    else if (v <= DBL_MAX) { v = sv; thr = p.thrs; s.f_ratio = sv / p.E; }
+  }
+  s.svbits = 0ull;
   s.last_act_s = s.act_s;
   s.last_act_f = s.prev_act_f;
   s.prev_act_f = s.act_f;
@@ -1231,7 +1383,7 @@ static __global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int
   s.act_f = 0ull;
   int done = 0;
   if (!(v <= DBL_MAX)) { done = 1; s.status = 6; }
-  else if (v <= p.thr && s.t >= p.min_iters) { done = 1; s.status = 0; }
+  else if (v <= thr && s.t >= p.min_iters) { done = 1; s.status = 0; }
   else if (s.t >= p.max_iters) { done = 1; s.status = 4; }
   if (done) {
     s.done = 1;
@@ -1248,7 +1400,7 @@ static __global__ void k_init(ItemState* st, int n, int only_uncertified, int* n
   if (i >= n) return;
   ItemState& s = st[i];
   const bool run = !only_uncertified || !s.certified;
-  s.vbits = 0ull; s.emaxbits = 0ull; s.sumsq = 0.0;
+  s.vbits = 0ull; s.svbits = 0ull; s.emaxbits = 0ull; s.sumsq = 0.0;
   s.act_s = s.act_f = 0ull; s.last_act_s = s.last_act_f = s.prev_act_f = 0ull;
   s.t = 0;
   s.done = run ? 0 : 1;

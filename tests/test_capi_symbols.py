@@ -34,7 +34,7 @@ def test_host_only_calls():
         assert L.ffcz_strerror(s)
     assert L.ffcz_launch_count() >= 0
     # struct layouts match the header (checked on the host compiler's ABI)
-    assert ctypes.sizeof(ffcz.Opts) == 56 and ctypes.sizeof(ffcz.Stats) == 80   # 12 int32 + 1 double
+    assert ctypes.sizeof(ffcz.Opts) == 64 and ctypes.sizeof(ffcz.Stats) == 80   # 14 int32 + 1 double
 
 
 def test_invalid_arguments_fail_before_any_device_work():
