@@ -445,13 +445,19 @@ void launch_axis_tma(const Args& a, int Nz, int M, int count, cudaStream_t s) {
   k_axis_tma<L, DIR, 8><<<dim3(tma_grid_x(tiles, count), (unsigned)count), Geo<float, L, 8>::NTHR, sm, s>>>(a);
   g_launches++;
 }
+// The check pass needs its full variant for the adjoint's mask modes and for
+// edit recording; every other launch takes the lean one.
+inline bool chk_full(const Args& a) { return (a.mode & (M_RECORD | M_MASK)) != 0 || a.ed_t != nullptr; }
+
 template <int L>
 void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_ntiles(8, M, Nmid);
   const size_t sm = TmaGeo<L, 8>::bytes;
-  if (g_dry) { set_smem(k_chk_tma<L, 8>, sm); return; }
+  if (g_dry) { set_smem(k_chk_tma<L, 8, true>, sm); set_smem(k_chk_tma<L, 8, false>, sm); return; }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk", 32, L, s);
-  k_chk_tma<L, 8><<<dim3(tma_grid_x(tiles, count), (unsigned)count), Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  const dim3 grid(tma_grid_x(tiles, count), (unsigned)count);
+  if (chk_full(a)) k_chk_tma<L, 8, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  else k_chk_tma<L, 8, false><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
   g_launches++;
 }
 
@@ -482,11 +488,27 @@ void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_ntiles(W, M, Nmid);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L, W>::bytes_axis;
-  if (g_dry) { set_smem(k_chk<T, L, W, PW, PV>, sm); return; }
+  // pointwise plans keep the full form (edits may be on); projection
+  // variants only run lean (no edits, no adjoint)
+  constexpr bool lean_ok = !PW, only_lean = PV != PV_POCS;
+  if (g_dry) {
+    if constexpr (!only_lean) set_smem(k_chk<T, L, W, PW, PV, true>, sm);
+    if constexpr (lean_ok) set_smem(k_chk<T, L, W, PW, PV, false>, sm);
+    return;
+  }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk",
                8 * (int)sizeof(T), L, s);
-  k_chk<T, L, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a);
-  g_launches++;
+  if constexpr (lean_ok) {
+    if (only_lean || !chk_full(a)) {
+      k_chk<T, L, W, PW, PV, false><<<grid, G_::NTHR, sm, s>>>(a);
+      g_launches++;
+      return;
+    }
+  }
+  if constexpr (!only_lean) {
+    k_chk<T, L, W, PW, PV, true><<<grid, G_::NTHR, sm, s>>>(a);
+    g_launches++;
+  }
 }
 template <typename T>
 struct CL {

@@ -803,7 +803,9 @@ __host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
 
 // Everything of the check pass between load and store for one tile in
 // registers.  cta_has_mirror must be uniform over the CTA.
-template <typename T, int L, class TL, bool PW = false, int PV = PV_POCS>
+// FULL = false compiles out the adjoint mask modes and the edit recording
+// (the forward loop's lean variant: less code, no mask-bit bookkeeping).
+template <typename T, int L, class TL, bool PW = false, int PV = PV_POCS, bool FULL = true>
 __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st,
                                          v2<T> (&v)[F2<L>::V], int j, int w, int64_t mthr,
                                          const ChkTile& c, bool cta_has_mirror, TL& tl,
@@ -839,10 +841,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   unsigned long long cnt = 0;
   MaskBits<MW> mb;
   mb.clear();
-  const bool rec = (a.mode & M_RECORD) != 0, use_mask = (a.mode & M_MASK) != 0;
+  const bool rec = FULL && (a.mode & M_RECORD) != 0, use_mask = FULL && (a.mode & M_MASK) != 0;
   const bool clip = (a.mode & M_CLIP) != 0, count = (a.mode & M_COUNT) != 0;
   // freq_edits += delta' - delta (not at the max_iters check, which stops)
-  const bool rec_f = clip && a.ed_t != nullptr && c.owner && t_chk < p.max_iters;
+  const bool rec_f = FULL && clip && a.ed_t != nullptr && c.owner && t_chk < p.max_iters;
   const bool may_stop = t_chk >= p.min_iters;
   const T thr = sizeof(T) == 4 ? (T)p.thrf : (T)p.thr;
   if (use_mask && c.live) mb.load(a.mask, mthr);
@@ -910,8 +912,9 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           const T cbr = clampT(br, PW ? Ds * bbr : Ds), cbi = clampT(bi, PW ? Ds * bbi : Ds);
           const bool iar = car == ar, iai = cai == ai, ibr = cbr == br, ibi = cbi == bi;
           if (c.owner) cnt += (!iar) + (!iai) + (!ibr) + (!ibi);
-          mb.template put<4>(u, (uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) |
-                                    ((uint32_t)ibi << 3));
+          if (FULL)
+            mb.template put<4>(u, (uint32_t)iar | ((uint32_t)iai << 1) | ((uint32_t)ibr << 2) |
+                                      ((uint32_t)ibi << 3));
           ar = car; ai = cai; br = cbr; bi = cbi;
           if (rec_f) {
             const T nx = ar - bi, ny = ai + br;
@@ -976,13 +979,13 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         const T cx = clampT(x, PW ? Ds * qx : Ds), cy = clampT(y, PW ? Ds * qy : Ds);
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
-        mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
+        if (FULL) mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
         if (rec_f)
           record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk,
                    may_stop && (PW ? fmax(fabs(x) / qx, fabs(y) / qy) : fmax(fabs(x), fabs(y))) <= thr);
         v[u] = mk<T>(cx, cy);
       }
-    } else if (clip) {
+    } else if (clip && FULL) {
       mb.fill();   // nothing clipped
     }
   }
@@ -1008,7 +1011,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 // (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
 // the inverse FFT of this axis is applied before the store.  Tiles: see
 // ChkTile.
-template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS>
+template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
 __global__ void __launch_bounds__(Geo<T, L, W_>::NTHR,
                                   (PW || PV != PV_POCS) ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
 k_chk(Args a) {
@@ -1028,7 +1031,7 @@ k_chk(Args a) {
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
   const float2* pwb = PW ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
-  chk_core<T, L, TL, PW, PV>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
+  chk_core<T, L, TL, PW, PV, FULL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
                              a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
@@ -1137,7 +1140,7 @@ k_axis_tma(Args a) {
   }
 }
 
-template <int L, int W>
+template <int L, int W, bool FULL = true>
 __global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
 k_chk_tma(Args a) {
   FFCZ_TMA_PROLOGUE(L, W)
@@ -1173,7 +1176,8 @@ k_chk_tma(Args a) {
     }
     TL tl{s_tiles + w, false};
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
-    chk_core<float, L, TL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red, &acc_vb, &acc_cnt,
+    chk_core<float, L, TL, false, PV_POCS, FULL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
+                                                 &acc_vb, &acc_cnt,
                            a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
