@@ -140,6 +140,8 @@ struct ffcz_plan_s {
   ffcz_opts opts{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+  cudaStream_t copy_stream = nullptr;  // host-buffer entry point: copy-back stream
+  cudaEvent_t ev_copy = nullptr;
   int device = 0;
 
   std::vector<DevGroup> groups;
@@ -1478,6 +1480,8 @@ void free_plan(ffcz_plan_s* p) {
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->ev2) cudaEventDestroy(p->ev2);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->ev_copy) cudaEventDestroy(p->ev_copy);
   delete p;
 }
 
@@ -1517,8 +1521,12 @@ void pw_prepare(ffcz_plan_s* p) {
   if (bad) fail(FFCZ_ERR_INVALID, "pointwise bounds must be finite and > 0");
 }
 
+// host_out (host-buffer entry point): the corrected field is copied back on a
+// second stream as soon as the loop is done, overlapping the certification,
+// which only reads e; a repair round waits for that copy and the field is
+// copied again at the end.
 ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const double* eps_f,
-                         ffcz_stats* stats) {
+                         ffcz_stats* stats, float* host_out = nullptr) {
   if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
   ProfOn prof_on(p);
   CK(cudaSetDevice(p->device));
@@ -1538,6 +1546,18 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
   if (cert) {
     cert_reset(p);
     certify(p, e, false);
+  }
+  bool recopy = false;
+  if (host_out) {
+    if (!p->copy_stream) {
+      CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&p->ev_copy, cudaEventDisableTiming));
+    }
+    CK(cudaStreamWaitEvent(p->copy_stream, p->ev1, 0));
+    CK(cudaMemcpyAsync(host_out, e, sizeof(float) * p->total, cudaMemcpyDeviceToHost, p->copy_stream));
+    CK(cudaEventRecord(p->ev_copy, p->copy_stream));
+  }
+  if (cert) {
     for (int round = 1; round <= p->opts.max_repairs; ++round) {
       CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(ItemState) * p->batch, cudaMemcpyDeviceToHost,
                          p->stream));
@@ -1547,6 +1567,10 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
         if (!p->h_st[i].certified && p->h_st[i].status != FFCZ_ERR_NONFINITE) all = false;
       if (all) break;
       // FP64 repair: Alg. 1 in FP64 from the current e, then re-certify.
+      if (host_out) {   // the early copy must finish reading e first
+        CK(cudaStreamWaitEvent(p->stream, p->ev_copy, 0));
+        recopy = true;
+      }
       upload_params(p, eps_s, eps_f, 0, p->opts.max_iters);
       k_set_repairs<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st,
                                                                              (int)p->batch, round);
@@ -1558,6 +1582,11 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
   }
   CK(cudaEventRecord(p->ev2, p->stream));
   CK(cudaEventSynchronize(p->ev2));
+  if (host_out) {
+    if (recopy)
+      CK(cudaMemcpyAsync(host_out, e, sizeof(float) * p->total, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(recopy ? p->stream : p->copy_stream));
+  }
   float ms = 0.f, ms_c = 0.f;
   CK(cudaEventElapsedTime(&ms, p->ev0, p->ev2));
   CK(cudaEventElapsedTime(&ms_c, p->ev1, p->ev2));
@@ -2394,11 +2423,7 @@ ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps
     if (!plan->staging) plan->staging = (float*)dalloc(plan, sizeof(float) * plan->total);
     CK(cudaMemcpyAsync(plan->staging, e_host, sizeof(float) * plan->total, cudaMemcpyHostToDevice,
                        plan->stream));
-    ffcz_status s = correct_impl(plan, plan->staging, eps_s, eps_f, stats);
-    CK(cudaMemcpyAsync(e_host, plan->staging, sizeof(float) * plan->total, cudaMemcpyDeviceToHost,
-                       plan->stream));
-    CK(cudaStreamSynchronize(plan->stream));
-    return s;
+    return correct_impl(plan, plan->staging, eps_s, eps_f, stats, e_host);
   });
 }
 
