@@ -1,0 +1,80 @@
+"""Edge cases of the GPU path against the FP64 oracle: the smallest and
+largest supported extents (every pass at its shortest and longest pencil),
+1D lengths at both ends of the Bluestein range, shapes the library must
+refuse, and degenerate bounds."""
+import numpy as np
+import pytest
+
+from oracle import ffcz_oracle as O
+from paper_2601_01596_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+def run(e0, E, D, **opts):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    plan = ffcz.Plan([e0.shape], **opts)
+    t = torch.from_numpy(np.ascontiguousarray(e0, dtype=np.float32).reshape(-1)).cuda()
+    st = plan.correct(t, [E], [D])
+    return t.cpu().numpy().reshape(e0.shape), st[0]
+
+
+def stress(shape, seed, frac=0.5):
+    e0 = W.bimodal_error(shape, seed, E=1.0, dtype=np.float32)
+    return e0, 1.0, frac * O.f_violation(O.dft(e0.astype(np.float64)))
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 16), (8, 16), (1024, 8, 16), (8, 1024, 16),
+                                   (8, 8, 2048), (1024, 2048), (8, 1024, 2048)])
+def test_extreme_extents_match_oracle(shape):
+    """Shortest (8; 16 on x) and longest (1024; 2048 on x) pencils of every pass."""
+    e0, E, D = stress(shape, 11)
+    ref = O.correct(e0, E, D)
+    e, st = run(e0, E, D)
+    assert ref.iters >= 1 and abs(st["iters"] - ref.iters) <= 2
+    assert st["status"] == 0 and st["certified"] == 1
+    same = O.correct(e0, E, D, min_iters=st["iters"], max_iters=st["iters"])
+    np.testing.assert_allclose(e, same.e, rtol=0, atol=TOL * E)
+
+
+@pytest.mark.parametrize("n", [32, 33, 524287, 524288])
+def test_1d_length_range_ends(n):
+    e0, E, D = stress((n,), 5)
+    ref = O.correct(e0, E, D)
+    e, st = run(e0, E, D)
+    assert abs(st["iters"] - ref.iters) <= 2 and st["certified"] == 1
+    same = O.correct(e0, E, D, min_iters=st["iters"], max_iters=st["iters"])
+    np.testing.assert_allclose(e, same.e, rtol=0, atol=TOL * E)
+
+
+@pytest.mark.parametrize("shapes", [[(8, 8, 24)], [(4, 8, 16)], [(8, 8, 8)], [(2048, 8, 16)],
+                                    [(8, 8, 4096)], [(31,)], [(524289,)], [(8, 12)],
+                                    [(16, 16), (16, 16, 16)]])
+def test_unsupported_shapes_are_refused(shapes):
+    import paper_2601_01596_b300 as ffcz
+    with pytest.raises((ffcz.FFCzError, ValueError)):
+        ffcz.Plan(shapes)
+
+
+def test_degenerate_bounds():
+    shape = (16, 32, 32)
+    e0, E, _ = stress(shape, 2)
+    # the f-bound above every coefficient: zero iterations, e returned as given
+    big = 2.0 * O.f_violation(O.dft(e0.astype(np.float64)))
+    e, st = run(e0, E, big)
+    assert st["iters"] == 0 and st["certified"] == 1 and np.array_equal(e, e0)
+    # a tiny f-bound drives the field to (almost) zero; the result is certified
+    tiny = 1e-4 * O.f_violation(O.dft(e0.astype(np.float64)))
+    ref = O.correct(e0, E, tiny)
+    e, st = run(e0, E, tiny)
+    assert st["status"] == 0 and st["certified"] == 1 and abs(st["iters"] - ref.iters) <= 2
+    # |e_n| <= (1/N) sum_k |delta_k| <= sqrt(2) Delta once every bin is in the box
+    assert float(np.max(np.abs(e))) <= np.sqrt(2.0) * tiny
+    # a field far outside the s-cube: pre-clip (A3), then the loop
+    wide = (e0 * 3.0).astype(np.float32)
+    ref = O.correct(wide, E, big)
+    e, st = run(wide, E, big)
+    assert ref.preclipped and st["preclipped"] == 1 and st["certified"] == 1
+    np.testing.assert_allclose(e, ref.e, rtol=0, atol=TOL * E)
