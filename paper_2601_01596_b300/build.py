@@ -35,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     extra = os.environ.get("FFCZ_NVCC_EXTRA", "").split()   # e.g. -DFFCZ_W32=4
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-split-compile=0", "-shared", "-Xcompiler", "-fPIC",
            "-cudart", "static", "-I", os.path.join(ROOT, "include"), *extra, *SRC, "-o", LIB + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

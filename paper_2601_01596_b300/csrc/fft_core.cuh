@@ -52,6 +52,29 @@ template <typename T>
 __device__ __forceinline__ v2<T> add(v2<T> a, v2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T>
 __device__ __forceinline__ v2<T> sub(v2<T> a, v2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// float32 complex add/sub as one packed two-lane operation (the f32x2 ops
+// of sm_100 and later: one instruction for both components, the same
+// round-to-nearest results as two scalar operations; a - b is computed as
+// b * (-1) + a, exact up to the single rounding of the sum).  Products that
+// mix the two components of a value (twiddles, multiplication by i) stay
+// scalar: the lane swaps they would need cost more than they save.
+template <>
+__device__ __forceinline__ float2 add<float>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <>
+__device__ __forceinline__ float2 sub<float>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// a + DIR i t and a - DIR i t (the odd outputs of a radix-4 butterfly)
+template <typename T, int DIR>
+__device__ __forceinline__ v2<T> add_mul_i(v2<T> a, v2<T> t) {
+  if constexpr (DIR < 0) return mk<T>(a.x + t.y, a.y - t.x);
+  else return mk<T>(a.x - t.y, a.y + t.x);
+}
+template <typename T, int DIR>
+__device__ __forceinline__ v2<T> sub_mul_i(v2<T> a, v2<T> t) {
+  if constexpr (DIR < 0) return mk<T>(a.x - t.y, a.y + t.x);
+  else return mk<T>(a.x + t.y, a.y - t.x);
+}
 template <typename T>
 __device__ __forceinline__ v2<T> cmul(v2<T> a, v2<T> b) {
   return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -126,9 +149,9 @@ __device__ __forceinline__ v2<T> mul_w32(v2<T> a, int m) {
 template <typename T, int DIR>
 __device__ __forceinline__ void dft4(v2<T>& a0, v2<T>& a1, v2<T>& a2, v2<T>& a3) {
   v2<T> s02 = add<T>(a0, a2), d02 = sub<T>(a0, a2);
-  v2<T> s13 = add<T>(a1, a3), d13 = mul_i<T, DIR>(sub<T>(a1, a3));
+  v2<T> s13 = add<T>(a1, a3), t13 = sub<T>(a1, a3);
   a0 = add<T>(s02, s13); a2 = sub<T>(s02, s13);
-  a1 = add<T>(d02, d13); a3 = sub<T>(d02, d13);
+  a1 = add_mul_i<T, DIR>(d02, t13); a3 = sub_mul_i<T, DIR>(d02, t13);
 }
 template <typename T, int DIR>
 __device__ __forceinline__ void dft8(v2<T> (&a)[8]) {
@@ -136,12 +159,11 @@ __device__ __forceinline__ void dft8(v2<T> (&a)[8]) {
   dft4<T, DIR>(a[0], a[2], a[4], a[6]);
   dft4<T, DIR>(a[1], a[3], a[5], a[7]);
   v2<T> o1 = mul_w8_1<T, DIR>(a[3]);
-  v2<T> o2 = mul_i<T, DIR>(a[5]);
   v2<T> o3 = mul_w8_3<T, DIR>(a[7]);
-  v2<T> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1];
+  v2<T> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1], t2 = a[5];
   a[0] = add<T>(e0, o0); a[4] = sub<T>(e0, o0);
   a[1] = add<T>(e1, o1); a[5] = sub<T>(e1, o1);
-  a[2] = add<T>(e2, o2); a[6] = sub<T>(e2, o2);
+  a[2] = add_mul_i<T, DIR>(e2, t2); a[6] = sub_mul_i<T, DIR>(e2, t2);
   a[3] = add<T>(e3, o3); a[7] = sub<T>(e3, o3);
 }
 
