@@ -302,7 +302,9 @@ void prof_collect(ffcz_plan_s* p) {
 // Strided float32 kernels exist with 4- and 8-pencil tiles, contiguous ones
 // (rows along x, 1D rows) with tiles of one or two warps; the tuner picks per
 // plan.  float64 kernels use 4-pencil strided tiles and one-warp rows.
-enum XKind { XFWD = 0, XPX = 1, XEXIT = 2 };
+// XCERT: the FP64 certification's x pass, which returns 2 X (exact; the
+// certification halves its maximum) to save the multiplications by 1/2.
+enum XKind { XFWD = 0, XPX = 1, XEXIT = 2, XCERT = 3 };
 
 #define FFCZ_DISPATCH_L(Lv, FN, ...)                                     \
   switch (Lv) {                                                           \
@@ -333,12 +335,16 @@ void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_
   const size_t sm = Smem<T, M, W>::bytes_x;
   if (g_dry) {
     set_smem(k_xfwd<T, M, W, PW>, sm);
+    if constexpr (sizeof(T) == 8) set_smem(k_xfwd<T, M, W, PW, true>, sm);
     set_smem(k_px<T, M, W, PW, PV>, sm);
     set_smem(k_xexit<T, M, W, PW, PV>, sm);
     return;
   }
-  ProfScope ps(kind == XFWD ? "xfwd" : kind == XPX ? "px" : "xexit", 8 * (int)sizeof(T), M, s);
+  ProfScope ps(kind == XFWD || kind == XCERT ? "xfwd" : kind == XPX ? "px" : "xexit", 8 * (int)sizeof(T), M, s);
   switch (kind) {
+    case XCERT:
+      if constexpr (sizeof(T) == 8) { k_xfwd<T, M, W, PW, true><<<grid, G_::NTHR, sm, s>>>(a); break; }
+      [[fallthrough]];
     case XFWD: k_xfwd<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
     case XPX: k_px<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
     case XEXIT: k_xexit<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
@@ -390,7 +396,7 @@ struct XL {
     }
     if constexpr (sizeof(T) == 4) {
       // projection variants: the x passes that carry q / u (one tile width)
-      if (a.pv == PV_DYKSTRA && kind != XFWD) {
+      if (a.pv == PV_DYKSTRA && (kind == XPX || kind == XEXIT)) {
         launch_x_tw<T, M, row_w1(M), false, PV_DYKSTRA>(kind, a, rows, count, s);
         return;
       }
@@ -1361,7 +1367,7 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
     tabs_x<double>(p, a, dg);
     a.e = const_cast<float*>(e);
     a.mode = M_MEASURE;
-    launch_x<double>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+    launch_x<double>(XCERT, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
     if (dg.ndim == 3) {
       a.tw = tw_of<double>(p->tb, dg.Ny);
       a.mode = 0;
@@ -1371,8 +1377,9 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
     a.mode = M_NOWRITE;
     launch_chk<double>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
   }
+  // 2D/3D certification transforms return 2 delta (XCERT)
   k_certify<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(
-      p->d_prm, p->d_st, (int)p->batch, repair_round ? 1 : 0);
+      p->d_prm, p->d_st, (int)p->batch, repair_round ? 1 : 0, p->ndim == 1 ? 1.0 : 0.5);
   g_launches++;
 }
 

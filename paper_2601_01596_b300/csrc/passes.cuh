@@ -335,11 +335,33 @@ __device__ __forceinline__ void load_tables(v2<T>* s_tw, const void* tw, int ntw
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
+// Exact binary32 -> binary64 widening by the IEEE 754 formats on the integer
+// pipe (sign kept, exponent rebiased by 1023 - 127 = 896, the 23 fraction
+// bits moved to the top of the 52), so that FP64 passes bound by the FP64
+// pipe do not spend it on conversions.  Zero takes the same path; subnormal
+// inputs, Inf and NaN (exponent field 0 with a nonzero fraction, or 255) use
+// the hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ex = (b >> 23) & 0xffu, fr = b & 0x7fffffu, sg = b & 0x80000000u;
+  if ((ex == 0u && fr != 0u) || ex == 0xffu) return (double)f;
+  const uint32_t hi = (ex == 0u) ? sg : (sg | ((ex + 896u) << 20) | (fr >> 3));
+  const uint32_t lo = (ex == 0u) ? 0u : (fr << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+template <typename T>
+__device__ __forceinline__ T from_f32(float f) {
+  if constexpr (sizeof(T) == 8) return widen_f32(f);
+  else return f;
+}
+
 // Post-processing of Z = FFT_M(z) into the packed half spectrum P (in place
 // in registers).  Each k needs Z[M-k], which another thread holds; it is
 // read through one exchange in natural order (a warp barrier only, when the
 // tile lies inside one warp).
-template <typename T, int M, class TL>
+// HALF = false leaves out the 1/2 of Fe and Fo: the result is 2 X, exact
+// (a power of two), for the certification, which halves its maximum once.
+template <typename T, int M, class TL, bool HALF = true>
 __device__ __forceinline__ void r2c_post(v2<T> (&v)[F2<M>::V], int j, TL& tl,
                                          const v2<T>* __restrict__ twr) {
   constexpr int NT = F2<M>::NT, V = F2<M>::V;
@@ -350,14 +372,15 @@ __device__ __forceinline__ void r2c_post(v2<T> (&v)[F2<M>::V], int j, TL& tl,
     const v2<T> zk = v[u];
     const v2<T> zm = tl.at((M - k) & (M - 1));
     if (k == 0) {
-      v[u] = mk<T>(zk.x + zk.y, zk.x - zk.y);
+      v[u] = HALF ? mk<T>(zk.x + zk.y, zk.x - zk.y) : mk<T>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
     } else {
       // Fe = (Zk + conj Zm)/2, Fo = (Zk - conj Zm)/(2i), X = Fe + W^k Fo;
       // with A = Zk + conj Zm, B = Zk - conj Zm:
       // X = ((A.x + W.x B.y + W.y B.x) / 2, (A.y - W.x B.x + W.y B.y) / 2)
       const v2<T> w = twr[k];
       const T ax = zk.x + zm.x, ay = zk.y - zm.y, bx = zk.x - zm.x, by = zk.y + zm.y;
-      v[u] = mk<T>(T(0.5) * fmaT(w.x, by, fmaT(w.y, bx, ax)), T(0.5) * fmaT(-w.x, bx, fmaT(w.y, by, ay)));
+      const T rx = fmaT(w.x, by, fmaT(w.y, bx, ax)), ry = fmaT(-w.x, bx, fmaT(w.y, by, ay));
+      v[u] = HALF ? mk<T>(T(0.5) * rx, T(0.5) * ry) : mk<T>(rx, ry);
     }
   }
   tl.done();
@@ -415,7 +438,8 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
 
 // Entry / certification x pass: float32 real rows -> packed spectrum.
 // PW: pointwise E_n (the measured maximum is max |e_n| / E_n).
-template <typename T, int M, int W = TileW<T>::value, bool PW = false>
+// X2 (certification): the output is 2 X (see r2c_post).
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, bool X2 = false>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
 k_xfwd(Args a) {
   FFCZ_X_PROLOGUE(T, M, W)
@@ -457,11 +481,11 @@ k_xfwd(Args a) {
       if (!(b2 & 1u)) x.x = 0.f;
       if (!(b2 & 2u)) x.y = 0.f;
     }
-    v[u] = mk<T>((T)x.x, (T)x.y);
+    v[u] = mk<T>(from_f32<T>(x.x), from_f32<T>(x.y));
   }
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   fft_pencil<T, M, -1>(v, j, s_tw, tl);
-  r2c_post<T, M>(v, j, tl, s_twr);
+  r2c_post<T, M, TL, !X2>(v, j, tl, s_twr);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
@@ -1425,20 +1449,31 @@ static __global__ void k_mark_preclip(const ItemParams* prm, ItemState* st, int 
 // ||y||_2 = sqrt(N sum e^2) (Parseval), u = 2^-53, c = 10 (>= the per-level
 // constant of radix-2 butterflies with rounded twiddles, radix 4/8 being
 // compositions of them).
-static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, int repair_round) {
+// vscale: the factor that undoes an exact power-of-two scaling of the
+// certification transform (0.5 when its x pass returned 2 X).
+static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, int repair_round,
+                                 double vscale = 1.0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ItemState& s = st[i];
   const ItemParams& p = prm[i];
   if (repair_round && s.certified) return;
   const double emax = __longlong_as_double((long long)s.emaxbits);
-  const double v = __longlong_as_double((long long)s.vbits);
+  const double v = vscale * __longlong_as_double((long long)s.vbits);
   const double ln = log2((double)p.n);
-  double b = 10.0 * (ln + 2.0) * 1.1102230246251565e-16 * sqrt((double)p.n * s.sumsq);
+  // ||e||_2 from above, two ways: the float32 partial sums of squares (each
+  // inflated for its rounding) plus at most 2^-126 per point for squares
+  // that fell below the float32 normal range, and sqrt(N) max|e| (exact);
+  // the first overflows for |e| beyond about 2^63, the second is looser
+  // when a few points dominate, so the smaller one is used
+  const double ssq = s.sumsq + (double)p.n * 0x1p-126;
+  const double nrm_max = sqrt((double)p.n) * emax;
+  const double nrm = (ssq <= DBL_MAX) ? fmin(sqrt(ssq), nrm_max) : nrm_max;
+  double b = 10.0 * (ln + 2.0) * 1.1102230246251565e-16 * sqrt((double)p.n) * nrm;
   if (p.logP > 0) {
     // Bluestein: FFT_P, product with Bt (|Bt_k| <= 2N), IFFT_P and two chirp
     // products; |err_k| <= ||err||_2 <= c (2 log2 P + 6) u 2N ||x||_2
-    b = 10.0 * (2.0 * p.logP + 6.0) * 1.1102230246251565e-16 * 2.0 * (double)p.n * sqrt(s.sumsq);
+    b = 10.0 * (2.0 * p.logP + 6.0) * 1.1102230246251565e-16 * 2.0 * (double)p.n * nrm;
   }
   s.v64 = v;
   s.emax64 = emax;

@@ -78,3 +78,28 @@ def test_degenerate_bounds():
     e, st = run(wide, E, big)
     assert ref.preclipped and st["preclipped"] == 1 and st["certified"] == 1
     np.testing.assert_allclose(e, ref.e, rtol=0, atol=TOL * E)
+
+
+def test_certification_of_special_float_values():
+    """The FP64 certification widens float32 on the integer pipe (subnormals,
+    signed zeros and the largest exponents included): its violation must
+    bracket the exact one computed from numpy's float64 upcast."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shape = (16, 32, 64)
+    r = np.random.default_rng(4)
+    e0 = W.bimodal_error(shape, 9, dtype=np.float32)
+    flat = e0.reshape(-1)
+    idx = r.choice(flat.size, 400, replace=False)
+    flat[idx[:100]] = np.float32(0.0)
+    flat[idx[100:200]] = np.float32(-0.0)
+    flat[idx[200:300]] = (r.uniform(-1, 1, 100) * 1e-40).astype(np.float32)   # subnormal
+    flat[idx[300:]] = (r.uniform(-1, 1, 100) * 1e-30).astype(np.float32)
+    for scale in (1.0, 2.0 ** 100, 2.0 ** -100):
+        x = (e0 * np.float32(scale)).astype(np.float32)
+        v = O.f_violation(O.dft(x.astype(np.float64)))
+        s = float(np.max(np.abs(x.astype(np.float64))))
+        plan = ffcz.Plan([shape])
+        t = torch.from_numpy(x.reshape(-1).copy()).cuda()
+        assert plan.check(t, [s], [v * (1 + 1e-8)])[0]["certified"] == 1, scale
+        assert plan.check(t, [s], [v * (1 - 1e-8)])[0]["certified"] == 0, scale
