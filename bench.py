@@ -45,13 +45,14 @@ FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # at 512^3 (profiles/); an entry is removed when its kernel changes.
 NCU_TRAFFIC = {
-    "chk<f32,512>": 566073344 + 506883584,        # k_chk_tma<512, 8>
-    "axis_fwd<f32,512>": 536967424 + 483203328,   # k_axis_tma<512, -1, 8>
-    "px<f32,256>": 536958976 + 479542016,         # k_px_tma<256, 2>
-    "axis_fwd<f64,512>": 1073873000 + 1018597000,  # k_axis<double, 512, -1, 4>
-    "chk_cert<f64,512>": 1105932000 + 3677696,     # k_chk<double, 512, 4> (check only)
+    "chk<f32,512>": 563948544 + 502807296,        # k_chk_tma<512, 8, lean>
+    "axis_fwd<f32,512>": 536954880 + 483795200,   # k_axis_tma<512, -1, 8>
+    "px<f32,256>": 537590016 + 477834240,         # k_px_tma<256, 2>
+    "xfwd<f64,256>": 537014784 + 1015413000,      # k_xfwd<double, 256, 2, X2>
+    "axis_fwd<f64,512>": 1075036000 + 1019320000,  # k_axis<double, 512, -1, 4>
+    "chk_cert<f64,512>": 1105017000 + 3545600,     # k_chk<double, 512, 4> (check only)
 }
-NCU_FP64_PIPE = {"axis_fwd<f64,512>": 0.847, "chk_cert<f64,512>": 0.841}
+NCU_FP64_PIPE = {"xfwd<f64,256>": 0.859, "axis_fwd<f64,512>": 0.846, "chk_cert<f64,512>": 0.841}
 
 
 def load_peaks():
