@@ -49,3 +49,20 @@ def test_invalid_arguments_fail_before_any_device_work():
     assert b"power" in L.ffcz_last_error()
     assert L.ffcz_correct(None, None, None, None, None) == ffcz.ERR_INVALID
     L.ffcz_destroy(None)
+
+
+def test_projection_variant_options_are_checked_on_the_host():
+    L = ffcz.lib()
+    h = ctypes.c_void_p()
+    sh3 = (ctypes.c_int64 * 3)(32, 32, 32)
+    sh1 = (ctypes.c_int64 * 1)(4096)
+    assert ffcz.default_opts().method == 0
+    assert ffcz.default_opts(method="dykstra").method == 1
+    assert ffcz.default_opts(method="dr").method == 2 and ffcz.default_opts(method="admm").method == 3
+    o = ffcz.default_opts(method=4)
+    assert L.ffcz_plan(ctypes.byref(h), 3, sh3, 1, ctypes.byref(o), None) == ffcz.ERR_INVALID
+    for kw in ({"method": 1, "edits": 1}, {"method": 2, "pointwise": 1}, {"method": 3, "precision": 64}):
+        o = ffcz.default_opts(**kw)
+        assert L.ffcz_plan(ctypes.byref(h), 3, sh3, 1, ctypes.byref(o), None) == ffcz.ERR_UNSUPPORTED, kw
+    o = ffcz.default_opts(method=1)
+    assert L.ffcz_plan(ctypes.byref(h), 1, sh1, 1, ctypes.byref(o), None) == ffcz.ERR_UNSUPPORTED
