@@ -366,6 +366,43 @@ __device__ __forceinline__ void r2c_post(v2<T> (&v)[F2<M>::V], int j, TL& tl,
                                          const v2<T>* __restrict__ twr) {
   constexpr int NT = F2<M>::NT, V = F2<M>::V;
   store_nat<T, M, TL>(v, j, tl);
+  if constexpr (!HALF) {
+    // Paired form (certification): X(k) and X(M-k) share A, B and the
+    // product Q = (W.x B.y + W.y B.x, W.y B.y - W.x B.x):
+    // X(k) = A + Q, X(M-k) = conj(A - Q) (since W^(M-k) = -conj W^k), so the
+    // threads holding k < M/2 compute both and hand X(M-k) over through the
+    // tile buffer: 12 instead of 16 operations per pair.
+    v2<T> xo[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int k = j + u * NT;
+      const v2<T> zk = v[u];
+      if (k == 0) {
+        v[u] = mk<T>(T(2) * (zk.x + zk.y), T(2) * (zk.x - zk.y));
+      } else if (2 * k <= M) {
+        const v2<T> zm = tl.at(M - k);
+        const v2<T> w = twr[k];
+        const T ax = zk.x + zm.x, ay = zk.y - zm.y, bx = zk.x - zm.x, by = zk.y + zm.y;
+        const T qx = fmaT(w.x, by, w.y * bx), qy = fmaT(-w.x, bx, w.y * by);
+        v[u] = mk<T>(ax + qx, ay + qy);
+        xo[u] = mk<T>(ax - qx, qy - ay);
+      }
+    }
+    TL::sync();   // every read of Z is done
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int k = j + u * NT;
+      if (k > 0 && 2 * k < M) tl.at(M - k) = xo[u];
+    }
+    TL::sync();
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int k = j + u * NT;
+      if (2 * k > M) v[u] = tl.at(k);
+    }
+    tl.done();
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     const int k = j + u * NT;
