@@ -386,6 +386,28 @@ void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
   }
 }
 
+// Persistent bulk-copy-fed entry x pass (float32, one-warp tiles), sized
+// like the loop's x pass.
+template <int M>
+void launch_xfwd_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
+  constexpr int W = row_w1(M);
+  using PG = PxTmaGeo<M, W>;
+  const size_t sm = PG::bytes;
+  if (g_dry) { set_smem(k_xfwd_tma<M, W>, sm); return; }
+  static int per_sm = 0;   // resident CTAs per SM (same for every plan)
+  if (per_sm == 0) {
+    int n = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_xfwd_tma<M, W>, Geo<float, M, W>::NTHR, sm));
+    per_sm = n > 0 ? n : 1;
+  }
+  const int64_t nblk = (rows + PG::RG - 1) / PG::RG;
+  const int64_t want = ((int64_t)per_sm * g_num_sms_x + count - 1) / count;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, want));
+  ProfScope ps("xfwd", 32, M, s);
+  k_xfwd_tma<M, W><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
+  g_launches++;
+}
+
 template <typename T>
 struct XL {
   template <int M>
@@ -408,6 +430,11 @@ struct XL {
     if constexpr (sizeof(T) == 4) {
       if (w < 0 && (kind == XPX || g_dry)) {
         launch_px_tma<M>(a, rows, count, s);
+        if (!g_dry) return;
+      }
+      // the entry pass follows the loop's x-pass choice (plain modes only)
+      if (w < 0 && ((kind == XFWD && !(a.mode & (M_PRECLIP | M_MASK))) || g_dry)) {
+        launch_xfwd_tma<M>(a, rows, count, s);
         if (!g_dry) return;
       }
       if (w == row_w2(M)) launch_x_tw<T, M, row_w2(M)>(kind, a, rows, count, s);

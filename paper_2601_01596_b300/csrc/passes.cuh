@@ -1423,6 +1423,110 @@ static __global__ void k_pw_scale(ItemParams* prm, const unsigned int* minbits, 
 
 // Loop decision after a check (Alg. 1: break when CheckConvergence passes;
 // readings: stop at v <= D(1 - eta/2) once t >= min_iters, cap at max_iters).
+// Persistent float32 entry x pass (e rows -> packed spectrum, with the
+// max |e|, sum e^2 and NaN measurement) fed by bulk copies of blocks of rows,
+// the same way as k_px_tma (no pre-clip, mask or pointwise bounds: those use
+// k_xfwd).  Each thread sums its squares per block in float32 (at most 2V
+// terms, inflated as in k_xfwd) and the blocks in double.
+template <int M, int W>
+__global__ void __launch_bounds__(Geo<float, M, W>::NTHR, Geo<float, M, W>::MINB)
+k_xfwd_tma(Args a) {
+  using G_ = Geo<float, M, W>;
+  using TL = Tile<float, M, W>;
+  using PG = PxTmaGeo<M, W>;
+  constexpr int V = G_::V, NT = G_::NT, RG = PG::RG;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const uint32_t s0 = smem_addr(smraw);   // staging rounded up to 128 bytes
+  float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0 + 127u) & ~127u) - s0));
+  float2* s_tiles = s_stage + RG * M;
+  float2* s_tw = s_tiles + G_::G * TL::ELEMS;
+  float2* s_twr = s_tw + M;
+  unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M);
+  __shared__ __align__(8) uint64_t bar;
+  const int gi = blockIdx.y;
+  const int item = a.g.item[gi];
+  const ItemParams& p = a.prm[item];
+  ItemState& st = a.st[item];
+  if (!pred_ok(a.pred, st, p)) return;
+  const int t_it = st.t;
+  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
+  const int w = tid % W, j = tid / W;
+  const int64_t rows = a.g.rows;
+  const int64_t nblk = (rows + RG - 1) / RG;
+  const float2* inb = reinterpret_cast<const float2*>(a.e + a.g.eoff[gi]);
+  float2* outb = pick<float>(a, a.sel_out, t_it) + a.g.soff[gi];
+  if ((smem_addr(s_stage) & 127u) != 0u || (reinterpret_cast<uintptr_t>(inb) & 15u) != 0u) {
+    if (threadIdx.x == 0) atomicExch(a.err, DERR_TMA_ALIGN);
+    return;
+  }
+  load_tables<float>(s_tw, a.tw, M, s_twr, a.twr, M);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t parity = 0;
+  auto issue = [&](int64_t blk) {
+    const int64_t r0 = blk * RG;
+    const int64_t nr = rows - r0 < RG ? rows - r0 : RG;
+    const uint32_t bytes = (uint32_t)(nr * M * sizeof(float2));
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_load(s_stage, inb + r0 * M, bytes, &bar);
+  };
+  int64_t blk = blockIdx.x;
+  if (threadIdx.x == 0 && blk < nblk) issue(blk);
+  const bool measure = (a.mode & M_MEASURE) != 0;
+  AbsMax<float> mx;
+  bool bad = false;
+  double ssq_d = 0.0;
+  while (blk < nblk) {
+    const int64_t next = blk + gridDim.x;
+    const bool ok = mbar_wait_bounded(&bar, parity, kTmaPollLimit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);
+      mbar_wait_bounded(&bar, parity, kTmaPollLimit);   // copies still in flight
+      return;
+    }
+    const int tile = (int)(blk * G_::G + g);
+    const int64_t prow = (int64_t)tile * W + w;
+    const bool live = prow < rows;
+    const int64_t row = live ? prow : 0;
+    float2 v[V];
+    float ssq = 0.f;
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      v[u] = s_stage[(g * W + w) * M + j + u * NT];
+      if (measure && live) {
+        mx.add(v[u].x); mx.add(v[u].y);
+        bad |= (v[u].x != v[u].x) | (v[u].y != v[u].y);
+        ssq = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, ssq));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && next < nblk) {
+      fence_proxy_async_smem();
+      issue(next);
+    }
+    parity ^= 1u;
+    ssq_d += (double)ssq * (1.0 + 0x1p-17);   // 2V float32 terms: relative error < (2V+1) u32
+    TL tl{s_tiles + g * TL::ELEMS + w, false};
+    fft_pencil<float, M, -1>(v, j, s_tw, tl);
+    r2c_post<float, M>(v, j, tl, s_twr);
+    if (live) {
+      float2* out = outb + row * M;
+#pragma unroll
+      for (int u = 0; u < V; ++u) out[j + u * NT] = v[u];
+    }
+    TL::sync();   // the warp's tile buffer is reused by the next block
+    blk = next;
+  }
+  if (measure) {
+    Red r{mx.dbits(bad), ssq_d, 0ull};
+    block_reduce(r, s_red);
+    if (threadIdx.x == 0) {
+      atomicMax(&st.emaxbits, r.vbits);
+      atomicAdd(&st.sumsq, r.sum);
+    }
+  }
+}
+
 // s_check: ADMM loops, whose candidate after iteration t >= 1 is a_t (inside
 // F' by construction) and whose stopping test is max|a_t| <= E(1 - eta/2).
 static __global__ void k_decide(const ItemParams* prm, ItemState* st, int n, int* n_active, int s_check = 0) {
