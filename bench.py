@@ -48,11 +48,12 @@ NCU_TRAFFIC = {
     "chk<f32,512>": 563948544 + 502807296,        # k_chk_tma<512, 8, lean>
     "axis_fwd<f32,512>": 536954880 + 483795200,   # k_axis_tma<512, -1, 8>
     "px<f32,256>": 537590016 + 477834240,         # k_px_tma<256, 2>
-    "xfwd<f64,256>": 537014784 + 1015413000,      # k_xfwd<double, 256, 2, X2>
+    "xfwd<f64,256>": 537062656 + 1016352000,      # k_xfwd<double, 256, 2, X2>
+    "xfwd<f32,256>": 536927488 + 489845760,       # k_xfwd_tma<256, 2> (entry)
     "axis_fwd<f64,512>": 1075036000 + 1019320000,  # k_axis<double, 512, -1, 4>
     "chk_cert<f64,512>": 1105017000 + 3545600,     # k_chk<double, 512, 4> (check only)
 }
-NCU_FP64_PIPE = {"xfwd<f64,256>": 0.859, "axis_fwd<f64,512>": 0.846, "chk_cert<f64,512>": 0.841}
+NCU_FP64_PIPE = {"xfwd<f64,256>": 0.847, "axis_fwd<f64,512>": 0.846, "chk_cert<f64,512>": 0.841}
 
 
 def load_peaks():
