@@ -327,6 +327,10 @@ constexpr int row_w2(int L) { return 2 * row_w1(L); }
 // g_pw_sel to reach them without bound pointers).
 thread_local bool g_pw_sel = false;
 
+// The x pass needs its full form for edit recording and the adjoint's mask,
+// record and checkpoint modes; every other launch takes the lean one.
+inline bool px_full(const Args& a) { return (a.mode & (M_RECORD | M_MASK | M_CKPT)) != 0 || a.ed_s != nullptr; }
+
 template <typename T, int M, int W, bool PW = false, int PV = PV_POCS>
 void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
   using G_ = Geo<T, M, W>;
@@ -336,7 +340,8 @@ void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_
   if (g_dry) {
     set_smem(k_xfwd<T, M, W, PW>, sm);
     if constexpr (sizeof(T) == 8) set_smem(k_xfwd<T, M, W, PW, true>, sm);
-    set_smem(k_px<T, M, W, PW, PV>, sm);
+    if constexpr (PV == PV_POCS) set_smem(k_px<T, M, W, PW, PV, true>, sm);
+    set_smem(k_px<T, M, W, PW, PV, false>, sm);
     set_smem(k_xexit<T, M, W, PW, PV>, sm);
     return;
   }
@@ -346,7 +351,13 @@ void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_
       if constexpr (sizeof(T) == 8) { k_xfwd<T, M, W, PW, true><<<grid, G_::NTHR, sm, s>>>(a); break; }
       [[fallthrough]];
     case XFWD: k_xfwd<T, M, W, PW><<<grid, G_::NTHR, sm, s>>>(a); break;
-    case XPX: k_px<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
+    case XPX:
+      // projection variants run lean only (no edits, no adjoint)
+      if constexpr (PV == PV_POCS) {
+        if (px_full(a)) { k_px<T, M, W, PW, PV, true><<<grid, G_::NTHR, sm, s>>>(a); break; }
+      }
+      k_px<T, M, W, PW, PV, false><<<grid, G_::NTHR, sm, s>>>(a);
+      break;
     case XEXIT: k_xexit<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
   }
   g_launches++;
@@ -379,7 +390,7 @@ void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
   if (g_dry) {
     launch_px_tma_ed<M, false>(a, rows, count, s);
     launch_px_tma_ed<M, true>(a, rows, count, s);
-  } else if (a.ed_s) {
+  } else if (px_full(a)) {
     launch_px_tma_ed<M, true>(a, rows, count, s);
   } else {
     launch_px_tma_ed<M, false>(a, rows, count, s);
@@ -523,9 +534,9 @@ void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_ntiles(W, M, Nmid);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L, W>::bytes_axis;
-  // pointwise plans keep the full form (edits may be on); projection
-  // variants only run lean (no edits, no adjoint)
-  constexpr bool lean_ok = !PW, only_lean = PV != PV_POCS;
+  // the full form when a mode needs it; projection variants only run lean
+  // (no edits, no adjoint)
+  constexpr bool lean_ok = true, only_lean = PV != PV_POCS;
   if (g_dry) {
     if constexpr (!only_lean) set_smem(k_chk<T, L, W, PW, PV, true>, sm);
     if constexpr (lean_ok) set_smem(k_chk<T, L, W, PW, PV, false>, sm);

@@ -310,6 +310,13 @@ __device__ __forceinline__ bool nan_probe(const v2<T> (&v)[V]) {
   return (v[0].x != v[0].x) | (v[V - 1].y != v[V - 1].y);
 }
 
+// x / b for the normalised violations of pointwise bounds (b > 0): float32
+// as x times the correctly rounded reciprocal (two roundings instead of an
+// IEEE division sequence per value; the ratio only decides when the float32
+// loop stops, the FP64 certification checks the bounds themselves).
+__device__ __forceinline__ float ratioT(float x, float b) { return x * __frcp_rn(b); }
+__device__ __forceinline__ double ratioT(double x, double b) { return x / b; }
+
 __device__ __forceinline__ float clampT(float x, float b) { return fminf(fmaxf(x, -b), b); }
 __device__ __forceinline__ double clampT(double x, double b) { return fmin(fmax(x, -b), b); }
 
@@ -498,7 +505,7 @@ k_xfwd(Args a) {
     float2 eb = make_float2(1.f, 1.f);
     if constexpr (PW) eb = ebrow[j + u * G_::NT];
     if (a.mode & M_MEASURE) {
-      if constexpr (PW) { mx.add(x.x / eb.x); mx.add(x.y / eb.y); }
+      if constexpr (PW) { mx.add(ratioT(x.x, eb.x)); mx.add(ratioT(x.y, eb.y)); }
       else { mx.add(x.x); mx.add(x.y); }
       bad |= (x.x != x.x) | (x.y != x.y);
       ssq = fmaf(x.x, x.x, fmaf(x.y, x.y, ssq));
@@ -562,6 +569,8 @@ __device__ __forceinline__ void s_clip_full(v2<T> (&v)[V], T Es, bool count, Mas
 
 // Loop body x pass on one tile held in registers: C2R, scale 1/N, s-clip
 // (or adjoint mask), R2C.  Returns the active-clip count of the thread.
+// ED = false is the lean form of the forward loop: the edit recording, the
+// adjoint mask modes and the checkpoints are compiled out.
 template <typename T, int M, class TL, bool PW = false, bool ED = true, int PV = PV_POCS>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
                                                       int j, int64_t mthr, int64_t row, bool live,
@@ -624,14 +633,14 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
   for (int u = 0; u < V; ++u) {
     v[u] = mk<T>(v[u].x * inv_n, v[u].y * inv_n);
     if constexpr (PW) {   // pointwise E_n: the vote runs on ratios
-      mx.add(v[u].x / (T)eb[u].x); mx.add(v[u].y / (T)eb[u].y);
+      mx.add(ratioT(v[u].x, (T)eb[u].x)); mx.add(ratioT(v[u].y, (T)eb[u].y));
     } else {
       mx.add(v[u].x); mx.add(v[u].y);
     }
   }
   const bool count = (a.mode & M_COUNT) != 0;
   const bool need_clip = __any_sync(0xffffffffu, mx.val() > Es);   // all lanes vote
-  if (a.mode & M_MASK) {
+  if (ED && (a.mode & M_MASK)) {
     MaskBits<MW> mb;
     mb.clear();
     if (live) mb.load(a.mask, mthr);
@@ -641,7 +650,7 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
       if (!(b2 & 1u)) v[u].x = T(0);
       if (!(b2 & 2u)) v[u].y = T(0);
     }
-  } else if (a.mode & (M_RECORD | M_CKPT)) {
+  } else if (ED && (a.mode & (M_RECORD | M_CKPT))) {
     const bool ckn = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 && live;
     float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * (2 * M * a.g.rows)) + row * M
                      : nullptr;
@@ -651,7 +660,7 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
     if ((a.mode & M_RECORD) && live) mb.store(a.mask, mthr);
   } else if (need_clip) {
     // lean path: only warps holding a value outside the s-cube clip
-    const bool rec_s = ED && edrow != nullptr && live;   // ED = false compiles the recording out
+    const bool rec_s = ED && edrow != nullptr && live;   // ED = false: the lean form
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       T bx = Es, by = Es;
@@ -667,7 +676,7 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
   return live ? cnt : 0ull;
 }
 
-template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS>
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR,
                                   (PW || PV != PV_POCS) ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
 k_px(Args a) {
@@ -686,7 +695,7 @@ k_px(Args a) {
     qout = reinterpret_cast<float2*>(a.pv_q[t_it & 1] + a.g.eoff[gi]) + row * M;
   }
   AbsMax<T> svm;
-  unsigned long long cnt = px_core<T, M, TL, PW, true, PV>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr,
+  unsigned long long cnt = px_core<T, M, TL, PW, FULL, PV>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr,
                                                            edrow, ebrow, qin, qout, &svm);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
@@ -964,7 +973,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
           bar = (T)qb[u].x; bai = (T)qb[u].y; bbr = (T)qB.x; bbi = (T)qB.y;
         }
         if (c.valid) {
-          if constexpr (PW) { mx.add(ar / bar); mx.add(ai / bai); mx.add(br / bbr); mx.add(bi / bbi); }
+          if constexpr (PW) { mx.add(ratioT(ar, bar)); mx.add(ratioT(ai, bai)); mx.add(ratioT(br, bbr)); mx.add(ratioT(bi, bbi)); }
           else { mx.add(ar); mx.add(ai); mx.add(br); mx.add(bi); }
         }
         bad |= c.valid && ((ar != ar) | (ai != ai) | (br != br) | (bi != bi));
@@ -982,8 +991,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
             T big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)), fabs(T(0.5) * (cc.y - m.y))),
                          fmax(fabs(T(0.5) * (cc.y + m.y)), fabs(T(0.5) * (m.x - cc.x))));
             if constexpr (PW)
-              big = fmax(fmax(fabs(T(0.5) * (cc.x + m.x)) / bar, fabs(T(0.5) * (cc.y - m.y)) / bai),
-                         fmax(fabs(T(0.5) * (cc.y + m.y)) / bbr, fabs(T(0.5) * (m.x - cc.x)) / bbi));
+              big = fmax(fmax(ratioT(fabs(T(0.5) * (cc.x + m.x)), bar), ratioT(fabs(T(0.5) * (cc.y - m.y)), bai)),
+                         fmax(ratioT(fabs(T(0.5) * (cc.y + m.y)), bbr), ratioT(fabs(T(0.5) * (m.x - cc.x)), bbi)));
             record_f(a, ed_slot0 + u * ed_ustride, (float)(nx - cc.x), (float)(ny - cc.y), t_chk,
                      may_stop && big <= thr);
           }
@@ -1005,7 +1014,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   AbsMax<T> tm;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
-    if constexpr (PW) { tm.add(v[u].x / (T)qb[u].x); tm.add(v[u].y / (T)qb[u].y); }
+    if constexpr (PW) { tm.add(ratioT(v[u].x, (T)qb[u].x)); tm.add(ratioT(v[u].y, (T)qb[u].y)); }
     else { tm.add(v[u].x); tm.add(v[u].y); }
   }
   const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
@@ -1043,7 +1052,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         if (FULL) mb.template put<2>(u, (uint32_t)ix | ((uint32_t)iy << 1));
         if (rec_f)
           record_f(a, ed_slot0 + u * ed_ustride, (float)(cx - x), (float)(cy - y), t_chk,
-                   may_stop && (PW ? fmax(fabs(x) / qx, fabs(y) / qy) : fmax(fabs(x), fabs(y))) <= thr);
+                   may_stop && (PW ? fmax(ratioT(fabs(x), qx), ratioT(fabs(y), qy)) : fmax(fabs(x), fabs(y))) <= thr);
         v[u] = mk<T>(cx, cy);
       }
     } else if (clip && FULL) {
@@ -1257,8 +1266,8 @@ k_chk_tma(Args a) {
   }
 }
 
-// Persistent float32 x pass (C2R, s-clip, R2C) fed by bulk copies (ED: with
-// the recording of spatial edits compiled in): a CTA
+// Persistent float32 x pass (C2R, s-clip, R2C) fed by bulk copies (ED: the
+// full form with edit recording and the adjoint modes, else lean): a CTA
 // holds G tiles of W rows each (one warp per tile); its G W consecutive rows
 // are one contiguous block of the packed spectrum, loaded by a single
 // cp.async.bulk while the previous block is transformed.  Shared memory:
