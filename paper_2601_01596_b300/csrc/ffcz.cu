@@ -366,23 +366,23 @@ int g_num_sms_x = 148;   // set from the device at plan creation
 
 // Persistent bulk-copy-fed loop x pass (float32, one-warp tiles): as many
 // CTAs as fit on the device, spread over the group's items.
-template <int M, bool ED>
+template <int M, bool ED, bool PW = false>
 void launch_px_tma_ed(const Args& a, int64_t rows, int count, cudaStream_t s) {
   constexpr int W = row_w1(M);
   using PG = PxTmaGeo<M, W>;
   const size_t sm = PG::bytes;
-  if (g_dry) { set_smem(k_px_tma<M, W, ED>, sm); return; }
+  if (g_dry) { set_smem(k_px_tma<M, W, ED, PW>, sm); return; }
   static int per_sm = 0;   // resident CTAs per SM (same for every plan)
   if (per_sm == 0) {
     int n = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W, ED>, Geo<float, M, W>::NTHR, sm));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W, ED, PW>, Geo<float, M, W>::NTHR, sm));
     per_sm = n > 0 ? n : 1;
   }
   const int64_t nblk = (rows + PG::RG - 1) / PG::RG;
   const int64_t want = ((int64_t)per_sm * g_num_sms_x + count - 1) / count;
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, want));
   ProfScope ps("px", 32, M, s);
-  k_px_tma<M, W, ED><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
+  k_px_tma<M, W, ED, PW><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
   g_launches++;
 }
 template <int M>
@@ -390,6 +390,11 @@ void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
   if (g_dry) {
     launch_px_tma_ed<M, false>(a, rows, count, s);
     launch_px_tma_ed<M, true>(a, rows, count, s);
+    launch_px_tma_ed<M, false, true>(a, rows, count, s);
+    launch_px_tma_ed<M, true, true>(a, rows, count, s);
+  } else if (a.pw_e) {   // pointwise E_n
+    if (px_full(a)) launch_px_tma_ed<M, true, true>(a, rows, count, s);
+    else launch_px_tma_ed<M, false, true>(a, rows, count, s);
   } else if (px_full(a)) {
     launch_px_tma_ed<M, true>(a, rows, count, s);
   } else {
@@ -424,6 +429,10 @@ struct XL {
   template <int M>
   static void go(XKind kind, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
     if (a.pw_e || g_pw_sel) {
+      if constexpr (sizeof(T) == 4) {
+        // the loop's x pass follows the plan's choice of the copy-engine-fed kernel
+        if (w < 0 && kind == XPX && !g_dry) { launch_px_tma<M>(a, rows, count, s); return; }
+      }
       launch_x_tw<T, M, row_w1(M), true>(kind, a, rows, count, s);
       return;
     }
@@ -499,11 +508,22 @@ template <int L>
 void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_ntiles(8, M, Nmid);
   const size_t sm = TmaGeo<L, 8>::bytes;
-  if (g_dry) { set_smem(k_chk_tma<L, 8, true>, sm); set_smem(k_chk_tma<L, 8, false>, sm); return; }
+  if (g_dry) {
+    set_smem(k_chk_tma<L, 8, true>, sm); set_smem(k_chk_tma<L, 8, false>, sm);
+    set_smem(k_chk_tma<L, 8, true, true>, sm); set_smem(k_chk_tma<L, 8, false, true>, sm);
+    return;
+  }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk", 32, L, s);
   const dim3 grid(tma_grid_x(tiles, count), (unsigned)count);
-  if (chk_full(a)) k_chk_tma<L, 8, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
-  else k_chk_tma<L, 8, false><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  const bool full = chk_full(a);
+  if (a.pw_f) {   // pointwise (Delta^Re, Delta^Im)
+    if (full) k_chk_tma<L, 8, true, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+    else k_chk_tma<L, 8, false, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  } else if (full) {
+    k_chk_tma<L, 8, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  } else {
+    k_chk_tma<L, 8, false><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  }
   g_launches++;
 }
 
@@ -561,6 +581,9 @@ struct CL {
   template <int L>
   static void go(int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
     if (a.pw_f || g_pw_sel) {
+      if constexpr (sizeof(T) == 4 && tma_ok<L>()) {
+        if (w < 0 && a.tm_chk && !g_dry) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
+      }
       launch_chk_tw<T, L, TileW<T>::value, true>(a, Nmid, M, count, s);
       return;
     }

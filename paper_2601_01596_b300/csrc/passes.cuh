@@ -1210,7 +1210,7 @@ k_axis_tma(Args a) {
   }
 }
 
-template <int L, int W, bool FULL = true>
+template <int L, int W, bool FULL = true, bool PW = false>
 __global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
 k_chk_tma(Args a) {
   FFCZ_TMA_PROLOGUE(L, W)
@@ -1246,9 +1246,10 @@ k_chk_tma(Args a) {
     }
     TL tl{s_tiles + w, false};
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
-    chk_core<float, L, TL, false, PV_POCS, FULL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
-                                                 &acc_vb, &acc_cnt,
-                           a.g.soff[gi] + c.off + j * estride, (int64_t)NT * estride, t_it);
+    const float2* pwb = PW ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
+    chk_core<float, L, TL, PW, PV_POCS, FULL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
+                                              &acc_vb, &acc_cnt, a.g.soff[gi] + c.off + j * estride,
+                                              (int64_t)NT * estride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
 #pragma unroll
@@ -1281,8 +1282,8 @@ struct PxTmaGeo {
                                   2 * (size_t)M * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
 };
 
-template <int M, int W, bool ED = false>
-__global__ void __launch_bounds__(Geo<float, M, W>::NTHR, Geo<float, M, W>::MINB)
+template <int M, int W, bool ED = false, bool PW = false>
+__global__ void __launch_bounds__(Geo<float, M, W>::NTHR, PW ? Geo<float, M, W>::MINB_PW : Geo<float, M, W>::MINB)
 k_px_tma(Args a) {
   using G_ = Geo<float, M, W>;
   using TL = Tile<float, M, W>;
@@ -1350,7 +1351,8 @@ k_px_tma(Args a) {
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
     TL tl{s_tiles + g * TL::ELEMS + w, false};
     float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
-    cnt += px_core<float, M, TL, false, ED>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow);
+    const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+    cnt += px_core<float, M, TL, PW, ED>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
     if (live) {
       float2* out = outb + row * M;
 #pragma unroll
