@@ -176,6 +176,9 @@ struct ffcz_plan_s {
   // pointwise bounds (opts.pointwise): copies of the caller's E_n and Delta_k
   float* pw_e = nullptr;
   float2* pw_f = nullptr;
+  float2* pw_fp = nullptr;          // the same in the packed spectrum layout
+  float4* pw_f0 = nullptr;          // per x-row: bounds of the kx = 0 and Nx/2 planes
+  int64_t total_rows = 0;
   unsigned int* pw_min = nullptr;   // per item min Delta (float bits)
   int* pw_bad = nullptr;
   // projection variant (opts.method): residual spectrum and the two
@@ -760,7 +763,8 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   a.err = p->d_err;
   if (p->opts.pointwise) {
     a.pw_e = p->pw_e;
-    a.pw_f = p->pw_f;
+    a.pw_f = p->pw_fp;
+    a.pw_f0 = p->pw_f0;
   }
   if (p->ed_on) {
     a.ed_s = p->ed_s;
@@ -1580,6 +1584,10 @@ void pw_prepare(ffcz_plan_s* p) {
     k_pw_check<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->pw_e, p->pw_f, dg.n, nb, p->pw_min,
                                                             p->pw_bad);
     g_launches++;
+    const unsigned gp = (unsigned)std::min<int64_t>((nb + 255) / 256, 2048);
+    k_pw_pack<<<dim3(gp, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->pw_f, p->pw_fp,
+                                                           reinterpret_cast<float2*>(p->pw_f0), nb);
+    g_launches++;
   }
   k_pw_scale<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->pw_min, (int)p->batch);
   g_launches++;
@@ -2201,6 +2209,20 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         CK(cudaMemcpy(d_co, co.data(), sizeof(int64_t) * co.size(), cudaMemcpyHostToDevice));
         dg.d_canon = d_co;
         dg.g.coff = d_co;
+        // x-row offsets (rows = points / Nx) of every item, for per-row tables
+        std::vector<int64_t> rowoff(batch), ro;
+        int64_t racc = 0;
+        for (int64_t i = 0; i < batch; ++i) {
+          rowoff[i] = racc;
+          int64_t r = 1;
+          for (int d = 0; d < ndim - 1; ++d) r *= shapes[i * ndim + d];
+          racc += r;
+        }
+        p->total_rows = racc;
+        for (int id : ids) ro.push_back(rowoff[id]);
+        int64_t* d_ro = (int64_t*)dalloc(p.get(), sizeof(int64_t) * ro.size());
+        CK(cudaMemcpy(d_ro, ro.data(), sizeof(int64_t) * ro.size(), cudaMemcpyHostToDevice));
+        dg.g.roff = d_ro;
       }
       int32_t* d_it = (int32_t*)dalloc(p.get(), sizeof(int32_t) * it.size());
       int64_t* d_eo = (int64_t*)dalloc(p.get(), sizeof(int64_t) * eo.size());
@@ -2308,6 +2330,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (p->opts.pointwise) {
       p->pw_e = (float*)dalloc(p.get(), sizeof(float) * p->total);
       p->pw_f = (float2*)dalloc(p.get(), sizeof(float2) * p->ed_total[1]);
+      p->pw_fp = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
+      p->pw_f0 = (float4*)dalloc(p.get(), sizeof(float4) * p->total_rows);
       p->pw_min = (unsigned int*)dalloc(p.get(), sizeof(unsigned int) * batch);
       p->pw_bad = (int*)dalloc(p.get(), sizeof(int));
     }

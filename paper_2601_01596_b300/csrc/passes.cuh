@@ -70,6 +70,7 @@ struct Group {
   const int64_t* eoff;           // float offset of each member in e
   const int64_t* soff;           // complex offset of each member's spectrum
   const int64_t* coff;           // offset of each member's canonical half spectrum
+  const int64_t* roff;           // offset of each member's first x-row among all items' rows
 };
 
 // Projection of the loop: Alg. 1 (POCS) or one of the variants that Sec. III
@@ -116,12 +117,14 @@ struct Args {
   float2* ed_f;
   float2* ed_p;
   int* ed_t;
-  // pointwise bounds (null: the item's scalar bounds): E_n laid out like e,
-  // (Delta^Re, Delta^Im) on each member's canonical half spectrum
-  // [Nz][Nmid][M+1]; with them the item's E and D are 1 and the kernels
-  // compare and reduce ratios
+  // pointwise bounds (null: the item's scalar bounds): E_n laid out like e;
+  // (Delta^Re, Delta^Im) in the packed spectrum layout (pw_f, slot kx of
+  // each row for 1 <= kx < M) and, for the kx = 0 and Nx/2 planes, one
+  // float4 (A bounds, B bounds) per row (pw_f0, at roff); with them the
+  // item's E and D are 1 and the kernels compare and reduce ratios
   const float* pw_e;
   const float2* pw_f;
+  const float4* pw_f0;
   // projection variant (Variant; float32 loops only).  pv_r: residual of the
   // frequency projection (Dykstra's p, Douglas-Rachford's z - P_F'(z)) in the
   // packed spectrum layout, read and rewritten in place by the check pass;
@@ -873,6 +876,20 @@ __host__ __device__ inline int chk_ntiles(int W, int M, int Nmid) {
 
 // Everything of the check pass between load and store for one tile in
 // registers.  cta_has_mirror must be uniform over the CTA.
+// Pointwise bounds of a check-pass pencil: its packed slots (step estride
+// per kz) or, on a mirror tile, the per-row float4 of the kx = 0 and Nx/2
+// planes (viewed as float2 pairs: A bounds, then B bounds).
+__device__ __forceinline__ void pw_pencil(const Args& a, int gi, const ChkTile& c, int M, int Nmid,
+                                          int64_t estride, const float2*& pwb, int64_t& pws) {
+  if (c.mirror) {
+    pwb = reinterpret_cast<const float2*>(a.pw_f0 + a.g.roff[gi] + c.off / M);
+    pws = 2 * (int64_t)Nmid;
+  } else {
+    pwb = a.pw_f + a.g.soff[gi] + c.off;
+    pws = estride;
+  }
+}
+
 // FULL = false compiles out the adjoint mask modes and the edit recording
 // (the forward loop's lean variant: less code, no mask-bit bookkeeping).
 template <typename T, int L, class TL, bool PW = false, int PV = PV_POCS, bool FULL = true>
@@ -884,9 +901,9 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
                                          unsigned long long* acc_cnt = nullptr,
                                          int64_t ed_slot0 = 0, int64_t ed_ustride = 0, int t_chk = 0,
                                          const float2* pwb = nullptr, int64_t pws = 0, int pwM = 0) {
-  // pwb: pointwise (Delta^Re, Delta^Im) of this pencil's bins at kz = 0 on the
-  // canonical half spectrum, pws the step per kz; on mirror tiles pwb is the
-  // kx = 0 bin (bounds of A) and pwb + pwM the kx = Nx/2 bin (bounds of B)
+  // pwb: pointwise (Delta^Re, Delta^Im) of this pencil's bin at kz = 0, pws
+  // the step per kz; on mirror tiles pwb holds the bounds of A and pwb + pwM
+  // those of B
   constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
   // pointwise bounds of the thread's bins, loaded before the forward
   // transform so that their latency hides behind it
@@ -1100,9 +1117,11 @@ k_chk(Args a) {
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = blockIdx.x * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
-  const float2* pwb = PW ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
+  const float2* pwb = nullptr;
+  int64_t pws = 0;
+  if constexpr (PW) pw_pencil(a, gi, c, M, Nmid, estride, pwb, pws);
   chk_core<T, L, TL, PW, PV, FULL>(a, p, st, v, j, w, mthr, c, cta_has_mirror, tl, s_tw, s_red, nullptr, nullptr,
-                             a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
+                                   a.g.soff[gi] + c.off + j * estride, ustride, t_it, pwb, pws, 1);
   if ((a.mode & M_NOWRITE) || !c.owner) return;
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
@@ -1246,10 +1265,12 @@ k_chk_tma(Args a) {
     }
     TL tl{s_tiles + w, false};
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
-    const float2* pwb = PW ? a.pw_f + a.g.coff[gi] + (int64_t)(c.off / M) * (M + 1) + c.off % M : nullptr;
+    const float2* pwb = nullptr;
+    int64_t pws = 0;
+    if constexpr (PW) pw_pencil(a, gi, c, M, Nmid, estride, pwb, pws);
     chk_core<float, L, TL, PW, PV_POCS, FULL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
                                               &acc_vb, &acc_cnt, a.g.soff[gi] + c.off + j * estride,
-                                              (int64_t)NT * estride, t_it, pwb, (int64_t)Nmid * (M + 1), M);
+                                              (int64_t)NT * estride, t_it, pwb, pws, 1);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
 #pragma unroll
@@ -1423,6 +1444,23 @@ static __global__ void k_pw_check(Group g, const float* pw_e, const float2* pw_f
     if (mn > 0.f) atomicMin(minbits + item, __float_as_uint(mn));
   }
 }
+// The caller's (Delta^Re, Delta^Im) on the canonical half spectrum
+// [Nz][Nmid][M+1] into the check pass's layouts: the packed slots kx of each
+// row (1 <= kx < M; slot 0 also gets the kx = 0 bounds) and one float4 per
+// row for the kx = 0 (A) and kx = Nx/2 (B) planes.
+static __global__ void k_pw_pack(Group g, const float2* canon, float2* packed, float2* mirror2, int64_t nb) {
+  const int gi = blockIdx.y;
+  const int M = g.M;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / (M + 1);
+    const int kx = (int)(i - row * (M + 1));
+    const float2 b = canon[g.coff[gi] + i];
+    if (kx < M) packed[g.soff[gi] + row * M + kx] = b;
+    if (kx == 0) mirror2[2 * (g.roff[gi] + row)] = b;
+    if (kx == M) mirror2[2 * (g.roff[gi] + row) + 1] = b;
+  }
+}
+
 static __global__ void k_pw_scale(ItemParams* prm, const unsigned int* minbits, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) prm[i].bscale = 1.0 / (double)__uint_as_float(minbits[i]);
