@@ -405,26 +405,47 @@ void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
   }
 }
 
-// Persistent bulk-copy-fed entry x pass (float32, one-warp tiles), sized
-// like the loop's x pass.
-template <int M>
-void launch_xfwd_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
+// Persistent bulk-copy-fed entry and exit x passes (float32, one-warp
+// tiles), sized like the loop's x pass; K selects the kernel.
+template <int M, XKind K, bool PW>
+void launch_xio_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
   constexpr int W = row_w1(M);
   using PG = PxTmaGeo<M, W>;
   const size_t sm = PG::bytes;
-  if (g_dry) { set_smem(k_xfwd_tma<M, W>, sm); return; }
+  auto kern = K == XFWD ? k_xfwd_tma<M, W, PW> : k_xexit_tma<M, W, PW>;
+  if (g_dry) { set_smem(kern, sm); return; }
   static int per_sm = 0;   // resident CTAs per SM (same for every plan)
   if (per_sm == 0) {
     int n = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_xfwd_tma<M, W>, Geo<float, M, W>::NTHR, sm));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Geo<float, M, W>::NTHR, sm));
     per_sm = n > 0 ? n : 1;
   }
   const int64_t nblk = (rows + PG::RG - 1) / PG::RG;
   const int64_t want = ((int64_t)per_sm * g_num_sms_x + count - 1) / count;
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, want));
-  ProfScope ps("xfwd", 32, M, s);
-  k_xfwd_tma<M, W><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
+  ProfScope ps(K == XFWD ? "xfwd" : "xexit", 32, M, s);
+  kern<<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
   g_launches++;
+}
+// The entry (measure only: no pre-clip, no mask) and exit (not Dykstra's)
+// follow the plan's choice of the persistent x pass.
+inline bool xio_tma_ok(XKind kind, const Args& a) {
+  if (kind == XFWD) return !(a.mode & (M_PRECLIP | M_MASK));
+  return kind == XEXIT && a.pv != PV_DYKSTRA;
+}
+template <int M, bool PW>
+bool launch_xio_tma_kind(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
+  if (g_dry) {   // both bound kinds (the pointwise dry run does not pass w < 0)
+    launch_xio_tma<M, XFWD, false>(a, rows, count, s);
+    launch_xio_tma<M, XEXIT, false>(a, rows, count, s);
+    launch_xio_tma<M, XFWD, true>(a, rows, count, s);
+    launch_xio_tma<M, XEXIT, true>(a, rows, count, s);
+    return false;
+  }
+  if (!xio_tma_ok(kind, a)) return false;
+  if (kind == XFWD) launch_xio_tma<M, XFWD, PW>(a, rows, count, s);
+  else launch_xio_tma<M, XEXIT, PW>(a, rows, count, s);
+  return true;
 }
 
 template <typename T>
@@ -433,8 +454,9 @@ struct XL {
   static void go(XKind kind, int w, const Args& a, int64_t rows, int count, cudaStream_t s) {
     if (a.pw_e || g_pw_sel) {
       if constexpr (sizeof(T) == 4) {
-        // the loop's x pass follows the plan's choice of the copy-engine-fed kernel
+        // the loop's x passes follow the plan's choice of the copy-engine-fed kernel
         if (w < 0 && kind == XPX && !g_dry) { launch_px_tma<M>(a, rows, count, s); return; }
+        if (w < 0 && launch_xio_tma_kind<M, true>(kind, a, rows, count, s)) return;
       }
       launch_x_tw<T, M, row_w1(M), true>(kind, a, rows, count, s);
       return;
@@ -455,11 +477,8 @@ struct XL {
         launch_px_tma<M>(a, rows, count, s);
         if (!g_dry) return;
       }
-      // the entry pass follows the loop's x-pass choice (plain modes only)
-      if (w < 0 && ((kind == XFWD && !(a.mode & (M_PRECLIP | M_MASK))) || g_dry)) {
-        launch_xfwd_tma<M>(a, rows, count, s);
-        if (!g_dry) return;
-      }
+      // the entry and exit passes follow the loop's x-pass choice
+      if (w < 0 && launch_xio_tma_kind<M, false>(kind, a, rows, count, s)) return;
       if (w == row_w2(M)) launch_x_tw<T, M, row_w2(M)>(kind, a, rows, count, s);
       else launch_x_tw<T, M, row_w1(M)>(kind, a, rows, count, s);
     } else {

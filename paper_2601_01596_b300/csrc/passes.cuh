@@ -718,6 +718,42 @@ k_px(Args a) {
   }
 }
 
+// Exit epilogue of one row (after the C2R): scale 1/N, (Dykstra) + q_{t-1},
+// s-clip when M_CLIP (again after rounding to float32), store or (M_ACC)
+// add to e.
+template <typename T, int V, bool PW, int PV>
+__device__ __forceinline__ void xexit_store(const Args& a, const ItemParams& p, v2<T> (&v)[V], int j, int NT,
+                                            float2* erow, const float2* ebrow, const float2* qrow) {
+  const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
+  const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
+#pragma unroll
+  for (int u = 0; u < V; ++u) {
+    T x = v[u].x * inv_n, y = v[u].y * inv_n;
+    if (PV == PV_DYKSTRA && qrow) {
+      const float2 q = qrow[j + u * NT];
+      x += (T)q.x;
+      y += (T)q.y;
+    }
+    float2 eb = make_float2(1.f, 1.f);
+    if constexpr (PW) eb = ebrow[j + u * NT];
+    if (a.mode & M_CLIP) {
+      if constexpr (PW) { x = clampT(x, Es * (T)eb.x); y = clampT(y, Es * (T)eb.y); }
+      else { x = clampT(x, Es); y = clampT(y, Es); }
+    }
+    float fx = (float)x, fy = (float)y;
+    if (a.mode & M_CLIP) {
+      // keep the float32 result inside the shrunk cube after rounding
+      if constexpr (PW) { fx = clampT(fx, p.Esf * eb.x); fy = clampT(fy, p.Esf * eb.y); }
+      else { fx = clampT(fx, p.Esf); fy = clampT(fy, p.Esf); }
+    }
+    if (a.mode & M_ACC) {
+      const float2 o = erow[j + u * NT];
+      fx += o.x; fy += o.y;
+    }
+    erow[j + u * NT] = make_float2(fx, fy);
+  }
+}
+
 // Exit x pass: C2R, scale 1/N, s-clip, store float32 e (rebuilds the iterate
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
 // no clip is applied.
@@ -732,44 +768,14 @@ k_xexit(Args a) {
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   c2r_pre<T, M>(v, j, tl, s_twr);
   fft_pencil<T, M, +1>(v, j, s_tw, tl);
-  const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
-  const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
   const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
   // Dykstra: x_t = P_S'(y_{t-1} + q_{t-1}) (q_0 = 0)
   const float2* qrow = (PV == PV_DYKSTRA && t_it >= 2)
                            ? reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M
                            : nullptr;
-  if (live) {
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      T x = v[u].x * inv_n, y = v[u].y * inv_n;
-      if (PV == PV_DYKSTRA && qrow) {
-        const float2 q = qrow[j + u * G_::NT];
-        x += (T)q.x;
-        y += (T)q.y;
-      }
-      float2 eb = make_float2(1.f, 1.f);
-      if constexpr (PW) eb = ebrow[j + u * G_::NT];
-      if (a.mode & M_CLIP) {
-        if constexpr (PW) { x = clampT(x, Es * (T)eb.x); y = clampT(y, Es * (T)eb.y); }
-        else { x = clampT(x, Es); y = clampT(y, Es); }
-      }
-      float fx = (float)x, fy = (float)y;
-      if (a.mode & M_CLIP) {
-        // keep the float32 result inside the shrunk cube after rounding
-        if constexpr (PW) { fx = clampT(fx, p.Esf * eb.x); fy = clampT(fy, p.Esf * eb.y); }
-        else { fx = clampT(fx, p.Esf); fy = clampT(fy, p.Esf); }
-      }
-      if (a.mode & M_ACC) {
-        const float2 o = erow[j + u * G_::NT];
-        fx += o.x; fy += o.y;
-      }
-      erow[j + u * G_::NT] = make_float2(fx, fy);
-    }
-  }
+  if (live) xexit_store<T, V, PW, PV>(a, p, v, j, G_::NT, erow, ebrow, qrow);
 }
-
 // ---------------------------------------------------------------------------
 // Strided axis passes
 // ---------------------------------------------------------------------------
@@ -1477,7 +1483,7 @@ static __global__ void k_pw_scale(ItemParams* prm, const unsigned int* minbits, 
 // the same way as k_px_tma (no pre-clip, mask or pointwise bounds: those use
 // k_xfwd).  Each thread sums its squares per block in float32 (at most 2V
 // terms, inflated as in k_xfwd) and the blocks in double.
-template <int M, int W>
+template <int M, int W, bool PW = false>
 __global__ void __launch_bounds__(Geo<float, M, W>::NTHR, Geo<float, M, W>::MINB)
 k_xfwd_tma(Args a) {
   using G_ = Geo<float, M, W>;
@@ -1539,11 +1545,17 @@ k_xfwd_tma(Args a) {
     const int64_t row = live ? prow : 0;
     float2 v[V];
     float ssq = 0.f;
+    const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       v[u] = s_stage[(g * W + w) * M + j + u * NT];
       if (measure && live) {
-        mx.add(v[u].x); mx.add(v[u].y);
+        if constexpr (PW) {   // pointwise E_n: the maximum of |e_n| / E_n
+          const float2 eb = ebrow[j + u * NT];
+          mx.add(ratioT(v[u].x, eb.x)); mx.add(ratioT(v[u].y, eb.y));
+        } else {
+          mx.add(v[u].x); mx.add(v[u].y);
+        }
         bad |= (v[u].x != v[u].x) | (v[u].y != v[u].y);
         ssq = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, ssq));
       }
@@ -1573,6 +1585,83 @@ k_xfwd_tma(Args a) {
       atomicMax(&st.emaxbits, r.vbits);
       atomicAdd(&st.sumsq, r.sum);
     }
+  }
+}
+
+// Persistent float32 exit x pass (C2R, scale 1/N, s-clip, store or add to
+// e) fed by bulk copies of blocks of spectrum rows, the same way as
+// k_px_tma; Alg. 1 and pointwise bounds (the Dykstra exit uses k_xexit).
+template <int M, int W, bool PW = false>
+__global__ void __launch_bounds__(Geo<float, M, W>::NTHR, PW ? Geo<float, M, W>::MINB_PW : Geo<float, M, W>::MINB)
+k_xexit_tma(Args a) {
+  using G_ = Geo<float, M, W>;
+  using TL = Tile<float, M, W>;
+  using PG = PxTmaGeo<M, W>;
+  constexpr int V = G_::V, NT = G_::NT, RG = PG::RG;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const uint32_t s0 = smem_addr(smraw);   // staging rounded up to 128 bytes
+  float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0 + 127u) & ~127u) - s0));
+  float2* s_tiles = s_stage + RG * M;
+  float2* s_tw = s_tiles + G_::G * TL::ELEMS;
+  float2* s_twr = s_tw + M;
+  __shared__ __align__(8) uint64_t bar;
+  const int gi = blockIdx.y;
+  const int item = a.g.item[gi];
+  const ItemParams& p = a.prm[item];
+  ItemState& st = a.st[item];
+  if (!pred_ok(a.pred, st, p)) return;
+  const int t_it = st.t;
+  const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;
+  const int w = tid % W, j = tid / W;
+  const int64_t rows = a.g.rows;
+  const int64_t nblk = (rows + RG - 1) / RG;
+  const float2* inb = pick<float>(a, a.sel_in, t_it) + a.g.soff[gi];
+  if ((smem_addr(s_stage) & 127u) != 0u || (reinterpret_cast<uintptr_t>(inb) & 15u) != 0u) {
+    if (threadIdx.x == 0) atomicExch(a.err, DERR_TMA_ALIGN);
+    return;
+  }
+  load_tables<float>(s_tw, a.tw, M, s_twr, a.twr, M);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t parity = 0;
+  auto issue = [&](int64_t blk) {
+    const int64_t r0 = blk * RG;
+    const int64_t nr = rows - r0 < RG ? rows - r0 : RG;
+    const uint32_t bytes = (uint32_t)(nr * M * sizeof(float2));
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_load(s_stage, inb + r0 * M, bytes, &bar);
+  };
+  int64_t blk = blockIdx.x;
+  if (threadIdx.x == 0 && blk < nblk) issue(blk);
+  while (blk < nblk) {
+    const int64_t next = blk + gridDim.x;
+    const bool ok = mbar_wait_bounded(&bar, parity, kTmaPollLimit);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);
+      mbar_wait_bounded(&bar, parity, kTmaPollLimit);   // copies still in flight
+      return;
+    }
+    float2 v[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) v[u] = s_stage[(g * W + w) * M + j + u * NT];
+    __syncthreads();
+    if (threadIdx.x == 0 && next < nblk) {
+      fence_proxy_async_smem();
+      issue(next);
+    }
+    parity ^= 1u;
+    const int tile = (int)(blk * G_::G + g);
+    const int64_t prow = (int64_t)tile * W + w;
+    const bool live = prow < rows;
+    const int64_t row = live ? prow : 0;
+    TL tl{s_tiles + g * TL::ELEMS + w, false};
+    c2r_pre<float, M>(v, j, tl, s_twr);
+    fft_pencil<float, M, +1>(v, j, s_tw, tl);
+    float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
+    const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+    if (live) xexit_store<float, V, PW, PV_POCS>(a, p, v, j, NT, erow, ebrow, nullptr);
+    TL::sync();   // the warp's tile buffer is reused by the next block
+    blk = next;
   }
 }
 
