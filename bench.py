@@ -45,9 +45,9 @@ FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
 # at 512^3 (profiles/); an entry is removed when its kernel changes.
 NCU_TRAFFIC = {
-    "chk<f32,512>": 563948544 + 502807296,        # k_chk_tma<512, 8, lean>
+    "chk<f32,512>": 563637504 + 501929472,        # k_chk_tma<512, 8, lean>
     "axis_fwd<f32,512>": 536954880 + 483795200,   # k_axis_tma<512, -1, 8>
-    "px<f32,256>": 537590016 + 477834240,         # k_px_tma<256, 2>
+    "px<f32,256>": 536950016 + 476919808,         # k_px_tma<256, 2, lean>
     "xfwd<f64,256>": 537062656 + 1016352000,      # k_xfwd<double, 256, 2, X2>
     "xfwd<f32,256>": 536927488 + 489845760,       # k_xfwd_tma<256, 2> (entry)
     "axis_fwd<f64,512>": 1075036000 + 1019320000,  # k_axis<double, 512, -1, 4>
