@@ -103,3 +103,24 @@ def test_certification_of_special_float_values():
         t = torch.from_numpy(x.reshape(-1).copy()).cuda()
         assert plan.check(t, [s], [v * (1 + 1e-8)])[0]["certified"] == 1, scale
         assert plan.check(t, [s], [v * (1 - 1e-8)])[0]["certified"] == 0, scale
+
+
+def test_fp64_repair_after_a_failed_certification():
+    """A float32 loop stopped by its cap short of feasibility fails the FP64
+    certification; the FP64 repair (Alg. 1 in float64 from the
+    float32 result) brings the field inside.  The oracle's own check confirms
+    the result, and the host-buffer entry point (which copies the field back
+    early and again after a repair) returns the same bits."""
+    import paper_2601_01596_b300 as ffcz
+    e0, E, D = stress((32, 32, 32), 5, frac=0.2)
+    ref = O.correct(e0, E, D)
+    cap = ref.iters - 2                  # e_cap is outside the true f-cube (checked below)
+    assert not O.certify(O.correct(e0, E, D, min_iters=cap, max_iters=cap).e, E, D)[0]
+    e, st = run(e0, E, D, max_iters=cap)
+    assert st["repairs"] >= 1 and st["certified"] == 1
+    ok, s, v = O.certify(e.astype(np.float64), E, D)
+    assert ok, (s, v)
+    host = e0.reshape(-1).copy()
+    plan = ffcz.Plan([e0.shape], max_iters=cap)
+    sth = plan.correct_host(host, [E], [D])[0]
+    assert sth["repairs"] == st["repairs"] and np.array_equal(host, e.reshape(-1))
