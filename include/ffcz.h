@@ -276,7 +276,10 @@ ffcz_status ffcz_correct(ffcz_plan_t plan, float* e_dev, const double* eps_s,
 /*
  * ffcz_correct_host -- ffcz_correct on host memory: copies e_host to the
  * plan's device staging buffer, corrects, copies the result back.
- * e_host may be pageable or pinned; it is read and written in place.
+ * e_host may be pageable or pinned; it is read and written in place.  The
+ * copy back starts on a second stream as soon as the loop is done, while the
+ * FP64 certification (which only reads the field) runs; if a repair round
+ * changes the field, it waits for that copy and copies the field again.
  */
 ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps_s,
                               const double* eps_f, ffcz_stats* stats);
@@ -286,7 +289,11 @@ ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps
  * (constraints_v1 with <=): max|e_n| <= E and, for every DFT bin,
  * max(|Re|, |Im|) + b <= Delta, where b is a rigorous bound on the FP64 FFT's
  * rounding error (error analysis of Cooley-Tukey FFTs: log2(N) stages of
- * radix-2/4/8 butterflies with correctly rounded twiddles).
+ * radix-2/4/8 butterflies with correctly rounded twiddles):
+ * b = 10 (log2 N + 2) u sqrt(N) ||e||_2, u = 2^-53, with ||e||_2 bounded by
+ * the smaller of the float32 sum of squares (inflated for its rounding and
+ * for squares below the float32 normal range) and sqrt(N) max|e|; for 1D
+ * Bluestein items b = 10 (2 log2 P + 6) u 2N ||e||_2.
  * Does not modify e.  stats[i].certified, s_ratio, f_margin64, s_margin64 are
  * filled.  Returns OK if every item passes, CERT_FAILED otherwise.
  */
