@@ -369,23 +369,24 @@ int g_num_sms_x = 148;   // set from the device at plan creation
 
 // Persistent bulk-copy-fed loop x pass (float32, one-warp tiles): as many
 // CTAs as fit on the device, spread over the group's items.
-template <int M, bool ED, bool PW = false>
+template <int M, bool ED, bool PW = false, int PV = PV_POCS>
 void launch_px_tma_ed(const Args& a, int64_t rows, int count, cudaStream_t s) {
   constexpr int W = row_w1(M);
   using PG = PxTmaGeo<M, W>;
   const size_t sm = PG::bytes;
-  if (g_dry) { set_smem(k_px_tma<M, W, ED, PW>, sm); return; }
+  if (g_dry) { set_smem(k_px_tma<M, W, ED, PW, PV>, sm); return; }
   static int per_sm = 0;   // resident CTAs per SM (same for every plan)
   if (per_sm == 0) {
     int n = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W, ED, PW>, Geo<float, M, W>::NTHR, sm));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_px_tma<M, W, ED, PW, PV>, Geo<float, M, W>::NTHR,
+                                                     sm));
     per_sm = n > 0 ? n : 1;
   }
   const int64_t nblk = (rows + PG::RG - 1) / PG::RG;
   const int64_t want = ((int64_t)per_sm * g_num_sms_x + count - 1) / count;
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, want));
   ProfScope ps("px", 32, M, s);
-  k_px_tma<M, W, ED, PW><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
+  k_px_tma<M, W, ED, PW, PV><<<dim3(gx, (unsigned)count), Geo<float, M, W>::NTHR, sm, s>>>(a);
   g_launches++;
 }
 template <int M>
@@ -395,6 +396,12 @@ void launch_px_tma(const Args& a, int64_t rows, int count, cudaStream_t s) {
     launch_px_tma_ed<M, true>(a, rows, count, s);
     launch_px_tma_ed<M, false, true>(a, rows, count, s);
     launch_px_tma_ed<M, true, true>(a, rows, count, s);
+    launch_px_tma_ed<M, false, false, PV_DYKSTRA>(a, rows, count, s);
+    launch_px_tma_ed<M, false, false, PV_ADMM>(a, rows, count, s);
+  } else if (a.pv == PV_DYKSTRA) {   // projection variants (lean only)
+    launch_px_tma_ed<M, false, false, PV_DYKSTRA>(a, rows, count, s);
+  } else if (a.pv == PV_ADMM) {
+    launch_px_tma_ed<M, false, false, PV_ADMM>(a, rows, count, s);
   } else if (a.pw_e) {   // pointwise E_n
     if (px_full(a)) launch_px_tma_ed<M, true, true>(a, rows, count, s);
     else launch_px_tma_ed<M, false, true>(a, rows, count, s);
@@ -462,7 +469,12 @@ struct XL {
       return;
     }
     if constexpr (sizeof(T) == 4) {
-      // projection variants: the x passes that carry q / u (one tile width)
+      // projection variants: the x passes that carry q / u (the loop's pass
+      // follows the plan's choice of the persistent kernel)
+      if ((a.pv == PV_DYKSTRA || a.pv == PV_ADMM) && kind == XPX && w < 0 && !g_dry) {
+        launch_px_tma<M>(a, rows, count, s);
+        return;
+      }
       if (a.pv == PV_DYKSTRA && (kind == XPX || kind == XEXIT)) {
         launch_x_tw<T, M, row_w1(M), false, PV_DYKSTRA>(kind, a, rows, count, s);
         return;

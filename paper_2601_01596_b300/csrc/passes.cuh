@@ -617,8 +617,7 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
       } else {
         // ADMM: a_t (the input) is checked against the s-cube; then
         // b = P_S'(a + u), u <- a + u - b, and the pass forwards b - u
-        svm->add(x);
-        svm->add(y);
+        if (live) { svm->add(x); svm->add(y); }
         const T wx = x + (T)qv[u].x, wy = y + (T)qv[u].y;
         const T bx = clampT(wx, Es), by = clampT(wy, Es);
         if (count) cnt += (bx != wx) + (by != wy);
@@ -1309,8 +1308,9 @@ struct PxTmaGeo {
                                   2 * (size_t)M * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
 };
 
-template <int M, int W, bool ED = false, bool PW = false>
-__global__ void __launch_bounds__(Geo<float, M, W>::NTHR, PW ? Geo<float, M, W>::MINB_PW : Geo<float, M, W>::MINB)
+template <int M, int W, bool ED = false, bool PW = false, int PV = PV_POCS>
+__global__ void __launch_bounds__(Geo<float, M, W>::NTHR,
+                                  (PW || PV != PV_POCS) ? Geo<float, M, W>::MINB_PW : Geo<float, M, W>::MINB)
 k_px_tma(Args a) {
   using G_ = Geo<float, M, W>;
   using TL = Tile<float, M, W>;
@@ -1354,6 +1354,7 @@ k_px_tma(Args a) {
   int64_t blk = blockIdx.x;
   if (threadIdx.x == 0 && blk < nblk) issue(blk);
   unsigned long long cnt = 0;
+  AbsMax<float> svm;   // ADMM: max |a_t| over the CTA's points
   while (blk < nblk) {
     const int64_t next = blk + gridDim.x;
     const bool ok = mbar_wait_bounded(&bar, parity, kTmaPollLimit);
@@ -1379,7 +1380,14 @@ k_px_tma(Args a) {
     TL tl{s_tiles + g * TL::ELEMS + w, false};
     float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
     const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
-    cnt += px_core<float, M, TL, PW, ED>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow);
+    const float2* qin = nullptr;
+    float2* qout = nullptr;
+    if constexpr (PV != PV_POCS) {   // Dykstra's q / ADMM's u, one buffer per iteration parity
+      qin = reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M;
+      qout = reinterpret_cast<float2*>(a.pv_q[t_it & 1] + a.g.eoff[gi]) + row * M;
+    }
+    cnt += px_core<float, M, TL, PW, ED, PV>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow,
+                                             qin, qout, &svm);
     if (live) {
       float2* out = outb + row * M;
 #pragma unroll
@@ -1387,6 +1395,12 @@ k_px_tma(Args a) {
     }
     TL::sync();   // the warp's tile buffer is reused by the next block
     blk = next;
+  }
+  if constexpr (PV == PV_ADMM) {
+    // spatial check of a_t over the CTA's rows (NaN -> +inf)
+    unsigned long long vb = svm.dbits(svm.val() != svm.val()), cz = 0ull;
+    block_max_count(vb, cz, false, s_red);
+    if (threadIdx.x == 0) atomicMax(&st.svbits, vb);
   }
   if (a.mode & M_COUNT) {
     Red r{0ull, 0.0, cnt};
