@@ -276,7 +276,11 @@ ffcz_status ffcz_correct(ffcz_plan_t plan, float* e_dev, const double* eps_s,
 /*
  * ffcz_correct_host -- ffcz_correct on host memory: copies e_host to the
  * plan's device staging buffer, corrects, copies the result back.
- * e_host may be pageable or pinned; it is read and written in place.  The
+ * e_host may be pageable or pinned; it is read and written in place.  For
+ * single-item 2D/3D plans the upload runs in row chunks while the FP64
+ * certification's x pass processes the chunks already on the device; when
+ * the loop stops at 0 iterations without a pre-clip (the field unchanged)
+ * the certification continues from that pass, else it runs in full.  The
  * copy back starts on a second stream as soon as the loop is done, while the
  * FP64 certification (which only reads the field) runs; if a repair round
  * changes the field, it waits for that copy and copies the field again.

@@ -142,6 +142,12 @@ struct ffcz_plan_s {
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
   cudaStream_t copy_stream = nullptr;  // host-buffer entry point: copy-back stream
   cudaEvent_t ev_copy = nullptr;
+  // host-buffer entry point: the upload in row chunks and the FP64 x pass on
+  // each chunk as it lands (spec_stream), into a side state d_stc
+  cudaStream_t spec_stream = nullptr;
+  std::vector<cudaEvent_t> ev_chunks;
+  cudaEvent_t ev_spec = nullptr;
+  ItemState* d_stc = nullptr;
   int device = 0;
 
   std::vector<DevGroup> groups;
@@ -1439,12 +1445,15 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
   if (p->ed_on) edits_finalize(p);
 }
 
-void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
+// st: the state the certification reads and writes (default the loop's);
+// x_done: the x pass already ran into the FP64 buffer (host entry point).
+void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = nullptr, bool x_done = false) {
+  ItemState* S = st ? st : p->d_st;
   if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total_c * sizeof(double2));
   if (p->ndim == 1 && !p->Bt64) build_bt<double>(p);
   for (auto& dg : p->groups) {
     if (p->ndim == 1) {
-      Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_st);
+      Args a = make_args<double>(p, dg, p->Bc, p->Bc, S);
       a.pred = repair_round ? P_UNCERT : P_ALL;
       a.e = const_cast<float*>(e);
       col1_args<double>(p, a, dg, OP1_ENTRY);
@@ -1458,12 +1467,12 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
       launch_col1<double>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
       continue;
     }
-    Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_st);
+    Args a = make_args<double>(p, dg, p->Bc, p->Bc, S);
     a.pred = repair_round ? P_UNCERT : P_ALL;
     tabs_x<double>(p, a, dg);
     a.e = const_cast<float*>(e);
     a.mode = M_MEASURE;
-    launch_x<double>(XCERT, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+    if (!x_done) launch_x<double>(XCERT, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
     if (dg.ndim == 3) {
       a.tw = tw_of<double>(p->tb, dg.Ny);
       a.mode = 0;
@@ -1475,8 +1484,19 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round) {
   }
   // 2D/3D certification transforms return 2 delta (XCERT)
   k_certify<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(
-      p->d_prm, p->d_st, (int)p->batch, repair_round ? 1 : 0, p->ndim == 1 ? 1.0 : 0.5);
+      p->d_prm, S, (int)p->batch, repair_round ? 1 : 0, p->ndim == 1 ? 1.0 : 0.5);
   g_launches++;
+}
+
+// Certification results computed in a side state (the host entry point's
+// x pass during the upload) adopted by the loop's state.
+__global__ void k_cert_adopt(ItemState* st, const ItemState* sc, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  st[i].certified = sc[i].certified;
+  st[i].v64 = sc[i].v64;
+  st[i].emax64 = sc[i].emax64;
+  st[i].bound64 = sc[i].bound64;
 }
 
 // Reset the certification accumulators (they are shared with the loop).
@@ -1585,6 +1605,9 @@ void free_plan(ffcz_plan_s* p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   if (p->ev_copy) cudaEventDestroy(p->ev_copy);
+  if (p->spec_stream) cudaStreamDestroy(p->spec_stream);
+  for (auto ev : p->ev_chunks) cudaEventDestroy(ev);
+  if (p->ev_spec) cudaEventDestroy(p->ev_spec);
   delete p;
 }
 
@@ -1632,8 +1655,74 @@ void pw_prepare(ffcz_plan_s* p) {
 // second stream as soon as the loop is done, overlapping the certification,
 // which only reads e; a repair round waits for that copy and the field is
 // copied again at the end.
+// Host-buffer entry point: upload the field in chunks of whole CTA rows on
+// the copy stream and run the FP64 certification's x pass on each chunk as
+// it lands (on a third stream, into the FP64 buffer and the side state
+// d_stc), so the transfer hides most of that pass.  The loop's stream waits
+// for the last chunk only.  Single-item 2D/3D plans with certification.
+bool spec_upload(ffcz_plan_s* p, float* e_dev, const float* host) {
+  if (p->batch != 1 || p->ndim < 2 || !p->opts.certify || p->opts.pointwise) return false;
+  const DevGroup& dg = p->groups[0];
+  if (!p->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_copy, cudaEventDisableTiming));
+  }
+  constexpr int K = 8;
+  if (!p->spec_stream) {
+    CK(cudaStreamCreateWithFlags(&p->spec_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_spec, cudaEventDisableTiming));
+    p->ev_chunks.resize(K + 1);
+    for (auto& ev : p->ev_chunks) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  if (!p->d_stc) p->d_stc = (ItemState*)dalloc(p, sizeof(ItemState) * p->batch);
+  if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total_c * sizeof(double2));
+  // everything earlier on the plan's stream (a previous call) is done with
+  // the staging and FP64 buffers before the chunks start
+  CK(cudaEventRecord(p->ev_chunks[K], p->stream));
+  CK(cudaStreamWaitEvent(p->copy_stream, p->ev_chunks[K], 0));
+  CK(cudaStreamWaitEvent(p->spec_stream, p->ev_chunks[K], 0));
+  CK(cudaMemsetAsync(p->d_stc, 0, sizeof(ItemState) * p->batch, p->spec_stream));
+  // rows of one CTA of the FP64 x pass (tiles of row_w1(M) rows, G per CTA)
+  const int W = row_w1(dg.M), tpt = f2_nt(dg.M) * W, rpc = (tpt >= 128 ? 1 : 128 / tpt) * W;
+  const int64_t rows = dg.rows, Nx = 2 * (int64_t)dg.M;
+  const int64_t crow = ((rows + K - 1) / K + rpc - 1) / rpc * rpc;
+  int c = 0;
+  for (int64_t r0 = 0; r0 < rows; r0 += crow, ++c) {
+    const int64_t nr = std::min(crow, rows - r0);
+    CK(cudaMemcpyAsync(e_dev + r0 * Nx, host + r0 * Nx, sizeof(float) * nr * Nx, cudaMemcpyHostToDevice,
+                       p->copy_stream));
+    CK(cudaEventRecord(p->ev_chunks[c], p->copy_stream));
+    CK(cudaStreamWaitEvent(p->spec_stream, p->ev_chunks[c], 0));
+    Args a = make_args<double>(p, dg, p->Bc, p->Bc, p->d_stc);
+    a.pred = P_ALL;
+    tabs_x<double>(p, a, dg);
+    a.e = e_dev;
+    a.mode = M_MEASURE;
+    a.tile0 = (int)(r0 / W);
+    launch_x<double>(XCERT, dg.M, dg.wx, a, nr, 1, p->spec_stream);
+  }
+  CK(cudaEventRecord(p->ev_spec, p->spec_stream));
+  CK(cudaStreamWaitEvent(p->stream, p->ev_chunks[c - 1], 0));   // the loop needs the whole field
+  return true;
+}
+
+// After the loop: if it stopped at 0 iterations without a pre-clip, the
+// field is the uploaded one and the certification continues from the x pass
+// of spec_upload (y and z passes, the check, adopted by the loop's state).
+bool spec_adopt(ffcz_plan_s* p, const float* e) {
+  CK(cudaStreamWaitEvent(p->stream, p->ev_spec, 0));
+  CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(ItemState) * p->batch, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  for (int64_t i = 0; i < p->batch; ++i)
+    if (p->h_st[i].t != 0 || p->h_st[i].preclip || p->h_st[i].status != 0) return false;
+  certify(p, e, false, p->d_stc, true);
+  k_cert_adopt<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, p->d_stc, (int)p->batch);
+  g_launches++;
+  return true;
+}
+
 ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const double* eps_f,
-                         ffcz_stats* stats, float* host_out = nullptr) {
+                         ffcz_stats* stats, float* host_out = nullptr, bool spec_x = false) {
   if (!e || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
   ProfOn prof_on(p);
   CK(cudaSetDevice(p->device));
@@ -1650,7 +1739,7 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
   else run_loop<float>(p, e, false);
   CK(cudaEventRecord(p->ev1, p->stream));
   bool cert = p->opts.certify != 0;
-  if (cert) {
+  if (cert && !(spec_x && spec_adopt(p, e))) {
     cert_reset(p);
     certify(p, e, false);
   }
@@ -2544,6 +2633,8 @@ ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps
     if (!e_host) fail(FFCZ_ERR_INVALID, "e_host is null");
     CK(cudaSetDevice(plan->device));
     if (!plan->staging) plan->staging = (float*)dalloc(plan, sizeof(float) * plan->total);
+    if (spec_upload(plan, plan->staging, e_host))
+      return correct_impl(plan, plan->staging, eps_s, eps_f, stats, e_host, true);
     CK(cudaMemcpyAsync(plan->staging, e_host, sizeof(float) * plan->total, cudaMemcpyHostToDevice,
                        plan->stream));
     return correct_impl(plan, plan->staging, eps_s, eps_f, stats, e_host);

@@ -133,6 +133,8 @@ struct Args {
   int pv;
   float2* pv_r;
   float* pv_q[2];
+  // first tile of a launch of the plain x passes (0: all rows)
+  int tile0;
 };
 
 // Spatial edit of one complex register (two real points): S += (c - v).
@@ -475,7 +477,7 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
   const int t_it = st.t;                                                          \
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
   const int w = tid % G_::W, j = tid / G_::W;                                     \
-  const int tile = blockIdx.x * G_::G + g;                                        \
+  const int tile = a.tile0 + blockIdx.x * G_::G + g;                              \
   const int64_t prow = (int64_t)tile * G_::W + w;                                 \
   const bool live = prow < a.g.rows;                                              \
   const int64_t row = live ? prow : 0;                                            \
