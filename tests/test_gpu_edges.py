@@ -124,3 +124,25 @@ def test_fp64_repair_after_a_failed_certification():
     plan = ffcz.Plan([e0.shape], max_iters=cap)
     sth = plan.correct_host(host, [E], [D])[0]
     assert sth["repairs"] == st["repairs"] and np.array_equal(host, e.reshape(-1))
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128)])
+def test_host_entry_certification_from_the_upload_matches_device(shape):
+    """At 0 iterations the host entry point certifies from the x pass it ran
+    while uploading: same bits out, certified, the same FP64 margins as the
+    device entry point (up to the summation order of the norm)."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    r = np.random.default_rng(17)
+    e0 = (r.uniform(-1, 1, shape) * 0.5).astype(np.float32)
+    E = 1.0
+    D = 2.0 * O.f_violation(O.dft(e0.astype(np.float64)))
+    plan = ffcz.Plan([shape])
+    t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    sd = plan.correct(t, [E], [D])[0]
+    host = e0.reshape(-1).copy()
+    sh = plan.correct_host(host, [E], [D])[0]
+    assert sd["iters"] == 0 and sh["iters"] == 0
+    assert sh["certified"] == 1 and np.array_equal(host, e0.reshape(-1))
+    assert abs(sh["f_margin64"] - sd["f_margin64"]) < 1e-12
+    assert sh["s_margin64"] == sd["s_margin64"]
