@@ -203,7 +203,7 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
  * ffcz_correct_pw -- ffcz_correct with pointwise bounds (the generalisation
  * E_n, Delta_k^Re, Delta_k^Im named in Sec. IV-A), for a plan created with
  * opts.pointwise = 1.
- *   eb_dev : device float32, E_n > 0 for every point, laid out like e.
+ *   eb_dev : device float32, E_n > 0 (normal) for every point, laid out like e.
  *   db_dev : device float32 pairs (Delta^Re, Delta^Im) > 0 on each item's
  *            half spectrum of a real-input FFT, [Nz][Ny][Nx/2+1] (2D:
  *            [Ny][Nx/2+1]), items back to back (the offsets of
@@ -215,7 +215,8 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
  * s_ratio; margins 1 - ratio), and certification requires max|e_n|/E_n <= 1
  * and (FP64 normalised violation) + (FP64 rounding bound) / min_k Delta_k <= 1.
  * The bounds are copied into the plan (the call may reuse its inputs at
- * once).  Non-positive or non-finite bounds give FFCZ_ERR_INVALID.  On a
+ * once).  Bounds must be normal float32 values (FLT_MIN <= b <= FLT_MAX):
+ * zero, subnormal, negative or non-finite bounds give FFCZ_ERR_INVALID.  On a
  * pointwise plan ffcz_correct, ffcz_correct_host, ffcz_check, the backward and
  * the edit compaction/application (whose codes are relative to scalar bounds)
  * return FFCZ_ERR_INVALID.

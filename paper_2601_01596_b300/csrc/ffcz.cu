@@ -100,6 +100,8 @@ struct DevGroup {
   // null where the TMA-fed kernels do not apply
   const CUtensorMap* tm_axis = nullptr;
   const CUtensorMap* tm_chk = nullptr;
+  // the check pass's view of the packed pointwise f-bounds (count maps)
+  const CUtensorMap* tm_pw = nullptr;
   std::vector<int64_t> h_soff;   // host copy of the members' spectrum offsets
   const int64_t* d_canon = nullptr;   // members' offsets in the canonical edit spectra
   // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
@@ -547,10 +549,11 @@ inline bool chk_full(const Args& a) { return (a.mode & (M_RECORD | M_MASK)) != 0
 template <int L>
 void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_ntiles(8, M, Nmid);
-  const size_t sm = TmaGeo<L, 8>::bytes;
+  const size_t sm = a.pw_f ? TmaGeo<L, 8>::bytes_pw : TmaGeo<L, 8>::bytes;
   if (g_dry) {
-    set_smem(k_chk_tma<L, 8, true>, sm); set_smem(k_chk_tma<L, 8, false>, sm);
-    set_smem(k_chk_tma<L, 8, true, true>, sm); set_smem(k_chk_tma<L, 8, false, true>, sm);
+    const size_t sp = TmaGeo<L, 8>::bytes_pw;
+    set_smem(k_chk_tma<L, 8, true>, TmaGeo<L, 8>::bytes); set_smem(k_chk_tma<L, 8, false>, TmaGeo<L, 8>::bytes);
+    set_smem(k_chk_tma<L, 8, true, true>, sp); set_smem(k_chk_tma<L, 8, false, true>, sp);
     return;
   }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk", 32, L, s);
@@ -622,7 +625,7 @@ struct CL {
   static void go(int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
     if (a.pw_f || g_pw_sel) {
       if constexpr (sizeof(T) == 4 && tma_ok<L>()) {
-        if (w < 0 && a.tm_chk && !g_dry) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
+        if (w < 0 && a.tm_chk && a.tm_pw && !g_dry) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
       }
       launch_chk_tw<T, L, TileW<T>::value, true>(a, Nmid, M, count, s);
       return;
@@ -786,6 +789,26 @@ void build_tensor_maps(ffcz_plan_s* p) {
   }
 }
 
+// Pointwise plans: the check pass's [Nz][Nmid M] view of the packed f-bounds
+// of every member (same boxes as the spectrum maps), where that pass has a
+// TMA-fed kernel.
+void build_pw_maps(ffcz_plan_s* p) {
+  for (auto& dg : p->groups) {
+    if (dg.ndim == 1 || !dg.tm_chk) continue;
+    const int Nmid = dg.ndim == 3 ? dg.Ny : 1;
+    std::vector<CUtensorMap> maps((size_t)dg.count);
+    bool ok = true;
+    for (int gi = 0; gi < dg.count && ok; ++gi) {
+      const char* base = reinterpret_cast<const char*>(p->pw_fp) + dg.h_soff[gi] * 8;
+      ok = encode_2d(&maps[gi], base, (uint64_t)Nmid * dg.M, (uint64_t)dg.Nz, 8, (uint32_t)std::min(dg.Nz, 256));
+    }
+    if (!ok) continue;
+    void* d = dalloc(p, sizeof(CUtensorMap) * maps.size());
+    CK(cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+    dg.tm_pw = static_cast<const CUtensorMap*>(d);
+  }
+}
+
 template <typename T>
 Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState* st) {
   Args a{};
@@ -812,6 +835,7 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   if (sizeof(T) == 4 && b0 == p->B32[0] && b1 == p->B32[1]) {
     a.tm_axis = dg.tm_axis;
     a.tm_chk = dg.tm_chk;
+    if (p->opts.pointwise) a.tm_pw = dg.tm_pw;
   }
   if (sizeof(T) == 4 && p->pv_on) {
     a.pv = p->opts.method;
@@ -2102,8 +2126,8 @@ void tune(ffcz_plan_s* p) {
   cudaStream_t s = p->stream;
   for (auto& dg : p->groups) {
     char base[160];
-    snprintf(base, sizeof base, "d%d_z%d_y%d_x%d_n%d_c%d", dg.ndim, dg.Nz, dg.Ny, dg.Nx, dg.P1,
-             dg.count);
+    snprintf(base, sizeof base, "d%d_z%d_y%d_x%d_n%d_c%d_pw%d", dg.ndim, dg.Nz, dg.Ny, dg.Nx, dg.P1,
+             dg.count, p->opts.pointwise ? 1 : 0);
     Args a = make_args<float>(p, dg, p->B32[0], p->B32[1], p->d_st);
     a.pred = P_ALL;
     if (dg.ndim == 1) {
@@ -2451,6 +2475,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       p->pw_e = (float*)dalloc(p.get(), sizeof(float) * p->total);
       p->pw_f = (float2*)dalloc(p.get(), sizeof(float2) * p->ed_total[1]);
       p->pw_fp = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
+      build_pw_maps(p.get());
       p->pw_f0 = (float4*)dalloc(p.get(), sizeof(float4) * p->total_rows);
       p->pw_min = (unsigned int*)dalloc(p.get(), sizeof(unsigned int) * batch);
       p->pw_bad = (int*)dalloc(p.get(), sizeof(int));

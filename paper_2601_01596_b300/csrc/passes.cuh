@@ -28,6 +28,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "tma.cuh"
 
@@ -108,6 +110,9 @@ struct Args {
   // not the plan's float32 pair
   const CUtensorMap* tm_axis;
   const CUtensorMap* tm_chk;
+  // the same view of the packed pointwise f-bounds (pw_f), one per group
+  // member (null: the check pass reads them with plain loads)
+  const CUtensorMap* tm_pw;
   int* err;                // device error word (DevErr)
   // Alg. 1 edit recording (null: off).  ed_s: spatial edits, float32 laid
   // out like e.  Frequency edits in the packed spectrum layout: ed_f the
@@ -315,11 +320,19 @@ __device__ __forceinline__ bool nan_probe(const v2<T> (&v)[V]) {
   return (v[0].x != v[0].x) | (v[V - 1].y != v[V - 1].y);
 }
 
-// x / b for the normalised violations of pointwise bounds (b > 0): float32
-// as x times the correctly rounded reciprocal (two roundings instead of an
-// IEEE division sequence per value; the ratio only decides when the float32
-// loop stops, the FP64 certification checks the bounds themselves).
-__device__ __forceinline__ float ratioT(float x, float b) { return x * __frcp_rn(b); }
+// x / b for the normalised violations of pointwise bounds: float32 as x
+// times the approximate reciprocal of PTX (rcp.approx.ftz.f32, within about
+// one ulp of 1/b for the normal bounds the library accepts, FLT_MIN <= b;
+// above 2^126 the reciprocal flushes to zero, so such a bin reads as inside
+// unless |x| exceeds 2^126).  The ratio only decides when the float32 loop
+// stops; the FP64 certification checks the bounds themselves.  A correctly
+// rounded reciprocal, or one that keeps subnormals, is a multi-instruction
+// sequence per value: at 512^3 it cost 0.16-0.19 ms per pass.
+__device__ __forceinline__ float ratioT(float x, float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return x * r;
+}
 __device__ __forceinline__ double ratioT(double x, double b) { return x / b; }
 
 __device__ __forceinline__ float clampT(float x, float b) { return fminf(fmaxf(x, -b), b); }
@@ -897,9 +910,18 @@ __device__ __forceinline__ void pw_pencil(const Args& a, int gi, const ChkTile& 
   }
 }
 
+// Source of the pointwise bounds in chk_core: by default they are read from
+// global memory into registers before the forward transform; a caller that
+// stages them in shared memory passes a functor with late = true, called
+// after the forward transform, which waits until the staged bounds landed.
+struct QEarly {
+  static constexpr bool late = false;
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // FULL = false compiles out the adjoint mask modes and the edit recording
 // (the forward loop's lean variant: less code, no mask-bit bookkeeping).
-template <typename T, int L, class TL, bool PW = false, int PV = PV_POCS, bool FULL = true>
+template <typename T, int L, class TL, bool PW = false, int PV = PV_POCS, bool FULL = true, class QW = QEarly>
 __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, ItemState& st,
                                          v2<T> (&v)[F2<L>::V], int j, int w, int64_t mthr,
                                          const ChkTile& c, bool cta_has_mirror, TL& tl,
@@ -907,18 +929,25 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
                                          unsigned long long* acc_vb = nullptr,
                                          unsigned long long* acc_cnt = nullptr,
                                          int64_t ed_slot0 = 0, int64_t ed_ustride = 0, int t_chk = 0,
-                                         const float2* pwb = nullptr, int64_t pws = 0, int pwM = 0) {
+                                         const float2* pwb = nullptr, int64_t pws = 0, int pwM = 0,
+                                         QW qwait = QW{}) {
   // pwb: pointwise (Delta^Re, Delta^Im) of this pencil's bin at kz = 0, pws
   // the step per kz; on mirror tiles pwb holds the bounds of A and pwb + pwM
   // those of B
   constexpr int NT = F2<L>::NT, V = F2<L>::V, MW = (V + 7) / 8;
   // pointwise bounds of the thread's bins, loaded before the forward
-  // transform so that their latency hides behind it
-  float2 qb[PW ? V : 1];
-  if constexpr (PW) {
+  // transform so that their latency hides behind it (or, staged in shared
+  // memory, read where they are used)
+  constexpr bool QLATE = PW && QW::late;
+  float2 qb[(PW && !QLATE) ? V : 1];
+  if constexpr (PW && !QLATE) {
 #pragma unroll
     for (int u = 0; u < V; ++u) qb[u] = pwb[(int64_t)(j + u * NT) * pws];
   }
+  auto qbound = [&](int u) -> float2 {
+    if constexpr (QLATE) return pwb[(int64_t)(j + u * NT) * pws];
+    else return qb[PW ? u : 0];
+  };
   // Dykstra / Douglas-Rachford: the residual r of the previous frequency
   // projection (zero before the first one), loaded before the transform
   constexpr bool RES = (PV == PV_DYKSTRA || PV == PV_DR);
@@ -929,6 +958,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
     for (int u = 0; u < V; ++u) rr[u] = res_in ? a.pv_r[ed_slot0 + u * ed_ustride] : make_float2(0.f, 0.f);
   }
   fft_pencil<T, L, -1>(v, j, twg, tl);
+  if constexpr (QLATE) qwait();
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
   AbsMax<T> mx;
   bool bad = false;
@@ -994,7 +1024,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
         T bar = T(1), bai = T(1), bbr = T(1), bbi = T(1);   // pointwise bounds (ratios)
         if constexpr (PW) {
           const float2 qB = pwb[(int64_t)(j + u * NT) * pws + pwM];
-          bar = (T)qb[u].x; bai = (T)qb[u].y; bbr = (T)qB.x; bbi = (T)qB.y;
+          const float2 qA = qbound(u);
+          bar = (T)qA.x; bai = (T)qA.y; bbr = (T)qB.x; bbi = (T)qB.y;
         }
         if (c.valid) {
           if constexpr (PW) { mx.add(ratioT(ar, bar)); mx.add(ratioT(ai, bai)); mx.add(ratioT(br, bbr)); mx.add(ratioT(bi, bbi)); }
@@ -1038,7 +1069,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   AbsMax<T> tm;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
-    if constexpr (PW) { tm.add(ratioT(v[u].x, (T)qb[u].x)); tm.add(ratioT(v[u].y, (T)qb[u].y)); }
+    if constexpr (PW) {
+      const float2 q = qbound(u);
+      tm.add(ratioT(v[u].x, (T)q.x)); tm.add(ratioT(v[u].y, (T)q.y));
+    }
     else { tm.add(v[u].x); tm.add(v[u].y); }
   }
   const bool need_clip = __any_sync(0xffffffffu, !c.mirror && tm.val() > Ds);
@@ -1069,7 +1103,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
       for (int u = 0; u < V; ++u) {
         const T x = v[u].x, y = v[u].y;
         T qx = T(1), qy = T(1);
-        if constexpr (PW) { qx = (T)qb[u].x; qy = (T)qb[u].y; }
+        if constexpr (PW) { const float2 q = qbound(u); qx = (T)q.x; qy = (T)q.y; }
         const T cx = clampT(x, PW ? Ds * qx : Ds), cy = clampT(y, PW ? Ds * qy : Ds);
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
@@ -1155,9 +1189,11 @@ struct TmaGeo {
   static constexpr size_t stage = (size_t)L * W * sizeof(float2);
   static constexpr size_t bytes =
       128 + stage + (size_t)Tile<float, L, W>::ELEMS * sizeof(float2) + (size_t)L * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
+  // the pointwise check pass stages the tile's f-bounds as well
+  static constexpr size_t bytes_pw = bytes + stage;
 };
 
-#define FFCZ_TMA_PROLOGUE(L_, W_)                                                        \
+#define FFCZ_TMA_PROLOGUE(L_, W_, EXTRA_)                                                \
   using G_ = Geo<float, L_, W_>;                                                         \
   using TL = Tile<float, L_, W_>;                                                        \
   using TG = TmaGeo<L_, W_>;                                                             \
@@ -1165,7 +1201,7 @@ struct TmaGeo {
   extern __shared__ __align__(16) unsigned char smraw[];                                 \
   const uint32_t s0_ = smem_addr(smraw);   /* staging rounded up to 128 bytes below */   \
   float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0_ + 127u) & ~127u) - s0_));  \
-  float2* s_tiles = s_stage + L_ * W_;                                                   \
+  float2* s_tiles = s_stage + L_ * W_ + (EXTRA_); /* EXTRA_: a second staging buffer */ \
   float2* s_tw = s_tiles + TL::ELEMS;                                                    \
   unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_tw + L_);         \
   __shared__ __align__(8) uint64_t bar;                                                  \
@@ -1188,13 +1224,15 @@ struct TmaGeo {
   (void)p; (void)NT; (void)s_red;
 
 // Wait for the staging buffer, copy it to registers, release it and start
-// the load of the next tile.  Returns false (uniformly) after a timeout.
-#define FFCZ_TMA_TAKE(ISSUE_NEXT)                                                        \
+// the load of the next tile.  After a timeout: DRAIN (waits for the caller's
+// other copies in flight), then return (uniformly).
+#define FFCZ_TMA_TAKE(ISSUE_NEXT, DRAIN)                                                 \
   {                                                                                      \
     const bool ok_ = mbar_wait_bounded(&bar, parity, kTmaPollLimit);                     \
     if (__syncthreads_or(!ok_)) {                                                        \
       if (tid == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);                                 \
       mbar_wait_bounded(&bar, parity, kTmaPollLimit); /* copies still in flight */       \
+      DRAIN;                                                                             \
       return;                                                                            \
     }                                                                                    \
     _Pragma("unroll") for (int u = 0; u < V; ++u) v[u] = s_stage[(j + u * NT) * W + w]; \
@@ -1206,7 +1244,7 @@ struct TmaGeo {
 template <int L, int DIR, int W>
 __global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
 k_axis_tma(Args a) {
-  FFCZ_TMA_PROLOGUE(L, W)
+  FFCZ_TMA_PROLOGUE(L, W, 0)
   const int M = a.g.M;
   const int tpr = M / W;
   const int ntiles = a.g.Nz * tpr;
@@ -1224,7 +1262,7 @@ k_axis_tma(Args a) {
   while (tile < ntiles) {
     const int next = tile + gridDim.x;
     float2 v[V];
-    FFCZ_TMA_TAKE(if (next < ntiles) { fence_proxy_async_smem(); issue(next); })
+    FFCZ_TMA_TAKE(if (next < ntiles) { fence_proxy_async_smem(); issue(next); }, (void)0)
     TL tl{s_tiles + w, false};
     fft_pencil<float, L, DIR>(v, j, s_tw, tl);
     const int z = tile / tpr, kx = (tile % tpr) * W + w;
@@ -1236,10 +1274,24 @@ k_axis_tma(Args a) {
   }
 }
 
+// Pointwise bounds staged in shared memory by the copy engine: chk_core
+// waits (bounded) for the tile's load after its forward transform; a
+// timeout raises *late_flag, on which the caller stops.
+struct QStaged {
+  static constexpr bool late = true;
+  uint64_t* b;
+  uint32_t par;
+  bool on;
+  bool* late_flag;
+  __device__ __forceinline__ void operator()() const {
+    if (on && !mbar_wait_bounded(b, par, kTmaPollLimit)) *late_flag = true;
+  }
+};
+
 template <int L, int W, bool FULL = true, bool PW = false>
 __global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
 k_chk_tma(Args a) {
-  FFCZ_TMA_PROLOGUE(L, W)
+  FFCZ_TMA_PROLOGUE(L, W, PW ? L * W : 0)
   const int M = a.g.M, Nmid = a.g.Nmid;
   const int tpr = M / W;
   const int nmain = Nmid * tpr;
@@ -1253,8 +1305,28 @@ k_chk_tma(Args a) {
 #pragma unroll
     for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_stage + b * TG::BOX * W, map, x, b * TG::BOX, &bar);
   };
+  // pointwise: the f-bounds of a main tile go to their own staging buffer
+  // (same view of pw_f), loaded once the previous tile has used its bounds,
+  // and waited for after the forward transform
+  float2* s_pw = s_stage + L * W;
+  __shared__ __align__(8) uint64_t bar_pw;
+  uint32_t par_pw = 0;
+  bool pw_late = false;   // a wait for the staged bounds ran out
+  auto issue_pw = [&](int t) {
+    const int x = (t / tpr) * M + (t % tpr) * W;
+    mbar_arrive_expect_tx(&bar_pw, (uint32_t)TG::stage);
+#pragma unroll
+    for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_pw + b * TG::BOX * W, a.tm_pw + gi, x, b * TG::BOX, &bar_pw);
+  };
+  if constexpr (PW) {
+    if (tid == 0) mbar_init(&bar_pw, 1);
+    __syncthreads();
+  }
   int tile = blockIdx.x;
-  if (tid == 0 && tile < nmain) issue(tile);
+  if (tid == 0 && tile < nmain) {
+    issue(tile);
+    if constexpr (PW) issue_pw(tile);
+  }
   const float2* inb = pick<float>(a, a.sel_in, t_it) + a.g.soff[gi];
   float2* outb = pick<float>(a, a.sel_out, t_it) + a.g.soff[gi];
   unsigned long long acc_vb = 0ull, acc_cnt = 0ull;
@@ -1263,7 +1335,8 @@ k_chk_tma(Args a) {
     const ChkTile c = chk_decode<W>(tile, w, M, Nmid);
     float2 v[V];
     if (tile < nmain) {
-      FFCZ_TMA_TAKE(if (next < nmain) { fence_proxy_async_smem(); issue(next); })
+      FFCZ_TMA_TAKE(if (next < nmain) { fence_proxy_async_smem(); issue(next); },
+                    if (PW) mbar_wait_bounded(&bar_pw, par_pw, kTmaPollLimit))
     } else {
       // kx = 0 mirror pencils are not one box: plain loads
       const float2* in = inb + c.off + j * estride;
@@ -1274,16 +1347,37 @@ k_chk_tma(Args a) {
     const int64_t mthr = (int64_t)tile * G_::TPT + tid;
     const float2* pwb = nullptr;
     int64_t pws = 0;
-    if constexpr (PW) pw_pencil(a, gi, c, M, Nmid, estride, pwb, pws);
-    chk_core<float, L, TL, PW, PV_POCS, FULL>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
-                                              &acc_vb, &acc_cnt, a.g.soff[gi] + c.off + j * estride,
-                                              (int64_t)NT * estride, t_it, pwb, pws, 1);
+    const bool main_tile = tile < nmain;
+    if constexpr (PW) {
+      if (main_tile) { pwb = s_pw + w; pws = W; }
+      else pw_pencil(a, gi, c, M, Nmid, estride, pwb, pws);
+    }
+    using QW = typename std::conditional<PW, QStaged, QEarly>::type;
+    QW qw{};
+    if constexpr (PW) qw = QStaged{&bar_pw, par_pw, main_tile, &pw_late};
+    chk_core<float, L, TL, PW, PV_POCS, FULL, QW>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
+                                                  &acc_vb, &acc_cnt, a.g.soff[gi] + c.off + j * estride,
+                                                  (int64_t)NT * estride, t_it, pwb, pws, 1, qw);
     if (!(a.mode & M_NOWRITE) && c.owner) {
       float2* out = outb + c.off + j * estride;
 #pragma unroll
       for (int u = 0; u < V; ++u) out[(int64_t)u * NT * estride] = v[u];
     }
-    __syncthreads();   // the tile buffer is reused by the next tile
+    if constexpr (PW) {
+      // the tile buffer and the bounds staging are reused by the next tile
+      if (__syncthreads_or(pw_late)) {
+        if (tid == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);
+        mbar_wait_bounded(&bar_pw, par_pw, kTmaPollLimit);                   // copies still in flight
+        if (main_tile && next < nmain) mbar_wait_bounded(&bar, parity, kTmaPollLimit);
+        return;
+      }
+      if (main_tile) {
+        par_pw ^= 1u;
+        if (tid == 0 && next < nmain) { fence_proxy_async_smem(); issue_pw(next); }
+      }
+    } else {
+      __syncthreads();   // the tile buffer is reused by the next tile
+    }
     tile = next;
   }
   if (!(a.mode & M_MASK)) {
@@ -1450,11 +1544,11 @@ static __global__ void k_pw_check(Group g, const float* pw_e, const float2* pw_f
   float mn = INFINITY;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npt; i += (int64_t)gridDim.x * blockDim.x) {
     const float v = eb[i];
-    nbad += !(v > 0.f && v <= FLT_MAX);
+    nbad += !(v >= FLT_MIN && v <= FLT_MAX);   // normal, finite, positive
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
     const float2 q = fb[i];
-    nbad += !(q.x > 0.f && q.x <= FLT_MAX) + !(q.y > 0.f && q.y <= FLT_MAX);
+    nbad += !(q.x >= FLT_MIN && q.x <= FLT_MAX) + !(q.y >= FLT_MIN && q.y <= FLT_MAX);
     mn = fminf(mn, fminf(q.x, q.y));
   }
   for (int o = 16; o > 0; o >>= 1) {

@@ -89,6 +89,17 @@ def test_invalid_bounds_and_scalar_calls_are_refused():
     E_n = np.ones(shape); E_n[3, 4] = 0.0
     with pytest.raises(ffcz.FFCzError):
         run_pw(e0, E_n, np.ones(shape), np.ones(shape))
+    # subnormal bounds (below FLT_MIN) are refused too, spatial and frequency
+    E_n[3, 4] = 1e-39
+    with pytest.raises(ffcz.FFCzError):
+        run_pw(e0, E_n, np.ones(shape), np.ones(shape))
+    D_im = np.ones(shape); D_im[0, 5] = D_im[0, -5] = 1e-40
+    with pytest.raises(ffcz.FFCzError):
+        run_pw(e0, np.ones(shape), np.ones(shape), D_im)
+    # the smallest and largest normal bounds are accepted
+    e, st = run_pw(e0, np.full(shape, np.finfo(np.float32).tiny), np.ones(shape),
+                   np.full(shape, np.finfo(np.float32).max))
+    assert st[0]["status"] == 0 and st[0]["certified"] == 1 and np.array_equal(e, e0)
     plan = ffcz.Plan([shape], pointwise=1)
     with pytest.raises(ffcz.FFCzError):
         plan.correct(torch.zeros(32 * 32, device="cuda"), [1.0], [1.0])
@@ -133,3 +144,54 @@ def test_power_spectrum_mode_end_to_end():
     assert np.max(rel) <= rho * (1 + 1e-3)
     P_base = O.power_spectrum(x.astype(np.float64) + e0, mean=float(np.mean(x.astype(np.float64))))
     assert np.max(np.abs(P_base[1:] - P[1:]) / P[1:]) > rho     # the base error did violate it
+
+
+def _pw_case(shape, seed, frac=0.3):
+    """Varying E_n and (Delta^Re, Delta^Im) (even in k), the f-clip active."""
+    r = np.random.default_rng(seed)
+    E_n = 0.5 + r.random(shape)
+    e0 = (r.uniform(-1, 1, shape) * E_n).astype(np.float32)
+    D_re, D_im = _even(0.5 + r.random(shape)), _even(0.5 + r.random(shape))
+    scale = frac * O.f_ratio_pw(O.dft(e0.astype(np.float64)), D_re, D_im)
+    return e0, E_n, D_re * scale, D_im * scale
+
+
+@pytest.mark.parametrize("shape", [(256, 32, 32), (256, 64), (512, 16, 32)])
+def test_tma_fed_pointwise_check_equals_plain_and_matches_oracle(shape, monkeypatch):
+    """The persistent check pass stages each tile's f-bounds in shared memory
+    by the copy engine; the tiled pass reads them from global memory.  Same
+    arithmetic: bit-identical results; and both match the FP64 oracle."""
+    e0, E_n, D_re, D_im = _pw_case(shape, 93)
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,px=tma,chk=tma")
+    a, sa = run_pw(e0, E_n, D_re, D_im)
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,px=tma,chk=8")
+    b, sb = run_pw(e0, E_n, D_re, D_im)
+    monkeypatch.delenv("FFCZ_TUNE_FORCE")
+    assert sa[0]["iters"] == sb[0]["iters"] >= 2 and sa[0]["certified"] == 1
+    assert np.array_equal(a, b)
+    ref = O.correct(e0, E_n, (D_re, D_im))
+    assert abs(sa[0]["iters"] - ref.iters) <= 2
+    same = O.correct(e0, E_n, (D_re, D_im), min_iters=sa[0]["iters"], max_iters=sa[0]["iters"])
+    np.testing.assert_allclose(a, same.e, rtol=0, atol=1e-3 * E_n.min())
+
+
+def test_tma_fed_pointwise_batch_equals_singles(monkeypatch):
+    """Every member of a batch has its own map of the packed f-bounds."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,px=tma,chk=tma")
+    shapes = [(256, 16, 32), (256, 32, 16), (256, 16, 32)]
+    cases = [_pw_case(sh, 100 + i, frac=0.25 + 0.1 * i) for i, sh in enumerate(shapes)]
+    plan = ffcz.Plan(shapes, pointwise=1)
+    t = torch.from_numpy(np.concatenate([c[0].reshape(-1) for c in cases])).cuda()
+    eb = torch.from_numpy(np.concatenate([c[1].reshape(-1) for c in cases]).astype(np.float32)).cuda()
+    half = np.concatenate([O.half_spectrum(c[2] + 1j * c[3]).reshape(-1) for c in cases]).astype(np.complex64)
+    st = plan.correct_pw(t, eb, torch.from_numpy(half).cuda())
+    out = t.cpu().numpy()
+    off = 0
+    for i, (sh, c) in enumerate(zip(shapes, cases)):
+        n = int(np.prod(sh))
+        single, s1 = run_pw(*c)
+        assert st[i]["iters"] == s1[0]["iters"] >= 2 and st[i]["certified"] == 1, i
+        assert np.array_equal(out[off:off + n], single.reshape(-1)), f"item {i}"
+        off += n
