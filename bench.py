@@ -754,12 +754,13 @@ def main():
     src = h_e0.numpy()
     np.copyto(hw, src)
     plan.correct_host(hw, [E], [D])
-    e2e_t = []
+    e2e_t, e2e_copies = [], []
     for _ in range(args.steps):
         np.copyto(hw, src)
         t0 = time.perf_counter()
-        plan.correct_host(hw, [E], [D])
+        sth = plan.correct_host(hw, [E], [D])
         e2e_t.append(time.perf_counter() - t0)
+        e2e_copies.append(sth[0]["host_copies"])
     e2e_ms = 1e3 * float(np.mean(e2e_t))
     e2e_ms_t = torch.tensor([e2e_ms], device="cuda")
     if dist:
@@ -791,7 +792,8 @@ def main():
                    "step": "ffcz_correct (loop + FP64 certification), e0 resident in HBM",
                    "variants": plan_desc},
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": field_bytes + 64,
-                "d2h_bytes_per_step": field_bytes + 4 + 160},
+                "d2h_bytes_per_step": int(round(field_bytes * float(np.mean(e2e_copies)))) + 4 + 160,
+                "field_copies_back": float(np.mean(e2e_copies))},
         "roofline": roof,
         "per_iteration": {"ms": round(it_ms, 4), "body_kernels_ms": round(body_ms, 4),
                           "design_bytes": design, "passes": passes,

@@ -103,7 +103,9 @@ typedef struct {
   int32_t repairs;     /* FP64 repair rounds run */
   int32_t certified;   /* 1 if the FP64 check passed against the true bounds */
   int32_t preclipped;  /* 1 if e0 was outside the s-cube and was clipped first */
-  int32_t pad_;
+  int32_t host_copies; /* ffcz_correct_host: copies of the field back to
+                          e_host (0 when the field came out unchanged, the
+                          host buffer already holding the result); else 0 */
   double f_ratio;      /* last loop violation / eps_f (working precision);
                           method 3 after >= 1 iteration: max|a_t| / eps_s,
                           its stopping measure */
@@ -281,10 +283,14 @@ ffcz_status ffcz_correct(ffcz_plan_t plan, float* e_dev, const double* eps_s,
  * single-item 2D/3D plans the upload runs in row chunks while the FP64
  * certification's x pass processes the chunks already on the device; when
  * the loop stops at 0 iterations without a pre-clip (the field unchanged)
- * the certification continues from that pass, else it runs in full.  The
+ * the certification continues from that pass, else it runs in full (3D
+ * items: the y pass of the certification runs on each chunk of whole
+ * z-planes too).  A field that comes out of the loop unchanged (0 iterations,
+ * no pre-clip) is not copied back: e_host already holds it.  Otherwise the
  * copy back starts on a second stream as soon as the loop is done, while the
  * FP64 certification (which only reads the field) runs; if a repair round
  * changes the field, it waits for that copy and copies the field again.
+ * stats.host_copies counts the copies back.
  */
 ffcz_status ffcz_correct_host(ffcz_plan_t plan, float* e_host, const double* eps_s,
                               const double* eps_f, ffcz_stats* stats);

@@ -50,14 +50,14 @@ METHODS = {"pocs": 0, "dykstra": 1, "dr": 2, "douglas_rachford": 2, "admm": 3}
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("repairs", ctypes.c_int32), ("certified", ctypes.c_int32),
-                ("preclipped", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("preclipped", ctypes.c_int32), ("host_copies", ctypes.c_int32),
                 ("f_ratio", ctypes.c_double), ("s_ratio", ctypes.c_double),
                 ("f_margin64", ctypes.c_double), ("s_margin64", ctypes.c_double),
                 ("active_s", ctypes.c_int64), ("active_f", ctypes.c_int64),
                 ("ms_total", ctypes.c_float), ("ms_cert", ctypes.c_float)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class StatsList(collections.abc.Sequence):

@@ -17,6 +17,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -144,12 +145,14 @@ struct ffcz_plan_s {
   cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
   cudaStream_t copy_stream = nullptr;  // host-buffer entry point: copy-back stream
   cudaEvent_t ev_copy = nullptr;
-  // host-buffer entry point: the upload in row chunks and the FP64 x pass on
-  // each chunk as it lands (spec_stream), into a side state d_stc
+  // host-buffer entry point: the upload in row chunks and the FP64 x pass
+  // (3D: and y pass) on each chunk as it lands (spec_stream), into a side
+  // state d_stc; spec_y: the y pass ran too
   cudaStream_t spec_stream = nullptr;
   std::vector<cudaEvent_t> ev_chunks;
   cudaEvent_t ev_spec = nullptr;
   ItemState* d_stc = nullptr;
+  bool spec_y = false;
   int device = 0;
 
   std::vector<DevGroup> groups;
@@ -570,6 +573,7 @@ void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   g_launches++;
 }
 
+constexpr int kAxisW64 = 4;   // tile width of the FP64 y pass
 template <typename T, int DIR>
 struct AL {
   template <int L>
@@ -581,7 +585,7 @@ struct AL {
       if (w == 4) launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
       else launch_axis_tw<T, L, DIR, 8>(a, Nz, M, count, s);
     } else {
-      launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
+      launch_axis_tw<T, L, DIR, kAxisW64>(a, Nz, M, count, s);
     }
   }
 };
@@ -1470,8 +1474,10 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
 }
 
 // st: the state the certification reads and writes (default the loop's);
-// x_done: the x pass already ran into the FP64 buffer (host entry point).
-void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = nullptr, bool x_done = false) {
+// x_done / y_done: the x pass (and the y pass) already ran into the FP64
+// buffer (host entry point).
+void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = nullptr, bool x_done = false,
+             bool y_done = false) {
   ItemState* S = st ? st : p->d_st;
   if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total_c * sizeof(double2));
   if (p->ndim == 1 && !p->Bt64) build_bt<double>(p);
@@ -1497,7 +1503,7 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = 
     a.e = const_cast<float*>(e);
     a.mode = M_MEASURE;
     if (!x_done) launch_x<double>(XCERT, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
-    if (dg.ndim == 3) {
+    if (dg.ndim == 3 && !y_done) {
       a.tw = tw_of<double>(p->tb, dg.Ny);
       a.mode = 0;
       launch_axis<double, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
@@ -1682,8 +1688,10 @@ void pw_prepare(ffcz_plan_s* p) {
 // Host-buffer entry point: upload the field in chunks of whole CTA rows on
 // the copy stream and run the FP64 certification's x pass on each chunk as
 // it lands (on a third stream, into the FP64 buffer and the side state
-// d_stc), so the transfer hides most of that pass.  The loop's stream waits
-// for the last chunk only.  Single-item 2D/3D plans with certification.
+// d_stc), so the transfer hides most of that pass; for 3D items the chunks
+// are whole z-planes and the certification's y pass runs on each as well.
+// The loop's stream waits for the last chunk only.  Single-item 2D/3D plans
+// with certification.
 bool spec_upload(ffcz_plan_s* p, float* e_dev, const float* host) {
   if (p->batch != 1 || p->ndim < 2 || !p->opts.certify || p->opts.pointwise) return false;
   const DevGroup& dg = p->groups[0];
@@ -1709,7 +1717,9 @@ bool spec_upload(ffcz_plan_s* p, float* e_dev, const float* host) {
   // rows of one CTA of the FP64 x pass (tiles of row_w1(M) rows, G per CTA)
   const int W = row_w1(dg.M), tpt = f2_nt(dg.M) * W, rpc = (tpt >= 128 ? 1 : 128 / tpt) * W;
   const int64_t rows = dg.rows, Nx = 2 * (int64_t)dg.M;
-  const int64_t crow = ((rows + K - 1) / K + rpc - 1) / rpc * rpc;
+  const int64_t unit = dg.ndim == 3 ? std::lcm((int64_t)rpc, (int64_t)dg.Ny) : rpc;
+  const int64_t crow = ((rows + K - 1) / K + unit - 1) / unit * unit;
+  const int tpr_y = dg.M / kAxisW64;   // y-pass tiles per z-plane
   int c = 0;
   for (int64_t r0 = 0; r0 < rows; r0 += crow, ++c) {
     const int64_t nr = std::min(crow, rows - r0);
@@ -1724,7 +1734,16 @@ bool spec_upload(ffcz_plan_s* p, float* e_dev, const float* host) {
     a.mode = M_MEASURE;
     a.tile0 = (int)(r0 / W);
     launch_x<double>(XCERT, dg.M, dg.wx, a, nr, 1, p->spec_stream);
+    if (dg.ndim == 3) {   // planes z0 .. z1 - 1
+      const int z0 = (int)(r0 / dg.Ny), z1 = (int)((r0 + nr) / dg.Ny);
+      a.tw = tw_of<double>(p->tb, dg.Ny);
+      a.mode = 0;
+      a.tile0 = z0 * tpr_y;
+      a.tile1 = z1 * tpr_y;
+      launch_axis<double, -1>(dg.Ny, dg.wa, a, z1 - z0, dg.M, 1, p->spec_stream);
+    }
   }
+  p->spec_y = dg.ndim == 3;
   CK(cudaEventRecord(p->ev_spec, p->spec_stream));
   CK(cudaStreamWaitEvent(p->stream, p->ev_chunks[c - 1], 0));   // the loop needs the whole field
   return true;
@@ -1739,7 +1758,7 @@ bool spec_adopt(ffcz_plan_s* p, const float* e) {
   CK(cudaStreamSynchronize(p->stream));
   for (int64_t i = 0; i < p->batch; ++i)
     if (p->h_st[i].t != 0 || p->h_st[i].preclip || p->h_st[i].status != 0) return false;
-  certify(p, e, false, p->d_stc, true);
+  certify(p, e, false, p->d_stc, true, p->spec_y);
   k_cert_adopt<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, p->d_stc, (int)p->batch);
   g_launches++;
   return true;
@@ -1763,12 +1782,17 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
   else run_loop<float>(p, e, false);
   CK(cudaEventRecord(p->ev1, p->stream));
   bool cert = p->opts.certify != 0;
-  if (cert && !(spec_x && spec_adopt(p, e))) {
+  // adopted: the loop left the uploaded field unchanged (0 iterations, no
+  // pre-clip), so the host buffer already holds the result
+  const bool adopted = cert && spec_x && spec_adopt(p, e);
+  if (cert && !adopted) {
     cert_reset(p);
     certify(p, e, false);
   }
   bool recopy = false;
-  if (host_out) {
+  int copies = 0;
+  if (host_out && !adopted) {
+    copies = 1;
     if (!p->copy_stream) {
       CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&p->ev_copy, cudaEventDisableTiming));
@@ -1803,14 +1827,18 @@ ffcz_status correct_impl(ffcz_plan_s* p, float* e, const double* eps_s, const do
   CK(cudaEventRecord(p->ev2, p->stream));
   CK(cudaEventSynchronize(p->ev2));
   if (host_out) {
-    if (recopy)
+    if (recopy) {
       CK(cudaMemcpyAsync(host_out, e, sizeof(float) * p->total, cudaMemcpyDeviceToHost, p->stream));
+      ++copies;
+    }
     CK(cudaStreamSynchronize(recopy ? p->stream : p->copy_stream));
   }
   float ms = 0.f, ms_c = 0.f;
   CK(cudaEventElapsedTime(&ms, p->ev0, p->ev2));
   CK(cudaEventElapsedTime(&ms_c, p->ev1, p->ev2));
   fill_stats(p, stats, ms, cert ? ms_c : 0.f, cert);
+  if (stats)
+    for (int64_t i = 0; i < p->batch; ++i) stats[i].host_copies = copies;
   CK(cudaGetLastError());
   return worst_status(p, cert);
 }

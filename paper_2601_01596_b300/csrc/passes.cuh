@@ -138,8 +138,10 @@ struct Args {
   int pv;
   float2* pv_r;
   float* pv_q[2];
-  // first tile of a launch of the plain x passes (0: all rows)
+  // first tile of a launch of the plain x and y passes (0: all rows), and
+  // for the y pass the end of its tile range (0: all planes)
   int tile0;
+  int tile1;
 };
 
 // Spatial edit of one complex register (two real points): S += (c - v).
@@ -811,7 +813,7 @@ k_xexit(Args a) {
   const int t_it = st.t;                                                          \
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
   const int w = tid % G_::W, j = tid / G_::W;                                     \
-  const int tile = blockIdx.x * G_::G + g;                                        \
+  const int tile = a.tile0 + blockIdx.x * G_::G + g;                              \
   const int64_t mthr = (int64_t)tile * G_::TPT + tid;                             \
   TL tl{s_tiles + g * TL::ELEMS + w, false};                                      \
   (void)mthr;
@@ -823,7 +825,7 @@ k_axis(Args a) {
   FFCZ_AXIS_PROLOGUE(T, L, W)
   const int M = a.g.M;
   const unsigned tpr = (unsigned)(M / G_::W);     // tiles per z-plane
-  const int ntiles = a.g.Nz * (int)tpr;
+  const int ntiles = a.tile1 ? a.tile1 : a.g.Nz * (int)tpr;
   const bool live = tile < ntiles;
   const int z = live ? (int)((unsigned)tile / tpr) : 0;
   const int kx = live ? (int)((unsigned)tile % tpr) * G_::W + w : 0;

@@ -124,13 +124,15 @@ def test_fp64_repair_after_a_failed_certification():
     plan = ffcz.Plan([e0.shape], max_iters=cap)
     sth = plan.correct_host(host, [E], [D])[0]
     assert sth["repairs"] == st["repairs"] and np.array_equal(host, e.reshape(-1))
+    assert sth["host_copies"] >= 1
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (16, 16, 64), (64, 8, 16), (8, 256, 32)])
 def test_host_entry_certification_from_the_upload_matches_device(shape):
-    """At 0 iterations the host entry point certifies from the x pass it ran
-    while uploading: same bits out, certified, the same FP64 margins as the
-    device entry point (up to the summation order of the norm)."""
+    """At 0 iterations the host entry point certifies from the x pass (3D:
+    and y pass, chunks of whole z-planes) it ran while uploading: same bits
+    out, no copy back, certified, the same FP64 margins as the device entry
+    point (up to the summation order of the norm)."""
     import torch
     import paper_2601_01596_b300 as ffcz
     r = np.random.default_rng(17)
@@ -144,5 +146,23 @@ def test_host_entry_certification_from_the_upload_matches_device(shape):
     sh = plan.correct_host(host, [E], [D])[0]
     assert sd["iters"] == 0 and sh["iters"] == 0
     assert sh["certified"] == 1 and np.array_equal(host, e0.reshape(-1))
+    assert sh["host_copies"] == 0
     assert abs(sh["f_margin64"] - sd["f_margin64"]) < 1e-12
     assert sh["s_margin64"] == sd["s_margin64"]
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 16, 64), (64, 128)])
+def test_host_entry_iterating_field_is_copied_back(shape):
+    """A field the loop edits comes back through the copy stream once, with
+    the device entry point's bits and certification."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    e0, E, D = stress(shape, 8)
+    plan = ffcz.Plan([shape])
+    t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    sd = plan.correct(t, [E], [D])[0]
+    host = e0.reshape(-1).copy()
+    sh = plan.correct_host(host, [E], [D])[0]
+    assert sd["iters"] >= 1 and sh["iters"] == sd["iters"] and sh["certified"] == 1
+    assert sh["host_copies"] == 1 and np.array_equal(host, t.cpu().numpy())
+    assert sh["f_margin64"] == sd["f_margin64"]
