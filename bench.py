@@ -471,19 +471,30 @@ def pointwise_form(ffcz, torch, it, D, hbm, K=20):
     d = torch.empty_like(d0)
     eb = torch.full((n,), float(E), dtype=torch.float32, device="cuda")
     out = {}
+    kernels = {}
     for k in (K, 0):
         plan = ffcz.Plan([shape], pointwise=1, min_iters=k, max_iters=k, certify=0)
         nb = plan.edit_layout(-1)[1]
         db = torch.full((2 * nb,), float(D), dtype=torch.float32, device="cuda")
         ms, st = _timed(torch, lambda: plan.correct_pw(d.copy_(d0), eb, db)[0], reps=3)
         out[k] = (ms, st)
+        if k == K:
+            # one call with every launch timed by CUDA events (direct launches,
+            # outside the graph): the per-kernel split of the iteration
+            plan.profile(True)
+            plan.correct_pw(d.copy_(d0), eb, db)
+            torch.cuda.synchronize()
+            kernels = {name: {"ms_per_launch": round(tms / cnt, 4), "launches": cnt}
+                       for name, (tms, cnt) in plan.profile_table().items()}
+            plan.profile(False)
         del plan, db
     it_ms = (out[K][0] - out[0][0]) / K
     design = 40.0 * n
     return {"workload": it["name"] + " stress bounds as uniform pointwise arrays",
             "forced_iters": K, "ms_per_iteration": round(it_ms, 4),
             "design_bytes": int(design),
-            "frac_hbm_design": round(design / (it_ms / 1e3) / 1e9 / hbm, 4)}
+            "frac_hbm_design": round(design / (it_ms / 1e3) / 1e9 / hbm, 4),
+            "kernels": kernels}
 
 
 def variants_form(ffcz, torch, it, D, hbm, K=20):
@@ -521,39 +532,52 @@ def variants_form(ffcz, torch, it, D, hbm, K=20):
     return out
 
 
-def measure_forms(ffcz, torch, fin, it, hbm):
+FORMS = ("stress", "cufft", "edits", "pointwise", "variants", "batched_2d", "batched_1d", "differentiable")
+
+
+def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS):
     """The stress variant, the batched and the differentiable forms (each a
-    median of 2 calls after 1 warm-up; CUDA events on the current stream)."""
+    median of 2 calls after 1 warm-up; CUDA events on the current stream);
+    `which` selects some of them."""
     out = {}
     shape, E = it["shape"], it["E"]
     n = int(np.prod(shape))
-    d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
-    d = torch.empty_like(d0)
-    plan = ffcz.Plan([shape])
-    Dst = fin["stress_D"]
-    ms_total, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [Dst])[0])
-    copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
-    ms = ms_total - copy_ms
-    out["stress_512"] = {"workload": it["name"] + " stress eps_f = 0.2 max box violation of e0",
-                         "ms_per_call": round(ms, 3), "GBps": round(4 * n / (ms / 1e3) / 1e9, 3),
-                         "iters": st["iters"], "certified": st["certified"],
-                         "ms_cert": round(st["ms_cert"], 3)}
-    del plan, d, d0
-    torch.cuda.empty_cache()
-    out["paper_design_cufft"] = paper_design_cufft(torch, it, fin["stress_D"], hbm)
-    torch.cuda.empty_cache()
-    out["edits_stress_512"] = edits_form(ffcz, torch, it, fin["stress_D"])
-    torch.cuda.empty_cache()
-    out["pointwise_512"] = pointwise_form(ffcz, torch, it, fin["stress_D"], hbm)
-    torch.cuda.empty_cache()
-    out["variants_512"] = variants_form(ffcz, torch, it, fin["stress_D"], hbm)
-    torch.cuda.empty_cache()
-    out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
-                                    "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")
-    torch.cuda.empty_cache()
-    out["batched_1d"] = _batch_form(ffcz, torch, fin["c4"],
-                                    "4096 EEG-like signals, lengths U{1024..65536} (Bluestein)")
-    torch.cuda.empty_cache()
+    if "stress" in which:
+        d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
+        d = torch.empty_like(d0)
+        plan = ffcz.Plan([shape])
+        Dst = fin["stress_D"]
+        ms_total, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [Dst])[0])
+        copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
+        ms = ms_total - copy_ms
+        out["stress_512"] = {"workload": it["name"] + " stress eps_f = 0.2 max box violation of e0",
+                             "ms_per_call": round(ms, 3), "GBps": round(4 * n / (ms / 1e3) / 1e9, 3),
+                             "iters": st["iters"], "certified": st["certified"],
+                             "ms_cert": round(st["ms_cert"], 3)}
+        del plan, d, d0
+        torch.cuda.empty_cache()
+    if "cufft" in which:
+        out["paper_design_cufft"] = paper_design_cufft(torch, it, fin["stress_D"], hbm)
+        torch.cuda.empty_cache()
+    if "edits" in which:
+        out["edits_stress_512"] = edits_form(ffcz, torch, it, fin["stress_D"])
+        torch.cuda.empty_cache()
+    if "pointwise" in which:
+        out["pointwise_512"] = pointwise_form(ffcz, torch, it, fin["stress_D"], hbm)
+        torch.cuda.empty_cache()
+    if "variants" in which:
+        out["variants_512"] = variants_form(ffcz, torch, it, fin["stress_D"], hbm)
+        torch.cuda.empty_cache()
+    if "batched_2d" in which:
+        out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
+                                        "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")
+        torch.cuda.empty_cache()
+    if "batched_1d" in which:
+        out["batched_1d"] = _batch_form(ffcz, torch, fin["c4"],
+                                        "4096 EEG-like signals, lengths U{1024..65536} (Bluestein)")
+        torch.cuda.empty_cache()
+    if "differentiable" not in which:
+        return out
     # differentiable: K = 50 forced iterations, checkpoint every 10, loss on the
     # log power spectrum of x + e_K (torch.fft in the loss only)
     from paper_2601_01596_b300.autograd import FFCzCorrect, power_spectrum_loss
@@ -597,6 +621,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the stress, batched and differentiable forms")
+    ap.add_argument("--forms", default=",".join(FORMS),
+                    help="comma-separated forms to run: " + ",".join(FORMS))
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -613,14 +639,19 @@ def main():
     # per-iteration cost of a field whose clips are active
     stress_D = W.max_box_fft(it["e0"]) * 0.2
     forms_in = None
-    if not args.no_forms:
+    which = tuple(f for f in args.forms.split(",") if f)
+    unknown = [f for f in which if f not in FORMS]
+    if unknown:
+        ap.error(f"unknown forms {unknown}; choose from {FORMS}")
+    if not args.no_forms and which:
         workers = min(8, os.cpu_count() or 1)
-        forms_in = {
-            "stress_D": stress_D,
-            "c3": W.diffraction_batch(workers=workers),
-            "c4": W.eeg_batch(workers=workers),
-            "c5": W.turbulence_field(256),
-        }
+        forms_in = {"stress_D": stress_D}
+        if "batched_2d" in which:
+            forms_in["c3"] = W.diffraction_batch(workers=workers)
+        if "batched_1d" in which:
+            forms_in["c4"] = W.eeg_batch(workers=workers)
+        if "differentiable" in which:
+            forms_in["c5"] = W.turbulence_field(256)
 
     import torch
     import paper_2601_01596_b300 as ffcz
@@ -767,7 +798,7 @@ def main():
         dist.all_reduce(e2e_ms_t, op=dist.ReduceOp.MAX)
     e2e_val = world * field_bytes / (float(e2e_ms_t.item()) / 1e3) / 1e9
 
-    forms = measure_forms(ffcz, torch, forms_in, it, hbm) if forms_in else None
+    forms = measure_forms(ffcz, torch, forms_in, it, hbm, which) if forms_in else None
     if forms and "paper_design_cufft" in forms:
         forms["paper_design_cufft"]["fused_speedup_per_iteration"] = round(
             forms["paper_design_cufft"]["ms_per_iteration"] / it_ms, 3)
