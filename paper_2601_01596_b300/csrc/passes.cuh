@@ -738,8 +738,11 @@ k_px(Args a) {
 // s-clip when M_CLIP (again after rounding to float32), store or (M_ACC)
 // add to e.
 template <typename T, int V, bool PW, int PV>
+// ebr: the thread's E_n loaded before the transform (pointwise bounds;
+// null: read from ebrow here).
 __device__ __forceinline__ void xexit_store(const Args& a, const ItemParams& p, v2<T> (&v)[V], int j, int NT,
-                                            float2* erow, const float2* ebrow, const float2* qrow) {
+                                            float2* erow, const float2* ebrow, const float2* qrow,
+                                            const float2* ebr = nullptr) {
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
 #pragma unroll
@@ -751,7 +754,7 @@ __device__ __forceinline__ void xexit_store(const Args& a, const ItemParams& p, 
       y += (T)q.y;
     }
     float2 eb = make_float2(1.f, 1.f);
-    if constexpr (PW) eb = ebrow[j + u * NT];
+    if constexpr (PW) eb = ebr ? ebr[u] : ebrow[j + u * NT];
     if (a.mode & M_CLIP) {
       if constexpr (PW) { x = clampT(x, Es * (T)eb.x); y = clampT(y, Es * (T)eb.y); }
       else { x = clampT(x, Es); y = clampT(y, Es); }
@@ -781,16 +784,22 @@ k_xexit(Args a) {
   v2<T> v[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
+  // pointwise E_n of the thread's points, loaded before the transform
+  const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+  float2 ebr[PW ? V : 1];
+  if constexpr (PW) {
+#pragma unroll
+    for (int u = 0; u < V; ++u) ebr[u] = ebrow[j + u * G_::NT];
+  }
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   c2r_pre<T, M>(v, j, tl, s_twr);
   fft_pencil<T, M, +1>(v, j, s_tw, tl);
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
-  const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
   // Dykstra: x_t = P_S'(y_{t-1} + q_{t-1}) (q_0 = 0)
   const float2* qrow = (PV == PV_DYKSTRA && t_it >= 2)
                            ? reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M
                            : nullptr;
-  if (live) xexit_store<T, V, PW, PV>(a, p, v, j, G_::NT, erow, ebrow, qrow);
+  if (live) xexit_store<T, V, PW, PV>(a, p, v, j, G_::NT, erow, ebrow, qrow, PW ? ebr : nullptr);
 }
 // ---------------------------------------------------------------------------
 // Strided axis passes
@@ -1767,11 +1776,17 @@ k_xexit_tma(Args a) {
     const bool live = prow < rows;
     const int64_t row = live ? prow : 0;
     TL tl{s_tiles + g * TL::ELEMS + w, false};
+    // pointwise E_n of the thread's points, loaded before the transform
+    const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
+    float2 ebr[PW ? V : 1];
+    if constexpr (PW) {
+#pragma unroll
+      for (int u = 0; u < V; ++u) ebr[u] = ebrow[j + u * NT];
+    }
     c2r_pre<float, M>(v, j, tl, s_twr);
     fft_pencil<float, M, +1>(v, j, s_tw, tl);
     float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
-    const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
-    if (live) xexit_store<float, V, PW, PV_POCS>(a, p, v, j, NT, erow, ebrow, nullptr);
+    if (live) xexit_store<float, V, PW, PV_POCS>(a, p, v, j, NT, erow, ebrow, nullptr, PW ? ebr : nullptr);
     TL::sync();   // the warp's tile buffer is reused by the next block
     blk = next;
   }
