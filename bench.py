@@ -599,11 +599,25 @@ def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS):
         return float(loss.item())
 
     fb_ms, loss = _timed(torch, fwd_bwd)
+    # the library's vector-Jacobian product alone (ffcz_correct_backward_ckpt
+    # from the forward's checkpoints), without the torch loss and its backward
+    from paper_2601_01596_b300.autograd import _plan
+    vplan = _plan(tuple(e0.shape), K, m)
+    ck = torch.empty(vplan.ckpt_floats(), dtype=torch.float32, device="cuda")
+    ek = e0.reshape(-1).clone()
+    vplan.correct_ckpt(ek, [c5["E"]], [c5["D"]], ck)
+    gvec = torch.ones_like(ek)
+    gin = torch.empty_like(ek)
+    vjp_ms, _ = _timed(torch, lambda: vplan.backward(e0.reshape(-1), gvec, gin, [c5["E"]], [c5["D"]], ckpt=ck))
+    del ck, ek, gvec, gin
     n5 = int(np.prod(c5["shape"]))
     out["differentiable"] = {"workload": c5["name"] + f", K={K} forced iterations, checkpoint every {m}",
                              "forward_ms": round(fwd_ms, 3),
+                             "backward_vjp_ms": round(vjp_ms, 3),
+                             "vjp_over_forward": round(vjp_ms / fwd_ms, 3),
                              "forward_backward_ms": round(fb_ms, 3),
                              "backward_over_forward": round((fb_ms - fwd_ms) / fwd_ms, 3),
+                             "note": "forward_backward includes the float64 torch power-spectrum loss and its backward",
                              "forward_ms_per_iteration": round(fwd_ms / K, 4),
                              "field_GBps_forward": round(4 * n5 / (fwd_ms / 1e3) / 1e9, 3),
                              "loss": loss}

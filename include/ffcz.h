@@ -329,6 +329,29 @@ ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0_dev,
                                   const float* grad_out_dev, float* grad_in_dev,
                                   const double* eps_s, const double* eps_f);
 
+/*
+ * Differentiable form without the second forward: ffcz_correct_ckpt is
+ * ffcz_correct for the plan of ffcz_correct_backward (min_iters = max_iters
+ * = opts.K, precision 32) whose loop also writes the backward's float32
+ * checkpoints -- e_t at t = 0 (e0 after the pre-clip), m, 2m, ... below K,
+ * m = opts.ckpt_every -- to ckpt_dev; ffcz_correct_backward_ckpt then
+ * replays each segment from them instead of running the K-step forward
+ * again (same vector-Jacobian product as ffcz_correct_backward, bit for bit).
+ *   ckpt_dev : device float32 of ffcz_ckpt_floats(plan) values
+ *              (ceil(K / m) x N), owned by the caller; the pair of calls
+ *              must use the same e0, bounds and buffer.
+ *   e_dev    : (forward) e0 in, e_K out; e0_dev (backward): the forward's
+ *              input, unmodified.
+ * The forward's loop runs its x pass in the form with checkpoint writes.
+ * ffcz_ckpt_floats returns 0 for a NULL plan.
+ */
+int64_t ffcz_ckpt_floats(ffcz_plan_t plan);
+ffcz_status ffcz_correct_ckpt(ffcz_plan_t plan, float* e_dev, const double* eps_s, const double* eps_f,
+                              float* ckpt_dev, ffcz_stats* stats);
+ffcz_status ffcz_correct_backward_ckpt(ffcz_plan_t plan, const float* e0_dev, const float* ckpt_dev,
+                                       const float* grad_out_dev, float* grad_in_dev,
+                                       const double* eps_s, const double* eps_f);
+
 /* Release the plan and its workspace.  NULL is ignored. */
 void ffcz_destroy(ffcz_plan_t plan);
 

@@ -27,7 +27,8 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
            "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
-           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw", "ffcz_power_spectrum_bounds")
+           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw", "ffcz_power_spectrum_bounds",
+           "ffcz_ckpt_floats", "ffcz_correct_ckpt", "ffcz_correct_backward_ckpt")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -112,6 +113,10 @@ def lib() -> ctypes.CDLL:
         L.ffcz_correct_host.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_check.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
         L.ffcz_correct_backward.argtypes = [vp, vp, vp, vp, dp, dp]
+        L.ffcz_ckpt_floats.argtypes = [vp]
+        L.ffcz_ckpt_floats.restype = ctypes.c_int64
+        L.ffcz_correct_ckpt.argtypes = [vp, vp, dp, dp, vp, ctypes.POINTER(Stats)]
+        L.ffcz_correct_backward_ckpt.argtypes = [vp, vp, vp, vp, vp, dp, dp]
         L.ffcz_destroy.argtypes = [vp]
         L.ffcz_destroy.restype = None
         L.ffcz_strerror.argtypes = [i32]
@@ -129,7 +134,7 @@ def lib() -> ctypes.CDLL:
         L.ffcz_check_static.restype = ctypes.c_int
         for name in ("ffcz_plan", "ffcz_set_stream", "ffcz_correct", "ffcz_correct_host",
                      "ffcz_check", "ffcz_correct_backward", "ffcz_profile_enable",
-                     "ffcz_profile_entry"):
+                     "ffcz_profile_entry", "ffcz_correct_ckpt", "ffcz_correct_backward_ckpt"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -351,13 +356,46 @@ class Plan:
         _check(s, (ERR_CERT_FAILED,))
         return StatsList(st)
 
-    def backward(self, e0, grad_out, grad_in, eps_s, eps_f, stream=None):
-        """grad_in <- (d e_K / d e0)^T grad_out for K = opts.K forced iterations."""
+    def backward(self, e0, grad_out, grad_in, eps_s, eps_f, stream=None, ckpt=None):
+        """grad_in <- (d e_K / d e0)^T grad_out for K = opts.K forced iterations
+        (``ckpt``: the checkpoints of ``correct_ckpt`` for this e0; else the
+        forward runs again to take them)."""
         self._bind_stream(stream)
-        _check(lib().ffcz_correct_backward(self._h, self._ptr(e0, "e0"),
-                                           self._ptr(grad_out, "grad_out"),
-                                           self._ptr(grad_in, "grad_in"),
-                                           _dbl(eps_s, 1), _dbl(eps_f, 1)))
+        if ckpt is None:
+            _check(lib().ffcz_correct_backward(self._h, self._ptr(e0, "e0"),
+                                               self._ptr(grad_out, "grad_out"),
+                                               self._ptr(grad_in, "grad_in"),
+                                               _dbl(eps_s, 1), _dbl(eps_f, 1)))
+            return
+        self._check_ckpt(ckpt)
+        _check(lib().ffcz_correct_backward_ckpt(self._h, self._ptr(e0, "e0"), ctypes.c_void_p(ckpt.data_ptr()),
+                                                self._ptr(grad_out, "grad_out"),
+                                                self._ptr(grad_in, "grad_in"),
+                                                _dbl(eps_s, 1), _dbl(eps_f, 1)))
+
+    def ckpt_floats(self) -> int:
+        """Size (float32 values) of the checkpoint buffer of ``correct_ckpt``."""
+        return int(lib().ffcz_ckpt_floats(self._h))
+
+    def _check_ckpt(self, ckpt):
+        import torch
+        n = self.ckpt_floats()
+        if not (isinstance(ckpt, torch.Tensor) and ckpt.is_cuda and ckpt.dtype == torch.float32
+                and ckpt.is_contiguous() and ckpt.numel() == n):
+            raise ValueError(f"ckpt must be {n} contiguous float32 values on the GPU")
+
+    def correct_ckpt(self, e, eps_s, eps_f, ckpt, stream=None,
+                     allow=(ERR_NOT_CONVERGED, ERR_CERT_FAILED, ERR_NONFINITE)):
+        """``correct`` for the differentiable form (min_iters = max_iters = K)
+        that also writes the backward's checkpoints into ``ckpt``
+        (``ckpt_floats()`` float32 values on the GPU)."""
+        self._bind_stream(stream)
+        self._check_ckpt(ckpt)
+        st = (Stats * self.batch)()
+        s = lib().ffcz_correct_ckpt(self._h, self._ptr(e, "e"), _dbl(eps_s, self.batch),
+                                    _dbl(eps_f, self.batch), ctypes.c_void_p(ckpt.data_ptr()), st)
+        _check(s, allow)
+        return StatsList(st)
 
 
 def check_static(e, eps_s: float, eps_f: float, stream=None):

@@ -1,10 +1,11 @@
 """Differentiable correction: e_K = F(e0) for K forced iterations of Alg. 1.
 
 ``FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every)`` runs K iterations
-(min_iters = max_iters = K, no certification) in the CUDA library; its
-backward calls ``ffcz_correct_backward``, the vector-Jacobian product built
-from the clips' active-set masks, regenerated from float32 checkpoints taken
-every ``ckpt_every`` iterations.  One step e <- P_s(IDFT(P_f(DFT(e)))) has the
+(min_iters = max_iters = K, no certification) in the CUDA library, writing
+float32 checkpoints of e every ``ckpt_every`` iterations
+(``ffcz_correct_ckpt``); its backward calls ``ffcz_correct_backward_ckpt``,
+the vector-Jacobian product built from the clips' active-set masks,
+regenerated by replaying each segment from its checkpoint.  One step e <- P_s(IDFT(P_f(DFT(e)))) has the
 Jacobian M_s IDFT M_f DFT, and IDFT M_f DFT is symmetric in the real frequency
 basis of Sec. IV-A, so the transposed step is g <- IDFT(M_f DFT(M_s g)).
 """
@@ -34,19 +35,20 @@ class FFCzCorrect(torch.autograd.Function):
         e0c = e0.detach().contiguous()
         plan = _plan(e0c.shape, K, ckpt_every)
         e = e0c.clone()
-        plan.correct(e.reshape(-1), [eps_s], [eps_f])
-        ctx.save_for_backward(e0c)
+        ckpt = torch.empty(plan.ckpt_floats(), dtype=torch.float32, device=e0c.device)
+        plan.correct_ckpt(e.reshape(-1), [eps_s], [eps_f], ckpt)
+        ctx.save_for_backward(e0c, ckpt)
         ctx.cfg = (float(eps_s), float(eps_f), int(K), int(ckpt_every))
         return e
 
     @staticmethod
     def backward(ctx, grad_out):
-        (e0,) = ctx.saved_tensors
+        e0, ckpt = ctx.saved_tensors
         eps_s, eps_f, K, m = ctx.cfg
         plan = _plan(e0.shape, K, m)
         g = grad_out.detach().to(torch.float32).contiguous()
         gin = torch.empty_like(e0)
-        plan.backward(e0.reshape(-1), g.reshape(-1), gin.reshape(-1), [eps_s], [eps_f])
+        plan.backward(e0.reshape(-1), g.reshape(-1), gin.reshape(-1), [eps_s], [eps_f], ckpt=ckpt)
         return gin, None, None, None, None
 
 

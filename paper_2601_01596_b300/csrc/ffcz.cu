@@ -223,7 +223,7 @@ struct ffcz_plan_s {
   int* d_loopcount = nullptr;   // bodies executed by the WHILE graph
   int* h_loopcount = nullptr;   // pinned copy
   bool count_pending = false;
-  int while_cap[2] = {-1, -1};
+  int while_cap[2][2] = {{-1, -1}, {-1, -1}};   // [precision][checkpoint recording]
   int pending_bodies_per = 0;
 
   // per-kernel profile (events around every launch; graphs off while on)
@@ -241,6 +241,9 @@ struct ffcz_plan_s {
   uint32_t* bw_fmask = nullptr;
   void* bw_G[2] = {nullptr, nullptr};
   int bw_K = -1, bw_m = -1;
+  // forward of the differentiable form: the loop's x pass writes the
+  // backward's checkpoints into bw_ck (ffcz_correct_ckpt)
+  bool ck_rec = false;
   int64_t px_words = 0, chk_words = 0;
 };
 
@@ -1030,7 +1033,14 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     }
     tabs_x<T>(p, a, dg);
     a.mode = M_CLIP | cnt_flag(p);
+    if (sizeof(T) == 4 && p->ck_rec) {
+      a.mode |= M_CKPT;
+      a.ckpt = p->bw_ck;
+      a.ckpt_every = p->bw_m;
+    }
     launch_x<T>(XPX, dg.M, dg.wx, a, dg.rows, dg.count, s);
+    a.ckpt = nullptr;
+    a.ckpt_every = 0;
     a.sel_in = a.sel_out = S_CUR;
     if (dg.ndim == 3) {
       a.tw = tw_of<T>(p->tb, dg.Ny);
@@ -1094,7 +1104,8 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, const int* n_active, in
 // and precision, replayed by one cudaGraphLaunch per call).
 template <typename T>
 void run_while_graph(ffcz_plan_s* p, LoopBufs B, int cap) {
-  const auto key = std::make_pair(-(int)sizeof(T), 0);
+  const int ckk = (sizeof(T) == 4 && p->ck_rec) ? 1 : 0;
+  const auto key = std::make_pair(-(int)sizeof(T), ckk);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     cudaGraph_t g;
@@ -1130,7 +1141,7 @@ void run_while_graph(ffcz_plan_s* p, LoopBufs B, int cap) {
     cudaGraphDestroy(g);
     it = p->graphs.emplace(key, ge).first;
     p->graph_nodes[key] = per_body;
-    p->while_cap[sizeof(T) == 4 ? 0 : 1] = cap;
+    p->while_cap[sizeof(T) == 4 ? 0 : 1][ckk] = cap;
   }
   CK(cudaMemsetAsync(p->d_loopcount, 0, sizeof(int), p->stream));
   CK(cudaGraphLaunch(it->second, p->stream));
@@ -1144,7 +1155,7 @@ void run_chunk(ffcz_plan_s* p, LoopBufs B, int C) {
     for (int i = 0; i < C; ++i) body<T>(p, B, p->stream);
     return;
   }
-  const auto key = std::make_pair((int)sizeof(T), C);
+  const auto key = std::make_pair((int)sizeof(T) + ((sizeof(T) == 4 && p->ck_rec) ? 16 : 0), C);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     cudaGraph_t g;
@@ -1444,13 +1455,16 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
                                                                    only_uncert ? 1 : 0, p->d_nactive);
   g_launches++;
   entry<T>(p, B, e, !only_uncert, p->stream);
+  if (sizeof(T) == 4 && p->ck_rec)   // checkpoint t = 0: e0 after the pre-clip
+    CK(cudaMemcpyAsync(p->bw_ck, e, sizeof(float) * p->total, cudaMemcpyDeviceToDevice, p->stream));
   const int cap = p->h_prm[0].max_iters;   // no item iterates past it
   if (p->opts.use_graph == 2 && !p->prof && cap > 0) {
     // the whole loop on the device (conditional WHILE node); graphs are
     // rebuilt when the cap changes
     const int slot = sizeof(T) == 4 ? 0 : 1;
-    const auto key = std::make_pair(-(int)sizeof(T), 0);
-    if (p->while_cap[slot] != cap && p->graphs.count(key)) {
+    const int ckk = (sizeof(T) == 4 && p->ck_rec) ? 1 : 0;
+    const auto key = std::make_pair(-(int)sizeof(T), ckk);
+    if (p->while_cap[slot][ckk] != cap && p->graphs.count(key)) {
       cudaGraphExecDestroy(p->graphs[key]);
       p->graphs.erase(key);
     }
@@ -1913,17 +1927,19 @@ void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uin
   launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
 }
 
-ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, float* gin,
-                          const double* eps_s, const double* eps_f) {
+// Plan checks shared by the differentiable entry points.
+void bw_check(ffcz_plan_s* p) {
   if (p->batch != 1) fail(FFCZ_ERR_UNSUPPORTED, "backward needs a single-item plan");
   if (p->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "backward supports 2D and 3D items");
   if (p->opts.pointwise) fail(FFCZ_ERR_INVALID, "backward uses scalar bounds");
   if (p->opts.method != PV_POCS) fail(FFCZ_ERR_UNSUPPORTED, "backward differentiates Alg. 1 (method 0)");
-  if (!e0 || !gout || !gin || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
+  if (p->opts.K < 1 || p->opts.ckpt_every < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
+}
+
+// Workspace of the backward (checkpoints, masks, adjoint buffers), sized
+// for the plan's K and ckpt_every.
+void bw_alloc(ffcz_plan_s* p) {
   const int K = p->opts.K, m = p->opts.ckpt_every;
-  if (K < 1 || m < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
-  CK(cudaSetDevice(p->device));
-  ProfOn prof_on(p);
   const DevGroup& dg = p->groups[0];
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
@@ -1941,15 +1957,38 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     p->bw_K = K;
     p->bw_m = m;
   }
+}
+
+// pre-clip adjoint from the t = 0 checkpoint: a point was clipped exactly
+// where the checkpoint differs from e0 (a NaN input included)
+__global__ void k_premask_ck(float* g, const float* e0, const float* ck0, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(ck0[i] == e0[i])) g[i] = 0.f;
+}
+
+// ckpt_in: checkpoints written by ffcz_correct_ckpt (null: the forward is run
+// again here to take them).
+ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, float* gin,
+                          const double* eps_s, const double* eps_f, const float* ckpt_in = nullptr) {
+  bw_check(p);
+  if (!e0 || !gout || !gin || !eps_s || !eps_f) fail(FFCZ_ERR_INVALID, "null pointer argument");
+  const int K = p->opts.K, m = p->opts.ckpt_every;
+  CK(cudaSetDevice(p->device));
+  ProfOn prof_on(p);
+  const DevGroup& dg = p->groups[0];
+  const int64_t N = p->total;
+  const int nseg = (K + m - 1) / m;
+  bw_alloc(p);
   upload_params(p, eps_s, eps_f, K, K);
   LoopBufs B{p->B32[0], p->B32[1]};
   LoopBufs GB{p->bw_G[0], p->bw_G[1]};
   // Forward with checkpoints of e_t at t = 0, m, 2m, ... (t < K).
-  CK(cudaMemcpyAsync(p->bw_e, e0, sizeof(float) * N, cudaMemcpyDeviceToDevice, p->stream));
   CK(cudaMemsetAsync(p->d_nactive, 0, sizeof(int), p->stream));
   k_init<<<1, 32, 0, p->stream>>>(p->d_st, 1, 0, p->d_nactive);
   g_launches++;
-  {
+  const float* ck = ckpt_in ? ckpt_in : p->bw_ck;
+  if (!ckpt_in) {
+    CK(cudaMemcpyAsync(p->bw_e, e0, sizeof(float) * N, cudaMemcpyDeviceToDevice, p->stream));
     // entry with A3 pre-clip on the working copy
     entry<float>(p, B, p->bw_e, true, p->stream);
     CK(cudaMemcpyAsync(p->bw_ck, p->bw_e, sizeof(float) * N, cudaMemcpyDeviceToDevice, p->stream));
@@ -1967,7 +2006,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     const int t0 = seg * m, t1 = std::min(K, t0 + m);
     // replay the segment from its checkpoint, recording masks of steps t0..t1-1
     set_t(p, p->d_st, t0);
-    replay_entry(p, dg, B, p->bw_ck + (int64_t)seg * N, p->bw_fmask);
+    replay_entry(p, dg, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
     for (int b = t0 + 1; b <= t1; ++b) {
       advance(p, p->d_st);
       replay_body(p, dg, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
@@ -2032,7 +2071,8 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     tabs_x<float>(p, a, dg);
     a.mode = 0;
     launch_x<float>(XEXIT, dg.M, dg.wx, a, dg.rows, 1, p->stream);
-    k_premask<<<1184, 256, 0, p->stream>>>(gin, e0, p->d_prm, p->d_st, 0, N);
+    if (ckpt_in) k_premask_ck<<<1184, 256, 0, p->stream>>>(gin, e0, ckpt_in, N);
+    else k_premask<<<1184, 256, 0, p->stream>>>(gin, e0, p->d_prm, p->d_st, 0, N);
     g_launches++;
   }
   CK(cudaStreamSynchronize(p->stream));
@@ -2724,6 +2764,41 @@ ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0, const float
                                   const double* eps_s, const double* eps_f) {
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() { return backward_impl(plan, e0, gout, gin, eps_s, eps_f); });
+}
+
+int64_t ffcz_ckpt_floats(ffcz_plan_t plan) {
+  if (!plan || plan->opts.K < 1 || plan->opts.ckpt_every < 1) return 0;
+  return (int64_t)((plan->opts.K + plan->opts.ckpt_every - 1) / plan->opts.ckpt_every) * plan->total;
+}
+
+ffcz_status ffcz_correct_ckpt(ffcz_plan_t plan, float* e, const double* eps_s, const double* eps_f,
+                              float* ckpt, ffcz_stats* stats) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    bw_check(plan);
+    if (!e || !ckpt) fail(FFCZ_ERR_INVALID, "null pointer argument");
+    const ffcz_opts& o = plan->opts;
+    if (o.min_iters != o.K || o.max_iters != o.K || o.precision != 32)
+      fail(FFCZ_ERR_INVALID, "the differentiable forward needs min_iters = max_iters = K and precision 32");
+    CK(cudaSetDevice(plan->device));
+    bw_alloc(plan);
+    plan->ck_rec = true;
+    struct Off { ffcz_plan_s* p; ~Off() { p->ck_rec = false; } } off{plan};
+    const ffcz_status st = correct_impl(plan, e, eps_s, eps_f, stats);
+    CK(cudaMemcpyAsync(ckpt, plan->bw_ck, sizeof(float) * ffcz_ckpt_floats(plan), cudaMemcpyDeviceToDevice,
+                       plan->stream));
+    CK(cudaStreamSynchronize(plan->stream));
+    return st;
+  });
+}
+
+ffcz_status ffcz_correct_backward_ckpt(ffcz_plan_t plan, const float* e0, const float* ckpt, const float* gout,
+                                       float* gin, const double* eps_s, const double* eps_f) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() {
+    if (!ckpt) fail(FFCZ_ERR_INVALID, "null pointer argument");
+    return backward_impl(plan, e0, gout, gin, eps_s, eps_f, ckpt);
+  });
 }
 
 void ffcz_destroy(ffcz_plan_t plan) {

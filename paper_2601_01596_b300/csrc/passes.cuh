@@ -670,7 +670,9 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
       if (!(b2 & 2u)) v[u].y = T(0);
     }
   } else if (ED && (a.mode & (M_RECORD | M_CKPT))) {
-    const bool ckn = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 && live;
+    // checkpoints of e_t for t = 0, m, 2m, ... below the item's K
+    const bool ckn = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 &&
+                     t_it < p.max_iters && live;
     float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * (2 * M * a.g.rows)) + row * M
                      : nullptr;
     MaskBits<MW> mb;
