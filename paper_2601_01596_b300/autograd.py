@@ -56,6 +56,31 @@ def correct_differentiable(e0, eps_s, eps_f, K=50, ckpt_every=10):
     return FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every)
 
 
+_shell_cache: dict = {}
+
+
+def _shells(n, device, k_max):
+    """Shell index round(|k|) of every half-spectrum bin, the bin weights (2
+    for bins standing for k and -k, 1 on the self-conjugate planes) and the
+    mask of bins with shell <= k_max, cached per shape and device."""
+    key = (tuple(n), str(device), int(k_max))
+    hit = _shell_cache.get(key)
+    if hit is None:
+        import torch
+        ks = [torch.fft.fftfreq(s, d=1.0 / s, device=device, dtype=torch.float64) for s in n[:-1]]
+        ks.append(torch.arange(n[-1] // 2 + 1, device=device, dtype=torch.float64))
+        grids = torch.meshgrid(*ks, indexing="ij")
+        kr = torch.sqrt(sum(g * g for g in grids)).round().long()
+        w = torch.full(kr.shape, 2.0, dtype=torch.float64, device=device)
+        w[..., 0] = 1.0
+        if n[-1] % 2 == 0:
+            w[..., -1] = 1.0
+        mask = kr <= k_max
+        hit = (kr[mask], w[mask], mask)
+        _shell_cache[key] = hit
+    return hit
+
+
 def power_spectrum_loss(x, e, k_max=None):
     """Squared log power-spectrum mismatch between x + e and x (float64 sums).
 
@@ -63,22 +88,15 @@ def power_spectrum_loss(x, e, k_max=None):
     (A13), integer shells round(|k|) in 1..N/2, half-spectrum bins weighted 2
     except the self-conjugate planes.  Test and benchmark use only (torch.fft).
     """
+    n = tuple(x.shape)
+    km = k_max or min(n) // 2
+    kr, w, mask = _shells(n, x.device, km)
+
     def spectrum(f):
         f = f.to(torch.float64)
         F = torch.fft.rfftn(f - f.mean())
         p = F.real ** 2 + F.imag ** 2
-        n = f.shape
-        ks = [torch.fft.fftfreq(s, d=1.0 / s, device=f.device, dtype=torch.float64) for s in n[:-1]]
-        ks.append(torch.arange(n[-1] // 2 + 1, device=f.device, dtype=torch.float64))
-        grids = torch.meshgrid(*ks, indexing="ij")
-        kr = torch.sqrt(sum(g * g for g in grids)).round().long()
-        w = torch.full_like(p, 2.0)
-        w[..., 0] = 1.0
-        if n[-1] % 2 == 0:
-            w[..., -1] = 1.0
-        km = k_max or min(n) // 2
         shells = torch.zeros(km + 1, dtype=torch.float64, device=f.device)
-        mask = kr <= km
-        shells.index_add_(0, kr[mask], (w * p)[mask])
+        shells.index_add_(0, kr, w * p[mask])
         return shells[1:]
     return torch.sum((torch.log(spectrum(x + e)) - torch.log(spectrum(x))) ** 2)
