@@ -929,6 +929,7 @@ __device__ __forceinline__ void pw_pencil(const Args& a, int gi, const ChkTile& 
 // after the forward transform, which waits until the staged bounds landed.
 struct QEarly {
   static constexpr bool late = false;
+  uint32_t sq = 0;
   __device__ __forceinline__ void operator()() const {}
 };
 
@@ -957,9 +958,23 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 #pragma unroll
     for (int u = 0; u < V; ++u) qb[u] = pwb[(int64_t)(j + u * NT) * pws];
   }
+  // bounds of value u: qbound on the mirror path (any tile), qmain where
+  // only main tiles' results are kept (staged: a shared-memory read at a
+  // compile-time offset, whatever the tile)
   auto qbound = [&](int u) -> float2 {
     if constexpr (QLATE) return pwb[(int64_t)(j + u * NT) * pws];
     else return qb[PW ? u : 0];
+  };
+  auto qmain = [&](int u) -> float2 {
+    if constexpr (QLATE) {
+      float2 q;
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                   : "=f"(q.x), "=f"(q.y)
+                   : "r"(qwait.sq + (uint32_t)((j + u * NT) * TL::W) * 8u));
+      return q;
+    } else {
+      return qb[PW ? u : 0];
+    }
   };
   // Dykstra / Douglas-Rachford: the residual r of the previous frequency
   // projection (zero before the first one), loaded before the transform
@@ -1083,7 +1098,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     if constexpr (PW) {
-      const float2 q = qbound(u);
+      const float2 q = qmain(u);
       tm.add(ratioT(v[u].x, (T)q.x)); tm.add(ratioT(v[u].y, (T)q.y));
     }
     else { tm.add(v[u].x); tm.add(v[u].y); }
@@ -1116,7 +1131,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
       for (int u = 0; u < V; ++u) {
         const T x = v[u].x, y = v[u].y;
         T qx = T(1), qy = T(1);
-        if constexpr (PW) { const float2 q = qbound(u); qx = (T)q.x; qy = (T)q.y; }
+        if constexpr (PW) { const float2 q = qmain(u); qx = (T)q.x; qy = (T)q.y; }
         const T cx = clampT(x, PW ? Ds * qx : Ds), cy = clampT(y, PW ? Ds * qy : Ds);
         const bool ix = cx == x, iy = cy == y;
         if (count && c.owner) cnt += 2 * ((!ix) + (!iy));   // a stored bin stands for k and -k
@@ -1292,6 +1307,7 @@ k_axis_tma(Args a) {
 // timeout raises *late_flag, on which the caller stops.
 struct QStaged {
   static constexpr bool late = true;
+  uint32_t sq;      // shared-memory address of the staged bounds of pencil w
   uint64_t* b;
   uint32_t par;
   bool on;
@@ -1367,7 +1383,7 @@ k_chk_tma(Args a) {
     }
     using QW = typename std::conditional<PW, QStaged, QEarly>::type;
     QW qw{};
-    if constexpr (PW) qw = QStaged{&bar_pw, par_pw, main_tile, &pw_late};
+    if constexpr (PW) qw = QStaged{smem_addr(s_pw + w), &bar_pw, par_pw, main_tile, &pw_late};
     chk_core<float, L, TL, PW, PV_POCS, FULL, QW>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
                                                   &acc_vb, &acc_cnt, a.g.soff[gi] + c.off + j * estride,
                                                   (int64_t)NT * estride, t_it, pwb, pws, 1, qw);
