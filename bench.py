@@ -497,6 +497,38 @@ def pointwise_form(ffcz, torch, it, D, hbm, K=20):
             "kernels": kernels}
 
 
+def fp64_form(ffcz, torch, it, D, K=4):
+    """The float32 loop with FP64 certification against an all-FP64 GPU run
+    (ffcz_opts.precision = 64: the loop in float64, then the same
+    certification) on the stress variant: time to certified feasibility
+    (the copy of e0 subtracted), iterations, per-iteration time from K forced
+    iterations minus 0, and the largest difference between the two corrected
+    fields relative to eps_s."""
+    shape, E = it["shape"], it["E"]
+    d0 = torch.from_numpy(it["e0"].reshape(-1)).cuda()
+    d = torch.empty_like(d0)
+    copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
+    out, fields = {}, {}
+    for prec in (32, 64):
+        plan = ffcz.Plan([shape], precision=prec)
+        ms, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [D])[0])
+        fields[prec] = d.clone()
+        del plan
+        per = {}
+        for k in (K, 0):
+            fp = ffcz.Plan([shape], precision=prec, min_iters=k, max_iters=k, certify=0)
+            per[k], _ = _timed(torch, lambda: fp.correct(d.copy_(d0), [E], [D])[0])
+            del fp
+        out[f"fp{prec}_loop"] = {"ms_to_certified": round(ms - copy_ms, 3), "iters": st["iters"],
+                                 "certified": st["certified"], "ms_cert": round(st["ms_cert"], 3),
+                                 "ms_per_iteration": round((per[K] - per[0]) / K, 4)}
+        torch.cuda.empty_cache()
+    diff = float((fields[32] - fields[64]).abs().max().item()) / E
+    del fields, d, d0
+    return {"workload": it["name"] + " stress eps_f = 0.2 max box violation of e0", **out,
+            "max_abs_diff_over_eps_s": diff, "forced_iters": K}
+
+
 def variants_form(ffcz, torch, it, D, hbm, K=20):
     """The projection variants of Sec. III (ffcz_opts.method) on the stress
     variant: time to certified feasibility (the copy of e0 subtracted),
@@ -532,7 +564,8 @@ def variants_form(ffcz, torch, it, D, hbm, K=20):
     return out
 
 
-FORMS = ("stress", "cufft", "edits", "pointwise", "variants", "batched_2d", "batched_1d", "differentiable")
+FORMS = ("stress", "cufft", "edits", "pointwise", "variants", "fp64", "batched_2d", "batched_1d",
+         "differentiable")
 
 
 def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS):
@@ -567,6 +600,9 @@ def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS):
         torch.cuda.empty_cache()
     if "variants" in which:
         out["variants_512"] = variants_form(ffcz, torch, it, fin["stress_D"], hbm)
+        torch.cuda.empty_cache()
+    if "fp64" in which:
+        out["fp64_512"] = fp64_form(ffcz, torch, it, fin["stress_D"])
         torch.cuda.empty_cache()
     if "batched_2d" in which:
         out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
