@@ -881,6 +881,9 @@ def main():
                           "design_GBps": round(design / (it_ms / 1e3) / 1e9, 1),
                           "frac_hbm_design": round(design / (it_ms / 1e3) / 1e9 / hbm, 4),
                           "frac_hbm_two_pass_minimum": round(minimum / (it_ms / 1e3) / 1e9 / hbm, 4),
+                          "frac_nominal_8TBps": round(design / (it_ms / 1e3) / 8e12, 4),
+                          # R2C + C2R per iteration: 2 x 2.5 N log2 N
+                          "gflops_achieved": round(5.0 * n * np.log2(n) / (it_ms / 1e3) / 1e9, 1),
                           "stress_ms": round(it_ms_stress, 4),
                           "stress_frac_hbm_design": round(design / (it_ms_stress / 1e3) / 1e9 / hbm, 4),
                           "forced_iters": args.forced, "kernels": body_kernels},
