@@ -230,7 +230,8 @@ def test_device_loop_graph_chunk_graphs_and_direct_launch_agree(shape):
 
 
 # ------------------------------------------------- TMA-fed persistent passes
-@pytest.mark.parametrize("shape", [(256, 256, 32), (512, 32, 16), (256, 64), (16, 32, 512), (8, 16, 16)])
+@pytest.mark.parametrize("shape", [(256, 256, 32), (512, 32, 16), (256, 64), (16, 32, 512), (8, 16, 16),
+                                   (1024, 16, 32), (16, 1024, 32), (1024, 64)])
 def test_tma_fed_passes_equal_plain_passes_and_match_oracle(shape, monkeypatch):
     e0, E, D = stress(shape, 43)
     monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,chk=tma,px=tma")

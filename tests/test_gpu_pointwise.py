@@ -156,7 +156,7 @@ def _pw_case(shape, seed, frac=0.3):
     return e0, E_n, D_re * scale, D_im * scale
 
 
-@pytest.mark.parametrize("shape", [(256, 32, 32), (256, 64), (512, 16, 32)])
+@pytest.mark.parametrize("shape", [(256, 32, 32), (256, 64), (512, 16, 32), (1024, 16, 32)])
 def test_tma_fed_pointwise_check_equals_plain_and_matches_oracle(shape, monkeypatch):
     """The persistent check pass stages each tile's f-bounds in shared memory
     by the copy engine; the tiled pass reads them from global memory.  Same
