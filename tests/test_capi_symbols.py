@@ -48,6 +48,9 @@ def test_invalid_arguments_fail_before_any_device_work():
     assert L.ffcz_plan(ctypes.byref(h), 3, bad, 1, None, None) == ffcz.ERR_UNSUPPORTED
     assert b"power" in L.ffcz_last_error()
     assert L.ffcz_correct(None, None, None, None, None) == ffcz.ERR_INVALID
+    assert L.ffcz_ckpt_floats(None) == 0
+    assert L.ffcz_correct_ckpt(None, None, None, None, None, None) == ffcz.ERR_INVALID
+    assert L.ffcz_correct_backward_ckpt(None, None, None, None, None, None, None) == ffcz.ERR_INVALID
     L.ffcz_destroy(None)
 
 
