@@ -332,7 +332,8 @@ ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0_dev,
 /*
  * Differentiable form without the second forward: ffcz_correct_ckpt is
  * ffcz_correct for the plan of ffcz_correct_backward (min_iters = max_iters
- * = opts.K, precision 32) whose loop also writes the backward's float32
+ * = opts.K, precision 32, certify 0; else FFCZ_ERR_INVALID: a repair would
+ * change e_K after the recorded steps) whose loop also writes the backward's float32
  * checkpoints -- e_t at t = 0 (e0 after the pre-clip), m, 2m, ... below K,
  * m = opts.ckpt_every -- to ckpt_dev; ffcz_correct_backward_ckpt then
  * replays each segment from them instead of running the K-step forward

@@ -2778,8 +2778,9 @@ ffcz_status ffcz_correct_ckpt(ffcz_plan_t plan, float* e, const double* eps_s, c
     bw_check(plan);
     if (!e || !ckpt) fail(FFCZ_ERR_INVALID, "null pointer argument");
     const ffcz_opts& o = plan->opts;
-    if (o.min_iters != o.K || o.max_iters != o.K || o.precision != 32)
-      fail(FFCZ_ERR_INVALID, "the differentiable forward needs min_iters = max_iters = K and precision 32");
+    if (o.min_iters != o.K || o.max_iters != o.K || o.precision != 32 || o.certify)
+      fail(FFCZ_ERR_INVALID, "the differentiable forward needs min_iters = max_iters = K, precision 32 "
+                             "and no certification");
     CK(cudaSetDevice(plan->device));
     bw_alloc(plan);
     plan->ck_rec = true;

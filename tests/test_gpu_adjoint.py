@@ -115,6 +115,10 @@ def test_checkpointed_forward_and_backward_equal_the_two_pass_form(shape, K, m, 
         e2 = te0.clone()
         p2.correct(e2, [E], [D])
         np.testing.assert_allclose(ckn[-1], e2.cpu().numpy(), rtol=0, atol=1e-6 * E)
+    # a plan that certifies (a repair could change e_K) is refused
+    pc = ffcz.Plan([shape], K=K, ckpt_every=m, min_iters=K, max_iters=K, certify=1)
+    with pytest.raises(ffcz.FFCzError):
+        pc.correct_ckpt(te0.clone(), [E], [D], ck)
     tg = torch.from_numpy(g.reshape(-1).copy()).cuda()
     ga, gb = torch.empty_like(te0), torch.empty_like(te0)
     plan.backward(te0, tg, ga, [E], [D])
