@@ -101,8 +101,9 @@ struct DevGroup {
   // null where the TMA-fed kernels do not apply
   const CUtensorMap* tm_axis = nullptr;
   const CUtensorMap* tm_chk = nullptr;
-  // the check pass's view of the packed pointwise f-bounds (count maps)
-  const CUtensorMap* tm_pw = nullptr;
+  // the check pass's view of its auxiliary packed field, the pointwise
+  // f-bounds or the variants' residual (count maps)
+  const CUtensorMap* tm_aux = nullptr;
   std::vector<int64_t> h_soff;   // host copy of the members' spectrum offsets
   const int64_t* d_canon = nullptr;   // members' offsets in the canonical edit spectra
   // 1D items (Bluestein): P = P1 P2 >= 2N - 1; exp(-2 pi i m / P) tables
@@ -555,11 +556,14 @@ inline bool chk_full(const Args& a) { return (a.mode & (M_RECORD | M_MASK)) != 0
 template <int L>
 void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   const int64_t tiles = chk_ntiles(8, M, Nmid);
-  const size_t sm = a.pw_f ? TmaGeo<L, 8>::bytes_pw : TmaGeo<L, 8>::bytes;
+  // pointwise bounds or a variant's residual ride in a second staging buffer
+  const bool res = a.pv == PV_DYKSTRA || a.pv == PV_DR;
+  const size_t sm = (a.pw_f || res) ? TmaGeo<L, 8>::bytes_pw : TmaGeo<L, 8>::bytes;
   if (g_dry) {
     const size_t sp = TmaGeo<L, 8>::bytes_pw;
     set_smem(k_chk_tma<L, 8, true>, TmaGeo<L, 8>::bytes); set_smem(k_chk_tma<L, 8, false>, TmaGeo<L, 8>::bytes);
     set_smem(k_chk_tma<L, 8, true, true>, sp); set_smem(k_chk_tma<L, 8, false, true>, sp);
+    set_smem(k_chk_tma<L, 8, false, false, PV_DYKSTRA>, sp); set_smem(k_chk_tma<L, 8, false, false, PV_DR>, sp);
     return;
   }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk", 32, L, s);
@@ -568,6 +572,10 @@ void launch_chk_tma(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   if (a.pw_f) {   // pointwise (Delta^Re, Delta^Im)
     if (full) k_chk_tma<L, 8, true, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
     else k_chk_tma<L, 8, false, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  } else if (a.pv == PV_DYKSTRA) {   // the variants run the lean form only
+    k_chk_tma<L, 8, false, false, PV_DYKSTRA><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
+  } else if (a.pv == PV_DR) {
+    k_chk_tma<L, 8, false, false, PV_DR><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
   } else if (full) {
     k_chk_tma<L, 8, true><<<grid, Geo<float, L, 8>::NTHR, sm, s>>>(a);
   } else {
@@ -632,15 +640,22 @@ struct CL {
   static void go(int w, const Args& a, int Nmid, int M, int count, cudaStream_t s) {
     if (a.pw_f || g_pw_sel) {
       if constexpr (sizeof(T) == 4 && tma_ok<L>()) {
-        if (w < 0 && a.tm_chk && a.tm_pw && !g_dry) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
+        if (w < 0 && a.tm_chk && a.tm_aux && !g_dry) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
       }
       launch_chk_tw<T, L, TileW<T>::value, true>(a, Nmid, M, count, s);
       return;
     }
     if constexpr (sizeof(T) == 4) {
-      // projection variants with a frequency residual (one tile width)
-      if (a.pv == PV_DYKSTRA) { launch_chk_tw<T, L, TileW<T>::value, false, PV_DYKSTRA>(a, Nmid, M, count, s); return; }
-      if (a.pv == PV_DR) { launch_chk_tw<T, L, TileW<T>::value, false, PV_DR>(a, Nmid, M, count, s); return; }
+      // projection variants with a frequency residual (one tile width, or
+      // the persistent kernel with the residual staged beside the spectrum)
+      if (a.pv == PV_DYKSTRA || a.pv == PV_DR) {
+        if constexpr (tma_ok<L>()) {
+          if (w < 0 && a.tm_chk && a.tm_aux && !g_dry) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
+        }
+        if (a.pv == PV_DYKSTRA) launch_chk_tw<T, L, TileW<T>::value, false, PV_DYKSTRA>(a, Nmid, M, count, s);
+        else launch_chk_tw<T, L, TileW<T>::value, false, PV_DR>(a, Nmid, M, count, s);
+        return;
+      }
     }
     if constexpr (sizeof(T) == 4) {
       if constexpr (tma_ok<L>()) {
@@ -796,23 +811,24 @@ void build_tensor_maps(ffcz_plan_s* p) {
   }
 }
 
-// Pointwise plans: the check pass's [Nz][Nmid M] view of the packed f-bounds
-// of every member (same boxes as the spectrum maps), where that pass has a
-// TMA-fed kernel.
-void build_pw_maps(ffcz_plan_s* p) {
+// The check pass's [Nz][Nmid M] view of an auxiliary packed field (the
+// pointwise f-bounds, or the Dykstra / Douglas-Rachford residual) of every
+// member (same boxes as the spectrum maps), where that pass has a TMA-fed
+// kernel.
+void build_aux_maps(ffcz_plan_s* p, const void* field) {
   for (auto& dg : p->groups) {
     if (dg.ndim == 1 || !dg.tm_chk) continue;
     const int Nmid = dg.ndim == 3 ? dg.Ny : 1;
     std::vector<CUtensorMap> maps((size_t)dg.count);
     bool ok = true;
     for (int gi = 0; gi < dg.count && ok; ++gi) {
-      const char* base = reinterpret_cast<const char*>(p->pw_fp) + dg.h_soff[gi] * 8;
+      const char* base = static_cast<const char*>(field) + dg.h_soff[gi] * 8;
       ok = encode_2d(&maps[gi], base, (uint64_t)Nmid * dg.M, (uint64_t)dg.Nz, 8, (uint32_t)std::min(dg.Nz, 256));
     }
     if (!ok) continue;
     void* d = dalloc(p, sizeof(CUtensorMap) * maps.size());
     CK(cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
-    dg.tm_pw = static_cast<const CUtensorMap*>(d);
+    dg.tm_aux = static_cast<const CUtensorMap*>(d);
   }
 }
 
@@ -842,7 +858,7 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   if (sizeof(T) == 4 && b0 == p->B32[0] && b1 == p->B32[1]) {
     a.tm_axis = dg.tm_axis;
     a.tm_chk = dg.tm_chk;
-    if (p->opts.pointwise) a.tm_pw = dg.tm_pw;
+    a.tm_aux = dg.tm_aux;
   }
   if (sizeof(T) == 4 && p->pv_on) {
     a.pv = p->opts.method;
@@ -2518,6 +2534,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       p->pv_q[1] = (float*)dalloc(p.get(), sizeof(float) * p->total);
     }
     build_tensor_maps(p.get());
+    if (p->pv_r) build_aux_maps(p.get(), p->pv_r);
     p->d_prm = (ItemParams*)dalloc(p.get(), sizeof(ItemParams) * batch);
     p->d_st = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
@@ -2543,7 +2560,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       p->pw_e = (float*)dalloc(p.get(), sizeof(float) * p->total);
       p->pw_f = (float2*)dalloc(p.get(), sizeof(float2) * p->ed_total[1]);
       p->pw_fp = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
-      build_pw_maps(p.get());
+      build_aux_maps(p.get(), p->pw_fp);
       p->pw_f0 = (float4*)dalloc(p.get(), sizeof(float4) * p->total_rows);
       p->pw_min = (unsigned int*)dalloc(p.get(), sizeof(unsigned int) * batch);
       p->pw_bad = (int*)dalloc(p.get(), sizeof(int));

@@ -110,9 +110,10 @@ struct Args {
   // not the plan's float32 pair
   const CUtensorMap* tm_axis;
   const CUtensorMap* tm_chk;
-  // the same view of the packed pointwise f-bounds (pw_f), one per group
-  // member (null: the check pass reads them with plain loads)
-  const CUtensorMap* tm_pw;
+  // the same view of the check pass's auxiliary packed field, one per group
+  // member: the pointwise f-bounds (pw_f) or the projection variants'
+  // residual (pv_r) (null: the check pass reads it with plain loads)
+  const CUtensorMap* tm_aux;
   int* err;                // device error word (DevErr)
   // Alg. 1 edit recording (null: off).  ed_s: spatial edits, float32 laid
   // out like e.  Frequency edits in the packed spectrum layout: ed_f the
@@ -979,14 +980,32 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
   // Dykstra / Douglas-Rachford: the residual r of the previous frequency
   // projection (zero before the first one), loaded before the transform
   constexpr bool RES = (PV == PV_DYKSTRA || PV == PV_DR);
-  float2 rr[RES ? V : 1];
-  if constexpr (RES) {
-    const bool res_in = t_chk >= 1 && c.valid;
+  constexpr bool RLATE = RES && QW::late;   // residual staged in shared memory
+  const bool res_in = RES && t_chk >= 1 && c.valid;
+  // residual of value u: rr_any on the mirror path (a global load when
+  // staged), rr_main where only main tiles' results are kept
+  float2 rr[(RES && !RLATE) ? V : 1];
+  auto rr_any = [&](int u) -> float2 {
+    if constexpr (RLATE) return res_in ? a.pv_r[ed_slot0 + u * ed_ustride] : make_float2(0.f, 0.f);
+    else return rr[RES ? u : 0];
+  };
+  auto rr_main = [&](int u) -> float2 {
+    if constexpr (RLATE) {
+      float2 r;
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                   : "=f"(r.x), "=f"(r.y)
+                   : "r"(qwait.sq + (uint32_t)((j + u * NT) * TL::W) * 8u));
+      return res_in ? r : make_float2(0.f, 0.f);
+    } else {
+      return rr[RES ? u : 0];
+    }
+  };
+  if constexpr (RES && !RLATE) {
 #pragma unroll
     for (int u = 0; u < V; ++u) rr[u] = res_in ? a.pv_r[ed_slot0 + u * ed_ustride] : make_float2(0.f, 0.f);
   }
   fft_pencil<T, L, -1>(v, j, twg, tl);
-  if constexpr (QLATE) qwait();
+  if constexpr (QW::late) qwait();
   const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
   AbsMax<T> mx;
   bool bad = false;
@@ -1019,7 +1038,10 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
       tl.done();
       if (c.mirror) {
 #pragma unroll
-        for (int u = 0; u < V; ++u) v[u] = mk<T>(v[u].x + (T)rr[u].x, v[u].y + (T)rr[u].y);
+        for (int u = 0; u < V; ++u) {
+          const float2 r = rr_any(u);
+          v[u] = mk<T>(v[u].x + (T)r.x, v[u].y + (T)r.y);
+        }
       }
       store_nat<T, L, TL>(v, j, tl);
       if (c.mirror) {
@@ -1110,7 +1132,8 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
     // y - r (Douglas-Rachford)
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-      const T x = v[u].x + (T)rr[u].x, y = v[u].y + (T)rr[u].y;
+      const float2 r = rr_main(u);
+      const T x = v[u].x + (T)r.x, y = v[u].y + (T)r.y;
       const T cx = clampT(x, Ds), cy = clampT(y, Ds);
       if (count && c.owner) cnt += 2 * ((cx != x) + (cy != y));
       const T rx = x - cx, ry = y - cy;
@@ -1317,10 +1340,14 @@ struct QStaged {
   }
 };
 
-template <int L, int W, bool FULL = true, bool PW = false>
+// AUX: the pass stages an auxiliary packed field per main tile beside the
+// spectrum: the pointwise f-bounds (PW) or the Dykstra / Douglas-Rachford
+// residual (read before this pass rewrites it in place).
+template <int L, int W, bool FULL = true, bool PW = false, int PV = PV_POCS>
 __global__ void __launch_bounds__(Geo<float, L, W>::NTHR, TmaGeo<L, W>::MINB)
 k_chk_tma(Args a) {
-  FFCZ_TMA_PROLOGUE(L, W, PW ? L * W : 0)
+  constexpr bool AUX = PW || PV == PV_DYKSTRA || PV == PV_DR;
+  FFCZ_TMA_PROLOGUE(L, W, AUX ? L * W : 0)
   const int M = a.g.M, Nmid = a.g.Nmid;
   const int tpr = M / W;
   const int nmain = Nmid * tpr;
@@ -1334,9 +1361,9 @@ k_chk_tma(Args a) {
 #pragma unroll
     for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_stage + b * TG::BOX * W, map, x, b * TG::BOX, &bar);
   };
-  // pointwise: the f-bounds of a main tile go to their own staging buffer
-  // (same view of pw_f), loaded once the previous tile has used its bounds,
-  // and waited for after the forward transform
+  // the auxiliary field of a main tile goes to its own staging buffer (same
+  // view), loaded once the previous tile has used its copy, and waited for
+  // after the forward transform
   float2* s_pw = s_stage + L * W;
   __shared__ __align__(8) uint64_t bar_pw;
   uint32_t par_pw = 0;
@@ -1345,16 +1372,16 @@ k_chk_tma(Args a) {
     const int x = (t / tpr) * M + (t % tpr) * W;
     mbar_arrive_expect_tx(&bar_pw, (uint32_t)TG::stage);
 #pragma unroll
-    for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_pw + b * TG::BOX * W, a.tm_pw + gi, x, b * TG::BOX, &bar_pw);
+    for (int b = 0; b < L / TG::BOX; ++b) tma_load_2d(s_pw + b * TG::BOX * W, a.tm_aux + gi, x, b * TG::BOX, &bar_pw);
   };
-  if constexpr (PW) {
+  if constexpr (AUX) {
     if (tid == 0) mbar_init(&bar_pw, 1);
     __syncthreads();
   }
   int tile = blockIdx.x;
   if (tid == 0 && tile < nmain) {
     issue(tile);
-    if constexpr (PW) issue_pw(tile);
+    if constexpr (AUX) issue_pw(tile);
   }
   const float2* inb = pick<float>(a, a.sel_in, t_it) + a.g.soff[gi];
   float2* outb = pick<float>(a, a.sel_out, t_it) + a.g.soff[gi];
@@ -1365,7 +1392,7 @@ k_chk_tma(Args a) {
     float2 v[V];
     if (tile < nmain) {
       FFCZ_TMA_TAKE(if (next < nmain) { fence_proxy_async_smem(); issue(next); },
-                    if (PW) mbar_wait_bounded(&bar_pw, par_pw, kTmaPollLimit))
+                    if (AUX) mbar_wait_bounded(&bar_pw, par_pw, kTmaPollLimit))
     } else {
       // kx = 0 mirror pencils are not one box: plain loads
       const float2* in = inb + c.off + j * estride;
@@ -1381,10 +1408,10 @@ k_chk_tma(Args a) {
       if (main_tile) { pwb = s_pw + w; pws = W; }
       else pw_pencil(a, gi, c, M, Nmid, estride, pwb, pws);
     }
-    using QW = typename std::conditional<PW, QStaged, QEarly>::type;
+    using QW = typename std::conditional<AUX, QStaged, QEarly>::type;
     QW qw{};
-    if constexpr (PW) qw = QStaged{smem_addr(s_pw + w), &bar_pw, par_pw, main_tile, &pw_late};
-    chk_core<float, L, TL, PW, PV_POCS, FULL, QW>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
+    if constexpr (AUX) qw = QStaged{smem_addr(s_pw + w), &bar_pw, par_pw, main_tile, &pw_late};
+    chk_core<float, L, TL, PW, PV, FULL, QW>(a, p, st, v, j, w, mthr, c, tile >= nmain, tl, s_tw, s_red,
                                                   &acc_vb, &acc_cnt, a.g.soff[gi] + c.off + j * estride,
                                                   (int64_t)NT * estride, t_it, pwb, pws, 1, qw);
     if (!(a.mode & M_NOWRITE) && c.owner) {
@@ -1392,8 +1419,8 @@ k_chk_tma(Args a) {
 #pragma unroll
       for (int u = 0; u < V; ++u) out[(int64_t)u * NT * estride] = v[u];
     }
-    if constexpr (PW) {
-      // the tile buffer and the bounds staging are reused by the next tile
+    if constexpr (AUX) {
+      // the tile buffer and the auxiliary staging are reused by the next tile
       if (__syncthreads_or(pw_late)) {
         if (tid == 0) atomicExch(a.err, DERR_TMA_TIMEOUT);
         mbar_wait_bounded(&bar_pw, par_pw, kTmaPollLimit);                   // copies still in flight

@@ -128,3 +128,29 @@ def test_variant_option_checks():
         ffcz.Plan([(32, 32, 32)], method="dykstra", precision=64)
     with pytest.raises(ffcz.FFCzError):
         ffcz.Plan([(32, 32, 32)], method=4)
+
+
+@pytest.mark.parametrize("method", ["dykstra", "dr"])
+@pytest.mark.parametrize("shape", [(256, 32, 32), (512, 16, 32), (256, 64)])
+def test_tma_fed_residual_check_equals_plain_and_matches_oracle(method, shape, monkeypatch):
+    """The persistent check pass stages the residual of Dykstra / Douglas-
+    Rachford beside the spectrum; the tiled pass loads it with plain loads.
+    Same arithmetic: bit-identical results, and both match the oracle."""
+    e0, E, D = stress(shape, 7)
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,px=tma,chk=tma")
+    a, sa = run_gpu(e0, E, D, method=method)
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,px=tma,chk=8")
+    b, sb = run_gpu(e0, E, D, method=method)
+    monkeypatch.delenv("FFCZ_TUNE_FORCE")
+    assert sa[0]["iters"] == sb[0]["iters"] >= 2 and sa[0]["certified"] == 1
+    assert np.array_equal(a, b)
+    ref = O.correct_method(e0, E, D, method)
+    assert abs(sa[0]["iters"] - ref.iters) <= 2
+    same = O.correct_method(e0, E, D, method, min_iters=sa[0]["iters"], max_iters=sa[0]["iters"])
+    np.testing.assert_allclose(a.reshape(shape), same.e, rtol=0, atol=TOL * E)
+    for K in (1, 3):
+        monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,px=tma,chk=tma")
+        f, _ = run_gpu(e0, E, D, method=method, min_iters=K, max_iters=K, certify=0)
+        monkeypatch.delenv("FFCZ_TUNE_FORCE")
+        refk = O.correct_method(e0, E, D, method, min_iters=K, max_iters=K)
+        np.testing.assert_allclose(f.reshape(shape), refk.e, rtol=0, atol=TOL * E, err_msg=f"K={K}")
