@@ -549,17 +549,27 @@ def variants_form(ffcz, torch, it, D, hbm, K=20):
         ms, st = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [D])[0])
         edit = float(torch.linalg.vector_norm((d - d0).double())) / nrm0
         del plan
-        per = {}
+        per, kernels = {}, {}
         for k in (K, 0):
             plan = ffcz.Plan([shape], method=m, min_iters=k, max_iters=k, certify=0)
             per[k], _ = _timed(torch, lambda: plan.correct(d.copy_(d0), [E], [D])[0], reps=3)
+            if k == K:
+                # one call with every launch timed by CUDA events (direct
+                # launches, outside the graph): the per-kernel split
+                plan.profile(True)
+                plan.correct(d.copy_(d0), [E], [D])
+                torch.cuda.synchronize()
+                kernels = {name: {"ms_per_launch": round(tms / cnt, 4), "launches": cnt}
+                           for name, (tms, cnt) in plan.profile_table().items()}
+                plan.profile(False)
             del plan
         it_ms = (per[K] - per[0]) / K
         out[m] = {"ms_to_certified": round(ms - copy_ms, 3), "iters": st["iters"],
                   "certified": st["certified"], "repairs": st["repairs"],
                   "edit_norm_rel": round(edit, 6), "ms_per_iteration": round(it_ms, 4),
                   "design_bytes": int(design[m] * n),
-                  "frac_hbm_design": round(design[m] * n / (it_ms / 1e3) / 1e9 / hbm, 4)}
+                  "frac_hbm_design": round(design[m] * n / (it_ms / 1e3) / 1e9 / hbm, 4),
+                  "kernels": kernels}
         torch.cuda.empty_cache()
     return out
 
