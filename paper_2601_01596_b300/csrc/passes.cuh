@@ -741,18 +741,18 @@ k_px(Args a) {
 // s-clip when M_CLIP (again after rounding to float32), store or (M_ACC)
 // add to e.
 template <typename T, int V, bool PW, int PV>
-// ebr: the thread's E_n loaded before the transform (pointwise bounds;
-// null: read from ebrow here).
+// ebr / qr: the thread's E_n / Dykstra q loaded before the transform
+// (null: read from ebrow / qrow here).
 __device__ __forceinline__ void xexit_store(const Args& a, const ItemParams& p, v2<T> (&v)[V], int j, int NT,
                                             float2* erow, const float2* ebrow, const float2* qrow,
-                                            const float2* ebr = nullptr) {
+                                            const float2* ebr = nullptr, const float2* qr = nullptr) {
   const T inv_n = sizeof(T) == 4 ? (T)p.inv_nf : (T)p.inv_n;
   const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     T x = v[u].x * inv_n, y = v[u].y * inv_n;
     if (PV == PV_DYKSTRA && qrow) {
-      const float2 q = qrow[j + u * NT];
+      const float2 q = qr ? qr[u] : qrow[j + u * NT];
       x += (T)q.x;
       y += (T)q.y;
     }
@@ -794,15 +794,25 @@ k_xexit(Args a) {
 #pragma unroll
     for (int u = 0; u < V; ++u) ebr[u] = ebrow[j + u * G_::NT];
   }
+  // Dykstra: x_t = P_S'(y_{t-1} + q_{t-1}) (q_0 = 0); q loaded before the
+  // transform too
+  const float2* qrow = (PV == PV_DYKSTRA && t_it >= 2)
+                           ? reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M
+                           : nullptr;
+  float2 qr[PV == PV_DYKSTRA ? V : 1];
+  if constexpr (PV == PV_DYKSTRA) {
+    if (qrow) {
+#pragma unroll
+      for (int u = 0; u < V; ++u) qr[u] = qrow[j + u * G_::NT];
+    }
+  }
   load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
   c2r_pre<T, M>(v, j, tl, s_twr);
   fft_pencil<T, M, +1>(v, j, s_tw, tl);
   float2* erow = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
-  // Dykstra: x_t = P_S'(y_{t-1} + q_{t-1}) (q_0 = 0)
-  const float2* qrow = (PV == PV_DYKSTRA && t_it >= 2)
-                           ? reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M
-                           : nullptr;
-  if (live) xexit_store<T, V, PW, PV>(a, p, v, j, G_::NT, erow, ebrow, qrow, PW ? ebr : nullptr);
+  if (live)
+    xexit_store<T, V, PW, PV>(a, p, v, j, G_::NT, erow, ebrow, qrow, PW ? ebr : nullptr,
+                              PV == PV_DYKSTRA ? qr : nullptr);
 }
 // ---------------------------------------------------------------------------
 // Strided axis passes
