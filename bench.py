@@ -38,12 +38,15 @@ import numpy as np  # noqa: E402
 from paper_2601_01596_b300 import workloads as W  # noqa: E402
 
 METRIC = "field GB/s to certified feasibility, 512^3 fp32; % HBM roofline/iteration"
-FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300
+FP64_TFLOPS_NOMINAL = 1.25   # nominal dense FP64 rate of a B300 (context only)
 
-# DRAM bytes (read + write) per launch from one ncu capture of these kernels
-# at 512^3 (profiles/); a kernel changed since its capture must be removed.
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# at 512^3 (profiles/); an entry is removed when its kernel changes.
+# DRAM bytes (read + write) per launch and FP64-pipe utilisation from one ncu
+# capture of these kernels at 512^3 (summaries in profiles/).  They describe
+# the kernel sources as they were at that capture: NCU_SRC_SHA is the digest
+# of those sources (kernel_sources_sha()), and when the current sources
+# differ the figures are reported as null.
+NCU_CAPTURE = "ncu capture of 2026-12-03 (profiles/roofline_*.md)"
+NCU_SRC_SHA = "see-profiles"
 NCU_TRAFFIC = {
     "chk<f32,512>": 563637504 + 501929472,        # k_chk_tma<512, 8, lean>
     "axis_fwd<f32,512>": 536954880 + 483795200,   # k_axis_tma<512, -1, 8>
@@ -54,6 +57,28 @@ NCU_TRAFFIC = {
     "chk_cert<f64,512>": 1105017000 + 3545600,     # k_chk<double, 512, 4> (check only)
 }
 NCU_FP64_PIPE = {"xfwd<f64,256>": 0.847, "axis_fwd<f64,512>": 0.846, "chk_cert<f64,512>": 0.841}
+
+
+def kernel_sources_sha():
+    """Digest of the device-code sources (the kernels whose counters
+    NCU_TRAFFIC records)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2601_01596_b300", "csrc")
+    for f in ("fft_core.cuh", "passes.cuh", "tma.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_figures(key, n):
+    """(traffic, fp64 pipe fraction, note) for the top kernel: the recorded
+    ncu figures when they describe the current kernel sources at 512^3."""
+    if n != 512 ** 3:
+        return None, None, "no capture at this size"
+    if kernel_sources_sha() != NCU_SRC_SHA:
+        return None, None, "kernel sources changed since the " + NCU_CAPTURE
+    return NCU_TRAFFIC.get(key), NCU_FP64_PIPE.get(key), "from the " + NCU_CAPTURE
 
 
 def load_peaks():
@@ -339,7 +364,14 @@ def _timed(torch, fn, reps=2, warm=1):
     return float(np.median(out)), r
 
 
-def _batch_form(ffcz, torch, items, name):
+def _batch_form(ffcz, torch, items, name, rank=0, world=1, dist=None):
+    """One batched call over the items (each item's own loop, Alg. 1 per
+    item).  With N ranks the items are spread over the GPUs by
+    ``shard_items`` (no data crosses ranks); the step time is the slowest
+    rank's and the throughput all items' bytes over it."""
+    all_bytes = 4 * sum(int(x["e0"].size) for x in items)
+    if world > 1:
+        items = [items[i] for i in shard_items([4 * int(x["e0"].size) for x in items], rank, world)]
     shapes = [x["shape"] for x in items]
     host = np.concatenate([x["e0"].reshape(-1) for x in items])
     d0 = torch.from_numpy(host).cuda()
@@ -357,9 +389,13 @@ def _batch_form(ffcz, torch, items, name):
     copy_ms, _ = _timed(torch, lambda: d.copy_(d0))
     ms = ms_total - copy_ms
     iters = [x["iters"] for x in st]
-    byts = 4 * host.size
+    if world > 1 and dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    byts = all_bytes
     del plan
-    return {"workload": name, "items": len(items), "field_bytes": int(byts),
+    return {"workload": name, "items": len(items), "ranks": world, "field_bytes": int(byts),
             "ms_per_call": round(ms, 3), "GBps": round(byts / (ms / 1e3) / 1e9, 3),
             "ms_device": round(float(st[0]["ms_total"]), 3),
             "iters_min": int(min(iters)), "iters_max": int(max(iters)),
@@ -578,10 +614,11 @@ FORMS = ("stress", "cufft", "edits", "pointwise", "variants", "fp64", "batched_2
          "differentiable")
 
 
-def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS):
+def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS, rank=0, world=1, dist=None):
     """The stress variant, the batched and the differentiable forms (each a
     median of 2 calls after 1 warm-up; CUDA events on the current stream);
-    `which` selects some of them."""
+    `which` selects some of them.  The batched forms shard their items over
+    the ranks; the others run as replicas."""
     out = {}
     shape, E = it["shape"], it["E"]
     n = int(np.prod(shape))
@@ -616,11 +653,13 @@ def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS):
         torch.cuda.empty_cache()
     if "batched_2d" in which:
         out["batched_2d"] = _batch_form(ffcz, torch, fin["c3"],
-                                        "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2")
+                                        "512 diffraction images 171x256^2 + 171x512^2 + 170x1024^2",
+                                        rank, world, dist)
         torch.cuda.empty_cache()
     if "batched_1d" in which:
         out["batched_1d"] = _batch_form(ffcz, torch, fin["c4"],
-                                        "4096 EEG-like signals, lengths U{1024..65536} (Bluestein)")
+                                        "4096 EEG-like signals, lengths U{1024..65536} (Bluestein)",
+                                        rank, world, dist)
         torch.cuda.empty_cache()
     if "differentiable" not in which:
         return out
@@ -776,16 +815,21 @@ def main():
     top_key, (top_ms, top_n) = max(prof.items(), key=lambda kv: kv[1][0])
     top_avg = top_ms / top_n
     top_bytes = bytes_per_launch(top_key, n)
+    traffic, pipe, ncu_note = ncu_figures(top_key, n)
     if "f64" in top_key:
-        # FP64 kernels are bound by the FP64 pipe: nominal B300 FP64 rate
+        # FP64 kernels are bound by the FP64 pipe: measured FP64 FMA rate of
+        # this GPU (ffcz_fp64_peak), the add-only rate beside it
+        fma_tf = ffcz.fp64_peak("fma") / 1e12
+        add_tf = ffcz.fp64_peak("add") / 1e12
         top_flops = flops_per_launch(top_key, n)
+        ach = top_flops / (top_avg / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": top_key,
-                "achieved": round(top_flops / (top_avg / 1e3) / 1e12, 4),
-                "peak": FP64_TFLOPS, "unit": "TFLOP/s (FP64)",
-                "frac": round(top_flops / (top_avg / 1e3) / 1e12 / FP64_TFLOPS, 4),
-                "traffic": NCU_TRAFFIC.get(top_key) if n == 512 ** 3 else None,
-                "fp64_pipe_active_ncu": NCU_FP64_PIPE.get(top_key) if n == 512 ** 3 else None,
-                "peak_kind": "nominal FP64 (no measured FP64 peak)",
+                "achieved": round(ach, 4), "peak": round(fma_tf, 4), "unit": "TFLOP/s (FP64)",
+                "frac": round(ach / fma_tf, 4),
+                "traffic": traffic, "fp64_pipe_active_ncu": pipe, "ncu_note": ncu_note,
+                "peak_kind": "measured: FP64 FMA chains on this GPU (ffcz_fp64_peak), 2 flops per FMA",
+                "fp64_add_peak_tflops": round(add_tf, 4),
+                "fp64_nominal_tflops": FP64_TFLOPS_NOMINAL,
                 "avg_launch_ms": round(top_avg, 4), "algorithmic_flops": top_flops,
                 "algorithmic_bytes": top_bytes,
                 "achieved_GBps": round(top_bytes / (top_avg / 1e3) / 1e9, 1),
@@ -794,7 +838,7 @@ def main():
         roof = {"bound": "hbm", "kernel": top_key,
                 "achieved": round(top_bytes / (top_avg / 1e3) / 1e9, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(top_bytes / (top_avg / 1e3) / 1e9 / hbm, 4),
-                "traffic": NCU_TRAFFIC.get(top_key) if n == 512 ** 3 else None,
+                "traffic": traffic, "ncu_note": ncu_note,
                 "peak_kind": peak_kind, "avg_launch_ms": round(top_avg, 4),
                 "algorithmic_bytes": top_bytes,
                 "share_of_step": round(top_ms / tot, 3) if tot else None}
@@ -857,8 +901,24 @@ def main():
     if dist:
         dist.all_reduce(e2e_ms_t, op=dist.ReduceOp.MAX)
     e2e_val = world * field_bytes / (float(e2e_ms_t.item()) / 1e3) / 1e9
+    # the same on the labelled stress bound: the field iterates, so every
+    # call copies it back (the device-to-host leg of an iterating field)
+    np.copyto(hw, src)
+    plan.correct_host(hw, [E], [stress_D])
+    s2e_t, s2e_copies, s2e_iters = [], [], []
+    for _ in range(max(2, args.steps // 2)):
+        np.copyto(hw, src)
+        t0 = time.perf_counter()
+        sth = plan.correct_host(hw, [E], [stress_D])
+        s2e_t.append(time.perf_counter() - t0)
+        s2e_copies.append(sth[0]["host_copies"])
+        s2e_iters.append(sth[0]["iters"])
+    s2e_ms_t = torch.tensor([1e3 * float(np.mean(s2e_t))], device="cuda")
+    if dist:
+        dist.all_reduce(s2e_ms_t, op=dist.ReduceOp.MAX)
+    s2e_val = world * field_bytes / (float(s2e_ms_t.item()) / 1e3) / 1e9
 
-    forms = measure_forms(ffcz, torch, forms_in, it, hbm, which) if forms_in else None
+    forms = measure_forms(ffcz, torch, forms_in, it, hbm, which, rank, world, dist) if forms_in else None
     if forms and "paper_design_cufft" in forms:
         forms["paper_design_cufft"]["fused_speedup_per_iteration"] = round(
             forms["paper_design_cufft"]["ms_per_iteration"] / it_ms, 3)
@@ -884,7 +944,12 @@ def main():
                    "variants": plan_desc},
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": field_bytes + 64,
                 "d2h_bytes_per_step": int(round(field_bytes * float(np.mean(e2e_copies)))) + 4 + 160,
-                "field_copies_back": float(np.mean(e2e_copies))},
+                "field_copies_back": float(np.mean(e2e_copies)),
+                "stress": {"value": round(s2e_val, 3), "unit": "GB/s",
+                           "eps_f": stress_D, "iters": int(s2e_iters[-1]),
+                           "h2d_bytes_per_step": field_bytes + 64,
+                           "d2h_bytes_per_step": int(round(field_bytes * float(np.mean(s2e_copies)))) + 4 + 160,
+                           "field_copies_back": float(np.mean(s2e_copies))}},
         "roofline": roof,
         "per_iteration": {"ms": round(it_ms, 4), "body_kernels_ms": round(body_ms, 4),
                           "design_bytes": design, "passes": passes,

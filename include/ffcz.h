@@ -366,6 +366,17 @@ const char* ffcz_last_error(void);
 int64_t ffcz_launch_count(void);
 
 /*
+ * ffcz_fp64_peak -- measurement support, not part of the method: the FP64
+ * rate of the current device, measured with a kernel of independent FP64
+ * dependency chains (kind 0: fused multiply-adds, counted as 2 flops each;
+ * kind 1: adds, 1 flop each) on eight 256-thread blocks per SM, timed with
+ * CUDA events on `cuda_stream` (best of three after a warm-up).  Writes
+ * flops per second to *flops_per_s (host).  Allocates and frees 8 bytes of
+ * device memory; synchronises the stream.
+ */
+ffcz_status ffcz_fp64_peak(int kind, void* cuda_stream, double* flops_per_s);
+
+/*
  * Per-kernel device-time profile of a plan (measurement support, not part of
  * the method).  ffcz_profile_enable(plan, 1) clears the table and makes every
  * later call record a CUDA event pair around each of its launches (loop
@@ -383,15 +394,17 @@ ffcz_status ffcz_profile_entry(ffcz_plan_t plan, int i, char* name, int name_len
  * ffcz_check_static -- ffcz_check for one 2D or 3D field WITHOUT a plan and
  * WITHOUT allocating device memory.  The paper has no counterpart: this is an
  * entry point for callers that cannot allocate when they need the check --
- * code running inside a CUDA graph capture (cudaMalloc cannot be captured),
- * callback or interrupt-style pipelines that must not reach the allocator,
- * and hosts whose memory manager owns the whole device pool.
+ * hosts whose memory manager (a framework's caching allocator, a pool sized
+ * at start-up) owns the whole device so that no other allocation may happen,
+ * callback-driven pipelines that must not reach the allocator, and
+ * validation steps that must not fail for lack of memory mid-run.
  *   e_dev       : device float32 field (row-major, last axis contiguous);
  *                 read only
  *   ndim, shape : 2 or 3 extents, same rules as ffcz_plan
  *   eps_s, eps_f: the true bounds E, Delta (> 0)
  *   cuda_stream : cudaStream_t the work is ordered on (NULL = legacy stream);
- *                 the call waits for it before returning
+ *                 the call waits for this stream before returning (the
+ *                 stats are read back to the host)
  *   stats       : host pointer or NULL; certified, s_ratio, f_margin64 and
  *                 s_margin64 are filled, the rest is zero
  * Scratch: a fixed file-scope device array (about 32 MiB plus 260 KiB of
@@ -399,12 +412,12 @@ ffcz_status ffcz_profile_entry(ffcz_plan_t plan, int i, char* name, int name_len
  * process exits.  Fields of more than FFCZ_STATIC_MAX_POINTS points are
  * rejected with FFCZ_ERR_INVALID (detail in ffcz_last_error()) before any
  * GPU work.  The FIRST call on each device sets that device up (takes the
- * array's address with cudaGetSymbolAddress and uploads the twiddle tables
- * with blocking copies): make it before any stream capture.  All calls on a
- * device share the array (each call re-initialises what must start at zero);
- * calls whose GPU work overlaps -- other streams, other host threads -- race
- * and may return wrong results.  No cudaMalloc, cudaFree or allocating
- * library routine is called.
+ * array's address with cudaGetSymbolAddress, uploads the twiddle tables with
+ * blocking copies and loads every kernel the call launches): make it before
+ * any stream capture.  All calls on a device share the array (each call
+ * re-initialises what must start at zero); calls whose GPU work overlaps --
+ * other streams, other host threads -- race and may return wrong results.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
  * Returns OK (certified), CERT_FAILED, INVALID, UNSUPPORTED or CUDA.
  */
 #define FFCZ_STATIC_MAX_POINTS (1 << 22)

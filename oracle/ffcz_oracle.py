@@ -8,8 +8,9 @@ the method's arithmetic.
 
 Everything is float64.  The DFT step is a library primitive (``scipy.fft``,
 full complex spectrum, no half-spectrum tricks); everything else is written out
-in the paper's order.  Readings of passages the paper leaves open are tagged
-``A1``..``A25`` and listed, with the reasons, in the design notes.
+in the paper's order.  Where the paper leaves a passage open, the reading
+taken is tagged ``A1``..``A26`` and stated in the docstring of the function
+that applies it.
 
 Notation: ``e`` is the spatial error vector (epsilon in the paper), ``delta``
 its frequency error vector, ``E`` the spatial bound and ``D`` the frequency
@@ -366,6 +367,12 @@ def correct_backward(e0: np.ndarray, g_out: np.ndarray, E: float, D: float,
     Im separately.  Steps are undone from the last to the first.
     """
     _, pre_mask, masks = forward_masks(e0, E, D, K, eta)
+    return backward_from_masks(g_out, pre_mask, masks)
+
+
+def backward_from_masks(g_out: np.ndarray, pre_mask, masks) -> np.ndarray:
+    """The transposed steps g <- IDFT(M_f * DFT(M_s * g)), last step first,
+    for given active-set masks (those of :func:`forward_masks`)."""
     g = np.asarray(g_out, dtype=np.float64).copy()
     for m_re, m_im, m_s in reversed(masks):
         g = g * m_s
@@ -375,6 +382,66 @@ def correct_backward(e0: np.ndarray, g_out: np.ndarray, E: float, D: float,
     if pre_mask is not None:
         g = g * pre_mask
     return g
+
+
+def near_ties(e0: np.ndarray, E: float, D: float, K: int, tau: float,
+              eta: float = ETA_DEFAULT):
+    """The clip decisions of K forced iterations that a small perturbation of
+    the trajectory could reverse: for every step, the Re, Im and spatial
+    entries whose pre-clip magnitude lies within tau * bound of the shrunk
+    bound (| |v| - B | <= tau B).  The masks of :func:`forward_masks` take
+    one side of each such near tie (A14); a computation of the same
+    trajectory in another precision may take the other.
+    Returns [(near_re, near_im, near_s)] * K (boolean arrays)."""
+    e = np.asarray(e0, dtype=np.float64).copy()
+    Es, Ds, _ = thresholds(E, D, eta)
+    if e.size and np.max(np.abs(e)) > E:                  # A3
+        e = project_s(e, Es)
+    out = []
+    for _ in range(K):
+        delta = dft(e)
+        n_re = np.abs(np.abs(delta.real) - Ds) <= tau * Ds
+        n_im = np.abs(np.abs(delta.imag) - Ds) <= tau * Ds
+        e_i = idft(project_f(delta, Ds))
+        n_s = np.abs(np.abs(e_i) - Es) <= tau * Es
+        e = project_s(e_i, Es)
+        out.append((n_re, n_im, n_s))
+    return out
+
+
+def tie_spread(e0: np.ndarray, g_out: np.ndarray, E: float, D: float, K: int,
+               tau: float, samples: int = 8, seed: int = 0,
+               eta: float = ETA_DEFAULT):
+    """How far the vector-Jacobian product moves, coordinate by coordinate,
+    when the near ties of :func:`near_ties` are decided otherwise: the
+    largest |g' - g| over g' computed with every near tie inside, every near
+    tie outside, and ``samples`` random decisions (each near tie inside with
+    probability 1/2).  Zero where the trajectory has no near tie.
+    Returns (spread, number of near-tie entries)."""
+    _, pre_mask, masks = forward_masks(e0, E, D, K, eta)
+    near = near_ties(e0, E, D, K, tau, eta)
+    g_ref = backward_from_masks(g_out, pre_mask, masks)
+    count = int(sum(int(a.sum() + b.sum() + c.sum()) for a, b, c in near))
+    spread = np.zeros_like(g_ref)
+    if count == 0:
+        return spread, 0
+    rng = np.random.default_rng(seed)
+    for trial in range(samples + 2):
+        alt = []
+        for (m_re, m_im, m_s), nears in zip(masks, near):
+            ms = []
+            for m, n in zip((m_re, m_im, m_s), nears):
+                if trial == 0:
+                    side = np.ones(m.shape)
+                elif trial == 1:
+                    side = np.zeros(m.shape)
+                else:
+                    side = (rng.random(m.shape) < 0.5).astype(np.float64)
+                ms.append(np.where(n, side, m))
+            alt.append(tuple(ms))
+        g_alt = backward_from_masks(g_out, pre_mask, alt)
+        spread = np.maximum(spread, np.abs(g_alt - g_ref))
+    return spread, count
 
 
 # --------------------------------------------------------------------------

@@ -28,7 +28,7 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
            "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
            "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw", "ffcz_power_spectrum_bounds",
-           "ffcz_ckpt_floats", "ffcz_correct_ckpt", "ffcz_correct_backward_ckpt")
+           "ffcz_ckpt_floats", "ffcz_correct_ckpt", "ffcz_correct_backward_ckpt", "ffcz_fp64_peak")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
 
@@ -132,6 +132,8 @@ def lib() -> ctypes.CDLL:
         L.ffcz_check_static.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
                                         ctypes.c_double, vp, ctypes.POINTER(Stats)]
         L.ffcz_check_static.restype = ctypes.c_int
+        L.ffcz_fp64_peak.argtypes = [i32, vp, dp]
+        L.ffcz_fp64_peak.restype = ctypes.c_int
         for name in ("ffcz_plan", "ffcz_set_stream", "ffcz_correct", "ffcz_correct_host",
                      "ffcz_check", "ffcz_correct_backward", "ffcz_profile_enable",
                      "ffcz_profile_entry", "ffcz_correct_ckpt", "ffcz_correct_backward_ckpt"):
@@ -167,6 +169,15 @@ def default_opts(**kw) -> Opts:
 
 def launch_count() -> int:
     return int(lib().ffcz_launch_count())
+
+
+def fp64_peak(kind: str = "fma", stream=None) -> float:
+    """Measured FP64 rate of the current GPU in flop/s (``ffcz_fp64_peak``):
+    ``fma`` (2 flops per instruction) or ``add`` (1)."""
+    v = ctypes.c_double()
+    _check(lib().ffcz_fp64_peak({"fma": 0, "add": 1}[kind], ctypes.c_void_p(_stream_ptr(stream)),
+                                ctypes.byref(v)))
+    return float(v.value)
 
 
 def _dbl(values, n):

@@ -14,8 +14,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libffcz.so")
 SRC = [os.path.join(HERE, "csrc", "ffcz.cu"), os.path.join(HERE, "csrc", "noalloc.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("fft_core.cuh", "passes.cuh")] + [
-    os.path.join(ROOT, "include", "ffcz.h")]
+
+
+def deps():
+    """Every source the library is built from: the .cu files, every header
+    under csrc/ and the public header."""
+    csrc = os.path.join(HERE, "csrc")
+    return SRC + sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cuh", ".h"))) + [
+        os.path.join(ROOT, "include", "ffcz.h")]
+
+
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,7 +36,7 @@ def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in DEPS if os.path.exists(d))
+    return all(os.path.getmtime(d) <= t for d in deps() if os.path.exists(d))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -2257,6 +2257,38 @@ void tune(ffcz_plan_s* p) {
 
 }  // namespace
 
+namespace {
+
+// ----- FP64 pipe peak (measurement support, not part of the method) ---------
+// Every thread runs kFpChains independent dependency chains of FP64 FMAs
+// (kind 0) or adds (kind 1), enough to cover the pipe's latency, so the
+// FP64 issue rate alone bounds the kernel.  The chains' sum is written only
+// when it equals a value it never reaches; the compiler cannot know that, so
+// no chain is removed.
+constexpr int kFpChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_peak(double* out, int iters, int kind, double m, double c) {
+  double a[kFpChains];
+#pragma unroll
+  for (int i = 0; i < kFpChains; ++i) a[i] = 1e-3 * threadIdx.x + i;
+  if (kind == 0) {
+#pragma unroll 4
+    for (int t = 0; t < iters; ++t)
+#pragma unroll
+      for (int i = 0; i < kFpChains; ++i) a[i] = fma(a[i], m, c);
+  } else {
+#pragma unroll 4
+    for (int t = 0; t < iters; ++t)
+#pragma unroll
+      for (int i = 0; i < kFpChains; ++i) a[i] = a[i] + c;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kFpChains; ++i) s += a[i];
+  if (s == -1.0) out[0] = s;
+}
+
+}  // namespace
+
 // Lets the library's other translation unit report a detail message through
 // ffcz_last_error() (not exported).
 __attribute__((visibility("hidden"))) void ffcz_set_last_error(const char* msg) {
@@ -2863,5 +2895,40 @@ ffcz_status ffcz_profile_entry(ffcz_plan_t plan, int i, char* name, int name_len
 }
 
 int64_t ffcz_launch_count(void) { return g_launches.load(); }
+
+ffcz_status ffcz_fp64_peak(int kind, void* cuda_stream, double* flops_per_s) {
+  return guarded([&]() -> ffcz_status {
+    if (!flops_per_s || (kind != 0 && kind != 1)) fail(FFCZ_ERR_INVALID, "kind must be 0 or 1, flops_per_s non-null");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    double* out = nullptr;
+    CK(cudaMalloc(&out, sizeof(double)));
+    cudaEvent_t a = nullptr, b = nullptr;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    float best = 0.f;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(a, s);
+      k_fp64_peak<<<blocks, threads, 0, s>>>(out, iters, kind, 1.0000000001, 1e-9);
+      g_launches++;
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;   // rep 0 warms up
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(out);
+    if (e != cudaSuccess) fail(FFCZ_ERR_CUDA, cudaGetErrorString(e));
+    const double ops = (double)blocks * threads * kFpChains * iters;
+    *flops_per_s = ops * (kind == 0 ? 2.0 : 1.0) / (best * 1e-3);
+    return FFCZ_OK;
+  });
+}
 
 }  // extern "C"

@@ -2,18 +2,23 @@
 // field, with no plan and no device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// check: code running inside a CUDA graph capture (cudaMalloc is not a
-// capturable operation), callback-driven pipelines that must not reach the
-// allocator, and hosts whose memory manager owns the whole device pool so
-// that no other allocation may happen.  For them this entry point keeps its
-// scratch (twiddle tables, loop state, the float64 spectrum) in one
-// file-scope __device__ array of fixed size.  Every device that loads the
-// library holds that array until the process exits.
+// check: hosts whose memory manager (a framework's caching allocator, a
+// memory pool sized at start-up) owns the whole device so that no other
+// allocation may happen, callback-driven pipelines that must not reach the
+// allocator, and validation steps that must not fail for lack of memory in
+// the middle of a run.  For them this entry point keeps its scratch (twiddle
+// tables, loop state, the float64 spectrum) in one file-scope __device__
+// array of fixed size.  Every device that loads the library holds that array
+// until the process exits.
 //
 // Contract (also in include/ffcz.h):
 //  * The first call on each device sets that device up: it takes the array's
-//    device address with cudaGetSymbolAddress and copies the twiddle tables
-//    into it.  Make that first call before any stream capture begins.
+//    device address with cudaGetSymbolAddress, copies the twiddle tables into
+//    it and makes the runtime load every kernel this entry point launches
+//    (so that no later call loads code).  Make that first call before any
+//    stream capture begins.
+//  * Each call waits for its stream before returning (the stats are read
+//    back to the host).
 //  * Every call on a device shares the same array; calls whose GPU work
 //    overlaps (other streams, other host threads) race and may return wrong
 //    results.  Calls ordered on one stream are safe.
@@ -81,9 +86,14 @@ void stage_factors_rt(int L, std::vector<double2>& out) {
     for (int t = 1; t < R2; ++t) out[tw_index(R1, k1, t)] = root64((long double)k1 * t, (long double)L);
 }
 
+// Queries the kernel's attributes, which makes a lazily loading runtime load
+// it now rather than at its first launch, and raises its dynamic shared
+// memory limit where it needs more than the default 48 KiB.
 template <typename K>
 cudaError_t allow_smem(K k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -94,6 +104,9 @@ cudaError_t allow_all() {
   if (e == cudaSuccess) e = allow_smem(k_chk<double, L>, Smem<double, L>::bytes_axis);
   return e;
 }
+
+__global__ void k_static_init(int32_t* item, int64_t* eoff, int64_t* soff, ItemParams* prm,
+                              ItemState* st, ItemParams p);
 
 // Once per device, with that device current.
 bool setup(int dev, DevSetup*& out) {
@@ -137,6 +150,8 @@ bool setup(int dev, DevSetup*& out) {
   if (e == cudaSuccess) e = allow_all<256>();
   if (e == cudaSuccess) e = allow_all<512>();
   if (e == cudaSuccess) e = allow_all<1024>();
+  if (e == cudaSuccess) e = allow_smem(k_static_init, 0);
+  if (e == cudaSuccess) e = allow_smem(k_certify, 0);
   if (e != cudaSuccess) { s_err = std::string("kernel attributes: ") + cudaGetErrorString(e); return false; }
   d.ready = true;
   out = &d;

@@ -1,4 +1,17 @@
-"""Adjoint (ffcz_correct_backward) vs the oracle's vector-Jacobian product."""
+"""Adjoint (ffcz_correct_backward) vs the oracle's vector-Jacobian product,
+element by element.
+
+The product depends on the clips' active-set masks, and a mask entry whose
+pre-clip value lies within rounding of its bound may be decided either way by
+a float32 trajectory.  One such decision moves EVERY coordinate of the
+gradient (the DFT spreads it), so no coordinate can simply be excused.
+Instead the oracle lists the near ties of its own FP64 trajectory (entries
+within TAU of the bound, relative; far above the float32 drift of the GPU's
+trajectory) and computes, coordinate by coordinate, how far its product moves
+over other decisions of exactly those entries (``tie_spread``; zero where
+there is none).  Every coordinate of the GPU's product must then lie within
+GTOL * max|g| + 2 * spread of the oracle's.
+"""
 import numpy as np
 import pytest
 
@@ -7,32 +20,145 @@ from paper_2601_01596_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+TAU = 2e-5     # near-tie band of a clip decision, relative to its bound
+GTOL = 1e-4    # element-wise tolerance, relative to max|g| (float32 steps)
+
+
+def _assert_vjp_elementwise(got, e0, g, E, D, K, label, samples=8):
+    ref = O.correct_backward(e0, g, E, D, K)
+    spread, nnear = O.tie_spread(e0, g, E, D, K, TAU, samples=samples, seed=1)
+    scale = float(np.max(np.abs(ref)))
+    err = np.abs(got.astype(np.float64) - ref)
+    allow = GTOL * scale + 2.0 * spread
+    bad = err > allow
+    print(f"{label}: max|dg|/max|g| = {err.max() / scale:.2e}, near ties {nnear}, "
+          f"coordinates with spread > GTOL: {np.mean(spread > GTOL * scale):.4f}, "
+          f"max|dg| where spread = 0: {err[spread == 0].max(initial=0.0) / scale:.2e}")
+    assert not bad.any(), (label, int(bad.sum()), float((err - allow).max() / scale))
+    return ref, spread
+
+
+def _gpu_backward(shape, e0, g, E, D, K, m, ckpt=False):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    te0 = torch.from_numpy(np.ascontiguousarray(e0).reshape(-1).copy()).cuda()
+    tg = torch.from_numpy(np.ascontiguousarray(g, dtype=np.float32).reshape(-1).copy()).cuda()
+    gi = torch.empty_like(te0)
+    if ckpt:
+        plan = ffcz.Plan([shape], K=K, ckpt_every=m, min_iters=K, max_iters=K, certify=0)
+        ck = torch.empty(plan.ckpt_floats(), dtype=torch.float32, device="cuda")
+        plan.correct_ckpt(te0.clone(), [E], [D], ck)
+        plan.backward(te0, tg, gi, [E], [D], ckpt=ck)
+    else:
+        plan = ffcz.Plan([shape], K=K, ckpt_every=m)
+        plan.backward(te0, tg, gi, [E], [D])
+    return gi.cpu().numpy().reshape(shape)
+
 
 @pytest.mark.parametrize("shape,K,m", [((16, 16, 32), 5, 2), ((32, 64), 6, 4), ((16, 16, 16), 3, 10)])
 def test_backward_matches_oracle_vjp(shape, K, m):
-    import torch
-    import paper_2601_01596_b300 as ffcz
     e0 = W.bimodal_error(shape, 50, dtype=np.float32)
     E = 1.0
     D = 0.4 * O.f_violation(O.dft(e0.astype(np.float64)))
     g = np.random.default_rng(51).standard_normal(shape).astype(np.float32)
-    ref = O.correct_backward(e0, g, E, D, K)
-    plan = ffcz.Plan([shape], K=K, ckpt_every=m)
-    te0 = torch.from_numpy(e0.reshape(-1).copy()).cuda()
-    tg = torch.from_numpy(g.reshape(-1).copy()).cuda()
-    gi = torch.empty_like(te0)
-    plan.backward(te0, tg, gi, [E], [D])
-    got = gi.cpu().numpy().reshape(shape)
-    scale = np.max(np.abs(ref))
-    # masks can flip for values within FP32 rounding of a bound; allow a tiny
-    # fraction of outliers, require the rest to agree to FP32 accuracy
-    err = np.abs(got - ref)
-    assert np.mean(err > 1e-4 * scale) < 1e-3
-    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+    got = _gpu_backward(shape, e0, g, E, D, K, m)
+    _assert_vjp_elementwise(got, e0, g, E, D, K, f"bimodal{shape} K={K}")
+
+
+def _turbulence_like(shape, seed):
+    """The differentiable workload's recipe on any shape: a GRF with E(k) ~
+    k^-5/3, its quantisation error at eps_s = 1e-4 range, eps_f = 0.2 max box
+    violation of e0 (A11)."""
+    x = W.grf(shape, 5.0 / 3.0, seed).astype(np.float32)
+    E = 1e-4 * (float(x.max()) - float(x.min()))
+    e0 = W.quantization_error(x, E)
+    return x, e0, E, 0.2 * W.max_box_fft(e0)
+
+
+@pytest.mark.parametrize("shape", [(256, 8, 256), (8, 256, 256)])
+def test_backward_K50_m10_on_256_point_passes(shape):
+    """The differentiable workload's K = 50 forced iterations with a
+    checkpoint every 10, on shapes whose z / y and x passes are the
+    256-point kernels of the 256^3 form (checkpoints written by the forward,
+    as the autograd function runs it)."""
+    K, m = 50, 10
+    x, e0, E, D = _turbulence_like(shape, 7)
+    g = np.random.default_rng(52).standard_normal(shape).astype(np.float32)
+    got = _gpu_backward(shape, e0, g, E, D, K, m, ckpt=True)
+    _assert_vjp_elementwise(got, e0, g, E, D, K, f"turbulence{shape} K=50", samples=4)
+
+
+def test_config5_crop_gradient_matches_fp64_finite_differences():
+    """The differentiable workload's own check: the gradient on a 32^3 crop of
+    the 256^3 turbulence field (an independent 32^3 problem: e0, the field's
+    eps_s, eps_f by A11 on the crop), K = 50, checkpoint every 10, against
+    central finite differences of the FP64 oracle's forward map (step 1e-6
+    eps_s): for L(e0) = <g, e_K(e0)> along random directions and along
+    single coordinates, and for the power-spectrum loss through the autograd
+    function."""
+    import torch
+    from paper_2601_01596_b300.autograd import FFCzCorrect, power_spectrum_loss
+    it = W.turbulence_field(256, seed=0)
+    c = (slice(0, 32),) * 3
+    x = np.ascontiguousarray(it["x"][c])
+    e0 = np.ascontiguousarray(it["e0"][c])
+    E = it["E"]
+    D = 0.2 * W.max_box_fft(e0)
+    del it
+    K, m, shape = 50, 10, (32, 32, 32)
+    e0d = e0.astype(np.float64)
+    h = 1e-6 * E
+    g = np.random.default_rng(53).standard_normal(shape).astype(np.float32).astype(np.float64)
+    got = _gpu_backward(shape, e0, g, E, D, K, m, ckpt=True).astype(np.float64)
+    ref, spread = _assert_vjp_elementwise(got, e0, g, E, D, K, "crop32 K=50")
+
+    def L(e):
+        return float(np.sum(g * O.forward_masks(e, E, D, K)[0]))
+    rng = np.random.default_rng(54)
+    for j in range(4):
+        v = rng.standard_normal(shape)
+        fd = (L(e0d + h * v) - L(e0d - h * v)) / (2 * h)
+        # the oracle's product is the derivative of its own map ...
+        assert abs(fd - np.sum(ref * v)) <= 1e-6 * np.linalg.norm(ref) * np.linalg.norm(v), j
+        # ... and the GPU's is within its element-wise allowance of it
+        slack = GTOL * np.max(np.abs(ref)) * np.sum(np.abs(v)) + 2.0 * np.sum(spread * np.abs(v))
+        assert abs(fd - np.sum(got * v)) <= slack + 1e-6 * np.linalg.norm(ref) * np.linalg.norm(v), j
+    for p in map(tuple, rng.integers(0, 32, size=(16, 3))):
+        u = np.zeros(shape)
+        u[p] = 1.0
+        fd = (L(e0d + h * u) - L(e0d - h * u)) / (2 * h)
+        assert abs(fd - ref[p]) <= 1e-6 * np.max(np.abs(ref)), p
+        assert abs(fd - got[p]) <= GTOL * np.max(np.abs(ref)) + 2.0 * spread[p] + 1e-6 * np.max(np.abs(ref)), p
+
+    # the power-spectrum loss of the workload, through torch.autograd
+    xt = torch.from_numpy(x).cuda()
+    e0t = torch.from_numpy(e0).cuda().requires_grad_(True)
+    loss = power_spectrum_loss(xt, FFCzCorrect.apply(e0t, E, D, K, m))
+    loss.backward()
+    g_gpu = e0t.grad.cpu().numpy().astype(np.float64)
+    xd = torch.from_numpy(x.astype(np.float64))
+
+    def Ls(e):
+        return float(power_spectrum_loss(xd, torch.from_numpy(O.forward_masks(e, E, D, K)[0])))
+    eK = torch.from_numpy(O.forward_masks(e0d, E, D, K)[0]).requires_grad_(True)
+    power_spectrum_loss(xd, eK).backward()
+    gl = eK.grad.numpy()
+    ref_l = O.correct_backward(e0, gl, E, D, K)
+    spread_l, _ = O.tie_spread(e0, gl, E, D, K, TAU, samples=4, seed=2)
+    scale = np.max(np.abs(ref_l))
+    err = np.abs(g_gpu - ref_l)
+    assert np.all(err <= 1e-3 * scale + 2.0 * spread_l), float(err.max() / scale)
+    for j in range(2):
+        v = rng.standard_normal(shape)
+        fd = (Ls(e0d + h * v) - Ls(e0d - h * v)) / (2 * h)
+        assert abs(fd - np.sum(ref_l * v)) <= 1e-5 * np.linalg.norm(ref_l) * np.linalg.norm(v), j
 
 
 def test_autograd_function_matches_oracle_through_spectrum_loss():
-    """d loss / d e0 for loss = log power-spectrum mismatch of x + e_K vs x."""
+    """d loss / d e0 for loss = log power-spectrum mismatch of x + e_K vs x,
+    element by element against the oracle's product of the FP64 loss
+    gradient (the loss gradient itself is taken at float32 e_K on the GPU:
+    GTOL * 10)."""
     import torch
     from paper_2601_01596_b300.autograd import FFCzCorrect, power_spectrum_loss
     it = W.turbulence_field(16, seed=4)
@@ -48,9 +174,13 @@ def test_autograd_function_matches_oracle_through_spectrum_loss():
     et = torch.from_numpy(eK_ref).requires_grad_(True)
     lref = power_spectrum_loss(torch.from_numpy(it["x"].astype(np.float64)), et)
     lref.backward()
-    g_ref = O.correct_backward(it["e0"], et.grad.numpy(), it["E"], it["D"], K)
+    gl = et.grad.numpy()
+    g_ref = O.correct_backward(it["e0"], gl, it["E"], it["D"], K)
+    spread, _ = O.tie_spread(it["e0"], gl, it["E"], it["D"], K, TAU, samples=8, seed=3)
     assert abs(loss.item() - lref.item()) <= 1e-3 * abs(lref.item()) + 1e-9
-    assert np.linalg.norm(g_gpu - g_ref) <= 2e-3 * np.linalg.norm(g_ref)
+    scale = np.max(np.abs(g_ref))
+    err = np.abs(g_gpu - g_ref)
+    assert np.all(err <= 10 * GTOL * scale + 2.0 * spread), float(err.max() / scale)
 
 
 def test_backward_with_copy_engine_fed_x_pass_equals_plain(monkeypatch):
