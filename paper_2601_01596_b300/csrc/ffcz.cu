@@ -53,14 +53,21 @@ void fail(ffcz_status s, const std::string& msg) {
 
 bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// exp(-2 pi i m / L) in long double, rounded once (exact zeros kept exact).
-template <typename T>
-v2<T> root(long double m, long double L) {
+// exp(-2 pi i m / L) in long double (exact zeros kept exact).
+void root_ld(long double m, long double L, long double& c, long double& s) {
   static const long double pi = acosl(-1.0L);
   const long double a = 2.0L * pi * m / L;
-  long double c = cosl(a), s = -sinl(a);
+  c = cosl(a);
+  s = -sinl(a);
   if (fabsl(c) < 1e-18L) c = 0.0L;
   if (fabsl(s) < 1e-18L) s = 0.0L;
+}
+
+// exp(-2 pi i m / L) rounded once to T.
+template <typename T>
+v2<T> root(long double m, long double L) {
+  long double c, s;
+  root_ld(m, L, c, s);
   v2<T> r;
   r.x = (T)c;
   r.y = (T)s;
@@ -83,7 +90,16 @@ std::vector<v2<T>> stage_table_rt(int L) {
   std::vector<v2<T>> t(L);
   for (auto& x : t) { x.x = 0; x.y = 0; }
   for (int k1 = 0; k1 < R1; ++k1)
-    for (int tt = 1; tt < R2; ++tt) t[tw_index(R1, k1, tt)] = root<T>((long double)k1 * tt, (long double)L);
+    for (int tt = 1; tt < R2; ++tt) {
+      if constexpr (sizeof(T) == 8) {
+        // FP64: factors tt >= R2/2 in the tangent form of the fused layer
+        long double c, sn;
+        root_ld((long double)k1 * tt, (long double)L, c, sn);
+        t[tw_index(R1, k1, tt)] = f64_stage_entry(c, sn, tt >= R2 / 2);
+      } else {
+        t[tw_index(R1, k1, tt)] = root<T>((long double)k1 * tt, (long double)L);
+      }
+    }
   return t;
 }
 

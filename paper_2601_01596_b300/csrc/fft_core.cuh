@@ -34,7 +34,9 @@
 // t+1 of one k1 are adjacent (one 128-bit load in float32) and, for a fixed
 // pair, the k1 of consecutive threads are consecutive, so a warp's loads hit
 // distinct banks.  Computed on the host in long double and rounded once; the
-// inverse uses the conjugates.
+// inverse uses the conjugates.  The FP64 table holds the factors t >= R2/2 in
+// the tangent form (c, s/c) that the fused first butterfly layer of stage 2
+// reads (fold_rt; host side: f64_stage_entry).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -199,9 +201,14 @@ __device__ __forceinline__ void dft_ab(v2<T> (&x)[A * B]) {
   for (int i = 0; i < N; ++i) x[i] = o[i];
 }
 
+template <int R, int DIR>
+__device__ __forceinline__ void dftN_f64(double2 (&x)[R]);
+
 template <int R, typename T, int DIR>
 __device__ __forceinline__ void dftN(v2<T> (&x)[R]) {
-  if constexpr (R == 1) {
+  if constexpr (sizeof(T) == 8) {
+    dftN_f64<R, DIR>(x);
+  } else if constexpr (R == 1) {
   } else if constexpr (R == 2) {
     const v2<T> a = x[0];
     x[0] = add<T>(a, x[1]);
@@ -215,6 +222,143 @@ __device__ __forceinline__ void dftN(v2<T> (&x)[R]) {
   } else {
     static_assert(R == 32, "register DFT sizes 1..32");
     dft_ab<T, DIR, 8, 4>(x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 register DFTs with the twiddle products fused into the butterflies.
+//
+// On B300 the FP64 pipe issues fused multiply-adds faster than separate adds
+// or multiplies, and the FP64 passes are bound by that pipe.  A twiddled
+// butterfly y+- = p +- w q costs 8 operations as a complex product followed
+// by two complex additions; written in the tangent form of Goedecker
+// (SIAM J. Sci. Comput. 18(6), 1997), w = c (1 + i tau) with tau = s / c,
+//   t = q (1 + i tau)      2 FMAs
+//   y+- = p +- c t         4 FMAs,
+// it costs 6 FMAs (the cotangent form w = s (kappa + i), kappa = c / s, when
+// |s| > |c|; 2 adds + 4 FMAs for the odd multiples of pi/4).  Every product
+// and sum is still rounded once per operation, so each output component
+// carries at most two roundings of a product-sum, as in the plain form.
+//
+// Structure: a size-R DFT is its first radix-2 layer, pairs (i, i + R/2),
+// then dpost1<R>, the rest of the transform given that layer's results
+// x[i] = a_i + a_{i+R/2} (P_i), x[i+R/2] = a_i - a_{i+R/2} (Q_i).  The
+// stage-2 DFT of fft_pencil fuses the table twiddles into its first layer
+// (fold_rt); the internal twiddles of the 16- and 32-point DFTs are folded
+// into the first layer of their 4-point DFTs (fold_c).
+// ---------------------------------------------------------------------------
+
+// y+ = p + w q, y- = p - w q, w = exp(DIR 2 pi i m / 32), m a compile-time
+// constant after unrolling (every branch but one folds away).
+template <int DIR>
+__device__ __forceinline__ void fold_c(double2 p, double2 q, int m, double2& yp, double2& ym) {
+  m &= 31;
+  if (m == 0) { yp = add<double>(p, q); ym = sub<double>(p, q); return; }
+  if (m == 16) { yp = sub<double>(p, q); ym = add<double>(p, q); return; }
+  if (m == 8) { yp = add_mul_i<double, DIR>(p, q); ym = sub_mul_i<double, DIR>(p, q); return; }
+  if (m == 24) { yp = sub_mul_i<double, DIR>(p, q); ym = add_mul_i<double, DIR>(p, q); return; }
+  const double c = cos32(m), sn = DIR * sin32(m);
+  double2 t;
+  double f;
+  if ((m & 3) == 0 && (m & 7) != 0) {
+    // odd multiple of pi/4: |c| = |s|, tau = s / c = +-1 exactly
+    if ((c > 0) == (sn > 0)) t = mk<double>(q.x - q.y, q.y + q.x);   // tau = +1
+    else t = mk<double>(q.x + q.y, q.y - q.x);                       // tau = -1
+    f = c;
+  } else if (fabs(c) >= fabs(sn)) {
+    const double tau = sn / c;
+    t = mk<double>(fma(-tau, q.y, q.x), fma(tau, q.x, q.y));
+    f = c;
+  } else {
+    const double kap = c / sn;                                       // w = s (kappa + i)
+    t = mk<double>(fma(kap, q.x, -q.y), fma(kap, q.y, q.x));
+    f = sn;
+  }
+  yp = mk<double>(fma(f, t.x, p.x), fma(f, t.y, p.y));
+  ym = mk<double>(fma(-f, t.x, p.x), fma(-f, t.y, p.y));
+}
+
+// The same with a table twiddle in tangent form: ct = (c, tau) of the
+// forward factor w = c (1 + i tau); the inverse (DIR = +1) uses conj(w).
+template <int DIR>
+__device__ __forceinline__ void fold_rt(double2 p, double2 q, double2 ct, double2& yp, double2& ym) {
+  const double tau = DIR < 0 ? ct.y : -ct.y;
+  const double2 t = mk<double>(fma(-tau, q.y, q.x), fma(tau, q.x, q.y));
+  yp = mk<double>(fma(ct.x, t.x, p.x), fma(ct.x, t.y, p.y));
+  ym = mk<double>(fma(-ct.x, t.x, p.x), fma(-ct.x, t.y, p.y));
+}
+
+// The 4-point DFT given its first layer (P0, P1 | Q0, Q1) in x[0..3].
+template <int DIR>
+__device__ __forceinline__ void dpost1_4(double2& x0, double2& x1, double2& x2, double2& x3) {
+  const double2 P0 = x0, P1 = x1, Q0 = x2, Q1 = x3;
+  x0 = add<double>(P0, P1);
+  x2 = sub<double>(P0, P1);
+  x1 = add_mul_i<double, DIR>(Q0, Q1);
+  x3 = sub_mul_i<double, DIR>(Q0, Q1);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dpost1(double2 (&x)[R]) {
+  if constexpr (R == 2) {
+    // the first layer is the whole transform
+  } else if constexpr (R == 4) {
+    dpost1_4<DIR>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 8) {
+    // even half (a0, a2, a4, a6): first layer (P0, P2 | Q0, Q2); odd half
+    // (a1, a3, a5, a7): (P1, P3 | Q1, Q3); then X_k, X_{k+4} = E_k +- w8^k O_k
+    double2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    double2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    dpost1_4<DIR>(e0, e1, e2, e3);
+    dpost1_4<DIR>(o0, o1, o2, o3);
+    fold_c<DIR>(e0, o0, 0, x[0], x[4]);
+    fold_c<DIR>(e1, o1, 4, x[1], x[5]);
+    fold_c<DIR>(e2, o2, 8, x[2], x[6]);
+    fold_c<DIR>(e3, o3, 12, x[3], x[7]);
+  } else {
+    // 16 = 4 x 4 and 32 = 8 x 4 (Cooley-Tukey, as dft_ab): A-point DFTs
+    // over a_{b + 4a} (b = 0..3), internal twiddles w_R^{b k1}, 4-point DFTs
+    // over b whose first layer takes the twiddles (fold_c).
+    static_assert(R == 16 || R == 32, "FP64 register DFT sizes 2..32");
+    constexpr int A = R / 4, H = R / 2, S = 32 / R;
+    double2 T[4][A];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      // the first layer of the A-point DFT over a_{b + 4a} pairs a and a + A/2,
+      // i.e. a_{b+4a} with a_{b+4a+H}: P_{b+4a} and Q_{b+4a}
+      double2 t[A];
+#pragma unroll
+      for (int a = 0; a < A / 2; ++a) {
+        t[a] = x[b + 4 * a];
+        t[a + A / 2] = x[b + 4 * a + H];
+      }
+      dpost1<A, DIR>(t);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) T[b][k1] = t[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      double2 y[4];
+      fold_c<DIR>(T[0][k1], T[2][k1], 2 * k1 * S, y[0], y[2]);
+      const double2 p1 = mul_w32<double, DIR>(T[1][k1], k1 * S);
+      fold_c<DIR>(p1, T[3][k1], 3 * k1 * S, y[1], y[3]);
+      dpost1_4<DIR>(y[0], y[1], y[2], y[3]);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) x[k1 + A * k2] = y[k2];
+    }
+  }
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dftN_f64(double2 (&x)[R]) {
+  if constexpr (R > 1) {
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      const double2 a = x[i], b = x[i + R / 2];
+      x[i] = add<double>(a, b);
+      x[i + R / 2] = sub<double>(a, b);
+    }
+    dpost1<R, DIR>(x);
   }
 }
 
@@ -240,6 +384,29 @@ inline int f2_v(int L) { return L / f2_nt(L); }
 // Table entry of factor t (1 <= t < R2) of stage-2 row k1 (layout above).
 __host__ __device__ constexpr int tw_index(int R1, int k1, int t) {
   return ((t - 1) >> 1) * 2 * R1 + 2 * k1 + ((t - 1) & 1);
+}
+
+// Host side of the FP64 stage table: entry of the factor w = c + i s
+// (c = cos, s = -sin of 2 pi k1 t / L, already rounded to exact zeros where
+// the exact value is zero).  Factors t < R2/2: (c, s).  Factors t >= R2/2:
+// the tangent form (c, tau), tau = s / c, both rounded once from the long
+// double values; at c = 0 (w = -+i) the pair (2^-600, s 2^600), whose
+// product form c (1 + i tau) equals w to within 2^-600 relative (far below
+// the rounding unit; no overflow for any finite float32-derived operand,
+// which stays below 2^160 in magnitude).
+inline double2 f64_stage_entry(long double c, long double s, bool tangent) {
+  double2 r;
+  if (!tangent) {
+    r.x = (double)c;
+    r.y = (double)s;
+  } else if (c == 0.0L) {
+    r.x = 0x1p-600;
+    r.y = (double)(s * 0x1p600L);
+  } else {
+    r.x = (double)c;
+    r.y = (double)(s / c);
+  }
+  return r;
 }
 
 // Pencils per tile of the strided passes: 64-byte rows (8 float32 or 4
@@ -302,11 +469,19 @@ __device__ __forceinline__ void fft_pencil(v2<T> (&v)[F2<L>::V], int j, const v2
       v[2 * i + 1] = twmul<T, DIR>(v[2 * i + 1], mk<T>(f.x, f.y));
       if (2 * i + 2 < R2) v[2 * i + 2] = twmul<T, DIR>(v[2 * i + 2], mk<T>(f.z, f.w));
     }
+    dftN<R2, T, DIR>(v);
   } else {
+    // the stage-2 DFT's first layer, pairs (t, t + R2/2), with the table
+    // twiddles fused in: factor t < R2/2 as a complex product, factor
+    // t + R2/2 in tangent form (c, tau) folded into the butterfly
+    constexpr int H = R2 / 2;
 #pragma unroll
-    for (int t = 1; t < R2; ++t) v[t] = twmul<T, DIR>(v[t], tw[tw_index(R1, j, t)]);
+    for (int t = 0; t < H; ++t) {
+      const v2<T> p = t == 0 ? v[0] : twmul<T, DIR>(v[t], tw[tw_index(R1, j, t)]);
+      fold_rt<DIR>(p, v[t + H], tw[tw_index(R1, j, t + H)], v[t], v[t + H]);
+    }
+    dpost1<R2, DIR>(v);
   }
-  dftN<R2, T, DIR>(v);
 }
 
 // Exchange in natural order: every thread stores its registers, the tile

@@ -70,20 +70,31 @@ std::mutex s_mu;
 
 long double twopi() { return 2.0L * acosl(-1.0L); }
 
-double2 root64(long double m, long double L) {
+void root_ld(long double m, long double L, long double& c, long double& s) {
   const long double a = twopi() * m / L;
-  long double c = cosl(a), s = -sinl(a);
+  c = cosl(a);
+  s = -sinl(a);
   if (fabsl(c) < 1e-18L) c = 0.0L;
   if (fabsl(s) < 1e-18L) s = 0.0L;
+}
+
+double2 root64(long double m, long double L) {
+  long double c, s;
+  root_ld(m, L, c, s);
   return make_double2((double)c, (double)s);
 }
 
-// Stage-2 twiddles of the two-stage split of L (layout in fft_core.cuh).
+// Stage-2 twiddles of the two-stage split of L (layout in fft_core.cuh; the
+// factors t >= R2/2 in tangent form).
 void stage_factors_rt(int L, std::vector<double2>& out) {
   const int R1 = f2_nt(L), R2 = L / R1;
   out.assign(L, make_double2(0.0, 0.0));
   for (int k1 = 0; k1 < R1; ++k1)
-    for (int t = 1; t < R2; ++t) out[tw_index(R1, k1, t)] = root64((long double)k1 * t, (long double)L);
+    for (int t = 1; t < R2; ++t) {
+      long double c, s;
+      root_ld((long double)k1 * t, (long double)L, c, s);
+      out[tw_index(R1, k1, t)] = f64_stage_entry(c, s, t >= R2 / 2);
+    }
 }
 
 // Queries the kernel's attributes, which makes a lazily loading runtime load
