@@ -66,8 +66,7 @@ __global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab) {
 // Column pass along n1 / k1 (length P1 = L), tile = W consecutive columns.
 // The chirp of each value is read from the item's table where it is used.
 template <typename T, int L, int W_ = TileW<T>::value>
-__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
-k1_col(Args a) {
+__device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const int by_) {
   FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int NT = G_::NT, W = G_::W;
   const int P2 = a.g.M;
@@ -210,11 +209,15 @@ k1_col(Args a) {
     for (int u = 0; u < V; ++u) out[u * ustride] = cmul<T>(v[u], twp[(j + u * NT) * n2]);
   }
 }
+template <typename T, int L, int W_ = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
+k1_col(Args a) {
+  k1_col_body<T, L, W_>(a, (int)blockIdx.x, (int)blockIdx.y);
+}
 
 // Row pass along n2 / k2 (length P2 = L), tile = W consecutive rows.
 template <typename T, int L, int W_ = TileW<T>::value>
-__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
-k1_row(Args a) {
+__device__ __forceinline__ void k1_row_body(const Args& a, const int bx_, const int by_) {
   FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int NT = G_::NT;
   const int P1 = a.g.Nz;
@@ -241,6 +244,11 @@ k1_row(Args a) {
 #pragma unroll
     for (int u = 0; u < V; ++u) out[u * NT] = v[u];
   }
+}
+template <typename T, int L, int W_ = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
+k1_row(Args a) {
+  k1_row_body<T, L, W_>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 }  // namespace ffcz

@@ -25,6 +25,7 @@
 #include "bluestein.cuh"
 #include "passes.cuh"
 #include "edits.cuh"
+#include "multi.cuh"
 
 using namespace ffcz;
 
@@ -250,6 +251,13 @@ struct ffcz_plan_s {
   std::vector<cudaEvent_t> evpool;
   std::map<std::string, std::pair<double, int64_t>> prof_tab;
   std::vector<std::string> prof_keys;
+
+  // multi-group form of the loop passes (one launch per pass kind over the
+  // members of every shape group, multi.cuh): the work list of each kind,
+  // the grid and shared memory of its launch, and whether the tuner took it
+  struct MultiPlan { int2* units = nullptr; int64_t n = 0; int grid = 0; size_t smem = 0; };
+  MultiPlan mp[MK_N];
+  bool multi_use[MK_N] = {};
 
   // backward workspace
   float* bw_e = nullptr;
@@ -905,6 +913,140 @@ void row1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
   a.op1 = op;
 }
 
+// ----- multi-group form of the loop passes -------------------------------------
+// The pass length and the two extents (multi_grid_of) of kind k for group dg.
+int multi_len(int k, const DevGroup& dg) {
+  switch (k) {
+    case MK_PX: return dg.M;
+    case MK_YINV: case MK_YFWD: return dg.Ny;
+    case MK_CHK: return dg.Nz;
+    case MK_COL1: return dg.P1;
+    default: return dg.P2;
+  }
+}
+template <int KIND>
+struct MG {
+  template <int L>
+  static void go(const DevGroup& dg, MultiGrid& r) {
+    if constexpr (KIND == MK_PX) r = multi_grid_of<KIND, L>(dg.rows, 0);
+    else if constexpr (KIND == MK_YINV || KIND == MK_YFWD) r = multi_grid_of<KIND, L>(dg.Nz, dg.M);
+    else if constexpr (KIND == MK_CHK) r = multi_grid_of<KIND, L>(dg.M, dg.ndim == 3 ? dg.Ny : 1);
+    else if constexpr (KIND == MK_COL1) r = multi_grid_of<KIND, L>(dg.P2, 0);
+    else r = multi_grid_of<KIND, L>(dg.P1, 0);
+  }
+};
+template <int KIND>
+MultiGrid multi_grid(const DevGroup& dg) {
+  MultiGrid r{0, 0};
+  FFCZ_DISPATCH_L(multi_len(KIND, dg), MG<KIND>::template go, dg, r)
+  return r;
+}
+template <int KIND>
+void* multi_kernel() { return reinterpret_cast<void*>(&k_multi<KIND>); }
+
+// Work list of kind KIND over every group (groups of longer transforms
+// first, then member by member), its shared memory and the grid of its
+// persistent launch (as many 128-thread CTAs as fit on the device).
+template <int KIND>
+void build_multi_kind(ffcz_plan_s* p) {
+  const int ng = (int)p->groups.size();
+  std::vector<int> order(ng);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return multi_len(KIND, p->groups[x]) > multi_len(KIND, p->groups[y]);
+  });
+  std::vector<int2> units;
+  size_t smem = 0;
+  for (int g : order) {
+    const DevGroup& dg = p->groups[g];
+    const MultiGrid mg = multi_grid<KIND>(dg);
+    smem = std::max(smem, mg.smem);
+    for (int gi = 0; gi < dg.count; ++gi)
+      for (int64_t bx = 0; bx < mg.gx; ++bx) units.push_back(make_int2(g | (gi << 4), (int)bx));
+  }
+  auto& m = p->mp[KIND];
+  m.n = (int64_t)units.size();
+  m.smem = smem;
+  if (smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_multi<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi<KIND>, kMultiThreads, smem));
+  m.grid = (int)std::min<int64_t>(m.n, (int64_t)std::max(per_sm, 1) * p->num_sms);
+  m.units = static_cast<int2*>(dalloc(p, sizeof(int2) * units.size()));
+  CK(cudaMemcpy(m.units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice));
+}
+
+// Work lists of the pass kinds the plan's loop runs, for plans of 2 to
+// kMultiGroups groups.
+void build_multi(ffcz_plan_s* p) {
+  const int ng = (int)p->groups.size();
+  if (ng < 2 || ng > kMultiGroups) return;
+  if (p->ndim == 1) {
+    build_multi_kind<MK_COL1>(p);
+    build_multi_kind<MK_ROW1>(p);
+    return;
+  }
+  build_multi_kind<MK_PX>(p);
+  build_multi_kind<MK_CHK>(p);
+  if (p->ndim == 3) {
+    build_multi_kind<MK_YINV>(p);
+    build_multi_kind<MK_YFWD>(p);
+  }
+}
+
+const char* multi_name(int k) {
+  static const char* n[MK_N] = {"px", "axis_inv", "axis_fwd", "chk", "col1", "row1"};
+  return n[k];
+}
+// profile key of a multi-group launch ("multi_chk<f32,0>": every length)
+const char* multi_prof_name(int k) {
+  static const char* n[MK_N] = {"multi_px", "multi_axis_inv", "multi_axis_fwd", "multi_chk", "multi_col1",
+                                "multi_row1"};
+  return n[k];
+}
+void* multi_kernel_of(int k) {
+  switch (k) {
+    case MK_PX: return multi_kernel<MK_PX>();
+    case MK_YINV: return multi_kernel<MK_YINV>();
+    case MK_YFWD: return multi_kernel<MK_YFWD>();
+    case MK_CHK: return multi_kernel<MK_CHK>();
+    case MK_COL1: return multi_kernel<MK_COL1>();
+    default: return multi_kernel<MK_ROW1>();
+  }
+}
+
+// One multi-group launch of kind k with the per-group arguments `args`
+// (p->groups order), if the plan took the multi-group form for k and every
+// argument set is one the form covers (float32, Alg. 1, no pointwise
+// bounds, lean passes: no adjoint modes, checkpoints or edit recording).
+// Returns false if the caller must launch the groups separately.
+template <typename T>
+bool multi_launch(ffcz_plan_s* p, int k, const std::vector<Args>& args, cudaStream_t s, bool force = false) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    const auto& m = p->mp[k];
+    if ((!p->multi_use[k] && !force) || m.n == 0 || g_pw_sel) return false;
+    for (const Args& a : args) {
+      if (a.pw_e || a.pw_f || a.pv != PV_POCS) return false;
+      if (k == MK_PX && px_full(a)) return false;
+      if (k == MK_CHK && chk_full(a)) return false;
+    }
+    MultiArgs ma{};
+    for (size_t g = 0; g < args.size(); ++g) {
+      ma.a[g] = args[g];
+      ma.len[g] = multi_len(k, p->groups[g]);
+    }
+    ma.units = m.units;
+    ma.nunits = m.n;
+    ProfScope ps(multi_prof_name(k), 32, 0, s);
+    void* params[] = {&ma};
+    CK(cudaLaunchKernel(multi_kernel_of(k), dim3((unsigned)m.grid), dim3(kMultiThreads), params, m.smem, s));
+    g_launches++;
+    return true;
+  }
+}
+
 // Chirp tables and Bt = FFT_P(wrapped chirp) for every 1D item, in the
 // precision T.
 template <typename T>
@@ -976,21 +1118,29 @@ void entry1(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStre
 
 template <typename T>
 void body1(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
-  for (auto& dg : p->groups) {
-    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
-    row1_args<T>(p, a, dg, OP1_CONVC);
-    a.sel_in = S_PREV; a.sel_out = S_CUR;
-    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
-    a.sel_in = S_CUR;
-    col1_args<T>(p, a, dg, OP1_SCLIP);
-    a.mode = M_CLIP | cnt_flag(p);
-    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
-    row1_args<T>(p, a, dg, OP1_CONV);
-    a.mode = 0;
-    launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
-    col1_args<T>(p, a, dg, OP1_FCLIP);
-    a.mode = M_CLIP | cnt_flag(p);
-    launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
+  // four passes, each over every group (one launch per group, or one
+  // multi-group launch); items of different groups are independent, so
+  // only the order of the passes matters
+  const int ng = (int)p->groups.size();
+  std::vector<Args> args(ng);
+  for (int step = 0; step < 4; ++step) {
+    const bool row = step % 2 == 0;
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+      a.sel_in = a.sel_out = S_CUR;
+      if (step == 0) { row1_args<T>(p, a, dg, OP1_CONVC); a.sel_in = S_PREV; }
+      if (step == 1) { col1_args<T>(p, a, dg, OP1_SCLIP); a.mode = M_CLIP | cnt_flag(p); }
+      if (step == 2) { row1_args<T>(p, a, dg, OP1_CONV); a.mode = 0; }
+      if (step == 3) { col1_args<T>(p, a, dg, OP1_FCLIP); a.mode = M_CLIP | cnt_flag(p); }
+      args[g] = a;
+    }
+    if (multi_launch<T>(p, row ? MK_ROW1 : MK_COL1, args, s)) continue;
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      if (row) launch_row1<T>(dg.P2, dg.w1r, args[g], dg.P1, dg.count, s);
+      else launch_col1<T>(dg.P1, dg.w1c, args[g], dg.P2, dg.count, s);
+    }
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
                                                              p->d_nactive);
@@ -1053,16 +1203,31 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
 template <typename T>
 void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
   if (p->ndim == 1) { body1<T>(p, B, s); return; }
-  for (auto& dg : p->groups) {
-    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
-    if (dg.ndim == 3) {
+  // y inverse (3D), x pass, y forward (3D), check pass, each over every
+  // group (one launch per group, or one multi-group launch); items of
+  // different groups are independent, so only the order of the passes matters
+  const int ng = (int)p->groups.size();
+  const bool three = p->ndim == 3;
+  std::vector<Args> args(ng);
+  if (three) {
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
       a.tw = tw_of<T>(p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
-      launch_axis<T, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
-      a.sel_in = S_CUR;
-    } else {
-      a.sel_in = S_PREV; a.sel_out = S_CUR;
+      args[g] = a;
     }
+    if (!multi_launch<T>(p, MK_YINV, args, s))
+      for (int g = 0; g < ng; ++g) {
+        const DevGroup& dg = p->groups[g];
+        launch_axis<T, +1>(dg.Ny, dg.wa, args[g], dg.Nz, dg.M, dg.count, s);
+      }
+  }
+  for (int g = 0; g < ng; ++g) {
+    const DevGroup& dg = p->groups[g];
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    a.sel_in = three ? S_CUR : S_PREV;
+    a.sel_out = S_CUR;
     tabs_x<T>(p, a, dg);
     a.mode = M_CLIP | cnt_flag(p);
     if (sizeof(T) == 4 && p->ck_rec) {
@@ -1070,19 +1235,41 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
       a.ckpt = p->bw_ck;
       a.ckpt_every = p->bw_m;
     }
-    launch_x<T>(XPX, dg.M, dg.wx, a, dg.rows, dg.count, s);
-    a.ckpt = nullptr;
-    a.ckpt_every = 0;
-    a.sel_in = a.sel_out = S_CUR;
-    if (dg.ndim == 3) {
+    args[g] = a;
+  }
+  if (!multi_launch<T>(p, MK_PX, args, s))
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      launch_x<T>(XPX, dg.M, dg.wx, args[g], dg.rows, dg.count, s);
+    }
+  if (three) {
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+      a.sel_in = a.sel_out = S_CUR;
       a.tw = tw_of<T>(p->tb, dg.Ny);
       a.mode = 0;
-      launch_axis<T, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
+      args[g] = a;
     }
+    if (!multi_launch<T>(p, MK_YFWD, args, s))
+      for (int g = 0; g < ng; ++g) {
+        const DevGroup& dg = p->groups[g];
+        launch_axis<T, -1>(dg.Ny, dg.wa, args[g], dg.Nz, dg.M, dg.count, s);
+      }
+  }
+  for (int g = 0; g < ng; ++g) {
+    const DevGroup& dg = p->groups[g];
+    Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
+    a.sel_in = a.sel_out = S_CUR;
     a.tw = tw_of<T>(p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
-    launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+    args[g] = a;
   }
+  if (!multi_launch<T>(p, MK_CHK, args, s))
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      launch_chk<T>(dg.Nz, dg.wc, args[g], dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
+    }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
                                                              p->d_nactive, s_check_of<T>(p));
   g_launches++;
@@ -2219,6 +2406,74 @@ int pick_width(ffcz_plan_s* p, const std::string& key, int dflt, std::vector<int
   return best;
 }
 
+// FFCZ_TUNE_FORCE="...,multi=1" (or 0) fixes the form of every loop pass
+// of multi-group plans; returns -1 when not forced.
+int forced_multi() {
+  const char* f = getenv("FFCZ_TUNE_FORCE");
+  if (!f) return -1;
+  const std::string spec(f);
+  const size_t pos = spec.find("multi=");
+  if (pos == std::string::npos) return -1;
+  return spec[pos + 6] == '1' ? 1 : 0;
+}
+
+// For plans of several shape groups: time each pass kind of the float32
+// loop over all groups, as separate launches (each group's tuned variant)
+// and as one multi-group launch, and keep the faster form per kind.
+void tune_multi(ffcz_plan_s* p) {
+  const int ng = (int)p->groups.size();
+  const int forced = forced_multi();
+  cudaStream_t s = p->stream;
+  std::string gkey = "multi_d" + std::to_string(p->ndim);
+  for (const auto& dg : p->groups) {
+    char b[96];
+    snprintf(b, sizeof b, "_%dx%dx%dx%d_%d", dg.Nz, dg.Ny, dg.Nx, dg.P1, dg.count);
+    gkey += b;
+  }
+  for (int k = 0; k < MK_N; ++k) {
+    if (p->mp[k].n == 0) continue;
+    if (forced >= 0) { p->multi_use[k] = forced == 1; continue; }
+    if (g_no_tune) continue;
+    const std::string key = gkey + "_" + multi_name(k);
+    {
+      std::lock_guard<std::mutex> lk(tune_mu());
+      tune_load();
+      auto it = tune_table().find(key);
+      if (it != tune_table().end()) { p->multi_use[k] = it->second == 1; continue; }
+    }
+    std::vector<Args> args(ng);
+    for (int g = 0; g < ng; ++g) {
+      const DevGroup& dg = p->groups[g];
+      Args a = make_args<float>(p, dg, p->B32[0], p->B32[1], p->d_st);
+      a.pred = P_ALL;
+      if (k == MK_PX) { tabs_x<float>(p, a, dg); a.mode = M_CLIP; }
+      else if (k == MK_YINV || k == MK_YFWD) a.tw = tw_of<float>(p->tb, dg.Ny);
+      else if (k == MK_CHK) { a.tw = tw_of<float>(p->tb, dg.Nz); a.mode = M_CLIP; }
+      else if (k == MK_COL1) { col1_args<float>(p, a, dg, OP1_SCLIP); a.mode = M_CLIP; }
+      else row1_args<float>(p, a, dg, OP1_CONV);
+      args[g] = a;
+    }
+    const float t_sep = time_launches(p, [&] {
+      for (int g = 0; g < ng; ++g) {
+        const DevGroup& dg = p->groups[g];
+        const Args& a = args[g];
+        switch (k) {
+          case MK_PX: launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, dg.count, s); break;
+          case MK_YINV: launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s); break;
+          case MK_YFWD: launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s); break;
+          case MK_CHK: launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s); break;
+          case MK_COL1: launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, s); break;
+          default: launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, s); break;
+        }
+      }
+    });
+    const float t_multi = time_launches(p, [&] { multi_launch<float>(p, k, args, s, true); });
+    p->multi_use[k] = t_multi < t_sep;
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_store(key, p->multi_use[k] ? 1 : 0);
+  }
+}
+
 void tune(ffcz_plan_s* p) {
   const char* env = getenv("FFCZ_TUNE");
   g_no_tune = env && env[0] == '0';
@@ -2265,6 +2520,7 @@ void tune(ffcz_plan_s* p) {
       launch_chk<float>(dg.Nz, w, b, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
     });
   }
+  tune_multi(p);
   CK(cudaMemsetAsync(p->d_st, 0, sizeof(ItemState) * p->batch, s));
   CK(cudaMemcpyAsync(p->h_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -2643,6 +2899,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       build_bt<float>(p.get());
       CK(cudaStreamSynchronize(p->stream));
     }
+    build_multi(p.get());
     tune(p.get());   // tile widths only regroup pencils: Bt and the tables are unchanged
     *out = p.release();
     return FFCZ_OK;
@@ -2751,6 +3008,12 @@ int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len) {
       out += " chk=" + var(dg.wc);
     }
     out += "\n";
+  }
+  {
+    std::string mk;
+    for (int k = 0; k < MK_N; ++k)
+      if (plan->mp[k].n) mk += std::string(" ") + multi_name(k) + "=" + (plan->multi_use[k] ? "multi" : "separate");
+    if (!mk.empty()) out += "passes over all groups:" + mk + "\n";
   }
   if (buf && len > 0) {
     const size_t n = std::min(out.size(), (size_t)len - 1);

@@ -485,7 +485,7 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
   v2<T_>* s_tw = s_tiles + G_::G * TL::ELEMS;                                     \
   v2<T_>* s_twr = s_tw + M_;                                                      \
   unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M_); \
-  const int gi = blockIdx.y;                                                      \
+  const int gi = by_;                                                             \
   const int item = a.g.item[gi];                                                  \
   const ItemParams& p = a.prm[item];                                              \
   ItemState& st = a.st[item];                                                     \
@@ -493,7 +493,7 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
   const int t_it = st.t;                                                          \
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
   const int w = tid % G_::W, j = tid / G_::W;                                     \
-  const int tile = a.tile0 + blockIdx.x * G_::G + g;                              \
+  const int tile = a.tile0 + bx_ * G_::G + g;                                     \
   const int64_t prow = (int64_t)tile * G_::W + w;                                 \
   const bool live = prow < a.g.rows;                                              \
   const int64_t row = live ? prow : 0;                                            \
@@ -505,8 +505,7 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
 // PW: pointwise E_n (the measured maximum is max |e_n| / E_n).
 // X2 (certification): the output is 2 X (see r2c_post).
 template <typename T, int M, int W = TileW<T>::value, bool PW = false, bool X2 = false>
-__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
-k_xfwd(Args a) {
+__device__ __forceinline__ void k_xfwd_body(const Args& a, const int bx_, const int by_) {
   FFCZ_X_PROLOGUE(T, M, W)
   const float* src = (a.mode & M_MASK) ? a.ein : a.e;
   const float2* erow = reinterpret_cast<const float2*>(src + a.g.eoff[gi]) + row * M;
@@ -569,6 +568,11 @@ k_xfwd(Args a) {
       if ((a.mode & M_PRECLIP) && r.cnt) atomicAdd(&st.act_s, r.cnt);
     }
   }
+}
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, bool X2 = false>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
+k_xfwd(Args a) {
+  k_xfwd_body<T, M, W, PW, X2>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // s-clip of the thread's values with every option (mask recording,
@@ -699,9 +703,7 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
 }
 
 template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
-__global__ void __launch_bounds__(Geo<T, M, W>::NTHR,
-                                  (PW || PV != PV_POCS) ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
-k_px(Args a) {
+__device__ __forceinline__ void k_px_body(const Args& a, const int bx_, const int by_) {
   FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[V];
@@ -735,6 +737,12 @@ k_px(Args a) {
     block_reduce(r, s_red);
     if (threadIdx.x == 0 && r.cnt) atomicAdd(&st.act_s, r.cnt);
   }
+}
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR,
+                                  (PW || PV != PV_POCS) ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
+k_px(Args a) {
+  k_px_body<T, M, W, PW, PV, FULL>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Exit epilogue of one row (after the C2R): scale 1/N, (Dykstra) + q_{t-1},
@@ -780,8 +788,7 @@ __device__ __forceinline__ void xexit_store(const Args& a, const ItemParams& p, 
 // e_t from the input of the last loop body).  In mask mode (adjoint exit)
 // no clip is applied.
 template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS>
-__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
-k_xexit(Args a) {
+__device__ __forceinline__ void k_xexit_body(const Args& a, const int bx_, const int by_) {
   FFCZ_X_PROLOGUE(T, M, W)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[V];
@@ -814,6 +821,11 @@ k_xexit(Args a) {
     xexit_store<T, V, PW, PV>(a, p, v, j, G_::NT, erow, ebrow, qrow, PW ? ebr : nullptr,
                               PV == PV_DYKSTRA ? qr : nullptr);
 }
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS>
+__global__ void __launch_bounds__(Geo<T, M, W>::NTHR, Geo<T, M, W>::MINB)
+k_xexit(Args a) {
+  k_xexit_body<T, M, W, PW, PV>(a, (int)blockIdx.x, (int)blockIdx.y);
+}
 // ---------------------------------------------------------------------------
 // Strided axis passes
 // ---------------------------------------------------------------------------
@@ -827,7 +839,7 @@ k_xexit(Args a) {
   v2<T_>* s_tw = s_tiles + G_::G * TL::ELEMS;                                     \
   unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_tw + L_);  \
   (void)s_red;                                                                    \
-  const int gi = blockIdx.y;                                                      \
+  const int gi = by_;                                                             \
   const int item = a.g.item[gi];                                                  \
   const ItemParams& p = a.prm[item];                                              \
   ItemState& st = a.st[item];                                                     \
@@ -835,15 +847,14 @@ k_xexit(Args a) {
   const int t_it = st.t;                                                          \
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
   const int w = tid % G_::W, j = tid / G_::W;                                     \
-  const int tile = a.tile0 + blockIdx.x * G_::G + g;                              \
+  const int tile = a.tile0 + bx_ * G_::G + g;                                     \
   const int64_t mthr = (int64_t)tile * G_::TPT + tid;                             \
   TL tl{s_tiles + g * TL::ELEMS + w, false};                                      \
   (void)mthr;
 
 // Plain C2C along the middle axis of a 3D item (y): pencils at fixed (z, kx).
 template <typename T, int L, int DIR, int W = TileW<T>::value>
-__global__ void __launch_bounds__(Geo<T, L, W>::NTHR, Geo<T, L, W>::MINB)
-k_axis(Args a) {
+__device__ __forceinline__ void k_axis_body(const Args& a, const int bx_, const int by_) {
   FFCZ_AXIS_PROLOGUE(T, L, W)
   const int M = a.g.M;
   const unsigned tpr = (unsigned)(M / G_::W);     // tiles per z-plane
@@ -865,6 +876,11 @@ k_axis(Args a) {
 #pragma unroll
     for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
   }
+}
+template <typename T, int L, int DIR, int W = TileW<T>::value>
+__global__ void __launch_bounds__(Geo<T, L, W>::NTHR, Geo<T, L, W>::MINB)
+k_axis(Args a) {
+  k_axis_body<T, L, DIR, W>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Check / f-clip pass along the outermost axis (z in 3D, y in 2D): forward
@@ -1201,9 +1217,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 // the inverse FFT of this axis is applied before the store.  Tiles: see
 // ChkTile.
 template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
-__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR,
-                                  (PW || PV != PV_POCS) ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
-k_chk(Args a) {
+__device__ __forceinline__ void k_chk_body(const Args& a, const int bx_, const int by_) {
   FFCZ_AXIS_PROLOGUE(T, L, W_)
   constexpr int W = G_::W, NT = G_::NT;
   const int M = a.g.M, Nmid = a.g.Nmid;
@@ -1217,7 +1231,7 @@ k_chk(Args a) {
   load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
   const int nmain = Nmid * (M / W);
   const int ntot = chk_ntiles(W, M, Nmid);
-  const int first_tile = blockIdx.x * G_::G;
+  const int first_tile = bx_ * G_::G;
   const bool cta_has_mirror = first_tile + G_::G - 1 >= nmain && first_tile < ntot;
   const float2* pwb = nullptr;
   int64_t pws = 0;
@@ -1228,6 +1242,12 @@ k_chk(Args a) {
   v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + c.off + j * estride;
 #pragma unroll
   for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
+}
+template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
+__global__ void __launch_bounds__(Geo<T, L, W_>::NTHR,
+                                  (PW || PV != PV_POCS) ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
+k_chk(Args a) {
+  k_chk_body<T, L, W_, PW, PV, FULL>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
