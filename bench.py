@@ -379,6 +379,7 @@ def _batch_form(ffcz, torch, items, name, rank=0, world=1, dist=None):
     Es = [x["E"] for x in items]
     Ds = [x["D"] for x in items]
     plan = ffcz.Plan(shapes)
+    desc = plan.describe().strip()
 
     def call():
         d.copy_(d0)
@@ -401,7 +402,7 @@ def _batch_form(ffcz, torch, items, name, rank=0, world=1, dist=None):
             "iters_min": int(min(iters)), "iters_max": int(max(iters)),
             "iters_mean": round(float(np.mean(iters)), 3),
             "certified": int(sum(x["certified"] for x in st)),
-            "ms_cert": round(float(st[0]["ms_cert"]), 3)}
+            "ms_cert": round(float(st[0]["ms_cert"]), 3), "variants": desc}
 
 
 def aggregate_ranks(torch, dist, local_ms, bytes_per_rank, world, device="cpu"):
