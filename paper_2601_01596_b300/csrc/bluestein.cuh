@@ -67,7 +67,7 @@ __global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab) {
 // The chirp of each value is read from the item's table where it is used.
 template <typename T, int L, int W_ = TileW<T>::value>
 __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_AXIS_PROLOGUE(T, L, W_)
+  FFCZ_AXIS_PROLOGUE(T, L, W_, 0)
   constexpr int NT = G_::NT, W = G_::W;
   const int P2 = a.g.M;
   const int64_t N = p.n;
@@ -218,7 +218,7 @@ k1_col(Args a) {
 // Row pass along n2 / k2 (length P2 = L), tile = W consecutive rows.
 template <typename T, int L, int W_ = TileW<T>::value>
 __device__ __forceinline__ void k1_row_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_AXIS_PROLOGUE(T, L, W_)
+  FFCZ_AXIS_PROLOGUE(T, L, W_, 0)
   constexpr int NT = G_::NT;
   const int P1 = a.g.Nz;
   const int prow = tile * G_::W + w;

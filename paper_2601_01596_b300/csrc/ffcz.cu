@@ -86,8 +86,8 @@ std::vector<v2<T>> r2c_table(int Nx) {
 // Stage-2 twiddles of the two-stage split of L (layout in fft_core.cuh):
 // exp(-2 pi i k1 t / L), k1 < R1, t = 1..R2-1, at tw_index(R1, k1, t).
 template <typename T>
-std::vector<v2<T>> stage_table_rt(int L) {
-  const int R1 = f2_nt(L), R2 = L / R1;
+std::vector<v2<T>> stage_table_rt(int L, int S = 0) {
+  const int R1 = split_r1(L, S), R2 = L / R1;
   std::vector<v2<T>> t(L);
   for (auto& x : t) { x.x = 0; x.y = 0; }
   for (int k1 = 0; k1 < R1; ++k1)
@@ -136,12 +136,26 @@ struct Tables {
   void* f64[12] = {};
   void* r32[12] = {};
   void* r64[12] = {};
+  // stage factors of the swapped radix split (odd p; fft_core.cuh Split)
+  void* f32s[12] = {};
+  void* f64s[12] = {};
 };
 
 template <typename T>
 const void* tw_of(const Tables& tb, int L) {
   const int p = ilog2(L);
   return sizeof(T) == 4 ? tb.f32[p] : tb.f64[p];
+}
+template <typename T>
+const void* tw1_of(const Tables& tb, int L) {
+  const int p = ilog2(L);
+  return sizeof(T) == 4 ? tb.f32s[p] : tb.f64s[p];
+}
+// The stage tables of a pass of length L in both radix splits.
+template <typename T>
+void set_tw(Args& a, const Tables& tb, int L) {
+  a.tw = tw_of<T>(tb, L);
+  a.tw1 = tw1_of<T>(tb, L);
 }
 template <typename T>
 const void* twr_of(const Tables& tb, int Nx) {
@@ -369,11 +383,17 @@ constexpr int row_w2(int L) { return 2 * row_w1(L); }
 // g_pw_sel to reach them without bound pointers).
 thread_local bool g_pw_sel = false;
 
+// Width codes of the tuner: a plain kernel's tile width W, -W for the
+// persistent copy-engine-fed kernel, and W | kSplit for the plain kernel in
+// the swapped radix split (fft_core.cuh Split<L, 1>; odd log2 L only).
+constexpr int kSplit = 256;
+template <int L> constexpr bool split1_ok() { return ilog2(L) % 2 == 1; }
+
 // The x pass needs its full form for edit recording and the adjoint's mask,
 // record and checkpoint modes; every other launch takes the lean one.
 inline bool px_full(const Args& a) { return (a.mode & (M_RECORD | M_MASK | M_CKPT)) != 0 || a.ed_s != nullptr; }
 
-template <typename T, int M, int W, bool PW = false, int PV = PV_POCS>
+template <typename T, int M, int W, bool PW = false, int PV = PV_POCS, int S = 0>
 void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_t s) {
   using G_ = Geo<T, M, W>;
   const int64_t tiles = (rows + G_::W - 1) / G_::W;
@@ -384,6 +404,7 @@ void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_
     if constexpr (sizeof(T) == 8) set_smem(k_xfwd<T, M, W, PW, true>, sm);
     if constexpr (PV == PV_POCS) set_smem(k_px<T, M, W, PW, PV, true>, sm);
     set_smem(k_px<T, M, W, PW, PV, false>, sm);
+    if constexpr (S == 1) { set_smem(k_px<T, M, W, PW, PV, true, 1>, sm); set_smem(k_px<T, M, W, PW, PV, false, 1>, sm); }
     set_smem(k_xexit<T, M, W, PW, PV>, sm);
     return;
   }
@@ -396,9 +417,9 @@ void launch_x_tw(XKind kind, const Args& a, int64_t rows, int count, cudaStream_
     case XPX:
       // projection variants run lean only (no edits, no adjoint)
       if constexpr (PV == PV_POCS) {
-        if (px_full(a)) { k_px<T, M, W, PW, PV, true><<<grid, G_::NTHR, sm, s>>>(a); break; }
+        if (px_full(a)) { k_px<T, M, W, PW, PV, true, S><<<grid, G_::NTHR, sm, s>>>(a); break; }
       }
-      k_px<T, M, W, PW, PV, false><<<grid, G_::NTHR, sm, s>>>(a);
+      k_px<T, M, W, PW, PV, false, S><<<grid, G_::NTHR, sm, s>>>(a);
       break;
     case XEXIT: k_xexit<T, M, W, PW, PV><<<grid, G_::NTHR, sm, s>>>(a); break;
   }
@@ -530,7 +551,14 @@ struct XL {
       }
       // the entry and exit passes follow the loop's x-pass choice
       if (w < 0 && launch_xio_tma_kind<M, false>(kind, a, rows, count, s)) return;
-      if (w == row_w2(M)) launch_x_tw<T, M, row_w2(M)>(kind, a, rows, count, s);
+      if constexpr (split1_ok<M>()) {
+        if ((w & kSplit) && (kind == XPX || g_dry)) {
+          if ((w & ~kSplit) == row_w2(M)) launch_x_tw<T, M, row_w2(M), false, PV_POCS, 1>(kind, a, rows, count, s);
+          else launch_x_tw<T, M, row_w1(M), false, PV_POCS, 1>(kind, a, rows, count, s);
+          if (!g_dry) return;
+        }
+      }
+      if ((w & ~kSplit) == row_w2(M)) launch_x_tw<T, M, row_w2(M)>(kind, a, rows, count, s);
       else launch_x_tw<T, M, row_w1(M)>(kind, a, rows, count, s);
     } else {
       launch_x_tw<T, M, row_w1(M)>(kind, a, rows, count, s);
@@ -542,15 +570,15 @@ void launch_x(XKind kind, int M, int w, const Args& a, int64_t rows, int count, 
   FFCZ_DISPATCH_L(M, XL<T>::template go, kind, w, a, rows, count, s)
 }
 
-template <typename T, int L, int DIR, int W>
+template <typename T, int L, int DIR, int W, int S = 0>
 void launch_axis_tw(const Args& a, int Nz, int M, int count, cudaStream_t s) {
   using G_ = Geo<T, L, W>;
   const int64_t tiles = (int64_t)Nz * (M / G_::W);
   dim3 grid((unsigned)((tiles + G_::G - 1) / G_::G), (unsigned)count);
   const size_t sm = Smem<T, L, W>::bytes_axis;
-  if (g_dry) { set_smem(k_axis<T, L, DIR, W>, sm); return; }
+  if (g_dry) { set_smem(k_axis<T, L, DIR, W, S>, sm); return; }
   ProfScope ps(DIR < 0 ? "axis_fwd" : "axis_inv", 8 * (int)sizeof(T), L, s);
-  k_axis<T, L, DIR, W><<<grid, G_::NTHR, sm, s>>>(a);
+  k_axis<T, L, DIR, W, S><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
 }
 // Persistent TMA-fed variants (float32, 8-pencil tiles, L >= 256): CTAs
@@ -617,7 +645,14 @@ struct AL {
       if constexpr (tma_ok<L>()) {
         if (w < 0 && (a.tm_axis || g_dry)) { launch_axis_tma<L, DIR>(a, Nz, M, count, s); return; }
       }
-      if (w == 4) launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
+      if constexpr (split1_ok<L>()) {
+        if ((w & kSplit) || g_dry) {
+          if ((w & ~kSplit) == 4) launch_axis_tw<T, L, DIR, 4, 1>(a, Nz, M, count, s);
+          else launch_axis_tw<T, L, DIR, 8, 1>(a, Nz, M, count, s);
+          if (!g_dry) return;
+        }
+      }
+      if ((w & ~kSplit) == 4) launch_axis_tw<T, L, DIR, 4>(a, Nz, M, count, s);
       else launch_axis_tw<T, L, DIR, 8>(a, Nz, M, count, s);
     } else {
       launch_axis_tw<T, L, DIR, kAxisW64>(a, Nz, M, count, s);
@@ -630,7 +665,7 @@ void launch_axis(int L, int w, const Args& a, int Nz, int M, int count, cudaStre
   FFCZ_DISPATCH_L(L, D::template go, w, a, Nz, M, count, s)
 }
 
-template <typename T, int L, int W, bool PW = false, int PV = PV_POCS>
+template <typename T, int L, int W, bool PW = false, int PV = PV_POCS, int S = 0>
 void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   using G_ = Geo<T, L, W>;
   const int64_t tiles = chk_ntiles(W, M, Nmid);
@@ -640,21 +675,21 @@ void launch_chk_tw(const Args& a, int Nmid, int M, int count, cudaStream_t s) {
   // (no edits, no adjoint)
   constexpr bool lean_ok = true, only_lean = PV != PV_POCS;
   if (g_dry) {
-    if constexpr (!only_lean) set_smem(k_chk<T, L, W, PW, PV, true>, sm);
-    if constexpr (lean_ok) set_smem(k_chk<T, L, W, PW, PV, false>, sm);
+    if constexpr (!only_lean) set_smem(k_chk<T, L, W, PW, PV, true, S>, sm);
+    if constexpr (lean_ok) set_smem(k_chk<T, L, W, PW, PV, false, S>, sm);
     return;
   }
   ProfScope ps((a.mode & M_NOWRITE) ? "chk_cert" : (a.mode & M_MASK) ? "chk_adj" : "chk",
                8 * (int)sizeof(T), L, s);
   if constexpr (lean_ok) {
     if (only_lean || !chk_full(a)) {
-      k_chk<T, L, W, PW, PV, false><<<grid, G_::NTHR, sm, s>>>(a);
+      k_chk<T, L, W, PW, PV, false, S><<<grid, G_::NTHR, sm, s>>>(a);
       g_launches++;
       return;
     }
   }
   if constexpr (!only_lean) {
-    k_chk<T, L, W, PW, PV, true><<<grid, G_::NTHR, sm, s>>>(a);
+    k_chk<T, L, W, PW, PV, true, S><<<grid, G_::NTHR, sm, s>>>(a);
     g_launches++;
   }
 }
@@ -685,7 +720,14 @@ struct CL {
       if constexpr (tma_ok<L>()) {
         if (w < 0 && (a.tm_chk || g_dry)) { launch_chk_tma<L>(a, Nmid, M, count, s); return; }
       }
-      if (w == 4) launch_chk_tw<T, L, 4>(a, Nmid, M, count, s);
+      if constexpr (split1_ok<L>()) {
+        if ((w & kSplit) || g_dry) {
+          if ((w & ~kSplit) == 4) launch_chk_tw<T, L, 4, false, PV_POCS, 1>(a, Nmid, M, count, s);
+          else launch_chk_tw<T, L, 8, false, PV_POCS, 1>(a, Nmid, M, count, s);
+          if (!g_dry) return;
+        }
+      }
+      if ((w & ~kSplit) == 4) launch_chk_tw<T, L, 4>(a, Nmid, M, count, s);
       else launch_chk_tw<T, L, 8>(a, Nmid, M, count, s);
     } else {
       launch_chk_tw<T, L, 4>(a, Nmid, M, count, s);
@@ -895,20 +937,20 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
 
 template <typename T>
 void tabs_x(ffcz_plan_s* p, Args& a, const DevGroup& dg) {
-  a.tw = tw_of<T>(p->tb, dg.M);
+  set_tw<T>(a, p->tb, dg.M);
   a.twr = twr_of<T>(p->tb, dg.Nx);
 }
 
 template <typename T>
 void col1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
-  a.tw = tw_of<T>(p->tb, dg.P1);
+  set_tw<T>(a, p->tb, dg.P1);
   a.twr = sizeof(T) == 4 ? dg.twp32 : dg.twp64;
   a.chirp = sizeof(T) == 4 ? p->ch32 : p->ch64;
   a.op1 = op;
 }
 template <typename T>
 void row1_args(ffcz_plan_s* p, Args& a, const DevGroup& dg, int op) {
-  a.tw = tw_of<T>(p->tb, dg.P2);
+  set_tw<T>(a, p->tb, dg.P2);
   a.bt = sizeof(T) == 4 ? p->Bt32 : p->Bt64;
   a.op1 = op;
 }
@@ -1188,10 +1230,10 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
   for (auto& dg : p->groups) {
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     if (dg.ndim == 3) {
-      a.tw = tw_of<T>(p->tb, dg.Ny);
+      set_tw<T>(a, p->tb, dg.Ny);
       launch_axis<T, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
     }
-    a.tw = tw_of<T>(p->tb, dg.Nz);
+    set_tw<T>(a, p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
     launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
@@ -1213,7 +1255,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     for (int g = 0; g < ng; ++g) {
       const DevGroup& dg = p->groups[g];
       Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
-      a.tw = tw_of<T>(p->tb, dg.Ny);
+      set_tw<T>(a, p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
       args[g] = a;
     }
@@ -1247,7 +1289,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
       const DevGroup& dg = p->groups[g];
       Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
       a.sel_in = a.sel_out = S_CUR;
-      a.tw = tw_of<T>(p->tb, dg.Ny);
+      set_tw<T>(a, p->tb, dg.Ny);
       a.mode = 0;
       args[g] = a;
     }
@@ -1261,7 +1303,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     const DevGroup& dg = p->groups[g];
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     a.sel_in = a.sel_out = S_CUR;
-    a.tw = tw_of<T>(p->tb, dg.Nz);
+    set_tw<T>(a, p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
     args[g] = a;
   }
@@ -1283,7 +1325,7 @@ void exit_pass(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
     a.pred = P_EXIT;
     a.e = e;
     if (dg.ndim == 3) {
-      a.tw = tw_of<T>(p->tb, dg.Ny);
+      set_tw<T>(a, p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
       launch_axis<T, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
       a.sel_in = S_CUR;
@@ -1560,13 +1602,13 @@ void ps_bounds(ffcz_plan_s* p, const float* x, const double* rho, float2* out) {
     a.mode = 0;
     launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, s);
     if (dg.ndim == 3) {
-      a.tw = tw_of<float>(p->tb, dg.Ny);
+      set_tw<float>(a, p->tb, dg.Ny);
       launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
     }
     Args az = a;
     az.g.Nz = 1;
     az.g.M = Nmid * dg.M;
-    az.tw = tw_of<float>(p->tb, dg.Nz);
+    set_tw<float>(az, p->tb, dg.Nz);
     launch_axis<float, -1>(dg.Nz, dg.wa, az, 1, Nmid * dg.M, dg.count, s);
     const int64_t nb = (int64_t)dg.Nz * Nmid * (dg.M + 1);
     const unsigned gx = (unsigned)std::min<int64_t>((nb + 255) / 256, 1024);
@@ -1647,10 +1689,10 @@ void apply_edits(ffcz_plan_s* p, float* xhat, int m, const uint8_t* sf, const in
     Args az = a;
     az.g.Nz = 1;
     az.g.M = Nmid * dg.M;
-    az.tw = tw_of<float>(p->tb, dg.Nz);
+    set_tw<float>(az, p->tb, dg.Nz);
     launch_axis<float, +1>(dg.Nz, dg.wa, az, 1, Nmid * dg.M, dg.count, s);
     if (dg.ndim == 3) {
-      a.tw = tw_of<float>(p->tb, dg.Ny);
+      set_tw<float>(a, p->tb, dg.Ny);
       launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, s);
     }
     tabs_x<float>(p, a, dg);
@@ -1737,11 +1779,11 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = 
     a.mode = M_MEASURE;
     if (!x_done) launch_x<double>(XCERT, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
     if (dg.ndim == 3 && !y_done) {
-      a.tw = tw_of<double>(p->tb, dg.Ny);
+      set_tw<double>(a, p->tb, dg.Ny);
       a.mode = 0;
       launch_axis<double, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
     }
-    a.tw = tw_of<double>(p->tb, dg.Nz);
+    set_tw<double>(a, p->tb, dg.Nz);
     a.mode = M_NOWRITE;
     launch_chk<double>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
   }
@@ -1969,7 +2011,7 @@ bool spec_upload(ffcz_plan_s* p, float* e_dev, const float* host) {
     launch_x<double>(XCERT, dg.M, dg.wx, a, nr, 1, p->spec_stream);
     if (dg.ndim == 3) {   // planes z0 .. z1 - 1
       const int z0 = (int)(r0 / dg.Ny), z1 = (int)((r0 + nr) / dg.Ny);
-      a.tw = tw_of<double>(p->tb, dg.Ny);
+      set_tw<double>(a, p->tb, dg.Ny);
       a.mode = 0;
       a.tile0 = z0 * tpr_y;
       a.tile1 = z1 * tpr_y;
@@ -2101,7 +2143,7 @@ void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask
   Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
   a.pred = P_ALL;
   if (dg.ndim == 3) {
-    a.tw = tw_of<float>(p->tb, dg.Ny);
+    set_tw<float>(a, p->tb, dg.Ny);
     a.sel_in = S_PREV; a.sel_out = S_CUR;
     launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
     a.sel_in = S_CUR;
@@ -2119,11 +2161,11 @@ void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask
   a.mask = nullptr;
   a.ckpt = nullptr;
   if (dg.ndim == 3) {
-    a.tw = tw_of<float>(p->tb, dg.Ny);
+    set_tw<float>(a, p->tb, dg.Ny);
     a.mode = 0;
     launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
   }
-  a.tw = tw_of<float>(p->tb, dg.Nz);
+  set_tw<float>(a, p->tb, dg.Nz);
   a.mode = M_CLIP | (fmask ? M_RECORD : 0);
   a.mask = fmask;
   launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
@@ -2137,10 +2179,10 @@ void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uin
   a.mode = 0;
   launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, p->stream);
   if (dg.ndim == 3) {
-    a.tw = tw_of<float>(p->tb, dg.Ny);
+    set_tw<float>(a, p->tb, dg.Ny);
     launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
   }
-  a.tw = tw_of<float>(p->tb, dg.Nz);
+  set_tw<float>(a, p->tb, dg.Nz);
   a.mode = M_CLIP | (fmask ? M_RECORD : 0);
   a.mask = fmask;
   launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
@@ -2248,7 +2290,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
       } else {
         advance(p, p->d_st2);
         if (dg.ndim == 3) {
-          a.tw = tw_of<float>(p->tb, dg.Ny);
+          set_tw<float>(a, p->tb, dg.Ny);
           a.sel_in = S_PREV; a.sel_out = S_CUR;
           launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
           a.sel_in = S_CUR;
@@ -2262,12 +2304,12 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
       }
       a.sel_in = a.sel_out = S_CUR;
       if (dg.ndim == 3) {
-        a.tw = tw_of<float>(p->tb, dg.Ny);
+        set_tw<float>(a, p->tb, dg.Ny);
         a.mode = 0;
         a.mask = nullptr;
         launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
       }
-      a.tw = tw_of<float>(p->tb, dg.Nz);
+      set_tw<float>(a, p->tb, dg.Nz);
       a.mode = M_MASK;
       a.mask = fm;
       launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
@@ -2280,7 +2322,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     a.pred = P_ALL;
     a.e = gin;
     if (dg.ndim == 3) {
-      a.tw = tw_of<float>(p->tb, dg.Ny);
+      set_tw<float>(a, p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
       launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
       a.sel_in = S_CUR;
@@ -2447,8 +2489,8 @@ void tune_multi(ffcz_plan_s* p) {
       Args a = make_args<float>(p, dg, p->B32[0], p->B32[1], p->d_st);
       a.pred = P_ALL;
       if (k == MK_PX) { tabs_x<float>(p, a, dg); a.mode = M_CLIP; }
-      else if (k == MK_YINV || k == MK_YFWD) a.tw = tw_of<float>(p->tb, dg.Ny);
-      else if (k == MK_CHK) { a.tw = tw_of<float>(p->tb, dg.Nz); a.mode = M_CLIP; }
+      else if (k == MK_YINV || k == MK_YFWD) set_tw<float>(a, p->tb, dg.Ny);
+      else if (k == MK_CHK) { set_tw<float>(a, p->tb, dg.Nz); a.mode = M_CLIP; }
       else if (k == MK_COL1) { col1_args<float>(p, a, dg, OP1_SCLIP); a.mode = M_CLIP; }
       else row1_args<float>(p, a, dg, OP1_CONV);
       args[g] = a;
@@ -2499,7 +2541,18 @@ void tune(ffcz_plan_s* p) {
       });
       continue;
     }
-    dg.wx = pick_width(p, std::string("px_") + base, dg.wx, {row_w1(dg.M), row_w2(dg.M), -row_w1(dg.M)}, [&](int w) {
+    // candidates: tile widths, the persistent copy-engine-fed kernel, and
+    // (odd log2 of the length) the swapped radix split of the plain kernel
+    auto with_split = [](std::vector<int> c, int L) {
+      if (split_ok(L, 1)) {
+        const size_t n = c.size();
+        for (size_t i = 0; i < n; ++i)
+          if (c[i] > 0) c.push_back(c[i] | kSplit);
+      }
+      return c;
+    };
+    dg.wx = pick_width(p, std::string("px_") + base, dg.wx,
+                       with_split({row_w1(dg.M), row_w2(dg.M), -row_w1(dg.M)}, dg.M), [&](int w) {
       Args b = a;
       tabs_x<float>(p, b, dg);
       b.mode = 0;
@@ -2507,15 +2560,17 @@ void tune(ffcz_plan_s* p) {
     });
     if (dg.ndim == 3)
       dg.wa = pick_width(p, std::string("axis_") + base, dg.wa,
-                         dg.tm_axis ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, [&](int w) {
+                         with_split(dg.tm_axis ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, dg.Ny),
+                         [&](int w) {
         Args b = a;
-        b.tw = tw_of<float>(p->tb, dg.Ny);
+        set_tw<float>(b, p->tb, dg.Ny);
         launch_axis<float, -1>(dg.Ny, w, b, dg.Nz, dg.M, dg.count, s);
       });
     dg.wc = pick_width(p, std::string("chk_") + base, dg.wc,
-                       dg.tm_chk ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, [&](int w) {
+                       with_split(dg.tm_chk ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, dg.Nz),
+                       [&](int w) {
       Args b = a;
-      b.tw = tw_of<float>(p->tb, dg.Nz);
+      set_tw<float>(b, p->tb, dg.Nz);
       b.mode = 0;
       launch_chk<float>(dg.Nz, w, b, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
     });
@@ -2672,6 +2727,14 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       p->tb.f64[pw] = dalloc(p.get(), sizeof(double2) * t64.size());
       CK(cudaMemcpy(p->tb.f32[pw], t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(p->tb.f64[pw], t64.data(), sizeof(double2) * t64.size(), cudaMemcpyHostToDevice));
+      if (split_ok(L, 1)) {
+        auto s32 = stage_table_rt<float>(L, 1);
+        auto s64 = stage_table_rt<double>(L, 1);
+        p->tb.f32s[pw] = dalloc(p.get(), sizeof(float2) * s32.size());
+        p->tb.f64s[pw] = dalloc(p.get(), sizeof(double2) * s64.size());
+        CK(cudaMemcpy(p->tb.f32s[pw], s32.data(), sizeof(float2) * s32.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->tb.f64s[pw], s64.data(), sizeof(double2) * s64.size(), cudaMemcpyHostToDevice));
+      }
     }
     for (int pw = 4; pw <= 11; ++pw) {
       const int Nx = 1 << pw;
@@ -2990,7 +3053,15 @@ ffcz_status ffcz_power_spectrum_bounds(ffcz_plan_t plan, const float* x_dev, con
 int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len) {
   if (!plan) return -1;
   std::string out;
-  auto var = [](int w) { return w < 0 ? "tma(" + std::to_string(-w) + ")" : std::to_string(w); };
+  // a pass variant: tile width (tma(W): the persistent copy-engine-fed
+  // kernel) and the radix split of its length, stage-1 x stage-2 sizes
+  auto var = [](int w, int L) {
+    const int S = (w > 0 && (w & kSplit)) ? 1 : 0;
+    const int R1 = split_r1(L, S);
+    const std::string split = " " + std::to_string(R1) + "x" + std::to_string(L / R1);
+    if (w < 0) return "tma(" + std::to_string(-w) + ")" + split;
+    return std::to_string(w & ~kSplit) + split;
+  };
   for (const auto& dg : plan->groups) {
     char head[160];
     if (dg.ndim == 1)
@@ -3001,11 +3072,11 @@ int ffcz_plan_describe(ffcz_plan_t plan, char* buf, int len) {
       snprintf(head, sizeof head, "3d %dx%dx%d count=%d:", dg.Nz, dg.Ny, dg.Nx, dg.count);
     out += head;
     if (dg.ndim == 1) {
-      out += " col1=" + var(dg.w1c) + " row1=" + var(dg.w1r);
+      out += " col1=" + var(dg.w1c, dg.P1) + " row1=" + var(dg.w1r, dg.P2);
     } else {
-      out += " px=" + var(dg.wx);
-      if (dg.ndim == 3) out += " axis=" + var(dg.wa);
-      out += " chk=" + var(dg.wc);
+      out += " px=" + var(dg.wx, dg.M);
+      if (dg.ndim == 3) out += " axis=" + var(dg.wa, dg.Ny);
+      out += " chk=" + var(dg.wc, dg.Nz);
     }
     out += "\n";
   }

@@ -413,10 +413,33 @@ inline double2 f64_stage_entry(long double c, long double s, bool tangent) {
 // float64 complex values).
 template <typename T> struct TileW { static constexpr int value = 16 / (int)sizeof(T) * 2; };
 
-// A thread's view of its pencil's column in the tile buffer.
-template <typename T, int L, int W_>
+// The radix split of the two-stage schedule.  S = 0: stage 1 of size
+// R1 = NT (V / NT DFTs per thread), stage 2 of size R2 = V (one per thread).
+// S = 1, for odd log2 L (V = 2 NT): the sizes swapped -- stage 1 one DFT of
+// size V on the thread's own values, stage 2 two DFTs of size NT -- with the
+// same threads, registers and buffer (its exchange needs L + NT rows, less
+// than the L + V of the natural-order exchanges).  Stage 1 runs R2 DFTs over
+// x[n2 + R2 n1]; its output k1 of DFT n2 is twiddled by w^(n2 k1) and
+// stage 2 runs the R1 DFTs over n2; output k1 + R1 k2 is X in natural order.
+template <int L, int S>
+struct Split {
+  static_assert(S == 0 || (F2<L>::lg % 2 == 1), "the swapped split exists for odd log2 L");
+  static constexpr int NT = F2<L>::NT, V = F2<L>::V;
+  static constexpr int R1 = S ? V : NT;     // stage-1 DFT size
+  static constexpr int R2 = S ? NT : V;     // stage-2 DFT size
+  static constexpr int NB1 = R2 / NT;       // stage-1 DFTs per thread
+  static constexpr int NB2 = R1 / NT;       // stage-2 DFTs per thread
+};
+// Host-side stage sizes of split S of L.
+inline int split_r1(int L, int S) { return S ? L / f2_nt(L) : f2_nt(L); }
+inline bool split_ok(int L, int S) { return S == 0 || (ilog2(L) % 2 == 1); }
+
+// A thread's view of its pencil's column in the tile buffer (S: the radix
+// split its transforms take).
+template <typename T, int L, int W_, int S_ = 0>
 struct Tile {
   static constexpr int W = W_;
+  static constexpr int S = S_;
   static constexpr int TPT = F2<L>::NT * W;       // threads of the tile
   static constexpr int ELEMS = F2<L>::ROWS * W;   // complex values of the buffer
   v2<T>* p;    // buffer + w
@@ -441,8 +464,8 @@ struct Tile {
 template <typename T, int L, int DIR, class TL>
 __device__ __forceinline__ void fft_pencil(v2<T> (&v)[F2<L>::V], int j, const v2<T>* __restrict__ tw,
                                            TL& tl) {
-  using F = F2<L>;
-  constexpr int R1 = F::R1, R2 = F::R2, NB1 = F::NB1, W = TL::W;
+  using SP = Split<L, TL::S>;
+  constexpr int R1 = SP::R1, R2 = SP::R2, NT = SP::NT, NB1 = SP::NB1, NB2 = SP::NB2, W = TL::W;
   tl.begin();
   v2<T>* buf = tl.buf();
 #pragma unroll
@@ -451,37 +474,46 @@ __device__ __forceinline__ void fft_pencil(v2<T> (&v)[F2<L>::V], int j, const v2
 #pragma unroll
     for (int t = 0; t < R1; ++t) x[t] = v[b + t * NB1];
     dftN<R1, T, DIR>(x);
-    // output t of stage-1 DFT n2 = j + b R1 is element n2 R1 + t
-    const int r0 = (j + b * R1) * (R1 + 1);
+    // output t of stage-1 DFT n2 = j + b NT is element n2 R1 + t
+    const int r0 = (j + b * NT) * (R1 + 1);
 #pragma unroll
     for (int t = 0; t < R1; ++t) buf[(r0 + t) * W] = x[t];
   }
   TL::sync();
-  // element j + t R1 (row j + t (R1 + 1)), twiddled by w_L^{j t}
 #pragma unroll
-  for (int t = 0; t < R2; ++t) v[t] = buf[(j + t * (R1 + 1)) * W];
-  tl.done();
-  if constexpr (sizeof(T) == 4) {
-    const float4* q = reinterpret_cast<const float4*>(tw) + j;
+  for (int b = 0; b < NB2; ++b) {
+    // stage-2 DFT k1 = j + b NT over n2 = t: element n2 R1 + k1 (row
+    // t (R1 + 1) + k1), twiddled by w_L^{k1 t}; its output k2 is X[k1 + R1 k2],
+    // the thread's natural-order value b + NB2 k2
+    const int k1 = j + b * NT;
+    v2<T> y[R2];
 #pragma unroll
-    for (int i = 0; i < R2 / 2; ++i) {
-      const float4 f = q[i * R1];   // factors 2i+1, 2i+2 of row j
-      v[2 * i + 1] = twmul<T, DIR>(v[2 * i + 1], mk<T>(f.x, f.y));
-      if (2 * i + 2 < R2) v[2 * i + 2] = twmul<T, DIR>(v[2 * i + 2], mk<T>(f.z, f.w));
+    for (int t = 0; t < R2; ++t) y[t] = buf[(t * (R1 + 1) + k1) * W];
+    if constexpr (sizeof(T) == 4) {
+      const float4* q = reinterpret_cast<const float4*>(tw) + k1;
+#pragma unroll
+      for (int i = 0; i < R2 / 2; ++i) {
+        const float4 f = q[i * R1];   // factors 2i+1, 2i+2 of row k1
+        y[2 * i + 1] = twmul<T, DIR>(y[2 * i + 1], mk<T>(f.x, f.y));
+        if (2 * i + 2 < R2) y[2 * i + 2] = twmul<T, DIR>(y[2 * i + 2], mk<T>(f.z, f.w));
+      }
+      dftN<R2, T, DIR>(y);
+    } else {
+      // the stage-2 DFT's first layer, pairs (t, t + R2/2), with the table
+      // twiddles fused in: factor t < R2/2 as a complex product, factor
+      // t + R2/2 in tangent form (c, tau) folded into the butterfly
+      constexpr int H = R2 / 2;
+#pragma unroll
+      for (int t = 0; t < H; ++t) {
+        const v2<T> p = t == 0 ? y[0] : twmul<T, DIR>(y[t], tw[tw_index(R1, k1, t)]);
+        fold_rt<DIR>(p, y[t + H], tw[tw_index(R1, k1, t + H)], y[t], y[t + H]);
+      }
+      dpost1<R2, DIR>(y);
     }
-    dftN<R2, T, DIR>(v);
-  } else {
-    // the stage-2 DFT's first layer, pairs (t, t + R2/2), with the table
-    // twiddles fused in: factor t < R2/2 as a complex product, factor
-    // t + R2/2 in tangent form (c, tau) folded into the butterfly
-    constexpr int H = R2 / 2;
 #pragma unroll
-    for (int t = 0; t < H; ++t) {
-      const v2<T> p = t == 0 ? v[0] : twmul<T, DIR>(v[t], tw[tw_index(R1, j, t)]);
-      fold_rt<DIR>(p, v[t + H], tw[tw_index(R1, j, t + H)], v[t], v[t + H]);
-    }
-    dpost1<R2, DIR>(v);
+    for (int k2 = 0; k2 < R2; ++k2) v[b + NB2 * k2] = y[k2];
   }
+  tl.done();
 }
 
 // Exchange in natural order: every thread stores its registers, the tile

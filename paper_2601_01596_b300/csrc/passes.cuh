@@ -101,6 +101,7 @@ struct Args {
   int ckpt_every;
   int pred, sel_in, sel_out, mode;
   const void* tw;          // Stockham stage factors for the pass length
+  const void* tw1;         // the same for the swapped radix split (Split<L, 1>; null if none)
   const void* twr;         // exp(-2 pi i k / Nx), k < M (x passes); exp(-2 pi i m / P) (1D)
   const void* bt;          // 1D: FFT of the wrapped chirp, [k1][k2] order, per item at soff
   const void* chirp;       // 1D: chirps b_n, n < N, per item at eoff
@@ -476,9 +477,9 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
   tl.done();
 }
 
-#define FFCZ_X_PROLOGUE(T_, M_, W_)                                               \
+#define FFCZ_X_PROLOGUE(T_, M_, W_, S_)                                           \
   using G_ = Geo<T_, M_, W_>;                                                     \
-  using TL = Tile<T_, M_, W_>;                                                    \
+  using TL = Tile<T_, M_, W_, S_>;                                                \
   constexpr int V = G_::V;                                                        \
   extern __shared__ __align__(16) unsigned char smraw[];                          \
   v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
@@ -506,7 +507,7 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
 // X2 (certification): the output is 2 X (see r2c_post).
 template <typename T, int M, int W = TileW<T>::value, bool PW = false, bool X2 = false>
 __device__ __forceinline__ void k_xfwd_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_X_PROLOGUE(T, M, W)
+  FFCZ_X_PROLOGUE(T, M, W, 0)
   const float* src = (a.mode & M_MASK) ? a.ein : a.e;
   const float2* erow = reinterpret_cast<const float2*>(src + a.g.eoff[gi]) + row * M;
   float2* erow_w = reinterpret_cast<float2*>(a.e + a.g.eoff[gi]) + row * M;
@@ -702,14 +703,14 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
   return live ? cnt : 0ull;
 }
 
-template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true, int S = 0>
 __device__ __forceinline__ void k_px_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_X_PROLOGUE(T, M, W)
+  FFCZ_X_PROLOGUE(T, M, W, S)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) v[u] = in[j + u * G_::NT];
-  load_tables<T>(s_tw, a.tw, M, s_twr, a.twr, M);
+  load_tables<T>(s_tw, S ? a.tw1 : a.tw, M, s_twr, a.twr, M);
   float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
   const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
   const float2* qin = nullptr;
@@ -738,11 +739,11 @@ __device__ __forceinline__ void k_px_body(const Args& a, const int bx_, const in
     if (threadIdx.x == 0 && r.cnt) atomicAdd(&st.act_s, r.cnt);
   }
 }
-template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
+template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true, int S = 0>
 __global__ void __launch_bounds__(Geo<T, M, W>::NTHR,
                                   (PW || PV != PV_POCS) ? Geo<T, M, W>::MINB_PW : Geo<T, M, W>::MINB)
 k_px(Args a) {
-  k_px_body<T, M, W, PW, PV, FULL>(a, (int)blockIdx.x, (int)blockIdx.y);
+  k_px_body<T, M, W, PW, PV, FULL, S>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Exit epilogue of one row (after the C2R): scale 1/N, (Dykstra) + q_{t-1},
@@ -789,7 +790,7 @@ __device__ __forceinline__ void xexit_store(const Args& a, const ItemParams& p, 
 // no clip is applied.
 template <typename T, int M, int W = TileW<T>::value, bool PW = false, int PV = PV_POCS>
 __device__ __forceinline__ void k_xexit_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_X_PROLOGUE(T, M, W)
+  FFCZ_X_PROLOGUE(T, M, W, 0)
   const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + row * M;
   v2<T> v[V];
 #pragma unroll
@@ -830,9 +831,9 @@ k_xexit(Args a) {
 // Strided axis passes
 // ---------------------------------------------------------------------------
 
-#define FFCZ_AXIS_PROLOGUE(T_, L_, W_)                                            \
+#define FFCZ_AXIS_PROLOGUE(T_, L_, W_, S_)                                        \
   using G_ = Geo<T_, L_, W_>;                                                     \
-  using TL = Tile<T_, L_, W_>;                                                    \
+  using TL = Tile<T_, L_, W_, S_>;                                                \
   constexpr int V = G_::V;                                                        \
   extern __shared__ __align__(16) unsigned char smraw[];                          \
   v2<T_>* s_tiles = reinterpret_cast<v2<T_>*>(smraw);                            \
@@ -853,9 +854,9 @@ k_xexit(Args a) {
   (void)mthr;
 
 // Plain C2C along the middle axis of a 3D item (y): pencils at fixed (z, kx).
-template <typename T, int L, int DIR, int W = TileW<T>::value>
+template <typename T, int L, int DIR, int W = TileW<T>::value, int S = 0>
 __device__ __forceinline__ void k_axis_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_AXIS_PROLOGUE(T, L, W)
+  FFCZ_AXIS_PROLOGUE(T, L, W, S)
   const int M = a.g.M;
   const unsigned tpr = (unsigned)(M / G_::W);     // tiles per z-plane
   const int ntiles = a.tile1 ? a.tile1 : a.g.Nz * (int)tpr;
@@ -869,7 +870,7 @@ __device__ __forceinline__ void k_axis_body(const Args& a, const int bx_, const 
   v2<T> v[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) v[u] = in[u * ustride];
-  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
+  load_tables<T>(s_tw, S ? a.tw1 : a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
   fft_pencil<T, L, DIR>(v, j, s_tw, tl);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + off + (int64_t)j * M;
@@ -877,10 +878,10 @@ __device__ __forceinline__ void k_axis_body(const Args& a, const int bx_, const 
     for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
   }
 }
-template <typename T, int L, int DIR, int W = TileW<T>::value>
+template <typename T, int L, int DIR, int W = TileW<T>::value, int S = 0>
 __global__ void __launch_bounds__(Geo<T, L, W>::NTHR, Geo<T, L, W>::MINB)
 k_axis(Args a) {
-  k_axis_body<T, L, DIR, W>(a, (int)blockIdx.x, (int)blockIdx.y);
+  k_axis_body<T, L, DIR, W, S>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Check / f-clip pass along the outermost axis (z in 3D, y in 2D): forward
@@ -1216,9 +1217,9 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
 // (CheckConvergence), Re and Im are clipped to +-D' (ProjectOntoFCube), and
 // the inverse FFT of this axis is applied before the store.  Tiles: see
 // ChkTile.
-template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
+template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true, int S = 0>
 __device__ __forceinline__ void k_chk_body(const Args& a, const int bx_, const int by_) {
-  FFCZ_AXIS_PROLOGUE(T, L, W_)
+  FFCZ_AXIS_PROLOGUE(T, L, W_, S)
   constexpr int W = G_::W, NT = G_::NT;
   const int M = a.g.M, Nmid = a.g.Nmid;
   const ChkTile c = chk_decode<W>(tile, w, M, Nmid);
@@ -1228,7 +1229,7 @@ __device__ __forceinline__ void k_chk_body(const Args& a, const int bx_, const i
   v2<T> v[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) v[u] = in[u * ustride];
-  load_tables<T>(s_tw, a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
+  load_tables<T>(s_tw, S ? a.tw1 : a.tw, L, nullptr, nullptr, 0);   // overlaps the loads
   const int nmain = Nmid * (M / W);
   const int ntot = chk_ntiles(W, M, Nmid);
   const int first_tile = bx_ * G_::G;
@@ -1243,11 +1244,11 @@ __device__ __forceinline__ void k_chk_body(const Args& a, const int bx_, const i
 #pragma unroll
   for (int u = 0; u < V; ++u) out[u * ustride] = v[u];
 }
-template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true>
+template <typename T, int L, int W_ = TileW<T>::value, bool PW = false, int PV = PV_POCS, bool FULL = true, int S = 0>
 __global__ void __launch_bounds__(Geo<T, L, W_>::NTHR,
                                   (PW || PV != PV_POCS) ? Geo<T, L, W_>::MINB_PW : Geo<T, L, W_>::MINB)
 k_chk(Args a) {
-  k_chk_body<T, L, W_, PW, PV, FULL>(a, (int)blockIdx.x, (int)blockIdx.y);
+  k_chk_body<T, L, W_, PW, PV, FULL, S>(a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------

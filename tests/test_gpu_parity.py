@@ -262,3 +262,50 @@ def test_tma_fed_batch_equals_singles(monkeypatch):
         assert np.array_equal(out[off:off + n], single), f"item {i}"
         assert st[i]["iters"] == s1[0]["iters"] and st[i]["certified"] == 1
         off += n
+
+
+# ------------------------------------------------ radix split of the passes
+def _split_force(shape):
+    """FFCZ_TUNE_FORCE pinning the plain kernels in the swapped radix split
+    (stage 1 of size V, stage 2 of size NT) for every pass whose length has
+    an odd log2; returns (spec, the splits describe() must show)."""
+    def lg(n):
+        return int(n).bit_length() - 1
+    M = shape[-1] // 2
+    Lc = shape[0]
+    parts, want = [], []
+    if lg(M) % 2:
+        parts.append(f"px={(32 >> (lg(M) // 2)) | 256}")
+        want.append(f"px={32 >> (lg(M) // 2)} {M >> (lg(M) // 2)}x{1 << (lg(M) // 2)}")
+    if len(shape) == 3 and lg(shape[1]) % 2:
+        Ly = shape[1]
+        parts.append(f"axis={8 | 256}")
+        want.append(f"axis=8 {Ly >> (lg(Ly) // 2)}x{1 << (lg(Ly) // 2)}")
+    if lg(Lc) % 2:
+        parts.append(f"chk={8 | 256}")
+        want.append(f"chk=8 {Lc >> (lg(Lc) // 2)}x{1 << (lg(Lc) // 2)}")
+    return ",".join(parts), want
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (128, 32, 512), (512, 32, 16), (128, 64), (512, 128)])
+def test_swapped_radix_split_matches_oracle(shape, monkeypatch):
+    """The tuner's radix-split candidates: the same passes with the stage
+    sizes swapped (e.g. 512 = 32 x 16 instead of 16 x 32) after each forced
+    iteration 1..3 and at convergence, against the oracle."""
+    import paper_2601_01596_b300 as ffcz
+    spec, want = _split_force(shape)
+    assert want
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", spec)
+    desc = ffcz.Plan([shape]).describe()
+    for w in want:
+        assert w in desc, (w, desc)
+    e0, E, D = stress(shape, 44)
+    for k in (1, 2, 3):
+        ref = O.correct(e0, E, D, min_iters=k, max_iters=k)
+        e, st = run_gpu(e0, E, D, min_iters=k, max_iters=k, certify=0)
+        assert st[0]["iters"] == k
+        np.testing.assert_allclose(e.reshape(shape), ref.e, rtol=0, atol=TOL * E, err_msg=f"iteration {k}")
+    ref = O.correct(e0, E, D)
+    e, st = run_gpu(e0, E, D)
+    assert abs(st[0]["iters"] - ref.iters) <= 2 and st[0]["certified"] == 1
+    np.testing.assert_allclose(e.reshape(shape), ref.e, rtol=0, atol=TOL * E)
