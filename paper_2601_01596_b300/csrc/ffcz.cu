@@ -801,13 +801,16 @@ void launch_row1(int L, int w, const Args& a, int P1, int count, cudaStream_t s)
 // Words of mask storage one float32 pass writes: MW words per thread of
 // every tile (tiles x threads per tile x words per thread).
 inline int64_t mask_words_per_thread(int L) { return (f2_v(L) + 7) / 8; }
+// Tile width of a tuner width code (fft_core.cuh split flag and the
+// persistent kernel's sign removed).
+inline int code_width(int w) { return std::abs(w) & ~kSplit; }
 inline int64_t x_words(int M, int64_t rows, int W) {
-  W = std::abs(W);
+  W = code_width(W);
   const int64_t tiles = (rows + W - 1) / W;
   return tiles * (int64_t)f2_nt(M) * W * mask_words_per_thread(M);
 }
 inline int64_t chkw(int L, int Nmid, int M, int W) {
-  W = std::abs(W);   // the TMA-fed variant (-8) tiles like the 8-pencil one
+  W = code_width(W);   // the TMA-fed variant (-8) tiles like the 8-pencil one
   return (int64_t)chk_ntiles(W, M, Nmid) * f2_nt(L) * W * mask_words_per_thread(L);
 }
 
@@ -1069,8 +1072,13 @@ bool multi_launch(ffcz_plan_s* p, int k, const std::vector<Args>& args, cudaStre
   } else {
     const auto& m = p->mp[k];
     if ((!p->multi_use[k] && !force) || m.n == 0 || g_pw_sel) return false;
-    for (const Args& a : args) {
+    for (size_t g = 0; g < args.size(); ++g) {
+      const Args& a = args[g];
       if (a.pw_e || a.pw_f || a.pv != PV_POCS) return false;
+      // the multi-group units run the default radix split
+      const DevGroup& dg = p->groups[g];
+      const int w = k == MK_PX ? dg.wx : (k == MK_YINV || k == MK_YFWD) ? dg.wa : k == MK_CHK ? dg.wc : 0;
+      if (w > 0 && (w & kSplit)) return false;
       if (k == MK_PX && px_full(a)) return false;
       if (k == MK_CHK && chk_full(a)) return false;
     }
@@ -2448,6 +2456,56 @@ int pick_width(ffcz_plan_s* p, const std::string& key, int dflt, std::vector<int
   return best;
 }
 
+// FFCZ_TUNE_FORCE="...,split=0" (or 1) fixes the radix split of every
+// tuned pass whose length allows both; returns -1 when not forced.
+int forced_split() {
+  const char* f = getenv("FFCZ_TUNE_FORCE");
+  if (!f) return -1;
+  const std::string spec(f);
+  const size_t pos = spec.find("split=");
+  if (pos == std::string::npos) return -1;
+  return spec[pos + 6] == '1' ? 1 : 0;
+}
+
+// A pass's variant: tile width and, where the length allows both, radix
+// split.  The split of a pass kind and length is ONE decision per process
+// (and per tune cache): the first plan that needs it times every candidate
+// of both splits and the winner's split is kept; later groups of that kind
+// and length tune their tile widths within it.  Tile widths and the
+// copy-engine-fed kernels only regroup the same arithmetic, the split changes
+// its order, so this keeps every plan that shares a length on the same
+// arithmetic (a batch and its single items agree bit for bit).
+template <typename F>
+int pick_variant(ffcz_plan_s* p, const std::string& kind, const std::string& key, int L, int dflt,
+                 const std::vector<int>& cand0, F&& run_w) {
+  std::vector<int> both = cand0;
+  if (split_ok(L, 1))
+    for (int c : cand0)
+      if (c > 0) both.push_back(c | kSplit);
+  if (const int w = forced_width(key, both)) return w;
+  if (!split_ok(L, 1)) return pick_width(p, key, dflt, cand0, run_w);
+  int S = forced_split();
+  const std::string skey = "split_" + kind + "_L" + std::to_string(L);
+  if (S < 0 && !g_no_tune) {
+    std::lock_guard<std::mutex> lk(tune_mu());
+    tune_load();
+    auto it = tune_table().find(skey);
+    if (it != tune_table().end()) S = it->second ? 1 : 0;
+  }
+  if (g_no_tune && S < 0) S = 0;
+  if (S == 0) return pick_width(p, key + "_s0", dflt, cand0, run_w);
+  if (S == 1) {
+    std::vector<int> c1;
+    for (int c : cand0)
+      if (c > 0) c1.push_back(c | kSplit);
+    return pick_width(p, key + "_s1", c1[0], c1, run_w);
+  }
+  const int best = pick_width(p, key + "_sx", dflt, both, run_w);
+  std::lock_guard<std::mutex> lk(tune_mu());
+  tune_store(skey, (best > 0 && (best & kSplit)) ? 1 : 0);
+  return best;
+}
+
 // FFCZ_TUNE_FORCE="...,multi=1" (or 0) fixes the form of every loop pass
 // of multi-group plans; returns -1 when not forced.
 int forced_multi() {
@@ -2474,6 +2532,13 @@ void tune_multi(ffcz_plan_s* p) {
   }
   for (int k = 0; k < MK_N; ++k) {
     if (p->mp[k].n == 0) continue;
+    // the multi-group units run the default radix split
+    bool split_any = false;
+    for (const auto& dg : p->groups) {
+      const int w = k == MK_PX ? dg.wx : (k == MK_YINV || k == MK_YFWD) ? dg.wa : k == MK_CHK ? dg.wc : 0;
+      split_any |= w > 0 && (w & kSplit);
+    }
+    if (split_any) { p->multi_use[k] = false; continue; }
     if (forced >= 0) { p->multi_use[k] = forced == 1; continue; }
     if (g_no_tune) continue;
     const std::string key = gkey + "_" + multi_name(k);
@@ -2543,32 +2608,22 @@ void tune(ffcz_plan_s* p) {
     }
     // candidates: tile widths, the persistent copy-engine-fed kernel, and
     // (odd log2 of the length) the swapped radix split of the plain kernel
-    auto with_split = [](std::vector<int> c, int L) {
-      if (split_ok(L, 1)) {
-        const size_t n = c.size();
-        for (size_t i = 0; i < n; ++i)
-          if (c[i] > 0) c.push_back(c[i] | kSplit);
-      }
-      return c;
-    };
-    dg.wx = pick_width(p, std::string("px_") + base, dg.wx,
-                       with_split({row_w1(dg.M), row_w2(dg.M), -row_w1(dg.M)}, dg.M), [&](int w) {
+    dg.wx = pick_variant(p, "px", std::string("px_") + base, dg.M, dg.wx,
+                         {row_w1(dg.M), row_w2(dg.M), -row_w1(dg.M)}, [&](int w) {
       Args b = a;
       tabs_x<float>(p, b, dg);
       b.mode = 0;
       launch_x<float>(XPX, dg.M, w, b, dg.rows, dg.count, s);
     });
     if (dg.ndim == 3)
-      dg.wa = pick_width(p, std::string("axis_") + base, dg.wa,
-                         with_split(dg.tm_axis ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, dg.Ny),
-                         [&](int w) {
+      dg.wa = pick_variant(p, "axis", std::string("axis_") + base, dg.Ny, dg.wa,
+                           dg.tm_axis ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, [&](int w) {
         Args b = a;
         set_tw<float>(b, p->tb, dg.Ny);
         launch_axis<float, -1>(dg.Ny, w, b, dg.Nz, dg.M, dg.count, s);
       });
-    dg.wc = pick_width(p, std::string("chk_") + base, dg.wc,
-                       with_split(dg.tm_chk ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, dg.Nz),
-                       [&](int w) {
+    dg.wc = pick_variant(p, "chk", std::string("chk_") + base, dg.Nz, dg.wc,
+                         dg.tm_chk ? std::vector<int>{4, 8, -8} : std::vector<int>{4, 8}, [&](int w) {
       Args b = a;
       set_tw<float>(b, p->tb, dg.Nz);
       b.mode = 0;

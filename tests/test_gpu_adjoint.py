@@ -193,7 +193,7 @@ def test_backward_with_copy_engine_fed_x_pass_equals_plain(monkeypatch):
     D = 0.4 * O.f_violation(O.dft(e0.astype(np.float64)))
     g = np.random.default_rng(53).standard_normal(shape).astype(np.float32)
     out = []
-    for force in ("px=tma", None):
+    for force in ("px=tma,split=0", None):
         if force:
             monkeypatch.setenv("FFCZ_TUNE_FORCE", force)
         else:

@@ -28,7 +28,7 @@ def _batch(shapes, seed):
 def _run(shapes, items, Es, Ds, monkeypatch, multi, **opts):
     import torch
     import paper_2601_01596_b300 as ffcz
-    monkeypatch.setenv("FFCZ_TUNE_FORCE", f"multi={multi}")
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", f"multi={multi},split=0")
     plan = ffcz.Plan(shapes, **opts)
     desc = plan.describe()
     packed = np.concatenate([x.reshape(-1) for x in items])
@@ -77,7 +77,7 @@ def test_multi_group_launches_per_iteration_do_not_grow_with_shapes(kind, monkey
     ngroups = len(set(shapes))
     per = {}
     for multi in (1, 0):
-        monkeypatch.setenv("FFCZ_TUNE_FORCE", f"multi={multi}")
+        monkeypatch.setenv("FFCZ_TUNE_FORCE", f"multi={multi},split=0")
         counts = []
         for K in (2, 6):
             plan = ffcz.Plan(shapes, min_iters=K, max_iters=K, certify=0, use_graph=0, chunk=1)

@@ -234,7 +234,7 @@ def test_device_loop_graph_chunk_graphs_and_direct_launch_agree(shape):
                                    (1024, 16, 32), (16, 1024, 32), (1024, 64)])
 def test_tma_fed_passes_equal_plain_passes_and_match_oracle(shape, monkeypatch):
     e0, E, D = stress(shape, 43)
-    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,chk=tma,px=tma")
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "axis=tma,chk=tma,px=tma,split=0")
     a, sa = run_gpu(e0, E, D)
     monkeypatch.delenv("FFCZ_TUNE_FORCE")
     monkeypatch.setenv("FFCZ_TUNE", "0")     # default plain variants
