@@ -100,6 +100,10 @@ def make_workload(name):
         return W.grf_field(32)
     if name == "turbulence256":
         return W.turbulence_field(256)
+    if name.startswith("lognormal:"):
+        # the same recipe on another 3D shape, e.g. lognormal:512x256x512
+        # (smaller cases of the 512-point kernels for profiling)
+        return W.lognormal_shape([int(v) for v in name.split(":", 1)[1].split("x")])
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -939,7 +943,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": it["name"], "shape": list(shape), "eps_s": E, "eps_f": D,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "input 537 MB > 126 MB L2, no flush", "certify": "fp64",
+                   "l2": f"input {field_bytes / 1e6:.0f} MB {'>' if field_bytes > 126e6 else '<'} 126 MB L2, no flush",
+                   "certify": "fp64",
                    "iters": st["iters"], "certified": st["certified"],
                    "step": "ffcz_correct (loop + FP64 certification), e0 resident in HBM",
                    "variants": plan_desc},

@@ -112,6 +112,21 @@ def lognormal_field(n=512, alpha=2.5, seed=0, rel_s=1e-4, rel_f=1e-3, stress=Non
     return it
 
 
+def lognormal_shape(shape, alpha=2.5, seed=0, rel_s=1e-4, rel_f=1e-3, stress=None):
+    """The 512^3 workload's recipe on any 3D shape (smaller cases of the same
+    kernels for profiling): lognormal of a GRF with P(k) ~ k^-alpha."""
+    g = grf(tuple(shape), alpha, seed)
+    np.exp(g, out=g)
+    x = g.astype(np.float32)
+    del g
+    rng = float(x.max()) - float(x.min())
+    E = rel_s * rng
+    it = _item("lognormal" + "x".join(str(n) for n in shape), x, E, 1.0)
+    it["D"] = (stress * max_box_fft(it["e0"])) if stress else rel_f * max_abs_fft(x)
+    it["stress"] = stress
+    return it
+
+
 def turbulence_field(n=256, seed=0, rel_s=1e-4, rel_fe0=0.2):
     """3D n^3 field with E(k) ~ k^-5/3 (per-mode |k|^-11/3).
 

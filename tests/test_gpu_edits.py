@@ -152,3 +152,24 @@ def test_apply_edits_matches_oracle_application(shapes):
         np.testing.assert_allclose(got[off:off + npt].reshape(sh), xs[i] + e[off:off + npt].reshape(sh),
                                    rtol=0, atol=1e-3 * Es[i] + 2e-6 * scale)
         off += npt
+
+
+@pytest.mark.parametrize("shape,seed,frac", [((32, 32, 32), 3, 0.4), ((64, 128), 5, 0.4), ((16, 32, 64), 7, 0.2)])
+def test_decompressed_field_certifies_with_the_doubled_shrink(shape, seed, frac):
+    """Reading A21 on the library: corrected with shrink 2^(1-m), the field
+    rebuilt from the stored m-bit edits (x_hat + S~ + IFFT(F~), here with
+    x = 0 so that x_hat is e0) passes the FP64 certification against the
+    true bounds."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    e0 = W.bimodal_error(shape, seed, E=1.0, dtype=np.float32)
+    E, D, m = 1.0, frac * O.f_violation(O.dft(e0.astype(np.float64))), 16
+    plan = ffcz.Plan([shape], edits=1, shrink=2.0 ** (1 - m))
+    t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    st = plan.correct(t, [E], [D])[0]
+    assert st["certified"] == 1 and st["iters"] >= 2
+    stored = plan.edits_compact(m)
+    xhat = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    plan.apply_edits(xhat, [E], [D], stored, m)
+    chk = plan.check(xhat, [E], [D])[0]
+    assert chk["certified"] == 1, chk
