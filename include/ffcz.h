@@ -75,7 +75,7 @@ typedef struct {
                           (ffcz_edits_dense / ffcz_edits_compact read them);
                           2D and 3D items; default 0 */
   int32_t pointwise;   /* 1: pointwise bounds E_n, Delta_k (ffcz_correct_pw);
-                          2D and 3D items; default 0 */
+                          default 0 */
   int32_t method;      /* projection of the loop (the alternatives Sec. III
                           names to POCS); every method checks its candidate
                           point with the rule of Alg. 1 and returns it:
@@ -160,7 +160,8 @@ size_t ffcz_workspace_bytes(ffcz_plan_t plan);
  * exact arithmetic e_out - e_in = spatial edits + IFFT(frequency edits).
  * The edits describe the last ffcz_correct call on the plan.
  *
- * ffcz_edit_layout -- (any 2D/3D plan) sizes and offsets for item `item`
+ * ffcz_edit_layout -- (any plan; 1D items: N points and N/2 + 1 bins, the
+ * layout of their pointwise frequency bounds) sizes and offsets for item `item`
  * (0-based), or the totals for item = -1, into out[6] (host): points, half-spectrum bins,
  * offset of the item's spatial flags (bytes), spatial codes (int32), frequency
  * flags (bytes), frequency codes (int32; two per bin).  For item = -1 the
@@ -208,9 +209,10 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
  *   eb_dev : device float32, E_n > 0 (normal) for every point, laid out like e.
  *   db_dev : device float32 pairs (Delta^Re, Delta^Im) > 0 on each item's
  *            half spectrum of a real-input FFT, [Nz][Ny][Nx/2+1] (2D:
- *            [Ny][Nx/2+1]), items back to back (the offsets of
- *            ffcz_edit_layout).  Bounds in the kx = 0 and kx = Nx/2 planes
- *            must be even in (ky, kz), as the spectrum of a real field is.
+ *            [Ny][Nx/2+1]; 1D: [N/2+1], bin N - k taking the bounds of bin
+ *            k), items back to back (the offsets of ffcz_edit_layout).
+ *            Bounds in the kx = 0 and kx = Nx/2 planes must be even in
+ *            (ky, kz), as the spectrum of a real field is.
  * The point n is clipped to E_n (1 - eta), Re/Im of bin k to
  * Delta_k^Re/Im (1 - eta); the loop stops when max_k max(|Re|/Delta^Re,
  * |Im|/Delta^Im) <= 1 - eta/2.  Stats carry the normalised ratios (f_ratio,

@@ -89,19 +89,25 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
   bool bad = false;
   float ssq = 0.f;
   unsigned long long cnt = 0;
+  // pointwise bounds (null: the item's scalar bounds): E_n at the item's e
+  // offset, (Delta^Re, Delta^Im) of bins k <= N/2 at its half-spectrum
+  // offset (bin k > N/2 takes those of N - k); the measures are then ratios
+  const float* pwe = a.pw_e ? a.pw_e + a.g.eoff[gi] : nullptr;
+  const float2* pwf = a.pw_f ? a.pw_f + a.g.coff[gi] : nullptr;
   if (op == OP1_ENTRY) {
     float* src = a.e + a.g.eoff[gi];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       const int64_t n = (int64_t)m0 + (int64_t)u * D;
       float x = (live && n < N) ? src[n] : 0.f;
+      const float ebn = (pwe && live && n < N) ? pwe[n] : 1.f;
       if (a.mode & M_MEASURE) {
-        mx.add((T)x);
+        mx.add(pwe ? (T)ratio_cert(x, ebn) : (T)x);
         bad |= (x != x);
         ssq = fmaf(x, x, ssq);
       }
       if (a.mode & M_PRECLIP) {
-        const float cx = clampT(x, p.Esf);
+        const float cx = clampT(x, p.Esf * ebn);
         cnt += (cx != x);
         x = cx;
         if (live && n < N) src[n] = x;
@@ -157,9 +163,18 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
         const v2<T> bk = chirp(u);
         v2<T> X = cmulc<T>(v[u], bk);            // X_k = conj(b_k) c_k / P
         X = mk<T>(X.x * invP, X.y * invP);
-        if (in_range) { mx.add(X.x); mx.add(X.y); bad |= (X.x != X.x) | (X.y != X.y); }
+        T qx = T(1), qy = T(1);
+        if (pwf && in_range) {
+          const float2 q = pwf[k <= N / 2 ? k : N - k];
+          qx = (T)q.x; qy = (T)q.y;
+        }
+        if (in_range) {
+          if (pwf) { mx.add(ratioT(X.x, qx)); mx.add(ratioT(X.y, qy)); }
+          else { mx.add(X.x); mx.add(X.y); }
+          bad |= (X.x != X.x) | (X.y != X.y);
+        }
         if (clip) {
-          const T cx = clampT(X.x, Ds), cy = clampT(X.y, Ds);
+          const T cx = clampT(X.x, Ds * qx), cy = clampT(X.y, Ds * qy);
           if (count && in_range) cnt += (cx != X.x) + (cy != X.y);
           X = mk<T>(cx, cy);
         }
@@ -182,13 +197,14 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
         const bool in_range = live && n < N;
         const v2<T> bn = chirp(u);
         T x = (bn.x * v[u].x - bn.y * v[u].y) * inv_pn;   // Re(b_n c'_n) / (P N)
+        const float ebn = (pwe && in_range) ? pwe[n] : 1.f;
         if (a.mode & M_CLIP) {
-          const T cx = clampT(x, Es);
+          const T cx = clampT(x, Es * (T)ebn);
           if (count && in_range) cnt += (cx != x);
           x = cx;
         }
         if (op == OP1_EXIT) {
-          if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf) : (float)x;
+          if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf * ebn) : (float)x;
         } else {
           v[u] = in_range ? cmulc<T>(mk<T>(x, T(0)), bn) : mk<T>(T(0), T(0));   // x_n conj(b_n)
         }

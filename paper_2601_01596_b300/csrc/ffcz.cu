@@ -915,7 +915,7 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   a.err = p->d_err;
   if (p->opts.pointwise) {
     a.pw_e = p->pw_e;
-    a.pw_f = p->pw_fp;
+    a.pw_f = p->ndim == 1 ? p->pw_f : p->pw_fp;   // 1D: bins k <= N/2 of each item
     a.pw_f0 = p->pw_f0;
   }
   if (p->ed_on) {
@@ -1478,6 +1478,7 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
     q.max_iters = max_iters;
     q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0;
     q.bscale = 1.0;
+    q.pw = p->opts.pointwise ? 1 : 0;
     q.thrs = E * (1.0 - eta / 2.0);
     q.thrsf = (float)q.thrs;
     if (p->ndim == 1) {
@@ -1946,6 +1947,12 @@ void pw_prepare(ffcz_plan_s* p) {
   std::vector<unsigned int> inf(p->batch, 0x7f800000u);
   CK(cudaMemcpyAsync(p->pw_min, inf.data(), sizeof(unsigned int) * p->batch, cudaMemcpyHostToDevice, s));
   for (auto& dg : p->groups) {
+    if (dg.ndim == 1) {   // members of uneven length: N and N/2 + 1 bins read per member
+      k_pw_check1<<<dim3(64, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->d_prm, p->pw_e, p->pw_f, p->pw_min,
+                                                               p->pw_bad);
+      g_launches++;
+      continue;
+    }
     const int64_t nb = (int64_t)dg.Nz * (dg.ndim == 3 ? dg.Ny : 1) * (dg.M + 1);
     const unsigned gx = (unsigned)std::min<int64_t>((std::max(dg.n, nb) + 255) / 256, 2048);
     k_pw_check<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->pw_e, p->pw_f, dg.n, nb, p->pw_min,
@@ -2844,7 +2851,9 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       std::vector<int32_t> it(ids.begin(), ids.end());
       std::vector<int64_t> eo, so;
       for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(soff_c[id]); }
-      if (ndim > 1) {
+      {
+        // each member's offset in the half spectra of a real-input FFT,
+        // items back to back (1D items: N/2 + 1 bins)
         std::vector<int64_t> co;
         int64_t acc = 0;
         std::vector<int64_t> canon(batch);
@@ -2859,6 +2868,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
         CK(cudaMemcpy(d_co, co.data(), sizeof(int64_t) * co.size(), cudaMemcpyHostToDevice));
         dg.d_canon = d_co;
         dg.g.coff = d_co;
+      }
+      if (ndim > 1) {
         // x-row offsets (rows = points / Nx) of every item, for per-row tables
         std::vector<int64_t> rowoff(batch), ro;
         int64_t racc = 0;
@@ -2899,6 +2910,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       if (p->opts.pointwise) {
         g_pw_sel = true;
         for (const auto& dg : p->groups) {
+          if (dg.ndim == 1) continue;   // the 1D passes read the bounds at run time
           launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, nullptr);
           launch_x<double>(XFWD, dg.M, dg.wx, a, dg.rows, 1, nullptr);
           launch_chk<float>(dg.Nz, dg.wc, a, dg.Ny, dg.M, 1, nullptr);
@@ -2963,8 +2975,9 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
     p->d_err = (int*)dalloc(p.get(), sizeof(int));
     if (p->opts.edits && ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edit recording supports 2D and 3D items");
-    if (p->opts.pointwise && ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "pointwise bounds support 2D and 3D items");
-    if (ndim > 1) {
+    {
+      // per item: points, half-spectrum bins, and the offsets of the edit
+      // arrays (1D items: bins of the layout of pointwise frequency bounds)
       p->ed_layout.resize(batch);
       std::array<int64_t, 6> acc{};
       for (int64_t i = 0; i < batch; ++i) {
@@ -2981,9 +2994,11 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (p->opts.pointwise) {
       p->pw_e = (float*)dalloc(p.get(), sizeof(float) * p->total);
       p->pw_f = (float2*)dalloc(p.get(), sizeof(float2) * p->ed_total[1]);
-      p->pw_fp = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
-      build_aux_maps(p.get(), p->pw_fp);
-      p->pw_f0 = (float4*)dalloc(p.get(), sizeof(float4) * p->total_rows);
+      if (ndim > 1) {   // the check pass's packed layouts (1D passes read pw_f)
+        p->pw_fp = (float2*)dalloc(p.get(), sizeof(float2) * p->total_c);
+        build_aux_maps(p.get(), p->pw_fp);
+        p->pw_f0 = (float4*)dalloc(p.get(), sizeof(float4) * p->total_rows);
+      }
       p->pw_min = (unsigned int*)dalloc(p.get(), sizeof(unsigned int) * batch);
       p->pw_bad = (int*)dalloc(p.get(), sizeof(int));
     }
@@ -3035,7 +3050,6 @@ size_t ffcz_workspace_bytes(ffcz_plan_t plan) { return plan ? plan->ws_bytes : 0
 ffcz_status ffcz_edit_layout(ffcz_plan_t plan, int64_t item, int64_t* out) {
   if (!plan || !out) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
-    if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edits exist for 2D and 3D items");
     if (item < -1 || item >= plan->batch) fail(FFCZ_ERR_INVALID, "item out of range");
     const auto& L = item < 0 ? plan->ed_total : plan->ed_layout[item];
     for (int k = 0; k < 6; ++k) out[k] = L[k];

@@ -49,7 +49,8 @@ struct ItemParams {
   double bscale;
   // spatial stopping threshold E(1 - eta/2) of the ADMM variant
   double thrs;
-  float thrsf, pad_f;
+  float thrsf;
+  int32_t pw;   // 1: pointwise bounds (E, D are 1; measures are ratios)
 };
 
 struct ItemState {
@@ -338,6 +339,13 @@ __device__ __forceinline__ float ratioT(float x, float b) {
   return x * r;
 }
 __device__ __forceinline__ double ratioT(double x, double b) { return x / b; }
+// |x| / b for a measured maximum that a certification compares with 1: the
+// approximate ratio, moved to the right side of 1 where it landed on the
+// wrong one (|x| <= b is decided exactly)
+__device__ __forceinline__ float ratio_cert(float x, float b) {
+  const float ax = fabsf(x), r = ratioT(ax, b);
+  return ax <= b ? fminf(r, 1.f) : fmaxf(r, 1.00000012f);
+}
 
 __device__ __forceinline__ float clampT(float x, float b) { return fminf(fmaxf(x, -b), b); }
 __device__ __forceinline__ double clampT(double x, double b) { return fmin(fmax(x, -b), b); }
@@ -526,7 +534,7 @@ __device__ __forceinline__ void k_xfwd_body(const Args& a, const int bx_, const 
     float2 eb = make_float2(1.f, 1.f);
     if constexpr (PW) eb = ebrow[j + u * G_::NT];
     if (a.mode & M_MEASURE) {
-      if constexpr (PW) { mx.add(ratioT(x.x, eb.x)); mx.add(ratioT(x.y, eb.y)); }
+      if constexpr (PW) { mx.add(ratio_cert(x.x, eb.x)); mx.add(ratio_cert(x.y, eb.y)); }
       else { mx.add(x.x); mx.add(x.y); }
       bad |= (x.x != x.x) | (x.y != x.y);
       ssq = fmaf(x.x, x.x, fmaf(x.y, x.y, ssq));
@@ -1647,6 +1655,37 @@ static __global__ void k_pw_check(Group g, const float* pw_e, const float2* pw_f
     if (mn > 0.f) atomicMin(minbits + item, __float_as_uint(mn));
   }
 }
+// The same for 1D items, whose members differ in length: N spatial bounds
+// and N/2 + 1 (Delta^Re, Delta^Im) pairs (bins k <= N/2; bin N - k uses
+// those of k) per member.
+static __global__ void k_pw_check1(Group g, const ItemParams* prm, const float* pw_e, const float2* pw_f,
+                                   unsigned int* minbits, int* bad) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const int64_t npt = prm[item].n, nb = npt / 2 + 1;
+  const float* eb = pw_e + g.eoff[gi];
+  const float2* fb = pw_f + g.coff[gi];
+  int nbad = 0;
+  float mn = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npt; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = eb[i];
+    nbad += !(v >= FLT_MIN && v <= FLT_MAX);
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 q = fb[i];
+    nbad += !(q.x >= FLT_MIN && q.x <= FLT_MAX) + !(q.y >= FLT_MIN && q.y <= FLT_MAX);
+    mn = fminf(mn, fminf(q.x, q.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nbad) atomicAdd(bad, nbad);
+    if (mn > 0.f) atomicMin(minbits + item, __float_as_uint(mn));
+  }
+}
+
 // The caller's (Delta^Re, Delta^Im) on the canonical half spectrum
 // [Nz][Nmid][M+1] into the check pass's layouts: the packed slots kx of each
 // row (1 <= kx < M; slot 0 also gets the kx = 0 bounds) and one float4 per
@@ -1948,9 +1987,11 @@ static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, in
   // that fell below the float32 normal range, and sqrt(N) max|e| (exact);
   // the first overflows for |e| beyond about 2^63, the second is looser
   // when a few points dominate, so the smaller one is used
+  // (with pointwise bounds emax is max |e_n| / E_n, not a bound on |e_n|:
+  // only the sum of squares of the values bounds the norm there)
   const double ssq = s.sumsq + (double)p.n * 0x1p-126;
   const double nrm_max = sqrt((double)p.n) * emax;
-  const double nrm = (ssq <= DBL_MAX) ? fmin(sqrt(ssq), nrm_max) : nrm_max;
+  const double nrm = p.pw ? sqrt(ssq) : (ssq <= DBL_MAX) ? fmin(sqrt(ssq), nrm_max) : nrm_max;
   double b = 10.0 * (ln + 2.0) * 1.1102230246251565e-16 * sqrt((double)p.n) * nrm;
   if (p.logP > 0) {
     // Bluestein: FFT_P, product with Bt (|Bt_k| <= 2N), IFFT_P and two chirp

@@ -195,3 +195,90 @@ def test_tma_fed_pointwise_batch_equals_singles(monkeypatch):
         assert st[i]["iters"] == s1[0]["iters"] >= 2 and st[i]["certified"] == 1, i
         assert np.array_equal(out[off:off + n], single.reshape(-1)), f"item {i}"
         off += n
+
+
+# ------------------------------------------------------------- 1D items
+def _pw1_batch(lengths, seed):
+    """1D signals with pointwise bounds: E_n in [0.6, 1.4], Delta_k random on
+    the half spectrum k <= N/2 (bin N - k takes the bounds of k), scaled so
+    that the f-clip is active."""
+    r = np.random.default_rng(seed)
+    out = []
+    for N in lengths:
+        E_n = 0.6 + 0.8 * r.random(N)
+        e0 = (r.uniform(-1, 1, N) * E_n * 0.999).astype(np.float32)
+        v = O.f_violation(O.dft(e0.astype(np.float64)))
+        half_re = 0.3 * v * (0.5 + r.random(N // 2 + 1))
+        half_im = 0.3 * v * (0.5 + r.random(N // 2 + 1))
+        k = np.arange(N)
+        kk = np.minimum(k, N - k)
+        out.append((e0, E_n, half_re, half_im, half_re[kk], half_im[kk]))
+    return out
+
+
+def _run_pw1(items, **opts):
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    plan = ffcz.Plan([(it[0].size,) for it in items], pointwise=1, **opts)
+    assert plan.edit_layout(-1)[1] == sum(it[0].size // 2 + 1 for it in items)
+    t = torch.from_numpy(np.concatenate([it[0] for it in items])).cuda()
+    eb = torch.from_numpy(np.concatenate([it[1] for it in items]).astype(np.float32)).cuda()
+    db = torch.from_numpy(np.concatenate([(it[2] + 1j * it[3]).astype(np.complex64) for it in items])).cuda()
+    st = plan.correct_pw(t, eb, db)
+    return t.cpu().numpy(), st
+
+
+def test_1d_pointwise_bounds_match_oracle():
+    """A batch of uneven 1D lengths (several Bluestein splits) with
+    pointwise bounds, each item against the oracle run with the same
+    bounds (full-spectrum arrays, even in k)."""
+    lengths = [700, 1500, 3001, 1500, 9000]
+    items = _pw1_batch(lengths, 95)
+    out, st = _run_pw1(items)
+    off = 0
+    for i, (e0, E_n, _, _, D_re, D_im) in enumerate(items):
+        N = e0.size
+        ref = O.correct(e0, E_n, (D_re, D_im))
+        assert ref.iters >= 1
+        assert abs(st[i]["iters"] - ref.iters) <= 2 and st[i]["certified"] == 1, (i, st[i])
+        np.testing.assert_allclose(out[off:off + N], ref.e, rtol=0, atol=1e-3 * E_n.min())
+        assert O.certify(out[off:off + N].astype(np.float64), E_n, (D_re, D_im))[0]
+        off += N
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_1d_pointwise_forced_iterations(k):
+    items = _pw1_batch([2000, 513], 96)
+    out, st = _run_pw1(items, min_iters=k, max_iters=k, certify=0)
+    off = 0
+    for i, (e0, E_n, _, _, D_re, D_im) in enumerate(items):
+        ref = O.correct(e0, E_n, (D_re, D_im), min_iters=k, max_iters=k)
+        assert st[i]["iters"] == k
+        np.testing.assert_allclose(out[off:off + e0.size], ref.e, rtol=0, atol=1e-3 * E_n.min())
+        off += e0.size
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (3000,)])
+def test_certification_bound_of_uniform_pointwise_bounds_equals_scalar(shape):
+    """Uniform pointwise bounds E_n = E = 100, Delta_k = D certify exactly
+    like the scalar bounds: the FP64 rounding bound (and so f_margin64) must
+    not depend on the spatial bounds' scale, whose ratio max|e_n|/E_n bounds
+    no norm."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    N = int(np.prod(shape))
+    e0 = W.bimodal_error(shape, 97, E=1.0, dtype=np.float32)
+    E, D = 100.0, 2.0 * O.f_violation(O.dft(e0.astype(np.float64)))   # feasible as given
+    plan = ffcz.Plan([shape], pointwise=1, max_iters=0, certify=1)
+    t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    nb = plan.edit_layout(-1)[1]
+    eb = torch.full((N,), E, dtype=torch.float32, device="cuda")
+    db = torch.full((nb,), D + 1j * D, dtype=torch.complex64, device="cuda")
+    spw = plan.correct_pw(t, eb, db)[0]
+    ps = ffcz.Plan([shape], max_iters=0, certify=1)
+    ts = torch.from_numpy(e0.reshape(-1).copy()).cuda()
+    ss = ps.correct(ts, [E], [D])[0]
+    assert spw["certified"] == ss["certified"] == 1
+    # the rounding bound is about 3e-13 D here; a norm bound taken from the
+    # ratio max|e_n|/E_n would shrink it about 75-fold
+    assert abs(spw["f_margin64"] - ss["f_margin64"]) <= 1e-14, (spw["f_margin64"], ss["f_margin64"])
