@@ -268,7 +268,8 @@ def test_certification_bound_of_uniform_pointwise_bounds_equals_scalar(shape):
     import paper_2601_01596_b300 as ffcz
     N = int(np.prod(shape))
     e0 = W.bimodal_error(shape, 97, E=1.0, dtype=np.float32)
-    E, D = 100.0, 2.0 * O.f_violation(O.dft(e0.astype(np.float64)))   # feasible as given
+    # feasible as given; D a float32 value, so the complex64 bounds hold it exactly
+    E, D = 100.0, float(np.float32(2.0 * O.f_violation(O.dft(e0.astype(np.float64)))))
     plan = ffcz.Plan([shape], pointwise=1, max_iters=0, certify=1)
     t = torch.from_numpy(e0.reshape(-1).copy()).cuda()
     nb = plan.edit_layout(-1)[1]
