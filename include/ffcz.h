@@ -73,7 +73,7 @@ typedef struct {
   int32_t count_active;/* 1 (default): count active clips for ffcz_stats */
   int32_t edits;       /* 1: record the spatial and frequency edits of Alg. 1
                           (ffcz_edits_dense / ffcz_edits_compact read them);
-                          2D and 3D items; default 0 */
+                          default 0 */
   int32_t pointwise;   /* 1: pointwise bounds E_n, Delta_k (ffcz_correct_pw);
                           default 0 */
   int32_t method;      /* projection of the loop (the alternatives Sec. III
@@ -88,11 +88,12 @@ typedef struct {
                           3 ADMM, a = P_F'(b - u), b = P_S'(a + u),
                             u += a - b; checks a against the s-cube
                             (max|a| <= E(1 - eta/2)).
-                          Methods 1-3 need precision 32, 2D/3D items, no
-                          edits or pointwise bounds (else UNSUPPORTED); they
-                          use one more half-spectrum buffer (1, 2) and two
-                          float32 fields (1, 3); a failed certification is
-                          repaired with FP64 iterations of Alg. 1 */
+                          Methods 1-3 need precision 32 and no edits or
+                          pointwise bounds (else UNSUPPORTED); they use one
+                          more spectrum buffer (1, 2; 1D items: N complex
+                          values each) and two float32 fields (1, 3); a
+                          failed certification is repaired with FP64
+                          iterations of Alg. 1 */
   int32_t reserved_;   /* 0 */
 } ffcz_opts;
 
@@ -150,14 +151,15 @@ size_t ffcz_workspace_bytes(ffcz_plan_t plan);
 
 /*
  * Edits (Alg. 1 "spat_edits"/"freq_edits", Sec. IV-B), recorded by
- * ffcz_correct when the plan was created with opts.edits = 1 (2D and 3D
- * items).  Spatial edits: the sum of the s-clip displacements eps' - eps
+ * ffcz_correct when the plan was created with opts.edits = 1 (1D, 2D and
+ * 3D items).  Spatial edits: the sum of the s-clip displacements eps' - eps
  * (the pre-loop clip of an input outside the s-cube included), float32,
  * laid out like e.  Frequency edits: the sum of the f-clip displacements
  * delta' - delta of every check that did not stop the loop, stored as the
  * half spectrum of a real-input FFT: complex64 (Re, Im float pairs)
- * [Nz][Ny][Nx/2+1] per item (2D: [Ny][Nx/2+1]), items back to back.  In
- * exact arithmetic e_out - e_in = spatial edits + IFFT(frequency edits).
+ * [Nz][Ny][Nx/2+1] per item (2D: [Ny][Nx/2+1]; 1D: [N/2+1]), items back to
+ * back.  In exact arithmetic e_out - e_in = spatial edits + IFFT(frequency
+ * edits).
  * The edits describe the last ffcz_correct call on the plan.
  *
  * ffcz_edit_layout -- (any plan; 1D items: N points and N/2 + 1 bins, the
@@ -194,13 +196,42 @@ ffcz_status ffcz_edits_compact(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, i
  * item) given in the stored form of ffcz_edits_compact (flags and codes at
  * the offsets of ffcz_edit_layout; device memory, read only).  xhat_dev:
  * device float32, the packed items of the base reconstruction, updated in
- * place.  Any 2D/3D plan (opts.edits not needed); uses the plan's spectrum
+ * place.  Any plan (opts.edits not needed); uses the plan's spectrum
  * buffers, so it must not overlap a ffcz_correct call on the same plan.
  * Synchronises the plan's stream.
  */
 ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* eps_s, const double* eps_f,
                              int m_bits, const uint8_t* s_flags, const int32_t* s_codes,
                              const uint8_t* f_flags, const int32_t* f_codes);
+
+/*
+ * ffcz_edits_compact16 -- ffcz_edits_compact with the codes stored in 16
+ * bits (Sec. IV-B: m-bit codes, m = 16 in the paper), for m_bits in [2, 16].
+ * The codes are those of ffcz_edits_compact, in the same order; a code in
+ * [-32767, 32767] is stored as itself (int16), any other (the end point
+ * 2^15 of m = 16, where an edit equals the bound, or an edit larger than the
+ * bound) as the escape -32768, its value going to the item's int32 list
+ * (*_wide) in order of appearance.  Regions: flags as in ffcz_edit_layout;
+ * codes and lists at the same element offsets as ffcz_edit_layout's code
+ * offsets (int16 and int32 elements; a list never holds more entries than
+ * its region has codes).  counts (host, 4 per item, may be NULL): nonzero
+ * spatial components, nonzero frequency bins, spatial escapes, frequency
+ * escapes -- what a reader needs with the flags, codes and lists.
+ * Synchronises the plan's stream; FFCZ_ERR_INVALID for a plan created
+ * without opts.edits or m_bits outside [2, 16].
+ *
+ * ffcz_apply_edits16 -- ffcz_apply_edits from the 16-bit form: the arrays
+ * of ffcz_edits_compact16 (device, read only) and its counts (host, 4 per
+ * item).  FFCZ_ERR_INVALID when a count is out of range or the number of
+ * escapes in an item's codes differs from its count (nothing applied).
+ */
+ffcz_status ffcz_edits_compact16(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, int16_t* s_codes,
+                                 int32_t* s_wide, uint8_t* f_flags, int16_t* f_codes, int32_t* f_wide,
+                                 int64_t* counts);
+ffcz_status ffcz_apply_edits16(ffcz_plan_t plan, float* xhat_dev, const double* eps_s, const double* eps_f,
+                               int m_bits, const uint8_t* s_flags, const int16_t* s_codes, const int32_t* s_wide,
+                               const uint8_t* f_flags, const int16_t* f_codes, const int32_t* f_wide,
+                               const int64_t* counts);
 
 /*
  * ffcz_correct_pw -- ffcz_correct with pointwise bounds (the generalisation
@@ -325,7 +356,10 @@ ffcz_status ffcz_check(ffcz_plan_t plan, const float* e_dev, const double* eps_s
  *   e0_dev       : device float32 input of the forward (not modified)
  *   grad_out_dev : device float32 dL/de_K
  *   grad_in_dev  : device float32 output dL/de0 (may not alias the others)
- * Single-item 2D/3D plans only (batch == 1); else UNSUPPORTED.
+ * All three packed like e (items back to back); eps_s / eps_f per item.  2D
+ * and 3D plans of any batch and any mix of shapes: every item runs exactly
+ * K steps, and each item's product is that of its own single-item plan.
+ * 1D plans: UNSUPPORTED.
  */
 ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0_dev,
                                   const float* grad_out_dev, float* grad_in_dev,

@@ -9,7 +9,7 @@ the method's arithmetic.
 Everything is float64.  The DFT step is a library primitive (``scipy.fft``,
 full complex spectrum, no half-spectrum tricks); everything else is written out
 in the paper's order.  Where the paper leaves a passage open, the reading
-taken is tagged ``A1``..``A26`` and stated in the docstring of the function
+taken is tagged ``A1``..``A27`` and stated in the docstring of the function
 that applies it.
 
 Notation: ``e`` is the spatial error vector (epsilon in the paper), ``delta``
@@ -316,6 +316,47 @@ def dequantize_edits(codes: np.ndarray, bound: float, m: int = 16, complex_pairs
     q = quant_step(bound, m)
     v = np.asarray(codes, dtype=np.float64) * q
     return v[..., 0] + 1j * v[..., 1] if complex_pairs else v
+
+
+ESCAPE16 = -(2 ** 15)
+
+
+def narrow_codes(codes: np.ndarray):
+    """m-bit storage of the codes (Sec. IV-B: each axis of the cube in 2^m
+    intervals, codes of m bits; m = 16).  A27: a code in [-32767, 32767] is
+    stored as itself in int16; any other code (the end point 2^15 = bound / q,
+    or an edit larger than the bound) is stored as the escape -32768 and its
+    value appended, in order of appearance, to an int32 list.  Returns
+    (int16 codes, int32 list); the codes are taken in flat order."""
+    c = np.asarray(codes, dtype=np.int64).reshape(-1)
+    lim = 2 ** 15 - 1
+    out = np.empty(c.size, dtype=np.int16)
+    wide = []
+    for i in range(c.size):
+        v = int(c[i])
+        if -lim <= v <= lim:
+            out[i] = v
+        else:
+            out[i] = ESCAPE16
+            wide.append(v)
+    return out, np.asarray(wide, dtype=np.int32)
+
+
+def widen_codes(c16: np.ndarray, wide: np.ndarray) -> np.ndarray:
+    """The codes back from their 16-bit storage (A27): each escape takes the
+    next entry of the list."""
+    c16 = np.asarray(c16, dtype=np.int16).reshape(-1)
+    out = np.empty(c16.size, dtype=np.int64)
+    k = 0
+    for i in range(c16.size):
+        if int(c16[i]) == ESCAPE16:
+            out[i] = int(wide[k])
+            k += 1
+        else:
+            out[i] = int(c16[i])
+    if k != len(wide):
+        raise ValueError("escape count does not match the list")
+    return out
 
 
 def apply_edits(xhat: np.ndarray, spat: np.ndarray, freq_half: np.ndarray) -> np.ndarray:

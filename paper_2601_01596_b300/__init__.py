@@ -27,7 +27,8 @@ SYMBOLS = ("ffcz_default_opts", "ffcz_plan", "ffcz_set_stream", "ffcz_workspace_
            "ffcz_destroy", "ffcz_strerror", "ffcz_last_error", "ffcz_launch_count",
            "ffcz_profile_enable", "ffcz_profile_count", "ffcz_profile_entry",
            "ffcz_check_static", "ffcz_plan_describe", "ffcz_edit_layout", "ffcz_edits_dense",
-           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_correct_pw", "ffcz_power_spectrum_bounds",
+           "ffcz_edits_compact", "ffcz_apply_edits", "ffcz_edits_compact16", "ffcz_apply_edits16",
+           "ffcz_correct_pw", "ffcz_power_spectrum_bounds",
            "ffcz_ckpt_floats", "ffcz_correct_ckpt", "ffcz_correct_backward_ckpt", "ffcz_fp64_peak")
 STATIC_MAX_POINTS = 1 << 22   # FFCZ_STATIC_MAX_POINTS
 
@@ -107,6 +108,9 @@ def lib() -> ctypes.CDLL:
         L.ffcz_edits_dense.argtypes = [vp, vp, vp]
         L.ffcz_edits_compact.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
         L.ffcz_apply_edits.argtypes = [vp, vp, dp, dp, i32, vp, vp, vp, vp]
+        L.ffcz_edits_compact16.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+        L.ffcz_apply_edits16.argtypes = [vp, vp, dp, dp, i32, vp, vp, vp, vp, vp, vp,
+                                         ctypes.POINTER(ctypes.c_int64)]
         L.ffcz_correct_pw.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.ffcz_power_spectrum_bounds.argtypes = [vp, vp, dp, vp]
         L.ffcz_correct.argtypes = [vp, vp, dp, dp, ctypes.POINTER(Stats)]
@@ -263,6 +267,38 @@ class Plan:
         d["counts"] = np.array(counts, dtype=np.int64).reshape(self.batch, 2)
         return d
 
+    def edits_compact16(self, m_bits: int = 16):
+        """``edits_compact`` with 16-bit codes: dict of CUDA tensors (s_flags,
+        s_codes int16, s_wide int32, f_flags, f_codes int16, f_wide int32) and
+        ``counts`` (numpy [batch, 4]: nonzero spatial / frequency components,
+        spatial / frequency escapes)."""
+        import numpy as np
+        import torch
+        tot = self.edit_layout(-1)
+        d = dict(s_flags=torch.zeros(max(1, tot[2]), dtype=torch.uint8, device="cuda"),
+                 s_codes=torch.zeros(max(1, tot[3]), dtype=torch.int16, device="cuda"),
+                 s_wide=torch.zeros(max(1, tot[3]), dtype=torch.int32, device="cuda"),
+                 f_flags=torch.zeros(max(1, tot[4]), dtype=torch.uint8, device="cuda"),
+                 f_codes=torch.zeros(max(1, tot[5]), dtype=torch.int16, device="cuda"),
+                 f_wide=torch.zeros(max(1, tot[5]), dtype=torch.int32, device="cuda"))
+        counts = (ctypes.c_int64 * (4 * self.batch))()
+        _check(lib().ffcz_edits_compact16(self._h, m_bits, *[ctypes.c_void_p(d[k].data_ptr()) for k in
+                                                           ("s_flags", "s_codes", "s_wide", "f_flags", "f_codes",
+                                                            "f_wide")], counts))
+        d["counts"] = np.array(counts, dtype=np.int64).reshape(self.batch, 4)
+        return d
+
+    def apply_edits16(self, xhat, eps_s, eps_f, stored, m_bits: int = 16, stream=None):
+        """``apply_edits`` from ``edits_compact16``'s dict (counts included)."""
+        import numpy as np
+        self._bind_stream(stream)
+        ptrs = [ctypes.c_void_p(stored[k].data_ptr()) for k in ("s_flags", "s_codes", "s_wide", "f_flags",
+                                                                "f_codes", "f_wide")]
+        c = np.ascontiguousarray(stored["counts"], dtype=np.int64).reshape(-1)
+        counts = (ctypes.c_int64 * c.size)(*[int(x) for x in c])
+        _check(lib().ffcz_apply_edits16(self._h, self._ptr(xhat, "xhat"), _dbl(eps_s, self.batch),
+                                        _dbl(eps_f, self.batch), m_bits, *ptrs, counts))
+
     def apply_edits(self, xhat, eps_s, eps_f, stored, m_bits: int = 16, stream=None):
         """x_hat += S~ + IFFT(F~) from the stored form (``edits_compact``'s
         dict: s_flags, s_codes, f_flags, f_codes); ``xhat`` float32 CUDA, the
@@ -376,13 +412,13 @@ class Plan:
             _check(lib().ffcz_correct_backward(self._h, self._ptr(e0, "e0"),
                                                self._ptr(grad_out, "grad_out"),
                                                self._ptr(grad_in, "grad_in"),
-                                               _dbl(eps_s, 1), _dbl(eps_f, 1)))
+                                               _dbl(eps_s, self.batch), _dbl(eps_f, self.batch)))
             return
         self._check_ckpt(ckpt)
         _check(lib().ffcz_correct_backward_ckpt(self._h, self._ptr(e0, "e0"), ctypes.c_void_p(ckpt.data_ptr()),
                                                 self._ptr(grad_out, "grad_out"),
                                                 self._ptr(grad_in, "grad_in"),
-                                                _dbl(eps_s, 1), _dbl(eps_f, 1)))
+                                                _dbl(eps_s, self.batch), _dbl(eps_f, self.batch)))
 
     def ckpt_floats(self) -> int:
         """Size (float32 values) of the checkpoint buffer of ``correct_ckpt``."""

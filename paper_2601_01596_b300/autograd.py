@@ -56,6 +56,50 @@ def correct_differentiable(e0, eps_s, eps_f, K=50, ckpt_every=10):
     return FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every)
 
 
+_bplans: dict = {}
+
+
+def _bplan(shapes, K, m):
+    key = (tuple(tuple(s) for s in shapes), int(K), int(m), torch.cuda.current_device())
+    p = _bplans.get(key)
+    if p is None:
+        p = Plan([tuple(s) for s in shapes], min_iters=K, max_iters=K, certify=0, K=K, ckpt_every=m)
+        _bplans[key] = p
+    return p
+
+
+class FFCzCorrectBatch(torch.autograd.Function):
+    """The same for a batch of items of any shapes (2D or 3D), packed back to
+    back in one float32 CUDA tensor; eps_s / eps_f one per item."""
+
+    @staticmethod
+    def forward(ctx, e0, shapes, eps_s, eps_f, K: int = 50, ckpt_every: int = 10):
+        if e0.dtype != torch.float32 or not e0.is_cuda:
+            raise TypeError("e0 must be a float32 CUDA tensor")
+        e0c = e0.detach().contiguous()
+        plan = _bplan(shapes, K, ckpt_every)
+        e = e0c.clone()
+        ckpt = torch.empty(plan.ckpt_floats(), dtype=torch.float32, device=e0c.device)
+        plan.correct_ckpt(e.reshape(-1), list(eps_s), list(eps_f), ckpt)
+        ctx.save_for_backward(e0c, ckpt)
+        ctx.cfg = (tuple(tuple(s) for s in shapes), tuple(eps_s), tuple(eps_f), int(K), int(ckpt_every))
+        return e
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        e0, ckpt = ctx.saved_tensors
+        shapes, eps_s, eps_f, K, m = ctx.cfg
+        plan = _bplan(shapes, K, m)
+        g = grad_out.detach().to(torch.float32).contiguous()
+        gin = torch.empty_like(e0)
+        plan.backward(e0.reshape(-1), g.reshape(-1), gin.reshape(-1), list(eps_s), list(eps_f), ckpt=ckpt)
+        return gin, None, None, None, None, None
+
+
+def correct_differentiable_batch(e0, shapes, eps_s, eps_f, K=50, ckpt_every=10):
+    return FFCzCorrectBatch.apply(e0, shapes, eps_s, eps_f, K, ckpt_every)
+
+
 _shell_cache: dict = {}
 
 

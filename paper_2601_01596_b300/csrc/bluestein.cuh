@@ -30,6 +30,7 @@ enum Op1 : int {
   OP1_SCLIP = 2,   // column: inverse step, x = Re(b c)/(P N), s-clip, pre, forward
   OP1_EXIT = 3,    // column: inverse step, x, s-clip, store float32 e
   OP1_FILTER = 4,  // column: forward column step of the wrapped chirp f (Bt build)
+  OP1_LOADX = 5,   // column: half spectrum X (k <= N/2) -> X_k b_k, forward column step
   OP1_CONV = 8,    // row: FFT, times Bt, IFFT
   OP1_CONVC = 9,   // row: FFT, times conj Bt, IFFT
   OP1_FWD = 10     // row: FFT only (Bt build)
@@ -109,10 +110,24 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
       if (a.mode & M_PRECLIP) {
         const float cx = clampT(x, p.Esf * ebn);
         cnt += (cx != x);
+        if (a.ed_s && live && n < N && cx != x) atomicAdd(a.ed_s + a.g.eoff[gi] + n, cx - x);   // S += eps' - eps
         x = cx;
         if (live && n < N) src[n] = x;
       }
       v[u] = mk<T>((T)x, T(0));
+    }
+  } else if (op == OP1_LOADX) {
+    // X_k b_k from the item's half spectrum (bin k > N/2 is conj X_{N-k})
+    const float2* hx = a.ed_f + a.g.coff[gi];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t k = (int64_t)m0 + (int64_t)u * D;
+      v2<T> X = mk<T>(T(0), T(0));
+      if (live && k < N) {
+        const float2 h = hx[k <= N / 2 ? k : N - k];
+        X = mk<T>((T)h.x, k <= N / 2 ? (T)h.y : -(T)h.y);
+      }
+      v[u] = cmul<T>(X, chirp(u));
     }
   } else if (op != OP1_FILTER) {
     const v2<T>* in = pick<T>(a, a.sel_in, t_it) + a.g.soff[gi] + m0;
@@ -146,7 +161,7 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
         if ((a.mode & M_PRECLIP) && rr.cnt) atomicAdd(&st.act_s, rr.cnt);
       }
     }
-  } else {
+  } else if (op != OP1_LOADX) {
     // inverse column step: conj twiddle, IFFT along k1 -> c[n1][n2] * P
 #pragma unroll
     for (int u = 0; u < V; ++u) v[u] = cmulc<T>(v[u], twp[(j + u * NT) * n2]);
@@ -156,6 +171,17 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
       const T invP = T(1) / (T)Pn;   // exact: P is a power of two
       const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
       const bool clip = (a.mode & M_CLIP) != 0;
+      // edits: bins k <= N/2 (the half spectrum); clips at the max_iters
+      // check are not recorded, and a marginal one (at most the stopping
+      // threshold, from min_iters on) is remembered for the loop's end
+      const bool rec_f = clip && a.ed_t != nullptr && t_it < p.max_iters;
+      const bool may_stop = t_it >= p.min_iters;
+      const T thr = sizeof(T) == 4 ? (T)p.thrf : (T)p.thr;
+      // Dykstra / Douglas-Rachford: residual r of the previous frequency
+      // projection per bin k < N (zero before the first one); y = P_F'(X + r),
+      // r <- X + r - y, output y (Dykstra) or y - r (Douglas-Rachford)
+      const bool res = clip && (a.pv == PV_DYKSTRA || a.pv == PV_DR);
+      float2* rr = res ? a.pv_r + a.g.eoff[gi] : nullptr;
 #pragma unroll
       for (int u = 0; u < V; ++u) {
         const int64_t k = (int64_t)m0 + (int64_t)u * D;
@@ -173,9 +199,21 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
           else { mx.add(X.x); mx.add(X.y); }
           bad |= (X.x != X.x) | (X.y != X.y);
         }
-        if (clip) {
+        if (res) {
+          const float2 r0 = (t_it >= 1 && in_range) ? rr[k] : make_float2(0.f, 0.f);
+          const T x = X.x + (T)r0.x, y = X.y + (T)r0.y;
+          const T cx = clampT(x, Ds), cy = clampT(y, Ds);
+          if (count && in_range) cnt += (cx != x) + (cy != y);
+          const T rx = x - cx, ry = y - cy;
+          if (in_range) rr[k] = make_float2((float)rx, (float)ry);
+          X = a.pv == PV_DYKSTRA ? mk<T>(cx, cy) : mk<T>(cx - rx, cy - ry);
+        } else if (clip) {
           const T cx = clampT(X.x, Ds * qx), cy = clampT(X.y, Ds * qy);
           if (count && in_range) cnt += (cx != X.x) + (cy != X.y);
+          if (rec_f && in_range && k <= N / 2) {
+            const T big = pwf ? fmax(ratioT(fabs(X.x), qx), ratioT(fabs(X.y), qy)) : fmax(fabs(X.x), fabs(X.y));
+            record_f(a, a.g.coff[gi] + k, (float)(cx - X.x), (float)(cy - X.y), t_it, may_stop && big <= thr);
+          }
           X = mk<T>(cx, cy);
         }
         v[u] = in_range ? cmul<T>(X, bk) : mk<T>(T(0), T(0));   // pre: X'_k b_k
@@ -191,6 +229,16 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
       const T inv_pn = sizeof(T) == 4 ? (T)p.inv_pnf : (T)p.inv_pn;
       const T Es = sizeof(T) == 4 ? (T)p.Esf : (T)p.Es;
       float* eo = a.e + a.g.eoff[gi];
+      float* eo_s = a.ed_s ? a.ed_s + a.g.eoff[gi] : nullptr;   // spatial edits S += eps' - eps
+      // Dykstra's q / ADMM's scaled dual u, one buffer per iteration parity
+      // (zero before the second s-projection); ADMM checks a_t (the input)
+      // against the s-cube
+      const int pv = a.pv;
+      const bool qv = (pv == PV_DYKSTRA || pv == PV_ADMM) && (a.mode & M_CLIP);
+      const float* q_in = (pv == PV_DYKSTRA || pv == PV_ADMM) && t_it >= 2 ? a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]
+                                                                            : nullptr;
+      float* q_out = qv && op == OP1_SCLIP ? a.pv_q[t_it & 1] + a.g.eoff[gi] : nullptr;
+      AbsMax<T> svm;
 #pragma unroll
       for (int u = 0; u < V; ++u) {
         const int64_t n = (int64_t)m0 + (int64_t)u * D;
@@ -198,22 +246,38 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
         const v2<T> bn = chirp(u);
         T x = (bn.x * v[u].x - bn.y * v[u].y) * inv_pn;   // Re(b_n c'_n) / (P N)
         const float ebn = (pwe && in_range) ? pwe[n] : 1.f;
-        if (a.mode & M_CLIP) {
+        if (qv && op == OP1_SCLIP) {
+          const T q0 = (q_in && in_range) ? (T)q_in[n] : T(0);
+          if (pv == PV_ADMM && in_range) svm.add(x);
+          const T wv = x + q0, c = clampT(wv, Es);
+          if (count && in_range) cnt += (c != wv);
+          if (in_range) q_out[n] = (float)(wv - c);
+          x = pv == PV_DYKSTRA ? c : c - (wv - c);   // ADMM forwards b - u
+        } else if (op == OP1_EXIT && pv == PV_DYKSTRA && q_in && in_range) {
+          x += (T)q_in[n];   // x_t = P_S'(y_{t-1} + q_{t-1})
+        }
+        if ((a.mode & M_CLIP) && !(qv && op == OP1_SCLIP)) {
           const T cx = clampT(x, Es * (T)ebn);
           if (count && in_range) cnt += (cx != x);
+          if (op == OP1_SCLIP && a.ed_s && in_range && cx != x) atomicAdd(eo_s + n, (float)(cx - x));
           x = cx;
         }
         if (op == OP1_EXIT) {
-          if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf * ebn) : (float)x;
+          if (in_range && (a.mode & M_ACC)) eo[n] += (float)x;   // decompression side: x_hat += IDFT(F)
+          else if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf * ebn) : (float)x;
         } else {
           v[u] = in_range ? cmulc<T>(mk<T>(x, T(0)), bn) : mk<T>(T(0), T(0));   // x_n conj(b_n)
         }
       }
       if (op == OP1_EXIT) return;
-      if (count) {
-        unsigned long long vb = 0ull;
-        block_max_count(vb, cnt, true, s_red);
-        if (threadIdx.x == 0 && cnt) atomicAdd(&st.act_s, cnt);
+      if (count || (qv && pv == PV_ADMM)) {
+        // ADMM: max |a_t| over the CTA's points (NaN -> +inf)
+        unsigned long long vb = (qv && pv == PV_ADMM) ? svm.dbits(svm.val() != svm.val()) : 0ull;
+        block_max_count(vb, cnt, count, s_red);
+        if (threadIdx.x == 0) {
+          if (qv && pv == PV_ADMM) atomicMax(&st.svbits, vb);
+          if (cnt) atomicAdd(&st.act_s, cnt);
+        }
       }
     }
   }

@@ -152,6 +152,126 @@ static __global__ void k_edits_scatter(const EdRegion<C>* regs) {
     if (byte & (1u << t)) put_codes(r.codes, k++, r.vals[b * 8 + t], r.q);
 }
 
+// ----- 16-bit storage of the codes (m <= 16) -----------------------------------
+// A code in [-32767, 32767] is stored as itself in int16; any other code (the
+// end point 2^15 of m = 16, or an edit beyond the bound) as the escape -32768,
+// with its value appended, in order of appearance, to an int32 list.
+
+constexpr int16_t kEscape16 = -32768;
+__device__ __forceinline__ bool code_escapes(int32_t c) { return c < -32767 || c > 32767; }
+
+// One region of codes: narrowing reads c32 and writes c16 + wide; widening
+// reads c16 + wide (nwide entries) and writes c32.
+struct CodeRegion {
+  int32_t* c32;
+  int16_t* c16;
+  int32_t* wide;
+  int64_t n;       // codes in the region
+  int64_t nwide;   // widening: entries of the list
+  int* chunks;     // escapes per chunk of kEdChunk codes -> exclusive offsets
+};
+
+// Block-wide exclusive scan of nch chunk counts in place (blockDim.x = 1024);
+// returns the total to every thread.
+__device__ long long scan_chunks(int* chunks, int64_t nch) {
+  __shared__ long long carry;
+  __shared__ long long s[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nch; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const long long v = i < nch ? chunks[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive Hillis-Steele scan
+      const long long add = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nch) chunks[i] = (int)(carry + s[threadIdx.x] - v);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+    __syncthreads();
+  }
+  return carry;
+}
+
+// Escapes per chunk; each thread owns 8 consecutive codes.
+template <bool NARROW>
+static __global__ void k_codes_count(const CodeRegion* regs) {
+  const CodeRegion r = regs[blockIdx.y];
+  const int64_t c0 = (int64_t)blockIdx.x * kEdChunk;
+  if (c0 >= r.n) return;
+  const int64_t i0 = c0 + (int64_t)threadIdx.x * 8;
+  int cnt = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t i = i0 + t;
+    if (i < r.n) cnt += NARROW ? (int)code_escapes(r.c32[i]) : (int)(r.c16[i] == kEscape16);
+  }
+  __shared__ int s[kEdThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kEdThreads / 32; ++w) t += s[w];
+    r.chunks[blockIdx.x] = t;
+  }
+}
+
+// Exclusive offsets of the chunks of each region (one CTA per region); the
+// region's escape count goes to totals[region].
+static __global__ void k_codes_scan(const CodeRegion* regs, int64_t* totals) {
+  const CodeRegion r = regs[blockIdx.x];
+  const long long t = scan_chunks(r.chunks, (r.n + kEdChunk - 1) / kEdChunk);
+  if (threadIdx.x == 0) totals[blockIdx.x] = t;
+}
+
+// Narrowing: int16 codes and the escaped values at their list positions.
+// Widening: int32 codes, an escape taking the list entry of its rank (the
+// host has checked that the escapes number exactly nwide).
+template <bool NARROW>
+static __global__ void k_codes_scatter(const CodeRegion* regs) {
+  const CodeRegion r = regs[blockIdx.y];
+  const int64_t c0 = (int64_t)blockIdx.x * kEdChunk;
+  if (c0 >= r.n) return;
+  const int64_t i0 = c0 + (int64_t)threadIdx.x * 8;
+  unsigned esc = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t i = i0 + t;
+    if (i < r.n && (NARROW ? code_escapes(r.c32[i]) : r.c16[i] == kEscape16)) esc |= 1u << t;
+  }
+  const int cnt = __popc(esc);
+  __shared__ int s[kEdThreads / 32];
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((threadIdx.x & 31) >= (unsigned)o) incl += y;
+  }
+  if ((threadIdx.x & 31) == 31) s[threadIdx.x >> 5] = incl;
+  __syncthreads();
+  int wbase = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbase += s[w];
+  int64_t k = (int64_t)r.chunks[blockIdx.x] + wbase + incl - cnt;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int64_t i = i0 + t;
+    if (i >= r.n) break;
+    const bool e = (esc >> t) & 1u;
+    if constexpr (NARROW) {
+      const int32_t c = r.c32[i];
+      r.c16[i] = e ? kEscape16 : (int16_t)c;
+      if (e) r.wide[k] = c;
+    } else {
+      r.c32[i] = e ? (k < r.nwide ? r.wide[k] : 0) : (int32_t)r.c16[i];
+    }
+    k += e;
+  }
+}
+
 // ----- power-spectrum relative bounds (reading: the per-shell positive root) -------
 // Shell of a canonical bin (kz, ky, kx): rounded radius of the signed
 // frequency vector; kx in [0, M] is already non-negative.

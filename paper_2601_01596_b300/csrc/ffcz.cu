@@ -241,6 +241,13 @@ struct ffcz_plan_s {
   int64_t* ed_tot = nullptr;     // device per-region counts [2 batch]
   void* ap_reg = nullptr;        // device ApRegion[2 batch] (edit application)
   int64_t ed_chunk_cap = 0;
+  // 16-bit code storage: int32 codes of every region, code regions, escape
+  // counts, chunk offsets
+  int32_t* cd_c32 = nullptr;
+  void* cd_reg = nullptr;        // device CodeRegion[2 batch]
+  int64_t* cd_tot = nullptr;     // device [2 batch]
+  int* cd_chunks = nullptr;
+  int64_t cd_chunk_cap = 0;
   int* h_err = nullptr;         // pinned copy
   int num_sms = 148;
   ItemState* h_st = nullptr;    // pinned
@@ -283,7 +290,8 @@ struct ffcz_plan_s {
   // forward of the differentiable form: the loop's x pass writes the
   // backward's checkpoints into bw_ck (ffcz_correct_ckpt)
   bool ck_rec = false;
-  int64_t px_words = 0, chk_words = 0;
+  int64_t px_words = 0, chk_words = 0;       // mask words of one step (all groups)
+  std::vector<int64_t> bw_pxoff, bw_chkoff;  // each group's offset in a step's block
 };
 
 namespace {
@@ -912,6 +920,8 @@ Args make_args(ffcz_plan_s* p, const DevGroup& dg, void* b0, void* b1, ItemState
   a.pred = P_ACTIVE;
   a.sel_in = a.sel_out = S_CUR;
   a.ckpt_every = 0;
+  a.ckpt_stride = p->total;
+  a.mask_thr = 0;
   a.err = p->d_err;
   if (p->opts.pointwise) {
     a.pw_e = p->pw_e;
@@ -1193,7 +1203,7 @@ void body1(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     }
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
-                                                             p->d_nactive);
+                                                             p->d_nactive, s_check_of<T>(p));
   g_launches++;
 }
 
@@ -1208,7 +1218,8 @@ void exit1(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
     launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
     a.sel_in = S_CUR;
     col1_args<T>(p, a, dg, OP1_EXIT);
-    a.mode = M_CLIP;
+    // ADMM returns a_t, which its check found inside the s-cube, unclipped
+    a.mode = s_check_of<T>(p) ? 0 : M_CLIP;
     launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
 }
@@ -1501,6 +1512,14 @@ int read_active(ffcz_plan_s* p) {
 // Commit the pending frequency edits of checks that did not stop the loop.
 void edits_finalize(ffcz_plan_s* p) {
   for (auto& dg : p->groups) {
+    if (dg.ndim == 1) {   // half spectra of N/2 + 1 <= P/4 + 1 bins per member
+      const int64_t slots = (int64_t)dg.P1 * dg.P2 / 4 + 1;
+      const unsigned gx = (unsigned)std::min<int64_t>((slots + 255) / 256, 4096);
+      k_edits_finalize1<<<dim3(gx, (unsigned)dg.count), 256, 0, p->stream>>>(dg.g, p->d_prm, p->d_st, p->ed_f,
+                                                                               p->ed_p, p->ed_t);
+      g_launches++;
+      continue;
+    }
     const int64_t slots = dg.n / 2;
     const unsigned gx = (unsigned)std::min<int64_t>((slots + 255) / 256, 4096);
     k_edits_finalize<<<dim3(gx, (unsigned)dg.count), 256, 0, p->stream>>>(dg.g, p->d_st, p->ed_f, p->ed_p,
@@ -1512,6 +1531,10 @@ void edits_finalize(ffcz_plan_s* p) {
 // Canonical half-spectrum form of the committed frequency edits.
 void edits_canon(ffcz_plan_s* p) {
   if (!p->ed_canon) p->ed_canon = (float2*)dalloc(p, sizeof(float2) * std::max<int64_t>(1, p->ed_total[1]));
+  if (p->ndim == 1) {   // 1D items record on their half spectra directly
+    CK(cudaMemcpyAsync(p->ed_canon, p->ed_f, sizeof(float2) * p->ed_total[1], cudaMemcpyDeviceToDevice, p->stream));
+    return;
+  }
   for (auto& dg : p->groups) {
     const int64_t nb = (int64_t)dg.Nz * (dg.ndim == 3 ? dg.Ny : 1) * (dg.M + 1);
     const unsigned gx = (unsigned)std::min<int64_t>((nb + 255) / 256, 4096);
@@ -1684,6 +1707,31 @@ void apply_edits(ffcz_plan_s* p, float* xhat, int m, const uint8_t* sf, const in
   k_apply_scan<<<(unsigned)B, 1024, 0, s>>>(rf);
   k_apply_expand<true><<<dim3((unsigned)maxf, (unsigned)B), kEdThreads, 0, s>>>(rf);
   g_launches += 6;
+  if (p->ndim == 1) {
+    // x_hat += IDFT(F): the half spectrum times the chirp, forward column
+    // step; row pass with conj Bt; inverse column step, x = Re(b c) / (P N)
+    // added to x_hat
+    for (auto& dg : p->groups) {
+      Args a = make_args<float>(p, dg, p->B32[0], p->B32[0], p->d_st);
+      a.pred = P_ALL;
+      a.sel_in = a.sel_out = S_CUR;
+      a.pw_e = nullptr; a.pw_f = nullptr;
+      a.ed_f = p->ed_canon;
+      col1_args<float>(p, a, dg, OP1_LOADX);
+      a.mode = 0;
+      launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
+      a.ed_f = nullptr;
+      row1_args<float>(p, a, dg, OP1_CONVC);
+      launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
+      col1_args<float>(p, a, dg, OP1_EXIT);
+      a.e = xhat;
+      a.mode = M_ACC;
+      launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    return;
+  }
   for (auto& dg : p->groups) {
     const int Nmid = dg.ndim == 3 ? dg.Ny : 1;
     const int64_t slots = (int64_t)dg.Nz * Nmid * dg.M;
@@ -1711,6 +1759,108 @@ void apply_edits(ffcz_plan_s* p, float* xhat, int m, const uint8_t* sf, const in
   }
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+}
+
+// 16-bit storage of the codes of 2 B regions: narrowing (int32 -> int16 and
+// the escaped values) or widening (back to int32; every region must hold
+// exactly its nwide escapes).  esc[r] receives region r's escape count.
+void codes_convert(ffcz_plan_s* p, std::vector<CodeRegion>& rg, bool narrow, std::vector<int64_t>& esc) {
+  const int64_t R = (int64_t)rg.size();
+  int64_t chunks = 0, maxc = 1;
+  for (auto& r : rg) {
+    const int64_t c = (r.n + kEdChunk - 1) / kEdChunk;
+    chunks += c;
+    maxc = std::max(maxc, c);
+  }
+  if (chunks > p->cd_chunk_cap) {
+    p->cd_chunks = (int*)dalloc(p, sizeof(int) * std::max<int64_t>(1, chunks));
+    p->cd_chunk_cap = chunks;
+  }
+  if (!p->cd_reg) {
+    p->cd_reg = dalloc(p, sizeof(CodeRegion) * R);
+    p->cd_tot = (int64_t*)dalloc(p, sizeof(int64_t) * R);
+  }
+  int64_t ch = 0;
+  for (auto& r : rg) {
+    r.chunks = p->cd_chunks + ch;
+    ch += (r.n + kEdChunk - 1) / kEdChunk;
+  }
+  cudaStream_t s = p->stream;
+  CK(cudaMemcpyAsync(p->cd_reg, rg.data(), sizeof(CodeRegion) * R, cudaMemcpyHostToDevice, s));
+  auto* d = static_cast<const CodeRegion*>(p->cd_reg);
+  if (narrow) k_codes_count<true><<<dim3((unsigned)maxc, (unsigned)R), kEdThreads, 0, s>>>(d);
+  else k_codes_count<false><<<dim3((unsigned)maxc, (unsigned)R), kEdThreads, 0, s>>>(d);
+  k_codes_scan<<<(unsigned)R, 1024, 0, s>>>(d, p->cd_tot);
+  g_launches += 2;
+  esc.assign(R, 0);
+  CK(cudaMemcpyAsync(esc.data(), p->cd_tot, sizeof(int64_t) * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!narrow)
+    for (int64_t r = 0; r < R; ++r)
+      if (esc[r] != rg[r].nwide) fail(FFCZ_ERR_INVALID, "escape count of the 16-bit codes differs from counts");
+  if (narrow) k_codes_scatter<true><<<dim3((unsigned)maxc, (unsigned)R), kEdThreads, 0, s>>>(d);
+  else k_codes_scatter<false><<<dim3((unsigned)maxc, (unsigned)R), kEdThreads, 0, s>>>(d);
+  g_launches++;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+}
+
+int32_t* codes32(ffcz_plan_s* p) {
+  if (!p->cd_c32)
+    p->cd_c32 = (int32_t*)dalloc(p, sizeof(int32_t) * std::max<int64_t>(1, p->ed_total[3] + p->ed_total[5]));
+  return p->cd_c32;
+}
+
+// CompactEdits + QuantizeEdits with the codes stored in 16 bits; counts (4
+// per item): nonzero spatial components, nonzero bins, spatial escapes,
+// frequency escapes.
+void edits_compact16(ffcz_plan_s* p, int m, uint8_t* sf, int16_t* sc, int32_t* sw, uint8_t* ff, int16_t* fc,
+                     int32_t* fw, int64_t* counts) {
+  const int64_t B = p->batch;
+  int32_t* s32 = codes32(p);
+  int32_t* f32 = s32 + p->ed_total[3];
+  std::vector<int64_t> nz(2 * B), esc;
+  edits_compact(p, m, sf, s32, ff, f32, nz.data());
+  std::vector<CodeRegion> rg(2 * B);
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    rg[i] = {s32 + L[3], sc + L[3], sw + L[3], nz[2 * i], 0, nullptr};
+    rg[B + i] = {f32 + L[5], fc + L[5], fw + L[5], 2 * nz[2 * i + 1], 0, nullptr};
+  }
+  codes_convert(p, rg, true, esc);
+  if (counts)
+    for (int64_t i = 0; i < B; ++i) {
+      counts[4 * i] = nz[2 * i];
+      counts[4 * i + 1] = nz[2 * i + 1];
+      counts[4 * i + 2] = esc[i];
+      counts[4 * i + 3] = esc[B + i];
+    }
+}
+
+// The decompression side from the 16-bit form: the codes widened to int32,
+// then applied as from ffcz_edits_compact's form.
+void apply_edits16(ffcz_plan_s* p, float* xhat, int m, const uint8_t* sf, const int16_t* sc, const int32_t* sw,
+                   const uint8_t* ff, const int16_t* fc, const int32_t* fw, const int64_t* counts) {
+  const int64_t B = p->batch;
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    const int64_t ns = counts[4 * i], nf = counts[4 * i + 1], es = counts[4 * i + 2], ef = counts[4 * i + 3];
+    if (ns < 0 || ns > L[0] || nf < 0 || nf > L[1] || es < 0 || es > ns || ef < 0 || ef > 2 * nf)
+      fail(FFCZ_ERR_INVALID, "edit counts out of range");
+  }
+  int32_t* s32 = codes32(p);
+  int32_t* f32 = s32 + p->ed_total[3];
+  std::vector<CodeRegion> rg(2 * B);
+  for (int64_t i = 0; i < B; ++i) {
+    const auto& L = p->ed_layout[i];
+    rg[i] = {s32 + L[3], const_cast<int16_t*>(sc) + L[3], const_cast<int32_t*>(sw) + L[3], counts[4 * i],
+             counts[4 * i + 2], nullptr};
+    rg[B + i] = {f32 + L[5], const_cast<int16_t*>(fc) + L[5], const_cast<int32_t*>(fw) + L[5],
+                 2 * counts[4 * i + 1], counts[4 * i + 3], nullptr};
+  }
+  std::vector<int64_t> esc;
+  codes_convert(p, rg, false, esc);
+  apply_edits(p, xhat, m, sf, s32, ff, f32);
 }
 
 template <typename T>
@@ -2144,68 +2294,84 @@ __global__ void k_set_t(ItemState* st, int n, int t) {
 }
 
 void advance(ffcz_plan_s* p, ItemState* st) {
-  k_advance<<<1, 32, 0, p->stream>>>(st, 1);
+  k_advance<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(st, (int)p->batch);
   g_launches++;
 }
 void set_t(ffcz_plan_s* p, ItemState* st, int t) {
-  k_set_t<<<1, 32, 0, p->stream>>>(st, 1, t);
+  k_set_t<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(st, (int)p->batch, t);
   g_launches++;
 }
 
-// One forward iteration body with mask recording (replay), no decide.
-void replay_body(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, uint32_t* smask,
-                 uint32_t* fmask, float* ckpt, bool do_chk) {
-  Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
-  a.pred = P_ALL;
-  if (dg.ndim == 3) {
-    set_tw<float>(a, p->tb, dg.Ny);
-    a.sel_in = S_PREV; a.sel_out = S_CUR;
-    launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
-    a.sel_in = S_CUR;
-  } else {
-    a.sel_in = S_PREV; a.sel_out = S_CUR;
-  }
-  tabs_x<float>(p, a, dg);
-  a.mode = M_CLIP | (smask ? M_RECORD : 0) | (ckpt ? M_CKPT : 0);
-  a.mask = smask;
-  a.ckpt = ckpt;
-  a.ckpt_every = p->bw_m;
-  launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, 1, p->stream);
-  if (!do_chk) return;
-  a.sel_in = a.sel_out = S_CUR;
-  a.mask = nullptr;
-  a.ckpt = nullptr;
-  if (dg.ndim == 3) {
-    set_tw<float>(a, p->tb, dg.Ny);
-    a.mode = 0;
-    launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
-  }
-  set_tw<float>(a, p->tb, dg.Nz);
-  a.mode = M_CLIP | (fmask ? M_RECORD : 0);
-  a.mask = fmask;
-  launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+// Mask threads per group member of the x pass and of the check pass (the
+// words of member gi start at gi x threads x words per thread).
+int64_t px_mask_thr(const DevGroup& dg) { return x_words(dg.M, dg.rows, dg.wx) / mask_words_per_thread(dg.M); }
+int64_t chk_mask_thr(const DevGroup& dg) {
+  return chkw(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc) / mask_words_per_thread(dg.Nz);
 }
 
-void replay_entry(ffcz_plan_s* p, const DevGroup& dg, LoopBufs B, float* e0, uint32_t* fmask) {
-  Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
-  a.pred = P_ALL;
-  tabs_x<float>(p, a, dg);
-  a.e = e0;
-  a.mode = 0;
-  launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, p->stream);
-  if (dg.ndim == 3) {
-    set_tw<float>(a, p->tb, dg.Ny);
-    launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
+// One forward iteration body with mask recording (replay), no decide, for
+// every group.  smask / fmask: one step's mask block (group g's words at
+// bw_pxoff[g] / bw_chkoff[g]).
+void replay_body(ffcz_plan_s* p, LoopBufs B, uint32_t* smask, uint32_t* fmask, float* ckpt, bool do_chk) {
+  for (size_t gidx = 0; gidx < p->groups.size(); ++gidx) {
+    const DevGroup& dg = p->groups[gidx];
+    Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
+    a.pred = P_ALL;
+    if (dg.ndim == 3) {
+      set_tw<float>(a, p->tb, dg.Ny);
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+      launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
+      a.sel_in = S_CUR;
+    } else {
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+    }
+    tabs_x<float>(p, a, dg);
+    a.mode = M_CLIP | (smask ? M_RECORD : 0) | (ckpt ? M_CKPT : 0);
+    a.mask = smask ? smask + p->bw_pxoff[gidx] : nullptr;
+    a.mask_thr = px_mask_thr(dg);
+    a.ckpt = ckpt;
+    a.ckpt_every = p->bw_m;
+    launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+    if (!do_chk) continue;
+    a.sel_in = a.sel_out = S_CUR;
+    a.mask = nullptr;
+    a.ckpt = nullptr;
+    if (dg.ndim == 3) {
+      set_tw<float>(a, p->tb, dg.Ny);
+      a.mode = 0;
+      launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
+    }
+    set_tw<float>(a, p->tb, dg.Nz);
+    a.mode = M_CLIP | (fmask ? M_RECORD : 0);
+    a.mask = fmask ? fmask + p->bw_chkoff[gidx] : nullptr;
+    a.mask_thr = chk_mask_thr(dg);
+    launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
   }
-  set_tw<float>(a, p->tb, dg.Nz);
-  a.mode = M_CLIP | (fmask ? M_RECORD : 0);
-  a.mask = fmask;
-  launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+}
+
+void replay_entry(ffcz_plan_s* p, LoopBufs B, float* e0, uint32_t* fmask) {
+  for (size_t gidx = 0; gidx < p->groups.size(); ++gidx) {
+    const DevGroup& dg = p->groups[gidx];
+    Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
+    a.pred = P_ALL;
+    tabs_x<float>(p, a, dg);
+    a.e = e0;
+    a.mode = 0;
+    launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+    if (dg.ndim == 3) {
+      set_tw<float>(a, p->tb, dg.Ny);
+      launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
+    }
+    set_tw<float>(a, p->tb, dg.Nz);
+    a.mode = M_CLIP | (fmask ? M_RECORD : 0);
+    a.mask = fmask ? fmask + p->bw_chkoff[gidx] : nullptr;
+    a.mask_thr = chk_mask_thr(dg);
+    launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
+  }
 }
 
 // Plan checks shared by the differentiable entry points.
 void bw_check(ffcz_plan_s* p) {
-  if (p->batch != 1) fail(FFCZ_ERR_UNSUPPORTED, "backward needs a single-item plan");
   if (p->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "backward supports 2D and 3D items");
   if (p->opts.pointwise) fail(FFCZ_ERR_INVALID, "backward uses scalar bounds");
   if (p->opts.method != PV_POCS) fail(FFCZ_ERR_UNSUPPORTED, "backward differentiates Alg. 1 (method 0)");
@@ -2213,15 +2379,24 @@ void bw_check(ffcz_plan_s* p) {
 }
 
 // Workspace of the backward (checkpoints, masks, adjoint buffers), sized
-// for the plan's K and ckpt_every.
+// for the plan's K and ckpt_every: per step one block of x-pass masks and
+// one of check-pass masks, the groups' members back to back in each.
 void bw_alloc(ffcz_plan_s* p) {
   const int K = p->opts.K, m = p->opts.ckpt_every;
-  const DevGroup& dg = p->groups[0];
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
   if (p->bw_K != K || p->bw_m != m) {
-    p->px_words = x_words(dg.M, dg.rows, dg.wx);
-    p->chk_words = chkw(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc);
+    p->bw_pxoff.clear();
+    p->bw_chkoff.clear();
+    int64_t px = 0, ck = 0;
+    for (const DevGroup& dg : p->groups) {
+      p->bw_pxoff.push_back(px);
+      p->bw_chkoff.push_back(ck);
+      px += x_words(dg.M, dg.rows, dg.wx) * dg.count;
+      ck += chkw(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc) * dg.count;
+    }
+    p->px_words = px;
+    p->chk_words = ck;
     p->bw_e = (float*)dalloc(p, sizeof(float) * N);
     p->bw_ck = (float*)dalloc(p, sizeof(float) * N * nseg);
     p->bw_smask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->px_words * m);
@@ -2243,7 +2418,8 @@ __global__ void k_premask_ck(float* g, const float* e0, const float* ck0, int64_
 }
 
 // ckpt_in: checkpoints written by ffcz_correct_ckpt (null: the forward is run
-// again here to take them).
+// again here to take them).  Every item runs exactly K steps, so all items
+// (any number of shape groups) go through the segments together.
 ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, float* gin,
                           const double* eps_s, const double* eps_f, const float* ckpt_in = nullptr) {
   bw_check(p);
@@ -2251,7 +2427,6 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
   const int K = p->opts.K, m = p->opts.ckpt_every;
   CK(cudaSetDevice(p->device));
   ProfOn prof_on(p);
-  const DevGroup& dg = p->groups[0];
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
   bw_alloc(p);
@@ -2260,7 +2435,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
   LoopBufs GB{p->bw_G[0], p->bw_G[1]};
   // Forward with checkpoints of e_t at t = 0, m, 2m, ... (t < K).
   CK(cudaMemsetAsync(p->d_nactive, 0, sizeof(int), p->stream));
-  k_init<<<1, 32, 0, p->stream>>>(p->d_st, 1, 0, p->d_nactive);
+  k_init<<<(unsigned)((p->batch + 255) / 256), 256, 0, p->stream>>>(p->d_st, (int)p->batch, 0, p->d_nactive);
   g_launches++;
   const float* ck = ckpt_in ? ckpt_in : p->bw_ck;
   if (!ckpt_in) {
@@ -2271,7 +2446,7 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     const int last_ck = (nseg - 1) * m;
     for (int t = 1; t <= last_ck; ++t) {
       // k_decide after entry set t = 1 (forced iterations never stop early)
-      replay_body(p, dg, B, nullptr, nullptr, p->bw_ck, t < last_ck);
+      replay_body(p, B, nullptr, nullptr, p->bw_ck, t < last_ck);
       if (t < last_ck) advance(p, p->d_st);
     }
   }
@@ -2282,74 +2457,86 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     const int t0 = seg * m, t1 = std::min(K, t0 + m);
     // replay the segment from its checkpoint, recording masks of steps t0..t1-1
     set_t(p, p->d_st, t0);
-    replay_entry(p, dg, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
+    replay_entry(p, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
     for (int b = t0 + 1; b <= t1; ++b) {
       advance(p, p->d_st);
-      replay_body(p, dg, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
-                  b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr,
-                  b < t1);
+      replay_body(p, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
+                  b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr, b < t1);
     }
     for (int t = t1 - 1; t >= t0; --t) {
       uint32_t* sm = p->bw_smask + (int64_t)(t - t0) * p->px_words;
       uint32_t* fm = p->bw_fmask + (int64_t)(t - t0) * p->chk_words;
-      Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
-      a.pred = P_ALL;
-      if (first) {
-        tabs_x<float>(p, a, dg);
-        a.ein = gout;
-        a.e = const_cast<float*>(gout);
-        a.mask = sm;
-        a.mode = M_MASK;
-        launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, 1, p->stream);
-        first = false;
-      } else {
-        advance(p, p->d_st2);
+      if (!first) advance(p, p->d_st2);
+      for (size_t gidx = 0; gidx < p->groups.size(); ++gidx) {
+        const DevGroup& dg = p->groups[gidx];
+        Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
+        a.pred = P_ALL;
+        a.mask_thr = px_mask_thr(dg);
+        if (first) {
+          tabs_x<float>(p, a, dg);
+          a.ein = gout;
+          a.e = const_cast<float*>(gout);
+          a.mask = sm + p->bw_pxoff[gidx];
+          a.mode = M_MASK;
+          launch_x<float>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+        } else {
+          if (dg.ndim == 3) {
+            set_tw<float>(a, p->tb, dg.Ny);
+            a.sel_in = S_PREV; a.sel_out = S_CUR;
+            launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
+            a.sel_in = S_CUR;
+          } else {
+            a.sel_in = S_PREV; a.sel_out = S_CUR;
+          }
+          tabs_x<float>(p, a, dg);
+          a.mask = sm + p->bw_pxoff[gidx];
+          a.mode = M_MASK;
+          launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+        }
+        a.sel_in = a.sel_out = S_CUR;
         if (dg.ndim == 3) {
           set_tw<float>(a, p->tb, dg.Ny);
-          a.sel_in = S_PREV; a.sel_out = S_CUR;
-          launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
-          a.sel_in = S_CUR;
-        } else {
-          a.sel_in = S_PREV; a.sel_out = S_CUR;
+          a.mode = 0;
+          a.mask = nullptr;
+          launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
         }
-        tabs_x<float>(p, a, dg);
-        a.mask = sm;
+        set_tw<float>(a, p->tb, dg.Nz);
         a.mode = M_MASK;
-        launch_x<float>(XPX, dg.M, dg.wx, a, dg.rows, 1, p->stream);
+        a.mask = fm + p->bw_chkoff[gidx];
+        a.mask_thr = chk_mask_thr(dg);
+        launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, p->stream);
       }
-      a.sel_in = a.sel_out = S_CUR;
-      if (dg.ndim == 3) {
-        set_tw<float>(a, p->tb, dg.Ny);
-        a.mode = 0;
-        a.mask = nullptr;
-        launch_axis<float, -1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
-      }
-      set_tw<float>(a, p->tb, dg.Nz);
-      a.mode = M_MASK;
-      a.mask = fm;
-      launch_chk<float>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, 1, p->stream);
+      first = false;
     }
   }
   // exit: inverse of the last step's spectrum, no clip
-  {
-    advance(p, p->d_st2);
+  advance(p, p->d_st2);
+  for (const DevGroup& dg : p->groups) {
     Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
     a.pred = P_ALL;
     a.e = gin;
     if (dg.ndim == 3) {
       set_tw<float>(a, p->tb, dg.Ny);
       a.sel_in = S_PREV; a.sel_out = S_CUR;
-      launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, 1, p->stream);
+      launch_axis<float, +1>(dg.Ny, dg.wa, a, dg.Nz, dg.M, dg.count, p->stream);
       a.sel_in = S_CUR;
     } else {
       a.sel_in = S_PREV;
     }
     tabs_x<float>(p, a, dg);
     a.mode = 0;
-    launch_x<float>(XEXIT, dg.M, dg.wx, a, dg.rows, 1, p->stream);
-    if (ckpt_in) k_premask_ck<<<1184, 256, 0, p->stream>>>(gin, e0, ckpt_in, N);
-    else k_premask<<<1184, 256, 0, p->stream>>>(gin, e0, p->d_prm, p->d_st, 0, N);
+    launch_x<float>(XEXIT, dg.M, dg.wx, a, dg.rows, dg.count, p->stream);
+  }
+  if (ckpt_in) {
+    k_premask_ck<<<1184, 256, 0, p->stream>>>(gin, e0, ckpt_in, N);
     g_launches++;
+  } else {
+    for (int64_t i = 0; i < p->batch; ++i) {
+      const int64_t n = p->h_prm[i].n;
+      k_premask<<<(unsigned)std::min<int64_t>(1184, (n + 255) / 256), 256, 0, p->stream>>>(
+          gin + p->eoff[i], e0 + p->eoff[i], p->d_prm, p->d_st, (int)i, n);
+      g_launches++;
+    }
   }
   CK(cudaStreamSynchronize(p->stream));
   CK(cudaGetLastError());
@@ -2723,9 +2910,8 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (!(o.shrink >= 0.0 && o.shrink < 0.5)) fail(FFCZ_ERR_INVALID, "shrink must be in [0, 0.5)");
     if (o.max_iters < 0 || o.min_iters < 0) fail(FFCZ_ERR_INVALID, "iteration limits must be >= 0");
     if (o.method < PV_POCS || o.method > PV_ADMM) fail(FFCZ_ERR_INVALID, "method must be 0..3");
-    if (o.method != PV_POCS && (ndim == 1 || o.edits || o.pointwise || o.precision != 32))
-      fail(FFCZ_ERR_UNSUPPORTED, "projection variants run float32 loops on 2D/3D items without "
-                                 "edits or pointwise bounds");
+    if (o.method != PV_POCS && (o.edits || o.pointwise || o.precision != 32))
+      fail(FFCZ_ERR_UNSUPPORTED, "projection variants run float32 loops without edits or pointwise bounds");
     for (int64_t i = 0; i < batch; ++i) {
       if (ndim == 1) {
         const int64_t n = shapes[i];
@@ -2974,7 +3160,6 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     p->d_st2 = (ItemState*)dalloc(p.get(), sizeof(ItemState) * batch);
     p->d_nactive = (int*)dalloc(p.get(), sizeof(int));
     p->d_err = (int*)dalloc(p.get(), sizeof(int));
-    if (p->opts.edits && ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edit recording supports 2D and 3D items");
     {
       // per item: points, half-spectrum bins, and the offsets of the edit
       // arrays (1D items: bins of the layout of pointwise frequency bounds)
@@ -3094,7 +3279,6 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
                              const uint8_t* f_flags, const int32_t* f_codes) {
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
-    if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "edits exist for 2D and 3D items");
     if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "edit codes are relative to scalar bounds");
     if (!xhat_dev || !eps_s || !eps_f || !s_flags || !s_codes || !f_flags || !f_codes)
       fail(FFCZ_ERR_INVALID, "null pointer argument");
@@ -3102,6 +3286,39 @@ ffcz_status ffcz_apply_edits(ffcz_plan_t plan, float* xhat_dev, const double* ep
     CK(cudaSetDevice(plan->device));
     upload_params(plan, eps_s, eps_f, 0, 0);
     apply_edits(plan, xhat_dev, m_bits, s_flags, s_codes, f_flags, f_codes);
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_edits_compact16(ffcz_plan_t plan, int m_bits, uint8_t* s_flags, int16_t* s_codes,
+                                 int32_t* s_wide, uint8_t* f_flags, int16_t* f_codes, int32_t* f_wide,
+                                 int64_t* counts) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (!plan->opts.edits) fail(FFCZ_ERR_INVALID, "the plan was created without opts.edits");
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "edit codes are relative to scalar bounds");
+    if (m_bits < 2 || m_bits > 16) fail(FFCZ_ERR_INVALID, "m_bits must be in [2, 16]");
+    if (!s_flags || !s_codes || !s_wide || !f_flags || !f_codes || !f_wide) fail(FFCZ_ERR_INVALID, "null edit array");
+    CK(cudaSetDevice(plan->device));
+    edits_compact16(plan, m_bits, s_flags, s_codes, s_wide, f_flags, f_codes, f_wide, counts);
+    return FFCZ_OK;
+  });
+}
+
+ffcz_status ffcz_apply_edits16(ffcz_plan_t plan, float* xhat_dev, const double* eps_s, const double* eps_f,
+                               int m_bits, const uint8_t* s_flags, const int16_t* s_codes, const int32_t* s_wide,
+                               const uint8_t* f_flags, const int16_t* f_codes, const int32_t* f_wide,
+                               const int64_t* counts) {
+  if (!plan) return FFCZ_ERR_INVALID;
+  return guarded([&]() -> ffcz_status {
+    if (plan->opts.pointwise) fail(FFCZ_ERR_INVALID, "edit codes are relative to scalar bounds");
+    if (!xhat_dev || !eps_s || !eps_f || !s_flags || !s_codes || !s_wide || !f_flags || !f_codes || !f_wide ||
+        !counts)
+      fail(FFCZ_ERR_INVALID, "null pointer argument");
+    if (m_bits < 2 || m_bits > 16) fail(FFCZ_ERR_INVALID, "m_bits must be in [2, 16]");
+    CK(cudaSetDevice(plan->device));
+    upload_params(plan, eps_s, eps_f, 0, 0);
+    apply_edits16(plan, xhat_dev, m_bits, s_flags, s_codes, s_wide, f_flags, f_codes, f_wide, counts);
     return FFCZ_OK;
   });
 }

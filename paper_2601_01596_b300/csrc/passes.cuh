@@ -98,7 +98,9 @@ struct Args {
   float* e;                // spatial float32 buffer (in or out)
   const float* ein;        // separate float32 input (adjoint entry)
   uint32_t* mask;          // mask words (one per thread per pass)
+  int64_t mask_thr;        // mask threads per group member (member gi's words start at gi mask_thr MW)
   float* ckpt;             // checkpoint buffer for e_t
+  int64_t ckpt_stride;     // floats per checkpoint (all items of the plan)
   int ckpt_every;
   int pred, sel_in, sel_out, mode;
   const void* tw;          // Stockham stage factors for the pass length
@@ -392,6 +394,43 @@ __device__ __forceinline__ T from_f32(float f) {
   else return f;
 }
 
+// The partner exchange of the R2C post- and C2R pre-processing without the
+// tile buffer, for float32 tiles inside one warp: thread j of a pencil holds
+// element j + NT u in v[u], and the partner M - k of k = j + NT u is element
+// V - 1 - u of thread (NT - j) mod NT, or for j = 0 its own element
+// (V - u) mod V.  The pairs (u, V - 1 - u) are exchanged together by
+// register shuffles (half the shared-memory traffic of a store and a load),
+// and f(k, x_k, x_{M-k}) gives the new value of element k.  Requires the
+// tile's thread order tid = j W + w.
+template <typename T, int M, class TL, class Fn>
+__device__ __forceinline__ void pair_shfl(v2<T> (&v)[F2<M>::V], int j, Fn f) {
+  constexpr int NT = F2<M>::NT, V = F2<M>::V, W = TL::W;
+  static_assert(TL::TPT <= 32 && sizeof(T) == 4, "one-warp float32 tiles");
+  const int lane = (int)(threadIdx.x & 31u);
+  const int src = lane + (((NT - j) & (NT - 1)) - j) * W;
+  const bool self = j == 0;
+  v2<T> keep = v[0];   // thread j = 0: the previous step's element V - u, before its update
+#pragma unroll
+  for (int u = 0; u < V / 2; ++u) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int i = V - 1 - u;
+    v2<T> mu, mi;   // x_{M-k} for k = j + NT u and for k = j + NT i
+    mu.x = __shfl_sync(FULL, v[i].x, src);
+    mu.y = __shfl_sync(FULL, v[i].y, src);
+    mi.x = __shfl_sync(FULL, v[u].x, src);
+    mi.y = __shfl_sync(FULL, v[u].y, src);
+    if (self) {
+      mu = keep;
+      mi = v[u + 1];
+    }
+    keep = v[i];
+    const v2<T> nu = f(j + NT * u, v[u], mu);
+    const v2<T> ni = f(j + NT * i, v[i], mi);
+    v[u] = nu;
+    v[i] = ni;
+  }
+}
+
 // Post-processing of Z = FFT_M(z) into the packed half spectrum P (in place
 // in registers).  Each k needs Z[M-k], which another thread holds; it is
 // read through one exchange in natural order (a warp barrier only, when the
@@ -402,6 +441,16 @@ template <typename T, int M, class TL, bool HALF = true>
 __device__ __forceinline__ void r2c_post(v2<T> (&v)[F2<M>::V], int j, TL& tl,
                                          const v2<T>* __restrict__ twr) {
   constexpr int NT = F2<M>::NT, V = F2<M>::V;
+  if constexpr (HALF && sizeof(T) == 4 && TL::TPT <= 32) {
+    pair_shfl<T, M, TL>(v, j, [&](int k, v2<T> zk, v2<T> zm) {
+      if (k == 0) return mk<T>(zk.x + zk.y, zk.x - zk.y);
+      const v2<T> w = twr[k];
+      const T ax = zk.x + zm.x, ay = zk.y - zm.y, bx = zk.x - zm.x, by = zk.y + zm.y;
+      const T rx = fmaT(w.x, by, fmaT(w.y, bx, ax)), ry = fmaT(-w.x, bx, fmaT(w.y, by, ay));
+      return mk<T>(T(0.5) * rx, T(0.5) * ry);
+    });
+    return;
+  }
   store_nat<T, M, TL>(v, j, tl);
   if constexpr (!HALF) {
     // Paired form (certification): X(k) and X(M-k) share A, B and the
@@ -466,6 +515,15 @@ template <typename T, int M, class TL>
 __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
                                         const v2<T>* __restrict__ twr) {
   constexpr int NT = F2<M>::NT, V = F2<M>::V;
+  if constexpr (sizeof(T) == 4 && TL::TPT <= 32) {
+    pair_shfl<T, M, TL>(v, j, [&](int k, v2<T> xk, v2<T> xm) {
+      if (k == 0) return mk<T>(xk.x + xk.y, xk.x - xk.y);
+      const v2<T> w = twr[k];
+      const T ax = xk.x + xm.x, ay = xk.y - xm.y, bx = xk.x - xm.x, by = xk.y + xm.y;
+      return mk<T>(fmaT(-w.x, by, fmaT(w.y, bx, ax)), fmaT(w.x, bx, fmaT(w.y, by, ay)));
+    });
+    return;
+  }
   store_nat<T, M, TL>(v, j, tl);
 #pragma unroll
   for (int u = 0; u < V; ++u) {
@@ -506,7 +564,7 @@ __device__ __forceinline__ void c2r_pre(v2<T> (&v)[F2<M>::V], int j, TL& tl,
   const int64_t prow = (int64_t)tile * G_::W + w;                                 \
   const bool live = prow < a.g.rows;                                              \
   const int64_t row = live ? prow : 0;                                            \
-  const int64_t mthr = (int64_t)tile * G_::TPT + tid;                             \
+  const int64_t mthr = (int64_t)gi * a.mask_thr + (int64_t)tile * G_::TPT + tid;  \
   TL tl{s_tiles + g * TL::ELEMS + w, false};                                      \
   (void)t_it; (void)mthr;
 
@@ -608,7 +666,7 @@ __device__ __forceinline__ void s_clip_full(v2<T> (&v)[V], T Es, bool count, Mas
 template <typename T, int M, class TL, bool PW = false, bool ED = true, int PV = PV_POCS>
 __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemParams& p, v2<T> (&v)[F2<M>::V],
                                                       int j, int64_t mthr, int64_t row, bool live,
-                                                      int t_it, TL& tl, const v2<T>* twg,
+                                                      int t_it, int64_t eoff, TL& tl, const v2<T>* twg,
                                                       const v2<T>* twr, float2* edrow = nullptr,
                                                       const float2* ebrow = nullptr,
                                                       const float2* qin = nullptr, float2* qout = nullptr,
@@ -687,7 +745,8 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
     // checkpoints of e_t for t = 0, m, 2m, ... below the item's K
     const bool ckn = (a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 &&
                      t_it < p.max_iters && live;
-    float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * (2 * M * a.g.rows)) + row * M
+    float2* ck = ckn ? reinterpret_cast<float2*>(a.ckpt + (int64_t)(t_it / a.ckpt_every) * a.ckpt_stride + eoff) +
+                           row * M
                      : nullptr;
     MaskBits<MW> mb;
     mb.clear();
@@ -728,8 +787,8 @@ __device__ __forceinline__ void k_px_body(const Args& a, const int bx_, const in
     qout = reinterpret_cast<float2*>(a.pv_q[t_it & 1] + a.g.eoff[gi]) + row * M;
   }
   AbsMax<T> svm;
-  unsigned long long cnt = px_core<T, M, TL, PW, FULL, PV>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr,
-                                                           edrow, ebrow, qin, qout, &svm);
+  unsigned long long cnt = px_core<T, M, TL, PW, FULL, PV>(a, p, v, j, mthr, row, live, t_it, a.g.eoff[gi], tl,
+                                                           s_tw, s_twr, edrow, ebrow, qin, qout, &svm);
   if (live) {
     v2<T>* out = pick<T>(a, a.sel_out, t_it) + a.g.soff[gi] + row * M;
 #pragma unroll
@@ -857,7 +916,7 @@ k_xexit(Args a) {
   const int g = threadIdx.x / G_::TPT, tid = threadIdx.x % G_::TPT;              \
   const int w = tid % G_::W, j = tid / G_::W;                                     \
   const int tile = a.tile0 + bx_ * G_::G + g;                                     \
-  const int64_t mthr = (int64_t)tile * G_::TPT + tid;                             \
+  const int64_t mthr = (int64_t)gi * a.mask_thr + (int64_t)tile * G_::TPT + tid;  \
   TL tl{s_tiles + g * TL::ELEMS + w, false};                                      \
   (void)mthr;
 
@@ -1439,7 +1498,7 @@ k_chk_tma(Args a) {
       for (int u = 0; u < V; ++u) v[u] = in[(int64_t)u * NT * estride];
     }
     TL tl{s_tiles + w, false};
-    const int64_t mthr = (int64_t)tile * G_::TPT + tid;
+    const int64_t mthr = (int64_t)gi * a.mask_thr + (int64_t)tile * G_::TPT + tid;
     const float2* pwb = nullptr;
     int64_t pws = 0;
     const bool main_tile = tile < nmain;
@@ -1490,14 +1549,35 @@ k_chk_tma(Args a) {
 // are one contiguous block of the packed spectrum, loaded by a single
 // cp.async.bulk while the previous block is transformed.  Shared memory:
 // [staging G W M][G tile buffers][twiddles][R2C twiddles][reduction].
+// The staged rows are RS = M + PAD values apart: the PAD (16 / W values, an
+// even count, so every row starts on a 16-byte boundary) puts the W rows a
+// half-warp reads at once in different banks.
 template <int M, int W>
 struct PxTmaGeo {
   using G_ = Geo<float, M, W>;
   static constexpr int RG = G_::G * W;                     // rows per block
-  static constexpr size_t stage = (size_t)RG * M * sizeof(float2);
+  static constexpr int PAD = (W >= 2 && W <= 8) ? 16 / W : 0;
+  static constexpr int RS = M + PAD;                       // staged row stride
+  static constexpr size_t stage = (size_t)RG * RS * sizeof(float2);
   static constexpr size_t bytes = 128 + stage + (size_t)G_::G * Tile<float, M, W>::ELEMS * sizeof(float2) +
                                   2 * (size_t)M * sizeof(float2) + 32 * 8 * 3 + 32 * 4;
 };
+
+// One block of rows r0 .. r0 + RG - 1 (fewer at the end) into the staging
+// buffer at row stride RS: one bulk copy per row when the rows are padded.
+template <int M, int W>
+__device__ __forceinline__ void px_stage_rows(float2* s_stage, const float2* inb, int64_t r0, int64_t rows,
+                                              uint64_t* bar) {
+  using PG = PxTmaGeo<M, W>;
+  const int64_t nr = rows - r0 < PG::RG ? rows - r0 : PG::RG;
+  const uint32_t rb = (uint32_t)(M * sizeof(float2));
+  mbar_arrive_expect_tx(bar, (uint32_t)nr * rb);
+  if constexpr (PG::PAD == 0) {
+    bulk_load(s_stage, inb + r0 * M, (uint32_t)nr * rb, bar);
+  } else {
+    for (int r = 0; r < (int)nr; ++r) bulk_load(s_stage + r * PG::RS, inb + (r0 + r) * M, rb, bar);
+  }
+}
 
 template <int M, int W, bool ED = false, bool PW = false, int PV = PV_POCS>
 __global__ void __launch_bounds__(Geo<float, M, W>::NTHR,
@@ -1510,7 +1590,7 @@ k_px_tma(Args a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const uint32_t s0 = smem_addr(smraw);   // staging rounded up to 128 bytes
   float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0 + 127u) & ~127u) - s0));
-  float2* s_tiles = s_stage + RG * M;
+  float2* s_tiles = s_stage + RG * PG::RS;
   float2* s_tw = s_tiles + G_::G * TL::ELEMS;
   float2* s_twr = s_tw + M;
   unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M);
@@ -1535,13 +1615,7 @@ k_px_tma(Args a) {
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t parity = 0;
-  auto issue = [&](int64_t blk) {
-    const int64_t r0 = blk * RG;
-    const int64_t nr = rows - r0 < RG ? rows - r0 : RG;
-    const uint32_t bytes = (uint32_t)(nr * M * sizeof(float2));
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_load(s_stage, inb + r0 * M, bytes, &bar);
-  };
+  auto issue = [&](int64_t blk) { px_stage_rows<M, W>(s_stage, inb, blk * RG, rows, &bar); };
   int64_t blk = blockIdx.x;
   if (threadIdx.x == 0 && blk < nblk) issue(blk);
   unsigned long long cnt = 0;
@@ -1556,7 +1630,7 @@ k_px_tma(Args a) {
     }
     float2 v[V];
 #pragma unroll
-    for (int u = 0; u < V; ++u) v[u] = s_stage[(g * W + w) * M + j + u * NT];
+    for (int u = 0; u < V; ++u) v[u] = s_stage[(g * W + w) * PG::RS + j + u * NT];
     __syncthreads();
     if (threadIdx.x == 0 && next < nblk) {
       fence_proxy_async_smem();
@@ -1567,7 +1641,7 @@ k_px_tma(Args a) {
     const int64_t prow = (int64_t)tile * W + w;
     const bool live = prow < rows;
     const int64_t row = live ? prow : 0;
-    const int64_t mthr = (int64_t)tile * G_::TPT + tid;
+    const int64_t mthr = (int64_t)gi * a.mask_thr + (int64_t)tile * G_::TPT + tid;
     TL tl{s_tiles + g * TL::ELEMS + w, false};
     float2* edrow = a.ed_s ? reinterpret_cast<float2*>(a.ed_s + a.g.eoff[gi]) + row * M : nullptr;
     const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
@@ -1577,8 +1651,8 @@ k_px_tma(Args a) {
       qin = reinterpret_cast<const float2*>(a.pv_q[(t_it - 1) & 1] + a.g.eoff[gi]) + row * M;
       qout = reinterpret_cast<float2*>(a.pv_q[t_it & 1] + a.g.eoff[gi]) + row * M;
     }
-    cnt += px_core<float, M, TL, PW, ED, PV>(a, p, v, j, mthr, row, live, t_it, tl, s_tw, s_twr, edrow, ebrow,
-                                             qin, qout, &svm);
+    cnt += px_core<float, M, TL, PW, ED, PV>(a, p, v, j, mthr, row, live, t_it, a.g.eoff[gi], tl, s_tw, s_twr,
+                                             edrow, ebrow, qin, qout, &svm);
     if (live) {
       float2* out = outb + row * M;
 #pragma unroll
@@ -1610,6 +1684,30 @@ static __global__ void k_edits_finalize(Group g, const ItemState* st, float2* ed
   const int T = st[g.item[gi]].t;
   const int64_t base = g.soff[gi];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < slots_per_item;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int tg = ed_t[base + i];
+    if (tg == 0) continue;
+    if (tg - 1 == T) {
+      float2 f = ed_f[base + i];
+      const float2 q = ed_p[base + i];
+      f.x -= q.x;
+      f.y -= q.y;
+      ed_f[base + i] = f;
+    }
+    ed_t[base + i] = 0;
+    ed_p[base + i] = make_float2(0.f, 0.f);
+  }
+}
+
+// The same for 1D items, whose frequency edits are kept on their half
+// spectrum (bins k <= N/2 at the item's canonical offset).
+static __global__ void k_edits_finalize1(Group g, const ItemParams* prm, const ItemState* st, float2* ed_f,
+                                         float2* ed_p, int* ed_t) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const int T = st[item].t;
+  const int64_t base = g.coff[gi], slots = prm[item].n / 2 + 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < slots;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tg = ed_t[base + i];
     if (tg == 0) continue;
@@ -1729,7 +1827,7 @@ k_xfwd_tma(Args a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const uint32_t s0 = smem_addr(smraw);   // staging rounded up to 128 bytes
   float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0 + 127u) & ~127u) - s0));
-  float2* s_tiles = s_stage + RG * M;
+  float2* s_tiles = s_stage + RG * PG::RS;
   float2* s_tw = s_tiles + G_::G * TL::ELEMS;
   float2* s_twr = s_tw + M;
   unsigned long long* s_red = reinterpret_cast<unsigned long long*>(s_twr + M);
@@ -1754,13 +1852,7 @@ k_xfwd_tma(Args a) {
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t parity = 0;
-  auto issue = [&](int64_t blk) {
-    const int64_t r0 = blk * RG;
-    const int64_t nr = rows - r0 < RG ? rows - r0 : RG;
-    const uint32_t bytes = (uint32_t)(nr * M * sizeof(float2));
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_load(s_stage, inb + r0 * M, bytes, &bar);
-  };
+  auto issue = [&](int64_t blk) { px_stage_rows<M, W>(s_stage, inb, blk * RG, rows, &bar); };
   int64_t blk = blockIdx.x;
   if (threadIdx.x == 0 && blk < nblk) issue(blk);
   const bool measure = (a.mode & M_MEASURE) != 0;
@@ -1784,7 +1876,7 @@ k_xfwd_tma(Args a) {
     const float2* ebrow = PW ? reinterpret_cast<const float2*>(a.pw_e + a.g.eoff[gi]) + row * M : nullptr;
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-      v[u] = s_stage[(g * W + w) * M + j + u * NT];
+      v[u] = s_stage[(g * W + w) * PG::RS + j + u * NT];
       if (measure && live) {
         if constexpr (PW) {   // pointwise E_n: the maximum of |e_n| / E_n
           const float2 eb = ebrow[j + u * NT];
@@ -1837,7 +1929,7 @@ k_xexit_tma(Args a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const uint32_t s0 = smem_addr(smraw);   // staging rounded up to 128 bytes
   float2* s_stage = reinterpret_cast<float2*>(smraw + (((s0 + 127u) & ~127u) - s0));
-  float2* s_tiles = s_stage + RG * M;
+  float2* s_tiles = s_stage + RG * PG::RS;
   float2* s_tw = s_tiles + G_::G * TL::ELEMS;
   float2* s_twr = s_tw + M;
   __shared__ __align__(8) uint64_t bar;
@@ -1860,13 +1952,7 @@ k_xexit_tma(Args a) {
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t parity = 0;
-  auto issue = [&](int64_t blk) {
-    const int64_t r0 = blk * RG;
-    const int64_t nr = rows - r0 < RG ? rows - r0 : RG;
-    const uint32_t bytes = (uint32_t)(nr * M * sizeof(float2));
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_load(s_stage, inb + r0 * M, bytes, &bar);
-  };
+  auto issue = [&](int64_t blk) { px_stage_rows<M, W>(s_stage, inb, blk * RG, rows, &bar); };
   int64_t blk = blockIdx.x;
   if (threadIdx.x == 0 && blk < nblk) issue(blk);
   while (blk < nblk) {
@@ -1879,7 +1965,7 @@ k_xexit_tma(Args a) {
     }
     float2 v[V];
 #pragma unroll
-    for (int u = 0; u < V; ++u) v[u] = s_stage[(g * W + w) * M + j + u * NT];
+    for (int u = 0; u < V; ++u) v[u] = s_stage[(g * W + w) * PG::RS + j + u * NT];
     __syncthreads();
     if (threadIdx.x == 0 && next < nblk) {
       fence_proxy_async_smem();
@@ -2000,8 +2086,8 @@ static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, in
   }
   s.v64 = v;
   s.emax64 = emax;
-  s.bound64 = b;
-  s.certified = (emax <= p.E) && (v + b * p.bscale <= p.D);
+  s.bound64 = b * p.bscale;   // in the units of v (pointwise: relative to min Delta_k)
+  s.certified = (emax <= p.E) && (v + s.bound64 <= p.D);
   s.vbits = 0ull;
   s.emaxbits = 0ull;
   s.sumsq = 0.0;

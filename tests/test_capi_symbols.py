@@ -67,5 +67,5 @@ def test_projection_variant_options_are_checked_on_the_host():
     for kw in ({"method": 1, "edits": 1}, {"method": 2, "pointwise": 1}, {"method": 3, "precision": 64}):
         o = ffcz.default_opts(**kw)
         assert L.ffcz_plan(ctypes.byref(h), 3, sh3, 1, ctypes.byref(o), None) == ffcz.ERR_UNSUPPORTED, kw
-    o = ffcz.default_opts(method=1)
+    o = ffcz.default_opts(method=1, edits=1)   # 1D items: the same rules
     assert L.ffcz_plan(ctypes.byref(h), 1, sh1, 1, ctypes.byref(o), None) == ffcz.ERR_UNSUPPORTED

@@ -278,3 +278,66 @@ def test_autograd_interleaved_forwards_keep_their_own_checkpoints():
         (o * g).sum().backward()
     for e, ref in zip(e0s, single):
         assert torch.equal(e.grad, ref)
+
+
+@pytest.mark.parametrize("shapes,K,m", [([(16, 16, 32), (16, 32, 16), (16, 16, 32)], 5, 2),
+                                        ([(32, 64), (64, 32), (32, 32), (32, 64)], 6, 4)])
+@pytest.mark.parametrize("ckpt", [False, True])
+def test_batched_backward_equals_single_items_and_oracle(shapes, K, m, ckpt, monkeypatch):
+    """A batch of items of several shapes: each item's product is that of its
+    own single-item plan, bit for bit, and matches the oracle's VJP element
+    by element."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    monkeypatch.setenv("FFCZ_TUNE_FORCE", "split=0")
+    items, gs, Es, Ds = [], [], [], []
+    for i, sh in enumerate(shapes):
+        e0 = W.bimodal_error(sh, 60 + i, dtype=np.float32)
+        items.append(e0)
+        gs.append(np.random.default_rng(61 + i).standard_normal(sh).astype(np.float32))
+        Es.append(1.0 + 0.25 * i)
+        Ds.append((0.3 + 0.05 * i) * O.f_violation(O.dft(e0.astype(np.float64))))
+        items[-1] = (items[-1] * Es[-1]).astype(np.float32)
+    te0 = torch.from_numpy(np.concatenate([x.reshape(-1) for x in items])).cuda()
+    tg = torch.from_numpy(np.concatenate([x.reshape(-1) for x in gs])).cuda()
+    gi = torch.empty_like(te0)
+    if ckpt:
+        plan = ffcz.Plan(shapes, K=K, ckpt_every=m, min_iters=K, max_iters=K, certify=0)
+        ck = torch.empty(plan.ckpt_floats(), dtype=torch.float32, device="cuda")
+        plan.correct_ckpt(te0.clone(), Es, Ds, ck)
+        plan.backward(te0, tg, gi, Es, Ds, ckpt=ck)
+    else:
+        plan = ffcz.Plan(shapes, K=K, ckpt_every=m)
+        plan.backward(te0, tg, gi, Es, Ds)
+    got = gi.cpu().numpy()
+    off = 0
+    for i, sh in enumerate(shapes):
+        n = int(np.prod(sh))
+        one = _gpu_backward(sh, items[i], gs[i], Es[i], Ds[i], K, m, ckpt=ckpt)
+        assert np.array_equal(got[off:off + n].reshape(sh), one), (i, sh)
+        off += n
+    # the oracle once per distinct item (the repeated shape has its own data)
+    off = 0
+    for i, sh in enumerate(shapes):
+        n = int(np.prod(sh))
+        _assert_vjp_elementwise(got[off:off + n].reshape(sh), items[i], gs[i], Es[i], Ds[i], K,
+                                f"batch item {i} {sh}", samples=4)
+        off += n
+
+
+def test_batched_autograd_function_runs_and_matches_backward():
+    import torch
+    from paper_2601_01596_b300.autograd import correct_differentiable_batch
+    import paper_2601_01596_b300 as ffcz
+    shapes = [(16, 16, 32), (32, 16, 16)]
+    items = [W.bimodal_error(sh, 70 + i, dtype=np.float32) for i, sh in enumerate(shapes)]
+    Es = [1.0, 1.0]
+    Ds = [0.4 * O.f_violation(O.dft(x.astype(np.float64))) for x in items]
+    e0 = torch.from_numpy(np.concatenate([x.reshape(-1) for x in items])).cuda().requires_grad_(True)
+    e = correct_differentiable_batch(e0, shapes, Es, Ds, K=4, ckpt_every=2)
+    w = torch.from_numpy(np.random.default_rng(71).standard_normal(e.numel()).astype(np.float32)).cuda()
+    (e * w).sum().backward()
+    plan = ffcz.Plan(shapes, K=4, ckpt_every=2)
+    gi = torch.empty_like(e0)
+    plan.backward(e0.detach(), w, gi, Es, Ds)
+    assert torch.equal(e0.grad, gi)

@@ -44,7 +44,8 @@ def split(plan, S, F, shapes):
     return out
 
 
-@pytest.mark.parametrize("shape,k", [((32, 32, 32), 3), ((64, 128), 4), ((16, 32, 64), 2)])
+@pytest.mark.parametrize("shape,k", [((32, 32, 32), 3), ((64, 128), 4), ((16, 32, 64), 2), ((3000,), 3),
+                                     ((1500,), 4)])
 def test_forced_iterations_edits_match_oracle(shape, k):
     e0, E, D = stress(shape, 70)
     ref = O.correct(e0, E, D, min_iters=k, max_iters=k, edits=True)
@@ -60,7 +61,7 @@ def test_forced_iterations_edits_match_oracle(shape, k):
     np.testing.assert_allclose(e.reshape(shape) - e0, disp, rtol=0, atol=1e-4 * E)
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (256, 64)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (256, 64), (3000,), (9000,)])
 def test_converged_run_drops_the_stopping_clip(shape):
     e0, E, D = stress(shape, 71)
     plan, e, st, S, F = run([e0], [E], [D])
@@ -106,6 +107,40 @@ def test_compaction_bit_exact_against_oracle_quantizer():
             np.testing.assert_array_equal(fc[fco:fco + 2 * comp.size].reshape(-1, 2), want)
 
 
+def test_preclip_recorded_as_spatial_edit_1d():
+    e0, E, D = stress((3000,), 74)
+    e0 = e0.copy(); e0[17] = 1.75; e0[2900] = -2.5
+    plan, e, st, S, F = run([e0], [E], [D])
+    assert st[0]["preclipped"] == 1
+    (Sg, Fg), = split(plan, S, F, [(3000,)])
+    assert Sg[17] != 0 and Sg[2900] != 0
+    disp = Sg.astype(np.float64) + np.fft.irfft(Fg.astype(np.complex128), n=3000)
+    np.testing.assert_allclose(e - e0, disp, rtol=0, atol=1e-4 * E)
+
+
+def test_compaction_bit_exact_against_oracle_quantizer_1d():
+    shapes = [(3000,), (1500,), (9000,)]
+    items, Es, Ds = [], [], []
+    for i, sh in enumerate(shapes):
+        e0, E, D = stress(sh, 75 + i)
+        items.append(e0); Es.append(E); Ds.append(D)
+    plan, e, st, S, F = run(items, Es, Ds)
+    c = plan.edits_compact(16)
+    sf, sc = c["s_flags"].cpu().numpy(), c["s_codes"].cpu().numpy()
+    ff, fc = c["f_flags"].cpu().numpy(), c["f_codes"].cpu().numpy()
+    for i, (Sg, Fg) in enumerate(split(plan, S, F, shapes)):
+        npt, nb, so, sco, fo, fco = plan.edit_layout(i)
+        assert (npt, nb) == (shapes[i][0], shapes[i][0] // 2 + 1)
+        flags, comp = O.compact_edits(Sg)
+        np.testing.assert_array_equal(sf[so:so + flags.size], flags)
+        np.testing.assert_array_equal(sc[sco:sco + comp.size],
+                                      O.quantize_edits(comp.astype(np.float32), Es[i], 16, dtype=np.float32))
+        flags, comp = O.compact_edits(Fg)
+        np.testing.assert_array_equal(ff[fo:fo + flags.size], flags)
+        np.testing.assert_array_equal(fc[fco:fco + 2 * comp.size].reshape(-1, 2),
+                                      O.quantize_edits(comp.astype(np.complex64), Ds[i], 16, dtype=np.float32))
+
+
 def test_edits_off_by_default_and_plan_without_edits_refuses():
     import paper_2601_01596_b300 as ffcz
     plan = ffcz.Plan([(32, 32)])
@@ -116,7 +151,8 @@ def test_edits_off_by_default_and_plan_without_edits_refuses():
         plan.edits_compact()
 
 
-@pytest.mark.parametrize("shapes", [[(32, 32, 32)], [(64, 128), (32, 256)], [(16, 32, 64), (16, 32, 64)]])
+@pytest.mark.parametrize("shapes", [[(32, 32, 32)], [(64, 128), (32, 256)], [(16, 32, 64), (16, 32, 64)],
+                                    [(3000,), (1500,), (9000,)]])
 def test_apply_edits_matches_oracle_application(shapes):
     """Decompression side: x_hat + S~ + IFFT(F~) from the stored codes, GPU vs
     the oracle's apply_edits on the same dequantized edits."""
@@ -154,7 +190,8 @@ def test_apply_edits_matches_oracle_application(shapes):
         off += npt
 
 
-@pytest.mark.parametrize("shape,seed,frac", [((32, 32, 32), 3, 0.4), ((64, 128), 5, 0.4), ((16, 32, 64), 7, 0.2)])
+@pytest.mark.parametrize("shape,seed,frac", [((32, 32, 32), 3, 0.4), ((64, 128), 5, 0.4), ((16, 32, 64), 7, 0.2),
+                                            ((3000,), 9, 0.3)])
 def test_decompressed_field_certifies_with_the_doubled_shrink(shape, seed, frac):
     """Reading A21 on the library: corrected with shrink 2^(1-m), the field
     rebuilt from the stored m-bit edits (x_hat + S~ + IFFT(F~), here with
@@ -173,3 +210,67 @@ def test_decompressed_field_certifies_with_the_doubled_shrink(shape, seed, frac)
     plan.apply_edits(xhat, [E], [D], stored, m)
     chk = plan.check(xhat, [E], [D])[0]
     assert chk["certified"] == 1, chk
+
+
+@pytest.mark.parametrize("shapes", [[(32, 32, 32), (16, 32, 64)], [(64, 128), (32, 256)], [(3000,), (1500,)]])
+def test_16bit_codes_bit_exact_against_oracle_and_apply_equals_int32_form(shapes):
+    """Codes stored in 16 bits with escapes (Sec. IV-B, m = 16; reading A27):
+    int16 codes and escape lists equal the oracle's narrowing of the oracle
+    quantiser's codes, and applying the 16-bit form gives the same bits as
+    applying the int32 form."""
+    import torch
+    items, Es, Ds = [], [], []
+    for i, sh in enumerate(shapes):
+        e0, E, D = stress(sh, 90 + i, frac=0.2)
+        items.append(e0); Es.append(E); Ds.append(D)
+    plan, e, st, S, F = run(items, Es, Ds)
+    c16 = plan.edits_compact16(16)
+    c32 = plan.edits_compact(16)
+    sc, sw = c16["s_codes"].cpu().numpy(), c16["s_wide"].cpu().numpy()
+    fc, fw = c16["f_codes"].cpu().numpy(), c16["f_wide"].cpu().numpy()
+    np.testing.assert_array_equal(c16["s_flags"].cpu().numpy(), c32["s_flags"].cpu().numpy())
+    np.testing.assert_array_equal(c16["f_flags"].cpu().numpy(), c32["f_flags"].cpu().numpy())
+    n_esc = 0
+    for i, (Sg, Fg) in enumerate(split(plan, S, F, shapes)):
+        npt, nb, so, sco, fo, fco = plan.edit_layout(i)
+        _, comp = O.compact_edits(Sg)
+        want16, wantw = O.narrow_codes(O.quantize_edits(comp.astype(np.float32), Es[i], 16, dtype=np.float32))
+        assert tuple(c16["counts"][i, [0, 2]]) == (comp.size, wantw.size)
+        np.testing.assert_array_equal(sc[sco:sco + comp.size], want16)
+        np.testing.assert_array_equal(sw[sco:sco + wantw.size], wantw)
+        _, comp = O.compact_edits(Fg)
+        codes = O.quantize_edits(comp.astype(np.complex64), Ds[i], 16, dtype=np.float32).reshape(-1)
+        want16, wantw = O.narrow_codes(codes)
+        assert tuple(c16["counts"][i, [1, 3]]) == (comp.size, wantw.size)
+        np.testing.assert_array_equal(fc[fco:fco + codes.size], want16)
+        np.testing.assert_array_equal(fw[fco:fco + wantw.size], wantw)
+        n_esc += wantw.size
+    assert n_esc > 0   # the stress bounds make frequency edits larger than the bound
+    rng = np.random.default_rng(91)
+    xhat = np.concatenate([(rng.standard_normal(sh) + x).reshape(-1) for sh, x in zip(shapes, items)])
+    t16 = torch.from_numpy(xhat.astype(np.float32)).cuda()
+    t32 = t16.clone()
+    plan.apply_edits16(t16, Es, Ds, c16, 16)
+    plan.apply_edits(t32, Es, Ds, c32, 16)
+    assert torch.equal(t16, t32)
+
+
+def test_16bit_codes_refuse_bad_counts_and_m_bits():
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    e0, E, D = stress((32, 32), 95, frac=0.2)
+    plan, e, st, S, F = run([e0], [E], [D])
+    with pytest.raises(ffcz.FFCzError):
+        plan.edits_compact16(17)
+    c16 = plan.edits_compact16(16)
+    x = torch.zeros(32 * 32, dtype=torch.float32, device="cuda")
+    bad = dict(c16)
+    bad["counts"] = c16["counts"].copy()
+    bad["counts"][0, 3] += 1          # one escape more than the codes hold
+    with pytest.raises(ffcz.FFCzError):
+        plan.apply_edits16(x, [E], [D], bad, 16)
+    assert float(x.abs().max()) == 0.0   # nothing applied
+    bad["counts"] = c16["counts"].copy()
+    bad["counts"][0, 0] = 32 * 32 + 1   # more nonzero points than the item has
+    with pytest.raises(ffcz.FFCzError):
+        plan.apply_edits16(x, [E], [D], bad, 16)

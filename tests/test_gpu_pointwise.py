@@ -280,6 +280,7 @@ def test_certification_bound_of_uniform_pointwise_bounds_equals_scalar(shape):
     ts = torch.from_numpy(e0.reshape(-1).copy()).cuda()
     ss = ps.correct(ts, [E], [D])[0]
     assert spw["certified"] == ss["certified"] == 1
-    # the rounding bound is about 3e-13 D here; a norm bound taken from the
-    # ratio max|e_n|/E_n would shrink it about 75-fold
+    # the rounding bound is about 5e-13 D here; a norm bound taken from the
+    # ratio max|e_n|/E_n would shrink it about 75-fold, and one left unscaled
+    # by 1 / min Delta_k would be D times larger
     assert abs(spw["f_margin64"] - ss["f_margin64"]) <= 1e-14, (spw["f_margin64"], ss["f_margin64"])

@@ -37,7 +37,7 @@ def stress(shape, seed, frac=0.5):
 
 
 @pytest.mark.parametrize("method", METHODS)
-@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 32, 64), (64, 128)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 32, 64), (64, 128), (3000,), (1500,)])
 def test_forced_iterations_match_oracle(method, shape):
     e0, E, D = stress(shape, 3)
     for K in (1, 2, 3, 5, 10):
@@ -49,7 +49,7 @@ def test_forced_iterations_match_oracle(method, shape):
 
 
 @pytest.mark.parametrize("method", METHODS)
-@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 32, 64), (64, 128), (256, 32)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 32, 64), (64, 128), (256, 32), (3000,), (9000,)])
 def test_converged_matches_oracle_and_certifies(method, shape):
     e0, E, D = stress(shape, 5)
     ref = O.correct_method(e0, E, D, method)
@@ -99,6 +99,23 @@ def test_single_mode_closed_forms_on_gpu():
 
 
 @pytest.mark.parametrize("method", METHODS)
+def test_batch_of_uneven_1d_items_equals_singles(method):
+    shapes = [(3000,), (1500,), (3000,), (9000,)]
+    items = [stress(s, 30 + i)[0] for i, s in enumerate(shapes)]
+    Es = [1.0] * 4
+    Ds = [0.5 * O.f_violation(O.dft(x.astype(np.float64))) for x in items]
+    flat = np.concatenate([x.reshape(-1) for x in items])
+    e, st = run_gpu(flat, Es, Ds, shapes=shapes, method=method)
+    off = 0
+    for i, (x, s) in enumerate(zip(items, shapes)):
+        es, ss = run_gpu(x, Es[i], Ds[i], method=method)
+        n = x.size
+        assert st[i]["iters"] == ss[0]["iters"] and st[i]["certified"] == 1
+        assert np.array_equal(e[off:off + n], es.reshape(-1))
+        off += n
+
+
+@pytest.mark.parametrize("method", METHODS)
 def test_batch_of_uneven_items_equals_singles(method):
     shapes = [(32, 32, 32), (16, 32, 64), (32, 32, 32)]
     items = [stress(s, 20 + i)[0] for i, s in enumerate(shapes)]
@@ -119,7 +136,7 @@ def test_batch_of_uneven_items_equals_singles(method):
 def test_variant_option_checks():
     import paper_2601_01596_b300 as ffcz
     with pytest.raises(ffcz.FFCzError):
-        ffcz.Plan([(4096,)], method="dykstra")            # 1D items
+        ffcz.Plan([(4096,)], method="dykstra", edits=1)   # 1D items: the same rules
     with pytest.raises(ffcz.FFCzError):
         ffcz.Plan([(32, 32, 32)], method="dr", edits=1)
     with pytest.raises(ffcz.FFCzError):
