@@ -273,7 +273,8 @@ ffcz_status ffcz_correct_pw(ffcz_plan_t plan, float* e_dev, const float* eb_dev,
  *   x_dev  : device float32, the ORIGINAL fields (packed items).
  *   rho    : host, one relative bound > 0 per item.
  *   db_dev : device float32 pairs, output in the layout ffcz_correct_pw reads
- *            (Delta^Re = Delta^Im = d of the bin's shell).
+ *            (Delta^Re = Delta^Im = d of the bin's shell; 1D items: the
+ *            shell of bin k <= N/2 is k, the pair of bins k and N - k).
  * The transform runs in float32 on the plan's first spectrum buffer (not
  * concurrently with a ffcz_correct on the same plan); synchronises.
  */
@@ -356,10 +357,11 @@ ffcz_status ffcz_check(ffcz_plan_t plan, const float* e_dev, const double* eps_s
  *   e0_dev       : device float32 input of the forward (not modified)
  *   grad_out_dev : device float32 dL/de_K
  *   grad_in_dev  : device float32 output dL/de0 (may not alias the others)
- * All three packed like e (items back to back); eps_s / eps_f per item.  2D
- * and 3D plans of any batch and any mix of shapes: every item runs exactly
- * K steps, and each item's product is that of its own single-item plan.
- * 1D plans: UNSUPPORTED.
+ * All three packed like e (items back to back); eps_s / eps_f per item.  Plans
+ * of any batch and any mix of shapes: every item runs exactly K steps, and
+ * each item's product is that of its own single-item plan.  1D items run the
+ * transposed step on the Bluestein passes: g <- Re(IDFT(M_f DFT(M_s g))), M_f
+ * per bin k < N (the forward takes the real part after its inverse).
  */
 ffcz_status ffcz_correct_backward(ffcz_plan_t plan, const float* e0_dev,
                                   const float* grad_out_dev, float* grad_in_dev,

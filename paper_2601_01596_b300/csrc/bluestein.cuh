@@ -17,7 +17,11 @@
 //               (-> X_k or x_n in natural order), the check and the clip of
 //               Alg. 1, chirp pre-multiply, forward column step.
 // One iteration is: row(conj Bt), column(s-clip), row(Bt), column(f-check,
-// f-clip) -- four passes, like the 3D schedule.  Only k, n < N carry data;
+// f-clip) -- four passes, like the 3D schedule.  The adjoint step
+// g <- Re(IDFT(M_f DFT(M_s g))) runs the same chain with the clips replaced by
+// their active-set masks (M_MASK), kept as one byte per point (1: inside the
+// s-cube) and one per bin k < N (bit 0: Re inside, bit 1: Im inside) at the
+// item's point offset; M_RECORD writes them while the forward is replayed.  Only k, n < N carry data;
 // the rest of the P-length buffers is the zero padding of the convolution.
 #pragma once
 #include "passes.cuh"
@@ -31,6 +35,7 @@ enum Op1 : int {
   OP1_EXIT = 3,    // column: inverse step, x, s-clip, store float32 e
   OP1_FILTER = 4,  // column: forward column step of the wrapped chirp f (Bt build)
   OP1_LOADX = 5,   // column: half spectrum X (k <= N/2) -> X_k b_k, forward column step
+  OP1_STOREX = 6,  // column: inverse step, X_k = conj(b_k) c_k / P, store bins k <= N/2
   OP1_CONV = 8,    // row: FFT, times Bt, IFFT
   OP1_CONVC = 9,   // row: FFT, times conj Bt, IFFT
   OP1_FWD = 10     // row: FFT only (Bt build)
@@ -107,6 +112,8 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
         bad |= (x != x);
         ssq = fmaf(x, x, ssq);
       }
+      if ((a.mode & M_MASK) && !(live && n < N && reinterpret_cast<const uint8_t*>(a.mask)[a.g.eoff[gi] + n]))
+        x = 0.f;   // adjoint: M_s of the first step
       if (a.mode & M_PRECLIP) {
         const float cx = clampT(x, p.Esf * ebn);
         cnt += (cx != x);
@@ -167,6 +174,18 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
     for (int u = 0; u < V; ++u) v[u] = cmulc<T>(v[u], twp[(j + u * NT) * n2]);
     fft_pencil<T, L, +1>(v, j, s_tw, tl);
     const bool count = (a.mode & M_COUNT) != 0;
+    if (op == OP1_STOREX) {   // the item's half spectrum into ed_f at its canonical offset
+      const T invP = T(1) / (T)Pn;
+      float2* hx = a.ed_f + a.g.coff[gi];
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int64_t k = (int64_t)m0 + (int64_t)u * D;
+        if (!(live && k <= N / 2)) continue;
+        const v2<T> X = cmulc<T>(v[u], chirp(u));
+        hx[k] = make_float2((float)(X.x * invP), (float)(X.y * invP));
+      }
+      return;
+    }
     if (op == OP1_FCLIP) {
       const T invP = T(1) / (T)Pn;   // exact: P is a power of two
       const T Ds = sizeof(T) == 4 ? (T)p.Dsf : (T)p.Ds;
@@ -199,7 +218,11 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
           else { mx.add(X.x); mx.add(X.y); }
           bad |= (X.x != X.x) | (X.y != X.y);
         }
-        if (res) {
+        uint8_t* fmk = (a.mode & (M_MASK | M_RECORD)) ? reinterpret_cast<uint8_t*>(a.mask) + a.g.eoff[gi] : nullptr;
+        if (a.mode & M_MASK) {   // adjoint: M_f
+          const unsigned b = in_range ? fmk[k] : 0u;
+          X = mk<T>((b & 1u) ? X.x : T(0), (b & 2u) ? X.y : T(0));
+        } else if (res) {
           const float2 r0 = (t_it >= 1 && in_range) ? rr[k] : make_float2(0.f, 0.f);
           const T x = X.x + (T)r0.x, y = X.y + (T)r0.y;
           const T cx = clampT(x, Ds), cy = clampT(y, Ds);
@@ -214,6 +237,7 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
             const T big = pwf ? fmax(ratioT(fabs(X.x), qx), ratioT(fabs(X.y), qy)) : fmax(fabs(X.x), fabs(X.y));
             record_f(a, a.g.coff[gi] + k, (float)(cx - X.x), (float)(cy - X.y), t_it, may_stop && big <= thr);
           }
+          if ((a.mode & M_RECORD) && in_range) fmk[k] = (uint8_t)((cx == X.x) | ((cy == X.y) << 1));
           X = mk<T>(cx, cy);
         }
         v[u] = in_range ? cmul<T>(X, bk) : mk<T>(T(0), T(0));   // pre: X'_k b_k
@@ -239,6 +263,10 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
                                                                             : nullptr;
       float* q_out = qv && op == OP1_SCLIP ? a.pv_q[t_it & 1] + a.g.eoff[gi] : nullptr;
       AbsMax<T> svm;
+      // checkpoints of e_t for t = 0, m, 2m, ... below the item's K
+      float* ckp = ((a.mode & M_CKPT) && a.ckpt_every > 0 && (t_it % a.ckpt_every) == 0 && t_it < p.max_iters)
+                       ? a.ckpt + (int64_t)(t_it / a.ckpt_every) * a.ckpt_stride + a.g.eoff[gi]
+                       : nullptr;
 #pragma unroll
       for (int u = 0; u < V; ++u) {
         const int64_t n = (int64_t)m0 + (int64_t)u * D;
@@ -256,12 +284,17 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
         } else if (op == OP1_EXIT && pv == PV_DYKSTRA && q_in && in_range) {
           x += (T)q_in[n];   // x_t = P_S'(y_{t-1} + q_{t-1})
         }
-        if ((a.mode & M_CLIP) && !(qv && op == OP1_SCLIP)) {
+        if ((a.mode & M_MASK) && op == OP1_SCLIP) {   // adjoint: M_s
+          if (!(in_range && reinterpret_cast<const uint8_t*>(a.mask)[a.g.eoff[gi] + n])) x = T(0);
+        } else if ((a.mode & M_CLIP) && !(qv && op == OP1_SCLIP)) {
           const T cx = clampT(x, Es * (T)ebn);
           if (count && in_range) cnt += (cx != x);
           if (op == OP1_SCLIP && a.ed_s && in_range && cx != x) atomicAdd(eo_s + n, (float)(cx - x));
+          if (op == OP1_SCLIP && (a.mode & M_RECORD) && in_range)
+            reinterpret_cast<uint8_t*>(a.mask)[a.g.eoff[gi] + n] = (uint8_t)(cx == x);
           x = cx;
         }
+        if (op == OP1_SCLIP && ckp && in_range) ckp[n] = (float)x;   // checkpoint e_t
         if (op == OP1_EXIT) {
           if (in_range && (a.mode & M_ACC)) eo[n] += (float)x;   // decompression side: x_hat += IDFT(F)
           else if (in_range) eo[n] = (a.mode & M_CLIP) ? clampT((float)x, p.Esf * ebn) : (float)x;

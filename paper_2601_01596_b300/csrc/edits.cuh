@@ -309,6 +309,25 @@ static __global__ void k_ps_shells(Group g, const float2* canon, double* acc, in
     if (hist[i] != 0.0) atomicAdd(&dst[i], hist[i]);
 }
 
+// 1D items: the shell of bin k <= N/2 is k itself (the signed frequencies k
+// and -k), one bin pair per shell: A = w |X|, P = w |X|^2, n = w, w = 2 for
+// 0 < k < N/2 and 1 at k = 0 and k = N/2.  acc: per item 3 x S doubles
+// (zeroed).  Grid (x: bins, y: members).
+static __global__ void k_ps_bins1(Group g, const ItemParams* prm, const float2* canon, double* acc, int S) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const int64_t N = prm[item].n, nb = N / 2 + 1;
+  const float2* c = canon + g.coff[gi];
+  double* A = acc + (int64_t)item * 3 * S;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+    const double w = (k == 0 || 2 * k == N) ? 1.0 : 2.0;
+    const double a = hypot((double)c[k].x, (double)c[k].y);
+    A[k] = w * a;
+    A[S + k] = w * a * a;
+    A[2 * S + k] = w;
+  }
+}
+
 // d_s = (-2 sqrt2 A + sqrt(8 A^2 + 8 n rho P)) / (4 n) per shell; shell 0 (the
 // mean) takes the smallest of the others.  One CTA per item.
 static __global__ void k_ps_roots(double* acc, int S, const double* rho) {
@@ -348,6 +367,19 @@ static __global__ void k_ps_write(Group g, const double* acc, int S, float2* out
     const int64_t r = i / (M + 1);
     const float b = (float)d[ps_shell((int)(r / Ny), (int)(r % Ny), kx, Nz, Ny)];
     o[i] = make_float2(b, b);
+  }
+}
+
+// 1D items: bounds (d_k, d_k) of bins k <= N/2.
+static __global__ void k_ps_write1(Group g, const ItemParams* prm, const double* acc, int S, float2* out) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const int64_t nb = prm[item].n / 2 + 1;
+  const double* d = acc + (int64_t)item * 3 * S;
+  float2* o = out + g.coff[gi];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nb; k += (int64_t)gridDim.x * blockDim.x) {
+    const float b = (float)d[k];
+    o[k] = make_float2(b, b);
   }
 }
 

@@ -1190,7 +1190,15 @@ void body1(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
       Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
       a.sel_in = a.sel_out = S_CUR;
       if (step == 0) { row1_args<T>(p, a, dg, OP1_CONVC); a.sel_in = S_PREV; }
-      if (step == 1) { col1_args<T>(p, a, dg, OP1_SCLIP); a.mode = M_CLIP | cnt_flag(p); }
+      if (step == 1) {
+        col1_args<T>(p, a, dg, OP1_SCLIP);
+        a.mode = M_CLIP | cnt_flag(p);
+        if (sizeof(T) == 4 && p->ck_rec) {   // the differentiable forward's checkpoints
+          a.mode |= M_CKPT;
+          a.ckpt = p->bw_ck;
+          a.ckpt_every = p->bw_m;
+        }
+      }
       if (step == 2) { row1_args<T>(p, a, dg, OP1_CONV); a.mode = 0; }
       if (step == 3) { col1_args<T>(p, a, dg, OP1_FCLIP); a.mode = M_CLIP | cnt_flag(p); }
       args[g] = a;
@@ -1605,9 +1613,55 @@ void edits_compact(ffcz_plan_s* p, int m, uint8_t* sf, int32_t* sc, uint8_t* ff,
 // sums of |X| and |X|^2, the positive root per shell, one bound per bin.
 // The normalisation (x - mean)/mean of the power spectrum cancels out of the
 // bound (a relative bound is scale-free and the mean only moves shell 0).
+void ps_bounds1(ffcz_plan_s* p, const float* x, const double* rho, float2* out) {
+  cudaStream_t s = p->stream;
+  int S = 2;
+  for (int64_t i = 0; i < p->batch; ++i) S = std::max<int64_t>(S, p->h_prm[i].n / 2 + 2);
+  if (!p->ps_acc || p->ps_S < S) {
+    p->ps_acc = (double*)dalloc(p, sizeof(double) * 3 * (size_t)S * p->batch);
+    p->ps_rho = (double*)dalloc(p, sizeof(double) * p->batch);
+    p->ps_S = S;
+  }
+  S = p->ps_S;
+  CK(cudaMemsetAsync(p->ps_acc, 0, sizeof(double) * 3 * (size_t)S * p->batch, s));
+  CK(cudaMemcpyAsync(p->ps_rho, rho, sizeof(double) * p->batch, cudaMemcpyHostToDevice, s));
+  for (auto& dg : p->groups) {
+    // X = DFT(x) by the Bluestein passes, bins k <= N/2 into ed_canon
+    Args a = make_args<float>(p, dg, p->B32[0], p->B32[0], p->d_st);
+    a.pred = P_ALL;
+    a.sel_in = a.sel_out = S_CUR;
+    a.pw_e = nullptr; a.pw_f = nullptr;
+    a.e = const_cast<float*>(x);
+    a.mode = 0;
+    col1_args<float>(p, a, dg, OP1_ENTRY);
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
+    row1_args<float>(p, a, dg, OP1_CONV);
+    launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
+    col1_args<float>(p, a, dg, OP1_STOREX);
+    a.ed_f = p->ed_canon;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
+    const unsigned gx = (unsigned)std::min<int64_t>((S + 255) / 256, 1024);
+    k_ps_bins1<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->d_prm, p->ed_canon, p->ps_acc, S);
+    g_launches++;
+  }
+  k_ps_roots<<<(unsigned)p->batch, 256, 0, s>>>(p->ps_acc, S, p->ps_rho);
+  g_launches++;
+  for (auto& dg : p->groups) {
+    const unsigned gx = (unsigned)std::min<int64_t>((S + 255) / 256, 1024);
+    k_ps_write1<<<dim3(gx, (unsigned)dg.count), 256, 0, s>>>(dg.g, p->d_prm, p->ps_acc, S, out);
+    g_launches++;
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+}
+
 void ps_bounds(ffcz_plan_s* p, const float* x, const double* rho, float2* out) {
   cudaStream_t s = p->stream;
   if (!p->ed_canon) p->ed_canon = (float2*)dalloc(p, sizeof(float2) * std::max<int64_t>(1, p->ed_total[1]));
+  if (p->ndim == 1) {
+    ps_bounds1(p, x, rho, out);
+    return;
+  }
   int S = 1;
   for (auto& dg : p->groups) {
     const double r = std::sqrt((double)dg.M * dg.M + std::pow(dg.Nz / 2, 2.0) +
@@ -2372,7 +2426,6 @@ void replay_entry(ffcz_plan_s* p, LoopBufs B, float* e0, uint32_t* fmask) {
 
 // Plan checks shared by the differentiable entry points.
 void bw_check(ffcz_plan_s* p) {
-  if (p->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "backward supports 2D and 3D items");
   if (p->opts.pointwise) fail(FFCZ_ERR_INVALID, "backward uses scalar bounds");
   if (p->opts.method != PV_POCS) fail(FFCZ_ERR_UNSUPPORTED, "backward differentiates Alg. 1 (method 0)");
   if (p->opts.K < 1 || p->opts.ckpt_every < 1) fail(FFCZ_ERR_INVALID, "K and ckpt_every must be >= 1");
@@ -2389,11 +2442,15 @@ void bw_alloc(ffcz_plan_s* p) {
     p->bw_pxoff.clear();
     p->bw_chkoff.clear();
     int64_t px = 0, ck = 0;
-    for (const DevGroup& dg : p->groups) {
-      p->bw_pxoff.push_back(px);
-      p->bw_chkoff.push_back(ck);
-      px += x_words(dg.M, dg.rows, dg.wx) * dg.count;
-      ck += chkw(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc) * dg.count;
+    if (p->ndim == 1) {   // one mask byte per point and per bin k < N, items at their point offsets
+      px = ck = (N + 3) / 4;
+    } else {
+      for (const DevGroup& dg : p->groups) {
+        p->bw_pxoff.push_back(px);
+        p->bw_chkoff.push_back(ck);
+        px += x_words(dg.M, dg.rows, dg.wx) * dg.count;
+        ck += chkw(dg.Nz, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.wc) * dg.count;
+      }
     }
     p->px_words = px;
     p->chk_words = ck;
@@ -2401,9 +2458,9 @@ void bw_alloc(ffcz_plan_s* p) {
     p->bw_ck = (float*)dalloc(p, sizeof(float) * N * nseg);
     p->bw_smask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->px_words * m);
     p->bw_fmask = (uint32_t*)dalloc(p, sizeof(uint32_t) * p->chk_words * m);
-    if (!p->bw_G[0]) {
-      p->bw_G[0] = dalloc(p, sizeof(float) * N);
-      p->bw_G[1] = dalloc(p, sizeof(float) * N);
+    if (!p->bw_G[0]) {   // the adjoint's spectra: the plan's spectrum length (1D: P per item)
+      p->bw_G[0] = dalloc(p, sizeof(float2) * p->total_c);
+      p->bw_G[1] = dalloc(p, sizeof(float2) * p->total_c);
     }
     p->bw_K = K;
     p->bw_m = m;
@@ -2415,6 +2472,140 @@ void bw_alloc(ffcz_plan_s* p) {
 __global__ void k_premask_ck(float* g, const float* e0, const float* ck0, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!(ck0[i] == e0[i])) g[i] = 0.f;
+}
+
+// 1D items (Bluestein passes): one forward body with mask recording or
+// checkpoint writes (replay), and the adjoint's passes.  Masks: one byte per
+// point (s) and per bin (f) at the items' point offsets.
+void replay_body1(ffcz_plan_s* p, LoopBufs B, uint32_t* smask, uint32_t* fmask, float* ckpt, bool do_chk) {
+  for (const DevGroup& dg : p->groups) {
+    Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
+    a.pred = P_ALL;
+    row1_args<float>(p, a, dg, OP1_CONVC);
+    a.sel_in = S_PREV; a.sel_out = S_CUR;
+    launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
+    a.sel_in = S_CUR;
+    col1_args<float>(p, a, dg, OP1_SCLIP);
+    a.mode = M_CLIP | (smask ? M_RECORD : 0) | (ckpt ? M_CKPT : 0);
+    a.mask = smask;
+    a.ckpt = ckpt;
+    a.ckpt_every = p->bw_m;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+    if (!do_chk) continue;
+    a.mask = nullptr;
+    a.ckpt = nullptr;
+    row1_args<float>(p, a, dg, OP1_CONV);
+    a.mode = 0;
+    launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
+    col1_args<float>(p, a, dg, OP1_FCLIP);
+    a.mode = M_CLIP | (fmask ? M_RECORD : 0);
+    a.mask = fmask;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+  }
+}
+
+void replay_entry1(ffcz_plan_s* p, LoopBufs B, float* e0, uint32_t* fmask) {
+  for (const DevGroup& dg : p->groups) {
+    Args a = make_args<float>(p, dg, B.b0, B.b1, p->d_st);
+    a.pred = P_ALL;
+    col1_args<float>(p, a, dg, OP1_ENTRY);
+    a.e = e0;
+    a.mode = 0;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+    row1_args<float>(p, a, dg, OP1_CONV);
+    launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
+    col1_args<float>(p, a, dg, OP1_FCLIP);
+    a.mode = M_CLIP | (fmask ? M_RECORD : 0);
+    a.mask = fmask;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+  }
+}
+
+// One adjoint step g <- Re(IDFT(M_f DFT(M_s g))) of every 1D item: the
+// first takes g from gout (column entry with M_s), the others from the
+// previous step's spectrum (row with conj Bt, column with M_s).
+void adjoint_step1(ffcz_plan_s* p, LoopBufs GB, const float* gout, uint32_t* sm, uint32_t* fm, bool first) {
+  for (const DevGroup& dg : p->groups) {
+    Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
+    a.pred = P_ALL;
+    if (first) {
+      col1_args<float>(p, a, dg, OP1_ENTRY);
+      a.e = const_cast<float*>(gout);
+    } else {
+      row1_args<float>(p, a, dg, OP1_CONVC);
+      a.sel_in = S_PREV; a.sel_out = S_CUR;
+      a.mode = 0;
+      launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
+      a.sel_in = S_CUR;
+      col1_args<float>(p, a, dg, OP1_SCLIP);
+    }
+    a.mode = M_MASK;
+    a.mask = sm;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+    a.sel_in = a.sel_out = S_CUR;
+    row1_args<float>(p, a, dg, OP1_CONV);
+    a.mode = 0;
+    a.mask = nullptr;
+    launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
+    col1_args<float>(p, a, dg, OP1_FCLIP);
+    a.mode = M_MASK;
+    a.mask = fm;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+  }
+}
+
+// The segments of the 1D backward (after the forward's checkpoints).
+ffcz_status backward1_tail(ffcz_plan_s* p, const float* e0, const float* gout, float* gin, const float* ck,
+                           const float* ckpt_in, LoopBufs B, LoopBufs GB) {
+  const int K = p->opts.K, m = p->opts.ckpt_every;
+  const int64_t N = p->total;
+  const int nseg = (K + m - 1) / m;
+  set_t(p, p->d_st2, 0);
+  bool first = true;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int t0 = seg * m, t1 = std::min(K, t0 + m);
+    set_t(p, p->d_st, t0);
+    replay_entry1(p, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
+    for (int b = t0 + 1; b <= t1; ++b) {
+      advance(p, p->d_st);
+      replay_body1(p, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
+                   b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr, b < t1);
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      if (!first) advance(p, p->d_st2);
+      adjoint_step1(p, GB, gout, p->bw_smask + (int64_t)(t - t0) * p->px_words,
+                    p->bw_fmask + (int64_t)(t - t0) * p->chk_words, first);
+      first = false;
+    }
+  }
+  // exit: x = Re(b c) / (P N) of the last step's spectrum, no clip
+  advance(p, p->d_st2);
+  for (const DevGroup& dg : p->groups) {
+    Args a = make_args<float>(p, dg, GB.b0, GB.b1, p->d_st2);
+    a.pred = P_ALL;
+    row1_args<float>(p, a, dg, OP1_CONVC);
+    a.sel_in = S_PREV; a.sel_out = S_CUR;
+    launch_row1<float>(dg.P2, dg.w1r, a, dg.P1, dg.count, p->stream);
+    a.sel_in = S_CUR;
+    col1_args<float>(p, a, dg, OP1_EXIT);
+    a.e = gin;
+    a.mode = 0;
+    launch_col1<float>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
+  }
+  if (ckpt_in) {
+    k_premask_ck<<<1184, 256, 0, p->stream>>>(gin, e0, ckpt_in, N);
+    g_launches++;
+  } else {
+    for (int64_t i = 0; i < p->batch; ++i) {
+      const int64_t n = p->h_prm[i].n;
+      k_premask<<<(unsigned)std::min<int64_t>(1184, (n + 255) / 256), 256, 0, p->stream>>>(
+          gin + p->eoff[i], e0 + p->eoff[i], p->d_prm, p->d_st, (int)i, n);
+      g_launches++;
+    }
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaGetLastError());
+  return FFCZ_OK;
 }
 
 // ckpt_in: checkpoints written by ffcz_correct_ckpt (null: the forward is run
@@ -2446,10 +2637,12 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     const int last_ck = (nseg - 1) * m;
     for (int t = 1; t <= last_ck; ++t) {
       // k_decide after entry set t = 1 (forced iterations never stop early)
-      replay_body(p, B, nullptr, nullptr, p->bw_ck, t < last_ck);
+      if (p->ndim == 1) replay_body1(p, B, nullptr, nullptr, p->bw_ck, t < last_ck);
+      else replay_body(p, B, nullptr, nullptr, p->bw_ck, t < last_ck);
       if (t < last_ck) advance(p, p->d_st);
     }
   }
+  if (p->ndim == 1) return backward1_tail(p, e0, gout, gin, ck, ckpt_in, B, GB);
   // Adjoint, segment by segment from the last.
   set_t(p, p->d_st2, 0);
   bool first = true;
@@ -3326,7 +3519,6 @@ ffcz_status ffcz_apply_edits16(ffcz_plan_t plan, float* xhat_dev, const double* 
 ffcz_status ffcz_power_spectrum_bounds(ffcz_plan_t plan, const float* x_dev, const double* rho, float* db_dev) {
   if (!plan) return FFCZ_ERR_INVALID;
   return guarded([&]() -> ffcz_status {
-    if (plan->ndim == 1) fail(FFCZ_ERR_UNSUPPORTED, "power-spectrum bounds for 2D and 3D items");
     if (!x_dev || !rho || !db_dev) fail(FFCZ_ERR_INVALID, "null pointer argument");
     for (int64_t i = 0; i < plan->batch; ++i)
       if (!(rho[i] > 0) || !std::isfinite(rho[i])) fail(FFCZ_ERR_INVALID, "rho must be finite and > 0");

@@ -341,3 +341,38 @@ def test_batched_autograd_function_runs_and_matches_backward():
     gi = torch.empty_like(e0)
     plan.backward(e0.detach(), w, gi, Es, Ds)
     assert torch.equal(e0.grad, gi)
+
+
+@pytest.mark.parametrize("shape,K,m", [((3000,), 5, 2), ((1500,), 6, 4), ((9000,), 3, 10)])
+@pytest.mark.parametrize("ckpt", [False, True])
+def test_1d_backward_matches_oracle_vjp(shape, K, m, ckpt):
+    """1D items: the transposed step on the Bluestein passes, element by
+    element against the oracle's VJP (near ties excused as above)."""
+    e0 = W.bimodal_error(shape, 55, dtype=np.float32)
+    E = 1.0
+    D = 0.4 * O.f_violation(O.dft(e0.astype(np.float64)))
+    g = np.random.default_rng(56).standard_normal(shape).astype(np.float32)
+    got = _gpu_backward(shape, e0, g, E, D, K, m, ckpt=ckpt)
+    _assert_vjp_elementwise(got, e0, g, E, D, K, f"1d{shape} K={K} ckpt={ckpt}")
+
+
+def test_1d_batched_backward_equals_single_items():
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    shapes = [(3000,), (1500,), (3000,)]
+    K, m = 4, 2
+    items = [W.bimodal_error(sh, 57 + i, dtype=np.float32) for i, sh in enumerate(shapes)]
+    gs = [np.random.default_rng(58 + i).standard_normal(sh).astype(np.float32) for i, sh in enumerate(shapes)]
+    Es = [1.0] * 3
+    Ds = [0.4 * O.f_violation(O.dft(x.astype(np.float64))) for x in items]
+    te0 = torch.from_numpy(np.concatenate(items)).cuda()
+    tg = torch.from_numpy(np.concatenate(gs)).cuda()
+    gi = torch.empty_like(te0)
+    plan = ffcz.Plan(shapes, K=K, ckpt_every=m)
+    plan.backward(te0, tg, gi, Es, Ds)
+    got = gi.cpu().numpy()
+    off = 0
+    for i, sh in enumerate(shapes):
+        one = _gpu_backward(sh, items[i], gs[i], Es[i], Ds[i], K, m)
+        assert np.array_equal(got[off:off + sh[0]], one), i
+        off += sh[0]

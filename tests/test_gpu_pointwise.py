@@ -105,7 +105,7 @@ def test_invalid_bounds_and_scalar_calls_are_refused():
         plan.correct(torch.zeros(32 * 32, device="cuda"), [1.0], [1.0])
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (16, 32, 64)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 128), (16, 32, 64), (3000,), (1501,)])
 def test_power_spectrum_bounds_match_oracle(shape):
     import torch
     import paper_2601_01596_b300 as ffcz
@@ -116,8 +116,11 @@ def test_power_spectrum_bounds_match_oracle(shape):
     got = plan.power_spectrum_bounds(torch.from_numpy(x.reshape(-1).copy()).cuda(), rho).cpu().numpy()
     D_re, D_im = O.power_spectrum_bounds(x.astype(np.float64), rho)
     want = O.half_spectrum(D_re + 1j * D_im).reshape(-1)
-    np.testing.assert_allclose(got.real, want.real, rtol=1e-4)
-    np.testing.assert_allclose(got.imag, want.imag, rtol=1e-4)
+    # 1D shells are single bin pairs: the float32 transform's absolute error
+    # on the smallest bins is not averaged over a shell
+    atol = 0.0 if len(shape) > 1 else 1e-4 * float(np.median(want.real))
+    np.testing.assert_allclose(got.real, want.real, rtol=1e-4, atol=atol)
+    np.testing.assert_allclose(got.imag, want.imag, rtol=1e-4, atol=atol)
 
 
 def test_power_spectrum_mode_end_to_end():
