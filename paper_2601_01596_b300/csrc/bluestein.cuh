@@ -36,6 +36,7 @@ enum Op1 : int {
   OP1_FILTER = 4,  // column: forward column step of the wrapped chirp f (Bt build)
   OP1_LOADX = 5,   // column: half spectrum X (k <= N/2) -> X_k b_k, forward column step
   OP1_STOREX = 6,  // column: inverse step, X_k = conj(b_k) c_k / P, store bins k <= N/2
+  OP1_ZOUT = 7,    // column: inverse step, Z_k = conj(b_k) c_k / P (k < N), float64 to zout
   OP1_CONV = 8,    // row: FFT, times Bt, IFFT
   OP1_CONVC = 9,   // row: FFT, times conj Bt, IFFT
   OP1_FWD = 10     // row: FFT only (Bt build)
@@ -57,10 +58,11 @@ __device__ __forceinline__ v2<T> chirp_r(uint64_t r, uint64_t N) {
 // Chirp table b_n, n < N, of every item of a group (one launch per plan and
 // precision); stored like the items' float32 data, at the item's e offset.
 template <typename T>
-__global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab) {
+__global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab, int half = 0) {
   const int gi = blockIdx.y;
   const int item = g.item[gi];
-  const uint64_t N = (uint64_t)prm[item].n, twoN = 2 * N;
+  if (half && !prm[item].h1) return;
+  const uint64_t N = (uint64_t)prm[item].n / (half ? 2 : 1), twoN = 2 * N;
   v2<T>* out = tab + g.eoff[gi];
   for (uint64_t n = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; n < N;
        n += (uint64_t)gridDim.x * blockDim.x) {
@@ -74,9 +76,10 @@ __global__ void k1_chirp_table(Group g, const ItemParams* prm, v2<T>* tab) {
 template <typename T, int L, int W_ = TileW<T>::value>
 __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const int by_) {
   FFCZ_AXIS_PROLOGUE(T, L, W_, 0)
+  if ((a.half1 == 1 && !p.h1) || (a.half1 == 2 && p.h1)) return;   // certification split (member-uniform)
   constexpr int NT = G_::NT, W = G_::W;
   const int P2 = a.g.M;
-  const int64_t N = p.n;
+  const int64_t N = a.half1 == 1 ? p.n / 2 : p.n;   // transform length
   const int ntiles = P2 / W;
   const bool live = tile < ntiles;
   const int n2 = live ? tile * W + w : 0;
@@ -100,7 +103,23 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
   // offset (bin k > N/2 takes those of N - k); the measures are then ratios
   const float* pwe = a.pw_e ? a.pw_e + a.g.eoff[gi] : nullptr;
   const float2* pwf = a.pw_f ? a.pw_f + a.g.coff[gi] : nullptr;
-  if (op == OP1_ENTRY) {
+  if (op == OP1_ENTRY && a.half1 == 1) {
+    // z_n = x_2n + i x_2n+1 (certification: measure only)
+    const float* src = a.e + a.g.eoff[gi];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const int64_t n = (int64_t)m0 + (int64_t)u * D;
+      const bool in = live && n < N;
+      const float x = in ? src[2 * n] : 0.f, y = in ? src[2 * n + 1] : 0.f;
+      if ((a.mode & M_MEASURE) && in) {
+        if (pwe) { mx.add((T)ratio_cert(x, pwe[2 * n])); mx.add((T)ratio_cert(y, pwe[2 * n + 1])); }
+        else { mx.add((T)x); mx.add((T)y); }
+        bad |= (x != x) | (y != y);
+        ssq = fmaf(x, x, fmaf(y, y, ssq));
+      }
+      v[u] = mk<T>((T)x, (T)y);
+    }
+  } else if (op == OP1_ENTRY) {
     float* src = a.e + a.g.eoff[gi];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
@@ -157,8 +176,8 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
 #pragma unroll
     for (int u = 0; u < V; ++u) v[u] = cmulc<T>(v[u], chirp(u));   // a_n = x_n conj(b_n)
     if (a.mode & (M_MEASURE | M_PRECLIP)) {
-      // V <= 32 float32 squares: relative error of the sum < 2^-19
-      Red rr{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-18) : 0.0, live ? cnt : 0ull};
+      // at most 2V <= 64 float32 squares: relative error of the sum < 2^-18
+      Red rr{live ? mx.dbits(bad) : 0ull, live ? (double)ssq * (1.0 + 0x1p-17) : 0.0, live ? cnt : 0ull};
       block_reduce(rr, s_red);
       if (threadIdx.x == 0) {
         if (a.mode & M_MEASURE) {
@@ -174,6 +193,18 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
     for (int u = 0; u < V; ++u) v[u] = cmulc<T>(v[u], twp[(j + u * NT) * n2]);
     fft_pencil<T, L, +1>(v, j, s_tw, tl);
     const bool count = (a.mode & M_COUNT) != 0;
+    if (op == OP1_ZOUT) {   // Z_k, k < N (certification of even lengths)
+      const T invP = T(1) / (T)Pn;
+      v2<T>* zo = reinterpret_cast<v2<T>*>(a.zout) + a.g.soff[gi];
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        const int64_t k = (int64_t)m0 + (int64_t)u * D;
+        if (!(live && k < N)) continue;
+        const v2<T> Z = cmulc<T>(v[u], chirp(u));
+        zo[k] = mk<T>(Z.x * invP, Z.y * invP);
+      }
+      return;
+    }
     if (op == OP1_STOREX) {   // the item's half spectrum into ed_f at its canonical offset
       const T invP = T(1) / (T)Pn;
       float2* hx = a.ed_f + a.g.coff[gi];
@@ -332,6 +363,7 @@ k1_col(Args a) {
 template <typename T, int L, int W_ = TileW<T>::value>
 __device__ __forceinline__ void k1_row_body(const Args& a, const int bx_, const int by_) {
   FFCZ_AXIS_PROLOGUE(T, L, W_, 0)
+  if ((a.half1 == 1 && !p.h1) || (a.half1 == 2 && p.h1)) return;   // certification split (member-uniform)
   constexpr int NT = G_::NT;
   const int P1 = a.g.Nz;
   const int prow = tile * G_::W + w;
@@ -362,6 +394,57 @@ template <typename T, int L, int W_ = TileW<T>::value>
 __global__ void __launch_bounds__(Geo<T, L, W_>::NTHR, Geo<T, L, W_>::MINB)
 k1_row(Args a) {
   k1_row_body<T, L, W_>(a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// Twiddles W_N^k = exp(-2 pi i k / N), k <= N/2, of the members certified
+// through the N/2-point transform (at the canonical offset; the CUDA
+// function is called).  Grid (x: any, y: members).
+__global__ void k1_rtw(Group g, const ItemParams* prm, double2* W) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  if (!prm[item].h1) return;
+  const int64_t N = prm[item].n;
+  double2* w = W + g.coff[gi];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= N / 2; k += (int64_t)gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi((double)(2 * k) / (double)N, &sn, &cs);
+    w[k] = make_double2(cs, -sn);
+  }
+}
+
+// Certification of even lengths: from Z = DFT_{N/2}(x_2n + i x_2n+1), the
+// spectrum of the real signal X_k = (A - i W_N^k B) / 2 with
+// A = Z_k + conj Z_{N/2-k}, B = Z_k - conj Z_{N/2-k} (indices mod N/2), for
+// k <= N/2 (the rest mirrors them), and the violation max (ratios with
+// pointwise bounds, NaN -> +inf) into the item's vbits.  Grid (x: any,
+// y: members), 256 threads.
+__global__ void __launch_bounds__(256) k1_rpost(Group g, const ItemParams* prm, ItemState* st, int pred,
+                                                const double2* Z, const double2* W, const float2* pwf) {
+  const int gi = blockIdx.y;
+  const int item = g.item[gi];
+  const ItemParams& p = prm[item];
+  ItemState& s = st[item];
+  if (!p.h1 || !pred_ok(pred, s, p)) return;
+  const int64_t N = p.n, H = N / 2;
+  const double2* z = Z + g.soff[gi];
+  const double2* w = W + g.coff[gi];
+  const float2* q = pwf ? pwf + g.coff[gi] : nullptr;
+  AbsMax<double> mx;
+  bool bad = false;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= H; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 zk = z[k == H ? 0 : k], zm = z[k == 0 ? 0 : H - k];
+    const double ar = zk.x + zm.x, ai = zk.y - zm.y, br = zk.x - zm.x, bi = zk.y + zm.y;
+    const double2 wk = w[k];
+    const double pr = wk.x * br - wk.y * bi, pi = wk.x * bi + wk.y * br;   // W B
+    const double xr = 0.5 * (ar + pi), xi = 0.5 * (ai - pr);               // (A - i W B) / 2
+    if (q) { mx.add(xr / (double)q[k].x); mx.add(xi / (double)q[k].y); }
+    else { mx.add(xr); mx.add(xi); }
+    bad |= (xr != xr) | (xi != xi);
+  }
+  __shared__ unsigned long long s_red[128];
+  unsigned long long vb = mx.dbits(bad), c = 0ull;
+  block_max_count(vb, c, false, s_red);
+  if (threadIdx.x == 0) atomicMax(&s.vbits, vb);
 }
 
 }  // namespace ffcz

@@ -196,6 +196,15 @@ struct ffcz_plan_s {
   void* Bt64 = nullptr;
   void* ch32 = nullptr;        // 1D: chirp tables b_n (float32 / float64)
   void* ch64 = nullptr;
+  // 1D certification of even lengths through the N/2-point transform of
+  // x_2n + i x_2n+1: groups of the P/2-point passes, the N/2-point chirps and
+  // their Bt, the spectrum Z and the twiddles W_N^k (built at the first
+  // certification)
+  std::vector<DevGroup> hgroups;
+  void* ch64h = nullptr;
+  void* Bt64h = nullptr;
+  void* Bz = nullptr;
+  double2* rtw = nullptr;
   void* B64[2] = {nullptr, nullptr};
   void* Bc = nullptr;
   float* staging = nullptr;
@@ -757,7 +766,7 @@ void launch_col1_tw(const Args& a, int P2, int count, cudaStream_t s) {
   if (g_dry) { set_smem(k1_col<T, L, W>, sm); return; }
   ProfScope ps(a.op1 == OP1_FCLIP ? ((a.mode & M_NOWRITE) ? "col1_cert" : "col1_fclip")
                : a.op1 == OP1_SCLIP ? "col1_sclip" : a.op1 == OP1_EXIT ? "col1_exit"
-               : a.op1 == OP1_FILTER ? "col1_filter" : "col1_entry",
+               : a.op1 == OP1_FILTER ? "col1_filter" : a.op1 == OP1_ZOUT ? "col1_zout" : "col1_entry",
                8 * (int)sizeof(T), L, s);
   k1_col<T, L, W><<<grid, G_::NTHR, sm, s>>>(a);
   g_launches++;
@@ -1477,6 +1486,9 @@ int64_t p1d_len(int64_t n) {
   while (P < 2 * n - 1) P <<= 1;
   return P;
 }
+// 1D items certified through the N/2-point transform: even N >= 64 (then
+// the N/2-point Bluestein length is P/2 >= 64).
+inline bool half_cert_ok(int64_t n) { return n % 2 == 0 && n >= 64; }
 
 void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int min_iters,
                    int max_iters) {
@@ -1498,6 +1510,7 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
     q.inv_pn = 0.0; q.inv_pnf = 0.f; q.logP = 0;
     q.bscale = 1.0;
     q.pw = p->opts.pointwise ? 1 : 0;
+    q.h1 = 0;
     q.thrs = E * (1.0 - eta / 2.0);
     q.thrsf = (float)q.thrs;
     if (p->ndim == 1) {
@@ -1505,6 +1518,7 @@ void upload_params(ffcz_plan_s* p, const double* eps_s, const double* eps_f, int
       q.inv_pn = 1.0 / ((double)P * (double)n);
       q.inv_pnf = (float)q.inv_pn;
       q.logP = ilog2((int)P);
+      q.h1 = half_cert_ok(n) ? 1 : 0;
     }
   }
   CK(cudaMemcpyAsync(p->d_prm, p->h_prm, sizeof(ItemParams) * p->batch, cudaMemcpyHostToDevice,
@@ -1961,6 +1975,32 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
   if (p->ed_on) edits_finalize(p);
 }
 
+// Tables of the N/2-point certification (1D, even N): chirps of length
+// N/2, Bt = FFT_{P/2} of their wrapped chirp, the twiddles W_N^k and the
+// buffer of Z (float64).
+void build_half(ffcz_plan_s* p) {
+  if (p->Bz || p->hgroups.empty()) return;
+  cudaStream_t s = p->stream;
+  p->ch64h = dalloc(p, sizeof(double2) * p->total);
+  p->Bt64h = dalloc(p, sizeof(double2) * p->total_c);
+  p->Bz = dalloc(p, sizeof(double2) * p->total_c);
+  p->rtw = (double2*)dalloc(p, sizeof(double2) * std::max<int64_t>(1, p->ed_total[1]));
+  for (auto& hg : p->hgroups) {
+    k1_chirp_table<double><<<dim3(64, (unsigned)hg.count), 256, 0, s>>>(hg.g, p->d_prm,
+                                                                      static_cast<double2*>(p->ch64h), 1);
+    k1_rtw<<<dim3(64, (unsigned)hg.count), 256, 0, s>>>(hg.g, p->d_prm, p->rtw);
+    g_launches += 2;
+    Args a = make_args<double>(p, hg, p->Bt64h, p->Bt64h, p->d_st);
+    a.pred = P_ALL;
+    a.half1 = 1;
+    col1_args<double>(p, a, hg, OP1_FILTER);
+    a.chirp = p->ch64h;
+    launch_col1<double>(hg.P1, hg.w1c, a, hg.P2, hg.count, s);
+    row1_args<double>(p, a, hg, OP1_FWD);
+    launch_row1<double>(hg.P2, hg.w1r, a, hg.P1, hg.count, s);
+  }
+}
+
 // st: the state the certification reads and writes (default the loop's);
 // x_done / y_done: the x pass (and the y pass) already ran into the FP64
 // buffer (host entry point).
@@ -1969,10 +2009,16 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = 
   ItemState* S = st ? st : p->d_st;
   if (!p->Bc) p->Bc = dalloc(p, (size_t)p->total_c * sizeof(double2));
   if (p->ndim == 1 && !p->Bt64) build_bt<double>(p);
-  for (auto& dg : p->groups) {
-    if (p->ndim == 1) {
+  if (p->ndim == 1) {
+    // odd (and short) lengths: the N-point transform; even lengths: the
+    // N/2-point transform of x_2n + i x_2n+1 and the real-input post-processing
+    const bool halves = !p->hgroups.empty();
+    if (halves) build_half(p);
+    const int pred = repair_round ? P_UNCERT : P_ALL;
+    for (auto& dg : p->groups) {
       Args a = make_args<double>(p, dg, p->Bc, p->Bc, S);
-      a.pred = repair_round ? P_UNCERT : P_ALL;
+      a.pred = pred;
+      a.half1 = halves ? 2 : 0;
       a.e = const_cast<float*>(e);
       col1_args<double>(p, a, dg, OP1_ENTRY);
       a.mode = M_MEASURE;
@@ -1983,8 +2029,33 @@ void certify(ffcz_plan_s* p, const float* e, bool repair_round, ItemState* st = 
       col1_args<double>(p, a, dg, OP1_FCLIP);
       a.mode = M_NOWRITE;
       launch_col1<double>(dg.P1, dg.w1c, a, dg.P2, dg.count, p->stream);
-      continue;
     }
+    for (auto& hg : p->hgroups) {
+      Args a = make_args<double>(p, hg, p->Bc, p->Bc, S);
+      a.pred = pred;
+      a.half1 = 1;
+      a.e = const_cast<float*>(e);
+      col1_args<double>(p, a, hg, OP1_ENTRY);
+      a.chirp = p->ch64h;
+      a.mode = M_MEASURE;
+      launch_col1<double>(hg.P1, hg.w1c, a, hg.P2, hg.count, p->stream);
+      row1_args<double>(p, a, hg, OP1_CONV);
+      a.bt = p->Bt64h;
+      a.mode = 0;
+      launch_row1<double>(hg.P2, hg.w1r, a, hg.P1, hg.count, p->stream);
+      col1_args<double>(p, a, hg, OP1_ZOUT);
+      a.chirp = p->ch64h;
+      a.zout = p->Bz;
+      launch_col1<double>(hg.P1, hg.w1c, a, hg.P2, hg.count, p->stream);
+      const unsigned gx = (unsigned)std::min<int64_t>(((int64_t)hg.P1 * hg.P2 / 2 + 256) / 256, 1024);
+      k1_rpost<<<dim3(gx, (unsigned)hg.count), 256, 0, p->stream>>>(
+          hg.g, p->d_prm, S, pred, static_cast<const double2*>(p->Bz), p->rtw,
+          p->opts.pointwise ? p->pw_f : nullptr);
+      g_launches++;
+    }
+  }
+  for (auto& dg : p->groups) {
+    if (p->ndim == 1) break;
     Args a = make_args<double>(p, dg, p->Bc, p->Bc, S);
     a.pred = repair_round ? P_UNCERT : P_ALL;
     tabs_x<double>(p, a, dg);
@@ -3281,6 +3352,62 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
       dg.h_soff = so;
       p->groups.push_back(dg);
     }
+    if (ndim == 1) {
+      // groups of the N/2-point certification passes (even N >= 64): the
+      // Bluestein length is P/2, split like any other; members keep their
+      // point, spectrum and half-spectrum offsets
+      std::map<std::pair<int64_t, int64_t>, std::vector<int>> hby;
+      std::vector<int64_t> canon(batch);
+      int64_t acc = 0;
+      for (int64_t i = 0; i < batch; ++i) {
+        canon[i] = acc;
+        acc += shapes[i] / 2 + 1;
+        if (!half_cert_ok(shapes[i])) continue;
+        const int64_t Ph = p1d_len(shapes[i] / 2);
+        const int64_t P1 = (int64_t)1 << (ilog2((int)Ph) / 2);
+        hby[{P1, Ph / P1}].push_back((int)i);
+      }
+      for (auto& kv : hby) {
+        const auto& ids = kv.second;
+        DevGroup hg{};
+        hg.ndim = 1;
+        hg.count = (int)ids.size();
+        hg.P1 = (int)kv.first.first;
+        hg.P2 = (int)kv.first.second;
+        hg.Nz = hg.P1; hg.M = hg.P2; hg.Ny = 1; hg.Nx = 2 * hg.P2;
+        hg.n = (int64_t)hg.P1 * hg.P2;
+        hg.rows = hg.P1;
+        hg.w1c = 4;
+        hg.w1r = row_w1(hg.M);
+        hg.wx = row_w1(hg.M);
+        const int P = hg.P1 * hg.P2;
+        std::vector<double2> t64(P);
+        std::vector<float2> t32(P);
+        for (int m = 0; m < P; ++m) { t64[m] = root<double>(m, P); t32[m] = root<float>(m, P); }
+        void* d64 = dalloc(p.get(), sizeof(double2) * P);
+        void* d32 = dalloc(p.get(), sizeof(float2) * P);
+        CK(cudaMemcpy(d64, t64.data(), sizeof(double2) * P, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d32, t32.data(), sizeof(float2) * P, cudaMemcpyHostToDevice));
+        hg.twp64 = d64;
+        hg.twp32 = d32;
+        std::vector<int32_t> it(ids.begin(), ids.end());
+        std::vector<int64_t> eo, so, co;
+        for (int id : ids) { eo.push_back(p->eoff[id]); so.push_back(soff_c[id]); co.push_back(canon[id]); }
+        int32_t* d_it = (int32_t*)dalloc(p.get(), sizeof(int32_t) * it.size());
+        int64_t* d_eo = (int64_t*)dalloc(p.get(), sizeof(int64_t) * eo.size());
+        int64_t* d_so = (int64_t*)dalloc(p.get(), sizeof(int64_t) * so.size());
+        int64_t* d_co = (int64_t*)dalloc(p.get(), sizeof(int64_t) * co.size());
+        CK(cudaMemcpy(d_it, it.data(), sizeof(int32_t) * it.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_eo, eo.data(), sizeof(int64_t) * eo.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_so, so.data(), sizeof(int64_t) * so.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d_co, co.data(), sizeof(int64_t) * co.size(), cudaMemcpyHostToDevice));
+        hg.g.ndim = 1; hg.g.Nz = hg.Nz; hg.g.Nmid = 1; hg.g.M = hg.M; hg.g.rows = hg.rows;
+        hg.g.item = d_it; hg.g.eoff = d_eo; hg.g.soff = d_so; hg.g.coff = d_co;
+        hg.d_canon = d_co;
+        hg.h_soff = so;
+        p->hgroups.push_back(hg);
+      }
+    }
     // Set the shared-memory attributes of every kernel the plan can launch
     // (both float32 tile widths).
     g_dry = true;
@@ -3330,6 +3457,10 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
           launch_axis<float, +1>(dg.Nz, dg.wa, a, 1, dg.M, 1, nullptr);   // edit application
           launch_axis<float, -1>(dg.Nz, dg.wa, a, 1, dg.M, 1, nullptr);   // power-spectrum bounds
         }
+      }
+      for (const auto& hg : p->hgroups) {
+        launch_col1<double>(hg.P1, hg.w1c, a, hg.P2, 1, nullptr);
+        launch_row1<double>(hg.P2, hg.w1r, a, hg.P1, 1, nullptr);
       }
     } catch (...) {
       g_dry = false;

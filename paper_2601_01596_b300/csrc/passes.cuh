@@ -51,6 +51,7 @@ struct ItemParams {
   double thrs;
   float thrsf;
   int32_t pw;   // 1: pointwise bounds (E, D are 1; measures are ratios)
+  int32_t h1;   // 1D, N even: certified through the N/2-point transform of x_2n + i x_2n+1
 };
 
 struct ItemState {
@@ -147,6 +148,12 @@ struct Args {
   // for the y pass the end of its tile range (0: all planes)
   int tile0;
   int tile1;
+  // 1D certification of even lengths: 0 every member; 1 the N/2-point pass
+  // of the members with h1 (the others return); 2 the N-point pass of the
+  // members without h1.  zout: the N/2-point spectrum Z (float64, at the
+  // member's spectrum offset)
+  int half1;
+  void* zout;
 };
 
 // Spatial edit of one complex register (two real points): S += (c - v).
@@ -2083,6 +2090,15 @@ static __global__ void k_certify(const ItemParams* prm, ItemState* st, int n, in
     // Bluestein: FFT_P, product with Bt (|Bt_k| <= 2N), IFFT_P and two chirp
     // products; |err_k| <= ||err||_2 <= c (2 log2 P + 6) u 2N ||x||_2
     b = 10.0 * (2.0 * p.logP + 6.0) * 1.1102230246251565e-16 * 2.0 * (double)p.n * nrm;
+    if (p.h1) {
+      // through Z = DFT_{N/2}(x_2n + i x_2n+1) (length P/2, ||z||_2 = ||x||_2):
+      // |dZ| <= b_Z = c (2 log2 (P/2) + 6) u N ||x||_2; X_k = (A - i W B)/2 is
+      // linear in Z_k, conj Z_{N/2-k} with coefficients of modulus <= 1, so the
+      // error of Z adds at most 2 b_Z, and the rounding of A, B, W B (W within
+      // a few ulps) and the sum at most 10 u (|Z_k| + |Z_{N/2-k}|) <= 20 u sqrt(N) ||x||_2
+      const double bz = 10.0 * (2.0 * (p.logP - 1) + 6.0) * 1.1102230246251565e-16 * (double)p.n * nrm;
+      b = 2.0 * bz + 20.0 * 1.1102230246251565e-16 * sqrt((double)p.n) * nrm;
+    }
   }
   s.v64 = v;
   s.emax64 = emax;

@@ -94,3 +94,50 @@ def test_certification_1d_brackets_true_violation():
         t = torch.from_numpy(e0.copy()).cuda()
         assert plan.check(t, [s], [v * (1 + 1e-7)])[0]["certified"] == 1
         assert plan.check(t, [s], [v * (1 - 1e-7)])[0]["certified"] == 0
+
+
+@pytest.mark.parametrize("n", [64, 1500, 3000, 9000, 31000, 3001])
+def test_certification_1d_even_lengths_through_half_transform(n):
+    """Even N is certified through the N/2-point transform of x_2n + i x_2n+1
+    and the real-input post-processing (odd N through the N-point one): the
+    FP64 violation equals the oracle's to far below the certification's
+    resolution, and the verdict brackets the true violation at 1e-8."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    e0 = W.bimodal_error((n,), 13, dtype=np.float32)
+    v = O.f_violation(O.dft(e0.astype(np.float64)))
+    s = float(np.max(np.abs(e0)))
+    plan = ffcz.Plan([(n,)])
+    t = torch.from_numpy(e0.copy()).cuda()
+    D = v * (1 + 1e-8)
+    ok = plan.check(t, [s], [D])[0]
+    assert ok["certified"] == 1
+    # f_margin64 = 1 - (v64 + b) / D: the shortfall against 1 - v / D is
+    # (v64 - v) / D plus the stated rounding bound b / D (u = 2^-53, ||x||_2
+    # from the sum of squares; log2 P of the N-point Bluestein length)
+    u, x = 2.0 ** -53, e0.astype(np.float64)
+    nrm = float(np.sqrt(np.sum(x * x)))
+    lP = int(np.log2(max(64, 1 << int(np.ceil(np.log2(2 * n - 1))))))
+    if n % 2 == 0 and n >= 64:
+        b = 2 * 10 * (2 * (lP - 1) + 6) * u * n * nrm + 20 * u * np.sqrt(n) * nrm
+    else:
+        b = 10 * (2 * lP + 6) * u * 2 * n * nrm
+    short = (1 - v / D) - ok["f_margin64"]
+    assert abs(short - b / D) <= 1e-12 + 1e-3 * b / D, (short, b / D)
+    assert plan.check(t, [s], [v * (1 - 1e-8)])[0]["certified"] == 0
+    assert plan.check(t, [s * (1 - 1e-7)], [2 * v])[0]["certified"] == 0
+
+
+def test_certification_1d_mixed_parities_in_one_batch():
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    ns = [1500, 1501, 3000, 2999, 64, 65]
+    items = [W.bimodal_error((n,), 14 + i, dtype=np.float32) for i, n in enumerate(ns)]
+    vs = [O.f_violation(O.dft(x.astype(np.float64))) for x in items]
+    ss = [float(np.max(np.abs(x))) for x in items]
+    plan = ffcz.Plan([(n,) for n in ns])
+    t = torch.from_numpy(np.concatenate(items)).cuda()
+    up = plan.check(t, ss, [v * (1 + 1e-8) for v in vs])
+    down = plan.check(t, ss, [v * (1 - 1e-8) for v in vs])
+    for i in range(len(ns)):
+        assert up[i]["certified"] == 1 and down[i]["certified"] == 0, (ns[i], up[i], down[i])
