@@ -40,23 +40,26 @@ from paper_2601_01596_b300 import workloads as W  # noqa: E402
 METRIC = "field GB/s to certified feasibility, 512^3 fp32; % HBM roofline/iteration"
 FP64_TFLOPS_NOMINAL = 1.25   # nominal dense FP64 rate of a B300 (context only)
 
-# DRAM bytes (read + write) per launch and FP64-pipe utilisation from one ncu
-# capture of these kernels at 512^3 (summaries in profiles/).  They describe
-# the kernel sources as they were at that capture: NCU_SRC_SHA is the digest
-# of those sources (kernel_sources_sha()), and when the current sources
-# differ the figures are reported as null.
-NCU_CAPTURE = "ncu capture of 2026-12-03 (profiles/roofline_*.md)"
-NCU_SRC_SHA = "see-profiles"
+# DRAM bytes (read + write) per 512^3 launch and FP64-pipe utilisation from
+# one ncu capture of each kernel (summaries in profiles/), taken on half-size
+# fields of the same kernels (512x256x512 for the x and z passes, 256x512x512
+# for the y passes, 268 MB each) and scaled by 2: every pass touches each
+# value once, so its traffic grows with the values processed.  The figures
+# describe the kernel sources as they were at that capture: NCU_SRC_SHA is the
+# digest of those sources (kernel_sources_sha()), and when the current
+# sources differ the figures are reported as null.
+NCU_CAPTURE = "ncu capture of 2026-12-04 (profiles/roofline_*.md; half-size fields, traffic x 2)"
+NCU_SRC_SHA = "d9d9b1bc4d8cd15b"
 NCU_TRAFFIC = {
-    "chk<f32,512>": 563637504 + 501929472,        # k_chk_tma<512, 8, lean>
-    "axis_fwd<f32,512>": 536954880 + 483795200,   # k_axis_tma<512, -1, 8>
-    "px<f32,256>": 536950016 + 476919808,         # k_px_tma<256, 2, lean>
-    "xfwd<f64,256>": 537062656 + 1016352000,      # k_xfwd<double, 256, 2, X2>
-    "xfwd<f32,256>": 536927488 + 489845760,       # k_xfwd_tma<256, 2> (entry)
-    "axis_fwd<f64,512>": 1075036000 + 1019320000,  # k_axis<double, 512, -1, 4>
-    "chk_cert<f64,512>": 1105017000 + 3545600,     # k_chk<double, 512, 4> (check only)
+    "chk<f32,512>": 2 * (280070912 + 223096064),      # k_chk_tma<512, 8, lean>
+    "axis_fwd<f32,512>": 2 * (268468992 + 214980096),  # k_axis_tma<512, -1, 8>
+    "px<f32,256>": 2 * (268497152 + 208788736),        # k_px_tma<256, 2, lean>
+    "xfwd<f64,256>": 2 * (268520448 + 479269632),      # k_xfwd<double, 256, 2, X2>
+    "xfwd<f32,256>": 2 * (268483840 + 216777728),      # k_xfwd_tma<256, 2> (entry)
+    "axis_fwd<f64,512>": 2 * (536954624 + 481857536),  # k_axis<double, 512, -1, 4>
+    "chk_cert<f64,512>": 2 * (552233728 + 3274752),    # k_chk<double, 512, 4> (check only)
 }
-NCU_FP64_PIPE = {"xfwd<f64,256>": 0.847, "axis_fwd<f64,512>": 0.846, "chk_cert<f64,512>": 0.841}
+NCU_FP64_PIPE = {"xfwd<f64,256>": 0.854, "axis_fwd<f64,512>": 0.855, "chk_cert<f64,512>": 0.848}
 
 
 def kernel_sources_sha():

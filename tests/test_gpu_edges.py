@@ -105,6 +105,37 @@ def test_certification_of_special_float_values():
         assert plan.check(t, [s], [v * (1 - 1e-8)])[0]["certified"] == 0, scale
 
 
+@pytest.mark.parametrize("n", [4096, 4097])
+def test_certification_1d_special_float_values_and_nonfinite(n):
+    """1D items (even N through the N/2-point transform, odd N through the
+    N-point one): signed zeros, subnormals and extreme scales keep the
+    verdict bracketing the exact violation; a NaN or an Inf is never
+    certified."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    r = np.random.default_rng(6)
+    e0 = W.bimodal_error((n,), 10, dtype=np.float32)
+    idx = r.choice(n, 200, replace=False)
+    e0[idx[:50]] = np.float32(0.0)
+    e0[idx[50:100]] = np.float32(-0.0)
+    e0[idx[100:150]] = (r.uniform(-1, 1, 50) * 1e-40).astype(np.float32)
+    e0[idx[150:]] = (r.uniform(-1, 1, 50) * 1e-30).astype(np.float32)
+    plan = ffcz.Plan([(n,)])
+    for scale in (1.0, 2.0 ** 100, 2.0 ** -100):
+        x = (e0 * np.float32(scale)).astype(np.float32)
+        v = O.f_violation(O.dft(x.astype(np.float64)))
+        s = float(np.max(np.abs(x.astype(np.float64))))
+        t = torch.from_numpy(x.copy()).cuda()
+        assert plan.check(t, [s], [v * (1 + 1e-8)])[0]["certified"] == 1, scale
+        assert plan.check(t, [s], [v * (1 - 1e-8)])[0]["certified"] == 0, scale
+    for bad in (np.nan, np.inf):
+        x = e0.copy()
+        x[n // 3] = bad
+        t = torch.from_numpy(x).cuda()
+        st = plan.check(t, [1e30], [1e30])[0]
+        assert st["certified"] == 0, (bad, st)
+
+
 def test_fp64_repair_after_a_failed_certification():
     """A float32 loop stopped by its cap short of feasibility fails the FP64
     certification; the FP64 repair (Alg. 1 in float64 from the
