@@ -324,11 +324,11 @@ def bytes_per_launch(key, n):
 
 
 def fft_flops_per_point(L):
-    """Real FP64/FP32 operations per complex point of one length-L transform
-    of the Stockham schedule (radix-8, one or two radix-4 stages first):
-    radix-8 butterfly 56 flops per 8 points, radix-4 16 per 4, twiddle
-    products 6 flops each for all but one input of every stage after the
-    first."""
+    """Algorithmic real operations per complex point of one length-L
+    transform, a conventional count independent of the kernels' schedule
+    (radix-8 stages, one or two radix-4 stages first): radix-8 butterfly 56
+    flops per 8 points, radix-4 16 per 4, twiddle products 6 flops each for
+    all but one input of every stage after the first."""
     lg = int(round(math.log2(L)))
     a, b = divmod(lg, 3)
     radices = [8] * a if b == 0 else ([4] + [8] * a if b == 2 else [4, 4] + [8] * (a - 1))
