@@ -702,6 +702,13 @@ def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS, rank=0, world=1, dist=
     gvec = torch.ones_like(ek)
     gin = torch.empty_like(ek)
     vjp_ms, _ = _timed(torch, lambda: vplan.backward(e0.reshape(-1), gvec, gin, [c5["E"]], [c5["D"]], ckpt=ck))
+    # the same with every step's masks kept by the forward (opts.keep_masks):
+    # one forward writing checkpoints and masks, then the adjoint steps alone
+    kplan = _plan(tuple(e0.shape), K, m, 1)
+    kfwd_ms, _ = _timed(torch, lambda: kplan.correct_ckpt(e0.reshape(-1).clone(), [c5["E"]], [c5["D"]], ck))
+    ek = e0.reshape(-1).clone()
+    kplan.correct_ckpt(ek, [c5["E"]], [c5["D"]], ck)
+    kvjp_ms, _ = _timed(torch, lambda: kplan.backward(e0.reshape(-1), gvec, gin, [c5["E"]], [c5["D"]], ckpt=ck))
     del ck, ek, gvec, gin
     n5 = int(np.prod(c5["shape"]))
     out["differentiable"] = {"workload": c5["name"] + f", K={K} forced iterations, checkpoint every {m}",
@@ -712,6 +719,9 @@ def measure_forms(ffcz, torch, fin, it, hbm, which=FORMS, rank=0, world=1, dist=
                              "backward_over_forward": round((fb_ms - fwd_ms) / fwd_ms, 3),
                              "note": "forward_backward includes the float64 torch power-spectrum loss and its backward",
                              "forward_ms_per_iteration": round(fwd_ms / K, 4),
+                             "kept_masks": {"forward_ms": round(kfwd_ms, 3), "backward_vjp_ms": round(kvjp_ms, 3),
+                                            "forward_plus_vjp_ms": round(kfwd_ms + kvjp_ms, 3),
+                                            "replay_forward_plus_vjp_ms": round(fwd_ms + vjp_ms, 3)},
                              "field_GBps_forward": round(4 * n5 / (fwd_ms / 1e3) / 1e9, 3),
                              "loss": loss}
     return out

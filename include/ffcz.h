@@ -94,7 +94,13 @@ typedef struct {
                           values each) and two float32 fields (1, 3); a
                           failed certification is repaired with FP64
                           iterations of Alg. 1 */
-  int32_t reserved_;   /* 0 */
+  int32_t keep_masks;  /* 1: ffcz_correct_ckpt also keeps the clips' masks of
+                          all K steps in the plan (about 1 bit per point for
+                          the spatial and 2 per packed value for the frequency
+                          masks, per step), and ffcz_correct_backward_ckpt
+                          then runs the adjoint steps without replaying the
+                          segments; 2D/3D plans (1D plans replay); default 0:
+                          replay from the checkpoints */
 } ffcz_opts;
 
 /* Per-item results. */

@@ -41,7 +41,7 @@ class Opts(ctypes.Structure):
                 ("chunk", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("count_active", ctypes.c_int32), ("edits", ctypes.c_int32),
                 ("pointwise", ctypes.c_int32), ("method", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32)]
+                ("keep_masks", ctypes.c_int32)]
 
 
 # Projection of the loop (ffcz_opts.method): Alg. 1 or one of the

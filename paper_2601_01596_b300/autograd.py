@@ -18,42 +18,45 @@ from . import Plan
 _plans: dict = {}
 
 
-def _plan(shape, K, m):
-    key = (tuple(shape), int(K), int(m), torch.cuda.current_device())
+def _plan(shape, K, m, keep=0):
+    key = (tuple(shape), int(K), int(m), int(keep), torch.cuda.current_device())
     p = _plans.get(key)
     if p is None:
-        p = Plan([tuple(shape)], min_iters=K, max_iters=K, certify=0, K=K, ckpt_every=m)
+        p = Plan([tuple(shape)], min_iters=K, max_iters=K, certify=0, K=K, ckpt_every=m, keep_masks=int(keep))
         _plans[key] = p
     return p
 
 
 class FFCzCorrect(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, e0, eps_s: float, eps_f: float, K: int = 50, ckpt_every: int = 10):
+    def forward(ctx, e0, eps_s: float, eps_f: float, K: int = 50, ckpt_every: int = 10, keep_masks: int = 0):
         if e0.dtype != torch.float32 or not e0.is_cuda:
             raise TypeError("e0 must be a float32 CUDA tensor")
         e0c = e0.detach().contiguous()
-        plan = _plan(e0c.shape, K, ckpt_every)
+        plan = _plan(e0c.shape, K, ckpt_every, keep_masks)
         e = e0c.clone()
         ckpt = torch.empty(plan.ckpt_floats(), dtype=torch.float32, device=e0c.device)
         plan.correct_ckpt(e.reshape(-1), [eps_s], [eps_f], ckpt)
         ctx.save_for_backward(e0c, ckpt)
-        ctx.cfg = (float(eps_s), float(eps_f), int(K), int(ckpt_every))
+        ctx.cfg = (float(eps_s), float(eps_f), int(K), int(ckpt_every), int(keep_masks))
         return e
 
     @staticmethod
     def backward(ctx, grad_out):
         e0, ckpt = ctx.saved_tensors
-        eps_s, eps_f, K, m = ctx.cfg
-        plan = _plan(e0.shape, K, m)
+        eps_s, eps_f, K, m, keep = ctx.cfg
+        plan = _plan(e0.shape, K, m, keep)
         g = grad_out.detach().to(torch.float32).contiguous()
         gin = torch.empty_like(e0)
         plan.backward(e0.reshape(-1), g.reshape(-1), gin.reshape(-1), [eps_s], [eps_f], ckpt=ckpt)
-        return gin, None, None, None, None
+        return gin, None, None, None, None, None
 
 
-def correct_differentiable(e0, eps_s, eps_f, K=50, ckpt_every=10):
-    return FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every)
+def correct_differentiable(e0, eps_s, eps_f, K=50, ckpt_every=10, keep_masks=0):
+    """keep_masks = 1: the forward keeps every step's clip masks in the plan
+    and the backward runs the adjoint steps without replaying the segments
+    (the masks must belong to this forward: one backward per forward)."""
+    return FFCzCorrect.apply(e0, eps_s, eps_f, K, ckpt_every, keep_masks)
 
 
 _bplans: dict = {}

@@ -271,7 +271,8 @@ struct ffcz_plan_s {
   int* d_loopcount = nullptr;   // bodies executed by the WHILE graph
   int* h_loopcount = nullptr;   // pinned copy
   bool count_pending = false;
-  int while_cap[2][2] = {{-1, -1}, {-1, -1}};   // [precision][checkpoint recording]
+  // [precision][checkpoint recording + 2 x mask keeping]
+  int while_cap[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
   int pending_bodies_per = 0;
 
   // per-kernel profile (events around every launch; graphs off while on)
@@ -299,6 +300,12 @@ struct ffcz_plan_s {
   // forward of the differentiable form: the loop's x pass writes the
   // backward's checkpoints into bw_ck (ffcz_correct_ckpt)
   bool ck_rec = false;
+  // ffcz_correct_ckpt with opts.keep_masks: the masks of every step (x-pass
+  // masks of step t at t px_words, check-pass masks of check t at t chk_words)
+  uint32_t* km_s = nullptr;
+  uint32_t* km_f = nullptr;
+  int km_K = 0;
+  bool km_valid = false;   // they describe the last ffcz_correct_ckpt call
   int64_t px_words = 0, chk_words = 0;       // mask words of one step (all groups)
   std::vector<int64_t> bw_pxoff, bw_chkoff;  // each group's offset in a step's block
 };
@@ -1241,6 +1248,23 @@ void exit1(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
   }
 }
 
+// The differentiable forward keeps every step's masks (2D/3D, float32).
+template <typename T>
+bool keep_masks_rec(const ffcz_plan_s* p) {
+  return sizeof(T) == 4 && p->ck_rec && p->opts.keep_masks && p->ndim > 1 && p->km_s;
+}
+int64_t px_mask_thr(const DevGroup& dg);
+int64_t chk_mask_thr(const DevGroup& dg);
+// x pass (s-masks) or check pass (f-masks) of group g records into the
+// plan's per-step mask store
+void km_args(ffcz_plan_s* p, Args& a, int g, bool chk) {
+  const DevGroup& dg = p->groups[g];
+  a.mode |= M_RECORD;
+  a.mask = chk ? p->km_f + p->bw_chkoff[g] : p->km_s + p->bw_pxoff[g];
+  a.mask_thr = chk ? chk_mask_thr(dg) : px_mask_thr(dg);
+  a.mask_step = chk ? p->chk_words : p->px_words;
+}
+
 template <typename T>
 void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStream_t s) {
   if (p->ndim == 1) { entry1<T>(p, B, e, measure_preclip, s); return; }
@@ -1263,7 +1287,8 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
       launch_x<T>(XFWD, dg.M, dg.wx, a, dg.rows, dg.count, s);
     }
   }
-  for (auto& dg : p->groups) {
+  for (size_t g = 0; g < p->groups.size(); ++g) {
+    const DevGroup& dg = p->groups[g];
     Args a = make_args<T>(p, dg, B.b0, B.b1, p->d_st);
     if (dg.ndim == 3) {
       set_tw<T>(a, p->tb, dg.Ny);
@@ -1271,6 +1296,7 @@ void entry(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStrea
     }
     set_tw<T>(a, p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
+    if (keep_masks_rec<T>(p)) km_args(p, a, (int)g, true);
     launch_chk<T>(dg.Nz, dg.wc, a, dg.ndim == 3 ? dg.Ny : 1, dg.M, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
@@ -1313,6 +1339,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
       a.ckpt = p->bw_ck;
       a.ckpt_every = p->bw_m;
     }
+    if (keep_masks_rec<T>(p)) km_args(p, a, g, false);
     args[g] = a;
   }
   if (!multi_launch<T>(p, MK_PX, args, s))
@@ -1341,6 +1368,7 @@ void body(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
     a.sel_in = a.sel_out = S_CUR;
     set_tw<T>(a, p->tb, dg.Nz);
     a.mode = M_CLIP | cnt_flag(p);
+    if (keep_masks_rec<T>(p)) km_args(p, a, g, true);
     args[g] = a;
   }
   if (!multi_launch<T>(p, MK_CHK, args, s))
@@ -1401,7 +1429,7 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, const int* n_active, in
 // and precision, replayed by one cudaGraphLaunch per call).
 template <typename T>
 void run_while_graph(ffcz_plan_s* p, LoopBufs B, int cap) {
-  const int ckk = (sizeof(T) == 4 && p->ck_rec) ? 1 : 0;
+  const int ckk = ((sizeof(T) == 4 && p->ck_rec) ? 1 : 0) + (keep_masks_rec<T>(p) ? 2 : 0);
   const auto key = std::make_pair(-(int)sizeof(T), ckk);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
@@ -1452,7 +1480,8 @@ void run_chunk(ffcz_plan_s* p, LoopBufs B, int C) {
     for (int i = 0; i < C; ++i) body<T>(p, B, p->stream);
     return;
   }
-  const auto key = std::make_pair((int)sizeof(T) + ((sizeof(T) == 4 && p->ck_rec) ? 16 : 0), C);
+  const auto key = std::make_pair((int)sizeof(T) + ((sizeof(T) == 4 && p->ck_rec) ? 16 : 0) +
+                                      (keep_masks_rec<T>(p) ? 32 : 0), C);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     cudaGraph_t g;
@@ -1950,7 +1979,7 @@ void run_loop(ffcz_plan_s* p, float* e, bool only_uncert) {
     // the whole loop on the device (conditional WHILE node); graphs are
     // rebuilt when the cap changes
     const int slot = sizeof(T) == 4 ? 0 : 1;
-    const int ckk = (sizeof(T) == 4 && p->ck_rec) ? 1 : 0;
+    const int ckk = ((sizeof(T) == 4 && p->ck_rec) ? 1 : 0) + (keep_masks_rec<T>(p) ? 2 : 0);
     const auto key = std::make_pair(-(int)sizeof(T), ckk);
     if (p->while_cap[slot][ckk] != cap && p->graphs.count(key)) {
       cudaGraphExecDestroy(p->graphs[key]);
@@ -2714,22 +2743,27 @@ ffcz_status backward_impl(ffcz_plan_s* p, const float* e0, const float* gout, fl
     }
   }
   if (p->ndim == 1) return backward1_tail(p, e0, gout, gin, ck, ckpt_in, B, GB);
-  // Adjoint, segment by segment from the last.
+  // Adjoint, segment by segment from the last.  With the masks the forward
+  // kept (opts.keep_masks), no segment is replayed: step t takes the x-pass
+  // masks of step t + 1 and the check-pass masks of check t.
+  const bool kept = ckpt_in && p->opts.keep_masks && p->km_valid && p->km_K == K;
   set_t(p, p->d_st2, 0);
   bool first = true;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int t0 = seg * m, t1 = std::min(K, t0 + m);
-    // replay the segment from its checkpoint, recording masks of steps t0..t1-1
-    set_t(p, p->d_st, t0);
-    replay_entry(p, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
-    for (int b = t0 + 1; b <= t1; ++b) {
-      advance(p, p->d_st);
-      replay_body(p, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
-                  b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr, b < t1);
+    if (!kept) {
+      // replay the segment from its checkpoint, recording masks of steps t0..t1-1
+      set_t(p, p->d_st, t0);
+      replay_entry(p, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
+      for (int b = t0 + 1; b <= t1; ++b) {
+        advance(p, p->d_st);
+        replay_body(p, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
+                    b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr, b < t1);
+      }
     }
     for (int t = t1 - 1; t >= t0; --t) {
-      uint32_t* sm = p->bw_smask + (int64_t)(t - t0) * p->px_words;
-      uint32_t* fm = p->bw_fmask + (int64_t)(t - t0) * p->chk_words;
+      uint32_t* sm = kept ? p->km_s + (int64_t)(t + 1) * p->px_words : p->bw_smask + (int64_t)(t - t0) * p->px_words;
+      uint32_t* fm = kept ? p->km_f + (int64_t)t * p->chk_words : p->bw_fmask + (int64_t)(t - t0) * p->chk_words;
       if (!first) advance(p, p->d_st2);
       for (size_t gidx = 0; gidx < p->groups.size(); ++gidx) {
         const DevGroup& dg = p->groups[gidx];
@@ -3156,7 +3190,7 @@ void ffcz_default_opts(ffcz_opts* o) {
   o->edits = 0;
   o->pointwise = 0;
   o->method = 0;
-  o->reserved_ = 0;
+  o->keep_masks = 0;
 }
 
 ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t batch,
@@ -3174,6 +3208,7 @@ ffcz_status ffcz_plan(ffcz_plan_t* out, int ndim, const int64_t* shapes, int64_t
     if (!(o.shrink >= 0.0 && o.shrink < 0.5)) fail(FFCZ_ERR_INVALID, "shrink must be in [0, 0.5)");
     if (o.max_iters < 0 || o.min_iters < 0) fail(FFCZ_ERR_INVALID, "iteration limits must be >= 0");
     if (o.method < PV_POCS || o.method > PV_ADMM) fail(FFCZ_ERR_INVALID, "method must be 0..3");
+    if (o.keep_masks != 0 && o.keep_masks != 1) fail(FFCZ_ERR_INVALID, "keep_masks must be 0 or 1");
     if (o.method != PV_POCS && (o.edits || o.pointwise || o.precision != 32))
       fail(FFCZ_ERR_UNSUPPORTED, "projection variants run float32 loops without edits or pointwise bounds");
     for (int64_t i = 0; i < batch; ++i) {
@@ -3791,12 +3826,21 @@ ffcz_status ffcz_correct_ckpt(ffcz_plan_t plan, float* e, const double* eps_s, c
                              "and no certification");
     CK(cudaSetDevice(plan->device));
     bw_alloc(plan);
+    plan->km_valid = false;
+    if (o.keep_masks && plan->ndim > 1 && plan->km_K != o.K) {
+      // one mask block per step t = 0..K (x-pass masks of steps 1..K,
+      // check-pass masks of checks 0..K - 1)
+      plan->km_s = (uint32_t*)dalloc(plan, sizeof(uint32_t) * plan->px_words * (o.K + 1));
+      plan->km_f = (uint32_t*)dalloc(plan, sizeof(uint32_t) * plan->chk_words * (o.K + 1));
+      plan->km_K = o.K;
+    }
     plan->ck_rec = true;
     struct Off { ffcz_plan_s* p; ~Off() { p->ck_rec = false; } } off{plan};
     const ffcz_status st = correct_impl(plan, e, eps_s, eps_f, stats);
     CK(cudaMemcpyAsync(ckpt, plan->bw_ck, sizeof(float) * ffcz_ckpt_floats(plan), cudaMemcpyDeviceToDevice,
                        plan->stream));
     CK(cudaStreamSynchronize(plan->stream));
+    plan->km_valid = o.keep_masks && plan->ndim > 1 && plan->km_K == o.K;
     return st;
   });
 }

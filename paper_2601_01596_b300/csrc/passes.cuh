@@ -100,6 +100,7 @@ struct Args {
   const float* ein;        // separate float32 input (adjoint entry)
   uint32_t* mask;          // mask words (one per thread per pass)
   int64_t mask_thr;        // mask threads per group member (member gi's words start at gi mask_thr MW)
+  int64_t mask_step;       // M_RECORD in the loop: words per iteration (the masks of iteration t at t mask_step)
   float* ckpt;             // checkpoint buffer for e_t
   int64_t ckpt_stride;     // floats per checkpoint (all items of the plan)
   int ckpt_every;
@@ -758,7 +759,7 @@ __device__ __forceinline__ unsigned long long px_core(const Args& a, const ItemP
     MaskBits<MW> mb;
     mb.clear();
     s_clip_full<T, V, MW>(v, Es, count, mb, cnt, ck, j, NT);
-    if ((a.mode & M_RECORD) && live) mb.store(a.mask, mthr);
+    if ((a.mode & M_RECORD) && live) mb.store(a.mask + (int64_t)t_it * a.mask_step, mthr);
   } else if (need_clip) {
     // lean path: only warps holding a value outside the s-cube clip
     const bool rec_s = ED && edrow != nullptr && live;   // ED = false: the lean form
@@ -1269,7 +1270,7 @@ __device__ __forceinline__ void chk_core(const Args& a, const ItemParams& p, Ite
       mb.fill();   // nothing clipped
     }
   }
-  if (rec && c.live) mb.store(a.mask, mthr);
+  if (rec && c.live) mb.store(a.mask + (int64_t)t_chk * a.mask_step, mthr);
   if (acc_vb) {
     // persistent callers reduce once per CTA after their last tile
     *acc_vb = max(*acc_vb, mx.dbits(bad));

@@ -376,3 +376,30 @@ def test_1d_batched_backward_equals_single_items():
         one = _gpu_backward(sh, items[i], gs[i], Es[i], Ds[i], K, m)
         assert np.array_equal(got[off:off + sh[0]], one), i
         off += sh[0]
+
+
+@pytest.mark.parametrize("shapes,K,m", [([(16, 16, 32)], 6, 2), ([(32, 64), (64, 32), (32, 64)], 5, 10),
+                                        ([(256, 8, 256)], 12, 4)])
+def test_kept_masks_backward_equals_replay(shapes, K, m):
+    """opts.keep_masks: the forward keeps every step's masks and the backward
+    skips the segment replays; the product is the replayed one, bit for bit."""
+    import torch
+    import paper_2601_01596_b300 as ffcz
+    items = [W.bimodal_error(sh, 80 + i, dtype=np.float32) for i, sh in enumerate(shapes)]
+    gs = [np.random.default_rng(81 + i).standard_normal(sh).astype(np.float32) for i, sh in enumerate(shapes)]
+    Es = [1.0] * len(shapes)
+    Ds = [0.4 * O.f_violation(O.dft(x.astype(np.float64))) for x in items]
+    te0 = torch.from_numpy(np.concatenate([x.reshape(-1) for x in items])).cuda()
+    tg = torch.from_numpy(np.concatenate([x.reshape(-1) for x in gs])).cuda()
+    out = {}
+    for keep in (0, 1):
+        plan = ffcz.Plan(shapes, K=K, ckpt_every=m, min_iters=K, max_iters=K, certify=0, keep_masks=keep)
+        ck = torch.empty(plan.ckpt_floats(), dtype=torch.float32, device="cuda")
+        e = te0.clone()
+        plan.correct_ckpt(e, Es, Ds, ck)
+        gi = torch.empty_like(te0)
+        plan.backward(te0, tg, gi, Es, Ds, ckpt=ck)
+        out[keep] = (e.cpu().numpy(), gi.cpu().numpy())
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.abs(out[1][1]).max() > 0
