@@ -49,17 +49,17 @@ FP64_TFLOPS_NOMINAL = 1.25   # nominal dense FP64 rate of a B300 (context only)
 # digest of those sources (kernel_sources_sha()), and when the current
 # sources differ the figures are reported as null.
 NCU_CAPTURE = "ncu capture of 2026-12-04 (profiles/roofline_*.md; half-size fields, traffic x 2)"
-NCU_SRC_SHA = "d9d9b1bc4d8cd15b"
+NCU_SRC_SHA = "a3922083cc7ba78a"
 NCU_TRAFFIC = {
-    "chk<f32,512>": 2 * (280070912 + 223096064),      # k_chk_tma<512, 8, lean>
-    "axis_fwd<f32,512>": 2 * (268468992 + 214980096),  # k_axis_tma<512, -1, 8>
-    "px<f32,256>": 2 * (268497152 + 208788736),        # k_px_tma<256, 2, lean>
-    "xfwd<f64,256>": 2 * (268520448 + 479269632),      # k_xfwd<double, 256, 2, X2>
-    "xfwd<f32,256>": 2 * (268483840 + 216777728),      # k_xfwd_tma<256, 2> (entry)
-    "axis_fwd<f64,512>": 2 * (536954624 + 481857536),  # k_axis<double, 512, -1, 4>
-    "chk_cert<f64,512>": 2 * (552233728 + 3274752),    # k_chk<double, 512, 4> (check only)
+    "chk<f32,512>": 2 * (280047616 + 223072256),      # k_chk_tma<512, 8, lean>
+    "axis_fwd<f32,512>": 2 * (268473856 + 215547904),  # k_axis_tma<512, -1, 8>
+    "px<f32,256>": 2 * (268479232 + 208703744),        # k_px_tma<256, 2, lean>
+    "xfwd<f64,256>": 2 * (269651712 + 479538688),      # k_xfwd<double, 256, 2, X2>
+    "xfwd<f32,256>": 2 * (268478720 + 217321472),      # k_xfwd_tma<256, 2> (entry)
+    "axis_fwd<f64,512>": 2 * (537792512 + 481961984),  # k_axis<double, 512, -1, 4>
+    "chk_cert<f64,512>": 2 * (551576576 + 3133184),    # k_chk<double, 512, 4> (check only)
 }
-NCU_FP64_PIPE = {"xfwd<f64,256>": 0.854, "axis_fwd<f64,512>": 0.855, "chk_cert<f64,512>": 0.848}
+NCU_FP64_PIPE = {"xfwd<f64,256>": 0.854, "axis_fwd<f64,512>": 0.854, "chk_cert<f64,512>": 0.848}
 
 
 def kernel_sources_sha():
