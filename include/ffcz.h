@@ -99,8 +99,8 @@ typedef struct {
                           the spatial and 2 per packed value for the frequency
                           masks, per step), and ffcz_correct_backward_ckpt
                           then runs the adjoint steps without replaying the
-                          segments; 2D/3D plans (1D plans replay); default 0:
-                          replay from the checkpoints */
+                          segments (1D items: one byte per point and per bin
+                          per step); default 0: replay from the checkpoints */
 } ffcz_opts;
 
 /* Per-item results. */

@@ -249,7 +249,9 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
           else { mx.add(X.x); mx.add(X.y); }
           bad |= (X.x != X.x) | (X.y != X.y);
         }
-        uint8_t* fmk = (a.mode & (M_MASK | M_RECORD)) ? reinterpret_cast<uint8_t*>(a.mask) + a.g.eoff[gi] : nullptr;
+        uint8_t* fmk = (a.mode & (M_MASK | M_RECORD))
+                           ? reinterpret_cast<uint8_t*>(a.mask + (int64_t)t_it * a.mask_step) + a.g.eoff[gi]
+                           : nullptr;
         if (a.mode & M_MASK) {   // adjoint: M_f
           const unsigned b = in_range ? fmk[k] : 0u;
           X = mk<T>((b & 1u) ? X.x : T(0), (b & 2u) ? X.y : T(0));
@@ -322,7 +324,7 @@ __device__ __forceinline__ void k1_col_body(const Args& a, const int bx_, const 
           if (count && in_range) cnt += (cx != x);
           if (op == OP1_SCLIP && a.ed_s && in_range && cx != x) atomicAdd(eo_s + n, (float)(cx - x));
           if (op == OP1_SCLIP && (a.mode & M_RECORD) && in_range)
-            reinterpret_cast<uint8_t*>(a.mask)[a.g.eoff[gi] + n] = (uint8_t)(cx == x);
+            reinterpret_cast<uint8_t*>(a.mask + (int64_t)t_it * a.mask_step)[a.g.eoff[gi] + n] = (uint8_t)(cx == x);
           x = cx;
         }
         if (op == OP1_SCLIP && ckp && in_range) ckp[n] = (float)x;   // checkpoint e_t

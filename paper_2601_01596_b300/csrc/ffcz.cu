@@ -1158,6 +1158,28 @@ struct LoopBufs {
   void* b1;
 };
 
+// The differentiable forward keeps every step's masks (float32 loops).
+template <typename T>
+bool keep_masks_rec(const ffcz_plan_s* p) {
+  return sizeof(T) == 4 && p->ck_rec && p->opts.keep_masks && p->km_s;
+}
+int64_t px_mask_thr(const DevGroup& dg);
+int64_t chk_mask_thr(const DevGroup& dg);
+// x pass (s-masks) or check pass (f-masks) of group g records into the
+// plan's per-step mask store
+void km_args(ffcz_plan_s* p, Args& a, int g, bool chk) {
+  const DevGroup& dg = p->groups[g];
+  a.mode |= M_RECORD;
+  if (p->ndim == 1) {   // mask bytes at the items' point offsets
+    a.mask = chk ? p->km_f : p->km_s;
+    a.mask_step = chk ? p->chk_words : p->px_words;
+    return;
+  }
+  a.mask = chk ? p->km_f + p->bw_chkoff[g] : p->km_s + p->bw_pxoff[g];
+  a.mask_thr = chk ? chk_mask_thr(dg) : px_mask_thr(dg);
+  a.mask_step = chk ? p->chk_words : p->px_words;
+}
+
 template <typename T>
 void entry1(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStream_t s) {
   for (auto& dg : p->groups) {
@@ -1185,6 +1207,7 @@ void entry1(ffcz_plan_s* p, LoopBufs B, float* e, bool measure_preclip, cudaStre
     launch_row1<T>(dg.P2, dg.w1r, a, dg.P1, dg.count, s);
     col1_args<T>(p, a, dg, OP1_FCLIP);
     a.mode = M_CLIP | cnt_flag(p);
+    if (keep_masks_rec<T>(p)) km_args(p, a, 0, true);
     launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
   k_decide<<<(unsigned)((p->batch + 255) / 256), 256, 0, s>>>(p->d_prm, p->d_st, (int)p->batch,
@@ -1214,9 +1237,14 @@ void body1(ffcz_plan_s* p, LoopBufs B, cudaStream_t s) {
           a.ckpt = p->bw_ck;
           a.ckpt_every = p->bw_m;
         }
+        if (keep_masks_rec<T>(p)) km_args(p, a, g, false);
       }
       if (step == 2) { row1_args<T>(p, a, dg, OP1_CONV); a.mode = 0; }
-      if (step == 3) { col1_args<T>(p, a, dg, OP1_FCLIP); a.mode = M_CLIP | cnt_flag(p); }
+      if (step == 3) {
+        col1_args<T>(p, a, dg, OP1_FCLIP);
+        a.mode = M_CLIP | cnt_flag(p);
+        if (keep_masks_rec<T>(p)) km_args(p, a, g, true);
+      }
       args[g] = a;
     }
     if (multi_launch<T>(p, row ? MK_ROW1 : MK_COL1, args, s)) continue;
@@ -1246,23 +1274,6 @@ void exit1(ffcz_plan_s* p, LoopBufs B, float* e, cudaStream_t s) {
     a.mode = s_check_of<T>(p) ? 0 : M_CLIP;
     launch_col1<T>(dg.P1, dg.w1c, a, dg.P2, dg.count, s);
   }
-}
-
-// The differentiable forward keeps every step's masks (2D/3D, float32).
-template <typename T>
-bool keep_masks_rec(const ffcz_plan_s* p) {
-  return sizeof(T) == 4 && p->ck_rec && p->opts.keep_masks && p->ndim > 1 && p->km_s;
-}
-int64_t px_mask_thr(const DevGroup& dg);
-int64_t chk_mask_thr(const DevGroup& dg);
-// x pass (s-masks) or check pass (f-masks) of group g records into the
-// plan's per-step mask store
-void km_args(ffcz_plan_s* p, Args& a, int g, bool chk) {
-  const DevGroup& dg = p->groups[g];
-  a.mode |= M_RECORD;
-  a.mask = chk ? p->km_f + p->bw_chkoff[g] : p->km_s + p->bw_pxoff[g];
-  a.mask_thr = chk ? chk_mask_thr(dg) : px_mask_thr(dg);
-  a.mask_step = chk ? p->chk_words : p->px_words;
 }
 
 template <typename T>
@@ -2660,21 +2671,26 @@ ffcz_status backward1_tail(ffcz_plan_s* p, const float* e0, const float* gout, f
   const int K = p->opts.K, m = p->opts.ckpt_every;
   const int64_t N = p->total;
   const int nseg = (K + m - 1) / m;
+  // with the masks the forward kept (opts.keep_masks) no segment is replayed
+  const bool kept = ckpt_in && p->opts.keep_masks && p->km_valid && p->km_K == K;
   set_t(p, p->d_st2, 0);
   bool first = true;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int t0 = seg * m, t1 = std::min(K, t0 + m);
-    set_t(p, p->d_st, t0);
-    replay_entry1(p, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
-    for (int b = t0 + 1; b <= t1; ++b) {
-      advance(p, p->d_st);
-      replay_body1(p, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
-                   b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr, b < t1);
+    if (!kept) {
+      set_t(p, p->d_st, t0);
+      replay_entry1(p, B, const_cast<float*>(ck) + (int64_t)seg * N, p->bw_fmask);
+      for (int b = t0 + 1; b <= t1; ++b) {
+        advance(p, p->d_st);
+        replay_body1(p, B, p->bw_smask + (int64_t)(b - 1 - t0) * p->px_words,
+                     b < t1 ? p->bw_fmask + (int64_t)(b - t0) * p->chk_words : nullptr, nullptr, b < t1);
+      }
     }
     for (int t = t1 - 1; t >= t0; --t) {
       if (!first) advance(p, p->d_st2);
-      adjoint_step1(p, GB, gout, p->bw_smask + (int64_t)(t - t0) * p->px_words,
-                    p->bw_fmask + (int64_t)(t - t0) * p->chk_words, first);
+      uint32_t* sm = kept ? p->km_s + (int64_t)(t + 1) * p->px_words : p->bw_smask + (int64_t)(t - t0) * p->px_words;
+      uint32_t* fm = kept ? p->km_f + (int64_t)t * p->chk_words : p->bw_fmask + (int64_t)(t - t0) * p->chk_words;
+      adjoint_step1(p, GB, gout, sm, fm, first);
       first = false;
     }
   }
@@ -3827,7 +3843,7 @@ ffcz_status ffcz_correct_ckpt(ffcz_plan_t plan, float* e, const double* eps_s, c
     CK(cudaSetDevice(plan->device));
     bw_alloc(plan);
     plan->km_valid = false;
-    if (o.keep_masks && plan->ndim > 1 && plan->km_K != o.K) {
+    if (o.keep_masks && plan->km_K != o.K) {
       // one mask block per step t = 0..K (x-pass masks of steps 1..K,
       // check-pass masks of checks 0..K - 1)
       plan->km_s = (uint32_t*)dalloc(plan, sizeof(uint32_t) * plan->px_words * (o.K + 1));
@@ -3840,7 +3856,7 @@ ffcz_status ffcz_correct_ckpt(ffcz_plan_t plan, float* e, const double* eps_s, c
     CK(cudaMemcpyAsync(ckpt, plan->bw_ck, sizeof(float) * ffcz_ckpt_floats(plan), cudaMemcpyDeviceToDevice,
                        plan->stream));
     CK(cudaStreamSynchronize(plan->stream));
-    plan->km_valid = o.keep_masks && plan->ndim > 1 && plan->km_K == o.K;
+    plan->km_valid = o.keep_masks && plan->km_K == o.K;
     return st;
   });
 }

@@ -379,7 +379,7 @@ def test_1d_batched_backward_equals_single_items():
 
 
 @pytest.mark.parametrize("shapes,K,m", [([(16, 16, 32)], 6, 2), ([(32, 64), (64, 32), (32, 64)], 5, 10),
-                                        ([(256, 8, 256)], 12, 4)])
+                                        ([(256, 8, 256)], 12, 4), ([(3000,), (1500,), (3001,)], 6, 4)])
 def test_kept_masks_backward_equals_replay(shapes, K, m):
     """opts.keep_masks: the forward keeps every step's masks and the backward
     skips the segment replays; the product is the replayed one, bit for bit."""
